@@ -1,0 +1,336 @@
+"""Seeded synthetic initial data, shared by the CUDA path and the oracle.
+
+This module holds no arithmetic of the scheme itself (no primitive/conserved
+map, no reconstruction, no flux): it only lays out primitive fields
+(rho, v^x, v^y, v^z, p at cell centres) and the staggered face field
+B~ = sqrt(gamma) B, built as the discrete curl of an edge-centred vector
+potential so that the discrete divergence vanishes to rounding.  Each side
+converts these to conserved variables with its own code.
+
+Workloads (all seeded with ``numpy.random.default_rng(seed)``):
+
+* ``smooth_box``: periodic special-relativistic MHD turbulence-like box in
+  [0,1)^3 -- a sum of random-phase Fourier modes for rho, low-pass-filtered
+  white noise for v, and a random low-k vector potential for B.  Used at 32^3
+  (10 steps, the parity size), 256^3 (the throughput size) and 512^3.
+* ``sweep_box``: the 256^3 variant with rho in [0.5, 1.5], log-uniform p in
+  [0.1, 1], |v| <= 0.6 and B scaled so that the plasma beta spans ~1-100.
+* ``linear_wave`` / ``alfven_wave``: 1-D smooth problems for convergence pins.
+
+Host layouts: prims (5, nz, ny, nx), x fastest; face field flat, in the order
+Bx (nz, ny, nx+1), By (nz, ny+1, nx), Bz (nz+1, ny, nx), face i-1/2 at index i.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+PERIODIC, OUTFLOW, AXIS = 0, 1, 2
+
+
+@dataclass
+class Problem:
+    name: str
+    n: tuple
+    x0: tuple
+    dx: tuple
+    bc: tuple = (PERIODIC,) * 6
+    metric: int = 0          # 0 flat Cartesian, 1 Kerr-Schild (ln r, theta, phi)
+    spin: float = 0.0
+    gamma: float = 4.0 / 3.0
+    cfl: float = 0.4
+    floors: bool = False
+    rho_floor: float = 0.0
+    rho_floor_pow: float = 0.0
+    p_floor: float = 0.0
+    p_floor_pow: float = 0.0
+    steps: int = 10
+    seed: int = 0
+    prims: np.ndarray = field(default=None, repr=False)   # (5, nz, ny, nx)
+    bface: np.ndarray = field(default=None, repr=False)   # flat host face layout
+
+    @property
+    def ncells(self) -> int:
+        return int(self.n[0]) * int(self.n[1]) * int(self.n[2])
+
+
+SEED_BASE = 1810_04597
+
+
+# ------------------------------------------------------------------ helpers
+
+def _axes(n, x0, dx, off):
+    """1-D coordinates of points at offset `off` (0 = centre, -0.5 = lower
+    face) along each axis; face/edge arrays carry one extra point."""
+    out = []
+    for d in range(3):
+        m = n[d] + (1 if off[d] != 0.0 else 0)
+        out.append(x0[d] + (np.arange(m) + 0.5 + off[d]) * dx[d])
+    return out
+
+
+def _mode_sum(modes, xs):
+    """sum_m a_m cos(2 pi k_m . x + phi_m) on the tensor grid xs = (x, y, z);
+    returns an array (nz, ny, nx)."""
+    x, y, z = xs
+    acc = np.zeros((len(z), len(y), len(x)))
+    for (kx, ky, kz, amp, ph) in modes:
+        ex = np.exp(2j * np.pi * kx * x)
+        ey = np.exp(2j * np.pi * ky * y)
+        ez = np.exp(2j * np.pi * kz * z + 1j * ph)
+        acc += amp * np.real(ez[:, None, None] * ey[None, :, None] * ex[None, None, :])
+    return acc
+
+
+def _random_k(rng, kmax):
+    while True:
+        k = rng.integers(-kmax, kmax + 1, size=3)
+        if np.max(np.abs(k)) >= 1:
+            return k
+
+
+def _random_modes(rng, count, kmax, amp_lo=0.5, amp_hi=1.0):
+    modes = []
+    for _ in range(count):
+        k = _random_k(rng, kmax)
+        modes.append((int(k[0]), int(k[1]), int(k[2]), float(rng.uniform(amp_lo, amp_hi)),
+                      float(rng.uniform(0.0, 2.0 * np.pi))))
+    return modes
+
+
+def _lowpass_noise(rng, n, kmax, lo, hi):
+    """White noise U[lo, hi] per cell, keeping only Fourier modes with
+    |k|_inf <= kmax (k in units of the box)."""
+    w = rng.uniform(lo, hi, size=(n[2], n[1], n[0]))
+    f = np.fft.rfftn(w)
+    kz = np.fft.fftfreq(n[2]) * n[2]
+    ky = np.fft.fftfreq(n[1]) * n[1]
+    kx = np.fft.rfftfreq(n[0]) * n[0]
+    mask = ((np.abs(kz)[:, None, None] <= kmax) & (np.abs(ky)[None, :, None] <= kmax)
+            & (np.abs(kx)[None, None, :] <= kmax))
+    f = f * mask
+    return np.fft.irfftn(f, s=(n[2], n[1], n[0]), axes=(0, 1, 2))
+
+
+def curl_faces(n, dx, Ax, Ay, Az):
+    """Face field from edge-centred vector potential components:
+    Ax (nz+1, ny+1, nx) at (i, j-1/2, k-1/2), Ay (nz+1, ny, nx+1) at
+    (i-1/2, j, k-1/2), Az (nz, ny+1, nx+1) at (i-1/2, j-1/2, k).
+    Returns the flat host face layout (Bx, By, Bz)."""
+    bx = (Az[:, 1:, :] - Az[:, :-1, :]) / dx[1] - (Ay[1:, :, :] - Ay[:-1, :, :]) / dx[2]
+    by = (Ax[1:, :, :] - Ax[:-1, :, :]) / dx[2] - (Az[:, :, 1:] - Az[:, :, :-1]) / dx[0]
+    bz = (Ay[:, :, 1:] - Ay[:, :, :-1]) / dx[0] - (Ax[:, 1:, :] - Ax[:, :-1, :]) / dx[1]
+    return bx, by, bz
+
+
+def pack_faces(bx, by, bz):
+    return np.concatenate([bx.reshape(-1), by.reshape(-1), bz.reshape(-1)])
+
+
+def _potential_faces(rng, n, x0, dx, kmax, count):
+    """Face field of a random periodic low-k vector potential (unit scale)."""
+    Ax = _mode_sum(_random_modes(rng, count, kmax), _axes(n, x0, dx, (0.0, -0.5, -0.5)))
+    Ay = _mode_sum(_random_modes(rng, count, kmax), _axes(n, x0, dx, (-0.5, 0.0, -0.5)))
+    Az = _mode_sum(_random_modes(rng, count, kmax), _axes(n, x0, dx, (-0.5, -0.5, 0.0)))
+    return curl_faces(n, dx, Ax, Ay, Az)
+
+
+def _cell_b_mag2(bx, by, bz):
+    """|B|^2 from face averages (flat metric), only for scaling the seed."""
+    cx = 0.5 * (bx[:, :, 1:] + bx[:, :, :-1])
+    cy = 0.5 * (by[:, 1:, :] + by[:, :-1, :])
+    cz = 0.5 * (bz[1:, :, :] + bz[:-1, :, :])
+    return cx * cx + cy * cy + cz * cz
+
+
+# ------------------------------------------------------------------ workloads
+
+def smooth_box(n: int = 32, seed: int | None = None, steps: int = 10) -> Problem:
+    """Periodic SRMHD box in [0,1)^3, Gamma = 4/3:
+    rho = 1 + 0.1 * sum_{m=1..4} (1/4) cos(2 pi k_m.x + phi_m), 1 <= |k_m|_inf <= 3;
+    p = 1; each v^i low-pass (|k|_inf <= 3) white noise rescaled to
+    max|v^i| = 0.3; B = discrete curl of a random low-k vector potential,
+    scaled so that max over faces |B~| = 0.1."""
+    seed = SEED_BASE + 1 if seed is None else seed
+    rng = np.random.default_rng(seed)
+    nn = (n, n, n)
+    x0 = (0.0, 0.0, 0.0)
+    dx = (1.0 / n,) * 3
+    cen = _axes(nn, x0, dx, (0.0, 0.0, 0.0))
+    modes = [(int(k[0]), int(k[1]), int(k[2]), 0.25, float(rng.uniform(0, 2 * np.pi)))
+             for k in (_random_k(rng, 3) for _ in range(4))]
+    rho = 1.0 + 0.1 * _mode_sum(modes, cen)
+    p = np.ones_like(rho)
+    v = []
+    for _ in range(3):
+        f = _lowpass_noise(rng, nn, 3, -0.3, 0.3)
+        v.append(f * (0.3 / np.max(np.abs(f))))
+    bx, by, bz = _potential_faces(rng, nn, x0, dx, 3, 4)
+    s = 0.1 / max(np.max(np.abs(bx)), np.max(np.abs(by)), np.max(np.abs(bz)))
+    prims = np.stack([rho, v[0], v[1], v[2], p])
+    return Problem(name=f"smooth_box_{n}", n=nn, x0=x0, dx=dx, steps=steps, seed=seed,
+                   prims=prims, bface=pack_faces(bx * s, by * s, bz * s))
+
+
+def sweep_box(n: int = 256, seed: int | None = None, steps: int = 20) -> Problem:
+    """Periodic SRMHD box in [0,1)^3, Gamma = 4/3, smooth fields with
+    |k|_inf <= 4: rho in [0.5, 1.5]; log10 p in [-1, 0]; |v| <= 0.6; B from a
+    random vector potential scaled so that the median plasma beta
+    2p/B^2 is 10 (beta then spans roughly 1-100)."""
+    seed = SEED_BASE + 2 if seed is None else seed
+    rng = np.random.default_rng(seed)
+    nn = (n, n, n)
+    x0 = (0.0, 0.0, 0.0)
+    dx = (1.0 / n,) * 3
+    cen = _axes(nn, x0, dx, (0.0, 0.0, 0.0))
+
+    def unit_field():
+        f = _mode_sum(_random_modes(rng, 6, 4), cen)
+        return f / np.max(np.abs(f))
+
+    rho = 1.0 + 0.5 * unit_field()
+    p = 10.0 ** (-0.5 + 0.5 * unit_field())
+    v = [unit_field() for _ in range(3)]
+    vmag = np.sqrt(v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
+    s = 0.6 / np.max(vmag)
+    v = [c * s for c in v]
+    bx, by, bz = _potential_faces(rng, nn, x0, dx, 4, 6)
+    b2 = _cell_b_mag2(bx, by, bz)
+    beta_unit = 2.0 * p / np.maximum(b2, 1e-300)
+    scale = np.sqrt(np.median(beta_unit) / 10.0)
+    prims = np.stack([rho, v[0], v[1], v[2], p])
+    return Problem(name=f"sweep_box_{n}", n=nn, x0=x0, dx=dx, steps=steps, seed=seed,
+                   prims=prims, bface=pack_faces(bx * scale, by * scale, bz * scale))
+
+
+def uniform_box(n=(8, 8, 8), rho=1.0, v=(0.2, -0.1, 0.05), p=0.7, B=(0.3, 0.2, -0.1)) -> Problem:
+    """Every cell the same state (face field uniform)."""
+    nn = tuple(int(x) for x in n)
+    nx, ny, nz = nn
+    dx = tuple(1.0 / m for m in nn)
+    prims = np.empty((5, nz, ny, nx))
+    prims[0] = rho
+    prims[1] = v[0]
+    prims[2] = v[1]
+    prims[3] = v[2]
+    prims[4] = p
+    bx = np.full((nz, ny, nx + 1), B[0])
+    by = np.full((nz, ny + 1, nx), B[1])
+    bz = np.full((nz + 1, ny, nx), B[2])
+    return Problem(name="uniform", n=nn, x0=(0.0, 0.0, 0.0), dx=dx, prims=prims,
+                   bface=pack_faces(bx, by, bz))
+
+
+def linear_wave(n: int, amp=0.1, v0=0.3, p0=1.0, B0=(0.2, 0.1, 0.05), t=0.0) -> Problem:
+    """1-D density wave along x: rho = 1 + amp sin(2 pi (x - v0 t)), uniform
+    v = (v0, 0, 0), p and B.  An exact solution of ideal (S)RMHD."""
+    nn = (n, 1, 1)
+    dx = (1.0 / n, 1.0, 1.0)
+    x = (np.arange(n) + 0.5) / n
+    prims = np.zeros((5, 1, 1, n))
+    prims[0, 0, 0] = 1.0 + amp * np.sin(2 * np.pi * (x - v0 * t))
+    prims[1] = v0
+    prims[4] = p0
+    bx = np.full((1, 1, n + 1), B0[0])
+    by = np.full((1, 2, n), B0[1])
+    bz = np.full((2, 1, n), B0[2])
+    return Problem(name=f"linear_wave_{n}", n=nn, x0=(0.0, 0.0, 0.0), dx=dx, prims=prims,
+                   bface=pack_faces(bx, by, bz))
+
+
+def alfven_speed(rho=1.0, p=1.0, B0=1.0, eta=1.0, gamma=4.0 / 3.0) -> float:
+    """Phase speed of the circularly polarised Alfven wave (exact nonlinear
+    SRMHD solution with v^x = 0, |B_perp| = eta B0): the smaller root u of
+    eta^2 B0^2 u^2 - (rho h + B0^2 (1 + eta^2)) u + B0^2 = 0, v_A = sqrt(u)."""
+    rh = rho + gamma / (gamma - 1.0) * p
+    bq = rh + B0 * B0 * (1.0 + eta * eta)
+    u = 2.0 * B0 * B0 / (bq + np.sqrt(bq * bq - 4.0 * eta * eta * B0 ** 4))
+    return float(np.sqrt(u))
+
+
+def alfven_wave(n: int, t=0.0, rho=1.0, p=1.0, B0=1.0, eta=1.0, gamma=4.0 / 3.0) -> Problem:
+    """Circularly polarised Alfven wave along x, phase k(x - v_A t), k = 2 pi:
+    B^y = eta B0 cos, B^z = eta B0 sin, v^{y,z} = -v_A B^{y,z}/B0, v^x = 0."""
+    vA = alfven_speed(rho, p, B0, eta, gamma)
+    nn = (n, 1, 1)
+    dx = (1.0 / n, 1.0, 1.0)
+    x = (np.arange(n) + 0.5) / n
+    ph = 2 * np.pi * (x - vA * t)
+    By = eta * B0 * np.cos(ph)
+    Bz = eta * B0 * np.sin(ph)
+    prims = np.zeros((5, 1, 1, n))
+    prims[0] = rho
+    prims[2, 0, 0] = -vA * By / B0
+    prims[3, 0, 0] = -vA * Bz / B0
+    prims[4] = p
+    bx = np.full((1, 1, n + 1), B0)
+    by = np.stack([By, By])[:, None, :].reshape(1, 2, n)
+    bz = np.stack([Bz, Bz]).reshape(2, 1, n)
+    return Problem(name=f"alfven_{n}", n=nn, x0=(0.0, 0.0, 0.0), dx=dx, gamma=gamma, prims=prims,
+                   bface=pack_faces(bx, by, bz))
+
+
+def permute_axes(prob: Problem) -> Problem:
+    """Cyclic relabelling x -> y -> z -> x of a problem (new y = old x, ...):
+    the new grid's axis d+1 is the old axis d.  Returns a new Problem."""
+    nx, ny, nz = prob.n
+    rho, vx, vy, vz, p = prob.prims
+    # arrays are (z, y, x); new axes x' = old z, y' = old x, z' = old y,
+    # so the new (z', y', x') = old (y, x, z): transpose axes (1, 2, 0)
+    def tr(a):
+        return np.ascontiguousarray(np.transpose(a, (1, 2, 0)))
+    prims = np.stack([tr(rho), tr(vz), tr(vx), tr(vy), tr(p)])
+    o = 0
+    bx = prob.bface[o:o + nz * ny * (nx + 1)].reshape(nz, ny, nx + 1)
+    o += bx.size
+    by = prob.bface[o:o + nz * (ny + 1) * nx].reshape(nz, ny + 1, nx)
+    o += by.size
+    bz = prob.bface[o:o + (nz + 1) * ny * nx].reshape(nz + 1, ny, nx)
+    nb = (tr(bz), tr(bx), tr(by))  # new Bx' = old Bz, By' = old Bx, Bz' = old By
+    n2 = (nz, nx, ny)
+    dx2 = (prob.dx[2], prob.dx[0], prob.dx[1])
+    x02 = (prob.x0[2], prob.x0[0], prob.x0[1])
+    return Problem(name=prob.name + "_perm", n=n2, x0=x02, dx=dx2, bc=prob.bc, metric=prob.metric,
+                   gamma=prob.gamma, cfl=prob.cfl, steps=prob.steps, seed=prob.seed, prims=prims,
+                   bface=pack_faces(*nb))
+
+
+def alfven_wave_2d(n: int, t=0.0, rho=1.0, p=1.0, B0=1.0, eta=1.0, gamma=4.0 / 3.0) -> Problem:
+    """The circularly polarised Alfven wave propagating along the diagonal
+    of the periodic unit square (n x n x 1), wave vector k = 2 pi (1, 1).
+    The in-plane perpendicular field comes from the discrete curl of an
+    edge-centred A_z, so the discrete divergence vanishes."""
+    vA = alfven_speed(rho, p, B0, eta, gamma)
+    nn = (n, n, 1)
+    dx = (1.0 / n, 1.0 / n, 1.0)
+    kvec = np.array([2 * np.pi, 2 * np.pi])
+    kmag = np.sqrt(2.0) * 2 * np.pi
+    nhat = kvec / kmag
+    that = np.array([-nhat[1], nhat[0]])
+
+    def phase(x, y):
+        return kvec[0] * x + kvec[1] * y - kmag * vA * t
+
+    xc = (np.arange(n) + 0.5) / n
+    xf = np.arange(n + 1) / n
+    X, Y = np.meshgrid(xc, xc, indexing="xy")          # (ny, nx)
+    ph = phase(X, Y)
+    Bt = eta * B0 * np.cos(ph)
+    Bzc = eta * B0 * np.sin(ph)
+    prims = np.zeros((5, 1, n, n))
+    prims[0] = rho
+    vt = -vA * Bt / B0
+    prims[1, 0] = vt * that[0]
+    prims[2, 0] = vt * that[1]
+    prims[3, 0] = -vA * Bzc / B0
+    prims[4] = p
+    # A_z at edges (i-1/2, j-1/2): B_perp = curl(A_z z) with
+    # A_z = -(eta B0/|k|) sin(phase)
+    XE, YE = np.meshgrid(xf, xf, indexing="xy")       # (ny+1, nx+1)
+    Az = -(eta * B0 / kmag) * np.sin(phase(XE, YE))
+    Azc = Az[None, :, :]
+    bx = (Azc[:, 1:, :] - Azc[:, :-1, :]) / dx[1] + B0 * nhat[0]     # (1, n, n+1)
+    by = -(Azc[:, :, 1:] - Azc[:, :, :-1]) / dx[0] + B0 * nhat[1]    # (1, n+1, n)
+    bz = np.stack([Bzc, Bzc])                                          # (2, n, n)
+    return Problem(name=f"alfven2d_{n}", n=nn, x0=(0.0, 0.0, 0.0), dx=dx, gamma=gamma, prims=prims,
+                   bface=pack_faces(bx, by, bz))

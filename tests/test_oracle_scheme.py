@@ -1,0 +1,205 @@
+"""Pins of the oracle's grid-level scheme: invariants, exact solutions and
+convergence orders.  These hold for the scheme as defined, independently of
+how the oracle's loops are written."""
+import numpy as np
+import pytest
+
+from paper_1810_04597_gb300 import inputs
+
+
+def setup(orc, prob):
+    cfg = orc.make_cfg(prob)
+    st, Z = orc.p2c(cfg, prob.prims, prob.bface)
+    return cfg, st, Z
+
+
+def test_uniform_state_stays_uniform(orc):
+    prob = inputs.uniform_box((8, 6, 5))
+    cfg, st, Z = setup(orc, prob)
+    L, _, _ = orc.rhs(cfg, st, Z)
+    assert np.all(L == 0.0)
+    st2, Z2, dts, _ = orc.steps(cfg, st, Z, 3)
+    cells, bx, by, bz = orc.split_state(st2, prob.n)
+    for q in range(5):
+        assert np.ptp(cells[q]) == 0.0
+    cells0, *_ = orc.split_state(st, prob.n)
+    assert np.max(np.abs(cells - cells0)) <= 1e-15 * np.max(np.abs(cells0))
+    for b in (bx, by, bz):
+        assert np.ptp(b) == 0.0
+
+
+def test_cfl_dt_at_rest(orc):
+    """Unmagnetised gas at rest: dt = CFL dx / (3 c_s)."""
+    prob = inputs.uniform_box((4, 4, 4), rho=1.0, v=(0, 0, 0), p=0.5, B=(0, 0, 0))
+    cfg, st, Z = setup(orc, prob)
+    _, _, rate = orc.rhs(cfg, st, Z)
+    cs = np.sqrt(4 / 3 * 0.5 / (1 + 4 * 0.5))
+    assert abs(rate - 3 * cs / prob.dx[0]) <= 1e-14 * rate
+    _, _, dts, _ = orc.steps(cfg, st, Z, 1)
+    assert abs(dts[0] - 0.4 * prob.dx[0] / (3 * cs)) <= 1e-15
+
+
+@pytest.fixture(scope="module")
+def box32(orc):
+    prob = inputs.smooth_box(32)
+    cfg, st, Z = setup(orc, prob)
+    st10, Z10, dts, stats = orc.steps(cfg, st, Z, 10)
+    return prob, cfg, st, Z, st10, Z10, dts, stats
+
+
+def test_conservation_periodic(orc, box32):
+    prob, cfg, st, Z, st10, Z10, dts, stats = box32
+    t0 = orc.reduce(cfg, st)
+    t1 = orc.reduce(cfg, st10)
+    assert abs(t1[0] - t0[0]) <= 1e-13 * abs(t0[0])
+    assert abs(t1[1] - t0[1]) <= 1e-13 * abs(t0[1])
+    cells, *_ = orc.split_state(st, prob.n)
+    dV = np.prod(prob.dx)
+    for q in range(3):
+        assert abs(t1[2 + q] - t0[2 + q]) <= 1e-13 * np.sum(np.abs(cells[1 + q])) * dV
+    assert stats["fails"] == 0
+
+
+def test_divergence_free(orc, box32):
+    prob, cfg, st, Z, st10, Z10, dts, stats = box32
+    _, bx, by, bz = orc.split_state(st10, prob.n)
+    bmax = max(np.max(np.abs(bx)), np.max(np.abs(by)), np.max(np.abs(bz)))
+    t1 = orc.reduce(cfg, st10)
+    assert t1[5] * prob.dx[0] / bmax <= 1e-12
+    # the state actually evolved
+    assert np.max(np.abs(st10 - st)) > 1e-3 * np.max(np.abs(st))
+
+
+def test_uct_reduces_to_1d_hll_flux_of_transverse_field(orc):
+    """For data that vary along x only, the CT update of the transverse field
+    is minus the difference of the 1-D HLL flux of B^y (resp. B^z) along x,
+    F(B^y) = v^x B^y - v^y B^x, built here from the pointwise MP5, speed and
+    velocity values."""
+    n = 24
+    x = (np.arange(n) + 0.5) / n
+    rng = np.random.default_rng(20)
+    prims = np.zeros((5, 1, 1, n))
+    prims[0, 0, 0] = 1 + 0.2 * np.sin(2 * np.pi * x + 0.3)
+    prims[1, 0, 0] = 0.3 * np.cos(2 * np.pi * x)
+    prims[2, 0, 0] = 0.2 * np.sin(4 * np.pi * x + 1.0)
+    prims[3, 0, 0] = -0.1 * np.cos(2 * np.pi * x + 0.5)
+    prims[4, 0, 0] = 0.8 + 0.1 * np.cos(2 * np.pi * x)
+    By = 0.3 * np.cos(2 * np.pi * x + 0.2)
+    Bz = 0.2 * np.sin(2 * np.pi * x)
+    Bx0 = 0.25
+    bface = inputs.pack_faces(np.full((1, 1, n + 1), Bx0), np.stack([By, By]).reshape(1, 2, n),
+                              np.stack([Bz, Bz]).reshape(2, 1, n))
+    prob = inputs.Problem(name="uct1d", n=(n, 1, 1), x0=(0, 0, 0), dx=(1.0 / n, 1.0, 1.0),
+                          prims=prims, bface=bface)
+    cfg, st, Z = setup(orc, prob)
+    L, _, _ = orc.rhs(cfg, st, Z)
+    _, Lbx, Lby, Lbz = orc.split_state(L, prob.n)
+    P8, _, _, _ = orc.c2p(cfg, st, Z)
+    P8 = P8.reshape(8, n)
+
+    def face_state(i):
+        """MP5 left/right primitive states at face i-1/2 (periodic)."""
+        idx = [(i + s) % n for s in range(-3, 3)]
+        PL = np.zeros(8)
+        PR = np.zeros(8)
+        for q in range(8):
+            if q == 5:
+                continue
+            u = P8[q, idx]
+            PL[q] = orc.mp5_face(u[0:5])
+            PR[q] = orc.mp5_face(u[5:0:-1])
+        PL[5] = PR[5] = Bx0
+        return PL, PR
+
+    FBy = np.zeros(n + 1)
+    FBz = np.zeros(n + 1)
+    for i in range(n + 1):
+        PL, PR = face_state(i % n)
+        lpL, lmL = orc.speeds_point(cfg, np.zeros(3), PL, 0)
+        lpR, lmR = orc.speeds_point(cfg, np.zeros(3), PR, 0)
+        ap = max(0.0, lpL, lpR)
+        am = max(0.0, -lmL, -lmR)
+        for comp, Fout in ((6, FBy), (7, FBz)):
+            vcomp = comp - 4   # v^y for B^y, v^z for B^z
+            fL = PL[1] * PL[comp] - PL[vcomp] * Bx0
+            fR = PR[1] * PR[comp] - PR[vcomp] * Bx0
+            Fout[i] = (ap * fL + am * fR - ap * am * (PR[comp] - PL[comp])) / (ap + am)
+    ref_by = -(FBy[1:] - FBy[:-1]) * n
+    ref_bz = -(FBz[1:] - FBz[:-1]) * n
+    scale = np.max(np.abs(ref_by)) + np.max(np.abs(ref_bz))
+    assert np.max(np.abs(Lby[0, 0, :] - ref_by)) <= 1e-12 * scale
+    assert np.max(np.abs(Lby[0, 1, :] - ref_by)) <= 1e-12 * scale
+    assert np.max(np.abs(Lbz[0, 0, :] - ref_bz)) <= 1e-12 * scale
+    assert np.all(np.abs(Lbx) <= 1e-14)
+
+
+def test_cyclic_axis_permutation_equivariance(orc):
+    """Relabelling the axes x -> y -> z -> x relabels the result: the scheme
+    has no preferred axis (the two-step EMF reconstruction order is cyclic)."""
+    prob = inputs.smooth_box(12, seed=77)
+    prob.n = (12, 12, 12)
+    perm = inputs.permute_axes(prob)
+    cfg, st, Z = setup(orc, prob)
+    cfgp, stp, Zp = setup(orc, perm)
+    L, _, r = orc.rhs(cfg, st, Z)
+    Lp, _, rp = orc.rhs(cfgp, stp, Zp)
+    assert abs(r - rp) <= 1e-14 * r
+    c, bx, by, bz = orc.split_state(L, prob.n)
+    cp, bxp, byp, bzp = orc.split_state(Lp, perm.n)
+
+    def tr(a):
+        return np.transpose(a, (1, 2, 0))
+
+    scale = np.max(np.abs(L))
+    tol = 1e-13 * scale
+    assert np.max(np.abs(tr(c[0]) - cp[0])) <= tol
+    assert np.max(np.abs(tr(c[4]) - cp[4])) <= tol
+    assert np.max(np.abs(tr(c[3]) - cp[1])) <= tol   # S_z -> S_x'
+    assert np.max(np.abs(tr(c[1]) - cp[2])) <= tol   # S_x -> S_y'
+    assert np.max(np.abs(tr(c[2]) - cp[3])) <= tol   # S_y -> S_z'
+    assert np.max(np.abs(tr(bz) - bxp)) <= tol
+    assert np.max(np.abs(tr(bx) - byp)) <= tol
+    assert np.max(np.abs(tr(by) - bzp)) <= tol
+
+
+def _wave_errors(orc, make, sizes, T, q, dt_of_n):
+    errs = []
+    for n in sizes:
+        p0 = make(n, 0.0)
+        ex = make(n, T)
+        cfg, st, Z = setup(orc, p0)
+        ns = int(np.ceil(T / dt_of_n(n)))
+        st2, Z2, _, stats = orc.steps(cfg, st, Z, ns, T / ns)
+        P8, _, _, _ = orc.c2p(cfg, st2, Z2)
+        errs.append(np.mean(np.abs(P8[q] - ex.prims[q].reshape(-1))))
+    errs = np.array(errs)
+    return errs, np.log2(errs[:-1] / errs[1:])
+
+
+def test_linear_density_wave_fifth_order(orc):
+    """Advected density wave (an exact solution); dt ~ dx^(5/3) so that the
+    third-order time error scales like dx^5."""
+    errs, orders = _wave_errors(orc, lambda n, t: inputs.linear_wave(n, t=t), [32, 64, 128], 1.0, 0,
+                                lambda n: 0.2 / n * (32.0 / n) ** (2 / 3))
+    assert np.all(orders >= 4.5), (errs, orders)
+
+
+def test_alfven_wave_1d_exact(orc):
+    """Circularly polarised Alfven wave along x: exact nonlinear solution;
+    the x-fluxes are linear in the reconstructed variables, so the
+    point-value scheme keeps fifth order."""
+    errs, orders = _wave_errors(orc, lambda n, t: inputs.alfven_wave(n, t=t), [32, 64, 128], 0.5, 2,
+                                lambda n: 0.2 / n * (32.0 / n) ** (2 / 3))
+    assert np.all(orders >= 4.5), (errs, orders)
+    assert errs[-1] < 1e-8
+
+
+def test_alfven_wave_oblique_2d(orc):
+    """The same wave along the diagonal: fluxes are nonlinear in the
+    reconstructed point values, so without a flux-derivative correction the
+    scheme is second order; a sign or index error in the EMF would break
+    convergence altogether."""
+    errs, orders = _wave_errors(orc, lambda n, t: inputs.alfven_wave_2d(n, t=t), [16, 32, 64], 0.25,
+                                3, lambda n: 0.2 / n * (16.0 / n) ** (2 / 3))
+    assert np.all(orders >= 1.8), (errs, orders)
+    assert errs[-1] < 1e-4
