@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Throughput of the GRMHD step on GB300: Mzone-updates/s per SSP-RK3 step.
+
+Workload (default): the 256^3 periodic special-relativistic MHD box of
+``inputs.sweep_box`` (rho in [0.5,1.5], log-uniform p in [0.1,1], |v| <= 0.6,
+plasma beta ~1-100, Gamma = 4/3, CFL 0.4), FP64 throughout.  A step is one
+whole SSP-RK3 step: three stages of ghost fill, c2p, MP5+HLL faces, UCT EMFs
+and the update, with the CFL dt reduced on the device.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 64|32]
+                  [--size 256] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
+only other implementation of this method) on a bounded sample of the same
+workload on this host's cores.  Under torchrun every rank runs an
+independent replica (the step has no data exchange on one GPU per run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mzone-updates/s per RK3 step"
+UNIT = "Mzone/s"
+
+# Algorithmic bytes per unit of each kernel class (FP64 values are 8 B; the
+# FP32 path stores 4 B values except Z, which stays FP64).  Counts: every
+# array element a kernel must read or write once (halo re-reads excluded).
+#   c2p     per cell: read D,S,tau (5) + 3 face B + Z; write 8 primitives + Z
+#   faces   per face: read 7 primitives + normal B; write 5 fluxes, a+, a-,
+#           4 face velocities
+#   emf     per edge: read 4 face velocities, 2 face B, 4 speeds; write E
+#   update  per cell: read 15 fluxes, 3 EMFs, U (8), U0 (8); write U (8)
+KMODEL = {
+    "c2p": dict(vals=18, z=2),
+    "faces_x": dict(vals=19), "faces_y": dict(vals=19), "faces_z": dict(vals=19),
+    "emf_x": dict(vals=11), "emf_y": dict(vals=11), "emf_z": dict(vals=11),
+    "update": dict(vals=42),
+}
+
+
+def kernel_units(name, n):
+    nx, ny, nz = n
+    g = 3
+    if name == "c2p" or name == "update":
+        return nx * ny * nz
+    if name == "faces_x":
+        return (nx + 1) * (ny + 2 * g) * (nz + 2 * g)
+    if name == "faces_y":
+        return (nx + 2 * g) * (ny + 1) * (nz + 2 * g)
+    if name == "faces_z":
+        return (nx + 2 * g) * (ny + 2 * g) * (nz + 1)
+    if name == "emf_x":
+        return nx * (ny + 1) * (nz + 1)
+    if name == "emf_y":
+        return (nx + 1) * ny * (nz + 1)
+    if name == "emf_z":
+        return (nx + 1) * (ny + 1) * nz
+    return 0
+
+
+def kernel_bytes_per_unit(name, precision):
+    m = KMODEL[name]
+    size = 8 if precision == 64 else 4
+    z = m.get("z", 0)
+    return (m["vals"] - z) * size + z * 8
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=None):
+        self.proc = None
+        self.lines = []
+        self.gpu_index = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r.split(",") for r in self.lines if r]
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        if self.gpu_index is not None:
+            sel = [r for r in rows if r[0] == str(self.gpu_index)]
+            rows = sel or rows
+        if rows:
+            first = rows[0][0]
+            rows = [r for r in rows if r[0] == first]
+
+        def num(x):
+            try:
+                return float(x.split()[0])
+            except Exception:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max([num(r[3]) for r in rows if num(r[3]) is not None], default=None)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_window(prob, w=48):
+    """The w^3 corner of the workload's seeded input as a periodic problem
+    (the oracle's bounded sample)."""
+    import numpy as np
+    from paper_1810_04597_gb300 import inputs
+    N = prob.n
+    prims = np.ascontiguousarray(prob.prims[:, :w, :w, :w])
+    o = 0
+    bx = prob.bface[o:o + N[2] * N[1] * (N[0] + 1)].reshape(N[2], N[1], N[0] + 1)
+    o += bx.size
+    by = prob.bface[o:o + N[2] * (N[1] + 1) * N[0]].reshape(N[2], N[1] + 1, N[0])
+    o += by.size
+    bz = prob.bface[o:o + (N[2] + 1) * N[1] * N[0]].reshape(N[2] + 1, N[1], N[0])
+    return inputs.Problem(name="window", n=(w, w, w), x0=(0, 0, 0), dx=prob.dx, cfl=prob.cfl,
+                          prims=prims, bface=inputs.pack_faces(bx[:w, :w, :w + 1], by[:w, :w + 1, :w],
+                                                               bz[:w + 1, :w, :w]))
+
+
+def oracle_sample(prob, nsteps_hint, budget_s, w=48):
+    """Time oracle SSP-RK3 steps on a w^3 window of the workload's seeded
+    input for about budget_s seconds.  Returns (zones_per_s, zones, steps,
+    seconds, threads, w)."""
+    import oracle
+    win = oracle_window(prob, w)
+    cfg = oracle.make_cfg(win)
+    st, Z = oracle.p2c(cfg, win.prims, win.bface)
+    t0 = time.perf_counter()
+    st, Z, _, _ = oracle.steps(cfg, st, Z, 1)
+    t1 = time.perf_counter() - t0
+    steps = max(1, min(nsteps_hint, int(budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.steps(cfg, st, Z, steps)
+    dt = time.perf_counter() - t0
+    zones = w ** 3
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return zones * steps / dt, zones, steps, dt, threads, w
+
+
+def cpu_description():
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "CPU part", "Hardware"):
+            for ln in txt.splitlines():
+                if ln.startswith(key):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+# ------------------------------------------------------------------ distributed
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, local):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        return dist
+    return None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args, world, rank):
+    """The oracle (plain FP64 C, OpenMP over cells) as the reference arm."""
+    if rank != 0:
+        return None
+    from paper_1810_04597_gb300 import inputs
+    import oracle
+    oracle.build()
+    prob = inputs.sweep_box(args.size)
+    w = 48
+    win = oracle_window(prob, w)
+    cfg = oracle.make_cfg(win)
+    st, Z = oracle.p2c(cfg, win.prims, win.bface)
+    st, Z, _, _ = oracle.steps(cfg, st, Z, args.warmup)
+    t0 = time.perf_counter()
+    st, Z, _, _ = oracle.steps(cfg, st, Z, args.steps)
+    dt = time.perf_counter() - t0
+    zones = w ** 3
+    value = zones * args.steps / dt / 1e6
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"{w}^3 periodic window of the {args.size}^3 sweep_box input, {args.steps} oracle "
+              f"SSP-RK3 steps (after {args.warmup} warm-up), FP64, OpenMP over cells")
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": f"sweep_box {args.size}^3 periodic SRMHD (oracle on a {w}^3 window)",
+                   "grid": [args.size] * 3},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample, "cpu": cpu_description()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_ours(args, world, rank, local, dist):
+    import numpy as np
+    import torch
+    from paper_1810_04597_gb300 import inputs, _lib
+    from paper_1810_04597_gb300.echo import Solver
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    prob = inputs.sweep_box(args.size)
+    n = prob.n
+    zones = prob.ncells
+    s = Solver(prob, precision=args.precision, device=str(dev))
+    stream = s.stream
+    s.set_prims()
+    for _ in range(args.warmup):
+        s.step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device-resident inputs
+    sampler = ClockSampler(gpu_index=None)
+    sampler.start()
+    time.sleep(0.3)
+    s.profile(True)
+    s.profile_read()
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        s.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    ms = ev0.elapsed_time(ev1)
+    prof = s.profile_read()
+    s.profile(False)
+    clocks = sampler.stop()
+    ms_max = max_over_ranks(dist, ms)
+    value = world * zones * args.steps / (ms_max * 1e-3) / 1e6
+    totals = s.reduce()
+
+    # kernels launched in the timed region (a fill call launches 3 kernels)
+    per_call = {"fill_faces": 3, "fill_prims": 3}
+    launches = int(sum(cnt * per_call.get(k, 1) for k, (_, cnt) in prof.items()))
+
+    # ---- roofline of the dominant kernel (live CUDA-event times)
+    peaks, peak_src = load_peaks()
+    timed = {k: v for k, v in prof.items() if k in KMODEL and v[1] > 0}
+    dom = max(timed, key=lambda k: timed[k][0])
+    dom_ms, dom_launches = timed[dom]
+    avg_s = dom_ms / dom_launches * 1e-3
+    bytes_launch = kernel_units(dom, n) * kernel_bytes_per_unit(dom, args.precision)
+    achieved = bytes_launch / avg_s / 1e9
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    share = {k: round(v[0] / ms, 4) for k, v in prof.items() if v[1] > 0}
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None,
+            "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+            else "fallback 6800 GB/s",
+            "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_s * 1e3, "time_share": share}
+
+    # ---- end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        nst = s.nstate
+        st_host = torch.empty(nst, dtype=torch.float64, pin_memory=True).numpy()
+        z_host = torch.empty(zones, dtype=torch.float64, pin_memory=True).numpy()
+        out_host = torch.empty(nst, dtype=torch.float64, pin_memory=True).numpy()
+        s.get_state(st_host)
+        s.get_z(z_host)
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            s.set_state(st_host, z_host)
+            s.step()
+            s.get_state(out_host)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        t_e2e = max_over_ranks(dist, t_e2e)
+        e2e = {"value": world * zones * e2e_steps / t_e2e / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(st_host.nbytes + z_host.nbytes),
+               "d2h_bytes_per_step": int(out_host.nbytes), "steps": e2e_steps,
+               "api": "echo_set_state(host) + echo_step + echo_get_state(host)"}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, z, nsteps_c, secs, threads, w = oracle_sample(prob, 50, args.cpu_budget)
+        cpu = {"value": v / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{w}^3 periodic window of this input, {nsteps_c} SSP-RK3 steps, "
+                         f"{secs:.1f} s, FP64 C oracle with OpenMP over cells",
+               "cpu": cpu_description()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == 64 else "f32 stencil + f64 c2p/reductions",
+        "data": "synthetic (seeded sweep_box)",
+        "config": {"workload": f"sweep_box {args.size}^3 periodic SRMHD, Gamma 4/3, CFL 0.4, "
+                               f"{'FP64' if args.precision == 64 else 'FP32 bulk'}",
+                   "grid": list(n), "zones": zones, "parallelism": f"replicas x{world}",
+                   "l2": "working set (~9 GB) larger than L2; no flush needed"},
+        "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches,
+        "check": {"c2p_fail": totals["c2p_fail"], "mean_newton_iters":
+                  totals["c2p_iters"] / max(totals["c2p_calls"], 1), "dt_cfl": totals["dt_cfl"]},
+    }
+    return line if rank == 0 else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--precision", type=int, default=64, choices=(32, 64))
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    world, rank, local = dist_info()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
+    dist = init_dist(world, local)
+    line = run_ours(args, world, rank, local, dist)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * echo.h -- C ABI of the GB300 library for the per-step update of the 3-D
+ * finite-difference GRMHD scheme (ECHO-3DHPC method) on a fixed metric.
+ *
+ * The paper (introduction) describes ECHO-3DHPC as a code that solves the
+ * equations of general-relativistic MHD with a 3-D finite-difference method
+ * and high-order reconstruction; it prints no equation.  The update this
+ * library computes restates published methods:
+ *   conservative-to-primitive inversion by Newton iteration on Z = rho h W^2;
+ *   MP5 reconstruction of primitives (Suresh & Huynh 1997);
+ *   HLL fluxes with the approximate fast speed of the ECHO family;
+ *   upwind constrained-transport (UCT-HLL) edge EMFs (Londrillo & Del Zanna
+ *   2004);
+ *   flux difference plus geometric sources of the 3+1 Valencia form, and the
+ *   three-stage SSP Runge-Kutta scheme (Shu & Osher 1988).
+ *
+ * Conventions
+ *   - Every entry point returns ECHO_OK (0) or a negative ECHO_E* code; the
+ *     message of the last failure is echo_last_error(ctx).  No exception
+ *     crosses the ABI.
+ *   - The library never allocates device memory: the caller allocates the
+ *     workspace (echo_workspace_bytes) and passes it to echo_bind together
+ *     with a CUDA stream.  All work is enqueued on that stream.  Pointers
+ *     stay owned by the caller.
+ *   - Only echo_get_state, echo_get_prims, echo_c2p (with stats) and
+ *     echo_reduce synchronise the bound stream.
+ *   - Host-layout arrays are FP64 regardless of the internal precision.
+ *     A state holds five cell arrays (D, S_x, S_y, S_z, tau), densitised by
+ *     sqrt(gamma), each nz*ny*nx with x fastest, followed by the face field
+ *     B~ = sqrt(gamma) B as Bx (nz, ny, nx+1), By (nz, ny+1, nx),
+ *     Bz (nz+1, ny, nx), face i-1/2 at index i.  On a periodic axis the last
+ *     face repeats the first (read: ignored; written: duplicated).
+ *   - A pointer argument flagged "on_device" is a device pointer when the
+ *     flag is 1 and a host pointer otherwise.  A host input buffer must stay
+ *     unchanged until the next synchronising call.
+ */
+#ifndef ECHO_H
+#define ECHO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ECHO_OK 0
+#define ECHO_EINVAL (-1)   /* bad argument or configuration */
+#define ECHO_ECUDA (-2)    /* a CUDA runtime call or kernel launch failed */
+#define ECHO_ENOMEM (-3)   /* workspace smaller than echo_workspace_bytes */
+#define ECHO_EC2P (-4)     /* conservative-to-primitive inversion failed */
+#define ECHO_ETIMEOUT (-5) /* a bounded device wait gave up */
+#define ECHO_ESTATE (-6)   /* call out of order (e.g. not bound, no state) */
+
+/* boundary kinds (echo_grid.bc[2*d + side], side 0 lower, 1 upper) */
+#define ECHO_BC_PERIODIC 0
+#define ECHO_BC_OUTFLOW 1
+#define ECHO_BC_AXIS 2
+
+/* metric kinds */
+#define ECHO_METRIC_FLAT 0
+#define ECHO_METRIC_KERR_SCHILD 1 /* coordinates (ln r, theta, phi), M = 1 */
+
+typedef struct echo_ctx echo_ctx; /* opaque, library-owned host object */
+
+typedef struct {
+    int n[3];      /* interior cells along x1, x2, x3 (each >= 1) */
+    double x0[3];  /* coordinate of the lower face of the domain */
+    double dx[3];  /* cell widths (> 0) */
+    int bc[6];     /* ECHO_BC_* per axis and side */
+} echo_grid;
+
+typedef struct {
+    int kind;      /* ECHO_METRIC_* */
+    double spin;   /* a/M for Kerr-Schild */
+} echo_metric;
+
+typedef struct {
+    double gamma;  /* ideal-gas adiabatic index, > 1 */
+    int floors;    /* 1: atmosphere floors after c2p, failures fall back */
+    double rho_floor, rho_floor_pow, p_floor, p_floor_pow; /* floor = f0 r^pow */
+} echo_eos;
+
+typedef struct {
+    double dt_cfl;        /* CFL time step of the current state */
+    double mass;          /* sum sqrt(g) D dV */
+    double energy;        /* sum sqrt(g) tau dV */
+    double mom[3];        /* sum sqrt(g) S_i dV */
+    double max_divb;      /* max over cells |sum_d dB~^d / dx^d| */
+    long long c2p_iters;  /* Newton iterations since bind (cumulative) */
+    long long c2p_calls;  /* cell inversions since bind */
+    long long c2p_fail;   /* failed inversions since bind */
+    long long floor_hits; /* cells reset by floors since bind */
+    long long fallback_faces; /* reserved (first-order face fallbacks) */
+} echo_totals;
+
+/* Create a context.  precision: 64 (FP64 everywhere) or 32 (FP32 storage
+ * and stencil arithmetic; c2p, metric and reductions in FP64).  cfl: the
+ * Courant number of the CFL time step.  Validates the configuration;
+ * returns ECHO_EINVAL (and *out = NULL) on a bad one. */
+int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *eos, int precision,
+              double cfl, echo_ctx **out);
+
+/* Bytes of device workspace the context needs (all arrays, with 3 ghost
+ * layers, plus staging and reduction scratch). */
+size_t echo_workspace_bytes(const echo_ctx *ctx);
+
+/* Number of doubles of a host-layout state. */
+size_t echo_state_count(const echo_ctx *ctx);
+
+/* Attach a caller-owned device workspace (>= echo_workspace_bytes bytes,
+ * 256-byte aligned) and a CUDA stream (cudaStream_t, may be NULL for the
+ * legacy default stream).  Resets the cumulative counters.  Returns
+ * ECHO_ENOMEM if the workspace is too small, ECHO_EINVAL if misaligned. */
+int echo_bind(echo_ctx *ctx, void *dev_workspace, size_t bytes, void *cuda_stream);
+
+/* Initial data: cell primitives (5, nz, ny, nx) = rho, v^x, v^y, v^z, p
+ * (contravariant v) and the face field B~ in host face layout.  Converts
+ * them to the conserved state on the device (cell-centre B = mean of the two
+ * faces over sqrt(gamma)) and sets the Newton memory Z = rho h W^2. */
+int echo_set_prims(echo_ctx *ctx, const double *prims5, const double *bface, int on_device);
+
+/* Set the conserved state (host layout).  Z (nz*ny*nx doubles, may be NULL)
+ * is the Newton guess memory; NULL selects the cold guess. */
+int echo_set_state(echo_ctx *ctx, const double *state, const double *Z, int on_device);
+
+/* Copy the conserved state out (host layout, periodic duplicate faces
+ * filled).  Synchronises the stream. */
+int echo_get_state(echo_ctx *ctx, double *state, int on_device);
+
+/* Copy the primitives of the last c2p out: 8 cell arrays rho, v^x, v^y, v^z,
+ * p, B^x, B^y, B^z (cell-centre B undensitised).  Synchronises. */
+int echo_get_prims(echo_ctx *ctx, double *prims8, int on_device);
+
+/* Copy the Newton memory Z (nz*ny*nx doubles) out.  Synchronises. */
+int echo_get_z(echo_ctx *ctx, double *Z, int on_device);
+
+/* Conservative-to-primitive inversion of the current state on every owned
+ * cell.  guess_mode: 0 = the stored Z of the cell (previous stage), 2 = cold
+ * guess (Z = 0, replaced by the admissibility rule).  If stats is non-NULL
+ * the call synchronises and fills the counters and dt_cfl of stats (the
+ * other fields are left untouched) and returns ECHO_EC2P if any cell failed. */
+int echo_c2p(echo_ctx *ctx, int guess_mode, echo_totals *stats);
+
+/* L(U) of the current state: c2p, ghost fill, reconstruction, HLL fluxes,
+ * UCT EMFs, flux difference + sources, and minus the curl of the EMFs for the
+ * face field.  Written in host layout (state_count doubles) to L. */
+int echo_rhs(echo_ctx *ctx, double *L, int on_device);
+
+/* One SSP-RK3 step.  dt > 0: that step size; dt <= 0: the CFL step
+ * cfl / max_cells sum_d max|lambda_d|/dx^d from the first-stage primitives. */
+int echo_step(echo_ctx *ctx, double dt);
+
+/* Totals of the current state (runs a c2p for dt_cfl), copied to *out.
+ * Synchronises.  Returns ECHO_EC2P if an inversion failed since the last
+ * call and floors are off. */
+int echo_reduce(echo_ctx *ctx, echo_totals *out);
+
+/* Kernel classes timed by the profiling facility below. */
+#define ECHO_K_FILL_FACES 0
+#define ECHO_K_C2P 1
+#define ECHO_K_FILL_PRIMS 2
+#define ECHO_K_FACES_X 3
+#define ECHO_K_FACES_Y 4
+#define ECHO_K_FACES_Z 5
+#define ECHO_K_EMF_X 6
+#define ECHO_K_EMF_Y 7
+#define ECHO_K_EMF_Z 8
+#define ECHO_K_UPDATE 9
+#define ECHO_K_SCALARS 10
+#define ECHO_K_TOTALS 11
+#define ECHO_NK 12
+
+/* Enable (1) or disable (0) per-kernel timing: while enabled, every kernel
+ * launch of echo_step/echo_rhs/echo_c2p/echo_reduce is bracketed by two
+ * CUDA events recorded on the bound stream.  Not part of the numerics; adds
+ * two event records per launch. */
+int echo_profile(echo_ctx *ctx, int enable);
+
+/* Synchronise, then write for each kernel class k < nk the summed device
+ * time in milliseconds (ms[k]) and the number of launches (launches[k])
+ * recorded since the last read, and reset the record. */
+int echo_profile_read(echo_ctx *ctx, double *ms, long long *launches, int nk);
+
+/* Name of kernel class k ("" if out of range). */
+const char *echo_kernel_name(int k);
+
+/* Message of the last failure on this context ("" if none). */
+const char *echo_last_error(const echo_ctx *ctx);
+
+/* Destroy a context (does not free the caller's workspace). */
+void echo_destroy(echo_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ECHO_H */

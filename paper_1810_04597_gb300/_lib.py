@@ -1,0 +1,253 @@
+"""ctypes binding of ``include/echo.h`` -- argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic on the state.  Array arguments may be NumPy arrays (host memory,
+FP64, C-contiguous) or torch CUDA tensors (device memory, FP64); the
+``on_device`` flag of the C call is derived from the argument.  A non-zero
+status raises :class:`EchoError` with the library's message.
+
+The library is ``_build/libecho.so`` next to this file (see ``build.py``).
+There is no fallback: if it is missing or cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ECHO_OK = 0
+ECHO_EINVAL = -1
+ECHO_ECUDA = -2
+ECHO_ENOMEM = -3
+ECHO_EC2P = -4
+ECHO_ETIMEOUT = -5
+ECHO_ESTATE = -6
+_NAMES = {0: "ECHO_OK", -1: "ECHO_EINVAL", -2: "ECHO_ECUDA", -3: "ECHO_ENOMEM", -4: "ECHO_EC2P",
+          -5: "ECHO_ETIMEOUT", -6: "ECHO_ESTATE"}
+
+BC_PERIODIC, BC_OUTFLOW, BC_AXIS = 0, 1, 2
+METRIC_FLAT, METRIC_KERR_SCHILD = 0, 1
+
+
+class EchoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class echo_grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("x0", ctypes.c_double * 3), ("dx", ctypes.c_double * 3),
+                ("bc", ctypes.c_int * 6)]
+
+
+class echo_metric(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("spin", ctypes.c_double)]
+
+
+class echo_eos(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("floors", ctypes.c_int), ("rho_floor", ctypes.c_double),
+                ("rho_floor_pow", ctypes.c_double), ("p_floor", ctypes.c_double),
+                ("p_floor_pow", ctypes.c_double)]
+
+
+class echo_totals(ctypes.Structure):
+    _fields_ = [("dt_cfl", ctypes.c_double), ("mass", ctypes.c_double), ("energy", ctypes.c_double),
+                ("mom", ctypes.c_double * 3), ("max_divb", ctypes.c_double),
+                ("c2p_iters", ctypes.c_longlong), ("c2p_calls", ctypes.c_longlong),
+                ("c2p_fail", ctypes.c_longlong), ("floor_hits", ctypes.c_longlong),
+                ("fallback_faces", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return dict(dt_cfl=self.dt_cfl, mass=self.mass, energy=self.energy, mom=list(self.mom),
+                    max_divb=self.max_divb, c2p_iters=self.c2p_iters, c2p_calls=self.c2p_calls,
+                    c2p_fail=self.c2p_fail, floor_hits=self.floor_hits,
+                    fallback_faces=self.fallback_faces)
+
+
+# Exported entry points and their C signatures.
+_P = ctypes.c_void_p
+_SIGS = {
+    "echo_init": (ctypes.c_int, [ctypes.POINTER(echo_grid), ctypes.POINTER(echo_metric),
+                                 ctypes.POINTER(echo_eos), ctypes.c_int, ctypes.c_double,
+                                 ctypes.POINTER(_P)]),
+    "echo_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "echo_state_count": (ctypes.c_size_t, [_P]),
+    "echo_bind": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
+    "echo_set_prims": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "echo_set_state": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "echo_get_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "echo_get_prims": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "echo_get_z": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "echo_c2p": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(echo_totals)]),
+    "echo_rhs": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "echo_step": (ctypes.c_int, [_P, ctypes.c_double]),
+    "echo_reduce": (ctypes.c_int, [_P, ctypes.POINTER(echo_totals)]),
+    "echo_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "echo_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
+    "echo_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "echo_last_error": (ctypes.c_char_p, [_P]),
+    "echo_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Load (building first if needed) the CUDA library.  Raises if it
+    cannot be built or loaded -- there is no CPU fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_needed and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(ctx, rc):
+    if rc != ECHO_OK:
+        msg = load().echo_last_error(ctx) if ctx else b""
+        raise EchoError(rc, (msg or b"").decode())
+
+
+def _ptr(a, writable=False):
+    """(pointer, on_device) of a NumPy array or torch CUDA tensor (FP64)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("host arrays must be C-contiguous float64")
+        if writable and not a.flags["WRITEABLE"]:
+            raise TypeError("output array is read-only")
+        return a.ctypes.data, 0
+    # torch tensor
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise TypeError(f"unsupported array type {type(a)}")
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        raise TypeError("tensors must be contiguous float64")
+    if a.is_cuda:
+        return a.data_ptr(), 1
+    return a.data_ptr(), 0
+
+
+# ---------------------------------------------------------------- entry points
+
+def echo_init(grid: echo_grid, metric: echo_metric, eos: echo_eos, precision: int, cfl: float):
+    ctx = _P()
+    rc = load().echo_init(ctypes.byref(grid), ctypes.byref(metric), ctypes.byref(eos), int(precision),
+                          float(cfl), ctypes.byref(ctx))
+    _check(None, rc)
+    return ctx
+
+
+def echo_workspace_bytes(ctx) -> int:
+    return int(load().echo_workspace_bytes(ctx))
+
+
+def echo_state_count(ctx) -> int:
+    return int(load().echo_state_count(ctx))
+
+
+def echo_bind(ctx, dev_ptr: int, nbytes: int, stream_handle: int):
+    _check(ctx, load().echo_bind(ctx, _P(dev_ptr), ctypes.c_size_t(nbytes), _P(stream_handle)))
+
+
+def echo_set_prims(ctx, prims5, bface):
+    p, dp = _ptr(prims5)
+    f, df = _ptr(bface)
+    if dp != df:
+        raise TypeError("prims and face field must both be host or both be device arrays")
+    _check(ctx, load().echo_set_prims(ctx, _P(p), _P(f), dp))
+
+
+def echo_set_state(ctx, state, Z=None):
+    s, ds = _ptr(state)
+    z, dz = _ptr(Z)
+    if Z is not None and dz != ds:
+        raise TypeError("state and Z must both be host or both be device arrays")
+    _check(ctx, load().echo_set_state(ctx, _P(s), _P(z) if z else None, ds))
+
+
+def echo_get_state(ctx, out):
+    p, d = _ptr(out, writable=True)
+    _check(ctx, load().echo_get_state(ctx, _P(p), d))
+    return out
+
+
+def echo_get_prims(ctx, out):
+    p, d = _ptr(out, writable=True)
+    _check(ctx, load().echo_get_prims(ctx, _P(p), d))
+    return out
+
+
+def echo_get_z(ctx, out):
+    p, d = _ptr(out, writable=True)
+    _check(ctx, load().echo_get_z(ctx, _P(p), d))
+    return out
+
+
+def echo_c2p(ctx, guess_mode: int = 0, stats: echo_totals | None = None):
+    rc = load().echo_c2p(ctx, int(guess_mode), ctypes.byref(stats) if stats is not None else None)
+    _check(ctx, rc)
+    return stats
+
+
+def echo_rhs(ctx, out):
+    p, d = _ptr(out, writable=True)
+    _check(ctx, load().echo_rhs(ctx, _P(p), d))
+    return out
+
+
+def echo_step(ctx, dt: float = 0.0):
+    _check(ctx, load().echo_step(ctx, float(dt)))
+
+
+def echo_reduce(ctx) -> echo_totals:
+    t = echo_totals()
+    _check(ctx, load().echo_reduce(ctx, ctypes.byref(t)))
+    return t
+
+
+ECHO_NK = 12
+
+
+def echo_profile(ctx, enable: bool):
+    _check(ctx, load().echo_profile(ctx, 1 if enable else 0))
+
+
+def echo_profile_read(ctx) -> dict:
+    """{kernel name: (total ms, launches)} since the last read."""
+    ms = (ctypes.c_double * ECHO_NK)()
+    n = (ctypes.c_longlong * ECHO_NK)()
+    _check(ctx, load().echo_profile_read(ctx, ms, n, ECHO_NK))
+    return {echo_kernel_name(k): (ms[k], n[k]) for k in range(ECHO_NK)}
+
+
+def echo_kernel_name(k: int) -> str:
+    return (load().echo_kernel_name(int(k)) or b"").decode()
+
+
+def echo_last_error(ctx) -> str:
+    return (load().echo_last_error(ctx) or b"").decode()
+
+
+def echo_destroy(ctx):
+    load().echo_destroy(ctx)

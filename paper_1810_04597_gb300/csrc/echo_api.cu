@@ -1,0 +1,614 @@
+// echo_api.cu -- extern "C" entry points of include/echo.h.
+//
+// Host-side orchestration only: validation, workspace layout, and the
+// order of kernel launches for c2p, L(U) and one SSP-RK3 step.  Every
+// operation on the state runs in the kernels of echo_kernels.cu.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/echo.h"
+#include "echo_device.cuh"
+#include "echo_launch.h"
+
+using namespace echo;
+
+struct echo_ctx {
+    echo_grid grid;
+    echo_metric metric;
+    echo_eos eos;
+    int precision;
+    double cfl;
+    Geom geo;
+    Phys ph;
+    size_t ws_need = 0;
+    char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    bool bound = false;
+    bool have_state = false;
+    Arrays<double> ad;
+    Arrays<float> af;
+    size_t nstate = 0;
+    size_t staging_count = 0;
+    int nblk_red = 0;
+    std::string err;
+    // per-kernel timing (echo_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;      // pool, pairs (start, end)
+    std::vector<int> ev_kind;         // kernel class of each recorded pair
+    size_t ev_used = 0;               // pairs in use
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int fail(echo_ctx *c, int code, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    return code;
+}
+
+int cuda_check(echo_ctx *c, const char *where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(c, ECHO_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return ECHO_OK;
+}
+
+// Walk the workspace in a fixed order; with base == nullptr only sizes.
+template <typename R>
+size_t layout(echo_ctx *c, char *base, Arrays<R> *A)
+{
+    size_t off = 0;
+    const size_t cells = (size_t)c->geo.cells_padded;
+    auto take = [&](size_t bytes) -> char * {
+        off = align_up(off, ALIGN);
+        char *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    auto arr = [&]() -> R * { return reinterpret_cast<R *>(take(cells * sizeof(R))); };
+    for (int q = 0; q < 8; ++q)
+        A->U[q] = arr();
+    for (int q = 0; q < 8; ++q)
+        A->U0[q] = arr();
+    for (int q = 0; q < 8; ++q)
+        A->P[q] = arr();
+    for (int d = 0; d < 3; ++d) {
+        for (int q = 0; q < 5; ++q)
+            A->F[d][q] = arr();
+        A->ap[d] = arr();
+        A->am[d] = arr();
+        for (int q = 0; q < 4; ++q)
+            A->fv[d][q] = arr();
+        A->E[d] = arr();
+    }
+    A->Z = reinterpret_cast<double *>(take(cells * sizeof(double)));
+    A->stage = reinterpret_cast<double *>(take(c->staging_count * sizeof(double)));
+    A->partials = reinterpret_cast<double *>(take((size_t)c->nblk_red * 6 * sizeof(double)));
+    A->scal = reinterpret_cast<DevScalars *>(take(sizeof(DevScalars)));
+    return align_up(off, ALIGN);
+}
+
+// Bracket one launch with two events when profiling is enabled.
+struct ProfScope {
+    echo_ctx *c;
+    size_t slot;
+    bool on;
+    ProfScope(echo_ctx *cc, int kind) : c(cc), slot(0), on(cc->prof)
+    {
+        if (!on)
+            return;
+        if (c->ev_used * 2 + 2 > c->ev.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+                on = false;
+                return;
+            }
+            c->ev.push_back(a);
+            c->ev.push_back(b);
+            c->ev_kind.push_back(kind);
+        }
+        slot = c->ev_used++;
+        c->ev_kind[slot] = kind;
+        cudaEventRecord(c->ev[2 * slot], c->stream);
+    }
+    ~ProfScope()
+    {
+        if (on)
+            cudaEventRecord(c->ev[2 * slot + 1], c->stream);
+    }
+};
+#define PROF(kind, stmt)              \
+    do {                              \
+        ProfScope _ps(c, (kind));     \
+        stmt;                         \
+    } while (0)
+
+template <typename R>
+FillList<R> face_list(const Arrays<R> &A)
+{
+    FillList<R> L{};
+    for (int d = 0; d < 3; ++d) {
+        L.a[d] = A.U[5 + d];
+        L.comp[d] = d;
+        L.face[d] = d;
+    }
+    L.count = 3;
+    return L;
+}
+
+template <typename R>
+FillList<R> prim_list(const Arrays<R> &A)
+{
+    FillList<R> L{};
+    const int comps[8] = {-1, 0, 1, 2, -1, 0, 1, 2};
+    for (int q = 0; q < 8; ++q) {
+        L.a[q] = A.P[q];
+        L.comp[q] = comps[q];
+        L.face[q] = -1;
+    }
+    L.count = 8;
+    return L;
+}
+
+template <typename R>
+Arrays<R> &arrays(echo_ctx *c);
+template <>
+Arrays<double> &arrays<double>(echo_ctx *c) { return c->ad; }
+template <>
+Arrays<float> &arrays<float>(echo_ctx *c) { return c->af; }
+
+// ---- operations, templated on the storage type
+
+template <typename R>
+void enqueue_rhs_pass(echo_ctx *c, int stage, double *Lout, bool want_rate, double dt_fixed)
+{
+    Arrays<R> &A = arrays<R>(c);
+    cudaStream_t s = c->stream;
+    PROF(ECHO_K_FILL_FACES, launch_fill<R>(c->geo, face_list(A), s));
+    PROF(ECHO_K_C2P, launch_c2p<R>(c->geo, c->ph, A, 0, want_rate ? 1 : 0, s));
+    if (want_rate)
+        PROF(ECHO_K_SCALARS, launch_set_dt(A.scal, c->cfl, dt_fixed <= 0.0 ? 1 : 0, s));
+    PROF(ECHO_K_FILL_PRIMS, launch_fill<R>(c->geo, prim_list(A), s));
+    for (int d = 0; d < 3; ++d)
+        PROF(ECHO_K_FACES_X + d, launch_faces<R>(c->geo, c->ph, A, d, s));
+    for (int e = 0; e < 3; ++e)
+        PROF(ECHO_K_EMF_X + e, launch_emf<R>(c->geo, A, e, s));
+    PROF(ECHO_K_UPDATE, launch_update<R>(c->geo, A, stage, Lout, s));
+}
+
+template <typename R>
+int op_step(echo_ctx *c, double dt)
+{
+    Arrays<R> &A = arrays<R>(c);
+    PROF(ECHO_K_SCALARS, launch_step_begin(A.scal, dt > 0.0 ? dt : 0.0, c->stream));
+    for (int st = 0; st < 3; ++st)
+        enqueue_rhs_pass<R>(c, st, nullptr, st == 0, dt);
+    return cuda_check(c, "echo_step");
+}
+
+template <typename R>
+int op_rhs(echo_ctx *c, double *Lout)
+{
+    Arrays<R> &A = arrays<R>(c);
+    launch_step_begin(A.scal, 0.0, c->stream);
+    enqueue_rhs_pass<R>(c, -1, Lout, true, 0.0);
+    return cuda_check(c, "echo_rhs");
+}
+
+template <typename R>
+int op_c2p(echo_ctx *c, int guess_mode)
+{
+    Arrays<R> &A = arrays<R>(c);
+    PROF(ECHO_K_SCALARS, launch_step_begin(A.scal, 0.0, c->stream));
+    PROF(ECHO_K_FILL_FACES, launch_fill<R>(c->geo, face_list(A), c->stream));
+    PROF(ECHO_K_C2P, launch_c2p<R>(c->geo, c->ph, A, guess_mode, 1, c->stream));
+    PROF(ECHO_K_SCALARS, launch_set_dt(A.scal, c->cfl, 1, c->stream));
+    return cuda_check(c, "echo_c2p");
+}
+
+int read_scalars(echo_ctx *c, DevScalars *hs)
+{
+    DevScalars *ds = c->precision == 64 ? c->ad.scal : c->af.scal;
+    if (cudaMemcpyAsync(hs, ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return cuda_check(c, "read scalars");
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return cuda_check(c, "synchronize");
+    return ECHO_OK;
+}
+
+int require_bound(echo_ctx *c, bool need_state)
+{
+    if (!c)
+        return ECHO_EINVAL;
+    if (!c->bound)
+        return fail(c, ECHO_ESTATE, "context has no workspace: call echo_bind first");
+    if (need_state && !c->have_state)
+        return fail(c, ECHO_ESTATE, "no state: call echo_set_prims or echo_set_state first");
+    return ECHO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *eos, int precision, double cfl,
+              echo_ctx **out)
+{
+    if (!out)
+        return ECHO_EINVAL;
+    *out = nullptr;
+    if (!grid || !metric || !eos)
+        return ECHO_EINVAL;
+    for (int d = 0; d < 3; ++d) {
+        if (grid->n[d] < 1 || !(grid->dx[d] > 0.0))
+            return ECHO_EINVAL;
+        const int lo = grid->bc[2 * d], hi = grid->bc[2 * d + 1];
+        if (lo < 0 || lo > 2 || hi < 0 || hi > 2)
+            return ECHO_EINVAL;
+        if ((lo == ECHO_BC_PERIODIC) != (hi == ECHO_BC_PERIODIC))
+            return ECHO_EINVAL;
+        if ((lo == ECHO_BC_AXIS || hi == ECHO_BC_AXIS) && grid->n[d] < NG)
+            return ECHO_EINVAL;
+    }
+    if (metric->kind != ECHO_METRIC_FLAT)
+        return ECHO_EINVAL;  // only the flat metric has device kernels
+    if (!(eos->gamma > 1.0) || !(cfl > 0.0) || (precision != 64 && precision != 32))
+        return ECHO_EINVAL;
+    const long long cells = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+    if (cells > (1LL << 31))
+        return ECHO_EINVAL;
+
+    echo_ctx *c = new (std::nothrow) echo_ctx();
+    if (!c)
+        return ECHO_ENOMEM;
+    c->grid = *grid;
+    c->metric = *metric;
+    c->eos = *eos;
+    c->precision = precision;
+    c->cfl = cfl;
+    Geom &g = c->geo;
+    for (int d = 0; d < 3; ++d) {
+        g.n[d] = grid->n[d];
+        g.np[d] = grid->n[d] + 2 * NG;
+        g.dx[d] = grid->dx[d];
+        g.idx[d] = 1.0 / grid->dx[d];
+        g.x0[d] = grid->x0[d];
+        g.bc[2 * d] = grid->bc[2 * d];
+        g.bc[2 * d + 1] = grid->bc[2 * d + 1];
+        const bool per = grid->bc[2 * d] == ECHO_BC_PERIODIC;
+        g.flo[d] = NG + (grid->bc[2 * d] == ECHO_BC_AXIS ? 1 : 0);
+        g.fhi[d] = per ? NG + g.n[d] - 1 : NG + g.n[d] - (grid->bc[2 * d + 1] == ECHO_BC_AXIS ? 1 : 0);
+    }
+    g.px = (long long)align_up((size_t)g.np[0], 8);
+    g.pxy = g.px * g.np[1];
+    g.cells_padded = g.pxy * g.np[2];
+    c->ph.gamma = eos->gamma;
+    c->ph.gr = eos->gamma / (eos->gamma - 1.0);
+    c->ph.gm1g = (eos->gamma - 1.0) / eos->gamma;
+    c->ph.cfl = cfl;
+    const size_t N = (size_t)cells;
+    c->nstate = 5 * N + (size_t)g.n[2] * g.n[1] * (g.n[0] + 1) + (size_t)g.n[2] * (g.n[1] + 1) * g.n[0]
+                + (size_t)(g.n[2] + 1) * g.n[1] * g.n[0];
+    c->staging_count = c->nstate > 8 * N ? c->nstate : 8 * N;
+    c->nblk_red = 152 * 4;
+    if (precision == 64)
+        c->ws_need = layout<double>(c, nullptr, &c->ad);
+    else
+        c->ws_need = layout<float>(c, nullptr, &c->af);
+    *out = c;
+    return ECHO_OK;
+}
+
+size_t echo_workspace_bytes(const echo_ctx *c) { return c ? c->ws_need : 0; }
+
+size_t echo_state_count(const echo_ctx *c) { return c ? c->nstate : 0; }
+
+int echo_bind(echo_ctx *c, void *ws, size_t bytes, void *stream)
+{
+    if (!c)
+        return ECHO_EINVAL;
+    if (!ws || ((uintptr_t)ws % ALIGN) != 0)
+        return fail(c, ECHO_EINVAL, "workspace must be a non-null 256-byte aligned device pointer");
+    if (bytes < c->ws_need)
+        return fail(c, ECHO_ENOMEM, "workspace smaller than echo_workspace_bytes");
+    c->ws = static_cast<char *>(ws);
+    c->stream = static_cast<cudaStream_t>(stream);
+    if (c->precision == 64)
+        layout<double>(c, c->ws, &c->ad);
+    else
+        layout<float>(c, c->ws, &c->af);
+    if (cudaMemsetAsync(c->ws, 0, c->ws_need, c->stream) != cudaSuccess)
+        return cuda_check(c, "echo_bind memset");
+    c->bound = true;
+    c->have_state = false;
+    return cuda_check(c, "echo_bind");
+}
+
+static const double *stage_input(echo_ctx *c, const double *src, size_t count, size_t at, int on_device,
+                                 int *rc)
+{
+    *rc = ECHO_OK;
+    if (on_device)
+        return src;
+    double *st = (c->precision == 64 ? c->ad.stage : c->af.stage) + at;
+    if (cudaMemcpyAsync(st, src, count * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        *rc = cuda_check(c, "host to device copy");
+    return st;
+}
+
+int echo_set_prims(echo_ctx *c, const double *prims5, const double *bface, int on_device)
+{
+    int rc = require_bound(c, false);
+    if (rc)
+        return rc;
+    if (!prims5 || !bface)
+        return fail(c, ECHO_EINVAL, "null pointer");
+    const size_t N = (size_t)c->geo.n[0] * c->geo.n[1] * c->geo.n[2];
+    const double *dp = stage_input(c, prims5, 5 * N, 0, on_device, &rc);
+    if (rc)
+        return rc;
+    const double *df = stage_input(c, bface, c->nstate - 5 * N, 5 * N, on_device, &rc);
+    if (rc)
+        return rc;
+    if (c->precision == 64) {
+        launch_unpack_state<double>(c->geo, df, c->ad, 1, c->stream);
+        launch_fill<double>(c->geo, face_list(c->ad), c->stream);
+        launch_p2c<double>(c->geo, c->ph, dp, c->ad, c->stream);
+    } else {
+        launch_unpack_state<float>(c->geo, df, c->af, 1, c->stream);
+        launch_fill<float>(c->geo, face_list(c->af), c->stream);
+        launch_p2c<float>(c->geo, c->ph, dp, c->af, c->stream);
+    }
+    rc = cuda_check(c, "echo_set_prims");
+    if (rc == ECHO_OK)
+        c->have_state = true;
+    return rc;
+}
+
+int echo_set_state(echo_ctx *c, const double *state, const double *Z, int on_device)
+{
+    int rc = require_bound(c, false);
+    if (rc)
+        return rc;
+    if (!state)
+        return fail(c, ECHO_EINVAL, "null state");
+    const size_t N = (size_t)c->geo.n[0] * c->geo.n[1] * c->geo.n[2];
+    const double *ds = stage_input(c, state, c->nstate, 0, on_device, &rc);
+    if (rc)
+        return rc;
+    if (c->precision == 64)
+        launch_unpack_state<double>(c->geo, ds, c->ad, 0, c->stream);
+    else
+        launch_unpack_state<float>(c->geo, ds, c->af, 0, c->stream);
+    const double *dz = nullptr;
+    if (Z) {
+        // the staging area is free again once the unpack above has run
+        dz = stage_input(c, Z, N, 0, on_device, &rc);
+        if (rc)
+            return rc;
+    }
+    if (c->precision == 64)
+        launch_unpack_z<double>(c->geo, dz, c->ad, c->stream);
+    else
+        launch_unpack_z<float>(c->geo, dz, c->af, c->stream);
+    rc = cuda_check(c, "echo_set_state");
+    if (rc == ECHO_OK)
+        c->have_state = true;
+    return rc;
+}
+
+static int finish_output(echo_ctx *c, double *dst, const double *staged, size_t count, int on_device)
+{
+    if (!on_device) {
+        if (cudaMemcpyAsync(dst, staged, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            return cuda_check(c, "device to host copy");
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return cuda_check(c, "synchronize");
+    return cuda_check(c, "output");
+}
+
+int echo_get_state(echo_ctx *c, double *out, int on_device)
+{
+    int rc = require_bound(c, true);
+    if (rc)
+        return rc;
+    if (!out)
+        return fail(c, ECHO_EINVAL, "null output");
+    double *dst = on_device ? out : (c->precision == 64 ? c->ad.stage : c->af.stage);
+    if (c->precision == 64) {
+        launch_fill<double>(c->geo, face_list(c->ad), c->stream);
+        launch_pack_state<double>(c->geo, c->ad, dst, c->stream);
+    } else {
+        launch_fill<float>(c->geo, face_list(c->af), c->stream);
+        launch_pack_state<float>(c->geo, c->af, dst, c->stream);
+    }
+    return finish_output(c, out, dst, c->nstate, on_device);
+}
+
+int echo_get_prims(echo_ctx *c, double *out, int on_device)
+{
+    int rc = require_bound(c, true);
+    if (rc)
+        return rc;
+    if (!out)
+        return fail(c, ECHO_EINVAL, "null output");
+    const size_t N = (size_t)c->geo.n[0] * c->geo.n[1] * c->geo.n[2];
+    double *dst = on_device ? out : (c->precision == 64 ? c->ad.stage : c->af.stage);
+    if (c->precision == 64)
+        launch_pack_cells<double>(c->geo, c->ad, dst, 0, c->stream);
+    else
+        launch_pack_cells<float>(c->geo, c->af, dst, 0, c->stream);
+    return finish_output(c, out, dst, 8 * N, on_device);
+}
+
+int echo_get_z(echo_ctx *c, double *out, int on_device)
+{
+    int rc = require_bound(c, true);
+    if (rc)
+        return rc;
+    if (!out)
+        return fail(c, ECHO_EINVAL, "null output");
+    const size_t N = (size_t)c->geo.n[0] * c->geo.n[1] * c->geo.n[2];
+    double *dst = on_device ? out : (c->precision == 64 ? c->ad.stage : c->af.stage);
+    if (c->precision == 64)
+        launch_pack_cells<double>(c->geo, c->ad, dst, 1, c->stream);
+    else
+        launch_pack_cells<float>(c->geo, c->af, dst, 1, c->stream);
+    return finish_output(c, out, dst, N, on_device);
+}
+
+int echo_c2p(echo_ctx *c, int guess_mode, echo_totals *stats)
+{
+    int rc = require_bound(c, true);
+    if (rc)
+        return rc;
+    if (guess_mode != 0 && guess_mode != 2)
+        return fail(c, ECHO_EINVAL, "guess_mode must be 0 (previous Z) or 2 (cold)");
+    rc = c->precision == 64 ? op_c2p<double>(c, guess_mode) : op_c2p<float>(c, guess_mode);
+    if (rc || !stats)
+        return rc;
+    DevScalars hs;
+    rc = read_scalars(c, &hs);
+    if (rc)
+        return rc;
+    stats->dt_cfl = hs.dt;
+    stats->c2p_iters = (long long)hs.c2p_iters;
+    stats->c2p_calls = (long long)hs.c2p_calls;
+    stats->c2p_fail = (long long)hs.c2p_fail;
+    stats->floor_hits = (long long)hs.floor_hits;
+    if (hs.fail_since_check) {
+        DevScalars *ds = c->precision == 64 ? c->ad.scal : c->af.scal;
+        cudaMemsetAsync(&ds->fail_since_check, 0, sizeof(unsigned long long), c->stream);
+        if (!c->eos.floors)
+            return fail(c, ECHO_EC2P, "conservative-to-primitive inversion failed in some cells");
+    }
+    return ECHO_OK;
+}
+
+int echo_rhs(echo_ctx *c, double *L, int on_device)
+{
+    int rc = require_bound(c, true);
+    if (rc)
+        return rc;
+    if (!L)
+        return fail(c, ECHO_EINVAL, "null output");
+    double *dst = on_device ? L : (c->precision == 64 ? c->ad.stage : c->af.stage);
+    rc = c->precision == 64 ? op_rhs<double>(c, dst) : op_rhs<float>(c, dst);
+    if (rc)
+        return rc;
+    if (!on_device)
+        return finish_output(c, L, dst, c->nstate, 0);
+    return ECHO_OK;
+}
+
+int echo_step(echo_ctx *c, double dt)
+{
+    int rc = require_bound(c, true);
+    if (rc)
+        return rc;
+    return c->precision == 64 ? op_step<double>(c, dt) : op_step<float>(c, dt);
+}
+
+int echo_reduce(echo_ctx *c, echo_totals *out)
+{
+    int rc = require_bound(c, true);
+    if (rc)
+        return rc;
+    if (!out)
+        return fail(c, ECHO_EINVAL, "null output");
+    rc = c->precision == 64 ? op_c2p<double>(c, 0) : op_c2p<float>(c, 0);
+    if (rc)
+        return rc;
+    if (c->precision == 64)
+        PROF(ECHO_K_TOTALS, launch_totals<double>(c->geo, c->ad, c->nblk_red, c->stream));
+    else
+        PROF(ECHO_K_TOTALS, launch_totals<float>(c->geo, c->af, c->nblk_red, c->stream));
+    rc = cuda_check(c, "echo_reduce");
+    if (rc)
+        return rc;
+    DevScalars hs;
+    rc = read_scalars(c, &hs);
+    if (rc)
+        return rc;
+    out->dt_cfl = hs.dt;
+    out->mass = hs.totals[0];
+    out->energy = hs.totals[1];
+    out->mom[0] = hs.totals[2];
+    out->mom[1] = hs.totals[3];
+    out->mom[2] = hs.totals[4];
+    out->max_divb = hs.totals[5];
+    out->c2p_iters = (long long)hs.c2p_iters;
+    out->c2p_calls = (long long)hs.c2p_calls;
+    out->c2p_fail = (long long)hs.c2p_fail;
+    out->floor_hits = (long long)hs.floor_hits;
+    out->fallback_faces = 0;
+    if (hs.fail_since_check) {
+        DevScalars *ds = c->precision == 64 ? c->ad.scal : c->af.scal;
+        cudaMemsetAsync(&ds->fail_since_check, 0, sizeof(unsigned long long), c->stream);
+        if (!c->eos.floors)
+            return fail(c, ECHO_EC2P, "conservative-to-primitive inversion failed in some cells");
+    }
+    return ECHO_OK;
+}
+
+int echo_profile(echo_ctx *c, int enable)
+{
+    if (!c)
+        return ECHO_EINVAL;
+    c->prof = enable != 0;
+    return ECHO_OK;
+}
+
+int echo_profile_read(echo_ctx *c, double *ms, long long *launches, int nk)
+{
+    if (!c || !ms || !launches || nk < 0)
+        return ECHO_EINVAL;
+    for (int k = 0; k < nk; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    if (c->ev_used && cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return cuda_check(c, "echo_profile_read");
+    for (size_t p = 0; p < c->ev_used; ++p) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, c->ev[2 * p], c->ev[2 * p + 1]) != cudaSuccess)
+            return cuda_check(c, "echo_profile_read elapsed");
+        const int k = c->ev_kind[p];
+        if (k >= 0 && k < nk) {
+            ms[k] += (double)t;
+            launches[k] += 1;
+        }
+    }
+    c->ev_used = 0;
+    return ECHO_OK;
+}
+
+const char *echo_kernel_name(int k)
+{
+    static const char *names[ECHO_NK] = {"fill_faces", "c2p", "fill_prims", "faces_x", "faces_y", "faces_z",
+                                         "emf_x", "emf_y", "emf_z", "update", "scalars", "totals"};
+    return (k >= 0 && k < ECHO_NK) ? names[k] : "";
+}
+
+const char *echo_last_error(const echo_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void echo_destroy(echo_ctx *c)
+{
+    if (!c)
+        return;
+    for (cudaEvent_t e : c->ev)
+        cudaEventDestroy(e);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,331 @@
+// echo_device.cuh -- device data structures and per-point physics of the
+// GRMHD step (flat metric).  Included by the kernel translation units only.
+//
+// Arithmetic follows the published methods named in include/echo.h; it is
+// written for the GPU (one division per reciprocal reused, rsqrt for the
+// Lorentz factor, compile-time direction), so it differs from a textbook
+// transcription only by rounding order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace echo {
+
+constexpr int NG = 3;              // ghost layers (MP5: 3 cells per side)
+constexpr double MP5_ALPHA = 4.0;  // Suresh & Huynh (1997) alpha
+constexpr double MP5_EPS = 1e-10;  // Suresh & Huynh (1997) epsilon
+constexpr double NEWTON_TOL = 1e-13;
+constexpr int NEWTON_MAXIT = 50;
+constexpr int NEWTON_MAXHALF = 30;
+
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_AXIS = 2 };
+
+// Geometry of the padded grid: every field (cell or face centred) is an
+// array of np0*np1*np2 elements with row pitch px (>= np0) and plane pitch
+// pxy = px*np1.  Face array d holds the face i-1/2 at index i along d.
+struct Geom {
+    int n[3];
+    int np[3];
+    long long px, pxy;
+    long long cells_padded;  // pxy * np2
+    double dx[3];
+    double idx[3];           // 1/dx
+    double x0[3];
+    int bc[6];
+    int flo[3], fhi[3];      // owned (evolved) face range along d, inclusive
+};
+
+__host__ __device__ __forceinline__ long long gidx(const Geom &g, int i, int j, int k)
+{
+    return (long long)k * g.pxy + (long long)j * g.px + i;
+}
+
+struct Phys {
+    double gamma;     // adiabatic index
+    double gr;        // gamma / (gamma - 1)
+    double gm1g;      // (gamma - 1) / gamma
+    double cfl;
+};
+
+// Device-resident scalars of a context.
+struct DevScalars {
+    double dt;                   // dt of the running step
+    unsigned long long rate_bits;  // max CFL rate (bits of a non-negative double)
+    unsigned long long c2p_iters;
+    unsigned long long c2p_calls;
+    unsigned long long c2p_fail;
+    unsigned long long floor_hits;
+    unsigned long long fail_since_check;
+    double totals[8];            // mass, energy, mom x3, max divB, rate, spare
+};
+
+// All device arrays of a context, R = storage type of the bulk fields.
+template <typename R>
+struct Arrays {
+    R *U[8];       // conserved: D, S_x, S_y, S_z, tau (cell), B~x, B~y, B~z (faces)
+    R *U0[8];      // RK base state
+    double *Z;     // Newton memory (cell)
+    R *P[8];       // primitives rho, v^x, v^y, v^z, p, B^x, B^y, B^z (cell)
+    R *F[3][5];    // HLL fluxes on d-faces
+    R *ap[3];      // HLL a+ on d-faces
+    R *am[3];      // HLL a- on d-faces
+    R *fv[3][4];   // d-face states used by the EMFs: v^d_L, v^d_R, v^{d+1}_L, v^{d+1}_R
+    R *E[3];       // edge EMFs: E_e at index (i,j,k) = edge at half-integer a, b
+    double *stage; // host-layout staging (FP64)
+    double *partials;  // reduction partials
+    DevScalars *scal;
+};
+
+// ------------------------------------------------------------------ MP5
+
+template <typename T>
+__device__ __forceinline__ T minmod2(T a, T b)
+{
+    const bool same = (a > T(0) && b > T(0)) || (a < T(0) && b < T(0));
+    return same ? copysign(fmin(fabs(a), fabs(b)), a) : T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ T minmod4(T w, T x, T y, T z)
+{
+    const bool pos = w > T(0) && x > T(0) && y > T(0) && z > T(0);
+    const bool neg = w < T(0) && x < T(0) && y < T(0) && z < T(0);
+    const T m = fmin(fmin(fabs(w), fabs(x)), fmin(fabs(y), fabs(z)));
+    return pos ? m : (neg ? -m : T(0));
+}
+
+// Interface value between u0 = u_j and up1 = u_{j+1}, biased to u_j
+// (Suresh & Huynh 1997): fifth-order interpolant of cell averages, kept
+// inside the monotonicity/accuracy-preserving interval.
+template <typename T>
+__device__ __forceinline__ T mp5(T um2, T um1, T u0, T up1, T up2)
+{
+    const T uor = (T(2) * um2 - T(13) * um1 + T(47) * u0 + T(27) * up1 - T(3) * up2) * T(1.0 / 60.0);
+    const T ump = u0 + minmod2(up1 - u0, T(MP5_ALPHA) * (u0 - um1));
+    if ((uor - u0) * (uor - ump) <= T(MP5_EPS))
+        return uor;
+    const T dm1 = um2 - T(2) * um1 + u0;
+    const T d0 = um1 - T(2) * u0 + up1;
+    const T dp1 = u0 - T(2) * up1 + up2;
+    const T dMp = minmod4(T(4) * d0 - dp1, T(4) * dp1 - d0, d0, dp1);
+    const T dMm = minmod4(T(4) * d0 - dm1, T(4) * dm1 - d0, d0, dm1);
+    const T uul = u0 + T(MP5_ALPHA) * (u0 - um1);
+    const T uav = T(0.5) * (u0 + up1);
+    const T umd = uav - T(0.5) * dMp;
+    const T ulc = u0 + T(0.5) * (u0 - um1) + T(4.0 / 3.0) * dMm;
+    const T umin = fmax(fmin(fmin(u0, up1), umd), fmin(fmin(u0, uul), ulc));
+    const T umax = fmin(fmax(fmax(u0, up1), umd), fmax(fmax(u0, uul), ulc));
+    return uor + minmod2(umin - uor, umax - uor);
+}
+
+// Left/right states at the face between q[2] and q[3] of q[0..5].
+template <typename T>
+__device__ __forceinline__ void mp5_lr(const T q[6], T &L, T &R)
+{
+    L = mp5(q[0], q[1], q[2], q[3], q[4]);
+    R = mp5(q[5], q[4], q[3], q[2], q[1]);
+}
+
+// ------------------------------------------------------------------ state
+
+// Flat-metric conserved vector, physical flux along D and HLL speeds of a
+// primitive state P = (rho, v^x, v^y, v^z, p, B^x, B^y, B^z).
+//   D = rho W, S_j = (rho h W^2 + B^2) v_j - (v.B) B_j,
+//   tau = rho h W^2 - p + (B^2 + B^2 v^2 - (v.B)^2)/2 - D;
+//   F(D) = D v^d, F(S_j) = (rho h + b^2) W^2 v^d v_j + (p + b^2/2) delta_dj - b^d b_j,
+//   F(tau) = S_d - D v^d, with b^i = B^i/W + W (v.B) v^i, b^2 = B^2/W^2 + (v.B)^2;
+//   a^2 = c_s^2 + c_A^2 - c_s^2 c_A^2 = (G p + b^2)/(rho h + b^2),
+//   lambda = [v^d (1 - a^2) +- sqrt(a^2 (1-v^2)((1 - v^2 a^2) - (1 - a^2)(v^d)^2))]
+//            / (1 - v^2 a^2).
+template <int D, typename T>
+__device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, T F[5], T U[5], T &lp, T &lm)
+{
+    const T rho = P[0], vx = P[1], vy = P[2], vz = P[3], p = P[4];
+    const T Bx = P[5], By = P[6], Bz = P[7];
+    const T v2 = vx * vx + vy * vy + vz * vz;
+    const T B2 = Bx * Bx + By * By + Bz * Bz;
+    const T vB = vx * Bx + vy * By + vz * Bz;
+    const T iW2 = T(1) - v2;
+    const T W = rsqrt(iW2);
+    const T iW = iW2 * W;
+    const T W2 = W * W;
+    const T rhoh = rho + gr * p;
+    const T b2 = B2 * iW2 + vB * vB;
+    const T Dn = rho * W;
+    const T Zw = rhoh * W2;
+    const T ZB = Zw + B2;
+    const T v[3] = {vx, vy, vz};
+    const T B[3] = {Bx, By, Bz};
+    U[0] = Dn;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        U[1 + j] = ZB * v[j] - vB * B[j];
+    U[4] = Zw - p + T(0.5) * (B2 + B2 * v2 - vB * vB) - Dn;
+    const T vd = v[D];
+    const T Wvb = W * vB;
+    const T bd = B[D] * iW + Wvb * vd;
+    const T wt = (rhoh + b2) * W2 * vd;
+    F[0] = Dn * vd;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const T bj = B[j] * iW + Wvb * v[j];
+        F[1 + j] = wt * v[j] - bd * bj + (j == D ? p + T(0.5) * b2 : T(0));
+    }
+    F[4] = U[1 + D] - Dn * vd;
+    const T a2 = (gam * p + b2) / (rhoh + b2);
+    const T disc = a2 * iW2 * ((T(1) - v2 * a2) - (T(1) - a2) * vd * vd);
+    const T sq = sqrt(fmax(disc, T(0)));
+    const T iden = T(1) / (T(1) - v2 * a2);
+    const T base = vd * (T(1) - a2);
+    lp = (base + sq) * iden;
+    lm = (base - sq) * iden;
+}
+
+// Sum over directions of max(|lambda+|, |lambda-|)/dx (CFL rate) of a cell.
+__device__ __forceinline__ double cfl_rate(const double P[8], double gam, double gr, const double idx[3])
+{
+    const double vx = P[1], vy = P[2], vz = P[3], p = P[4];
+    const double v2 = vx * vx + vy * vy + vz * vz;
+    const double B2 = P[5] * P[5] + P[6] * P[6] + P[7] * P[7];
+    const double vB = vx * P[5] + vy * P[6] + vz * P[7];
+    const double iW2 = 1.0 - v2;
+    const double rhoh = P[0] + gr * p;
+    const double b2 = B2 * iW2 + vB * vB;
+    const double a2 = (gam * p + b2) / (rhoh + b2);
+    const double iden = 1.0 / (1.0 - v2 * a2);
+    const double v[3] = {vx, vy, vz};
+    double s = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double disc = a2 * iW2 * ((1.0 - v2 * a2) - (1.0 - a2) * v[d] * v[d]);
+        const double sq = sqrt(fmax(disc, 0.0));
+        const double base = v[d] * (1.0 - a2);
+        const double lp = (base + sq) * iden, lm = (base - sq) * iden;
+        s += fmax(fabs(lp), fabs(lm)) * idx[d];
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------ c2p
+
+// Newton iteration on Z = rho h W^2 (flat metric, FP64 always).
+//   v^2(Z) = [S^2 Z^2 + (S.B)^2 (2Z + B^2)] / [Z^2 (Z + B^2)^2]
+//   p(Z)   = (G-1)/G [Z (1 - v^2) - D sqrt(1 - v^2)]
+//   f(Z)   = Z - p + (1 + v^2) B^2 / 2 - (S.B)^2 / (2 Z^2) - (tau + D)
+// An inadmissible guess (Z <= 0 or v^2 >= 1) is replaced by doubling
+// max(Z, tau + D); a step leaving the admissible set is halved (<= 30 times);
+// stop at |dZ| <= 1e-13 Z or after 50 iterations.
+struct C2PResult {
+    double rho, v[3], p, Z;
+    int iters;
+    bool ok;
+};
+
+__device__ __forceinline__ double c2p_v2(double Z, double S2, double SB2, double B2)
+{
+    const double ZB = Z + B2;
+    return (S2 * Z * Z + SB2 * (2.0 * Z + B2)) / (Z * Z * ZB * ZB);
+}
+
+__device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], double tau, const double B[3],
+                                                double Zguess, double gm1g)
+{
+    const double S2 = S[0] * S[0] + S[1] * S[1] + S[2] * S[2];
+    const double SB = S[0] * B[0] + S[1] * B[1] + S[2] * B[2];
+    const double SB2 = SB * SB;
+    const double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const double Uen = tau + Dc;
+    C2PResult r;
+    double Z = Zguess;
+    int tries = 0;
+    bool ok = true;
+    while (!(Z > 0.0) || !(c2p_v2(Z, S2, SB2, B2) < 1.0)) {
+        Z = 2.0 * fmax(Z, Uen);
+        if (++tries > 60) {
+            ok = false;
+            break;
+        }
+    }
+    int it = 0;
+    bool conv = false;
+    while (ok && it < NEWTON_MAXIT) {
+        ++it;
+        const double Z2 = Z * Z;
+        const double ZB = Z + B2;
+        const double den = 1.0 / (Z2 * ZB * ZB);
+        const double v2 = (S2 * Z2 + SB2 * (2.0 * Z + B2)) * den;
+        const double sq = sqrt(1.0 - v2);
+        const double p = gm1g * (Z * (1.0 - v2) - Dc * sq);
+        const double iZ = 1.0 / Z;
+        const double f = Z - p + 0.5 * (1.0 + v2) * B2 - 0.5 * SB2 * iZ * iZ - Uen;
+        const double dv2 = -2.0 * (S2 * Z2 * Z + SB2 * (3.0 * Z2 + 3.0 * Z * B2 + B2 * B2)) * den * iZ / ZB;
+        const double dp = gm1g * ((1.0 - v2) - Z * dv2 + 0.5 * Dc * dv2 / sq);
+        const double fp = 1.0 - dp + 0.5 * B2 * dv2 + SB2 * iZ * iZ * iZ;
+        double dZ = f / fp;
+        double Zn = Z - dZ;
+        int h = 0;
+        while ((!(Zn > 0.0) || !(c2p_v2(Zn, S2, SB2, B2) < 1.0)) && h < NEWTON_MAXHALF) {
+            dZ *= 0.5;
+            Zn = Z - dZ;
+            ++h;
+        }
+        if (!(Zn > 0.0) || !(c2p_v2(Zn, S2, SB2, B2) < 1.0))
+            break;
+        Z = Zn;
+        if (fabs(dZ) <= NEWTON_TOL * Z) {
+            conv = true;
+            break;
+        }
+    }
+    const double v2 = c2p_v2(Z, S2, SB2, B2);
+    const double sq = sqrt(1.0 - v2);
+    const double p = gm1g * (Z * (1.0 - v2) - Dc * sq);
+    const double ivs = 1.0 / (Z + B2);
+    const double sbz = SB / Z;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        r.v[j] = (S[j] + sbz * B[j]) * ivs;
+    r.rho = Dc * sq;
+    r.p = p;
+    r.Z = Z;
+    r.iters = it;
+    r.ok = ok && conv && p > 0.0 && r.rho > 0.0;
+    return r;
+}
+
+// ------------------------------------------------------------------ bc
+
+// Source index along one axis for padded index i (cell array: face = 0,
+// d-face array: face = 1); returns i itself for an owned entry, -1 for the
+// polar-axis face (value 0).  *flip: sign change under axis reflection.
+__device__ __forceinline__ int bc_src(int i, int n, int face, int bclo, int bchi, bool &flip)
+{
+    flip = false;
+    const int lo = NG;
+    int hi = NG + n - 1 + face;
+    if (face && bclo == BC_PERIODIC)
+        hi = NG + n - 1;
+    if (i >= lo && i <= hi)
+        return i;
+    const int side = i < lo ? 0 : 1;
+    const int kind = side == 0 ? bclo : bchi;
+    if (kind == BC_PERIODIC) {
+        int r = (i - NG) % n;
+        if (r < 0)
+            r += n;
+        return NG + r;
+    }
+    if (kind == BC_OUTFLOW)
+        return side == 0 ? lo : hi;
+    flip = true;
+    if (face) {
+        const int ax = side == 0 ? NG : NG + n;
+        if (i == ax)
+            return -1;
+        return 2 * ax - i;
+    }
+    return side == 0 ? 2 * NG - 1 - i : 2 * (NG + n) - 1 - i;
+}
+
+}  // namespace echo

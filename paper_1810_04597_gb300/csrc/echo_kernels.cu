@@ -1,0 +1,734 @@
+// echo_kernels.cu -- CUDA kernels of the GRMHD step (sm_103a).
+//
+// One pass of the hot path per RK stage:
+//   fill(face B~) -> c2p (FP64 Newton) -> fill(primitives)
+//   -> faces<x,y,z> (MP5 + HLL) -> emf<x,y,z> (UCT-HLL) -> update (flux
+//   difference + CT curl + SSP-RK3 combination).
+// Reductions (CFL rate, conserved totals, div B~) use warp shuffles and a
+// fixed block tree, so results are bitwise reproducible run to run.
+#include "echo_device.cuh"
+#include "echo_launch.h"
+
+namespace echo {
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ long long stride_of(const Geom &g, int d)
+{
+    return d == 0 ? 1LL : (d == 1 ? g.px : g.pxy);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------------ ghost fill
+
+// Fill the ghost slab of axis d for a list of arrays.  Thread (s, t1, t2):
+// s in [0, 2 NG) selects the ghost layer (lower layers 0..NG-1, upper
+// n+NG..n+2NG-1), t1/t2 run over the full padded extent of the other axes.
+template <typename R>
+__global__ void k_fill(Geom g, int d, FillList<R> L)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t1 = blockIdx.y * blockDim.y + threadIdx.y;
+    const int t2 = blockIdx.z;
+    const int d1 = d == 0 ? 1 : 0;
+    const int d2 = d == 2 ? 1 : 2;
+    if (s >= 2 * NG || t1 >= g.np[d1] || t2 >= g.np[d2])
+        return;
+    const int id_d = s < NG ? s : g.n[d] + s;
+    int ijk[3];
+    ijk[d] = id_d;
+    ijk[d1] = t1;
+    ijk[d2] = t2;
+    const long long dst = gidx(g, ijk[0], ijk[1], ijk[2]);
+    const long long sd = d == 0 ? 1LL : (d == 1 ? g.px : g.pxy);
+    for (int a = 0; a < L.count; ++a) {
+        bool flip;
+        const int face = L.face[a] == d ? 1 : 0;
+        const int src = bc_src(id_d, g.n[d], face, g.bc[2 * d], g.bc[2 * d + 1], flip);
+        if (src == id_d)
+            continue;
+        R val = R(0);
+        if (src >= 0) {
+            val = L.a[a][dst + (long long)(src - id_d) * sd];
+            if (flip && L.comp[a] == d)
+                val = -val;
+        }
+        L.a[a][dst] = val;
+    }
+}
+
+// ------------------------------------------------------------------ c2p
+
+// Conservative-to-primitive inversion of every owned cell (FP64 Newton);
+// cell-centre B = mean of the two faces.  Optionally accumulates the CFL
+// rate max (atomicMax on the bits of a non-negative double, order
+// independent) and the Newton counters.
+template <typename R>
+__global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate)
+{
+    const int i = NG + blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = NG + blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = NG + blockIdx.z;
+    const bool live = i < NG + g.n[0] && j < NG + g.n[1] && k < NG + g.n[2];
+    double rate = 0.0;
+    unsigned long long its = 0, calls = 0, fails = 0;
+    if (live) {
+        const long long id = gidx(g, i, j, k);
+        double B[3];
+        B[0] = 0.5 * ((double)A.U[5][id] + (double)A.U[5][id + 1]);
+        B[1] = 0.5 * ((double)A.U[6][id] + (double)A.U[6][id + g.px]);
+        B[2] = 0.5 * ((double)A.U[7][id] + (double)A.U[7][id + g.pxy]);
+        const double S[3] = {(double)A.U[1][id], (double)A.U[2][id], (double)A.U[3][id]};
+        const double zg = guess_mode == 2 ? 0.0 : A.Z[id];
+        const C2PResult r = c2p_newton((double)A.U[0][id], S, (double)A.U[4][id], B, zg, ph.gm1g);
+        A.P[0][id] = (R)r.rho;
+        A.P[1][id] = (R)r.v[0];
+        A.P[2][id] = (R)r.v[1];
+        A.P[3][id] = (R)r.v[2];
+        A.P[4][id] = (R)r.p;
+        A.P[5][id] = (R)B[0];
+        A.P[6][id] = (R)B[1];
+        A.P[7][id] = (R)B[2];
+        A.Z[id] = r.Z;
+        its = r.iters;
+        calls = 1;
+        fails = r.ok ? 0 : 1;
+        if (want_rate) {
+            const double P[8] = {r.rho, r.v[0], r.v[1], r.v[2], r.p, B[0], B[1], B[2]};
+            rate = cfl_rate(P, ph.gamma, ph.gr, g.idx);
+        }
+    }
+    // warp-aggregated counters
+    its = warp_sum_u64(its);
+    calls = warp_sum_u64(calls);
+    fails = warp_sum_u64(fails);
+    if (want_rate)
+        rate = warp_max(rate);
+    if ((threadIdx.x & 31) == 0) {
+        if (calls) {
+            atomicAdd(&A.scal->c2p_iters, its);
+            atomicAdd(&A.scal->c2p_calls, calls);
+        }
+        if (fails) {
+            atomicAdd(&A.scal->c2p_fail, fails);
+            atomicAdd(&A.scal->fail_since_check, fails);
+        }
+        if (want_rate && rate > 0.0)
+            atomicMax(&A.scal->rate_bits, (unsigned long long)__double_as_longlong(rate));
+    }
+}
+
+// ------------------------------------------------------------------ faces
+
+// MP5 left/right states, HLL flux and speeds on the D-faces.  Face index
+// along D runs over NG..NG+n (every face of an owned cell); transversally
+// the full padded range (the EMFs need face data three rows into the
+// ghosts).  A reconstructed side with rho <= 0, p <= 0 or v^2 >= 1 takes the
+// adjacent cell's primitives.
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
+{
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    int t[3];
+    t[0] = blockIdx.x * blockDim.x + threadIdx.x;
+    t[1] = blockIdx.y * blockDim.y + threadIdx.y;
+    t[2] = blockIdx.z;
+    int ijk[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (d == D) {
+            if (t[d] > g.n[d])
+                return;
+            ijk[d] = NG + t[d];
+        } else {
+            if (t[d] >= g.np[d])
+                return;
+            ijk[d] = t[d];
+        }
+    }
+    const long long id = gidx(g, ijk[0], ijk[1], ijk[2]);
+    const long long sd = D == 0 ? 1LL : (D == 1 ? g.px : g.pxy);
+    using T = R;
+    T PL[8], PR[8];
+    const int qs[7] = {0, 1, 2, 3, 4, 5 + T1, 5 + T2};
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+        const R *__restrict__ a = A.P[qs[m]];
+        T q[6];
+#pragma unroll
+        for (int s = 0; s < 6; ++s)
+            q[s] = a[id + (s - 3) * sd];
+        mp5_lr(q, PL[qs[m]], PR[qs[m]]);
+    }
+    const T Bn = A.U[5 + D][id];
+    PL[5 + D] = Bn;
+    PR[5 + D] = Bn;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        T *Ps = side == 0 ? PL : PR;
+        const T v2 = Ps[1] * Ps[1] + Ps[2] * Ps[2] + Ps[3] * Ps[3];
+        if (!(Ps[0] > T(0)) || !(Ps[4] > T(0)) || !(v2 < T(1))) {
+            const long long c = id + (side == 0 ? -sd : 0);
+#pragma unroll
+            for (int m = 0; m < 7; ++m)
+                Ps[qs[m]] = A.P[qs[m]][c];
+        }
+    }
+    T FL[5], UL[5], FR[5], UR[5], lpL, lmL, lpR, lmR;
+    state_flux<D>(PL, (T)ph.gamma, (T)ph.gr, FL, UL, lpL, lmL);
+    state_flux<D>(PR, (T)ph.gamma, (T)ph.gr, FR, UR, lpR, lmR);
+    const T ap = fmax(T(0), fmax(lpL, lpR));
+    const T am = fmax(T(0), fmax(-lmL, -lmR));
+    const T ssum = ap + am;
+    if (ssum > T(0)) {
+        const T is = T(1) / ssum;
+        const T apam = ap * am;
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            A.F[D][q][id] = (ap * FL[q] + am * FR[q] - apam * (UR[q] - UL[q])) * is;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            A.F[D][q][id] = T(0.5) * (FL[q] + FR[q]);
+    }
+    A.ap[D][id] = ap;
+    A.am[D][id] = am;
+    A.fv[D][0][id] = PL[1 + D];
+    A.fv[D][1][id] = PR[1 + D];
+    A.fv[D][2][id] = PL[1 + T1];
+    A.fv[D][3][id] = PR[1 + T1];
+}
+
+// ------------------------------------------------------------------ EMF
+
+// UCT-HLL EMF on the edges along E; (a, b, E) cyclic.  The edge with index
+// (i,j,k) sits at the lower half-integer positions along a and b.
+//   E = [ap_a ap_b E_LL + ap_a am_b E_LR + am_a ap_b E_RL + am_a am_b E_RR]
+//       / ((ap_a + am_a)(ap_b + am_b))
+//     + ap_a am_a / (ap_a + am_a) (B~b_R - B~b_L) - ap_b am_b / (ap_b + am_b) (B~a_R - B~a_L),
+//   E_st = -(v^a_st B~b_s - v^b_st B~a_t)   (s: a-side, t: b-side).
+// v^a, v^b: a-face states (MP5 along a) reconstructed along b; B~b (b-faces)
+// along a; B~a (a-faces) along b; speeds: max over the two adjacent faces.
+template <int E, typename R>
+__global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
+{
+    constexpr int a = (E + 1) % 3, b = (E + 2) % 3;
+    int t[3];
+    t[0] = blockIdx.x * blockDim.x + threadIdx.x;
+    t[1] = blockIdx.y * blockDim.y + threadIdx.y;
+    t[2] = blockIdx.z;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int lim = d == E ? g.n[d] : g.n[d] + 1;
+        if (t[d] >= lim)
+            return;
+    }
+    const long long id = gidx(g, NG + t[0], NG + t[1], NG + t[2]);
+    const long long sa = a == 0 ? 1LL : (a == 1 ? g.px : g.pxy);
+    const long long sb = b == 0 ? 1LL : (b == 1 ? g.px : g.pxy);
+    using T = R;
+    T va[2][2], vb[2][2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        T qa[6], qb[6];
+        const R *__restrict__ pa = A.fv[a][s];
+        const R *__restrict__ pb = A.fv[a][2 + s];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            qa[m] = pa[id + (m - 3) * sb];
+            qb[m] = pb[id + (m - 3) * sb];
+        }
+        mp5_lr(qa, va[s][0], va[s][1]);
+        mp5_lr(qb, vb[s][0], vb[s][1]);
+    }
+    T Bb[2], Ba[2];
+    {
+        T q[6];
+        const R *__restrict__ pbb = A.U[5 + b];
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+            q[m] = pbb[id + (m - 3) * sa];
+        mp5_lr(q, Bb[0], Bb[1]);
+        const R *__restrict__ pba = A.U[5 + a];
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+            q[m] = pba[id + (m - 3) * sb];
+        mp5_lr(q, Ba[0], Ba[1]);
+    }
+    const T apa = fmax(A.ap[a][id - sb], A.ap[a][id]);
+    const T ama = fmax(A.am[a][id - sb], A.am[a][id]);
+    const T apb = fmax(A.ap[b][id - sa], A.ap[b][id]);
+    const T amb = fmax(A.am[b][id - sa], A.am[b][id]);
+    T Est[2][2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            Est[s][u] = -(va[s][u] * Bb[s] - vb[s][u] * Ba[u]);
+    const T sA = apa + ama, sB = apb + amb;
+    T wLL, wLR, wRL, wRR;
+    if (sA > T(0) && sB > T(0)) {
+        const T iden = T(1) / (sA * sB);
+        wLL = apa * apb * iden;
+        wLR = apa * amb * iden;
+        wRL = ama * apb * iden;
+        wRR = ama * amb * iden;
+    } else {
+        wLL = wLR = wRL = wRR = T(0.25);
+    }
+    const T da = sA > T(0) ? apa * ama / sA : T(0);
+    const T db = sB > T(0) ? apb * amb / sB : T(0);
+    A.E[E][id] = wLL * Est[0][0] + wLR * Est[0][1] + wRL * Est[1][0] + wRR * Est[1][1]
+                 + da * (Bb[1] - Bb[0]) - db * (Ba[1] - Ba[0]);
+}
+
+// ------------------------------------------------------------------ update
+
+// Flux difference + CT curl + SSP-RK3 stage combination (Shu & Osher 1988):
+//   stage 0: U = U0 + dt L (U0 saved);  stage 1: U = 3/4 U0 + 1/4 (U + dt L);
+//   stage 2: U = 1/3 U0 + 2/3 (U + dt L).
+// stage < 0: write L in host layout to Lout instead (faces NG..NG+n along
+// their axis; a face that is not evolved, e.g. on the polar axis, gets 0).
+template <typename R>
+__global__ void __launch_bounds__(256) k_update(Geom g, Arrays<R> A, int stage, double *Lout)
+{
+    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tj = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tk = blockIdx.z;
+    if (ti > g.n[0] || tj > g.n[1] || tk > g.n[2])
+        return;
+    const int i = NG + ti, j = NG + tj, k = NG + tk;
+    const long long id = gidx(g, i, j, k);
+    const long long st[3] = {1LL, g.px, g.pxy};
+    const int own[3] = {ti < g.n[0], tj < g.n[1], tk < g.n[2]};
+    const int ijk[3] = {i, j, k};
+    const R dt = stage >= 0 ? (R)A.scal->dt : R(0);
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+
+    if (own[0] && own[1] && own[2]) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            R r = R(0);
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                r -= (A.F[d][q][id + st[d]] - A.F[d][q][id]) * (R)g.idx[d];
+            if (stage < 0) {
+                Lout[q * N + ((long long)tk * g.n[1] + tj) * g.n[0] + ti] = (double)r;
+            } else {
+                const R u = A.U[q][id];
+                R un;
+                if (stage == 0) {
+                    A.U0[q][id] = u;
+                    un = u + dt * r;
+                } else if (stage == 1) {
+                    un = R(0.75) * A.U0[q][id] + R(0.25) * (u + dt * r);
+                } else {
+                    un = R(1.0 / 3.0) * A.U0[q][id] + R(2.0 / 3.0) * (u + dt * r);
+                }
+                A.U[q][id] = un;
+            }
+        }
+    }
+    long long off = 5 * N;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int a = (d + 1) % 3, b = (d + 2) % 3;
+        int e[3] = {g.n[0], g.n[1], g.n[2]};
+        e[d] += 1;
+        const bool trans_own = own[a] && own[b];
+        const bool evolved = ijk[d] >= g.flo[d] && ijk[d] <= g.fhi[d];
+        if (trans_own) {
+            R l = R(0);
+            if (evolved) {
+                // dB~^d/dt = -(d_a E_b - d_b E_a)
+                const R dEb = (A.E[b][id + st[a]] - A.E[b][id]) * (R)g.idx[a];
+                const R dEa = (A.E[a][id + st[b]] - A.E[a][id]) * (R)g.idx[b];
+                l = -(dEb - dEa);
+            }
+            if (stage < 0) {
+                // periodic duplicate face: same EMF values as the first face
+                if (ijk[d] <= NG + g.n[d]) {
+                    const bool dup = ijk[d] == NG + g.n[d] && g.bc[2 * d] == BC_PERIODIC;
+                    R lo = l;
+                    if (dup) {
+                        const R dEb = (A.E[b][id + st[a]] - A.E[b][id]) * (R)g.idx[a];
+                        const R dEa = (A.E[a][id + st[b]] - A.E[a][id]) * (R)g.idx[b];
+                        lo = -(dEb - dEa);
+                    }
+                    Lout[off + ((long long)tk * e[1] + tj) * e[0] + ti] = (double)lo;
+                }
+            } else if (evolved) {
+                const R u = A.U[5 + d][id];
+                R un;
+                if (stage == 0) {
+                    A.U0[5 + d][id] = u;
+                    un = u + dt * l;
+                } else if (stage == 1) {
+                    un = R(0.75) * A.U0[5 + d][id] + R(0.25) * (u + dt * l);
+                } else {
+                    un = R(1.0 / 3.0) * A.U0[5 + d][id] + R(2.0 / 3.0) * (u + dt * l);
+                }
+                A.U[5 + d][id] = un;
+            }
+        }
+        off += (long long)e[0] * e[1] * e[2];
+    }
+}
+
+// ------------------------------------------------------------------ scalars
+
+__global__ void k_step_begin(DevScalars *s, double dt_fixed)
+{
+    s->rate_bits = 0ULL;
+    s->dt = dt_fixed;
+}
+
+__global__ void k_set_dt(DevScalars *s, double cfl, int use_cfl)
+{
+    const double rate = __longlong_as_double((long long)s->rate_bits);
+    s->totals[6] = rate;
+    if (use_cfl)
+        s->dt = rate > 0.0 ? cfl / rate : 0.0;
+}
+
+// ------------------------------------------------------------------ totals
+
+// Sums of D, tau, S_i over owned cells and max |div B~|; per-block partials
+// (6 per block) from a fixed shared-memory tree, then one block combines the
+// partials in a fixed order.
+template <typename R>
+__global__ void __launch_bounds__(256) k_totals(Geom g, Arrays<R> A)
+{
+    __shared__ double sh[6][256];
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < N;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int ti = (int)(t % g.n[0]);
+        const long long r = t / g.n[0];
+        const int tj = (int)(r % g.n[1]);
+        const int tk = (int)(r / g.n[1]);
+        const long long id = gidx(g, NG + ti, NG + tj, NG + tk);
+        acc[0] += (double)A.U[0][id];
+        acc[1] += (double)A.U[4][id];
+        acc[2] += (double)A.U[1][id];
+        acc[3] += (double)A.U[2][id];
+        acc[4] += (double)A.U[3][id];
+        const double dv = ((double)A.U[5][id + 1] - (double)A.U[5][id]) * g.idx[0]
+                          + ((double)A.U[6][id + g.px] - (double)A.U[6][id]) * g.idx[1]
+                          + ((double)A.U[7][id + g.pxy] - (double)A.U[7][id]) * g.idx[2];
+        acc[5] = fmax(acc[5], fabs(dv));
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        sh[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+                sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+            sh[5][threadIdx.x] = fmax(sh[5][threadIdx.x], sh[5][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            A.partials[blockIdx.x * 6 + q] = sh[q][0];
+}
+
+__global__ void __launch_bounds__(256) k_totals_final(DevScalars *s, const double *partials, int nblk, double dV)
+{
+    __shared__ double sh[6][256];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            acc[q] += partials[b * 6 + q];
+        acc[5] = fmax(acc[5], partials[b * 6 + 5]);
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        sh[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+                sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+            sh[5][threadIdx.x] = fmax(sh[5][threadIdx.x], sh[5][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 5; ++q)
+            s->totals[q] = sh[q][0] * dV;
+        s->totals[5] = sh[5][0];
+    }
+}
+
+// ------------------------------------------------------------------ layout
+
+// Host layout (interior only, FP64) <-> padded arrays.  what: 0 = the five
+// cell arrays and the three face arrays of U, 1 = the face arrays only.
+template <typename R>
+__global__ void k_unpack_state(Geom g, const double *src, Arrays<R> A, int what)
+{
+    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tj = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tk = blockIdx.z;
+    if (ti > g.n[0] || tj > g.n[1] || tk > g.n[2])
+        return;
+    const long long id = gidx(g, NG + ti, NG + tj, NG + tk);
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int t[3] = {ti, tj, tk};
+    if (what == 0 && ti < g.n[0] && tj < g.n[1] && tk < g.n[2]) {
+        const long long h = ((long long)tk * g.n[1] + tj) * g.n[0] + ti;
+        for (int q = 0; q < 5; ++q)
+            A.U[q][id] = (R)src[q * N + h];
+    }
+    const double *f = what == 0 ? src + 5 * N : src;
+    for (int d = 0; d < 3; ++d) {
+        int e[3] = {g.n[0], g.n[1], g.n[2]};
+        e[d] += 1;
+        if (t[0] < e[0] && t[1] < e[1] && t[2] < e[2])
+            A.U[5 + d][id] = (R)f[((long long)tk * e[1] + tj) * e[0] + ti];
+        f += (long long)e[0] * e[1] * e[2];
+    }
+}
+
+template <typename R>
+__global__ void k_pack_state(Geom g, Arrays<R> A, double *dst)
+{
+    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tj = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tk = blockIdx.z;
+    if (ti > g.n[0] || tj > g.n[1] || tk > g.n[2])
+        return;
+    const long long id = gidx(g, NG + ti, NG + tj, NG + tk);
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int t[3] = {ti, tj, tk};
+    if (ti < g.n[0] && tj < g.n[1] && tk < g.n[2]) {
+        const long long h = ((long long)tk * g.n[1] + tj) * g.n[0] + ti;
+        for (int q = 0; q < 5; ++q)
+            dst[q * N + h] = (double)A.U[q][id];
+    }
+    double *f = dst + 5 * N;
+    for (int d = 0; d < 3; ++d) {
+        int e[3] = {g.n[0], g.n[1], g.n[2]};
+        e[d] += 1;
+        if (t[0] < e[0] && t[1] < e[1] && t[2] < e[2])
+            f[((long long)tk * e[1] + tj) * e[0] + ti] = (double)A.U[5 + d][id];
+        f += (long long)e[0] * e[1] * e[2];
+    }
+}
+
+// Cell arrays -> host layout: what 0 = primitives (8 arrays), 1 = Z.
+template <typename R>
+__global__ void k_pack_cells(Geom g, Arrays<R> A, double *dst, int what)
+{
+    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tj = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tk = blockIdx.z;
+    if (ti >= g.n[0] || tj >= g.n[1] || tk >= g.n[2])
+        return;
+    const long long id = gidx(g, NG + ti, NG + tj, NG + tk);
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long h = ((long long)tk * g.n[1] + tj) * g.n[0] + ti;
+    if (what == 0) {
+        for (int q = 0; q < 8; ++q)
+            dst[q * N + h] = (double)A.P[q][id];
+    } else {
+        dst[h] = A.Z[id];
+    }
+}
+
+template <typename R>
+__global__ void k_unpack_z(Geom g, const double *src, Arrays<R> A)
+{
+    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tj = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tk = blockIdx.z;
+    if (ti >= g.n[0] || tj >= g.n[1] || tk >= g.n[2])
+        return;
+    const long long id = gidx(g, NG + ti, NG + tj, NG + tk);
+    const long long h = ((long long)tk * g.n[1] + tj) * g.n[0] + ti;
+    A.Z[id] = src ? src[h] : 0.0;
+}
+
+// Primitives (host layout, 5 arrays) + face B~ (already in U, ghosts
+// filled) -> conserved cell variables and Z = rho h W^2 (flat metric).
+template <typename R>
+__global__ void k_p2c(Geom g, Phys ph, const double *prims5, Arrays<R> A)
+{
+    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tj = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tk = blockIdx.z;
+    if (ti >= g.n[0] || tj >= g.n[1] || tk >= g.n[2])
+        return;
+    const long long id = gidx(g, NG + ti, NG + tj, NG + tk);
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long h = ((long long)tk * g.n[1] + tj) * g.n[0] + ti;
+    const double rho = prims5[h], v[3] = {prims5[N + h], prims5[2 * N + h], prims5[3 * N + h]};
+    const double p = prims5[4 * N + h];
+    const double B[3] = {0.5 * ((double)A.U[5][id] + (double)A.U[5][id + 1]),
+                         0.5 * ((double)A.U[6][id] + (double)A.U[6][id + g.px]),
+                         0.5 * ((double)A.U[7][id] + (double)A.U[7][id + g.pxy])};
+    const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const double vB = v[0] * B[0] + v[1] * B[1] + v[2] * B[2];
+    const double W2 = 1.0 / (1.0 - v2);
+    const double W = sqrt(W2);
+    const double Zw = (rho + ph.gr * p) * W2;
+    const double Dn = rho * W;
+    A.U[0][id] = (R)Dn;
+    for (int c = 0; c < 3; ++c)
+        A.U[1 + c][id] = (R)((Zw + B2) * v[c] - vB * B[c]);
+    A.U[4][id] = (R)(Zw - p + 0.5 * (B2 + B2 * v2 - vB * vB) - Dn);
+    A.Z[id] = Zw;
+}
+
+// ------------------------------------------------------------------ launchers
+
+namespace {
+inline dim3 grid3(int nx, int ny, int nz, dim3 blk)
+{
+    return dim3((unsigned)((nx + blk.x - 1) / blk.x), (unsigned)((ny + blk.y - 1) / blk.y), (unsigned)nz);
+}
+}  // namespace
+
+template <typename R>
+void launch_fill(const Geom &g, const FillList<R> &L, cudaStream_t s)
+{
+    for (int d = 0; d < 3; ++d) {
+        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+        dim3 blk(8, 32, 1);
+        dim3 grd(1, (unsigned)((g.np[d1] + 31) / 32), (unsigned)g.np[d2]);
+        k_fill<R><<<grd, blk, 0, s>>>(g, d, L);
+    }
+}
+
+template <typename R>
+void launch_c2p(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mode, int want_rate, cudaStream_t s)
+{
+    dim3 blk(32, 4, 1);
+    k_c2p<R><<<grid3(g.n[0], g.n[1], g.n[2], blk), blk, 0, s>>>(g, ph, A, guess_mode, want_rate);
+}
+
+template <typename R>
+void launch_faces(const Geom &g, const Phys &ph, const Arrays<R> &A, int d, cudaStream_t s)
+{
+    dim3 blk(32, 4, 1);
+    if (d == 0)
+        k_faces<0, R><<<grid3(g.n[0] + 1, g.np[1], g.np[2], blk), blk, 0, s>>>(g, ph, A);
+    else if (d == 1)
+        k_faces<1, R><<<grid3(g.np[0], g.n[1] + 1, g.np[2], blk), blk, 0, s>>>(g, ph, A);
+    else
+        k_faces<2, R><<<grid3(g.np[0], g.np[1], g.n[2] + 1, blk), blk, 0, s>>>(g, ph, A);
+}
+
+template <typename R>
+void launch_emf(const Geom &g, const Arrays<R> &A, int e, cudaStream_t s)
+{
+    dim3 blk(32, 4, 1);
+    if (e == 0)
+        k_emf<0, R><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1, blk), blk, 0, s>>>(g, A);
+    else if (e == 1)
+        k_emf<1, R><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1, blk), blk, 0, s>>>(g, A);
+    else
+        k_emf<2, R><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2], blk), blk, 0, s>>>(g, A);
+}
+
+template <typename R>
+void launch_update(const Geom &g, const Arrays<R> &A, int stage, double *Lout, cudaStream_t s)
+{
+    dim3 blk(32, 8, 1);
+    k_update<R><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2] + 1, blk), blk, 0, s>>>(g, A, stage, Lout);
+}
+
+void launch_step_begin(DevScalars *sc, double dt_fixed, cudaStream_t s)
+{
+    k_step_begin<<<1, 1, 0, s>>>(sc, dt_fixed);
+}
+
+void launch_set_dt(DevScalars *sc, double cfl, int use_cfl, cudaStream_t s)
+{
+    k_set_dt<<<1, 1, 0, s>>>(sc, cfl, use_cfl);
+}
+
+template <typename R>
+void launch_totals(const Geom &g, const Arrays<R> &A, int nblk, cudaStream_t s)
+{
+    k_totals<R><<<nblk, 256, 0, s>>>(g, A);
+    k_totals_final<<<1, 256, 0, s>>>(A.scal, A.partials, nblk, g.dx[0] * g.dx[1] * g.dx[2]);
+}
+
+template <typename R>
+void launch_unpack_state(const Geom &g, const double *src, const Arrays<R> &A, int what, cudaStream_t s)
+{
+    dim3 blk(32, 8, 1);
+    k_unpack_state<R><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2] + 1, blk), blk, 0, s>>>(g, src, A, what);
+}
+
+template <typename R>
+void launch_pack_state(const Geom &g, const Arrays<R> &A, double *dst, cudaStream_t s)
+{
+    dim3 blk(32, 8, 1);
+    k_pack_state<R><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2] + 1, blk), blk, 0, s>>>(g, A, dst);
+}
+
+template <typename R>
+void launch_pack_cells(const Geom &g, const Arrays<R> &A, double *dst, int what, cudaStream_t s)
+{
+    dim3 blk(32, 8, 1);
+    k_pack_cells<R><<<grid3(g.n[0], g.n[1], g.n[2], blk), blk, 0, s>>>(g, A, dst, what);
+}
+
+template <typename R>
+void launch_unpack_z(const Geom &g, const double *src, const Arrays<R> &A, cudaStream_t s)
+{
+    dim3 blk(32, 8, 1);
+    k_unpack_z<R><<<grid3(g.n[0], g.n[1], g.n[2], blk), blk, 0, s>>>(g, src, A);
+}
+
+template <typename R>
+void launch_p2c(const Geom &g, const Phys &ph, const double *prims5, const Arrays<R> &A, cudaStream_t s)
+{
+    dim3 blk(32, 8, 1);
+    k_p2c<R><<<grid3(g.n[0], g.n[1], g.n[2], blk), blk, 0, s>>>(g, ph, prims5, A);
+}
+
+#define ECHO_INSTANTIATE(R)                                                                             \
+    template void launch_fill<R>(const Geom &, const FillList<R> &, cudaStream_t);                     \
+    template void launch_c2p<R>(const Geom &, const Phys &, const Arrays<R> &, int, int, cudaStream_t); \
+    template void launch_faces<R>(const Geom &, const Phys &, const Arrays<R> &, int, cudaStream_t);   \
+    template void launch_emf<R>(const Geom &, const Arrays<R> &, int, cudaStream_t);                   \
+    template void launch_update<R>(const Geom &, const Arrays<R> &, int, double *, cudaStream_t);      \
+    template void launch_totals<R>(const Geom &, const Arrays<R> &, int, cudaStream_t);                \
+    template void launch_unpack_state<R>(const Geom &, const double *, const Arrays<R> &, int, cudaStream_t); \
+    template void launch_pack_state<R>(const Geom &, const Arrays<R> &, double *, cudaStream_t);       \
+    template void launch_pack_cells<R>(const Geom &, const Arrays<R> &, double *, int, cudaStream_t);  \
+    template void launch_unpack_z<R>(const Geom &, const double *, const Arrays<R> &, cudaStream_t);   \
+    template void launch_p2c<R>(const Geom &, const Phys &, const double *, const Arrays<R> &, cudaStream_t);
+
+ECHO_INSTANTIATE(double)
+ECHO_INSTANTIATE(float)
+
+}  // namespace echo

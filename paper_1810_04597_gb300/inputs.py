@@ -74,11 +74,15 @@ def _mode_sum(modes, xs):
     returns an array (nz, ny, nx)."""
     x, y, z = xs
     acc = np.zeros((len(z), len(y), len(x)))
+    tmp = np.empty_like(acc)
     for (kx, ky, kz, amp, ph) in modes:
-        ex = np.exp(2j * np.pi * kx * x)
-        ey = np.exp(2j * np.pi * ky * y)
-        ez = np.exp(2j * np.pi * kz * z + 1j * ph)
-        acc += amp * np.real(ez[:, None, None] * ey[None, :, None] * ex[None, None, :])
+        # cos(A + B) = cos A cos B - sin A sin B, A along x, B on the (z, y) plane
+        A = 2 * np.pi * kx * x + ph
+        B = 2 * np.pi * (kz * z[:, None] + ky * y[None, :])
+        np.multiply.outer(amp * np.cos(B), np.cos(A), out=tmp)
+        acc += tmp
+        np.multiply.outer(amp * np.sin(B), np.sin(A), out=tmp)
+        acc -= tmp
     return acc
 
 

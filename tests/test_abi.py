@@ -1,0 +1,101 @@
+"""The C-ABI library builds for sm_103a, loads, exports every entry point
+declared in include/echo.h, and validates configurations on the host (no
+GPU needed: nothing here launches a kernel)."""
+import os
+import re
+
+import pytest
+
+from paper_1810_04597_gb300 import _lib, build, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "echo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(echo_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in _lib._SIGS, f"binding lacks {name}"
+
+
+def _grid(n=(8, 8, 8), bc=(0,) * 6, dx=0.1):
+    g = _lib.echo_grid()
+    for d in range(3):
+        g.n[d] = n[d]
+        g.dx[d] = dx
+    for s in range(6):
+        g.bc[s] = bc[s]
+    return g
+
+
+def test_init_validates_and_sizes(lib):
+    eos = _lib.echo_eos(4.0 / 3.0, 0, 0, 0, 0, 0)
+    flat = _lib.echo_metric(0, 0.0)
+    ctx = _lib.echo_init(_grid((37, 29, 23)), flat, eos, 64, 0.4)
+    try:
+        n = (37, 29, 23)
+        N = n[0] * n[1] * n[2]
+        count = 5 * N + n[2] * n[1] * (n[0] + 1) + n[2] * (n[1] + 1) * n[0] + (n[2] + 1) * n[1] * n[0]
+        assert _lib.echo_state_count(ctx) == count
+        padded = (n[0] + 6) * (n[1] + 6) * (n[2] + 6)
+        assert _lib.echo_workspace_bytes(ctx) >= 60 * padded * 8
+    finally:
+        _lib.echo_destroy(ctx)
+    ctx32 = _lib.echo_init(_grid((37, 29, 23)), flat, eos, 32, 0.4)
+    ctx64 = _lib.echo_init(_grid((37, 29, 23)), flat, eos, 64, 0.4)
+    assert _lib.echo_workspace_bytes(ctx32) < _lib.echo_workspace_bytes(ctx64)
+    _lib.echo_destroy(ctx32)
+    _lib.echo_destroy(ctx64)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n=(0, 8, 8)),
+    dict(dx=-1.0),
+    dict(bc=(0, 1, 0, 0, 0, 0)),
+    dict(bc=(3, 3, 0, 0, 0, 0)),
+])
+def test_init_rejects_bad_grids(lib, kw):
+    eos = _lib.echo_eos(4.0 / 3.0, 0, 0, 0, 0, 0)
+    with pytest.raises(_lib.EchoError) as e:
+        _lib.echo_init(_grid(**kw), _lib.echo_metric(0, 0.0), eos, 64, 0.4)
+    assert e.value.code == _lib.ECHO_EINVAL
+
+
+def test_init_rejects_bad_physics(lib):
+    g = _grid()
+    with pytest.raises(_lib.EchoError):
+        _lib.echo_init(g, _lib.echo_metric(0, 0.0), _lib.echo_eos(1.0, 0, 0, 0, 0, 0), 64, 0.4)
+    with pytest.raises(_lib.EchoError):
+        _lib.echo_init(g, _lib.echo_metric(0, 0.0), _lib.echo_eos(4 / 3, 0, 0, 0, 0, 0), 16, 0.4)
+    with pytest.raises(_lib.EchoError):
+        _lib.echo_init(g, _lib.echo_metric(0, 0.0), _lib.echo_eos(4 / 3, 0, 0, 0, 0, 0), 64, 0.0)
+
+
+def test_calls_out_of_order_are_rejected(lib):
+    ctx = _lib.echo_init(_grid(), _lib.echo_metric(0, 0.0), _lib.echo_eos(4 / 3, 0, 0, 0, 0, 0), 64, 0.4)
+    try:
+        with pytest.raises(_lib.EchoError) as e:
+            _lib.echo_step(ctx, 0.0)
+        assert e.value.code == _lib.ECHO_ESTATE
+        assert "echo_bind" in _lib.echo_last_error(ctx)
+    finally:
+        _lib.echo_destroy(ctx)
+
+
+def test_kernel_names(lib):
+    names = [_lib.echo_kernel_name(k) for k in range(_lib.ECHO_NK)]
+    assert names[1] == "c2p" and names[3] == "faces_x" and len(set(names)) == _lib.ECHO_NK
+    assert _lib.echo_kernel_name(99) == ""

@@ -1,0 +1,111 @@
+"""Parity at the full 256^3 throughput size, in the launch configuration the
+benchmark times.  The oracle cannot run the whole grid in seconds, so:
+  * L(U) is compared on sampled windows: the oracle evaluates a 24^3 window
+    of the same seeded input (periodically wrapped, so its edges are wrong),
+    and the centre 12^3 cells, whose dependency radius stays inside the
+    window, are compared with the GPU's full-grid result;
+  * after whole steps, properties that hold at any size are checked:
+    conservation of mass and energy, div B~ at rounding, no c2p failure.
+"""
+import numpy as np
+import pytest
+
+from paper_1810_04597_gb300 import inputs
+from gpu_util import FIELDS, max_rel
+
+pytestmark = pytest.mark.gpu
+
+NFULL = 256
+W = 24          # window edge
+M = 6           # margin not compared (dependency radius of L is < 6 cells)
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    return inputs.sweep_box(NFULL)
+
+
+def window(prob, c, w):
+    n = prob.n[0]
+    idx = [(c[d] - w // 2 + np.arange(w)) % n for d in range(3)]
+    fidx = [(c[d] - w // 2 + np.arange(w + 1)) % n for d in range(3)]
+    ix, iy, iz = idx
+    prims = np.ascontiguousarray(prob.prims[:, iz][:, :, iy][:, :, :, ix])
+    N = prob.n
+    o = 0
+    bx = prob.bface[o:o + N[2] * N[1] * (N[0] + 1)].reshape(N[2], N[1], N[0] + 1)
+    o += bx.size
+    by = prob.bface[o:o + N[2] * (N[1] + 1) * N[0]].reshape(N[2], N[1] + 1, N[0])
+    o += by.size
+    bz = prob.bface[o:o + (N[2] + 1) * N[1] * N[0]].reshape(N[2] + 1, N[1], N[0])
+    wbx = bx[iz][:, iy][:, :, fidx[0]]
+    wby = by[iz][:, fidx[1]][:, :, ix]
+    wbz = bz[fidx[2]][:, iy][:, :, ix]
+    return inputs.Problem(name="win", n=(w, w, w), x0=(0, 0, 0), dx=prob.dx,
+                          prims=prims, bface=inputs.pack_faces(wbx, wby, wbz)), idx, fidx
+
+
+def split(L, n):
+    nx, ny, nz = n
+    N = nx * ny * nz
+    cells = L[:5 * N].reshape(5, nz, ny, nx)
+    o = 5 * N
+    bx = L[o:o + nz * ny * (nx + 1)].reshape(nz, ny, nx + 1)
+    o += bx.size
+    by = L[o:o + nz * (ny + 1) * nx].reshape(nz, ny + 1, nx)
+    o += by.size
+    bz = L[o:o + (nz + 1) * ny * nx].reshape(nz + 1, ny, nx)
+    return [cells[0], cells[1], cells[2], cells[3], cells[4], bx, by, bz]
+
+
+def test_rhs_windows_full_size(orc, full):
+    from paper_1810_04597_gb300.echo import Solver
+    s = Solver(full)
+    s.set_prims()
+    Lg = split(s.rhs(), full.n)
+    P_g = s.get_prims()
+    rng = np.random.default_rng(123)
+    sl = slice(M, W - M)
+    for _ in range(3):
+        c = rng.integers(0, NFULL, size=3)
+        win, idx, fidx = window(full, c, W)
+        cfg = orc.make_cfg(win)
+        st, Z = orc.p2c(cfg, win.prims, win.bface)
+        Lo = split(orc.rhs(cfg, st, Z)[0], win.n)
+        P_o, _, _, _ = orc.c2p(cfg, st, Z)
+        gi = [i[sl] for i in idx]
+        for q, name in enumerate(FIELDS):
+            o = Lo[q][sl, sl, sl]
+            g = Lg[q][np.ix_(gi[2], gi[1], gi[0])] if q < 5 else None
+            if q >= 5:
+                d = q - 5
+                ids = [gi[0], gi[1], gi[2]]
+                ids[d] = fidx[d][sl]
+                g = Lg[q][np.ix_(ids[2], ids[1], ids[0])]
+            assert max_rel(g, o) <= 1e-12, (name, c, max_rel(g, o))
+        # c2p at the same cells
+        Pg = P_g.reshape(8, NFULL, NFULL, NFULL)
+        for q in range(8):
+            o = P_o[q].reshape(W, W, W)[sl, sl, sl]
+            g = Pg[q][np.ix_(gi[2], gi[1], gi[0])]
+            assert max_rel(g, o) <= 1e-13, (q, c)
+
+
+def test_full_size_steps_conserve(full):
+    from paper_1810_04597_gb300.echo import Solver
+    s = Solver(full)
+    s.set_prims()
+    t0 = s.reduce()
+    for _ in range(2):
+        s.step()
+    t1 = s.reduce()
+    assert t1["c2p_fail"] == 0
+    assert abs(t1["mass"] - t0["mass"]) <= 1e-13 * abs(t0["mass"])
+    assert abs(t1["energy"] - t0["energy"]) <= 1e-13 * abs(t0["energy"])
+    st = s.get_state()
+    bmax = np.max(np.abs(st[5 * full.ncells:]))
+    assert t1["max_divb"] * full.dx[0] / bmax <= 1e-12
+    assert t1["dt_cfl"] > 0.0
