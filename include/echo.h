@@ -50,6 +50,7 @@ extern "C" {
 #define ECHO_EC2P (-4)     /* conservative-to-primitive inversion failed */
 #define ECHO_ETIMEOUT (-5) /* a bounded device wait gave up */
 #define ECHO_ESTATE (-6)   /* call out of order (e.g. not bound, no state) */
+#define ECHO_ERANGE (-7)   /* size beyond a fixed maximum (echo_totals_static) */
 
 /* boundary kinds (echo_grid.bc[2*d + side], side 0 lower, 1 upper) */
 #define ECHO_BC_PERIODIC 0
@@ -183,6 +184,32 @@ int echo_profile_read(echo_ctx *ctx, double *ms, long long *launches, int nk);
 
 /* Name of kernel class k ("" if out of range). */
 const char *echo_kernel_name(int k);
+
+/* Totals of a state without allocating anything and without a context.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory at the moment they want the numbers, such as an
+ * application whose own memory manager has reserved all of HBM, or a
+ * monitoring hook that must not change the device's memory footprint while
+ * a large run sits near the HBM limit.
+ *   state: device pointer, FP64 host layout of an n[0] x n[1] x n[2] grid
+ *          (as written by echo_get_state with on_device = 1).
+ *   n, dx: host arrays of 3 (cells > 0, widths > 0).
+ *   out6:  device pointer to 6 doubles, written with sum D dV, sum tau dV,
+ *          sum S_x dV, sum S_y dV, sum S_z dV and max |div B~| (dV = dx dy dz),
+ *          the same quantities echo_reduce reports.
+ *   cuda_stream: stream to enqueue on (cudaStream_t, NULL = legacy stream).
+ * The per-row partial sums live in one file-scope device array of
+ * ECHO_STATIC_MAX_ROWS x 6 doubles (3 MiB) that every GPU loading the
+ * library holds until the process exits; calls allocate nothing (no
+ * cudaMalloc, no library allocator).  Rows = n[1] * n[2] above
+ * ECHO_STATIC_MAX_ROWS return ECHO_ERANGE; bad arguments ECHO_EINVAL.  The
+ * first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race,
+ * so order them on one stream.  Asynchronous: out6 is valid once the stream
+ * reaches the call. */
+#define ECHO_STATIC_MAX_ROWS 65536
+int echo_totals_static(const double *state, const int *n, const double *dx, double *out6, void *cuda_stream);
 
 /* Message of the last failure on this context ("" if none). */
 const char *echo_last_error(const echo_ctx *ctx);

@@ -26,8 +26,10 @@ ECHO_ENOMEM = -3
 ECHO_EC2P = -4
 ECHO_ETIMEOUT = -5
 ECHO_ESTATE = -6
+ECHO_ERANGE = -7
+ECHO_STATIC_MAX_ROWS = 65536
 _NAMES = {0: "ECHO_OK", -1: "ECHO_EINVAL", -2: "ECHO_ECUDA", -3: "ECHO_ENOMEM", -4: "ECHO_EC2P",
-          -5: "ECHO_ETIMEOUT", -6: "ECHO_ESTATE"}
+          -5: "ECHO_ETIMEOUT", -6: "ECHO_ESTATE", -7: "ECHO_ERANGE"}
 
 BC_PERIODIC, BC_OUTFLOW, BC_AXIS = 0, 1, 2
 METRIC_FLAT, METRIC_KERR_SCHILD = 0, 1
@@ -90,6 +92,8 @@ _SIGS = {
     "echo_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "echo_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "echo_totals_static": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                          _P, _P]),
     "echo_last_error": (ctypes.c_char_p, [_P]),
     "echo_destroy": (None, [_P]),
 }
@@ -243,6 +247,22 @@ def echo_profile_read(ctx) -> dict:
 
 def echo_kernel_name(k: int) -> str:
     return (load().echo_kernel_name(int(k)) or b"").decode()
+
+
+def echo_totals_static(state, n, dx, out6, stream_handle: int = 0):
+    """Totals of a device state (torch CUDA tensor, FP64 host layout) into
+    the device tensor out6 (6 doubles), allocating nothing.  For callers
+    that cannot allocate device memory; see include/echo.h."""
+    s, ds = _ptr(state)
+    o, do = _ptr(out6, writable=True)
+    if not (ds and do):
+        raise TypeError("echo_totals_static takes device arrays")
+    nn = (ctypes.c_int * 3)(*[int(v) for v in n])
+    dd = (ctypes.c_double * 3)(*[float(v) for v in dx])
+    rc = load().echo_totals_static(_P(s), nn, dd, _P(o), _P(stream_handle))
+    if rc != ECHO_OK:
+        raise EchoError(rc, "echo_totals_static")
+    return out6
 
 
 def echo_last_error(ctx) -> str:
