@@ -316,6 +316,7 @@ def run_ours(args, world, rank, local, dist):
     ms_max = max_over_ranks(dist, ms)
     value = world * zones * args.steps / (ms_max * 1e-3) / 1e6
     totals = s.reduce()
+    fin64 = s.get_state() if (args.precision == 64 and not args.no_variants) else None
 
     # kernels launched in the timed region (a fill call launches 3 kernels)
     per_call = {"fill_faces": 3, "fill_prims": 3}
@@ -362,6 +363,42 @@ def run_ours(args, world, rank, local, dist):
                "d2h_bytes_per_step": int(out_host.nbytes), "steps": e2e_steps,
                "api": "echo_set_state(host) + echo_step + echo_get_state(host)"}
 
+    # ---- FP32-bulk variant on the same input (timed the same way), and its
+    #      relative L1 distance per field from the FP64 run after W + K steps
+    variants = None
+    if fin64 is not None:
+        s32 = Solver(prob, precision=32, device=str(dev))
+        s32.set_prims()
+        for _ in range(args.warmup):
+            s32.step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s32.stream)
+        for _ in range(args.steps):
+            s32.step()
+        e1.record(s32.stream)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1)
+        fin32 = s32.get_state()
+        t32 = s32.reduce()
+        N = zones
+        bounds = [0, N, 2 * N, 3 * N, 4 * N, 5 * N]
+        nx, ny, nz = n
+        bounds += [5 * N + nz * ny * (nx + 1), 5 * N + nz * ny * (nx + 1) + nz * (ny + 1) * nx, len(fin64)]
+        names = ["D", "S_x", "S_y", "S_z", "tau", "Bx", "By", "Bz"]
+        l1 = {}
+        for name, a, b in zip(names, bounds[:-1], bounds[1:]):
+            den = float(np.sum(np.abs(fin64[a:b])))
+            l1[name] = float(np.sum(np.abs(fin32[a:b] - fin64[a:b])) / den) if den > 0 else 0.0
+        variants = {"fp32_bulk": {
+            "value": world * zones * args.steps / (max_over_ranks(dist, ms32) * 1e-3) / 1e6, "unit": UNIT,
+            "ms_per_step": ms32 / args.steps, "speedup_vs_fp64": ms / ms32,
+            "l1_rel_vs_fp64_gpu": l1, "max_l1": max(l1.values()),
+            "mean_newton_iters": t32["c2p_iters"] / max(t32["c2p_calls"], 1),
+            "note": "FP32 storage/stencil, FP64 c2p and reductions; same input, same step count"}}
+        del s32
+
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -381,7 +418,7 @@ def run_ours(args, world, rank, local, dist):
                                f"{'FP64' if args.precision == 64 else 'FP32 bulk'}",
                    "grid": list(n), "zones": zones, "parallelism": f"replicas x{world}",
                    "l2": "working set (~9 GB) larger than L2; no flush needed"},
-        "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "variants": variants,
         "gpu_launches": launches,
         "check": {"c2p_fail": totals["c2p_fail"], "mean_newton_iters":
                   totals["c2p_iters"] / max(totals["c2p_calls"], 1), "dt_cfl": totals["dt_cfl"]},
@@ -399,6 +436,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     world, rank, local = dist_info()

@@ -77,22 +77,79 @@ struct Arrays {
     DevScalars *scal;
 };
 
+// ------------------------------------------------------------------ exact
+// comparisons on the integer pipe
+//
+// GB300 runs FP64 arithmetic, comparisons and min/max on a pipe ~70x slower
+// than FP32, so sign tests, |x|, min/max and threshold tests are done on
+// the IEEE-754 bit patterns instead (integer pipe).  For non-NaN values
+// the map key(x) = bits ^ ((bits >> 63) & 0x7ff..f) is strictly monotonic
+// in x (IEEE 754 total order of bit patterns), so every result below equals
+// the floating-point comparison it replaces.
+
+__device__ __forceinline__ long long bits_of(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ int bits_of(float x) { return __float_as_int(x); }
+
+__device__ __forceinline__ long long okey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ int okey(float x)
+{
+    const int b = __float_as_int(x);
+    return b ^ ((b >> 31) & 0x7fffffff);
+}
+// x > 0 and x < 0 (strict; +0 and -0 are neither)
+__device__ __forceinline__ bool is_pos(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool is_pos(float x) { return __float_as_int(x) > 0; }
+__device__ __forceinline__ bool is_neg(double x)
+{
+    return (__double_as_longlong(x) ^ (long long)0x8000000000000000ULL) > 0;
+}
+__device__ __forceinline__ bool is_neg(float x) { return (__float_as_int(x) ^ (int)0x80000000u) > 0; }
+__device__ __forceinline__ double iabs(double x)
+{
+    return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ float iabs(float x) { return __int_as_float(__float_as_int(x) & 0x7fffffff); }
+template <typename T>
+__device__ __forceinline__ T imin(T a, T b) { return okey(a) < okey(b) ? a : b; }
+template <typename T>
+__device__ __forceinline__ T imax(T a, T b) { return okey(a) < okey(b) ? b : a; }
+// a < b, a <= b
+template <typename T>
+__device__ __forceinline__ bool ilt(T a, T b) { return okey(a) < okey(b); }
+template <typename T>
+__device__ __forceinline__ bool ile(T a, T b) { return okey(a) <= okey(b); }
+__device__ __forceinline__ double with_sign_of(double mag, double s)
+{
+    return __longlong_as_double(__double_as_longlong(mag)
+                                | (__double_as_longlong(s) & (long long)0x8000000000000000ULL));
+}
+__device__ __forceinline__ float with_sign_of(float mag, float s)
+{
+    return __int_as_float(__float_as_int(mag) | (__float_as_int(s) & (int)0x80000000u));
+}
+
 // ------------------------------------------------------------------ MP5
 
+// minmod(a, b) = sign(a) min(|a|, |b|) if a, b have the same strict sign, else 0
 template <typename T>
 __device__ __forceinline__ T minmod2(T a, T b)
 {
-    const bool same = (a > T(0) && b > T(0)) || (a < T(0) && b < T(0));
-    return same ? copysign(fmin(fabs(a), fabs(b)), a) : T(0);
+    const bool same = (is_pos(a) && is_pos(b)) || (is_neg(a) && is_neg(b));
+    return same ? with_sign_of(imin(iabs(a), iabs(b)), a) : T(0);
 }
 
+// minmod of four: sign * min |.| if all four share a strict sign, else 0
 template <typename T>
 __device__ __forceinline__ T minmod4(T w, T x, T y, T z)
 {
-    const bool pos = w > T(0) && x > T(0) && y > T(0) && z > T(0);
-    const bool neg = w < T(0) && x < T(0) && y < T(0) && z < T(0);
-    const T m = fmin(fmin(fabs(w), fabs(x)), fmin(fabs(y), fabs(z)));
-    return pos ? m : (neg ? -m : T(0));
+    const bool pos = is_pos(w) && is_pos(x) && is_pos(y) && is_pos(z);
+    const bool neg = is_neg(w) && is_neg(x) && is_neg(y) && is_neg(z);
+    const T m = imin(imin(iabs(w), iabs(x)), imin(iabs(y), iabs(z)));
+    return (pos || neg) ? with_sign_of(m, w) : T(0);
 }
 
 // Interface value between u0 = u_j and up1 = u_{j+1}, biased to u_j
@@ -102,20 +159,53 @@ template <typename T>
 __device__ __forceinline__ T mp5(T um2, T um1, T u0, T up1, T up2)
 {
     const T uor = (T(2) * um2 - T(13) * um1 + T(47) * u0 + T(27) * up1 - T(3) * up2) * T(1.0 / 60.0);
-    const T ump = u0 + minmod2(up1 - u0, T(MP5_ALPHA) * (u0 - um1));
-    if ((uor - u0) * (uor - ump) <= T(MP5_EPS))
+    const T a4 = T(MP5_ALPHA) * (u0 - um1);
+    const T ump = u0 + minmod2(up1 - u0, a4);
+    if (ile((uor - u0) * (uor - ump), T(MP5_EPS)))
         return uor;
     const T dm1 = um2 - T(2) * um1 + u0;
     const T d0 = um1 - T(2) * u0 + up1;
     const T dp1 = u0 - T(2) * up1 + up2;
     const T dMp = minmod4(T(4) * d0 - dp1, T(4) * dp1 - d0, d0, dp1);
     const T dMm = minmod4(T(4) * d0 - dm1, T(4) * dm1 - d0, d0, dm1);
-    const T uul = u0 + T(MP5_ALPHA) * (u0 - um1);
+    const T uul = u0 + a4;
     const T uav = T(0.5) * (u0 + up1);
     const T umd = uav - T(0.5) * dMp;
     const T ulc = u0 + T(0.5) * (u0 - um1) + T(4.0 / 3.0) * dMm;
-    const T umin = fmax(fmin(fmin(u0, up1), umd), fmin(fmin(u0, uul), ulc));
-    const T umax = fmin(fmax(fmax(u0, up1), umd), fmax(fmax(u0, uul), ulc));
+    const T umin = imax(imin(imin(u0, up1), umd), imin(imin(u0, uul), ulc));
+    const T umax = imin(imax(imax(u0, up1), umd), imax(imax(u0, uul), ulc));
+    return uor + minmod2(umin - uor, umax - uor);
+}
+
+// MP5 split for divergence-free evaluation on the GPU.  mp5_try returns the
+// unlimited value and whether it is accepted (the Suresh & Huynh test);
+// mp5_limit returns the limited value for a stencil whose unlimited value
+// was rejected.  mp5_try + (if rejected) mp5_limit == mp5 exactly.
+template <typename T>
+__device__ __forceinline__ T mp5_try(T um2, T um1, T u0, T up1, T up2, bool &accept)
+{
+    const T uor = (T(2) * um2 - T(13) * um1 + T(47) * u0 + T(27) * up1 - T(3) * up2) * T(1.0 / 60.0);
+    const T ump = u0 + minmod2(up1 - u0, T(MP5_ALPHA) * (u0 - um1));
+    accept = ile((uor - u0) * (uor - ump), T(MP5_EPS));
+    return uor;
+}
+
+template <typename T>
+__device__ __forceinline__ T mp5_limit(T um2, T um1, T u0, T up1, T up2)
+{
+    const T uor = (T(2) * um2 - T(13) * um1 + T(47) * u0 + T(27) * up1 - T(3) * up2) * T(1.0 / 60.0);
+    const T a4 = T(MP5_ALPHA) * (u0 - um1);
+    const T dm1 = um2 - T(2) * um1 + u0;
+    const T d0 = um1 - T(2) * u0 + up1;
+    const T dp1 = u0 - T(2) * up1 + up2;
+    const T dMp = minmod4(T(4) * d0 - dp1, T(4) * dp1 - d0, d0, dp1);
+    const T dMm = minmod4(T(4) * d0 - dm1, T(4) * dm1 - d0, d0, dm1);
+    const T uul = u0 + a4;
+    const T uav = T(0.5) * (u0 + up1);
+    const T umd = uav - T(0.5) * dMp;
+    const T ulc = u0 + T(0.5) * (u0 - um1) + T(4.0 / 3.0) * dMm;
+    const T umin = imax(imin(imin(u0, up1), umd), imin(imin(u0, uul), ulc));
+    const T umax = imin(imax(imax(u0, up1), umd), imax(imax(u0, uul), ulc));
     return uor + minmod2(umin - uor, umax - uor);
 }
 
@@ -173,16 +263,23 @@ __device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, T F[5], T 
         F[1 + j] = wt * v[j] - bd * bj + (j == D ? p + T(0.5) * b2 : T(0));
     }
     F[4] = U[1 + D] - Dn * vd;
-    const T a2 = (gam * p + b2) / (rhoh + b2);
-    const T disc = a2 * iW2 * ((T(1) - v2 * a2) - (T(1) - a2) * vd * vd);
-    const T sq = sqrt(fmax(disc, T(0)));
-    const T iden = T(1) / (T(1) - v2 * a2);
-    const T base = vd * (T(1) - a2);
-    lp = (base + sq) * iden;
-    lm = (base - sq) * iden;
+    // With G = G p + b^2 and X = rho h + b^2 (a^2 = G/X), multiplying the
+    // eigenvalue formula through by X leaves one division:
+    //   lambda = [v^d (rho h - G p) +- sqrt(G (1-v^2)(Y - (rho h - G p)(v^d)^2))] / Y,
+    //   Y = X - v^2 G.
+    const T Gs = gam * p + b2;
+    const T Y = (rhoh + b2) - v2 * Gs;
+    const T rmg = rhoh - gam * p;
+    const T disc = Gs * iW2 * (Y - rmg * vd * vd);
+    const T sq = sqrt(is_pos(disc) ? disc : T(0));
+    const T iY = T(1) / Y;
+    const T base = vd * rmg;
+    lp = (base + sq) * iY;
+    lm = (base - sq) * iY;
 }
 
-// Sum over directions of max(|lambda+|, |lambda-|)/dx (CFL rate) of a cell.
+// Sum over directions of max(|lambda+|, |lambda-|)/dx (CFL rate) of a cell
+// (same eigenvalue form as state_flux).
 __device__ __forceinline__ double cfl_rate(const double P[8], double gam, double gr, const double idx[3])
 {
     const double vx = P[1], vy = P[2], vz = P[3], p = P[4];
@@ -192,17 +289,18 @@ __device__ __forceinline__ double cfl_rate(const double P[8], double gam, double
     const double iW2 = 1.0 - v2;
     const double rhoh = P[0] + gr * p;
     const double b2 = B2 * iW2 + vB * vB;
-    const double a2 = (gam * p + b2) / (rhoh + b2);
-    const double iden = 1.0 / (1.0 - v2 * a2);
+    const double Gs = gam * p + b2;
+    const double Y = (rhoh + b2) - v2 * Gs;
+    const double rmg = rhoh - gam * p;
+    const double iY = 1.0 / Y;
     const double v[3] = {vx, vy, vz};
     double s = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const double disc = a2 * iW2 * ((1.0 - v2 * a2) - (1.0 - a2) * v[d] * v[d]);
-        const double sq = sqrt(fmax(disc, 0.0));
-        const double base = v[d] * (1.0 - a2);
-        const double lp = (base + sq) * iden, lm = (base - sq) * iden;
-        s += fmax(fabs(lp), fabs(lm)) * idx[d];
+        const double disc = Gs * iW2 * (Y - rmg * v[d] * v[d]);
+        const double sq = sqrt(is_pos(disc) ? disc : 0.0);
+        const double base = v[d] * rmg;
+        s += imax(iabs(base + sq), iabs(base - sq)) * iY * idx[d];
     }
     return s;
 }
@@ -222,10 +320,19 @@ struct C2PResult {
     bool ok;
 };
 
-__device__ __forceinline__ double c2p_v2(double Z, double S2, double SB2, double B2)
+// v^2 at Z from the reciprocals iZ = 1/Z, iZB = 1/(Z + B^2).
+__device__ __forceinline__ double c2p_v2r(double Z, double iZ, double iZB, double S2, double SB2, double B2)
+{
+    return (S2 + SB2 * (2.0 * Z + B2) * iZ * iZ) * iZB * iZB;
+}
+
+// One division gives both reciprocals: 1/(Z (Z + B^2)).
+__device__ __forceinline__ void c2p_recip(double Z, double B2, double &iZ, double &iZB)
 {
     const double ZB = Z + B2;
-    return (S2 * Z * Z + SB2 * (2.0 * Z + B2)) / (Z * Z * ZB * ZB);
+    const double inv = 1.0 / (Z * ZB);
+    iZ = inv * ZB;
+    iZB = inv * Z;
 }
 
 __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], double tau, const double B[3],
@@ -237,11 +344,17 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
     const double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
     const double Uen = tau + Dc;
     C2PResult r;
-    double Z = Zguess;
+    double Z = Zguess, iZ = 0.0, iZB = 0.0, v2 = 0.0;
     int tries = 0;
     bool ok = true;
-    while (!(Z > 0.0) || !(c2p_v2(Z, S2, SB2, B2) < 1.0)) {
-        Z = 2.0 * fmax(Z, Uen);
+    for (;;) {
+        if (is_pos(Z)) {
+            c2p_recip(Z, B2, iZ, iZB);
+            v2 = c2p_v2r(Z, iZ, iZB, S2, SB2, B2);
+            if (ilt(v2, 1.0))
+                break;
+        }
+        Z = 2.0 * imax(Z, Uen);
         if (++tries > 60) {
             ok = false;
             break;
@@ -251,46 +364,55 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
     bool conv = false;
     while (ok && it < NEWTON_MAXIT) {
         ++it;
-        const double Z2 = Z * Z;
-        const double ZB = Z + B2;
-        const double den = 1.0 / (Z2 * ZB * ZB);
-        const double v2 = (S2 * Z2 + SB2 * (2.0 * Z + B2)) * den;
-        const double sq = sqrt(1.0 - v2);
-        const double p = gm1g * (Z * (1.0 - v2) - Dc * sq);
-        const double iZ = 1.0 / Z;
-        const double f = Z - p + 0.5 * (1.0 + v2) * B2 - 0.5 * SB2 * iZ * iZ - Uen;
-        const double dv2 = -2.0 * (S2 * Z2 * Z + SB2 * (3.0 * Z2 + 3.0 * Z * B2 + B2 * B2)) * den * iZ / ZB;
-        const double dp = gm1g * ((1.0 - v2) - Z * dv2 + 0.5 * Dc * dv2 / sq);
-        const double fp = 1.0 - dp + 0.5 * B2 * dv2 + SB2 * iZ * iZ * iZ;
+        const double om = 1.0 - v2;
+        const double isq = rsqrt(om);
+        const double sq = om * isq;
+        const double p = gm1g * (Z * om - Dc * sq);
+        const double iZ2 = iZ * iZ;
+        const double f = Z - p + 0.5 * (1.0 + v2) * B2 - 0.5 * SB2 * iZ2 - Uen;
+        const double iZB3 = iZB * iZB * iZB;
+        const double dv2 = -2.0 * (S2 * Z * Z * Z + SB2 * (3.0 * Z * Z + 3.0 * Z * B2 + B2 * B2)) * iZ2 * iZ * iZB3;
+        const double dp = gm1g * (om - Z * dv2 + 0.5 * Dc * dv2 * isq);
+        const double fp = 1.0 - dp + 0.5 * B2 * dv2 + SB2 * iZ2 * iZ;
         double dZ = f / fp;
-        double Zn = Z - dZ;
+        double Zn = Z - dZ, iZn = 0.0, iZBn = 0.0, v2n = 2.0;
         int h = 0;
-        while ((!(Zn > 0.0) || !(c2p_v2(Zn, S2, SB2, B2) < 1.0)) && h < NEWTON_MAXHALF) {
+        for (;;) {
+            if (is_pos(Zn)) {
+                c2p_recip(Zn, B2, iZn, iZBn);
+                v2n = c2p_v2r(Zn, iZn, iZBn, S2, SB2, B2);
+                if (ilt(v2n, 1.0))
+                    break;
+            }
+            if (h >= NEWTON_MAXHALF)
+                break;
             dZ *= 0.5;
             Zn = Z - dZ;
             ++h;
         }
-        if (!(Zn > 0.0) || !(c2p_v2(Zn, S2, SB2, B2) < 1.0))
+        if (!is_pos(Zn) || !ilt(v2n, 1.0))
             break;
         Z = Zn;
-        if (fabs(dZ) <= NEWTON_TOL * Z) {
+        iZ = iZn;
+        iZB = iZBn;
+        v2 = v2n;
+        if (ile(iabs(dZ), NEWTON_TOL * Z)) {
             conv = true;
             break;
         }
     }
-    const double v2 = c2p_v2(Z, S2, SB2, B2);
-    const double sq = sqrt(1.0 - v2);
-    const double p = gm1g * (Z * (1.0 - v2) - Dc * sq);
-    const double ivs = 1.0 / (Z + B2);
-    const double sbz = SB / Z;
+    const double om = 1.0 - v2;
+    const double sq = sqrt(om);
+    const double p = gm1g * (Z * om - Dc * sq);
+    const double sbz = SB * iZ;
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-        r.v[j] = (S[j] + sbz * B[j]) * ivs;
+        r.v[j] = (S[j] + sbz * B[j]) * iZB;
     r.rho = Dc * sq;
     r.p = p;
     r.Z = Z;
     r.iters = it;
-    r.ok = ok && conv && p > 0.0 && r.rho > 0.0;
+    r.ok = ok && conv && is_pos(p) && is_pos(r.rho);
     return r;
 }
 

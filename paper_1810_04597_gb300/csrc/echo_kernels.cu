@@ -134,47 +134,156 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
     }
 }
 
+// ------------------------------------------------------------------ limiter
+// compaction
+//
+// Each lane holds up to 16 reconstructions (slot = 2 m + side); `pend` marks
+// those whose unlimited MP5 value was rejected.  The warp packs all pending
+// items of its 32 lanes into a shared list (warp prefix sum of the counts),
+// processes the list 32 items per round -- lane L takes item r*32 + L, loads
+// the owning lane's stencil itself and evaluates the limited value -- and
+// returns the results through shared memory.  Rounds per warp drop from the
+// max over lanes of their pending count to ceil(total / 32).
+constexpr int kWarpsPerBlock = 4;   // kernels using this run 128 threads
+
+template <typename T>
+struct LimScratch {
+    T res[kWarpsPerBlock][32][16];
+    unsigned short desc[kWarpsPerBlock][32 * 16];
+};
+
+// limited(id_of_owner, m, side) -> T
+template <typename T, typename F>
+__device__ __forceinline__ void compact_limit(unsigned pend, long long id, LimScratch<T> &sm, F limited)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int cnt = __popc(pend);
+    int excl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, excl, o);
+        if (lane >= o)
+            excl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, excl, 31);
+    if (total == 0)
+        return;
+    excl -= cnt;
+    {
+        unsigned m = pend;
+        int k = excl;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            sm.desc[w][k++] = (unsigned short)((lane << 4) | b);
+        }
+    }
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {
+        const int item = base + lane;
+        const bool act = item < total;
+        const unsigned d = act ? sm.desc[w][item] : (unsigned)(lane << 4);
+        const int o = (int)(d >> 4);
+        const long long ido = __shfl_sync(0xffffffffu, id, o);
+        if (act) {
+            const int b = (int)(d & 15);
+            sm.res[w][o][b] = limited(ido, b >> 1, b & 1);
+        }
+    }
+    __syncwarp();
+}
+
 // ------------------------------------------------------------------ faces
 
 // MP5 left/right states, HLL flux and speeds on the D-faces.  Face index
 // along D runs over NG..NG+n (every face of an owned cell); transversally
 // the full padded range (the EMFs need face data three rows into the
-// ghosts).  A reconstructed side with rho <= 0, p <= 0 or v^2 >= 1 takes the
-// adjacent cell's primitives.
+// ghosts).  Threads map linearly onto that box so that warps stay full at
+// row ends.  A reconstructed side with rho <= 0, p <= 0 or v^2 >= 1 takes
+// the adjacent cell's primitives.
+//
+// The MP5 limiter is taken by ~10-15% of reconstructions; evaluated inline
+// it would run for the whole warp at every one of the 14 calls.  Instead
+// all unlimited values are computed first, a bitmask records the rejected
+// ones, and compact_limit evaluates them packed 32 per warp round.
+template <typename R>
+__device__ __forceinline__ const R *pick7(const Arrays<R> &A, const int qs[7], int m)
+{
+    const R *p = A.P[qs[0]];
+#pragma unroll
+    for (int u = 1; u < 7; ++u)
+        if (m == u)
+            p = A.P[qs[u]];
+    return p;
+}
+
 template <int D, typename R>
 __global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
 {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-    int t[3];
-    t[0] = blockIdx.x * blockDim.x + threadIdx.x;
-    t[1] = blockIdx.y * blockDim.y + threadIdx.y;
-    t[2] = blockIdx.z;
+    int cnt[3] = {g.np[0], g.np[1], g.np[2]};
+    cnt[D] = g.n[D] + 1;
+    const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = t < tot;
     int ijk[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (d == D) {
-            if (t[d] > g.n[d])
-                return;
-            ijk[d] = NG + t[d];
-        } else {
-            if (t[d] >= g.np[d])
-                return;
-            ijk[d] = t[d];
-        }
+    {
+        const long long tt = live ? t : 0;
+        ijk[0] = (int)(tt % cnt[0]);
+        const long long r = tt / cnt[0];
+        ijk[1] = (int)(r % cnt[1]);
+        ijk[2] = (int)(r / cnt[1]);
+        ijk[D] += NG;
     }
     const long long id = gidx(g, ijk[0], ijk[1], ijk[2]);
     const long long sd = D == 0 ? 1LL : (D == 1 ? g.px : g.pxy);
     using T = R;
-    T PL[8], PR[8];
     const int qs[7] = {0, 1, 2, 3, 4, 5 + T1, 5 + T2};
+    T Lv[7], Rv[7];
+    unsigned pend = 0;
+    if (live) {
 #pragma unroll
-    for (int m = 0; m < 7; ++m) {
-        const R *__restrict__ a = A.P[qs[m]];
+        for (int m = 0; m < 7; ++m) {
+            const R *__restrict__ a = A.P[qs[m]];
+            T q[6];
+#pragma unroll
+            for (int s = 0; s < 6; ++s)
+                q[s] = a[id + (s - 3) * sd];
+            bool okL, okR;
+            Lv[m] = mp5_try(q[0], q[1], q[2], q[3], q[4], okL);
+            Rv[m] = mp5_try(q[5], q[4], q[3], q[2], q[1], okR);
+            pend |= (okL ? 0u : 1u) << (2 * m);
+            pend |= (okR ? 0u : 1u) << (2 * m + 1);
+        }
+    }
+    // limiter on the rejected items, compacted across the warp
+    __shared__ LimScratch<T> lsm;
+    compact_limit<T>(pend, id, lsm, [&](long long ido, int m, int side) -> T {
+        const R *__restrict__ a = pick7(A, qs, m);
         T q[6];
 #pragma unroll
         for (int s = 0; s < 6; ++s)
-            q[s] = a[id + (s - 3) * sd];
-        mp5_lr(q, PL[qs[m]], PR[qs[m]]);
+            q[s] = a[ido + (s - 3) * sd];
+        return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1]) : mp5_limit(q[0], q[1], q[2], q[3], q[4]);
+    });
+    if (!live)
+        return;
+    {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int m = 0; m < 7; ++m) {
+            if (pend & (1u << (2 * m)))
+                Lv[m] = lsm.res[w][lane][2 * m];
+            if (pend & (1u << (2 * m + 1)))
+                Rv[m] = lsm.res[w][lane][2 * m + 1];
+        }
+    }
+    T PL[8], PR[8];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+        PL[qs[m]] = Lv[m];
+        PR[qs[m]] = Rv[m];
     }
     const T Bn = A.U[5 + D][id];
     PL[5 + D] = Bn;
@@ -183,7 +292,7 @@ __global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
     for (int side = 0; side < 2; ++side) {
         T *Ps = side == 0 ? PL : PR;
         const T v2 = Ps[1] * Ps[1] + Ps[2] * Ps[2] + Ps[3] * Ps[3];
-        if (!(Ps[0] > T(0)) || !(Ps[4] > T(0)) || !(v2 < T(1))) {
+        if (!is_pos(Ps[0]) || !is_pos(Ps[4]) || !ilt(v2, T(1))) {
             const long long c = id + (side == 0 ? -sd : 0);
 #pragma unroll
             for (int m = 0; m < 7; ++m)
@@ -193,10 +302,10 @@ __global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
     T FL[5], UL[5], FR[5], UR[5], lpL, lmL, lpR, lmR;
     state_flux<D>(PL, (T)ph.gamma, (T)ph.gr, FL, UL, lpL, lmL);
     state_flux<D>(PR, (T)ph.gamma, (T)ph.gr, FR, UR, lpR, lmR);
-    const T ap = fmax(T(0), fmax(lpL, lpR));
-    const T am = fmax(T(0), fmax(-lmL, -lmR));
+    const T ap = imax(T(0), imax(lpL, lpR));
+    const T am = imax(T(0), imax(-lmL, -lmR));
     const T ssum = ap + am;
-    if (ssum > T(0)) {
+    if (is_pos(ssum)) {
         const T is = T(1) / ssum;
         const T apam = ap * am;
 #pragma unroll
@@ -225,56 +334,103 @@ __global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
 //   E_st = -(v^a_st B~b_s - v^b_st B~a_t)   (s: a-side, t: b-side).
 // v^a, v^b: a-face states (MP5 along a) reconstructed along b; B~b (b-faces)
 // along a; B~a (a-faces) along b; speeds: max over the two adjacent faces.
+// The 12 reconstructions use the same compacted limiter as k_faces.
+template <typename R>
+struct EmfSrc {
+    const R *p[6];      // v^a_L, v^a_R, v^b_L, v^b_R (a-faces, along b), B~b (along a), B~a (along b)
+    long long st[6];    // stencil stride of each source
+};
+
+template <typename R>
+__device__ __forceinline__ void emf_pick(const EmfSrc<R> &S, int m, const R *&p, long long &st)
+{
+    p = S.p[0];
+    st = S.st[0];
+#pragma unroll
+    for (int u = 1; u < 6; ++u)
+        if (m == u) {
+            p = S.p[u];
+            st = S.st[u];
+        }
+}
+
 template <int E, typename R>
 __global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
 {
     constexpr int a = (E + 1) % 3, b = (E + 2) % 3;
-    int t[3];
-    t[0] = blockIdx.x * blockDim.x + threadIdx.x;
-    t[1] = blockIdx.y * blockDim.y + threadIdx.y;
-    t[2] = blockIdx.z;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int lim = d == E ? g.n[d] : g.n[d] + 1;
-        if (t[d] >= lim)
-            return;
+    int cnt[3] = {g.n[0] + 1, g.n[1] + 1, g.n[2] + 1};
+    cnt[E] = g.n[E];
+    const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = t < tot;
+    long long id;
+    {
+        const long long tt = live ? t : 0;
+        const int i = (int)(tt % cnt[0]);
+        const long long r = tt / cnt[0];
+        id = gidx(g, NG + i, NG + (int)(r % cnt[1]), NG + (int)(r / cnt[1]));
     }
-    const long long id = gidx(g, NG + t[0], NG + t[1], NG + t[2]);
     const long long sa = a == 0 ? 1LL : (a == 1 ? g.px : g.pxy);
     const long long sb = b == 0 ? 1LL : (b == 1 ? g.px : g.pxy);
     using T = R;
-    T va[2][2], vb[2][2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        T qa[6], qb[6];
-        const R *__restrict__ pa = A.fv[a][s];
-        const R *__restrict__ pb = A.fv[a][2 + s];
+    EmfSrc<R> S;
+    S.p[0] = A.fv[a][0];
+    S.p[1] = A.fv[a][1];
+    S.p[2] = A.fv[a][2];
+    S.p[3] = A.fv[a][3];
+    S.p[4] = A.U[5 + b];
+    S.p[5] = A.U[5 + a];
+    S.st[0] = S.st[1] = S.st[2] = S.st[3] = sb;
+    S.st[4] = sa;
+    S.st[5] = sb;
+    T Lv[6], Rv[6];
+    unsigned pend = 0;
+    if (live) {
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
-            qa[m] = pa[id + (m - 3) * sb];
-            qb[m] = pb[id + (m - 3) * sb];
+            T q[6];
+#pragma unroll
+            for (int s = 0; s < 6; ++s)
+                q[s] = S.p[m][id + (s - 3) * S.st[m]];
+            bool okL, okR;
+            Lv[m] = mp5_try(q[0], q[1], q[2], q[3], q[4], okL);
+            Rv[m] = mp5_try(q[5], q[4], q[3], q[2], q[1], okR);
+            pend |= (okL ? 0u : 1u) << (2 * m);
+            pend |= (okR ? 0u : 1u) << (2 * m + 1);
         }
-        mp5_lr(qa, va[s][0], va[s][1]);
-        mp5_lr(qb, vb[s][0], vb[s][1]);
     }
-    T Bb[2], Ba[2];
-    {
+    __shared__ LimScratch<T> lsm;
+    compact_limit<T>(pend, id, lsm, [&](long long ido, int m, int side) -> T {
+        const R *p;
+        long long st;
+        emf_pick(S, m, p, st);
         T q[6];
-        const R *__restrict__ pbb = A.U[5 + b];
 #pragma unroll
-        for (int m = 0; m < 6; ++m)
-            q[m] = pbb[id + (m - 3) * sa];
-        mp5_lr(q, Bb[0], Bb[1]);
-        const R *__restrict__ pba = A.U[5 + a];
+        for (int s = 0; s < 6; ++s)
+            q[s] = p[ido + (s - 3) * st];
+        return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1]) : mp5_limit(q[0], q[1], q[2], q[3], q[4]);
+    });
+    if (!live)
+        return;
+    {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-        for (int m = 0; m < 6; ++m)
-            q[m] = pba[id + (m - 3) * sb];
-        mp5_lr(q, Ba[0], Ba[1]);
+        for (int m = 0; m < 6; ++m) {
+            if (pend & (1u << (2 * m)))
+                Lv[m] = lsm.res[w][lane][2 * m];
+            if (pend & (1u << (2 * m + 1)))
+                Rv[m] = lsm.res[w][lane][2 * m + 1];
+        }
     }
-    const T apa = fmax(A.ap[a][id - sb], A.ap[a][id]);
-    const T ama = fmax(A.am[a][id - sb], A.am[a][id]);
-    const T apb = fmax(A.ap[b][id - sa], A.ap[b][id]);
-    const T amb = fmax(A.am[b][id - sa], A.am[b][id]);
+    // va[s][t]: a-face side s (0 L, 1 R), reconstructed along b to side t
+    const T va[2][2] = {{Lv[0], Rv[0]}, {Lv[1], Rv[1]}};
+    const T vb[2][2] = {{Lv[2], Rv[2]}, {Lv[3], Rv[3]}};
+    const T Bb[2] = {Lv[4], Rv[4]};
+    const T Ba[2] = {Lv[5], Rv[5]};
+    const T apa = imax(A.ap[a][id - sb], A.ap[a][id]);
+    const T ama = imax(A.am[a][id - sb], A.am[a][id]);
+    const T apb = imax(A.ap[b][id - sa], A.ap[b][id]);
+    const T amb = imax(A.am[b][id - sa], A.am[b][id]);
     T Est[2][2];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
@@ -283,7 +439,7 @@ __global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
             Est[s][u] = -(va[s][u] * Bb[s] - vb[s][u] * Ba[u]);
     const T sA = apa + ama, sB = apb + amb;
     T wLL, wLR, wRL, wRR;
-    if (sA > T(0) && sB > T(0)) {
+    if (is_pos(sA) && is_pos(sB)) {
         const T iden = T(1) / (sA * sB);
         wLL = apa * apb * iden;
         wLR = apa * amb * iden;
@@ -292,8 +448,8 @@ __global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
     } else {
         wLL = wLR = wRL = wRR = T(0.25);
     }
-    const T da = sA > T(0) ? apa * ama / sA : T(0);
-    const T db = sB > T(0) ? apb * amb / sB : T(0);
+    const T da = is_pos(sA) ? apa * ama / sA : T(0);
+    const T db = is_pos(sB) ? apb * amb / sB : T(0);
     A.E[E][id] = wLL * Est[0][0] + wLR * Est[0][1] + wRL * Est[1][0] + wRR * Est[1][1]
                  + da * (Bb[1] - Bb[0]) - db * (Ba[1] - Ba[0]);
 }
@@ -635,25 +791,31 @@ void launch_c2p(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mod
 template <typename R>
 void launch_faces(const Geom &g, const Phys &ph, const Arrays<R> &A, int d, cudaStream_t s)
 {
-    dim3 blk(32, 4, 1);
+    long long cnt[3] = {g.np[0], g.np[1], g.np[2]};
+    cnt[d] = g.n[d] + 1;
+    const long long tot = cnt[0] * cnt[1] * cnt[2];
+    const unsigned blocks = (unsigned)((tot + 127) / 128);
     if (d == 0)
-        k_faces<0, R><<<grid3(g.n[0] + 1, g.np[1], g.np[2], blk), blk, 0, s>>>(g, ph, A);
+        k_faces<0, R><<<blocks, 128, 0, s>>>(g, ph, A);
     else if (d == 1)
-        k_faces<1, R><<<grid3(g.np[0], g.n[1] + 1, g.np[2], blk), blk, 0, s>>>(g, ph, A);
+        k_faces<1, R><<<blocks, 128, 0, s>>>(g, ph, A);
     else
-        k_faces<2, R><<<grid3(g.np[0], g.np[1], g.n[2] + 1, blk), blk, 0, s>>>(g, ph, A);
+        k_faces<2, R><<<blocks, 128, 0, s>>>(g, ph, A);
 }
 
 template <typename R>
 void launch_emf(const Geom &g, const Arrays<R> &A, int e, cudaStream_t s)
 {
-    dim3 blk(32, 4, 1);
+    long long cnt[3] = {g.n[0] + 1, g.n[1] + 1, g.n[2] + 1};
+    cnt[e] = g.n[e];
+    const long long tot = cnt[0] * cnt[1] * cnt[2];
+    const unsigned blocks = (unsigned)((tot + 127) / 128);
     if (e == 0)
-        k_emf<0, R><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1, blk), blk, 0, s>>>(g, A);
+        k_emf<0, R><<<blocks, 128, 0, s>>>(g, A);
     else if (e == 1)
-        k_emf<1, R><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1, blk), blk, 0, s>>>(g, A);
+        k_emf<1, R><<<blocks, 128, 0, s>>>(g, A);
     else
-        k_emf<2, R><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2], blk), blk, 0, s>>>(g, A);
+        k_emf<2, R><<<blocks, 128, 0, s>>>(g, A);
 }
 
 template <typename R>

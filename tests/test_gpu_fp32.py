@@ -1,0 +1,58 @@
+"""FP32-bulk path (stencil, fluxes, EMFs and RK update in FP32; c2p,
+metric and reductions in FP64) against the FP64 oracle.  Target: relative L1
+error per field <= 1e-5 after 10 steps."""
+import numpy as np
+import pytest
+
+from paper_1810_04597_gb300 import inputs
+from gpu_util import gpu_run, l1_rel, max_rel, oracle_run, per_field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def test_fp32_ten_steps_l1(orc):
+    prob = inputs.smooth_box(32)
+    st_g, s = gpu_run(prob, 10, precision=32)
+    st_o, _, _, _ = oracle_run(orc, prob, 10)
+    l1 = per_field(orc, st_g, st_o, prob.n, metric=l1_rel)
+    assert max(l1.values()) <= 1e-5, l1
+    mx = per_field(orc, st_g, st_o, prob.n, metric=max_rel)
+    assert max(mx.values()) <= 1e-4, mx
+    t = s.reduce()
+    assert t["c2p_fail"] == 0
+
+
+def test_fp32_conservation_and_divb():
+    prob = inputs.sweep_box(48, seed=8)
+    from paper_1810_04597_gb300.echo import Solver
+    s = Solver(prob, precision=32)
+    s.set_prims()
+    t0 = s.reduce()
+    for _ in range(5):
+        s.step()
+    t1 = s.reduce()
+    assert abs(t1["mass"] - t0["mass"]) <= 1e-6 * abs(t0["mass"])
+    assert abs(t1["energy"] - t0["energy"]) <= 1e-6 * abs(t0["energy"])
+    st = s.get_state()
+    bmax = np.max(np.abs(st[5 * prob.ncells:]))
+    assert t1["max_divb"] * prob.dx[0] / bmax <= 1e-5
+
+
+def test_fp32_rhs_close_to_oracle(orc):
+    prob = inputs.smooth_box(24, seed=13)
+    from paper_1810_04597_gb300.echo import Solver
+    s = Solver(prob, precision=32)
+    s.set_prims()
+    L_g = s.rhs()
+    cfg = orc.make_cfg(prob)
+    st, Z = orc.p2c(cfg, prob.prims, prob.bface)
+    L_o, _, _ = orc.rhs(cfg, st, Z)
+    l1 = per_field(orc, L_g, L_o, prob.n, metric=l1_rel)
+    assert max(l1.values()) <= 1e-4, l1
