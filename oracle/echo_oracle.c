@@ -1132,12 +1132,20 @@ static void assemble(const ocfg *c, ogrid *G)
     }
 }
 
-/* One evaluation of L(U) on the grid G (U, B, Z set on owned cells). */
-static int eval_rhs(const ocfg *c, ogrid *G, ostats *st, double *rate_max)
+/* One evaluation of L(U) on the grid G (U, B, Z set on owned cells).
+ * save (may be NULL): 8 arrays that receive U and B~ right after the c2p,
+ * i.e. after floors and failure fallbacks have reset the conserved state. */
+static int eval_rhs(const ocfg *c, ogrid *G, ostats *st, double *rate_max, double *const *save)
 {
     fill_faces(c, G);
     if (c2p_grid(c, G, st))
         return -1;
+    if (save) {
+        for (int q = 0; q < 5; ++q)
+            memcpy(save[q], G->U[q], G->ncell * sizeof(double));
+        for (int q = 0; q < 3; ++q)
+            memcpy(save[5 + q], G->B[q], G->ncell * sizeof(double));
+    }
     if (rate_max)
         *rate_max = cfl_rate_max(c, G);
     fill_prims(c, G);
@@ -1334,7 +1342,7 @@ int oracle_rhs(const ocfg *c, const double *state, double *Z, double *L, double 
     unpack_state(&G, state);
     unpack_cell(&G, Z, G.Z);
     ostats st = {0, 0, 0, 0, 0};
-    int rc = eval_rhs(c, &G, &st, rate_max);
+    int rc = eval_rhs(c, &G, &st, rate_max, NULL);
     if (rc == 0) {
         /* periodic axes: the duplicate last face repeats the first */
         for (int d = 0; d < 3; ++d)
@@ -1350,6 +1358,8 @@ int oracle_rhs(const ocfg *c, const double *state, double *Z, double *L, double 
  *   U1 = U0 + dt L(U0)
  *   U2 = 3/4 U0 + 1/4 (U1 + dt L(U1))
  *   U3 = 1/3 U0 + 2/3 (U2 + dt L(U2)).
+ * U0 is the state at the start of the step after the first stage's c2p
+ * (floors and failure fallbacks reset the conserved variables there).
  * dt_in > 0: fixed dt; otherwise dt = cfl / max_cells sum_d max|lambda_d|/dx_d
  * from the primitives of the first stage of each step.  dts (may be NULL)
  * receives the dt of each step; stats5 (may be NULL): c2p iterations, c2p
@@ -1365,21 +1375,17 @@ int oracle_steps(const ocfg *c, double *state, double *Z, int nsteps, double dt_
     unpack_cell(&G, Z, G.Z);
     ostats st = {0, 0, 0, 0, 0};
     size_t N = G.ncell;
-    double *U0[8], *U1[8];
-    for (int q = 0; q < 8; ++q) {
+    double *U0[8];
+    for (int q = 0; q < 8; ++q)
         U0[q] = (double *)malloc(N * sizeof(double));
-        U1[q] = (double *)malloc(N * sizeof(double));
-    }
     double *const Ucur[8] = {G.U[0], G.U[1], G.U[2], G.U[3], G.U[4], G.B[0], G.B[1], G.B[2]};
     double *const Lcur[8] = {G.LU[0], G.LU[1], G.LU[2], G.LU[3], G.LU[4], G.LB[0], G.LB[1], G.LB[2]};
     int rc = 0;
     for (int step = 0; step < nsteps && rc == 0; ++step) {
-        for (int q = 0; q < 8; ++q)
-            memcpy(U0[q], Ucur[q], N * sizeof(double));
         double dt = dt_in;
         for (int s = 0; s < 3 && rc == 0; ++s) {
             double rmax = 0.0;
-            rc = eval_rhs(c, &G, &st, s == 0 && dt_in <= 0.0 ? &rmax : NULL);
+            rc = eval_rhs(c, &G, &st, s == 0 && dt_in <= 0.0 ? &rmax : NULL, s == 0 ? U0 : NULL);
             if (rc)
                 break;
             if (s == 0 && dt_in <= 0.0)
@@ -1420,10 +1426,8 @@ int oracle_steps(const ocfg *c, double *state, double *Z, int nsteps, double dt_
         stats5[3] = st.floor_hits;
         stats5[4] = st.fallback_faces;
     }
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 8; ++q)
         free(U0[q]);
-        free(U1[q]);
-    }
     grid_free(&G);
     return rc;
 }

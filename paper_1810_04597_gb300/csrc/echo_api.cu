@@ -91,6 +91,18 @@ size_t layout(echo_ctx *c, char *base, Arrays<R> *A)
         A->E[d] = arr();
     }
     A->Z = reinterpret_cast<double *>(take(cells * sizeof(double)));
+    A->met = MetTables{};
+    A->met.np0 = c->geo.np[0];
+    A->met.use_floors = c->eos.floors;
+    if (c->metric.kind == ECHO_METRIC_KERR_SCHILD) {
+        const size_t plane = (size_t)c->geo.np[0] * c->geo.np[1];
+        A->met.C = reinterpret_cast<MetPt *>(take(plane * sizeof(MetPt)));
+        A->met.F1 = reinterpret_cast<MetPt *>(take(plane * sizeof(MetPt)));
+        A->met.F2 = reinterpret_cast<MetPt *>(take(plane * sizeof(MetPt)));
+        A->met.K = reinterpret_cast<MetPt *>(take(plane * sizeof(MetPt)));
+        A->met.dC = reinterpret_cast<MetDer *>(take(plane * sizeof(MetDer)));
+        A->met.floors = reinterpret_cast<double *>(take((size_t)c->geo.np[0] * 2 * sizeof(double)));
+    }
     A->stage = reinterpret_cast<double *>(take(c->staging_count * sizeof(double)));
     A->partials = reinterpret_cast<double *>(take((size_t)c->nblk_red * 6 * sizeof(double)));
     A->scal = reinterpret_cast<DevScalars *>(take(sizeof(DevScalars)));
@@ -168,52 +180,58 @@ Arrays<float> &arrays<float>(echo_ctx *c) { return c->af; }
 
 // ---- operations, templated on the storage type
 
-template <typename R>
+template <int MK, typename R>
 void enqueue_rhs_pass(echo_ctx *c, int stage, double *Lout, bool want_rate, double dt_fixed)
 {
     Arrays<R> &A = arrays<R>(c);
     cudaStream_t s = c->stream;
     PROF(ECHO_K_FILL_FACES, launch_fill<R>(c->geo, face_list(A), s));
-    PROF(ECHO_K_C2P, launch_c2p<R>(c->geo, c->ph, A, 0, want_rate ? 1 : 0, s));
+    PROF(ECHO_K_C2P, (launch_c2p<MK, R>(c->geo, c->ph, A, 0, want_rate ? 1 : 0, s)));
     if (want_rate)
         PROF(ECHO_K_SCALARS, launch_set_dt(A.scal, c->cfl, dt_fixed <= 0.0 ? 1 : 0, s));
     PROF(ECHO_K_FILL_PRIMS, launch_fill<R>(c->geo, prim_list(A), s));
     for (int d = 0; d < 3; ++d)
-        PROF(ECHO_K_FACES_X + d, launch_faces<R>(c->geo, c->ph, A, d, s));
+        PROF(ECHO_K_FACES_X + d, (launch_faces<MK, R>(c->geo, c->ph, A, d, s)));
     for (int e = 0; e < 3; ++e)
-        PROF(ECHO_K_EMF_X + e, launch_emf<R>(c->geo, A, e, s));
-    PROF(ECHO_K_UPDATE, launch_update<R>(c->geo, A, stage, Lout, s));
+        PROF(ECHO_K_EMF_X + e, (launch_emf<MK, R>(c->geo, A, e, s)));
+    PROF(ECHO_K_UPDATE, (launch_update<MK, R>(c->geo, c->ph, A, stage, Lout, s)));
 }
 
-template <typename R>
+template <int MK, typename R>
 int op_step(echo_ctx *c, double dt)
 {
     Arrays<R> &A = arrays<R>(c);
     PROF(ECHO_K_SCALARS, launch_step_begin(A.scal, dt > 0.0 ? dt : 0.0, c->stream));
     for (int st = 0; st < 3; ++st)
-        enqueue_rhs_pass<R>(c, st, nullptr, st == 0, dt);
+        enqueue_rhs_pass<MK, R>(c, st, nullptr, st == 0, dt);
     return cuda_check(c, "echo_step");
 }
 
-template <typename R>
+template <int MK, typename R>
 int op_rhs(echo_ctx *c, double *Lout)
 {
     Arrays<R> &A = arrays<R>(c);
     launch_step_begin(A.scal, 0.0, c->stream);
-    enqueue_rhs_pass<R>(c, -1, Lout, true, 0.0);
+    enqueue_rhs_pass<MK, R>(c, -1, Lout, true, 0.0);
     return cuda_check(c, "echo_rhs");
 }
 
-template <typename R>
+template <int MK, typename R>
 int op_c2p(echo_ctx *c, int guess_mode)
 {
     Arrays<R> &A = arrays<R>(c);
     PROF(ECHO_K_SCALARS, launch_step_begin(A.scal, 0.0, c->stream));
     PROF(ECHO_K_FILL_FACES, launch_fill<R>(c->geo, face_list(A), c->stream));
-    PROF(ECHO_K_C2P, launch_c2p<R>(c->geo, c->ph, A, guess_mode, 1, c->stream));
+    PROF(ECHO_K_C2P, (launch_c2p<MK, R>(c->geo, c->ph, A, guess_mode, 1, c->stream)));
     PROF(ECHO_K_SCALARS, launch_set_dt(A.scal, c->cfl, 1, c->stream));
     return cuda_check(c, "echo_c2p");
 }
+
+// Dispatch an operation template on (metric kind, storage type).
+#define ECHO_DISPATCH(c, fn, ...)                                                               \
+    ((c)->metric.kind == ECHO_METRIC_KERR_SCHILD                                                \
+         ? ((c)->precision == 64 ? fn<1, double>((c), __VA_ARGS__) : fn<1, float>((c), __VA_ARGS__)) \
+         : ((c)->precision == 64 ? fn<0, double>((c), __VA_ARGS__) : fn<0, float>((c), __VA_ARGS__)))
 
 int read_scalars(echo_ctx *c, DevScalars *hs)
 {
@@ -259,8 +277,10 @@ int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *
         if ((lo == ECHO_BC_AXIS || hi == ECHO_BC_AXIS) && grid->n[d] < NG)
             return ECHO_EINVAL;
     }
-    if (metric->kind != ECHO_METRIC_FLAT)
-        return ECHO_EINVAL;  // only the flat metric has device kernels
+    if (metric->kind != ECHO_METRIC_FLAT && metric->kind != ECHO_METRIC_KERR_SCHILD)
+        return ECHO_EINVAL;
+    if (metric->kind == ECHO_METRIC_KERR_SCHILD && !(metric->spin >= 0.0 && metric->spin < 1.0))
+        return ECHO_EINVAL;
     if (!(eos->gamma > 1.0) || !(cfl > 0.0) || (precision != 64 && precision != 32))
         return ECHO_EINVAL;
     const long long cells = (long long)grid->n[0] * grid->n[1] * grid->n[2];
@@ -328,6 +348,11 @@ int echo_bind(echo_ctx *c, void *ws, size_t bytes, void *stream)
         layout<float>(c, c->ws, &c->af);
     if (cudaMemsetAsync(c->ws, 0, c->ws_need, c->stream) != cudaSuccess)
         return cuda_check(c, "echo_bind memset");
+    if (c->metric.kind == ECHO_METRIC_KERR_SCHILD) {
+        const MetTables &T = c->precision == 64 ? c->ad.met : c->af.met;
+        launch_metric_tables(c->geo, c->metric.spin, T, c->eos.rho_floor, c->eos.rho_floor_pow, c->eos.p_floor,
+                             c->eos.p_floor_pow, c->stream);
+    }
     c->bound = true;
     c->have_state = false;
     return cuda_check(c, "echo_bind");
@@ -359,14 +384,21 @@ int echo_set_prims(echo_ctx *c, const double *prims5, const double *bface, int o
     const double *df = stage_input(c, bface, c->nstate - 5 * N, 5 * N, on_device, &rc);
     if (rc)
         return rc;
+    const bool ks = c->metric.kind == ECHO_METRIC_KERR_SCHILD;
     if (c->precision == 64) {
         launch_unpack_state<double>(c->geo, df, c->ad, 1, c->stream);
         launch_fill<double>(c->geo, face_list(c->ad), c->stream);
-        launch_p2c<double>(c->geo, c->ph, dp, c->ad, c->stream);
+        if (ks)
+            launch_p2c<1, double>(c->geo, c->ph, dp, c->ad, c->stream);
+        else
+            launch_p2c<0, double>(c->geo, c->ph, dp, c->ad, c->stream);
     } else {
         launch_unpack_state<float>(c->geo, df, c->af, 1, c->stream);
         launch_fill<float>(c->geo, face_list(c->af), c->stream);
-        launch_p2c<float>(c->geo, c->ph, dp, c->af, c->stream);
+        if (ks)
+            launch_p2c<1, float>(c->geo, c->ph, dp, c->af, c->stream);
+        else
+            launch_p2c<0, float>(c->geo, c->ph, dp, c->af, c->stream);
     }
     rc = cuda_check(c, "echo_set_prims");
     if (rc == ECHO_OK)
@@ -474,7 +506,7 @@ int echo_c2p(echo_ctx *c, int guess_mode, echo_totals *stats)
         return rc;
     if (guess_mode != 0 && guess_mode != 2)
         return fail(c, ECHO_EINVAL, "guess_mode must be 0 (previous Z) or 2 (cold)");
-    rc = c->precision == 64 ? op_c2p<double>(c, guess_mode) : op_c2p<float>(c, guess_mode);
+    rc = ECHO_DISPATCH(c, op_c2p, guess_mode);
     if (rc || !stats)
         return rc;
     DevScalars hs;
@@ -503,7 +535,7 @@ int echo_rhs(echo_ctx *c, double *L, int on_device)
     if (!L)
         return fail(c, ECHO_EINVAL, "null output");
     double *dst = on_device ? L : (c->precision == 64 ? c->ad.stage : c->af.stage);
-    rc = c->precision == 64 ? op_rhs<double>(c, dst) : op_rhs<float>(c, dst);
+    rc = ECHO_DISPATCH(c, op_rhs, dst);
     if (rc)
         return rc;
     if (!on_device)
@@ -516,7 +548,7 @@ int echo_step(echo_ctx *c, double dt)
     int rc = require_bound(c, true);
     if (rc)
         return rc;
-    return c->precision == 64 ? op_step<double>(c, dt) : op_step<float>(c, dt);
+    return ECHO_DISPATCH(c, op_step, dt);
 }
 
 int echo_reduce(echo_ctx *c, echo_totals *out)
@@ -526,7 +558,7 @@ int echo_reduce(echo_ctx *c, echo_totals *out)
         return rc;
     if (!out)
         return fail(c, ECHO_EINVAL, "null output");
-    rc = c->precision == 64 ? op_c2p<double>(c, 0) : op_c2p<float>(c, 0);
+    rc = ECHO_DISPATCH(c, op_c2p, 0);
     if (rc)
         return rc;
     if (c->precision == 64)

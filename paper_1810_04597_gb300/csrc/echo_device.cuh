@@ -1,5 +1,6 @@
 // echo_device.cuh -- device data structures and per-point physics of the
-// GRMHD step (flat metric).  Included by the kernel translation units only.
+// GRMHD step on a flat or Kerr-Schild metric.  Included by the kernel
+// translation units only.
 //
 // Arithmetic follows the published methods named in include/echo.h; it is
 // written for the GPU (one division per reciprocal reused, rsqrt for the
@@ -60,6 +61,32 @@ struct DevScalars {
     double totals[8];            // mass, energy, mom x3, max divB, rate, spare
 };
 
+// Metric at one point of the axisymmetric (x1, x2) plane, FP64: lapse,
+// shift^1 (the only non-zero shift component of Kerr-Schild), the non-zero
+// spatial metric components gamma_11, _13, _22, _33, their inverse, and
+// sqrt(gamma) with its reciprocal (0 on the polar axis).
+struct MetPt {
+    double al, b1, g11, g13, g22, g33, i11, i13, i22, i33, sg, isg;
+};
+
+// d_1 and d_2 of alpha, beta^1, gamma_11, _13, _22, _33 at a cell centre
+// (fourth-order centred differences of the closed form, step dx^d).
+struct MetDer {
+    double dal[2], db1[2], dg11[2], dg13[2], dg22[2], dg33[2];
+};
+
+// Tables over the padded (x1, x2) plane, index j * np0 + i: cell centres C,
+// x1-faces F1 (i-1/2, j), x2-faces F2 (i, j-1/2), corners K (i-1/2, j-1/2);
+// the x3-faces and x3-edges share C, F1/F2 and K positions.  floors: per i,
+// the density and pressure floors at the cell centre.
+struct MetTables {
+    MetPt *C, *F1, *F2, *K;
+    MetDer *dC;
+    double *floors;   // 2 * np0
+    int np0;
+    int use_floors;
+};
+
 // All device arrays of a context, R = storage type of the bulk fields.
 template <typename R>
 struct Arrays {
@@ -75,6 +102,7 @@ struct Arrays {
     double *stage; // host-layout staging (FP64)
     double *partials;  // reduction partials
     DevScalars *scal;
+    MetTables met; // Kerr-Schild tables (unused in flat space)
 };
 
 // ------------------------------------------------------------------ exact
@@ -130,6 +158,79 @@ __device__ __forceinline__ double with_sign_of(double mag, double s)
 __device__ __forceinline__ float with_sign_of(float mag, float s)
 {
     return __int_as_float(__float_as_int(mag) | (__float_as_int(s) & (int)0x80000000u));
+}
+
+// ------------------------------------------------------------------ metric
+// accessors.  MFlat is the Minkowski metric in Cartesian coordinates (every
+// metric factor folds away at compile time); MKS holds one table point.
+
+template <typename T>
+struct MFlat {
+    static constexpr bool flat = true;
+};
+
+template <typename T>
+struct MKS {
+    static constexpr bool flat = false;
+    T al, b1, g11, g13, g22, g33, i11, i13, i22, i33, sg;
+    __device__ __forceinline__ explicit MKS(const MetPt &m)
+        : al((T)m.al), b1((T)m.b1), g11((T)m.g11), g13((T)m.g13), g22((T)m.g22), g33((T)m.g33),
+          i11((T)m.i11), i13((T)m.i13), i22((T)m.i22), i33((T)m.i33), sg((T)m.sg)
+    {
+    }
+};
+
+template <typename T, typename M>
+__device__ __forceinline__ void lower(const M &m, const T u[3], T d[3])
+{
+    if constexpr (M::flat) {
+        d[0] = u[0];
+        d[1] = u[1];
+        d[2] = u[2];
+    } else {
+        d[0] = m.g11 * u[0] + m.g13 * u[2];
+        d[1] = m.g22 * u[1];
+        d[2] = m.g13 * u[0] + m.g33 * u[2];
+    }
+}
+
+template <typename T, typename M>
+__device__ __forceinline__ void raise(const M &m, const T d[3], T u[3])
+{
+    if constexpr (M::flat) {
+        u[0] = d[0];
+        u[1] = d[1];
+        u[2] = d[2];
+    } else {
+        u[0] = m.i11 * d[0] + m.i13 * d[2];
+        u[1] = m.i22 * d[1];
+        u[2] = m.i13 * d[0] + m.i33 * d[2];
+    }
+}
+
+// component D of gamma^{Dk} d_k
+template <int D, typename T, typename M>
+__device__ __forceinline__ T raise_c(const M &m, const T d[3])
+{
+    if constexpr (M::flat) {
+        return d[D];
+    } else {
+        if constexpr (D == 0)
+            return m.i11 * d[0] + m.i13 * d[2];
+        else if constexpr (D == 1)
+            return m.i22 * d[1];
+        else
+            return m.i13 * d[0] + m.i33 * d[2];
+    }
+}
+
+template <int D, typename T, typename M>
+__device__ __forceinline__ T gup(const M &m)
+{
+    if constexpr (M::flat)
+        return T(1);
+    else
+        return D == 0 ? m.i11 : (D == 1 ? m.i22 : m.i33);
 }
 
 // ------------------------------------------------------------------ MP5
@@ -219,23 +320,30 @@ __device__ __forceinline__ void mp5_lr(const T q[6], T &L, T &R)
 
 // ------------------------------------------------------------------ state
 
-// Flat-metric conserved vector, physical flux along D and HLL speeds of a
-// primitive state P = (rho, v^x, v^y, v^z, p, B^x, B^y, B^z).
+// Conserved vector, physical flux along D and HLL speeds of a primitive
+// state P = (rho, v^1, v^2, v^3, p, B^1, B^2, B^3) (contravariant v, B),
+// both vectors multiplied by sqrt(gamma) of the point (3+1 Valencia form):
 //   D = rho W, S_j = (rho h W^2 + B^2) v_j - (v.B) B_j,
 //   tau = rho h W^2 - p + (B^2 + B^2 v^2 - (v.B)^2)/2 - D;
-//   F(D) = D v^d, F(S_j) = (rho h + b^2) W^2 v^d v_j + (p + b^2/2) delta_dj - b^d b_j,
-//   F(tau) = S_d - D v^d, with b^i = B^i/W + W (v.B) v^i, b^2 = B^2/W^2 + (v.B)^2;
+//   F(D) = D (alpha v^d - beta^d),
+//   F(S_j) = alpha [(rho h + b^2) W^2 v^d v_j + (p + b^2/2) delta^d_j - b^d b_j] - beta^d S_j,
+//   F(tau) = alpha (S^d - D v^d) - beta^d tau,
+// with b^i = B^i/W + W (v.B) v^i, b^2 = B^2/W^2 + (v.B)^2;
 //   a^2 = c_s^2 + c_A^2 - c_s^2 c_A^2 = (G p + b^2)/(rho h + b^2),
-//   lambda = [v^d (1 - a^2) +- sqrt(a^2 (1-v^2)((1 - v^2 a^2) - (1 - a^2)(v^d)^2))]
-//            / (1 - v^2 a^2).
-template <int D, typename T>
-__device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, T F[5], T U[5], T &lp, T &lm)
+//   lambda = alpha [v^d (1 - a^2) +- sqrt(a^2 (1-v^2)((1 - v^2 a^2) gamma^dd
+//            - (1 - a^2)(v^d)^2))] / (1 - v^2 a^2) - beta^d.
+template <int D, typename T, typename M>
+__device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m, T F[5], T U[5], T &lp, T &lm)
 {
-    const T rho = P[0], vx = P[1], vy = P[2], vz = P[3], p = P[4];
-    const T Bx = P[5], By = P[6], Bz = P[7];
-    const T v2 = vx * vx + vy * vy + vz * vz;
-    const T B2 = Bx * Bx + By * By + Bz * Bz;
-    const T vB = vx * Bx + vy * By + vz * Bz;
+    const T rho = P[0], p = P[4];
+    const T v[3] = {P[1], P[2], P[3]};
+    const T B[3] = {P[5], P[6], P[7]};
+    T vl[3], Bl[3];
+    lower<T>(m, v, vl);
+    lower<T>(m, B, Bl);
+    const T v2 = vl[0] * v[0] + vl[1] * v[1] + vl[2] * v[2];
+    const T B2 = Bl[0] * B[0] + Bl[1] * B[1] + Bl[2] * B[2];
+    const T vB = vl[0] * B[0] + vl[1] * B[1] + vl[2] * B[2];
     const T iW2 = T(1) - v2;
     const T W = rsqrt(iW2);
     const T iW = iW2 * W;
@@ -245,47 +353,70 @@ __device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, T F[5], T 
     const T Dn = rho * W;
     const T Zw = rhoh * W2;
     const T ZB = Zw + B2;
-    const T v[3] = {vx, vy, vz};
-    const T B[3] = {Bx, By, Bz};
     U[0] = Dn;
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-        U[1 + j] = ZB * v[j] - vB * B[j];
+        U[1 + j] = ZB * vl[j] - vB * Bl[j];
     U[4] = Zw - p + T(0.5) * (B2 + B2 * v2 - vB * vB) - Dn;
     const T vd = v[D];
     const T Wvb = W * vB;
     const T bd = B[D] * iW + Wvb * vd;
     const T wt = (rhoh + b2) * W2 * vd;
-    F[0] = Dn * vd;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const T bj = B[j] * iW + Wvb * v[j];
-        F[1 + j] = wt * v[j] - bd * bj + (j == D ? p + T(0.5) * b2 : T(0));
-    }
-    F[4] = U[1 + D] - Dn * vd;
     // With G = G p + b^2 and X = rho h + b^2 (a^2 = G/X), multiplying the
     // eigenvalue formula through by X leaves one division:
-    //   lambda = [v^d (rho h - G p) +- sqrt(G (1-v^2)(Y - (rho h - G p)(v^d)^2))] / Y,
-    //   Y = X - v^2 G.
+    //   lambda = alpha [v^d (rho h - G p) +- sqrt(G (1-v^2)(Y gamma^dd - (rho h - G p)(v^d)^2))] / Y
+    //            - beta^d,  Y = X - v^2 G.
     const T Gs = gam * p + b2;
     const T Y = (rhoh + b2) - v2 * Gs;
     const T rmg = rhoh - gam * p;
-    const T disc = Gs * iW2 * (Y - rmg * vd * vd);
+    const T disc = Gs * iW2 * (Y * gup<D, T>(m) - rmg * vd * vd);
     const T sq = sqrt(is_pos(disc) ? disc : T(0));
     const T iY = T(1) / Y;
     const T base = vd * rmg;
-    lp = (base + sq) * iY;
-    lm = (base - sq) * iY;
+    if constexpr (M::flat) {
+        F[0] = Dn * vd;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const T bj = Bl[j] * iW + Wvb * vl[j];
+            F[1 + j] = wt * vl[j] - bd * bj + (j == D ? p + T(0.5) * b2 : T(0));
+        }
+        F[4] = U[1 + D] - Dn * vd;
+        lp = (base + sq) * iY;
+        lm = (base - sq) * iY;
+    } else {
+        const T al = m.al;
+        const T be = D == 0 ? m.b1 : T(0);
+        F[0] = Dn * (al * vd - be);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const T bj = Bl[j] * iW + Wvb * vl[j];
+            F[1 + j] = al * (wt * vl[j] - bd * bj + (j == D ? p + T(0.5) * b2 : T(0))) - be * U[1 + j];
+        }
+        const T Su[3] = {U[1], U[2], U[3]};
+        F[4] = al * (raise_c<D, T>(m, Su) - Dn * vd) - be * U[4];
+        lp = al * (base + sq) * iY - be;
+        lm = al * (base - sq) * iY - be;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            F[q] *= m.sg;
+            U[q] *= m.sg;
+        }
+    }
 }
 
 // Sum over directions of max(|lambda+|, |lambda-|)/dx (CFL rate) of a cell
-// (same eigenvalue form as state_flux).
-__device__ __forceinline__ double cfl_rate(const double P[8], double gam, double gr, const double idx[3])
+// (same eigenvalue form as state_flux), FP64.
+template <typename M>
+__device__ __forceinline__ double cfl_rate(const double P[8], double gam, double gr, const double idx[3], const M &m)
 {
-    const double vx = P[1], vy = P[2], vz = P[3], p = P[4];
-    const double v2 = vx * vx + vy * vy + vz * vz;
-    const double B2 = P[5] * P[5] + P[6] * P[6] + P[7] * P[7];
-    const double vB = vx * P[5] + vy * P[6] + vz * P[7];
+    const double v[3] = {P[1], P[2], P[3]}, B[3] = {P[5], P[6], P[7]};
+    double vl[3], Bl[3];
+    lower<double>(m, v, vl);
+    lower<double>(m, B, Bl);
+    const double p = P[4];
+    const double v2 = vl[0] * v[0] + vl[1] * v[1] + vl[2] * v[2];
+    const double B2 = Bl[0] * B[0] + Bl[1] * B[1] + Bl[2] * B[2];
+    const double vB = vl[0] * B[0] + vl[1] * B[1] + vl[2] * B[2];
     const double iW2 = 1.0 - v2;
     const double rhoh = P[0] + gr * p;
     const double b2 = B2 * iW2 + vB * vB;
@@ -293,21 +424,54 @@ __device__ __forceinline__ double cfl_rate(const double P[8], double gam, double
     const double Y = (rhoh + b2) - v2 * Gs;
     const double rmg = rhoh - gam * p;
     const double iY = 1.0 / Y;
-    const double v[3] = {vx, vy, vz};
     double s = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const double disc = Gs * iW2 * (Y - rmg * v[d] * v[d]);
+        double gdd = 1.0, al = 1.0, be = 0.0;
+        if constexpr (!M::flat) {
+            gdd = d == 0 ? m.i11 : (d == 1 ? m.i22 : m.i33);
+            al = m.al;
+            be = d == 0 ? m.b1 : 0.0;
+        }
+        const double disc = Gs * iW2 * (Y * gdd - rmg * v[d] * v[d]);
         const double sq = sqrt(is_pos(disc) ? disc : 0.0);
         const double base = v[d] * rmg;
-        s += imax(iabs(base + sq), iabs(base - sq)) * iY * idx[d];
+        double lp = (base + sq) * iY, lm = (base - sq) * iY;
+        if constexpr (!M::flat) {
+            lp = al * lp - be;
+            lm = al * lm - be;
+        }
+        s += imax(iabs(lp), iabs(lm)) * idx[d];
     }
     return s;
 }
 
+// Conserved (undensitised, C5) and Z = rho h W^2 of cell primitives (FP64).
+template <typename M>
+__device__ __forceinline__ void p2c_point(const double P[8], double gr, const M &m, double C5[5], double &Z)
+{
+    const double v[3] = {P[1], P[2], P[3]}, B[3] = {P[5], P[6], P[7]};
+    double vl[3], Bl[3];
+    lower<double>(m, v, vl);
+    lower<double>(m, B, Bl);
+    const double v2 = vl[0] * v[0] + vl[1] * v[1] + vl[2] * v[2];
+    const double B2 = Bl[0] * B[0] + Bl[1] * B[1] + Bl[2] * B[2];
+    const double vB = vl[0] * B[0] + vl[1] * B[1] + vl[2] * B[2];
+    const double W2 = 1.0 / (1.0 - v2);
+    const double W = sqrt(W2);
+    const double Zw = (P[0] + gr * P[4]) * W2;
+    const double Dn = P[0] * W;
+    C5[0] = Dn;
+    for (int c = 0; c < 3; ++c)
+        C5[1 + c] = (Zw + B2) * vl[c] - vB * Bl[c];
+    C5[4] = Zw - P[4] + 0.5 * (B2 + B2 * v2 - vB * vB) - Dn;
+    Z = Zw;
+}
+
 // ------------------------------------------------------------------ c2p
 
-// Newton iteration on Z = rho h W^2 (flat metric, FP64 always).
+// Newton iteration on Z = rho h W^2 (FP64 always), with
+// S^2 = gamma^ij S_i S_j, S.B = S_i B^i, B^2 = gamma_ij B^i B^j:
 //   v^2(Z) = [S^2 Z^2 + (S.B)^2 (2Z + B^2)] / [Z^2 (Z + B^2)^2]
 //   p(Z)   = (G-1)/G [Z (1 - v^2) - D sqrt(1 - v^2)]
 //   f(Z)   = Z - p + (1 + v^2) B^2 / 2 - (S.B)^2 / (2 Z^2) - (tau + D)
@@ -335,13 +499,17 @@ __device__ __forceinline__ void c2p_recip(double Z, double B2, double &iZ, doubl
     iZB = inv * Z;
 }
 
+template <typename M>
 __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], double tau, const double B[3],
-                                                double Zguess, double gm1g)
+                                                double Zguess, double gm1g, const M &m)
 {
-    const double S2 = S[0] * S[0] + S[1] * S[1] + S[2] * S[2];
+    double Su[3], Bl[3];
+    raise<double>(m, S, Su);
+    lower<double>(m, B, Bl);
+    const double S2 = S[0] * Su[0] + S[1] * Su[1] + S[2] * Su[2];
     const double SB = S[0] * B[0] + S[1] * B[1] + S[2] * B[2];
     const double SB2 = SB * SB;
-    const double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const double B2 = Bl[0] * B[0] + Bl[1] * B[1] + Bl[2] * B[2];
     const double Uen = tau + Dc;
     C2PResult r;
     double Z = Zguess, iZ = 0.0, iZB = 0.0, v2 = 0.0;
@@ -405,9 +573,11 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
     const double sq = sqrt(om);
     const double p = gm1g * (Z * om - Dc * sq);
     const double sbz = SB * iZ;
+    double vl[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-        r.v[j] = (S[j] + sbz * B[j]) * iZB;
+        vl[j] = (S[j] + sbz * Bl[j]) * iZB;
+    raise<double>(m, vl, r.v);
     r.rho = Dc * sq;
     r.p = p;
     r.Z = Z;

@@ -1,15 +1,21 @@
-// echo_kernels.cu -- CUDA kernels of the GRMHD step (sm_103a).
+// echo_kernels.cuh -- CUDA kernel templates of the GRMHD step (sm_103a).
 //
 // One pass of the hot path per RK stage:
 //   fill(face B~) -> c2p (FP64 Newton) -> fill(primitives)
 //   -> faces<x,y,z> (MP5 + HLL) -> emf<x,y,z> (UCT-HLL) -> update (flux
-//   difference + CT curl + SSP-RK3 combination).
+//   difference + sources + CT curl + SSP-RK3 combination).
+// Templates over the metric kind MK (0 flat, 1 Kerr-Schild) and the storage
+// type R are instantiated in echo_kernels_flat.cu and echo_kernels_ks.cu;
+// metric-independent kernels live in echo_kernels_common.cu.
 // Reductions (CFL rate, conserved totals, div B~) use warp shuffles and a
 // fixed block tree, so results are bitwise reproducible run to run.
+#pragma once
+
 #include "echo_device.cuh"
 #include "echo_launch.h"
 
 namespace echo {
+
 
 // ------------------------------------------------------------------ helpers
 
@@ -35,51 +41,16 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
-// ------------------------------------------------------------------ ghost fill
-
-// Fill the ghost slab of axis d for a list of arrays.  Thread (s, t1, t2):
-// s in [0, 2 NG) selects the ghost layer (lower layers 0..NG-1, upper
-// n+NG..n+2NG-1), t1/t2 run over the full padded extent of the other axes.
-template <typename R>
-__global__ void k_fill(Geom g, int d, FillList<R> L)
-{
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t1 = blockIdx.y * blockDim.y + threadIdx.y;
-    const int t2 = blockIdx.z;
-    const int d1 = d == 0 ? 1 : 0;
-    const int d2 = d == 2 ? 1 : 2;
-    if (s >= 2 * NG || t1 >= g.np[d1] || t2 >= g.np[d2])
-        return;
-    const int id_d = s < NG ? s : g.n[d] + s;
-    int ijk[3];
-    ijk[d] = id_d;
-    ijk[d1] = t1;
-    ijk[d2] = t2;
-    const long long dst = gidx(g, ijk[0], ijk[1], ijk[2]);
-    const long long sd = d == 0 ? 1LL : (d == 1 ? g.px : g.pxy);
-    for (int a = 0; a < L.count; ++a) {
-        bool flip;
-        const int face = L.face[a] == d ? 1 : 0;
-        const int src = bc_src(id_d, g.n[d], face, g.bc[2 * d], g.bc[2 * d + 1], flip);
-        if (src == id_d)
-            continue;
-        R val = R(0);
-        if (src >= 0) {
-            val = L.a[a][dst + (long long)(src - id_d) * sd];
-            if (flip && L.comp[a] == d)
-                val = -val;
-        }
-        L.a[a][dst] = val;
-    }
-}
-
 // ------------------------------------------------------------------ c2p
 
 // Conservative-to-primitive inversion of every owned cell (FP64 Newton);
-// cell-centre B = mean of the two faces.  Optionally accumulates the CFL
-// rate max (atomicMax on the bits of a non-negative double, order
-// independent) and the Newton counters.
-template <typename R>
+// cell-centre B = mean of the two faces / sqrt(gamma).  Kerr-Schild runs with
+// floors: a failed inversion keeps the cell's previous primitives, density
+// and pressure are raised to the floors, and a cell changed that way has its
+// conserved state reset from the floored primitives (counted in floor_hits).
+// Optionally accumulates the CFL rate max (atomicMax on the bits of a
+// non-negative double, order independent) and the Newton counters.
+template <int MK, typename R>
 __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate)
 {
     const int i = NG + blockIdx.x * blockDim.x + threadIdx.x;
@@ -87,37 +58,71 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
     const int k = NG + blockIdx.z;
     const bool live = i < NG + g.n[0] && j < NG + g.n[1] && k < NG + g.n[2];
     double rate = 0.0;
-    unsigned long long its = 0, calls = 0, fails = 0;
+    unsigned long long its = 0, calls = 0, fails = 0, floors = 0;
     if (live) {
         const long long id = gidx(g, i, j, k);
+        double isg = 1.0, sg = 1.0;
+        const MetPt *mp = nullptr;
+        if constexpr (MK == 1) {
+            mp = &A.met.C[j * A.met.np0 + i];
+            isg = mp->isg;
+            sg = mp->sg;
+        }
         double B[3];
-        B[0] = 0.5 * ((double)A.U[5][id] + (double)A.U[5][id + 1]);
-        B[1] = 0.5 * ((double)A.U[6][id] + (double)A.U[6][id + g.px]);
-        B[2] = 0.5 * ((double)A.U[7][id] + (double)A.U[7][id + g.pxy]);
-        const double S[3] = {(double)A.U[1][id], (double)A.U[2][id], (double)A.U[3][id]};
+        B[0] = 0.5 * ((double)A.U[5][id] + (double)A.U[5][id + 1]) * isg;
+        B[1] = 0.5 * ((double)A.U[6][id] + (double)A.U[6][id + g.px]) * isg;
+        B[2] = 0.5 * ((double)A.U[7][id] + (double)A.U[7][id + g.pxy]) * isg;
+        const double S[3] = {(double)A.U[1][id] * isg, (double)A.U[2][id] * isg, (double)A.U[3][id] * isg};
         const double zg = guess_mode == 2 ? 0.0 : A.Z[id];
-        const C2PResult r = c2p_newton((double)A.U[0][id], S, (double)A.U[4][id], B, zg, ph.gm1g);
-        A.P[0][id] = (R)r.rho;
-        A.P[1][id] = (R)r.v[0];
-        A.P[2][id] = (R)r.v[1];
-        A.P[3][id] = (R)r.v[2];
-        A.P[4][id] = (R)r.p;
-        A.P[5][id] = (R)B[0];
-        A.P[6][id] = (R)B[1];
-        A.P[7][id] = (R)B[2];
-        A.Z[id] = r.Z;
+        C2PResult r;
+        if constexpr (MK == 1)
+            r = c2p_newton((double)A.U[0][id] * isg, S, (double)A.U[4][id] * isg, B, zg, ph.gm1g, MKS<double>(*mp));
+        else
+            r = c2p_newton((double)A.U[0][id], S, (double)A.U[4][id], B, zg, ph.gm1g, MFlat<double>());
         its = r.iters;
         calls = 1;
         fails = r.ok ? 0 : 1;
+        double P8[8] = {r.rho, r.v[0], r.v[1], r.v[2], r.p, B[0], B[1], B[2]};
+        double Z = r.Z;
+        if constexpr (MK == 1) {
+            if (A.met.use_floors) {
+                bool reset = !r.ok;
+                if (reset)
+                    for (int q = 0; q < 5; ++q)
+                        P8[q] = (double)A.P[q][id];
+                const double rf = A.met.floors[2 * i], pf = A.met.floors[2 * i + 1];
+                if (!ile(rf, P8[0])) {
+                    P8[0] = rf;
+                    reset = true;
+                }
+                if (!ile(pf, P8[4])) {
+                    P8[4] = pf;
+                    reset = true;
+                }
+                if (reset) {
+                    floors = 1;
+                    double C5[5];
+                    p2c_point(P8, ph.gr, MKS<double>(*mp), C5, Z);
+                    for (int q = 0; q < 5; ++q)
+                        A.U[q][id] = (R)(C5[q] * sg);
+                }
+            }
+        }
+        for (int q = 0; q < 8; ++q)
+            A.P[q][id] = (R)P8[q];
+        A.Z[id] = Z;
         if (want_rate) {
-            const double P[8] = {r.rho, r.v[0], r.v[1], r.v[2], r.p, B[0], B[1], B[2]};
-            rate = cfl_rate(P, ph.gamma, ph.gr, g.idx);
+            if constexpr (MK == 1)
+                rate = cfl_rate(P8, ph.gamma, ph.gr, g.idx, MKS<double>(*mp));
+            else
+                rate = cfl_rate(P8, ph.gamma, ph.gr, g.idx, MFlat<double>());
         }
     }
     // warp-aggregated counters
     its = warp_sum_u64(its);
     calls = warp_sum_u64(calls);
     fails = warp_sum_u64(fails);
+    floors = warp_sum_u64(floors);
     if (want_rate)
         rate = warp_max(rate);
     if ((threadIdx.x & 31) == 0) {
@@ -129,6 +134,8 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
             atomicAdd(&A.scal->c2p_fail, fails);
             atomicAdd(&A.scal->fail_since_check, fails);
         }
+        if (floors)
+            atomicAdd(&A.scal->floor_hits, floors);
         if (want_rate && rate > 0.0)
             atomicMax(&A.scal->rate_bits, (unsigned long long)__double_as_longlong(rate));
     }
@@ -218,7 +225,7 @@ __device__ __forceinline__ const R *pick7(const Arrays<R> &A, const int qs[7], i
     return p;
 }
 
-template <int D, typename R>
+template <int D, int MK, typename R>
 __global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
 {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
@@ -279,19 +286,48 @@ __global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
                 Rv[m] = lsm.res[w][lane][2 * m + 1];
         }
     }
+    // face metric (x1-faces: F1, x2-faces: F2, x3-faces: the cell-centre table)
+    const MetPt *mp = nullptr;
+    T isgf = T(1);
+    if constexpr (MK == 1) {
+        const int ti = ijk[1] * A.met.np0 + ijk[0];
+        mp = D == 0 ? &A.met.F1[ti] : (D == 1 ? &A.met.F2[ti] : &A.met.C[ti]);
+        if (!(mp->sg > 0.0)) {
+            // polar-axis face: zero area, no flux
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+                A.F[D][q][id] = T(0);
+            A.ap[D][id] = T(0);
+            A.am[D][id] = T(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                A.fv[D][q][id] = T(0);
+            return;
+        }
+        isgf = (T)mp->isg;
+    }
     T PL[8], PR[8];
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
         PL[qs[m]] = Lv[m];
         PR[qs[m]] = Rv[m];
     }
-    const T Bn = A.U[5 + D][id];
+    const T Bn = A.U[5 + D][id] * isgf;
     PL[5 + D] = Bn;
     PR[5 + D] = Bn;
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
         T *Ps = side == 0 ? PL : PR;
-        const T v2 = Ps[1] * Ps[1] + Ps[2] * Ps[2] + Ps[3] * Ps[3];
+        T v2;
+        if constexpr (MK == 1) {
+            const MKS<T> m(*mp);
+            const T vv[3] = {Ps[1], Ps[2], Ps[3]};
+            T vl[3];
+            lower<T>(m, vv, vl);
+            v2 = vl[0] * vv[0] + vl[1] * vv[1] + vl[2] * vv[2];
+        } else {
+            v2 = Ps[1] * Ps[1] + Ps[2] * Ps[2] + Ps[3] * Ps[3];
+        }
         if (!is_pos(Ps[0]) || !is_pos(Ps[4]) || !ilt(v2, T(1))) {
             const long long c = id + (side == 0 ? -sd : 0);
 #pragma unroll
@@ -300,8 +336,15 @@ __global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
         }
     }
     T FL[5], UL[5], FR[5], UR[5], lpL, lmL, lpR, lmR;
-    state_flux<D>(PL, (T)ph.gamma, (T)ph.gr, FL, UL, lpL, lmL);
-    state_flux<D>(PR, (T)ph.gamma, (T)ph.gr, FR, UR, lpR, lmR);
+    if constexpr (MK == 1) {
+        const MKS<T> m(*mp);
+        state_flux<D>(PL, (T)ph.gamma, (T)ph.gr, m, FL, UL, lpL, lmL);
+        state_flux<D>(PR, (T)ph.gamma, (T)ph.gr, m, FR, UR, lpR, lmR);
+    } else {
+        const MFlat<T> m;
+        state_flux<D>(PL, (T)ph.gamma, (T)ph.gr, m, FL, UL, lpL, lmL);
+        state_flux<D>(PR, (T)ph.gamma, (T)ph.gr, m, FR, UR, lpR, lmR);
+    }
     const T ap = imax(T(0), imax(lpL, lpR));
     const T am = imax(T(0), imax(-lmL, -lmR));
     const T ssum = ap + am;
@@ -354,7 +397,7 @@ __device__ __forceinline__ void emf_pick(const EmfSrc<R> &S, int m, const R *&p,
         }
 }
 
-template <int E, typename R>
+template <int E, int MK, typename R>
 __global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
 {
     constexpr int a = (E + 1) % 3, b = (E + 2) % 3;
@@ -364,11 +407,13 @@ __global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = t < tot;
     long long id;
+    int ei, ej;
     {
         const long long tt = live ? t : 0;
-        const int i = (int)(tt % cnt[0]);
+        ei = NG + (int)(tt % cnt[0]);
         const long long r = tt / cnt[0];
-        id = gidx(g, NG + i, NG + (int)(r % cnt[1]), NG + (int)(r / cnt[1]));
+        ej = NG + (int)(r % cnt[1]);
+        id = gidx(g, ei, ej, NG + (int)(r / cnt[1]));
     }
     const long long sa = a == 0 ? 1LL : (a == 1 ? g.px : g.pxy);
     const long long sb = b == 0 ? 1LL : (b == 1 ? g.px : g.pxy);
@@ -431,12 +476,27 @@ __global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
     const T ama = imax(A.am[a][id - sb], A.am[a][id]);
     const T apb = imax(A.ap[b][id - sa], A.ap[b][id]);
     const T amb = imax(A.am[b][id - sa], A.am[b][id]);
+    // transport velocity alpha v - beta at the edge (E_x1 edges sit at x2-face
+    // positions of the (x1, x2) plane, E_x2 edges at x1-face positions, E_x3
+    // edges at the corners)
+    T al = T(1), bea = T(0), beb = T(0);
+    if constexpr (MK == 1) {
+        const int ti = ej * A.met.np0 + ei;
+        const MetPt &mp = E == 0 ? A.met.F2[ti] : (E == 1 ? A.met.F1[ti] : A.met.K[ti]);
+        al = (T)mp.al;
+        bea = a == 0 ? (T)mp.b1 : T(0);
+        beb = b == 0 ? (T)mp.b1 : T(0);
+    }
     T Est[2][2];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
-            Est[s][u] = -(va[s][u] * Bb[s] - vb[s][u] * Ba[u]);
+        for (int u = 0; u < 2; ++u) {
+            if constexpr (MK == 1)
+                Est[s][u] = -((al * va[s][u] - bea) * Bb[s] - (al * vb[s][u] - beb) * Ba[u]);
+            else
+                Est[s][u] = -(va[s][u] * Bb[s] - vb[s][u] * Ba[u]);
+        }
     const T sA = apa + ama, sB = apb + amb;
     T wLL, wLR, wRL, wRR;
     if (is_pos(sA) && is_pos(sB)) {
@@ -454,6 +514,68 @@ __global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
                  + da * (Bb[1] - Bb[0]) - db * (Ba[1] - Ba[0]);
 }
 
+// ------------------------------------------------------------------ sources
+
+// Geometric sources of the Valencia form on the stationary Kerr-Schild metric
+// at a cell centre, times sqrt(gamma) (only beta^1 is non-zero and nothing
+// depends on x3):
+//   S(S_i) = 1/2 alpha W^jk d_i gamma_jk + S_1 d_i beta^1 - U d_i alpha     (i = 1, 2)
+//   S(tau) = 1/2 beta^1 W^ik d_1 gamma_ik + W_1^j d_j beta^1 - S^j d_j alpha
+// with W^jk = (rho h + b^2) W^2 v^j v^k + (p + b^2/2) gamma^jk - b^j b^k.
+template <typename T>
+__device__ __forceinline__ void ks_sources(const T P[8], T gr, const MetPt &mp, const MetDer &md, T src[5])
+{
+    const MKS<T> m(mp);
+    const T v[3] = {P[1], P[2], P[3]}, B[3] = {P[5], P[6], P[7]};
+    T vl[3], Bl[3];
+    lower<T>(m, v, vl);
+    lower<T>(m, B, Bl);
+    const T p = P[4];
+    const T v2 = vl[0] * v[0] + vl[1] * v[1] + vl[2] * v[2];
+    const T B2 = Bl[0] * B[0] + Bl[1] * B[1] + Bl[2] * B[2];
+    const T vB = vl[0] * B[0] + vl[1] * B[1] + vl[2] * B[2];
+    const T iW2 = T(1) - v2;
+    const T W = rsqrt(iW2);
+    const T iW = iW2 * W;
+    const T W2 = W * W;
+    const T rhoh = P[0] + gr * p;
+    const T b2 = B2 * iW2 + vB * vB;
+    const T Zw = rhoh * W2;
+    const T ZB = Zw + B2;
+    T bu[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        bu[c] = B[c] * iW + W * vB * v[c];
+    const T hw = (rhoh + b2) * W2;
+    const T pt = p + T(0.5) * b2;
+    const T W11 = hw * v[0] * v[0] + pt * m.i11 - bu[0] * bu[0];
+    const T W13 = hw * v[0] * v[2] + pt * m.i13 - bu[0] * bu[2];
+    const T W22 = hw * v[1] * v[1] + pt * m.i22 - bu[1] * bu[1];
+    const T W33 = hw * v[2] * v[2] + pt * m.i33 - bu[2] * bu[2];
+    const T W12 = hw * v[0] * v[1] - bu[0] * bu[1];
+    const T W32 = hw * v[2] * v[1] - bu[2] * bu[1];
+    const T Sl[3] = {ZB * vl[0] - vB * Bl[0], ZB * vl[1] - vB * Bl[1], ZB * vl[2] - vB * Bl[2]};
+    const T Uen = Zw - p + T(0.5) * (B2 + B2 * v2 - vB * vB);
+    T s[2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+        const T wdg = W11 * (T)md.dg11[d] + T(2) * W13 * (T)md.dg13[d] + W22 * (T)md.dg22[d] + W33 * (T)md.dg33[d];
+        s[d] = T(0.5) * m.al * wdg + Sl[0] * (T)md.db1[d] - Uen * (T)md.dal[d];
+    }
+    const T wdg1 = W11 * (T)md.dg11[0] + T(2) * W13 * (T)md.dg13[0] + W22 * (T)md.dg22[0] + W33 * (T)md.dg33[0];
+    const T W1_1 = m.g11 * W11 + m.g13 * W13;
+    const T W1_2 = m.g11 * W12 + m.g13 * W32;
+    const T Su1 = m.i11 * Sl[0] + m.i13 * Sl[2];
+    const T Su2 = m.i22 * Sl[1];
+    const T st = T(0.5) * m.b1 * wdg1 + W1_1 * (T)md.db1[0] + W1_2 * (T)md.db1[1] - Su1 * (T)md.dal[0]
+                 - Su2 * (T)md.dal[1];
+    src[0] = T(0);
+    src[1] = s[0] * m.sg;
+    src[2] = s[1] * m.sg;
+    src[3] = T(0);
+    src[4] = st * m.sg;
+}
+
 // ------------------------------------------------------------------ update
 
 // Flux difference + CT curl + SSP-RK3 stage combination (Shu & Osher 1988):
@@ -461,8 +583,8 @@ __global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
 //   stage 2: U = 1/3 U0 + 2/3 (U + dt L).
 // stage < 0: write L in host layout to Lout instead (faces NG..NG+n along
 // their axis; a face that is not evolved, e.g. on the polar axis, gets 0).
-template <typename R>
-__global__ void __launch_bounds__(256) k_update(Geom g, Arrays<R> A, int stage, double *Lout)
+template <int MK, typename R>
+__global__ void __launch_bounds__(256) k_update(Geom g, Phys ph, Arrays<R> A, int stage, double *Lout)
 {
     const int ti = blockIdx.x * blockDim.x + threadIdx.x;
     const int tj = blockIdx.y * blockDim.y + threadIdx.y;
@@ -478,12 +600,22 @@ __global__ void __launch_bounds__(256) k_update(Geom g, Arrays<R> A, int stage, 
     const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
 
     if (own[0] && own[1] && own[2]) {
+        R src[5] = {R(0), R(0), R(0), R(0), R(0)};
+        if constexpr (MK == 1) {
+            R P[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                P[q] = A.P[q][id];
+            const int ti = j * A.met.np0 + i;
+            ks_sources(P, (R)ph.gr, A.met.C[ti], A.met.dC[ti], src);
+        }
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             R r = R(0);
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 r -= (A.F[d][q][id + st[d]] - A.F[d][q][id]) * (R)g.idx[d];
+            r += src[q];
             if (stage < 0) {
                 Lout[q * N + ((long long)tk * g.n[1] + tj) * g.n[0] + ti] = (double)r;
             } else {
@@ -544,6 +676,79 @@ __global__ void __launch_bounds__(256) k_update(Geom g, Arrays<R> A, int stage, 
             }
         }
         off += (long long)e[0] * e[1] * e[2];
+    }
+}
+
+// Primitives (host layout, 5 arrays) + face B~ (already in U, ghosts
+// filled) -> conserved cell variables (times sqrt(gamma)) and Z = rho h W^2.
+template <int MK, typename R>
+__global__ void k_p2c(Geom g, Phys ph, const double *prims5, Arrays<R> A)
+{
+    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tj = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tk = blockIdx.z;
+    if (ti >= g.n[0] || tj >= g.n[1] || tk >= g.n[2])
+        return;
+    const long long id = gidx(g, NG + ti, NG + tj, NG + tk);
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long h = ((long long)tk * g.n[1] + tj) * g.n[0] + ti;
+    double isg = 1.0, sg = 1.0;
+    const MetPt *mp = nullptr;
+    if constexpr (MK == 1) {
+        mp = &A.met.C[(NG + tj) * A.met.np0 + NG + ti];
+        isg = mp->isg;
+        sg = mp->sg;
+    }
+    const double P8[8] = {prims5[h], prims5[N + h], prims5[2 * N + h], prims5[3 * N + h], prims5[4 * N + h],
+                          0.5 * ((double)A.U[5][id] + (double)A.U[5][id + 1]) * isg,
+                          0.5 * ((double)A.U[6][id] + (double)A.U[6][id + g.px]) * isg,
+                          0.5 * ((double)A.U[7][id] + (double)A.U[7][id + g.pxy]) * isg};
+    double C5[5], Z;
+    if constexpr (MK == 1)
+        p2c_point(P8, ph.gr, MKS<double>(*mp), C5, Z);
+    else
+        p2c_point(P8, ph.gr, MFlat<double>(), C5, Z);
+    for (int q = 0; q < 5; ++q)
+        A.U[q][id] = (R)(C5[q] * sg);
+    A.Z[id] = Z;
+}
+
+#ifdef ECHO_COMMON_KERNELS
+// ------------------------------------------------------------------ ghost fill
+
+// Fill the ghost slab of axis d for a list of arrays.  Thread (s, t1, t2):
+// s in [0, 2 NG) selects the ghost layer (lower layers 0..NG-1, upper
+// n+NG..n+2NG-1), t1/t2 run over the full padded extent of the other axes.
+template <typename R>
+__global__ void k_fill(Geom g, int d, FillList<R> L)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t1 = blockIdx.y * blockDim.y + threadIdx.y;
+    const int t2 = blockIdx.z;
+    const int d1 = d == 0 ? 1 : 0;
+    const int d2 = d == 2 ? 1 : 2;
+    if (s >= 2 * NG || t1 >= g.np[d1] || t2 >= g.np[d2])
+        return;
+    const int id_d = s < NG ? s : g.n[d] + s;
+    int ijk[3];
+    ijk[d] = id_d;
+    ijk[d1] = t1;
+    ijk[d2] = t2;
+    const long long dst = gidx(g, ijk[0], ijk[1], ijk[2]);
+    const long long sd = d == 0 ? 1LL : (d == 1 ? g.px : g.pxy);
+    for (int a = 0; a < L.count; ++a) {
+        bool flip;
+        const int face = L.face[a] == d ? 1 : 0;
+        const int src = bc_src(id_d, g.n[d], face, g.bc[2 * d], g.bc[2 * d + 1], flip);
+        if (src == id_d)
+            continue;
+        R val = R(0);
+        if (src >= 0) {
+            val = L.a[a][dst + (long long)(src - id_d) * sd];
+            if (flip && L.comp[a] == d)
+                val = -val;
+        }
+        L.a[a][dst] = val;
     }
 }
 
@@ -729,168 +934,6 @@ __global__ void k_unpack_z(Geom g, const double *src, Arrays<R> A)
     A.Z[id] = src ? src[h] : 0.0;
 }
 
-// Primitives (host layout, 5 arrays) + face B~ (already in U, ghosts
-// filled) -> conserved cell variables and Z = rho h W^2 (flat metric).
-template <typename R>
-__global__ void k_p2c(Geom g, Phys ph, const double *prims5, Arrays<R> A)
-{
-    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
-    const int tj = blockIdx.y * blockDim.y + threadIdx.y;
-    const int tk = blockIdx.z;
-    if (ti >= g.n[0] || tj >= g.n[1] || tk >= g.n[2])
-        return;
-    const long long id = gidx(g, NG + ti, NG + tj, NG + tk);
-    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-    const long long h = ((long long)tk * g.n[1] + tj) * g.n[0] + ti;
-    const double rho = prims5[h], v[3] = {prims5[N + h], prims5[2 * N + h], prims5[3 * N + h]};
-    const double p = prims5[4 * N + h];
-    const double B[3] = {0.5 * ((double)A.U[5][id] + (double)A.U[5][id + 1]),
-                         0.5 * ((double)A.U[6][id] + (double)A.U[6][id + g.px]),
-                         0.5 * ((double)A.U[7][id] + (double)A.U[7][id + g.pxy])};
-    const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    const double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-    const double vB = v[0] * B[0] + v[1] * B[1] + v[2] * B[2];
-    const double W2 = 1.0 / (1.0 - v2);
-    const double W = sqrt(W2);
-    const double Zw = (rho + ph.gr * p) * W2;
-    const double Dn = rho * W;
-    A.U[0][id] = (R)Dn;
-    for (int c = 0; c < 3; ++c)
-        A.U[1 + c][id] = (R)((Zw + B2) * v[c] - vB * B[c]);
-    A.U[4][id] = (R)(Zw - p + 0.5 * (B2 + B2 * v2 - vB * vB) - Dn);
-    A.Z[id] = Zw;
-}
-
-// ------------------------------------------------------------------ launchers
-
-namespace {
-inline dim3 grid3(int nx, int ny, int nz, dim3 blk)
-{
-    return dim3((unsigned)((nx + blk.x - 1) / blk.x), (unsigned)((ny + blk.y - 1) / blk.y), (unsigned)nz);
-}
-}  // namespace
-
-template <typename R>
-void launch_fill(const Geom &g, const FillList<R> &L, cudaStream_t s)
-{
-    for (int d = 0; d < 3; ++d) {
-        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
-        dim3 blk(8, 32, 1);
-        dim3 grd(1, (unsigned)((g.np[d1] + 31) / 32), (unsigned)g.np[d2]);
-        k_fill<R><<<grd, blk, 0, s>>>(g, d, L);
-    }
-}
-
-template <typename R>
-void launch_c2p(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mode, int want_rate, cudaStream_t s)
-{
-    dim3 blk(32, 4, 1);
-    k_c2p<R><<<grid3(g.n[0], g.n[1], g.n[2], blk), blk, 0, s>>>(g, ph, A, guess_mode, want_rate);
-}
-
-template <typename R>
-void launch_faces(const Geom &g, const Phys &ph, const Arrays<R> &A, int d, cudaStream_t s)
-{
-    long long cnt[3] = {g.np[0], g.np[1], g.np[2]};
-    cnt[d] = g.n[d] + 1;
-    const long long tot = cnt[0] * cnt[1] * cnt[2];
-    const unsigned blocks = (unsigned)((tot + 127) / 128);
-    if (d == 0)
-        k_faces<0, R><<<blocks, 128, 0, s>>>(g, ph, A);
-    else if (d == 1)
-        k_faces<1, R><<<blocks, 128, 0, s>>>(g, ph, A);
-    else
-        k_faces<2, R><<<blocks, 128, 0, s>>>(g, ph, A);
-}
-
-template <typename R>
-void launch_emf(const Geom &g, const Arrays<R> &A, int e, cudaStream_t s)
-{
-    long long cnt[3] = {g.n[0] + 1, g.n[1] + 1, g.n[2] + 1};
-    cnt[e] = g.n[e];
-    const long long tot = cnt[0] * cnt[1] * cnt[2];
-    const unsigned blocks = (unsigned)((tot + 127) / 128);
-    if (e == 0)
-        k_emf<0, R><<<blocks, 128, 0, s>>>(g, A);
-    else if (e == 1)
-        k_emf<1, R><<<blocks, 128, 0, s>>>(g, A);
-    else
-        k_emf<2, R><<<blocks, 128, 0, s>>>(g, A);
-}
-
-template <typename R>
-void launch_update(const Geom &g, const Arrays<R> &A, int stage, double *Lout, cudaStream_t s)
-{
-    dim3 blk(32, 8, 1);
-    k_update<R><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2] + 1, blk), blk, 0, s>>>(g, A, stage, Lout);
-}
-
-void launch_step_begin(DevScalars *sc, double dt_fixed, cudaStream_t s)
-{
-    k_step_begin<<<1, 1, 0, s>>>(sc, dt_fixed);
-}
-
-void launch_set_dt(DevScalars *sc, double cfl, int use_cfl, cudaStream_t s)
-{
-    k_set_dt<<<1, 1, 0, s>>>(sc, cfl, use_cfl);
-}
-
-template <typename R>
-void launch_totals(const Geom &g, const Arrays<R> &A, int nblk, cudaStream_t s)
-{
-    k_totals<R><<<nblk, 256, 0, s>>>(g, A);
-    k_totals_final<<<1, 256, 0, s>>>(A.scal, A.partials, nblk, g.dx[0] * g.dx[1] * g.dx[2]);
-}
-
-template <typename R>
-void launch_unpack_state(const Geom &g, const double *src, const Arrays<R> &A, int what, cudaStream_t s)
-{
-    dim3 blk(32, 8, 1);
-    k_unpack_state<R><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2] + 1, blk), blk, 0, s>>>(g, src, A, what);
-}
-
-template <typename R>
-void launch_pack_state(const Geom &g, const Arrays<R> &A, double *dst, cudaStream_t s)
-{
-    dim3 blk(32, 8, 1);
-    k_pack_state<R><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2] + 1, blk), blk, 0, s>>>(g, A, dst);
-}
-
-template <typename R>
-void launch_pack_cells(const Geom &g, const Arrays<R> &A, double *dst, int what, cudaStream_t s)
-{
-    dim3 blk(32, 8, 1);
-    k_pack_cells<R><<<grid3(g.n[0], g.n[1], g.n[2], blk), blk, 0, s>>>(g, A, dst, what);
-}
-
-template <typename R>
-void launch_unpack_z(const Geom &g, const double *src, const Arrays<R> &A, cudaStream_t s)
-{
-    dim3 blk(32, 8, 1);
-    k_unpack_z<R><<<grid3(g.n[0], g.n[1], g.n[2], blk), blk, 0, s>>>(g, src, A);
-}
-
-template <typename R>
-void launch_p2c(const Geom &g, const Phys &ph, const double *prims5, const Arrays<R> &A, cudaStream_t s)
-{
-    dim3 blk(32, 8, 1);
-    k_p2c<R><<<grid3(g.n[0], g.n[1], g.n[2], blk), blk, 0, s>>>(g, ph, prims5, A);
-}
-
-#define ECHO_INSTANTIATE(R)                                                                             \
-    template void launch_fill<R>(const Geom &, const FillList<R> &, cudaStream_t);                     \
-    template void launch_c2p<R>(const Geom &, const Phys &, const Arrays<R> &, int, int, cudaStream_t); \
-    template void launch_faces<R>(const Geom &, const Phys &, const Arrays<R> &, int, cudaStream_t);   \
-    template void launch_emf<R>(const Geom &, const Arrays<R> &, int, cudaStream_t);                   \
-    template void launch_update<R>(const Geom &, const Arrays<R> &, int, double *, cudaStream_t);      \
-    template void launch_totals<R>(const Geom &, const Arrays<R> &, int, cudaStream_t);                \
-    template void launch_unpack_state<R>(const Geom &, const double *, const Arrays<R> &, int, cudaStream_t); \
-    template void launch_pack_state<R>(const Geom &, const Arrays<R> &, double *, cudaStream_t);       \
-    template void launch_pack_cells<R>(const Geom &, const Arrays<R> &, double *, int, cudaStream_t);  \
-    template void launch_unpack_z<R>(const Geom &, const double *, const Arrays<R> &, cudaStream_t);   \
-    template void launch_p2c<R>(const Geom &, const Phys &, const double *, const Arrays<R> &, cudaStream_t);
-
-ECHO_INSTANTIATE(double)
-ECHO_INSTANTIATE(float)
+#endif  // ECHO_COMMON_KERNELS
 
 }  // namespace echo

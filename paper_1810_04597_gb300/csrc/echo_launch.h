@@ -23,14 +23,16 @@ struct FillList {
 
 template <typename R>
 void launch_fill(const Geom &g, const FillList<R> &L, cudaStream_t s);
-template <typename R>
+template <int MK, typename R>
 void launch_c2p(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mode, int want_rate, cudaStream_t s);
-template <typename R>
+template <int MK, typename R>
 void launch_faces(const Geom &g, const Phys &ph, const Arrays<R> &A, int d, cudaStream_t s);
-template <typename R>
+template <int MK, typename R>
 void launch_emf(const Geom &g, const Arrays<R> &A, int e, cudaStream_t s);
-template <typename R>
-void launch_update(const Geom &g, const Arrays<R> &A, int stage, double *Lout, cudaStream_t s);
+template <int MK, typename R>
+void launch_update(const Geom &g, const Phys &ph, const Arrays<R> &A, int stage, double *Lout, cudaStream_t s);
+template <int MK, typename R>
+void launch_p2c(const Geom &g, const Phys &ph, const double *prims5, const Arrays<R> &A, cudaStream_t s);
 template <typename R>
 void launch_totals(const Geom &g, const Arrays<R> &A, int nblk, cudaStream_t s);
 template <typename R>
@@ -41,10 +43,10 @@ template <typename R>
 void launch_pack_cells(const Geom &g, const Arrays<R> &A, double *dst, int what, cudaStream_t s);
 template <typename R>
 void launch_unpack_z(const Geom &g, const double *src, const Arrays<R> &A, cudaStream_t s);
-template <typename R>
-void launch_p2c(const Geom &g, const Phys &ph, const double *prims5, const Arrays<R> &A, cudaStream_t s);
-
 void launch_step_begin(DevScalars *sc, double dt_fixed, cudaStream_t s);
+struct MetTables;
+void launch_metric_tables(const Geom &g, double spin, const MetTables &T, double rho_floor, double rho_pow,
+                          double p_floor, double p_pow, cudaStream_t s);
 void launch_set_dt(DevScalars *sc, double cfl, int use_cfl, cudaStream_t s);
 
 }  // namespace echo

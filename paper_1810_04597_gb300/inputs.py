@@ -338,3 +338,154 @@ def alfven_wave_2d(n: int, t=0.0, rho=1.0, p=1.0, B0=1.0, eta=1.0, gamma=4.0 / 3
     bz = np.stack([Bzc, Bzc])                                          # (2, n, n)
     return Problem(name=f"alfven2d_{n}", n=nn, x0=(0.0, 0.0, 0.0), dx=dx, gamma=gamma, prims=prims,
                    bface=pack_faces(bx, by, bz))
+
+
+# ------------------------------------------------------------------ torus
+
+def _bl_equatorial(r, th, a):
+    """Boyer-Lindquist g_tt, g_tphi, g_phiphi and Delta (M = 1)."""
+    s2 = np.sin(th) ** 2
+    sig = r * r + a * a * np.cos(th) ** 2
+    dl = r * r - 2.0 * r + a * a
+    A = (r * r + a * a) ** 2 - dl * a * a * s2
+    return -(1.0 - 2.0 * r / sig), -2.0 * a * r * s2 / sig, A * s2 / sig, dl, sig, A, s2
+
+
+def _fm_lnh_raw(r, th, a, ell):
+    """ln(u^t) - ell * Omega for circular flow with u^t u_phi = ell.
+
+    For u = u^t (1, 0, 0, Omega), the Euler equation of a barotropic fluid
+    gives d ln h = (1/2) d g_{mn} u^m u^n = d ln u^t - ell dOmega, so
+    ln h = ln u^t - ell Omega + const (Fishbone & Moncrief 1976).
+    (u^t)^2 = X solves |D| X^2 - g_phiphi X - ell^2 = 0 with
+    D = g_tt g_phiphi - g_tphi^2 = -Delta sin^2, and
+    Omega = (ell / X - g_tphi) / g_phiphi."""
+    gtt, gtp, gpp, dl, sig, A, s2 = _bl_equatorial(r, th, a)
+    absD = dl * s2
+    with np.errstate(divide="ignore", invalid="ignore"):
+        X = (gpp + np.sqrt(gpp * gpp + 4.0 * absD * ell * ell)) / (2.0 * absD)
+        om = (ell / X - gtp) / gpp
+        return 0.5 * np.log(X) - ell * om, X, om
+
+
+def fm_angular_momentum(a, r_max):
+    """ell = u^t u_phi that puts the pressure maximum at (r_max, pi/2):
+    the root of d(ln h)/dr = 0 there (found numerically)."""
+    from scipy.optimize import brentq
+
+    def dlnh(ell):
+        h = 1e-5 * r_max
+        return (_fm_lnh_raw(r_max + h, np.pi / 2, a, ell)[0]
+                - _fm_lnh_raw(r_max - h, np.pi / 2, a, ell)[0]) / (2 * h)
+
+    return brentq(dlnh, 1.0, 20.0, xtol=1e-14)
+
+
+def ks_metric_arrays(x1, th, a):
+    """Kerr-Schild lapse, shift^1 and spatial metric in (ln r, theta, phi),
+    used here only to lay out the initial data (velocities, field scale)."""
+    r = np.exp(x1)
+    sig = r * r + a * a * np.cos(th) ** 2
+    z = 2.0 * r / sig
+    s2 = np.sin(th) ** 2
+    alpha = 1.0 / np.sqrt(1.0 + z)
+    beta1 = z / (1.0 + z) / r
+    g11 = (1.0 + z) * r * r
+    g13 = -a * (1.0 + z) * s2 * r
+    g22 = sig
+    g33 = s2 * (sig + a * a * (1.0 + z) * s2)
+    return alpha, beta1, g11, g13, g22, g33
+
+
+def fm_torus(n=(64, 32, 32), spin=0.9, beta=100.0, r_in=6.0, r_max=12.0, r_out=50.0, noise=0.02,
+             seed=None, steps=10, with_field=True, rho_floor=1e-5, p_floor=1e-7) -> Problem:
+    """Fishbone-Moncrief constant-ell torus on Kerr-Schild (ln r, theta, phi).
+
+    Grid: ln r uniform on [ln(1.2 r_h), ln r_out], theta uniform on (0, pi),
+    phi uniform on [0, 2 pi); outflow in r, polar-axis reflection in theta,
+    periodic in phi.  Inside the torus (h > 1): rho = ((h - 1)/(h_max - 1))^(1/(G-1))
+    (max 1), p = kappa rho^G with kappa = (h_max - 1)(G-1)/G, times (1 + noise u),
+    u ~ U[-1, 1] per cell.  Velocity: the torus orbits with u^r = u^th = 0 in
+    Boyer-Lindquist coordinates; those contravariant components are the same
+    in Kerr-Schild, and the Eulerian 3-velocity is v^i = u^i / (alpha u^t) +
+    beta^i / alpha.  Outside: atmosphere at the floors rho_floor r^-3/2,
+    p_floor r^-5/2, at rest for the Eulerian observer.  Field: poloidal loops
+    from A_phi = max(rho/rho_max - 0.2, 0) at the (r, theta) corners, discrete
+    curl, scaled so that max p / max(b^2/2) = beta over the torus.  The
+    atmosphere starts at twice the floors."""
+    seed = SEED_BASE + 3 if seed is None else seed
+    rng = np.random.default_rng(seed)
+    gam = 4.0 / 3.0
+    a = float(spin)
+    nr, nt, nph = (int(v) for v in n)
+    rh = 1.0 + np.sqrt(1.0 - a * a)
+    x0 = (np.log(1.2 * rh), 0.0, 0.0)
+    dx = ((np.log(r_out) - x0[0]) / nr, np.pi / nt, 2.0 * np.pi / nph)
+    ell = fm_angular_momentum(a, r_max)
+    lnh_in = _fm_lnh_raw(r_in, np.pi / 2, a, ell)[0]
+    lnh_mx = _fm_lnh_raw(r_max, np.pi / 2, a, ell)[0]
+    hmax = np.exp(lnh_mx - lnh_in)
+    kappa = (hmax - 1.0) * (gam - 1.0) / gam
+
+    def torus_rho(x1, th):
+        r = np.exp(x1)
+        lnh, X, om = _fm_lnh_raw(r, th, a, ell)
+        h = np.nan_to_num(np.exp(lnh - lnh_in), nan=0.0)
+        inside = (h > 1.0) & (r >= r_in)
+        rho = np.where(inside, ((np.maximum(h, 1.0) - 1.0) / (hmax - 1.0)) ** (1.0 / (gam - 1.0)), 0.0)
+        return rho, inside, X, om
+
+    x1c = x0[0] + (np.arange(nr) + 0.5) * dx[0]
+    thc = (np.arange(nt) + 0.5) * dx[1]
+    X1, TH = np.meshgrid(x1c, thc, indexing="xy")        # (nt, nr)
+    rho_t, inside, X, om = torus_rho(X1, TH)
+    r = np.exp(X1)
+    rho_atm = 2.0 * rho_floor * r ** -1.5     # atmosphere starts above the floors
+    p_atm = 2.0 * p_floor * r ** -2.5
+    alpha, beta1, g11, g13, g22, g33 = ks_metric_arrays(X1, TH, a)
+    ut = np.sqrt(X)
+    W = alpha * ut
+    v1 = np.where(inside, beta1 / alpha, 0.0)   # u^1 = 0 in the torus
+    v3 = np.where(inside, om * ut / W, 0.0)
+    rho2 = np.where(inside, np.maximum(rho_t, rho_atm), rho_atm)
+    p2 = np.where(inside, np.maximum(kappa * rho_t ** gam, p_atm), p_atm)
+    prims = np.zeros((5, nph, nt, nr))
+    prims[0] = rho2[None]
+    prims[1] = v1[None]
+    prims[3] = v3[None]
+    pn = np.broadcast_to(p2[None], (nph, nt, nr)).copy()
+    pn *= np.where(inside[None], 1.0 + noise * rng.uniform(-1.0, 1.0, size=(nph, nt, nr)), 1.0)
+    prims[4] = pn
+
+    bx = np.zeros((nph, nt, nr + 1))
+    by = np.zeros((nph, nt + 1, nr))
+    bz = np.zeros((nph + 1, nt, nr))
+    if with_field:
+        x1f = x0[0] + np.arange(nr + 1) * dx[0]
+        thf = np.arange(nt + 1) * dx[1]
+        XF, TF = np.meshgrid(x1f, thf, indexing="xy")   # (nt+1, nr+1) corners
+        rc, _, _, _ = torus_rho(XF, TF)
+        Aph = np.maximum(rc - 0.2, 0.0)
+        # B~^1 = d_theta A_phi, B~^2 = -d_r A_phi (A_r = A_theta = 0)
+        b1 = (Aph[1:, :] - Aph[:-1, :]) / dx[1]           # (nt, nr+1)
+        b2 = -(Aph[:, 1:] - Aph[:, :-1]) / dx[0]          # (nt+1, nr)
+        b2[0, :] = 0.0
+        b2[-1, :] = 0.0
+        # field scale from the cell-centre field (flat-index average of faces)
+        sqrtg = np.sqrt((g11 * g33 - g13 * g13) * g22)
+        B1 = 0.5 * (b1[:, 1:] + b1[:, :-1]) / sqrtg
+        B2 = 0.5 * (b2[1:, :] + b2[:-1, :]) / sqrtg
+        vl1 = g11 * v1 + g13 * v3
+        vl3 = g13 * v1 + g33 * v3
+        Bsq = g11 * B1 * B1 + g22 * B2 * B2
+        vB = vl1 * B1
+        b2c = Bsq / (W * W) + vB * vB
+        pm = np.max(np.where(inside, b2c, 0.0)) / 2.0
+        scale = np.sqrt(np.max(np.where(inside, p2, 0.0)) / (beta * pm)) if pm > 0 else 0.0
+        bx[:] = (b1 * scale)[None]
+        by[:] = (b2 * scale)[None]
+        del vl3
+    return Problem(name=f"fm_torus_{nr}x{nt}x{nph}", n=(nr, nt, nph), x0=x0, dx=dx,
+                   bc=(OUTFLOW, OUTFLOW, AXIS, AXIS, PERIODIC, PERIODIC), metric=1, spin=a, gamma=gam,
+                   floors=True, rho_floor=rho_floor, rho_floor_pow=-1.5, p_floor=p_floor, p_floor_pow=-2.5,
+                   steps=steps, seed=seed, prims=prims, bface=pack_faces(bx, by, bz))

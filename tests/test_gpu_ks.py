@@ -1,0 +1,76 @@
+"""Kerr-Schild torus on the GPU (metric tables, sources, floors, outflow and
+polar-axis boundaries) against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from paper_1810_04597_gb300 import inputs
+from gpu_util import FIELDS, fields, gpu_run, l1_rel, max_rel, oracle_run, per_field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def test_ks_p2c_and_c2p(orc):
+    from paper_1810_04597_gb300.echo import Solver
+    prob = inputs.fm_torus((48, 24, 8))
+    s = Solver(prob)
+    s.set_prims()
+    st_g = s.get_state()
+    cfg = orc.make_cfg(prob)
+    st_o, Z_o = orc.p2c(cfg, prob.prims, prob.bface)
+    errs = per_field(orc, st_g, st_o, prob.n)
+    assert max(errs.values()) <= 1e-13, errs
+    stats = s.c2p(guess_mode=2)
+    P_g = s.get_prims()
+    P_o, _, ostats, _ = orc.c2p(cfg, st_o, None)
+    # velocity and field components are compared against the largest
+    # component (v^theta, B^phi vanish in the initial torus)
+    vs = np.max(np.abs(P_o[1:4]))
+    bs = np.max(np.abs(P_o[5:8]))
+    for q in range(8):
+        den = vs if 1 <= q <= 3 else (bs if q >= 5 else np.max(np.abs(P_o[q])))
+        assert np.max(np.abs(P_g[q] - P_o[q])) <= 1e-12 * den, q
+    assert stats["floor_hits"] == ostats["floors"]
+
+
+def test_ks_rhs_parity(orc):
+    from paper_1810_04597_gb300.echo import Solver
+    prob = inputs.fm_torus((48, 24, 8), seed=5)
+    s = Solver(prob)
+    s.set_prims()
+    L_g = s.rhs()
+    cfg = orc.make_cfg(prob)
+    st, Z = orc.p2c(cfg, prob.prims, prob.bface)
+    L_o, _, _ = orc.rhs(cfg, st, Z)
+    errs = per_field(orc, L_g, L_o, prob.n)
+    assert max(errs.values()) <= 1e-11, errs
+
+
+@pytest.mark.parametrize("spin,field", [(0.9, True), (0.0, False)])
+def test_ks_ten_step_parity(orc, spin, field):
+    prob = inputs.fm_torus((64, 32, 16), spin=spin, with_field=field)
+    st_g, s = gpu_run(prob, 10)
+    st_o, _, dts, ostats = oracle_run(orc, prob, 10)
+    errs = per_field(orc, st_g, st_o, prob.n)
+    t = s.reduce()
+    diag = dict(errs=errs, gpu=(t["c2p_fail"], t["floor_hits"]), oracle=(ostats["fails"], ostats["floors"]))
+    assert max(errs.values()) <= 1e-11, diag
+    assert t["c2p_calls"] > 0
+    # the polar-axis faces hold B~^theta = 0
+    _, _, by, _ = orc.split_state(st_g, prob.n)
+    assert np.all(by[:, 0, :] == 0.0) and np.all(by[:, -1, :] == 0.0)
+
+
+def test_ks_fp32_bulk(orc):
+    prob = inputs.fm_torus((64, 32, 16))
+    st_g, s = gpu_run(prob, 10, precision=32)
+    st_o, _, _, _ = oracle_run(orc, prob, 10)
+    l1 = per_field(orc, st_g, st_o, prob.n, metric=l1_rel)
+    assert l1["D"] <= 1e-5 and l1["tau"] <= 1e-5, l1
+    assert max(l1.values()) <= 1e-4, l1
