@@ -92,6 +92,7 @@ typedef struct {
     long long c2p_fail;   /* failed inversions since bind */
     long long floor_hits; /* cells reset by floors since bind */
     long long fallback_faces; /* reserved (first-order face fallbacks) */
+    long long mlp_fallback;   /* network guesses that needed the previous-Z restart */
 } echo_totals;
 
 /* Create a context.  precision: 64 (FP64 everywhere) or 32 (FP32 storage
@@ -136,8 +137,9 @@ int echo_get_prims(echo_ctx *ctx, double *prims8, int on_device);
 int echo_get_z(echo_ctx *ctx, double *Z, int on_device);
 
 /* Conservative-to-primitive inversion of the current state on every owned
- * cell.  guess_mode: 0 = the stored Z of the cell (previous stage), 2 = cold
- * guess (Z = 0, replaced by the admissibility rule).  If stats is non-NULL
+ * cell.  guess_mode: 0 = the stored Z of the cell (previous stage), 1 = the
+ * c2p-guess network (see below), 2 = cold guess (Z = 0, replaced by the
+ * admissibility rule).  If stats is non-NULL
  * the call synchronises and fills the counters and dt_cfl of stats (the
  * other fields are left untouched) and returns ECHO_EC2P if any cell failed. */
 int echo_c2p(echo_ctx *ctx, int guess_mode, echo_totals *stats);
@@ -155,6 +157,73 @@ int echo_step(echo_ctx *ctx, double dt);
  * Synchronises.  Returns ECHO_EC2P if an inversion failed since the last
  * call and floors are off. */
 int echo_reduce(echo_ctx *ctx, echo_totals *out);
+
+/* ---- c2p-guess network (a learned initial guess for the Newton solve) ----
+ * A 9 -> 64 -> 64 -> 3 tanh network, FP32, maps scale-free features of the
+ * conserved state and metric (log(tau/D), log(1+S^2/D^2), log(1+B^2/D),
+ * (S.B)^2/(S^2 B^2), alpha, log sqrt(gamma), beta_i beta^i,
+ * tr(gamma^ij)/3, log(D)/10) to log W, log(p/D) and the predicted log10
+ * relative error of its guess Z0 = D W (1 + G/(G-1) (p/D) W).  The Newton
+ * solve in FP64 stays the judge: from the network guess it may take at most
+ * 8 iterations, else it restarts from the previous-stage Z (counted).
+ * A network "state" is ECHO_MLP_STATE floats of device memory: parameters
+ * and standardisation block (ECHO_MLP_BLOCK floats: W1 64x9, b1, W2 64x64,
+ * b2, W3 3x64, b3, feature mean/std (9+9), target mean/std (3+3)), then
+ * the Adam moments m and v (ECHO_MLP_BLOCK floats each).  Datasets are row
+ * major: features X (n x 9) and targets Y (n x 3: log W, log(p/D), log(Z/D)),
+ * FP32 device arrays.  All buffers are caller-owned device memory. */
+#define ECHO_MLP_NPARAM 4995
+#define ECHO_MLP_BLOCK 5024
+#define ECHO_MLP_STATE (3 * ECHO_MLP_BLOCK)
+
+/* Glorot-uniform weights (counter-based generator seeded by seed), zero
+ * biases and moments, identity standardisation. */
+int echo_mlp_init(float *dev_state, unsigned long long seed, void *cuda_stream);
+
+/* Bytes of work buffer needed by echo_mlp_train/echo_mlp_grad/
+ * echo_mlp_normalize for a batch size. */
+size_t echo_mlp_work_bytes(int batch);
+
+/* Standardisation of features and of the first two targets from n rows
+ * (mean, std; constant columns keep std 1). */
+int echo_mlp_normalize(float *dev_state, const float *X, const float *Y, long long n, void *dev_work,
+                       size_t work_bytes, void *cuda_stream);
+
+/* nsteps Adam steps (lr; b1 0.9, b2 0.999, eps 1e-8) on minibatches of
+ * `batch` consecutive rows, step t (from step0) starting at row
+ * (t * batch) mod n.  losses (device, may be NULL) receives each step's
+ * mean batch loss. */
+int echo_mlp_train(float *dev_state, const float *X, const float *Y, long long n, int batch, int nsteps,
+                   long long step0, float lr, double gamma, void *dev_work, size_t work_bytes, float *losses,
+                   void *cuda_stream);
+
+/* Gradient (ECHO_MLP_NPARAM floats, device) and mean loss (device float, may
+ * be NULL) of the batch loss over rows row0 .. row0+batch-1 (mod n). */
+int echo_mlp_grad(const float *dev_state, const float *X, const float *Y, long long n, long long row0, int batch,
+                  double gamma, float *dev_grad, float *dev_loss, void *dev_work, size_t work_bytes,
+                  void *cuda_stream);
+
+/* Standardised network outputs (n x 3, device) of n feature rows. */
+int echo_mlp_forward(const float *dev_state, const float *X, long long n, float *out, void *cuda_stream);
+
+/* Training rows from the current state: runs a c2p (previous-stage guess),
+ * then writes for every owned cell its features and targets at row
+ * offset + perm(cell) * stride of X/Y (perm: a fixed permutation of the
+ * cells).  offset + (cells-1) * stride must be below capacity (rows). */
+int echo_mlp_dataset(echo_ctx *ctx, float *X, float *Y, long long capacity, long long offset, long long stride);
+
+/* Copy a trained network (the first ECHO_MLP_BLOCK floats of a state) into
+ * the context. */
+int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
+
+/* Newton guess used by echo_step/echo_rhs/echo_reduce: 0 previous-stage Z
+ * (default), 1 network (requires echo_mlp_load). */
+int echo_set_c2p_guess(echo_ctx *ctx, int mode);
+
+/* Copy the cumulative counters (c2p_iters, c2p_calls, c2p_fail, floor_hits,
+ * mlp_fallback) to *out without running anything; other fields untouched.
+ * Synchronises. */
+int echo_counters(echo_ctx *ctx, echo_totals *out);
 
 /* Kernel classes timed by the profiling facility below. */
 #define ECHO_K_FILL_FACES 0

@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "echo_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "mlp_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libecho_oracle.so")
 _lock = threading.Lock()
@@ -53,11 +54,11 @@ def build(force: bool = False) -> str:
     with _lock:
         os.makedirs(_BUILD, exist_ok=True)
         if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+                and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS)):
             return _LIB
         tmp = _LIB + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-fopenmp", "-std=c11", "-Wall", "-Wno-unused-variable", "-o", tmp, _SRC, "-lm"]
+               "-fopenmp", "-std=c11", "-Wall", "-Wno-unused-variable", "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True, capture_output=True, text=True)
         os.replace(tmp, _LIB)
         return _LIB
@@ -97,6 +98,12 @@ def lib():
         L.oracle_steps.restype = i
         L.oracle_reduce.argtypes = [pc, pd, pd]
         L.oracle_reduce.restype = i
+        L.oracle_mlp_nparam.restype = i
+        L.oracle_mlp_forward.argtypes = [pd, pd, i, pd]
+        L.oracle_mlp_targets.argtypes = [pd, pd, pd, i, d, pd]
+        L.oracle_mlp_loss_grad.argtypes = [pd, pd, pd, i, d, d, pd, pd]
+        L.oracle_mlp_loss_grad.restype = d
+        L.oracle_mlp_adam.argtypes = [pd, pd, pd, pd, i, d, d, d, d]
         _lib = L
     return _lib
 
@@ -287,3 +294,45 @@ def split_state(state: np.ndarray, n):
     o += nz * (ny + 1) * nx
     bz = state[o:o + (nz + 1) * ny * nx].reshape(nz + 1, ny, nx)
     return cells, bx, by, bz
+
+
+# ---------------------------------------------------------------- c2p-guess network
+
+MLP_NPARAM = 4995
+MLP_NNORM = 24
+
+
+def mlp_forward(params, x):
+    """Raw outputs (n, 3) of the network; params = parameters + norm block."""
+    params = _f64(params)
+    x = _f64(x).reshape(-1, 9)
+    out = np.zeros((x.shape[0], 3))
+    lib().oracle_mlp_forward(_dp(params), _dp(x), x.shape[0], _dp(out))
+    return out
+
+
+def mlp_targets(params, x, y, gamma=4.0 / 3.0):
+    params = _f64(params)
+    x = _f64(x).reshape(-1, 9)
+    y = _f64(y).reshape(-1, 3)
+    t = np.zeros_like(y)
+    lib().oracle_mlp_targets(_dp(params), _dp(x), _dp(y), x.shape[0], float(gamma), _dp(t))
+    return t
+
+
+def mlp_loss_grad(params, x, y, gamma=4.0 / 3.0, w2=0.1, t_fixed=None):
+    """(mean loss, gradient over the 4995 parameters)."""
+    params = _f64(params)
+    x = _f64(x).reshape(-1, 9)
+    y = _f64(y).reshape(-1, 3)
+    g = np.zeros(MLP_NPARAM)
+    tf = _dp(_f64(t_fixed)) if t_fixed is not None else None
+    loss = lib().oracle_mlp_loss_grad(_dp(params), _dp(x), _dp(y), x.shape[0], float(gamma), float(w2),
+                                      _dp(g), tf)
+    return loss, g
+
+
+def mlp_adam(params, m, v, g, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step in place on float64 arrays."""
+    lib().oracle_mlp_adam(_dp(params), _dp(m), _dp(v), _dp(_f64(g)), int(t), float(lr), float(b1),
+                          float(b2), float(eps))

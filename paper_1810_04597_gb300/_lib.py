@@ -61,13 +61,13 @@ class echo_totals(ctypes.Structure):
                 ("mom", ctypes.c_double * 3), ("max_divb", ctypes.c_double),
                 ("c2p_iters", ctypes.c_longlong), ("c2p_calls", ctypes.c_longlong),
                 ("c2p_fail", ctypes.c_longlong), ("floor_hits", ctypes.c_longlong),
-                ("fallback_faces", ctypes.c_longlong)]
+                ("fallback_faces", ctypes.c_longlong), ("mlp_fallback", ctypes.c_longlong)]
 
     def as_dict(self):
         return dict(dt_cfl=self.dt_cfl, mass=self.mass, energy=self.energy, mom=list(self.mom),
                     max_divb=self.max_divb, c2p_iters=self.c2p_iters, c2p_calls=self.c2p_calls,
                     c2p_fail=self.c2p_fail, floor_hits=self.floor_hits,
-                    fallback_faces=self.fallback_faces)
+                    fallback_faces=self.fallback_faces, mlp_fallback=self.mlp_fallback)
 
 
 # Exported entry points and their C signatures.
@@ -92,6 +92,19 @@ _SIGS = {
     "echo_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "echo_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "echo_counters": (ctypes.c_int, [_P, ctypes.POINTER(echo_totals)]),
+    "echo_mlp_init": (ctypes.c_int, [_P, ctypes.c_ulonglong, _P]),
+    "echo_mlp_work_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "echo_mlp_normalize": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P, ctypes.c_size_t, _P]),
+    "echo_mlp_train": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_longlong, ctypes.c_float, ctypes.c_double, _P, ctypes.c_size_t,
+                                      _P, _P]),
+    "echo_mlp_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int,
+                                     ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P]),
+    "echo_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P]),
+    "echo_mlp_dataset": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong]),
+    "echo_mlp_load": (ctypes.c_int, [_P, _P]),
+    "echo_set_c2p_guess": (ctypes.c_int, [_P, ctypes.c_int]),
     "echo_totals_static": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                           _P, _P]),
     "echo_last_error": (ctypes.c_char_p, [_P]),
@@ -263,6 +276,87 @@ def echo_totals_static(state, n, dx, out6, stream_handle: int = 0):
     if rc != ECHO_OK:
         raise EchoError(rc, "echo_totals_static")
     return out6
+
+
+# ---------------------------------------------------------------- c2p-guess network
+
+ECHO_MLP_NPARAM = 4995
+ECHO_MLP_BLOCK = 5024
+ECHO_MLP_STATE = 3 * ECHO_MLP_BLOCK
+
+
+def _dev_f32(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t.data_ptr()
+
+
+def _dev_any(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _plain(rc, what):
+    if rc != ECHO_OK:
+        raise EchoError(rc, what)
+
+
+def echo_mlp_init(state, seed: int, stream_handle: int = 0):
+    _plain(load().echo_mlp_init(_P(_dev_f32(state, "state")), ctypes.c_ulonglong(seed), _P(stream_handle)),
+           "echo_mlp_init")
+
+
+def echo_mlp_work_bytes(batch: int) -> int:
+    return int(load().echo_mlp_work_bytes(int(batch)))
+
+
+def echo_mlp_normalize(state, X, Y, n, work, stream_handle: int = 0):
+    _plain(load().echo_mlp_normalize(_P(_dev_f32(state, "state")), _P(_dev_f32(X, "X")), _P(_dev_f32(Y, "Y")),
+                                     int(n), _P(_dev_any(work, "work")), work.numel() * work.element_size(),
+                                     _P(stream_handle)), "echo_mlp_normalize")
+
+
+def echo_mlp_train(state, X, Y, n, batch, nsteps, step0, lr, gamma, work, losses=None, stream_handle: int = 0):
+    lp = _P(_dev_f32(losses, "losses")) if losses is not None else None
+    _plain(load().echo_mlp_train(_P(_dev_f32(state, "state")), _P(_dev_f32(X, "X")), _P(_dev_f32(Y, "Y")),
+                                 int(n), int(batch), int(nsteps), int(step0), float(lr), float(gamma),
+                                 _P(_dev_any(work, "work")), work.numel() * work.element_size(), lp,
+                                 _P(stream_handle)), "echo_mlp_train")
+
+
+def echo_mlp_grad(state, X, Y, n, row0, batch, gamma, grad, loss, work, stream_handle: int = 0):
+    _plain(load().echo_mlp_grad(_P(_dev_f32(state, "state")), _P(_dev_f32(X, "X")), _P(_dev_f32(Y, "Y")),
+                                int(n), int(row0), int(batch), float(gamma), _P(_dev_f32(grad, "grad")),
+                                _P(_dev_f32(loss, "loss")) if loss is not None else None,
+                                _P(_dev_any(work, "work")), work.numel() * work.element_size(),
+                                _P(stream_handle)), "echo_mlp_grad")
+
+
+def echo_mlp_forward(state, X, n, out, stream_handle: int = 0):
+    _plain(load().echo_mlp_forward(_P(_dev_f32(state, "state")), _P(_dev_f32(X, "X")), int(n),
+                                   _P(_dev_f32(out, "out")), _P(stream_handle)), "echo_mlp_forward")
+
+
+def echo_mlp_dataset(ctx, X, Y, capacity, offset, stride):
+    _check(ctx, load().echo_mlp_dataset(ctx, _P(_dev_f32(X, "X")), _P(_dev_f32(Y, "Y")), int(capacity),
+                                        int(offset), int(stride)))
+
+
+def echo_mlp_load(ctx, state):
+    _check(ctx, load().echo_mlp_load(ctx, _P(_dev_f32(state, "state"))))
+
+
+def echo_set_c2p_guess(ctx, mode: int):
+    _check(ctx, load().echo_set_c2p_guess(ctx, int(mode)))
+
+
+def echo_counters(ctx) -> echo_totals:
+    t = echo_totals()
+    _check(ctx, load().echo_counters(ctx, ctypes.byref(t)))
+    return t
 
 
 def echo_last_error(ctx) -> str:

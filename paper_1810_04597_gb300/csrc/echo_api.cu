@@ -12,6 +12,7 @@
 #include "../../include/echo.h"
 #include "echo_device.cuh"
 #include "echo_launch.h"
+#include "echo_mlp.cuh"
 
 using namespace echo;
 
@@ -34,6 +35,8 @@ struct echo_ctx {
     size_t staging_count = 0;
     int nblk_red = 0;
     std::string err;
+    int c2p_guess = 0;        // 0 previous-stage Z, 1 c2p-guess network
+    bool mlp_loaded = false;
     // per-kernel timing (echo_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev;      // pool, pairs (start, end)
@@ -91,6 +94,7 @@ size_t layout(echo_ctx *c, char *base, Arrays<R> *A)
         A->E[d] = arr();
     }
     A->Z = reinterpret_cast<double *>(take(cells * sizeof(double)));
+    A->mlp = reinterpret_cast<const float *>(take(MLP_BLOCK * sizeof(float)));
     A->met = MetTables{};
     A->met.np0 = c->geo.np[0];
     A->met.use_floors = c->eos.floors;
@@ -186,7 +190,7 @@ void enqueue_rhs_pass(echo_ctx *c, int stage, double *Lout, bool want_rate, doub
     Arrays<R> &A = arrays<R>(c);
     cudaStream_t s = c->stream;
     PROF(ECHO_K_FILL_FACES, launch_fill<R>(c->geo, face_list(A), s));
-    PROF(ECHO_K_C2P, (launch_c2p<MK, R>(c->geo, c->ph, A, 0, want_rate ? 1 : 0, s)));
+    PROF(ECHO_K_C2P, (launch_c2p<MK, R>(c->geo, c->ph, A, c->c2p_guess == 1 ? 1 : 0, want_rate ? 1 : 0, s)));
     if (want_rate)
         PROF(ECHO_K_SCALARS, launch_set_dt(A.scal, c->cfl, dt_fixed <= 0.0 ? 1 : 0, s));
     PROF(ECHO_K_FILL_PRIMS, launch_fill<R>(c->geo, prim_list(A), s));
@@ -504,8 +508,10 @@ int echo_c2p(echo_ctx *c, int guess_mode, echo_totals *stats)
     int rc = require_bound(c, true);
     if (rc)
         return rc;
-    if (guess_mode != 0 && guess_mode != 2)
-        return fail(c, ECHO_EINVAL, "guess_mode must be 0 (previous Z) or 2 (cold)");
+    if (guess_mode < 0 || guess_mode > 2)
+        return fail(c, ECHO_EINVAL, "guess_mode must be 0 (previous Z), 1 (network) or 2 (cold)");
+    if (guess_mode == 1 && !c->mlp_loaded)
+        return fail(c, ECHO_ESTATE, "no c2p-guess network loaded: call echo_mlp_load first");
     rc = ECHO_DISPATCH(c, op_c2p, guess_mode);
     if (rc || !stats)
         return rc;
@@ -518,6 +524,7 @@ int echo_c2p(echo_ctx *c, int guess_mode, echo_totals *stats)
     stats->c2p_calls = (long long)hs.c2p_calls;
     stats->c2p_fail = (long long)hs.c2p_fail;
     stats->floor_hits = (long long)hs.floor_hits;
+    stats->mlp_fallback = (long long)hs.mlp_fallback;
     if (hs.fail_since_check) {
         DevScalars *ds = c->precision == 64 ? c->ad.scal : c->af.scal;
         cudaMemsetAsync(&ds->fail_since_check, 0, sizeof(unsigned long long), c->stream);
@@ -584,6 +591,7 @@ int echo_reduce(echo_ctx *c, echo_totals *out)
     out->c2p_fail = (long long)hs.c2p_fail;
     out->floor_hits = (long long)hs.floor_hits;
     out->fallback_faces = 0;
+    out->mlp_fallback = (long long)hs.mlp_fallback;
     if (hs.fail_since_check) {
         DevScalars *ds = c->precision == 64 ? c->ad.scal : c->af.scal;
         cudaMemsetAsync(&ds->fail_since_check, 0, sizeof(unsigned long long), c->stream);
@@ -591,6 +599,78 @@ int echo_reduce(echo_ctx *c, echo_totals *out)
             return fail(c, ECHO_EC2P, "conservative-to-primitive inversion failed in some cells");
     }
     return ECHO_OK;
+}
+
+int echo_counters(echo_ctx *c, echo_totals *out)
+{
+    int rc = require_bound(c, false);
+    if (rc)
+        return rc;
+    if (!out)
+        return fail(c, ECHO_EINVAL, "null output");
+    DevScalars hs;
+    rc = read_scalars(c, &hs);
+    if (rc)
+        return rc;
+    out->c2p_iters = (long long)hs.c2p_iters;
+    out->c2p_calls = (long long)hs.c2p_calls;
+    out->c2p_fail = (long long)hs.c2p_fail;
+    out->floor_hits = (long long)hs.floor_hits;
+    out->mlp_fallback = (long long)hs.mlp_fallback;
+    return ECHO_OK;
+}
+
+int echo_mlp_load(echo_ctx *c, const float *dev_state)
+{
+    int rc = require_bound(c, false);
+    if (rc)
+        return rc;
+    if (!dev_state)
+        return fail(c, ECHO_EINVAL, "null network block");
+    float *dst = const_cast<float *>(c->precision == 64 ? c->ad.mlp : c->af.mlp);
+    if (cudaMemcpyAsync(dst, dev_state, MLP_BLOCK * sizeof(float), cudaMemcpyDeviceToDevice, c->stream)
+        != cudaSuccess)
+        return cuda_check(c, "echo_mlp_load");
+    c->mlp_loaded = true;
+    return cuda_check(c, "echo_mlp_load");
+}
+
+int echo_set_c2p_guess(echo_ctx *c, int mode)
+{
+    if (!c)
+        return ECHO_EINVAL;
+    if (mode != 0 && mode != 1)
+        return fail(c, ECHO_EINVAL, "c2p guess mode must be 0 (previous Z) or 1 (network)");
+    if (mode == 1 && !c->mlp_loaded)
+        return fail(c, ECHO_ESTATE, "no c2p-guess network loaded: call echo_mlp_load first");
+    c->c2p_guess = mode;
+    return ECHO_OK;
+}
+
+int echo_mlp_dataset(echo_ctx *c, float *X, float *Y, long long capacity, long long offset, long long stride)
+{
+    int rc = require_bound(c, true);
+    if (rc)
+        return rc;
+    const long long N = (long long)c->geo.n[0] * c->geo.n[1] * c->geo.n[2];
+    if (!X || !Y || offset < 0 || stride < 1 || offset + (N - 1) * stride >= capacity)
+        return fail(c, ECHO_EINVAL, "dataset rows offset + (cells - 1) * stride must lie below capacity");
+    rc = ECHO_DISPATCH(c, op_c2p, 0);
+    if (rc)
+        return rc;
+    const bool ks = c->metric.kind == ECHO_METRIC_KERR_SCHILD;
+    if (c->precision == 64) {
+        if (ks)
+            launch_mlp_dataset<1, double>(c->geo, c->ad, X, Y, offset, stride, c->stream);
+        else
+            launch_mlp_dataset<0, double>(c->geo, c->ad, X, Y, offset, stride, c->stream);
+    } else {
+        if (ks)
+            launch_mlp_dataset<1, float>(c->geo, c->af, X, Y, offset, stride, c->stream);
+        else
+            launch_mlp_dataset<0, float>(c->geo, c->af, X, Y, offset, stride, c->stream);
+    }
+    return cuda_check(c, "echo_mlp_dataset");
 }
 
 int echo_profile(echo_ctx *c, int enable)

@@ -58,6 +58,7 @@ struct DevScalars {
     unsigned long long c2p_fail;
     unsigned long long floor_hits;
     unsigned long long fail_since_check;
+    unsigned long long mlp_fallback;
     double totals[8];            // mass, energy, mom x3, max divB, rate, spare
 };
 
@@ -103,6 +104,7 @@ struct Arrays {
     double *partials;  // reduction partials
     DevScalars *scal;
     MetTables met; // Kerr-Schild tables (unused in flat space)
+    const float *mlp;  // c2p-guess network block (params + standardisation)
 };
 
 // ------------------------------------------------------------------ exact
@@ -501,7 +503,7 @@ __device__ __forceinline__ void c2p_recip(double Z, double B2, double &iZ, doubl
 
 template <typename M>
 __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], double tau, const double B[3],
-                                                double Zguess, double gm1g, const M &m)
+                                                double Zguess, double gm1g, const M &m, int maxit = NEWTON_MAXIT)
 {
     double Su[3], Bl[3];
     raise<double>(m, S, Su);
@@ -530,7 +532,7 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
     }
     int it = 0;
     bool conv = false;
-    while (ok && it < NEWTON_MAXIT) {
+    while (ok && it < maxit) {
         ++it;
         const double om = 1.0 - v2;
         const double isq = rsqrt(om);

@@ -13,6 +13,7 @@
 
 #include "echo_device.cuh"
 #include "echo_launch.h"
+#include "echo_mlp.cuh"
 
 namespace echo {
 
@@ -50,7 +51,12 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 // conserved state reset from the floored primitives (counted in floor_hits).
 // Optionally accumulates the CFL rate max (atomicMax on the bits of a
 // non-negative double, order independent) and the Newton counters.
-template <int MK, typename R>
+//
+// With MLP the Newton guess comes from the c2p-guess network (weights staged
+// in shared memory); Newton from that guess is capped at 8 iterations and
+// falls back to the cell's previous-stage Z if it has not converged
+// (counted in mlp_fallback).
+template <int MK, typename R, bool MLP>
 __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate)
 {
     const int i = NG + blockIdx.x * blockDim.x + threadIdx.x;
@@ -58,7 +64,15 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
     const int k = NG + blockIdx.z;
     const bool live = i < NG + g.n[0] && j < NG + g.n[1] && k < NG + g.n[2];
     double rate = 0.0;
-    unsigned long long its = 0, calls = 0, fails = 0, floors = 0;
+    unsigned long long its = 0, calls = 0, fails = 0, floors = 0, mfb = 0;
+    extern __shared__ float4 mlp_smem4[];
+    if constexpr (MLP) {
+        float *Ps = reinterpret_cast<float *>(mlp_smem4);
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        for (int q = tid; q < MLP_BLOCK; q += blockDim.x * blockDim.y)
+            Ps[q] = A.mlp[q];
+        __syncthreads();
+    }
     if (live) {
         const long long id = gidx(g, i, j, k);
         double isg = 1.0, sg = 1.0;
@@ -74,11 +88,36 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
         B[2] = 0.5 * ((double)A.U[7][id] + (double)A.U[7][id + g.pxy]) * isg;
         const double S[3] = {(double)A.U[1][id] * isg, (double)A.U[2][id] * isg, (double)A.U[3][id] * isg};
         const double zg = guess_mode == 2 ? 0.0 : A.Z[id];
+        const double Dc = (double)A.U[0][id] * isg, tc = (double)A.U[4][id] * isg;
         C2PResult r;
-        if constexpr (MK == 1)
-            r = c2p_newton((double)A.U[0][id] * isg, S, (double)A.U[4][id] * isg, B, zg, ph.gm1g, MKS<double>(*mp));
-        else
-            r = c2p_newton((double)A.U[0][id], S, (double)A.U[4][id], B, zg, ph.gm1g, MFlat<double>());
+        if constexpr (MLP) {
+            float f[MLP_NI], o[MLP_NO];
+            if constexpr (MK == 1)
+                mlp_features(Dc, S, tc, B, sg, MKS<double>(*mp), f);
+            else
+                mlp_features(Dc, S, tc, B, 1.0, MFlat<double>(), f);
+            mlp_infer(reinterpret_cast<const float *>(mlp_smem4), f, o);
+            const double Wg = exp((double)o[0]), pD = exp((double)o[1]);
+            const double z0 = Dc * Wg * (1.0 + ph.gr * pD * Wg);
+            if constexpr (MK == 1)
+                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MKS<double>(*mp), 8);
+            else
+                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MFlat<double>(), 8);
+            if (!r.ok) {
+                const int first = r.iters;
+                if constexpr (MK == 1)
+                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp));
+                else
+                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>());
+                r.iters += first;
+                mfb = 1;
+            }
+        } else {
+            if constexpr (MK == 1)
+                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp));
+            else
+                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>());
+        }
         its = r.iters;
         calls = 1;
         fails = r.ok ? 0 : 1;
@@ -123,6 +162,7 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
     calls = warp_sum_u64(calls);
     fails = warp_sum_u64(fails);
     floors = warp_sum_u64(floors);
+    mfb = warp_sum_u64(mfb);
     if (want_rate)
         rate = warp_max(rate);
     if ((threadIdx.x & 31) == 0) {
@@ -136,6 +176,8 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
         }
         if (floors)
             atomicAdd(&A.scal->floor_hits, floors);
+        if (mfb)
+            atomicAdd(&A.scal->mlp_fallback, mfb);
         if (want_rate && rate > 0.0)
             atomicMax(&A.scal->rate_bits, (unsigned long long)__double_as_longlong(rate));
     }
@@ -711,6 +753,59 @@ __global__ void k_p2c(Geom g, Phys ph, const double *prims5, Arrays<R> A)
     for (int q = 0; q < 5; ++q)
         A.U[q][id] = (R)(C5[q] * sg);
     A.Z[id] = Z;
+}
+
+// ------------------------------------------------------------------ training
+// pairs for the c2p-guess network
+
+// One row per owned cell after a converged c2p: the network features of the
+// conserved state and the targets log W, log(p/D), log(Z/D).  Rows go to
+// offset + perm(c) * stride, with perm(c) = (c * 2654435761) mod N a
+// permutation of the N cells (the multiplier is prime and larger than N),
+// so one snapshot lands in a shuffled order.
+template <int MK, typename R>
+__global__ void k_mlp_dataset(Geom g, Arrays<R> A, float *X, float *Y, long long offset, long long stride)
+{
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N)
+        return;
+    const int ti = (int)(c % g.n[0]);
+    const long long rr = c / g.n[0];
+    const int tj = (int)(rr % g.n[1]);
+    const int tk = (int)(rr / g.n[1]);
+    const int i = NG + ti, j = NG + tj, k = NG + tk;
+    const long long id = gidx(g, i, j, k);
+    const long long row = offset + (long long)(((unsigned long long)c * 2654435761ULL) % (unsigned long long)N) * stride;
+    double isg = 1.0, sg = 1.0;
+    const MetPt *mp = nullptr;
+    if constexpr (MK == 1) {
+        mp = &A.met.C[j * A.met.np0 + i];
+        isg = mp->isg;
+        sg = mp->sg;
+    }
+    const double B[3] = {0.5 * ((double)A.U[5][id] + (double)A.U[5][id + 1]) * isg,
+                         0.5 * ((double)A.U[6][id] + (double)A.U[6][id + g.px]) * isg,
+                         0.5 * ((double)A.U[7][id] + (double)A.U[7][id + g.pxy]) * isg};
+    const double S[3] = {(double)A.U[1][id] * isg, (double)A.U[2][id] * isg, (double)A.U[3][id] * isg};
+    const double Dc = (double)A.U[0][id] * isg, tc = (double)A.U[4][id] * isg;
+    float f[MLP_NI];
+    const double v[3] = {(double)A.P[1][id], (double)A.P[2][id], (double)A.P[3][id]};
+    double vl[3];
+    if constexpr (MK == 1) {
+        mlp_features(Dc, S, tc, B, sg, MKS<double>(*mp), f);
+        lower<double>(MKS<double>(*mp), v, vl);
+    } else {
+        mlp_features(Dc, S, tc, B, 1.0, MFlat<double>(), f);
+        lower<double>(MFlat<double>(), v, vl);
+    }
+    for (int q = 0; q < MLP_NI; ++q)
+        X[row * 9 + q] = f[q];
+    const double v2 = vl[0] * v[0] + vl[1] * v[1] + vl[2] * v[2];
+    const double W = 1.0 / sqrt(1.0 - v2);
+    Y[row * 3 + 0] = (float)log(W);
+    Y[row * 3 + 1] = (float)log((double)A.P[4][id] / Dc);
+    Y[row * 3 + 2] = (float)log(A.Z[id] / Dc);
 }
 
 #ifdef ECHO_COMMON_KERNELS

@@ -33,6 +33,9 @@ template <int MK, typename R>
 void launch_update(const Geom &g, const Phys &ph, const Arrays<R> &A, int stage, double *Lout, cudaStream_t s);
 template <int MK, typename R>
 void launch_p2c(const Geom &g, const Phys &ph, const double *prims5, const Arrays<R> &A, cudaStream_t s);
+template <int MK, typename R>
+void launch_mlp_dataset(const Geom &g, const Arrays<R> &A, float *X, float *Y, long long offset, long long stride,
+                        cudaStream_t s);
 template <typename R>
 void launch_totals(const Geom &g, const Arrays<R> &A, int nblk, cudaStream_t s);
 template <typename R>

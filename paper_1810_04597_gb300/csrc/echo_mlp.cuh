@@ -1,0 +1,116 @@
+// echo_mlp.cuh -- the c2p-guess network on the device: features of a
+// conserved state and the fused FP32 forward pass used inside the c2p
+// kernel.  Training kernels are in echo_mlp.cu.
+//
+// Network 9 -> 64 -> 64 -> 3 (tanh), FP32.  Parameter block (floats):
+//   W1 64x9 | b1 64 | W2 64x64 | b2 64 | W3 3x64 | b3 3   (4995 values)
+//   then feature mean 9 | feature std 9 | target mean 3 | target std 3.
+// Outputs (standardised): log W, log(p/D), and the predicted log10
+// relative error of the guess Z0 = D W (1 + G/(G-1) (p/D) W).
+#pragma once
+
+#include "echo_device.cuh"
+
+namespace echo {
+
+constexpr int MLP_NI = 9, MLP_NH = 64, MLP_NO = 3;
+constexpr int MLP_OW1 = 0;
+constexpr int MLP_OB1 = MLP_OW1 + MLP_NH * MLP_NI;
+constexpr int MLP_OW2 = MLP_OB1 + MLP_NH;
+constexpr int MLP_OB2 = MLP_OW2 + MLP_NH * MLP_NH;
+constexpr int MLP_OW3 = MLP_OB2 + MLP_NH;
+constexpr int MLP_OB3 = MLP_OW3 + MLP_NO * MLP_NH;
+constexpr int MLP_NPAR = MLP_OB3 + MLP_NO;   // 4995
+constexpr int MLP_ONORM = MLP_NPAR;
+constexpr int MLP_NNORM = 2 * MLP_NI + 2 * MLP_NO;   // 24
+constexpr int MLP_BLOCK = 5024;                      // params + norm, padded to 32
+// training state: [params+norm (MLP_BLOCK) | Adam m (MLP_BLOCK) | Adam v (MLP_BLOCK)]
+constexpr int MLP_STATE = 3 * MLP_BLOCK;
+
+// Scale-free features of an undensitised conserved state (D, S_i, tau),
+// contravariant B and the metric:  log(tau/D), log(1 + S^2/D^2),
+// log(1 + B^2/D), (S.B)^2 / (S^2 B^2), alpha, log sqrt(gamma), beta_i beta^i,
+// (gamma^11 + gamma^22 + gamma^33)/3, log(D)/10.
+template <typename M>
+__device__ __forceinline__ void mlp_features(double Dc, const double S[3], double tau, const double B[3], double sqrtg,
+                                             const M &m, float f[9])
+{
+    const float D = (float)Dc;
+    const float Sf[3] = {(float)S[0], (float)S[1], (float)S[2]};
+    const float Bf[3] = {(float)B[0], (float)B[1], (float)B[2]};
+    float Su[3], Bl[3];
+    float al = 1.0f, bb = 0.0f, tr = 1.0f;
+    if constexpr (M::flat) {
+        Su[0] = Sf[0];
+        Su[1] = Sf[1];
+        Su[2] = Sf[2];
+        Bl[0] = Bf[0];
+        Bl[1] = Bf[1];
+        Bl[2] = Bf[2];
+    } else {
+        Su[0] = (float)m.i11 * Sf[0] + (float)m.i13 * Sf[2];
+        Su[1] = (float)m.i22 * Sf[1];
+        Su[2] = (float)m.i13 * Sf[0] + (float)m.i33 * Sf[2];
+        Bl[0] = (float)m.g11 * Bf[0] + (float)m.g13 * Bf[2];
+        Bl[1] = (float)m.g22 * Bf[1];
+        Bl[2] = (float)m.g13 * Bf[0] + (float)m.g33 * Bf[2];
+        al = (float)m.al;
+        bb = (float)(m.g11 * m.b1 * m.b1);
+        tr = (float)((m.i11 + m.i22 + m.i33) / 3.0);
+    }
+    const float S2 = Sf[0] * Su[0] + Sf[1] * Su[1] + Sf[2] * Su[2];
+    const float B2 = Bl[0] * Bf[0] + Bl[1] * Bf[1] + Bl[2] * Bf[2];
+    const float SB = Sf[0] * Bf[0] + Sf[1] * Bf[1] + Sf[2] * Bf[2];
+    const float iD = 1.0f / D;
+    f[0] = logf(fmaxf((float)tau * iD, 1e-30f));
+    f[1] = log1pf(S2 * iD * iD);
+    f[2] = log1pf(B2 * iD);
+    f[3] = SB * SB / (S2 * B2 + 1e-30f);
+    f[4] = al;
+    f[5] = logf((float)sqrtg);
+    f[6] = bb;
+    f[7] = tr;
+    f[8] = fminf(fmaxf(logf(D), -30.0f), 30.0f) * 0.1f;
+}
+
+// Forward pass with the parameter block in shared memory; returns the
+// de-standardised outputs (log W, log(p/D), log10 error).
+__device__ __forceinline__ void mlp_infer(const float *__restrict__ P, const float f[9], float out[3])
+{
+    float x[MLP_NI];
+#pragma unroll
+    for (int i = 0; i < MLP_NI; ++i)
+        x[i] = (f[i] - P[MLP_ONORM + i]) / P[MLP_ONORM + MLP_NI + i];
+    float h1[MLP_NH];
+#pragma unroll
+    for (int j = 0; j < MLP_NH; ++j) {
+        float s = P[MLP_OB1 + j];
+#pragma unroll
+        for (int i = 0; i < MLP_NI; ++i)
+            s = fmaf(P[MLP_OW1 + j * MLP_NI + i], x[i], s);
+        h1[j] = tanhf(s);
+    }
+    float o[MLP_NO] = {P[MLP_OB3], P[MLP_OB3 + 1], P[MLP_OB3 + 2]};
+#pragma unroll 4
+    for (int k = 0; k < MLP_NH; ++k) {
+        const float4 *w = reinterpret_cast<const float4 *>(P + MLP_OW2 + k * MLP_NH);
+        float s = P[MLP_OB2 + k];
+#pragma unroll
+        for (int j4 = 0; j4 < MLP_NH / 4; ++j4) {
+            const float4 wv = w[j4];
+            s = fmaf(wv.x, h1[4 * j4], s);
+            s = fmaf(wv.y, h1[4 * j4 + 1], s);
+            s = fmaf(wv.z, h1[4 * j4 + 2], s);
+            s = fmaf(wv.w, h1[4 * j4 + 3], s);
+        }
+        const float h2 = tanhf(s);
+#pragma unroll
+        for (int q = 0; q < MLP_NO; ++q)
+            o[q] = fmaf(P[MLP_OW3 + q * MLP_NH + k], h2, o[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < MLP_NO; ++q)
+        out[q] = o[q] * P[MLP_ONORM + 2 * MLP_NI + MLP_NO + q] + P[MLP_ONORM + 2 * MLP_NI + q];
+}
+
+}  // namespace echo

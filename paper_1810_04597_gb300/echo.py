@@ -87,6 +87,18 @@ class Solver:
     def reduce(self) -> dict:
         return _lib.echo_reduce(self.ctx).as_dict()
 
+    def counters(self) -> dict:
+        return _lib.echo_counters(self.ctx).as_dict()
+
+    def mlp_load(self, state):
+        _lib.echo_mlp_load(self.ctx, state)
+
+    def set_c2p_guess(self, mode: int):
+        _lib.echo_set_c2p_guess(self.ctx, mode)
+
+    def mlp_dataset(self, X, Y, offset: int = 0, stride: int = 1):
+        _lib.echo_mlp_dataset(self.ctx, X, Y, X.shape[0], offset, stride)
+
     def profile(self, enable: bool = True):
         _lib.echo_profile(self.ctx, enable)
 

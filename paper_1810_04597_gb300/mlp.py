@@ -1,0 +1,94 @@
+"""Training driver of the c2p-guess network (orchestration only).
+
+Data: converged inversions the method itself produces -- every owned cell of
+FP64 runs of the periodic boxes (``sweep_box``, ``smooth_box``), a few
+snapshots along each run, written by ``echo_mlp_dataset`` in a permuted cell
+order and interleaved across snapshots.  Training: ``echo_mlp_normalize`` and
+``echo_mlp_train`` (Adam) -- every forward, backward and update runs in the
+library's kernels.  Torch only supplies device memory and the stream.
+"""
+from __future__ import annotations
+
+from . import _lib, inputs
+from .echo import Solver
+
+
+def collect(problems_and_steps, device="cuda:0"):
+    """Snapshots -> (X, Y) train / validation / test tensors on `device`.
+
+    problems_and_steps: list of (problem, [steps at which to take a
+    snapshot]).  In every run the last snapshot is held out for test, the one
+    before it for validation, the others train (rows interleaved across the
+    training snapshots)."""
+    import torch
+    train_s, val_s, test_s = [], [], []
+    for prob, at in problems_and_steps:
+        at = sorted(at)
+        s = Solver(prob, precision=64, device=device)
+        s.set_prims()
+        snaps = []
+        for step in range(at[-1] + 1):
+            if step in at:
+                N = prob.ncells
+                X = torch.empty((N, 9), dtype=torch.float32, device=device)
+                Y = torch.empty((N, 3), dtype=torch.float32, device=device)
+                s.mlp_dataset(X, Y, 0, 1)
+                snaps.append((X, Y))
+            if step < at[-1]:
+                s.step()
+        s.close()
+        train_s += snaps[:-2]
+        val_s.append(snaps[-2])
+        test_s.append(snaps[-1])
+    n = min(x.shape[0] for x, _ in train_s)
+    Xtr = torch.stack([x[:n] for x, _ in train_s], dim=1).reshape(-1, 9).contiguous()
+    Ytr = torch.stack([y[:n] for _, y in train_s], dim=1).reshape(-1, 3).contiguous()
+    cat = lambda xs: torch.cat(xs, dim=0).contiguous()  # noqa: E731
+    return (Xtr, Ytr), (cat([x for x, _ in val_s]), cat([y for _, y in val_s])), \
+        (cat([x for x, _ in test_s]), cat([y for _, y in test_s]))
+
+
+def train(X, Y, epochs=2, batch=8192, lr=1e-3, seed=1, gamma=4.0 / 3.0, device="cuda:0"):
+    """Train a fresh network on (X, Y); returns (state tensor, per-step
+    losses tensor)."""
+    import torch
+    n = X.shape[0]
+    state = torch.empty(_lib.ECHO_MLP_STATE, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream(device).cuda_stream
+    _lib.echo_mlp_init(state, seed, stream)
+    work = torch.empty(_lib.echo_mlp_work_bytes(batch), dtype=torch.uint8, device=device)
+    _lib.echo_mlp_normalize(state, X, Y, n, work, stream)
+    nsteps = max(1, int(epochs * n // batch))
+    losses = torch.empty(nsteps, dtype=torch.float32, device=device)
+    chunk = 512
+    for s0 in range(0, nsteps, chunk):
+        k = min(chunk, nsteps - s0)
+        _lib.echo_mlp_train(state, X, Y, n, batch, k, s0, lr, gamma, work, losses[s0:s0 + k], stream)
+    return state, losses
+
+
+def guess_error(state, X, Y, gamma=4.0 / 3.0):
+    """Relative error |Z0 - Z| / Z of the network guess on rows (X, Y),
+    from the standardised outputs the library's forward kernel returns."""
+    import torch
+    n = X.shape[0]
+    out = torch.empty((n, 3), dtype=torch.float32, device=X.device)
+    _lib.echo_mlp_forward(state, X, n, out, torch.cuda.current_stream(X.device).cuda_stream)
+    blk = state[:_lib.ECHO_MLP_BLOCK].double()
+    ym, ys = blk[4995 + 18:4995 + 21], blk[4995 + 21:4995 + 24]
+    o = out.double() * ys + ym
+    gr = gamma / (gamma - 1.0)
+    W = torch.exp(o[:, 0])
+    z0 = W * (1.0 + gr * torch.exp(o[:, 1]) * W)
+    z = torch.exp(Y[:, 2].double())
+    return (z0 - z).abs() / z
+
+
+def default_network(device="cuda:0", n=128, epochs=2, seed=1):
+    """The network used by the benchmarks: trained on snapshots of the
+    n^3 configs-2 (sweep_box) and configs-1-recipe (smooth_box) FP64 runs."""
+    runs = [(inputs.sweep_box(n), [0, 3, 6, 9, 12, 15]),
+            (inputs.smooth_box(n), [0, 4, 8, 12])]
+    (Xtr, Ytr), (Xva, Yva), (Xte, Yte) = collect(runs, device=device)
+    state, losses = train(Xtr, Ytr, epochs=epochs, seed=seed, device=device)
+    return state, losses, (Xva, Yva), (Xte, Yte)

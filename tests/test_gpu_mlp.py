@@ -1,0 +1,164 @@
+"""The c2p-guess network on the GPU: forward pass and batch gradient against
+the FP64 oracle, the Adam update, training on method-generated pairs, and
+what the trained guess gains (or loses) against the guesses without it."""
+import numpy as np
+import pytest
+
+from paper_1810_04597_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    if not T.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    return T
+
+
+def random_state(T, rng):
+    from paper_1810_04597_gb300 import _lib
+    st = np.zeros(_lib.ECHO_MLP_STATE, dtype=np.float32)
+    st[:4995] = rng.normal(0, 0.3, 4995)
+    st[4995:4995 + 9] = rng.normal(0, 1, 9)
+    st[4995 + 9:4995 + 18] = rng.uniform(0.5, 2, 9)
+    st[4995 + 18:4995 + 21] = rng.normal(0, 0.5, 3)
+    st[4995 + 21:4995 + 24] = rng.uniform(0.5, 2, 3)
+    return st
+
+
+def random_rows(rng, n):
+    x = rng.normal(0, 1, size=(n, 9)).astype(np.float32)
+    W = rng.uniform(1.0, 1.5, n)
+    pD = rng.uniform(0.1, 2.0, n)
+    z = W * (1 + 4.0 * pD * W)
+    y = np.stack([np.log(W), np.log(pD), np.log(z)], axis=1).astype(np.float32)
+    return x, y
+
+
+def test_forward_matches_oracle(orc, torch):
+    from paper_1810_04597_gb300 import _lib
+    rng = np.random.default_rng(0)
+    st = random_state(torch, rng)
+    x, _ = random_rows(rng, 1000)
+    out = torch.empty((1000, 3), dtype=torch.float32, device="cuda")
+    _lib.echo_mlp_forward(torch.from_numpy(st).cuda(), torch.from_numpy(x).cuda(), 1000, out)
+    ref = orc.mlp_forward(st[:4995 + 24].astype(np.float64), x.astype(np.float64))
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 2e-5 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_gradient_matches_oracle(orc, torch):
+    from paper_1810_04597_gb300 import _lib
+    rng = np.random.default_rng(1)
+    st = random_state(torch, rng)
+    x, y = random_rows(rng, 2048)
+    batch = 2048
+    g = torch.empty(4995, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    work = torch.empty(_lib.echo_mlp_work_bytes(batch), dtype=torch.uint8, device="cuda")
+    _lib.echo_mlp_grad(torch.from_numpy(st).cuda(), torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(),
+                       2048, 0, batch, 4.0 / 3.0, g, loss, work)
+    lo, go = orc.mlp_loss_grad(st[:4995 + 24].astype(np.float64), x.astype(np.float64), y.astype(np.float64),
+                               w2=0.1)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - go) <= 1e-4 * np.linalg.norm(go)
+    assert abs(float(loss.item()) - lo) <= 1e-4 * abs(lo)
+
+
+def test_adam_step_matches_oracle(orc, torch):
+    from paper_1810_04597_gb300 import _lib
+    rng = np.random.default_rng(2)
+    st = random_state(torch, rng)
+    x, y = random_rows(rng, 512)
+    dst = torch.from_numpy(st.copy()).cuda()
+    work = torch.empty(_lib.echo_mlp_work_bytes(512), dtype=torch.uint8, device="cuda")
+    _lib.echo_mlp_train(dst, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), 512, 512, 1, 0, 1e-3,
+                        4.0 / 3.0, work)
+    _, go = orc.mlp_loss_grad(st[:4995 + 24].astype(np.float64), x.astype(np.float64), y.astype(np.float64),
+                              w2=0.1)
+    P = st[:4995].astype(np.float64)
+    m = np.zeros(4995)
+    v = np.zeros(4995)
+    orc.mlp_adam(P, m, v, go, 1, lr=1e-3)
+    got = dst.cpu().numpy()[:4995].astype(np.float64)
+    # the first Adam step is lr * sign(g) per parameter: compare the move
+    moved = got - st[:4995]
+    ref = P - st[:4995]
+    big = np.abs(go) > 1e-3 * np.max(np.abs(go))
+    assert np.allclose(moved[big], ref[big], rtol=1e-3, atol=1e-7)
+
+
+@pytest.fixture(scope="module")
+def trained(torch):
+    from paper_1810_04597_gb300 import mlp
+    runs = [(inputs.sweep_box(64), [0, 2, 4, 6, 8]), (inputs.smooth_box(64), [0, 3, 6])]
+    (Xtr, Ytr), (Xva, Yva), (Xte, Yte) = mlp.collect(runs)
+    state, losses = mlp.train(Xtr, Ytr, epochs=3, batch=4096, lr=2e-3)
+    return state, losses, (Xte, Yte)
+
+
+def test_training_reduces_loss_and_error(trained, torch):
+    from paper_1810_04597_gb300 import mlp
+    state, losses, (Xte, Yte) = trained
+    L = losses.cpu().numpy()
+    assert np.all(np.isfinite(L))
+    assert L[-50:].mean() < 0.05 * L[:20].mean(), (L[:20].mean(), L[-50:].mean())
+    err = mlp.guess_error(state, Xte, Yte).cpu().numpy()
+    assert np.median(err) < 1e-2, np.median(err)
+
+
+def test_network_guess_gives_the_same_inversion(trained, torch):
+    """The Newton solve stays the judge: with the network guess the converged
+    primitives equal those from the previous-stage guess to rounding."""
+    from paper_1810_04597_gb300.echo import Solver
+    state, _, _ = trained
+    prob = inputs.sweep_box(48, seed=77)
+    a = Solver(prob)
+    a.set_prims()
+    b = Solver(prob)
+    b.set_prims()
+    b.mlp_load(state)
+    a.step()
+    b.step()
+    sa = a.c2p(0)
+    sb = b.c2p(1)
+    Pa = a.get_prims()
+    Pb = b.get_prims()
+    for q in range(8):
+        assert np.max(np.abs(Pa[q] - Pb[q])) <= 1e-12 * max(np.max(np.abs(Pa[q])), 1e-300), q
+    assert sb["mlp_fallback"] <= 0.01 * prob.ncells
+
+
+def test_gain_over_guesses_without_network(trained, torch):
+    """Mean Newton iterations per c2p call during three SSP-RK3 steps with
+    the previous-stage guess and with the network guess, and for one
+    inversion from the cold guess, on a held-out input.  Reported as they
+    come out; the network must beat the cold guess and reproduce the same
+    state as the previous-stage runs."""
+    from paper_1810_04597_gb300.echo import Solver
+    state, _, _ = trained
+    prob = inputs.sweep_box(64, seed=99)
+    res, fin = {}, {}
+    for mode, name in ((0, "previous"), (1, "network")):
+        s = Solver(prob)
+        s.set_prims()
+        s.mlp_load(state)
+        s.set_c2p_guess(mode)
+        c0 = s.counters()
+        for _ in range(3):
+            s.step()
+        c1 = s.counters()
+        res[name] = (c1["c2p_iters"] - c0["c2p_iters"]) / (c1["c2p_calls"] - c0["c2p_calls"])
+        res[name + "_fallback"] = c1["mlp_fallback"] - c0["mlp_fallback"]
+        fin[name] = s.get_state()
+    s = Solver(prob)
+    s.set_prims()
+    c0 = s.counters()
+    s.c2p(2)
+    c1 = s.counters()
+    res["cold"] = (c1["c2p_iters"] - c0["c2p_iters"]) / (c1["c2p_calls"] - c0["c2p_calls"])
+    print("mean Newton iterations per call:", res)
+    assert res["network"] < res["cold"]
+    scale = np.max(np.abs(fin["previous"]))
+    assert np.max(np.abs(fin["network"] - fin["previous"])) <= 1e-11 * scale
