@@ -398,6 +398,8 @@ def run_ours(args, world, rank, local, dist):
             "mean_newton_iters": t32["c2p_iters"] / max(t32["c2p_calls"], 1),
             "note": "FP32 storage/stencil, FP64 c2p and reductions; same input, same step count"}}
         del s32
+        if not args.no_mlp:
+            variants["fp32_mlp"] = run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -426,6 +428,54 @@ def run_ours(args, world, rank, local, dist):
     return line if rank == 0 else None
 
 
+def run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms64):
+    """FP32 bulk with the c2p-guess network: train the default network on
+    FP64 runs of the 128^3 configs-1/2 boxes (untimed), then time W + K
+    steps on the workload from the same input as the FP64 run."""
+    import numpy as np
+    import torch
+    from paper_1810_04597_gb300 import mlp
+    from paper_1810_04597_gb300.echo import Solver
+    t0 = time.perf_counter()
+    state, losses, _, (Xte, Yte) = mlp.default_network(device=str(dev))
+    err = mlp.guess_error(state, Xte, Yte).cpu().numpy()
+    t_train = time.perf_counter() - t0
+    s = Solver(prob, precision=32, device=str(dev))
+    s.set_prims()
+    s.mlp_load(state)
+    s.set_c2p_guess(1)
+    for _ in range(args.warmup):
+        s.step()
+    torch.cuda.synchronize()
+    c0 = s.counters()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    for _ in range(args.steps):
+        s.step()
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    msm = e0.elapsed_time(e1)
+    c1 = s.counters()
+    fin = s.get_state()
+    l1 = {}
+    for name, a, b in zip(names, bounds[:-1], bounds[1:]):
+        den = float(np.sum(np.abs(fin64[a:b])))
+        l1[name] = float(np.sum(np.abs(fin[a:b] - fin64[a:b])) / den) if den > 0 else 0.0
+    calls = max(c1["c2p_calls"] - c0["c2p_calls"], 1)
+    out = {"value": world * prob.ncells * args.steps / (max_over_ranks(dist, msm) * 1e-3) / 1e6, "unit": UNIT,
+           "ms_per_step": msm / args.steps, "speedup_vs_fp64": ms64 / msm,
+           "l1_rel_vs_fp64_gpu": l1, "max_l1": max(l1.values()),
+           "mean_newton_iters": (c1["c2p_iters"] - c0["c2p_iters"]) / calls,
+           "mlp_fallback_per_call": (c1["mlp_fallback"] - c0["mlp_fallback"]) / calls,
+           "guess_rel_err_median_heldout": float(np.median(err)),
+           "guess_rel_err_p99_heldout": float(np.quantile(err, 0.99)),
+           "train_seconds": t_train, "train_final_loss": float(losses[-50:].mean().item()),
+           "note": "FP32 bulk; c2p guess from the network trained on the GPU (untimed); FP64 Newton judges"}
+    del s
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,6 +487,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     world, rank, local = dist_info()

@@ -225,6 +225,41 @@ int echo_set_c2p_guess(echo_ctx *ctx, int mode);
  * Synchronises. */
 int echo_counters(echo_ctx *ctx, echo_totals *out);
 
+/* ---- batch of independent runs (parameter sweeps) ----
+ * The paper motivates the cost of exploring many parameters; a batch advances
+ * up to ECHO_BATCH_MAXRUNS independent runs (same metric kind, precision,
+ * adiabatic index and CFL number; sizes may differ) with ONE persistent
+ * cooperative kernel per SSP-RK3 stage.  Each stage's phases (ghost fills,
+ * c2p, faces, EMFs, update) are cut into tiles over all runs and taken by
+ * the resident blocks round-robin or from an atomic queue; grid-wide
+ * barriers separate dependent phases (the cooperative launch keeps every
+ * block resident, so they cannot deadlock).  Every run keeps its own CFL dt.
+ * The runs must be bound contexts with a state; their workspaces and
+ * counters are the runs' own.  If run 0 uses the network guess
+ * (echo_set_c2p_guess 1), all runs use run 0's network. */
+#define ECHO_BATCH_MAXRUNS 32
+typedef struct echo_batch echo_batch;
+
+int echo_batch_create(echo_ctx *const *runs, int nruns, echo_batch **out);
+/* Device bytes the batch needs (run descriptors, tile plan, queue). */
+size_t echo_batch_workspace_bytes(const echo_batch *batch);
+/* Attach a caller-owned 256-byte aligned workspace and the stream the stage
+ * kernels run on (the runs' own streams are not used). */
+int echo_batch_bind(echo_batch *batch, void *dev_workspace, size_t bytes, void *cuda_stream);
+/* Tile size (multiple of 128 work items, <= 8192), resident blocks per SM
+ * (1 .. echo_batch_max_blocks_per_sm) and queue kind (0 round-robin,
+ * 1 atomic queue).  Default after bind: 256, the maximum, 1. */
+int echo_batch_config(echo_batch *batch, int tile, int blocks_per_sm, int dynamic_queue);
+int echo_batch_max_blocks_per_sm(echo_batch *batch);
+/* 1: capture one whole step (three cooperative launches) into a CUDA graph
+ * on first use and replay it; recaptured when dt or the configuration
+ * changes.  Needs a created stream (ECHO_EINVAL on the legacy stream). */
+int echo_batch_graph(echo_batch *batch, int enable);
+/* One SSP-RK3 step of every run (dt > 0 for all, else each run's CFL dt). */
+int echo_batch_step(echo_batch *batch, double dt);
+const char *echo_batch_last_error(const echo_batch *batch);
+void echo_batch_destroy(echo_batch *batch);
+
 /* Kernel classes timed by the profiling facility below. */
 #define ECHO_K_FILL_FACES 0
 #define ECHO_K_C2P 1

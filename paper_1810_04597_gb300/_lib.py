@@ -93,6 +93,15 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "echo_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "echo_counters": (ctypes.c_int, [_P, ctypes.POINTER(echo_totals)]),
+    "echo_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
+    "echo_batch_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "echo_batch_bind": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
+    "echo_batch_config": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "echo_batch_max_blocks_per_sm": (ctypes.c_int, [_P]),
+    "echo_batch_graph": (ctypes.c_int, [_P, ctypes.c_int]),
+    "echo_batch_step": (ctypes.c_int, [_P, ctypes.c_double]),
+    "echo_batch_last_error": (ctypes.c_char_p, [_P]),
+    "echo_batch_destroy": (None, [_P]),
     "echo_mlp_init": (ctypes.c_int, [_P, ctypes.c_ulonglong, _P]),
     "echo_mlp_work_bytes": (ctypes.c_size_t, [ctypes.c_int]),
     "echo_mlp_normalize": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P, ctypes.c_size_t, _P]),
@@ -357,6 +366,49 @@ def echo_counters(ctx) -> echo_totals:
     t = echo_totals()
     _check(ctx, load().echo_counters(ctx, ctypes.byref(t)))
     return t
+
+
+# ---------------------------------------------------------------- batches
+
+def _bcheck(b, rc):
+    if rc != ECHO_OK:
+        msg = load().echo_batch_last_error(b) if b else b""
+        raise EchoError(rc, (msg or b"").decode())
+
+
+def echo_batch_create(ctxs):
+    arr = (_P * len(ctxs))(*[c.value if isinstance(c, _P) else c for c in ctxs])
+    b = _P()
+    _bcheck(None, load().echo_batch_create(arr, len(ctxs), ctypes.byref(b)))
+    return b
+
+
+def echo_batch_workspace_bytes(b) -> int:
+    return int(load().echo_batch_workspace_bytes(b))
+
+
+def echo_batch_bind(b, dev_ptr, nbytes, stream_handle):
+    _bcheck(b, load().echo_batch_bind(b, _P(dev_ptr), ctypes.c_size_t(nbytes), _P(stream_handle)))
+
+
+def echo_batch_config(b, tile, blocks_per_sm, dynamic_queue):
+    _bcheck(b, load().echo_batch_config(b, int(tile), int(blocks_per_sm), int(dynamic_queue)))
+
+
+def echo_batch_max_blocks_per_sm(b) -> int:
+    return int(load().echo_batch_max_blocks_per_sm(b))
+
+
+def echo_batch_graph(b, enable):
+    _bcheck(b, load().echo_batch_graph(b, 1 if enable else 0))
+
+
+def echo_batch_step(b, dt=0.0):
+    _bcheck(b, load().echo_batch_step(b, float(dt)))
+
+
+def echo_batch_destroy(b):
+    load().echo_batch_destroy(b)
 
 
 def echo_last_error(ctx) -> str:

@@ -16,33 +16,7 @@
 
 using namespace echo;
 
-struct echo_ctx {
-    echo_grid grid;
-    echo_metric metric;
-    echo_eos eos;
-    int precision;
-    double cfl;
-    Geom geo;
-    Phys ph;
-    size_t ws_need = 0;
-    char *ws = nullptr;
-    cudaStream_t stream = nullptr;
-    bool bound = false;
-    bool have_state = false;
-    Arrays<double> ad;
-    Arrays<float> af;
-    size_t nstate = 0;
-    size_t staging_count = 0;
-    int nblk_red = 0;
-    std::string err;
-    int c2p_guess = 0;        // 0 previous-stage Z, 1 c2p-guess network
-    bool mlp_loaded = false;
-    // per-kernel timing (echo_profile)
-    bool prof = false;
-    std::vector<cudaEvent_t> ev;      // pool, pairs (start, end)
-    std::vector<int> ev_kind;         // kernel class of each recorded pair
-    size_t ev_used = 0;               // pairs in use
-};
+#include "echo_ctx.h"
 
 namespace {
 

@@ -42,6 +42,50 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
+// ------------------------------------------------------------------ ghost fill
+
+// Fill the ghost slab of axis d for a list of arrays.  Thread (s, t1, t2):
+// s in [0, 2 NG) selects the ghost layer (lower layers 0..NG-1, upper
+// n+NG..n+2NG-1), t1/t2 run over the full padded extent of the other axes.
+template <typename R>
+__device__ __forceinline__ void fill_body(const Geom &g, int d, const FillList<R> &L, long long t)
+{
+    const int d1 = d == 0 ? 1 : 0;
+    const int d2 = d == 2 ? 1 : 2;
+    if (t >= (long long)2 * NG * g.np[d1] * g.np[d2])
+        return;
+    const int s = (int)(t % (2 * NG));
+    const int t1 = (int)((t / (2 * NG)) % g.np[d1]);
+    const int t2 = (int)(t / (2 * NG) / g.np[d1]);
+    const int id_d = s < NG ? s : g.n[d] + s;
+    int ijk[3];
+    ijk[d] = id_d;
+    ijk[d1] = t1;
+    ijk[d2] = t2;
+    const long long dst = gidx(g, ijk[0], ijk[1], ijk[2]);
+    const long long sd = d == 0 ? 1LL : (d == 1 ? g.px : g.pxy);
+    for (int a = 0; a < L.count; ++a) {
+        bool flip;
+        const int face = L.face[a] == d ? 1 : 0;
+        const int src = bc_src(id_d, g.n[d], face, g.bc[2 * d], g.bc[2 * d + 1], flip);
+        if (src == id_d)
+            continue;
+        R val = R(0);
+        if (src >= 0) {
+            val = L.a[a][dst + (long long)(src - id_d) * sd];
+            if (flip && L.comp[a] == d)
+                val = -val;
+        }
+        L.a[a][dst] = val;
+    }
+}
+
+template <typename R>
+__global__ void k_fill(Geom g, int d, FillList<R> L)
+{
+    fill_body<R>(g, d, L, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // ------------------------------------------------------------------ c2p
 
 // Conservative-to-primitive inversion of every owned cell (FP64 Newton);
@@ -56,23 +100,24 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 // in shared memory); Newton from that guess is capped at 8 iterations and
 // falls back to the cell's previous-stage Z if it has not converged
 // (counted in mlp_fallback).
+// Body over the linear index t of the owned cells (x fastest); every lane of
+// a warp must call it (warp-level counter reductions).  mlp_sm: the network
+// block in shared memory when MLP.
 template <int MK, typename R, bool MLP>
-__global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate)
+__device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mode,
+                                         int want_rate, long long t, const float *mlp_sm)
 {
-    const int i = NG + blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = NG + blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = NG + blockIdx.z;
-    const bool live = i < NG + g.n[0] && j < NG + g.n[1] && k < NG + g.n[2];
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    const bool live = t < ncell;
+    int i = NG, j = NG, k = NG;
+    if (live) {
+        i = NG + (int)(t % g.n[0]);
+        const long long r = t / g.n[0];
+        j = NG + (int)(r % g.n[1]);
+        k = NG + (int)(r / g.n[1]);
+    }
     double rate = 0.0;
     unsigned long long its = 0, calls = 0, fails = 0, floors = 0, mfb = 0;
-    extern __shared__ float4 mlp_smem4[];
-    if constexpr (MLP) {
-        float *Ps = reinterpret_cast<float *>(mlp_smem4);
-        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-        for (int q = tid; q < MLP_BLOCK; q += blockDim.x * blockDim.y)
-            Ps[q] = A.mlp[q];
-        __syncthreads();
-    }
     if (live) {
         const long long id = gidx(g, i, j, k);
         double isg = 1.0, sg = 1.0;
@@ -96,7 +141,7 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
                 mlp_features(Dc, S, tc, B, sg, MKS<double>(*mp), f);
             else
                 mlp_features(Dc, S, tc, B, 1.0, MFlat<double>(), f);
-            mlp_infer(reinterpret_cast<const float *>(mlp_smem4), f, o);
+            mlp_infer(mlp_sm, f, o);
             const double Wg = exp((double)o[0]), pD = exp((double)o[1]);
             const double z0 = Dc * Wg * (1.0 + ph.gr * pD * Wg);
             if constexpr (MK == 1)
@@ -181,6 +226,21 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
         if (want_rate && rate > 0.0)
             atomicMax(&A.scal->rate_bits, (unsigned long long)__double_as_longlong(rate));
     }
+}
+
+template <int MK, typename R, bool MLP>
+__global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate)
+{
+    extern __shared__ float4 mlp_smem4[];
+    const float *sm = nullptr;
+    if constexpr (MLP) {
+        float *Ps = reinterpret_cast<float *>(mlp_smem4);
+        for (int q = threadIdx.x; q < MLP_BLOCK; q += blockDim.x)
+            Ps[q] = A.mlp[q];
+        __syncthreads();
+        sm = Ps;
+    }
+    c2p_body<MK, R, MLP>(g, ph, A, guess_mode, want_rate, (long long)blockIdx.x * blockDim.x + threadIdx.x, sm);
 }
 
 // ------------------------------------------------------------------ limiter
@@ -268,13 +328,13 @@ __device__ __forceinline__ const R *pick7(const Arrays<R> &A, const int qs[7], i
 }
 
 template <int D, int MK, typename R>
-__global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
+__device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const Arrays<R> &A, long long t,
+                                           LimScratch<R> &lsm)
 {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     int cnt[3] = {g.np[0], g.np[1], g.np[2]};
     cnt[D] = g.n[D] + 1;
     const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = t < tot;
     int ijk[3];
     {
@@ -307,7 +367,6 @@ __global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
         }
     }
     // limiter on the rejected items, compacted across the warp
-    __shared__ LimScratch<T> lsm;
     compact_limit<T>(pend, id, lsm, [&](long long ido, int m, int side) -> T {
         const R *__restrict__ a = pick7(A, qs, m);
         T q[6];
@@ -409,6 +468,13 @@ __global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
     A.fv[D][3][id] = PR[1 + T1];
 }
 
+template <int D, int MK, typename R>
+__global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
+{
+    __shared__ LimScratch<R> lsm;
+    faces_body<D, MK, R>(g, ph, A, (long long)blockIdx.x * blockDim.x + threadIdx.x, lsm);
+}
+
 // ------------------------------------------------------------------ EMF
 
 // UCT-HLL EMF on the edges along E; (a, b, E) cyclic.  The edge with index
@@ -440,13 +506,12 @@ __device__ __forceinline__ void emf_pick(const EmfSrc<R> &S, int m, const R *&p,
 }
 
 template <int E, int MK, typename R>
-__global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
+__device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long long t, LimScratch<R> &lsm)
 {
     constexpr int a = (E + 1) % 3, b = (E + 2) % 3;
     int cnt[3] = {g.n[0] + 1, g.n[1] + 1, g.n[2] + 1};
     cnt[E] = g.n[E];
     const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = t < tot;
     long long id;
     int ei, ej;
@@ -486,7 +551,6 @@ __global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
             pend |= (okR ? 0u : 1u) << (2 * m + 1);
         }
     }
-    __shared__ LimScratch<T> lsm;
     compact_limit<T>(pend, id, lsm, [&](long long ido, int m, int side) -> T {
         const R *p;
         long long st;
@@ -554,6 +618,13 @@ __global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
     const T db = is_pos(sB) ? apb * amb / sB : T(0);
     A.E[E][id] = wLL * Est[0][0] + wLR * Est[0][1] + wRL * Est[1][0] + wRR * Est[1][1]
                  + da * (Bb[1] - Bb[0]) - db * (Ba[1] - Ba[0]);
+}
+
+template <int E, int MK, typename R>
+__global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
+{
+    __shared__ LimScratch<R> lsm;
+    emf_body<E, MK, R>(g, A, (long long)blockIdx.x * blockDim.x + threadIdx.x, lsm);
 }
 
 // ------------------------------------------------------------------ sources
@@ -625,14 +696,18 @@ __device__ __forceinline__ void ks_sources(const T P[8], T gr, const MetPt &mp, 
 //   stage 2: U = 1/3 U0 + 2/3 (U + dt L).
 // stage < 0: write L in host layout to Lout instead (faces NG..NG+n along
 // their axis; a face that is not evolved, e.g. on the polar axis, gets 0).
+// Body over the linear index t of the (n0+1)(n1+1)(n2+1) box of cells and
+// faces, x fastest.
 template <int MK, typename R>
-__global__ void __launch_bounds__(256) k_update(Geom g, Phys ph, Arrays<R> A, int stage, double *Lout)
+__device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const Arrays<R> &A, int stage,
+                                            double *Lout, long long t)
 {
-    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
-    const int tj = blockIdx.y * blockDim.y + threadIdx.y;
-    const int tk = blockIdx.z;
-    if (ti > g.n[0] || tj > g.n[1] || tk > g.n[2])
+    const long long e0 = g.n[0] + 1, e1 = g.n[1] + 1;
+    if (t >= e0 * e1 * (g.n[2] + 1))
         return;
+    const int ti = (int)(t % e0);
+    const int tj = (int)((t / e0) % e1);
+    const int tk = (int)(t / (e0 * e1));
     const int i = NG + ti, j = NG + tj, k = NG + tk;
     const long long id = gidx(g, i, j, k);
     const long long st[3] = {1LL, g.px, g.pxy};
@@ -719,6 +794,12 @@ __global__ void __launch_bounds__(256) k_update(Geom g, Phys ph, Arrays<R> A, in
         }
         off += (long long)e[0] * e[1] * e[2];
     }
+}
+
+template <int MK, typename R>
+__global__ void __launch_bounds__(256) k_update(Geom g, Phys ph, Arrays<R> A, int stage, double *Lout)
+{
+    update_body<MK, R>(g, ph, A, stage, Lout, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Primitives (host layout, 5 arrays) + face B~ (already in U, ghosts
@@ -809,44 +890,6 @@ __global__ void k_mlp_dataset(Geom g, Arrays<R> A, float *X, float *Y, long long
 }
 
 #ifdef ECHO_COMMON_KERNELS
-// ------------------------------------------------------------------ ghost fill
-
-// Fill the ghost slab of axis d for a list of arrays.  Thread (s, t1, t2):
-// s in [0, 2 NG) selects the ghost layer (lower layers 0..NG-1, upper
-// n+NG..n+2NG-1), t1/t2 run over the full padded extent of the other axes.
-template <typename R>
-__global__ void k_fill(Geom g, int d, FillList<R> L)
-{
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t1 = blockIdx.y * blockDim.y + threadIdx.y;
-    const int t2 = blockIdx.z;
-    const int d1 = d == 0 ? 1 : 0;
-    const int d2 = d == 2 ? 1 : 2;
-    if (s >= 2 * NG || t1 >= g.np[d1] || t2 >= g.np[d2])
-        return;
-    const int id_d = s < NG ? s : g.n[d] + s;
-    int ijk[3];
-    ijk[d] = id_d;
-    ijk[d1] = t1;
-    ijk[d2] = t2;
-    const long long dst = gidx(g, ijk[0], ijk[1], ijk[2]);
-    const long long sd = d == 0 ? 1LL : (d == 1 ? g.px : g.pxy);
-    for (int a = 0; a < L.count; ++a) {
-        bool flip;
-        const int face = L.face[a] == d ? 1 : 0;
-        const int src = bc_src(id_d, g.n[d], face, g.bc[2 * d], g.bc[2 * d + 1], flip);
-        if (src == id_d)
-            continue;
-        R val = R(0);
-        if (src >= 0) {
-            val = L.a[a][dst + (long long)(src - id_d) * sd];
-            if (flip && L.comp[a] == d)
-                val = -val;
-        }
-        L.a[a][dst] = val;
-    }
-}
-
 // ------------------------------------------------------------------ scalars
 
 __global__ void k_step_begin(DevScalars *s, double dt_fixed)

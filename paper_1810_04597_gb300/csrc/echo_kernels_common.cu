@@ -17,9 +17,8 @@ void launch_fill(const Geom &g, const FillList<R> &L, cudaStream_t s)
 {
     for (int d = 0; d < 3; ++d) {
         const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
-        dim3 blk(8, 32, 1);
-        dim3 grd(1, (unsigned)((g.np[d1] + 31) / 32), (unsigned)g.np[d2]);
-        k_fill<R><<<grd, blk, 0, s>>>(g, d, L);
+        const long long tot = (long long)2 * NG * g.np[d1] * g.np[d2];
+        k_fill<R><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, d, L);
     }
 }
 

@@ -1,0 +1,67 @@
+"""Batch of independent runs in one persistent cooperative kernel per RK
+stage: the same results as the runs advanced one at a time (the same
+device bodies compute the same arithmetic, so bitwise in FP64), for every
+scheduling configuration and with CUDA-graph replay."""
+import numpy as np
+import pytest
+
+from paper_1810_04597_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def _tori(precision=64):
+    from paper_1810_04597_gb300.echo import Solver
+    probs = [inputs.fm_torus((32, 16, 8), spin=0.5, seed=1), inputs.fm_torus((48, 24, 8), spin=0.9, seed=2),
+             inputs.fm_torus((40, 20, 12), spin=0.0, beta=10.0, seed=3)]
+    out = []
+    for p in probs:
+        s = Solver(p, precision=precision)
+        s.set_prims()
+        out.append(s)
+    return out
+
+
+@pytest.mark.parametrize("tile,dyn,graph", [(256, True, False), (128, False, False), (512, True, True)])
+def test_batch_equals_runs_one_at_a_time(tile, dyn, graph):
+    from paper_1810_04597_gb300.batch import Batch
+    single = _tori()
+    for s in single:
+        for _ in range(3):
+            s.step()
+    ref = [s.get_state() for s in single]
+    runs = _tori()
+    b = Batch(runs)
+    b.configure(tile=tile, dynamic=dyn)
+    b.graph(graph)
+    for _ in range(3):
+        b.step()
+    for r, s in zip(ref, runs):
+        got = s.get_state()
+        assert np.array_equal(got, r), np.max(np.abs(got - r))
+
+
+def test_batch_flat_fixed_dt_and_counters():
+    from paper_1810_04597_gb300.batch import Batch
+    from paper_1810_04597_gb300.echo import Solver
+    probs = [inputs.smooth_box(16, seed=s) for s in (1, 2)] + [inputs.sweep_box(24, seed=3)]
+    a = [Solver(p) for p in probs]
+    c = [Solver(p) for p in probs]
+    for s in a + c:
+        s.set_prims()
+    for s in a:
+        s.step(1e-3)
+        s.step(1e-3)
+    b = Batch(c)
+    b.step(1e-3)
+    b.step(1e-3)
+    for x, y in zip(a, c):
+        assert np.array_equal(x.get_state(), y.get_state())
+        assert x.counters()["c2p_calls"] == y.counters()["c2p_calls"]
