@@ -369,6 +369,7 @@ def run_ours(args, world, rank, local, dist):
     if fin64 is not None:
         s32 = Solver(prob, precision=32, device=str(dev))
         s32.set_prims()
+        s32.set_c2p_guess(4)
         for _ in range(args.warmup):
             s32.step()
         torch.cuda.synchronize()
@@ -396,10 +397,15 @@ def run_ours(args, world, rank, local, dist):
             "ms_per_step": ms32 / args.steps, "speedup_vs_fp64": ms / ms32,
             "l1_rel_vs_fp64_gpu": l1, "max_l1": max(l1.values()),
             "mean_newton_iters": t32["c2p_iters"] / max(t32["c2p_calls"], 1),
+            "c2p_guess": "previous-stage Z refined by FP32 Newton steps; FP64 Newton judges",
             "note": "FP32 storage/stencil, FP64 c2p and reductions; same input, same step count"}}
         del s32
+        mlp_state = None
         if not args.no_mlp:
-            variants["fp32_mlp"] = run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms)
+            variants["fp32_mlp"], mlp_state = run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds,
+                                                              ms)
+        if not args.no_sweep:
+            variants["sweep_batch"] = run_sweep_variant(args, dev, world, dist, mlp_state)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -443,7 +449,7 @@ def run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms64):
     s = Solver(prob, precision=32, device=str(dev))
     s.set_prims()
     s.mlp_load(state)
-    s.set_c2p_guess(1)
+    s.set_c2p_guess(5)
     for _ in range(args.warmup):
         s.step()
     torch.cuda.synchronize()
@@ -471,9 +477,79 @@ def run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms64):
            "guess_rel_err_median_heldout": float(np.median(err)),
            "guess_rel_err_p99_heldout": float(np.quantile(err, 0.99)),
            "train_seconds": t_train, "train_final_loss": float(losses[-50:].mean().item()),
-           "note": "FP32 bulk; c2p guess from the network trained on the GPU (untimed); FP64 Newton judges"}
+           "c2p_guess": "network (trained on the GPU, untimed) refined by FP32 Newton steps; FP64 Newton judges",
+           "note": "FP32 bulk"}
     del s
-    return out
+    return out, state
+
+
+def run_sweep_variant(args, dev, world, dist, mlp_state):
+    """The 16-run Fishbone-Moncrief torus sweep (uneven sizes 64x32x32 ..
+    192x96x96, spins 0..0.98, beta 10/100), FP32 bulk + network c2p guess,
+    advanced as one batch (schedule and tiles autotuned over persistent
+    cooperative, per-phase and run-major, replayed from one CUDA graph) and,
+    for comparison, one run at a time without a graph."""
+    import torch
+    from paper_1810_04597_gb300.batch import MODE_NAMES, Batch, autotune, sweep_runs
+
+    def make():
+        sol = sweep_runs(precision=32, device=str(dev))
+        for x in sol:
+            if mlp_state is not None:
+                x.mlp_load(mlp_state)
+                x.set_c2p_guess(5)
+            else:
+                x.set_c2p_guess(4)
+        return sol
+
+    sol = make()
+    zones = sum(x.ncells for x in sol)
+    b = Batch(sol)
+    tune = autotune(b, reps=2, cache=False, graph=True)
+    for _ in range(args.warmup):
+        b.step()
+    torch.cuda.synchronize()
+    c0 = [x.counters() for x in sol]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    for _ in range(args.steps):
+        b.step()
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    msb = e0.elapsed_time(e1)
+    c1 = [x.counters() for x in sol]
+    calls = sum(y["c2p_calls"] - x["c2p_calls"] for x, y in zip(c0, c1))
+    fb = sum(y["mlp_fallback"] - x["mlp_fallback"] for x, y in zip(c0, c1))
+    fl = sum(y["floor_hits"] - x["floor_hits"] for x, y in zip(c0, c1))
+    its = sum(y["c2p_iters"] - x["c2p_iters"] for x, y in zip(c0, c1))
+    b.close()
+    del sol
+    # the same sweep, one run at a time (a launch sequence per run and stage)
+    sol = make()
+    for _ in range(args.warmup):
+        for x in sol:
+            x.step()
+    torch.cuda.synchronize()
+    e0.record(torch.cuda.current_stream())
+    for _ in range(args.steps):
+        for x in sol:
+            x.step()
+    e1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    mss = e0.elapsed_time(e1)
+    del sol
+    return {"value": world * zones * args.steps / (max_over_ranks(dist, msb) * 1e-3) / 1e6, "unit": UNIT,
+            "zones": zones, "runs": 16, "ms_per_step": msb / args.steps,
+            "one_at_a_time_value": zones * args.steps / (mss * 1e-3) / 1e6,
+            "batch_speedup": mss / msb,
+            "autotune": {"best": {k: tune[k] for k in ("mode", "tile", "blocks_per_sm", "dynamic", "branches", "ms")},
+                         "best_per_mode_ms": {MODE_NAMES[m]: min(c["ms"] for c in tune["candidates"] if c["mode"] == m)
+                                              for m in MODE_NAMES}},
+            "mean_newton_iters": its / max(calls, 1), "mlp_fallback_per_call": fb / max(calls, 1),
+            "floor_hits_per_call": fl / max(calls, 1),
+            "note": "FP32 bulk + network c2p guess, per-run CFL dt, whole step replayed from one CUDA graph"}
+
 
 
 def main():
@@ -488,6 +564,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-mlp", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     world, rank, local = dist_info()

@@ -139,7 +139,7 @@ int echo_get_z(echo_ctx *ctx, double *Z, int on_device);
 /* Conservative-to-primitive inversion of the current state on every owned
  * cell.  guess_mode: 0 = the stored Z of the cell (previous stage), 1 = the
  * c2p-guess network (see below), 2 = cold guess (Z = 0, replaced by the
- * admissibility rule).  If stats is non-NULL
+ * admissibility rule); adding 4 refines the guess in FP32 first.  If stats is non-NULL
  * the call synchronises and fills the counters and dt_cfl of stats (the
  * other fields are left untouched) and returns ECHO_EC2P if any cell failed. */
 int echo_c2p(echo_ctx *ctx, int guess_mode, echo_totals *stats);
@@ -216,8 +216,10 @@ int echo_mlp_dataset(echo_ctx *ctx, float *X, float *Y, long long capacity, long
  * the context. */
 int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
 
-/* Newton guess used by echo_step/echo_rhs/echo_reduce: 0 previous-stage Z
- * (default), 1 network (requires echo_mlp_load). */
+/* Newton guess used by echo_step/echo_rhs: 0 previous-stage Z (default),
+ * 1 network (requires echo_mlp_load); adding 4 first refines that guess by
+ * up to four Newton steps of the same residual in FP32 (the FP64 iterations
+ * that follow still decide convergence). */
 int echo_set_c2p_guess(echo_ctx *ctx, int mode);
 
 /* Copy the cumulative counters (c2p_iters, c2p_calls, c2p_fail, floor_hits,
@@ -228,15 +230,16 @@ int echo_counters(echo_ctx *ctx, echo_totals *out);
 /* ---- batch of independent runs (parameter sweeps) ----
  * The paper motivates the cost of exploring many parameters; a batch advances
  * up to ECHO_BATCH_MAXRUNS independent runs (same metric kind, precision,
- * adiabatic index and CFL number; sizes may differ) with ONE persistent
- * cooperative kernel per SSP-RK3 stage.  Each stage's phases (ghost fills,
+ * adiabatic index and CFL number; sizes may differ), by default with ONE
+ * persistent cooperative kernel per SSP-RK3 stage.  Each stage's phases (ghost fills,
  * c2p, faces, EMFs, update) are cut into tiles over all runs and taken by
  * the resident blocks round-robin or from an atomic queue; grid-wide
  * barriers separate dependent phases (the cooperative launch keeps every
  * block resident, so they cannot deadlock).  Every run keeps its own CFL dt.
  * The runs must be bound contexts with a state; their workspaces and
- * counters are the runs' own.  If run 0 uses the network guess
- * (echo_set_c2p_guess 1), all runs use run 0's network. */
+ * counters are the runs' own.  In schedules 0 and 1, if run 0 uses the
+ * network guess, all runs use run 0's guess mode and network; schedule 2
+ * uses each run's own. */
 #define ECHO_BATCH_MAXRUNS 32
 typedef struct echo_batch echo_batch;
 
@@ -251,7 +254,19 @@ int echo_batch_bind(echo_batch *batch, void *dev_workspace, size_t bytes, void *
  * 1 atomic queue).  Default after bind: 256, the maximum, 1. */
 int echo_batch_config(echo_batch *batch, int tile, int blocks_per_sm, int dynamic_queue);
 int echo_batch_max_blocks_per_sm(echo_batch *batch);
-/* 1: capture one whole step (three cooperative launches) into a CUDA graph
+/* Schedule: 0 (default) one persistent cooperative kernel per stage;
+ * 1 one ordinary launch per phase over all runs' tiles (each phase with its
+ * own register budget; blocks_per_sm and the queue kind do not apply);
+ * 2 run-major: each run's own launch sequence (as echo_step) in turn, so a
+ * run's working set stays in L2 across its phases (tile, blocks_per_sm and
+ * queue kind do not apply).  ECHO_EINVAL for any other value. */
+int echo_batch_mode(echo_batch *batch, int mode);
+/* Schedule 2 only: spread the runs over `branches` (1 .. number of runs)
+ * concurrent streams forked from and joined back into the batch stream (in a
+ * captured graph they become parallel branches), runs assigned
+ * longest-first by zone count.  Default 1 (all runs on the batch stream). */
+int echo_batch_branches(echo_batch *batch, int branches);
+/* 1: capture one whole step (every launch of the schedule) into a CUDA graph
  * on first use and replay it; recaptured when dt or the configuration
  * changes.  Needs a created stream (ECHO_EINVAL on the legacy stream). */
 int echo_batch_graph(echo_batch *batch, int enable);
@@ -259,6 +274,13 @@ int echo_batch_graph(echo_batch *batch, int enable);
 int echo_batch_step(echo_batch *batch, double dt);
 const char *echo_batch_last_error(const echo_batch *batch);
 void echo_batch_destroy(echo_batch *batch);
+
+/* Self-check of the library's integer-pipe float <-> double conversions
+ * against the hardware casts on n hashed test values (all float classes,
+ * doubles over and beyond the float range, exact rounding ties): adds the
+ * number of mismatches to *dev_mismatch (device, caller-zeroed). */
+int echo_selftest_conversions(long long n, unsigned long long seed, unsigned long long *dev_mismatch,
+                              void *cuda_stream);
 
 /* Kernel classes timed by the profiling facility below. */
 #define ECHO_K_FILL_FACES 0

@@ -93,12 +93,15 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "echo_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "echo_counters": (ctypes.c_int, [_P, ctypes.POINTER(echo_totals)]),
+    "echo_selftest_conversions": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
     "echo_batch_workspace_bytes": (ctypes.c_size_t, [_P]),
     "echo_batch_bind": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
     "echo_batch_config": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "echo_batch_max_blocks_per_sm": (ctypes.c_int, [_P]),
     "echo_batch_graph": (ctypes.c_int, [_P, ctypes.c_int]),
+    "echo_batch_mode": (ctypes.c_int, [_P, ctypes.c_int]),
+    "echo_batch_branches": (ctypes.c_int, [_P, ctypes.c_int]),
     "echo_batch_step": (ctypes.c_int, [_P, ctypes.c_double]),
     "echo_batch_last_error": (ctypes.c_char_p, [_P]),
     "echo_batch_destroy": (None, [_P]),
@@ -399,6 +402,14 @@ def echo_batch_max_blocks_per_sm(b) -> int:
     return int(load().echo_batch_max_blocks_per_sm(b))
 
 
+def echo_batch_mode(b, mode):
+    _bcheck(b, load().echo_batch_mode(b, int(mode)))
+
+
+def echo_batch_branches(b, branches):
+    _bcheck(b, load().echo_batch_branches(b, int(branches)))
+
+
 def echo_batch_graph(b, enable):
     _bcheck(b, load().echo_batch_graph(b, 1 if enable else 0))
 
@@ -409,6 +420,11 @@ def echo_batch_step(b, dt=0.0):
 
 def echo_batch_destroy(b):
     load().echo_batch_destroy(b)
+
+
+def echo_selftest_conversions(n, seed, dev_counter, stream_handle: int = 0):
+    _plain(load().echo_selftest_conversions(int(n), ctypes.c_ulonglong(seed), _P(_dev_any(dev_counter, "counter")),
+                                            _P(stream_handle)), "echo_selftest_conversions")
 
 
 def echo_last_error(ctx) -> str:

@@ -1,6 +1,9 @@
-"""A batch of independent runs advanced by one persistent cooperative kernel
-per SSP-RK3 stage (see ``echo_batch_*`` in include/echo.h), and the tile
-autotuner.  Torch supplies the batch workspace and the stream only."""
+"""A batch of independent runs advanced together (see ``echo_batch_*`` in
+include/echo.h) under one of three schedules -- one persistent cooperative
+kernel per SSP-RK3 stage, one launch per phase over all runs, or each run's
+own launch sequence in turn -- optionally replayed from one CUDA graph, and
+the autotuner that picks the schedule and its tiles.  Torch supplies the
+batch workspace and the stream only."""
 from __future__ import annotations
 
 import json
@@ -11,6 +14,9 @@ from .echo import Solver
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 TUNE_CACHE = os.path.join(_HERE, "_build", "batch_autotune.json")
+
+PERSISTENT, PHASED, RUN_MAJOR = 0, 1, 2
+MODE_NAMES = {PERSISTENT: "persistent", PHASED: "phased", RUN_MAJOR: "run_major"}
 
 
 class Batch:
@@ -34,11 +40,19 @@ class Batch:
     def zones(self) -> int:
         return sum(s.ncells for s in self.solvers)
 
-    def configure(self, tile=256, blocks_per_sm=None, dynamic=True):
+    def configure(self, tile=256, blocks_per_sm=None, dynamic=True, mode=PERSISTENT, branches=1):
+        """`mode`: PERSISTENT, PHASED or RUN_MAJOR; tile, blocks per SM and the
+        queue kind apply to the first two, `branches` (concurrent streams) to
+        RUN_MAJOR."""
+        import torch
         mb = _lib.echo_batch_max_blocks_per_sm(self.b)
         bps = mb if blocks_per_sm is None else min(blocks_per_sm, mb)
         _lib.echo_batch_config(self.b, tile, bps, 1 if dynamic else 0)
-        self.config = dict(tile=tile, blocks_per_sm=bps, dynamic=bool(dynamic))
+        _lib.echo_batch_mode(self.b, int(mode))
+        with torch.cuda.device(self.device):
+            _lib.echo_batch_branches(self.b, min(int(branches), len(self.solvers)))
+        self.config = dict(tile=tile, blocks_per_sm=bps, dynamic=bool(dynamic), mode=MODE_NAMES[int(mode)],
+                           branches=int(branches))
 
     def graph(self, enable=True):
         _lib.echo_batch_graph(self.b, enable)
@@ -79,44 +93,50 @@ def sweep_runs(scale=1, precision=32, device="cuda:0", steps=100):
     return sol
 
 
-def autotune(batch: Batch, tiles=(128, 256, 512, 1024), queue=(True, False), reps=2, key=None, cache=True):
-    """Time `reps` steps for every (tile, blocks per SM, queue kind) and keep
-    the fastest; the choice is cached per device and batch signature.  The
-    runs' states advance while tuning."""
+def autotune(batch: Batch, tiles=(128, 256, 512, 1024), queue=(True, False), reps=2, key=None, cache=True,
+             graph=True):
+    """Time `reps` steps (replayed from a graph when `graph`) for every
+    schedule -- persistent with each (tile, blocks per SM, queue kind), phased
+    with each tile, run-major -- and keep the fastest; the choice is cached
+    per device and batch signature.  The runs' states advance while tuning."""
     import torch
     mb = _lib.echo_batch_max_blocks_per_sm(batch.b)
-    bpss = sorted({mb, max(1, mb // 2)})
+    bpss = sorted({mb, max(1, mb // 2), min(mb, 2), min(mb, 3)})
     dev = torch.cuda.get_device_name(batch.solvers[0].device)
     sig = key or "|".join("x".join(str(v) for v in s.problem.n) for s in batch.solvers)
-    ck = f"{dev}|p{batch.solvers[0].precision}|{sig}"
+    ck = f"{dev}|p{batch.solvers[0].precision}|g{int(graph)}|{sig}"
     if cache and os.path.exists(TUNE_CACHE):
         try:
             db = json.load(open(TUNE_CACHE))
             if ck in db:
                 c = db[ck]
-                batch.configure(c["tile"], c["blocks_per_sm"], c["dynamic"])
+                batch.configure(c["tile"], c["blocks_per_sm"], c["dynamic"], c["mode"], c["branches"])
+                batch.graph(graph)
                 return dict(c, cached=True)
         except Exception:
             pass
     best = None
     results = []
-    for tile in tiles:
-        for bps in bpss:
-            for dyn in queue:
-                batch.configure(tile, bps, dyn)
-                batch.step()                       # warm
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(batch.stream)
-                for _ in range(reps):
-                    batch.step()
-                e1.record(batch.stream)
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / reps
-                results.append(dict(tile=tile, blocks_per_sm=bps, dynamic=dyn, ms=ms))
-                if best is None or ms < best["ms"]:
-                    best = results[-1]
-    batch.configure(best["tile"], best["blocks_per_sm"], best["dynamic"])
+    nr = len(batch.solvers)
+    cands = [(tile, bps, dyn, PERSISTENT, 1) for tile in tiles for bps in bpss for dyn in queue]
+    cands += [(tile, mb, True, PHASED, 1) for tile in tiles]
+    cands += [(256, mb, True, RUN_MAJOR, k) for k in sorted({1, 2, 4, 8, nr}) if k <= nr]
+    batch.graph(graph)
+    for tile, bps, dyn, mode, br in cands:
+        batch.configure(tile, bps, dyn, mode, br)
+        batch.step()                       # warm (and capture)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(batch.stream)
+        for _ in range(reps):
+            batch.step()
+        e1.record(batch.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        results.append(dict(tile=tile, blocks_per_sm=bps, dynamic=dyn, mode=mode, branches=br, ms=ms))
+        if best is None or ms < best["ms"]:
+            best = results[-1]
+    batch.configure(best["tile"], best["blocks_per_sm"], best["dynamic"], best["mode"], best["branches"])
     out = dict(best, cached=False, candidates=results)
     if cache:
         os.makedirs(os.path.dirname(TUNE_CACHE), exist_ok=True)
@@ -126,6 +146,6 @@ def autotune(batch: Batch, tiles=(128, 256, 512, 1024), queue=(True, False), rep
                 db = json.load(open(TUNE_CACHE))
             except Exception:
                 db = {}
-        db[ck] = {k: best[k] for k in ("tile", "blocks_per_sm", "dynamic", "ms")}
+        db[ck] = {k: best[k] for k in ("tile", "blocks_per_sm", "dynamic", "mode", "branches", "ms")}
         json.dump(db, open(TUNE_CACHE, "w"), indent=1)
     return out

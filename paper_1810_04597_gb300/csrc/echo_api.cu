@@ -164,7 +164,7 @@ void enqueue_rhs_pass(echo_ctx *c, int stage, double *Lout, bool want_rate, doub
     Arrays<R> &A = arrays<R>(c);
     cudaStream_t s = c->stream;
     PROF(ECHO_K_FILL_FACES, launch_fill<R>(c->geo, face_list(A), s));
-    PROF(ECHO_K_C2P, (launch_c2p<MK, R>(c->geo, c->ph, A, c->c2p_guess == 1 ? 1 : 0, want_rate ? 1 : 0, s)));
+    PROF(ECHO_K_C2P, (launch_c2p<MK, R>(c->geo, c->ph, A, c->c2p_guess, want_rate ? 1 : 0, s)));
     if (want_rate)
         PROF(ECHO_K_SCALARS, launch_set_dt(A.scal, c->cfl, dt_fixed <= 0.0 ? 1 : 0, s));
     PROF(ECHO_K_FILL_PRIMS, launch_fill<R>(c->geo, prim_list(A), s));
@@ -293,6 +293,10 @@ int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *
     c->ph.gr = eos->gamma / (eos->gamma - 1.0);
     c->ph.gm1g = (eos->gamma - 1.0) / eos->gamma;
     c->ph.cfl = cfl;
+    c->ph.gamma_f = (float)c->ph.gamma;
+    c->ph.gr_f = (float)c->ph.gr;
+    for (int d = 0; d < 3; ++d)
+        g.idx_f[d] = (float)g.idx[d];
     const size_t N = (size_t)cells;
     c->nstate = 5 * N + (size_t)g.n[2] * g.n[1] * (g.n[0] + 1) + (size_t)g.n[2] * (g.n[1] + 1) * g.n[0]
                 + (size_t)(g.n[2] + 1) * g.n[1] * g.n[0];
@@ -482,9 +486,9 @@ int echo_c2p(echo_ctx *c, int guess_mode, echo_totals *stats)
     int rc = require_bound(c, true);
     if (rc)
         return rc;
-    if (guess_mode < 0 || guess_mode > 2)
-        return fail(c, ECHO_EINVAL, "guess_mode must be 0 (previous Z), 1 (network) or 2 (cold)");
-    if (guess_mode == 1 && !c->mlp_loaded)
+    if (guess_mode < 0 || guess_mode > 6 || guess_mode == 3)
+        return fail(c, ECHO_EINVAL, "guess_mode: 0 previous Z, 1 network, 2 cold, +4 FP32 refinement");
+    if ((guess_mode & 3) == 1 && !c->mlp_loaded)
         return fail(c, ECHO_ESTATE, "no c2p-guess network loaded: call echo_mlp_load first");
     rc = ECHO_DISPATCH(c, op_c2p, guess_mode);
     if (rc || !stats)
@@ -530,6 +534,20 @@ int echo_step(echo_ctx *c, double dt)
     if (rc)
         return rc;
     return ECHO_DISPATCH(c, op_step, dt);
+}
+
+// Enqueue one step of context c on another stream (used by the run-major
+// batch schedule); per-kernel timing is off while the batch records.
+int echo_internal_enqueue_step(echo_ctx *c, double dt, cudaStream_t s)
+{
+    cudaStream_t own = c->stream;
+    const bool prof = c->prof;
+    c->stream = s;
+    c->prof = false;
+    const int rc = ECHO_DISPATCH(c, op_step, dt);
+    c->stream = own;
+    c->prof = prof;
+    return rc;
 }
 
 int echo_reduce(echo_ctx *c, echo_totals *out)
@@ -613,9 +631,9 @@ int echo_set_c2p_guess(echo_ctx *c, int mode)
 {
     if (!c)
         return ECHO_EINVAL;
-    if (mode != 0 && mode != 1)
-        return fail(c, ECHO_EINVAL, "c2p guess mode must be 0 (previous Z) or 1 (network)");
-    if (mode == 1 && !c->mlp_loaded)
+    if (mode != 0 && mode != 1 && mode != 4 && mode != 5)
+        return fail(c, ECHO_EINVAL, "c2p guess mode: 0 previous Z, 1 network, +4 FP32 refinement");
+    if ((mode & 3) == 1 && !c->mlp_loaded)
         return fail(c, ECHO_ESTATE, "no c2p-guess network loaded: call echo_mlp_load first");
     c->c2p_guess = mode;
     return ECHO_OK;

@@ -1,6 +1,12 @@
 // echo_batch.cu -- a batch of independent runs (e.g. a parameter sweep of
-// tori of uneven sizes) advanced by ONE persistent cooperative kernel per
-// SSP-RK3 stage, optionally replayed from a captured CUDA graph.
+// tori of uneven sizes) advanced together, optionally replayed from one
+// captured CUDA graph.  Three schedules (echo_batch_mode):
+//   0  ONE persistent cooperative kernel per SSP-RK3 stage (below);
+//   1  one ordinary launch per phase over the tiles of all runs;
+//   2  run-major: each run's own launch sequence, so that the working set of
+//      one run stays in L2 across its phases; the runs may be spread over
+//      concurrent branches (side streams forked from the batch stream; in a
+//      captured graph, parallel branches) so that small runs overlap.
 //
 // Inside the stage kernel the work of every phase of the stage -- ghost fill
 // of faces (3 passes), c2p, ghost fill of primitives (3 passes), faces
@@ -11,151 +17,16 @@
 // Tiles never straddle two (run, kind) segments, so every warp calls one
 // body with one set of template arguments (the bodies use warp-collective
 // operations).  Each run keeps its own CFL dt.
-#include <cooperative_groups.h>
-
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "echo_ctx.h"
-#include "echo_kernels.cuh"
+#include "echo_batch_kernels.cuh"
 
-namespace cg = cooperative_groups;
 using namespace echo;
-
-namespace echo {
-
-constexpr int BATCH_MAXRUNS = 32;
-constexpr int BATCH_NPHASE = 10;
-constexpr int BATCH_MAXSEG = 3 * BATCH_MAXRUNS;
-
-// phase kinds
-enum { PH_FILLF0 = 0, PH_FILLF1, PH_FILLF2, PH_C2P, PH_FILLP0, PH_FILLP1, PH_FILLP2, PH_FACES, PH_EMF, PH_UPDATE };
-
-template <typename R>
-struct RunDesc {
-    Geom g;
-    Arrays<R> A;
-    FillList<R> ff;   // face field
-    FillList<R> fp;   // primitives
-};
-
-struct Segment {
-    long long first_tile;   // global tile index of the segment's first tile
-    long long count;        // work items
-    int run;
-    int kind;               // sub-kind: direction for fills/faces/emf
-};
-
-struct BatchPlan {
-    int nruns;
-    int tile;
-    int dynamic;
-    int nseg[BATCH_NPHASE];
-    long long ntiles[BATCH_NPHASE];
-    Segment seg[BATCH_NPHASE][BATCH_MAXSEG];
-};
-
-template <int MK, typename R, bool MLP>
-__global__ void __launch_bounds__(128) k_batch_stage(const RunDesc<R> *__restrict__ runs, const BatchPlan *__restrict__ plan,
-                                                     unsigned long long *qctr, Phys ph, int stage, double dt_fixed,
-                                                     double cfl)
-{
-    cg::grid_group grid = cg::this_grid();
-    __shared__ LimScratch<R> lsm;
-    __shared__ long long s_tile;
-    extern __shared__ float4 mlp_smem4[];
-    const int nruns = plan->nruns;
-    const int tile = plan->tile;
-    const float *sm = nullptr;
-    if constexpr (MLP) {
-        float *Ps = reinterpret_cast<float *>(mlp_smem4);
-        const float *src = runs[0].A.mlp;
-        for (int q = threadIdx.x; q < MLP_BLOCK; q += blockDim.x)
-            Ps[q] = src[q];
-        __syncthreads();
-        sm = Ps;
-    }
-    if (stage == 0 && blockIdx.x == 0 && (int)threadIdx.x < nruns) {
-        DevScalars *sc = runs[threadIdx.x].A.scal;
-        sc->rate_bits = 0ULL;
-        sc->dt = dt_fixed > 0.0 ? dt_fixed : 0.0;
-    }
-    for (int p = 0; p < BATCH_NPHASE; ++p) {
-        if (blockIdx.x == 0 && threadIdx.x == 0)
-            qctr[(p + 1) % BATCH_NPHASE] = 0ULL;   // next phase's queue (visible after grid.sync)
-        if (p == PH_FILLP0 && stage == 0 && dt_fixed <= 0.0 && blockIdx.x == 0 && (int)threadIdx.x < nruns) {
-            DevScalars *sc = runs[threadIdx.x].A.scal;
-            const double rate = __longlong_as_double((long long)sc->rate_bits);
-            sc->totals[6] = rate;
-            sc->dt = rate > 0.0 ? cfl / rate : 0.0;
-        }
-        const long long ntiles = plan->ntiles[p];
-        const int nseg = plan->nseg[p];
-        for (long long it = 0;; ++it) {
-            long long tl;
-            if (plan->dynamic) {
-                if (threadIdx.x == 0)
-                    s_tile = (long long)atomicAdd(&qctr[p], 1ULL);
-                __syncthreads();
-                tl = s_tile;
-                __syncthreads();
-            } else {
-                tl = blockIdx.x + it * (long long)gridDim.x;
-            }
-            if (tl >= ntiles)
-                break;
-            int sgi = 0;
-            while (sgi + 1 < nseg && plan->seg[p][sgi + 1].first_tile <= tl)
-                ++sgi;
-            const Segment sgm = plan->seg[p][sgi];
-            const RunDesc<R> &rd = runs[sgm.run];
-            const long long base = (tl - sgm.first_tile) * tile;
-            for (int c = 0; c < tile; c += blockDim.x) {
-                const long long t = base + c + threadIdx.x;
-                switch (p) {
-                case PH_FILLF0:
-                case PH_FILLF1:
-                case PH_FILLF2:
-                    fill_body<R>(rd.g, p - PH_FILLF0, rd.ff, t);
-                    break;
-                case PH_C2P:
-                    c2p_body<MK, R, MLP>(rd.g, ph, rd.A, 0, stage == 0 ? 1 : 0, t, sm);
-                    break;
-                case PH_FILLP0:
-                case PH_FILLP1:
-                case PH_FILLP2:
-                    fill_body<R>(rd.g, p - PH_FILLP0, rd.fp, t);
-                    break;
-                case PH_FACES:
-                    if (sgm.kind == 0)
-                        faces_body<0, MK, R>(rd.g, ph, rd.A, t, lsm);
-                    else if (sgm.kind == 1)
-                        faces_body<1, MK, R>(rd.g, ph, rd.A, t, lsm);
-                    else
-                        faces_body<2, MK, R>(rd.g, ph, rd.A, t, lsm);
-                    break;
-                case PH_EMF:
-                    if (sgm.kind == 0)
-                        emf_body<0, MK, R>(rd.g, rd.A, t, lsm);
-                    else if (sgm.kind == 1)
-                        emf_body<1, MK, R>(rd.g, rd.A, t, lsm);
-                    else
-                        emf_body<2, MK, R>(rd.g, rd.A, t, lsm);
-                    break;
-                default:
-                    update_body<MK, R>(rd.g, ph, rd.A, stage, nullptr, t);
-                    break;
-                }
-            }
-            __syncthreads();   // shared scratch reused by the next tile
-        }
-        grid.sync();
-    }
-}
-
-}  // namespace echo
 
 // ------------------------------------------------------------------ host side
 
@@ -165,6 +36,7 @@ struct echo_batch {
     int mk = 0;
     int precision = 64;
     bool mlp = false;
+    int guess = 0;
     Phys ph;
     double cfl = 0.4;
     BatchPlan plan;
@@ -174,7 +46,12 @@ struct echo_batch {
     bool bound = false;
     int grid_blocks = 0;
     int blocks_per_sm = 0;
+    int phased = 0;       // 0 persistent kernel per stage, 1 one launch per phase, 2 run-major
     bool use_graph = false;
+    int branches = 1;                       // run-major: concurrent branches
+    std::vector<cudaStream_t> side;         // one per branch
+    std::vector<cudaEvent_t> fork_join;     // [0] fork, [1 + k] join of branch k
+    std::vector<int> branch_of;             // run -> branch
     cudaGraphExec_t gexec = nullptr;
     double graph_dt = 0.0;
     std::string err;
@@ -276,22 +153,14 @@ FillList<R> prims_fill(const Arrays<R> &A)
 template <typename R>
 size_t desc_bytes(int nruns) { return a256(sizeof(RunDesc<R>) * nruns); }
 
-template <typename R>
-const void *kernel_ptr(int mk, bool mlp)
-{
-    if (mk == 1)
-        return mlp ? (const void *)k_batch_stage<1, R, true> : (const void *)k_batch_stage<1, R, false>;
-    return mlp ? (const void *)k_batch_stage<0, R, true> : (const void *)k_batch_stage<0, R, false>;
-}
-
 const void *stage_kernel(const echo_batch *b)
 {
-    return b->precision == 64 ? kernel_ptr<double>(b->mk, b->mlp) : kernel_ptr<float>(b->mk, b->mlp);
+    return b->precision == 64 ? batch_stage_kernel<double>(b->mk, b->mlp) : batch_stage_kernel<float>(b->mk, b->mlp);
 }
 
 size_t dyn_smem(const echo_batch *b) { return b->mlp ? MLP_BLOCK * sizeof(float) : 0; }
 
-int max_blocks_per_sm(echo_batch *b)
+int occupancy(const echo_batch *b)
 {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel(b), 128, dyn_smem(b)) != cudaSuccess) {
@@ -300,6 +169,8 @@ int max_blocks_per_sm(echo_batch *b)
     }
     return nb;
 }
+
+int max_blocks_per_sm(echo_batch *b) { return occupancy(b); }
 
 int upload(echo_batch *b)
 {
@@ -344,7 +215,8 @@ int launch_stage(echo_batch *b, int stage, double dt)
     unsigned long long *qctr = reinterpret_cast<unsigned long long *>(b->ws + dsz + a256(sizeof(BatchPlan)));
     Phys ph = b->ph;
     double cfl = b->cfl;
-    void *args[] = {&descs, &planp, &qctr, &ph, &stage, &dt, &cfl};
+    int guess = b->guess;
+    void *args[] = {&descs, &planp, &qctr, &ph, &stage, &dt, &cfl, &guess};
     cudaError_t e = cudaLaunchCooperativeKernel(stage_kernel(b), dim3(b->grid_blocks), dim3(128), args, dyn_smem(b),
                                                 b->stream);
     if (e != cudaSuccess)
@@ -354,6 +226,47 @@ int launch_stage(echo_batch *b, int stage, double dt)
 
 int enqueue_step(echo_batch *b, double dt)
 {
+    if (b->phased == 1) {
+        const size_t dsz = b->precision == 64 ? desc_bytes<double>(b->nruns) : desc_bytes<float>(b->nruns);
+        const BatchPlan *planp = reinterpret_cast<const BatchPlan *>(b->ws + dsz);
+        if (b->precision == 64)
+            batch_enqueue_phased<double>(b->mk, b->mlp, b->ws, planp, b->plan, b->nruns, b->ph, b->guess, dt, b->cfl,
+                                         b->stream);
+        else
+            batch_enqueue_phased<float>(b->mk, b->mlp, b->ws, planp, b->plan, b->nruns, b->ph, b->guess, dt, b->cfl,
+                                        b->stream);
+        return bcheck(b, "phased step");
+    }
+    if (b->phased == 2) {
+        // run-major: every run's own launch sequence; with several branches the
+        // runs are split over side streams forked from and joined back into the
+        // batch stream (in a captured graph: parallel branches)
+        if (b->branches == 1) {
+            for (echo_ctx *c : b->runs) {
+                const int rc = echo_internal_enqueue_step(c, dt, b->stream);
+                if (rc)
+                    return bfail(b, rc, std::string("run step: ") + c->err);
+            }
+            return ECHO_OK;
+        }
+        if (cudaEventRecord(b->fork_join[0], b->stream) != cudaSuccess)
+            return bcheck(b, "fork");
+        for (int k = 0; k < b->branches; ++k)
+            if (cudaStreamWaitEvent(b->side[k], b->fork_join[0], 0) != cudaSuccess)
+                return bcheck(b, "fork");
+        for (int r = 0; r < b->nruns; ++r) {
+            echo_ctx *c = b->runs[r];
+            const int rc = echo_internal_enqueue_step(c, dt, b->side[b->branch_of[r]]);
+            if (rc)
+                return bfail(b, rc, std::string("run step: ") + c->err);
+        }
+        for (int k = 0; k < b->branches; ++k) {
+            if (cudaEventRecord(b->fork_join[1 + k], b->side[k]) != cudaSuccess
+                || cudaStreamWaitEvent(b->stream, b->fork_join[1 + k], 0) != cudaSuccess)
+                return bcheck(b, "join");
+        }
+        return ECHO_OK;
+    }
     for (int st = 0; st < 3; ++st) {
         const int rc = launch_stage(b, st, dt);
         if (rc)
@@ -367,6 +280,39 @@ void drop_graph(echo_batch *b)
     if (b->gexec) {
         cudaGraphExecDestroy(b->gexec);
         b->gexec = nullptr;
+    }
+}
+
+void drop_branches(echo_batch *b)
+{
+    for (cudaStream_t s : b->side)
+        cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->fork_join)
+        cudaEventDestroy(e);
+    b->side.clear();
+    b->fork_join.clear();
+}
+
+// Longest-processing-time assignment of runs (by zone count) to branches.
+void assign_branches(echo_batch *b)
+{
+    std::vector<int> order(b->nruns);
+    for (int r = 0; r < b->nruns; ++r)
+        order[r] = r;
+    auto zones = [b](int r) {
+        const Geom &g = b->runs[r]->geo;
+        return (long long)g.n[0] * g.n[1] * g.n[2];
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return zones(x) > zones(y); });
+    std::vector<long long> load(b->branches, 0);
+    b->branch_of.assign(b->nruns, 0);
+    for (int r : order) {
+        int k = 0;
+        for (int q = 1; q < b->branches; ++q)
+            if (load[q] < load[k])
+                k = q;
+        b->branch_of[r] = k;
+        load[k] += zones(r);
     }
 }
 
@@ -398,8 +344,10 @@ int echo_batch_create(echo_ctx *const *runs, int nruns, echo_batch **out)
     b->precision = runs[0]->precision;
     b->ph = runs[0]->ph;
     b->cfl = runs[0]->cfl;
-    b->mlp = runs[0]->c2p_guess == 1;
+    b->mlp = (runs[0]->c2p_guess & 3) == 1;
+    b->guess = runs[0]->c2p_guess;
     build_plan(b, 256, 1);
+    assign_branches(b);
     const size_t dsz = b->precision == 64 ? desc_bytes<double>(nruns) : desc_bytes<float>(nruns);
     b->ws_need = dsz + a256(sizeof(BatchPlan)) + a256(BATCH_NPHASE * sizeof(unsigned long long));
     *out = b;
@@ -423,14 +371,25 @@ int echo_batch_bind(echo_batch *b, void *ws, size_t bytes, void *stream)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int mb = max_blocks_per_sm(b);
-    if (mb < 1)
+    const int m = occupancy(b);
+    if (m < 1)
         return bfail(b, ECHO_ECUDA, "stage kernel cannot be resident");
-    b->blocks_per_sm = mb;
-    b->grid_blocks = mb * sms;
+    b->blocks_per_sm = m;
+    b->grid_blocks = b->blocks_per_sm * sms;
     b->bound = true;
     drop_graph(b);
     return upload(b);
+}
+
+int echo_batch_mode(echo_batch *b, int phased)
+{
+    if (!b)
+        return ECHO_EINVAL;
+    if (phased < 0 || phased > 2)
+        return bfail(b, ECHO_EINVAL, "batch mode: 0 persistent, 1 phased, 2 run-major");
+    b->phased = phased;
+    drop_graph(b);
+    return ECHO_OK;
 }
 
 int echo_batch_config(echo_batch *b, int tile, int blocks_per_sm, int dynamic_queue)
@@ -439,8 +398,7 @@ int echo_batch_config(echo_batch *b, int tile, int blocks_per_sm, int dynamic_qu
         return b ? bfail(b, ECHO_ESTATE, "bind the batch first") : ECHO_EINVAL;
     if (tile < 128 || tile % 128 != 0 || tile > 8192)
         return bfail(b, ECHO_EINVAL, "tile must be a multiple of 128 in [128, 8192]");
-    const int mb = max_blocks_per_sm(b);
-    if (blocks_per_sm < 1 || blocks_per_sm > mb)
+    if (blocks_per_sm < 1 || blocks_per_sm > occupancy(b))
         return bfail(b, ECHO_EINVAL, "blocks_per_sm must be in [1, max resident]");
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -453,6 +411,37 @@ int echo_batch_config(echo_batch *b, int tile, int blocks_per_sm, int dynamic_qu
 }
 
 int echo_batch_max_blocks_per_sm(echo_batch *b) { return b ? max_blocks_per_sm(b) : 0; }
+
+int echo_batch_branches(echo_batch *b, int branches)
+{
+    if (!b)
+        return ECHO_EINVAL;
+    if (branches < 1 || branches > b->nruns)
+        return bfail(b, ECHO_EINVAL, "branches must be in [1, number of runs]");
+    drop_graph(b);
+    drop_branches(b);
+    b->branches = branches;
+    if (branches > 1) {
+        b->side.assign(branches, nullptr);
+        b->fork_join.assign(branches + 1, nullptr);
+        for (int k = 0; k < branches; ++k)
+            if (cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) != cudaSuccess) {
+                b->side.resize(k);
+                drop_branches(b);
+                b->branches = 1;
+                return bcheck(b, "branch streams");
+            }
+        for (int k = 0; k <= branches; ++k)
+            if (cudaEventCreateWithFlags(&b->fork_join[k], cudaEventDisableTiming) != cudaSuccess) {
+                b->fork_join.resize(k);
+                drop_branches(b);
+                b->branches = 1;
+                return bcheck(b, "branch events");
+            }
+    }
+    assign_branches(b);
+    return ECHO_OK;
+}
 
 int echo_batch_graph(echo_batch *b, int enable)
 {
@@ -513,6 +502,7 @@ void echo_batch_destroy(echo_batch *b)
     if (!b)
         return;
     drop_graph(b);
+    drop_branches(b);
     delete b;
 }
 

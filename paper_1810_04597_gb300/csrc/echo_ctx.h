@@ -40,3 +40,5 @@ struct echo_ctx {
     size_t ev_used = 0;               // pairs in use
 };
 
+// One step of c enqueued on stream s instead of its own (internal).
+extern "C" __attribute__((visibility("hidden"))) int echo_internal_enqueue_step(echo_ctx *c, double dt, cudaStream_t s);

@@ -32,6 +32,7 @@ struct Geom {
     long long cells_padded;  // pxy * np2
     double dx[3];
     double idx[3];           // 1/dx
+    float idx_f[3];          // 1/dx in FP32
     double x0[3];
     int bc[6];
     int flo[3], fhi[3];      // owned (evolved) face range along d, inclusive
@@ -47,7 +48,21 @@ struct Phys {
     double gr;        // gamma / (gamma - 1)
     double gm1g;      // (gamma - 1) / gamma
     double cfl;
+    float gamma_f, gr_f;   // the same constants in FP32 (no per-thread conversion)
 };
+
+template <typename T>
+__device__ __forceinline__ T phys_gamma(const Phys &ph);
+template <>
+__device__ __forceinline__ double phys_gamma<double>(const Phys &ph) { return ph.gamma; }
+template <>
+__device__ __forceinline__ float phys_gamma<float>(const Phys &ph) { return ph.gamma_f; }
+template <typename T>
+__device__ __forceinline__ T phys_gr(const Phys &ph);
+template <>
+__device__ __forceinline__ double phys_gr<double>(const Phys &ph) { return ph.gr; }
+template <>
+__device__ __forceinline__ float phys_gr<float>(const Phys &ph) { return ph.gr_f; }
 
 // Device-resident scalars of a context.
 struct DevScalars {
@@ -161,6 +176,56 @@ __device__ __forceinline__ float with_sign_of(float mag, float s)
 {
     return __int_as_float(__float_as_int(mag) | (__float_as_int(s) & (int)0x80000000u));
 }
+
+// ------------------------------------------------------------------ exact
+// float <-> double conversions on the integer pipe
+//
+// GB300 executes F2F conversions on the FP64 pipe.  These build the IEEE 754
+// binary64 / binary32 encodings directly (sign, re-biased exponent, shifted
+// mantissa; round to nearest even when narrowing) and hand only zero-exponent
+// (zero / subnormal), overflowing and non-finite values to the hardware
+// conversion, so every result equals the hardware cast.
+
+__device__ __forceinline__ double f2d(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) {
+        if ((b & 0x7fffffffu) == 0u)
+            return __longlong_as_double((long long)((unsigned long long)(b & 0x80000000u) << 32));
+        return (double)x;   // subnormal, inf, nan
+    }
+    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32)
+                                 | ((unsigned long long)(e + (1023u - 127u)) << 52)
+                                 | ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+__device__ __forceinline__ float d2f(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+    if (e >= 1 && e <= 254) {
+        const unsigned long long m = b & 0xfffffffffffffULL;
+        unsigned r = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)e << 23) | (unsigned)(m >> 29);
+        const unsigned long long rem = m & 0x1fffffffULL;
+        const unsigned long long half = 0x10000000ULL;
+        r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;   // carry may raise the exponent (to inf)
+        return __uint_as_float(r);
+    }
+    if ((b & 0x7fffffffffffffffULL) == 0ULL)
+        return __uint_as_float((unsigned)(b >> 32) & 0x80000000u);
+    return (float)x;   // subnormal result, overflow, inf, nan
+}
+
+template <typename R>
+__device__ __forceinline__ double to_d(R x) { return (double)x; }
+template <>
+__device__ __forceinline__ double to_d<float>(float x) { return f2d(x); }
+template <typename R>
+__device__ __forceinline__ R from_d(double x) { return (R)x; }
+template <>
+__device__ __forceinline__ float from_d<float>(double x) { return d2f(x); }
 
 // ------------------------------------------------------------------ metric
 // accessors.  MFlat is the Minkowski metric in Cartesian coordinates (every
@@ -501,9 +566,43 @@ __device__ __forceinline__ void c2p_recip(double Z, double B2, double &iZ, doubl
     iZB = inv * Z;
 }
 
+// Optional FP32 pre-refinement of the guess: up to 4 Newton steps of the same
+// residual in FP32 (stopping at |dZ| <= 4e-7 Z or at a step that leaves the
+// admissible set).  It only moves the starting point; the FP64 iterations
+// that follow decide convergence.
+__device__ __forceinline__ double c2p_refine_f32(double Zg, double S2d, double SB2d, double B2d, double Dd,
+                                                 double Ud, double gm1gd)
+{
+    const float S2 = d2f(S2d), SB2 = d2f(SB2d), B2 = d2f(B2d), D = d2f(Dd), U = d2f(Ud), gm1g = d2f(gm1gd);
+    float Z = d2f(Zg);
+    for (int k = 0; k < 4; ++k) {
+        const float iZ = 1.0f / Z, ZB = Z + B2, iZB = 1.0f / ZB;
+        const float v2 = (S2 + SB2 * (2.0f * Z + B2) * iZ * iZ) * iZB * iZB;
+        if (!(v2 < 1.0f) || !(Z > 0.0f))
+            break;
+        const float om = 1.0f - v2;
+        const float isq = rsqrtf(om);
+        const float p = gm1g * (Z * om - D * om * isq);
+        const float f = Z - p + 0.5f * (1.0f + v2) * B2 - 0.5f * SB2 * iZ * iZ - U;
+        const float dv2 = -2.0f * (S2 * Z * Z * Z + SB2 * (3.0f * Z * Z + 3.0f * Z * B2 + B2 * B2)) * iZ * iZ * iZ
+                          * iZB * iZB * iZB;
+        const float dp = gm1g * (om - Z * dv2 + 0.5f * D * dv2 * isq);
+        const float fp = 1.0f - dp + 0.5f * B2 * dv2 + SB2 * iZ * iZ * iZ;
+        const float dZ = f / fp;
+        const float Zn = Z - dZ;
+        if (!(Zn > 0.0f))
+            break;
+        Z = Zn;
+        if (fabsf(dZ) <= 4e-7f * Z)
+            break;
+    }
+    return f2d(Z);
+}
+
 template <typename M>
 __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], double tau, const double B[3],
-                                                double Zguess, double gm1g, const M &m, int maxit = NEWTON_MAXIT)
+                                                double Zguess, double gm1g, const M &m, int maxit = NEWTON_MAXIT,
+                                                bool refine = false)
 {
     double Su[3], Bl[3];
     raise<double>(m, S, Su);
@@ -515,6 +614,8 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
     const double Uen = tau + Dc;
     C2PResult r;
     double Z = Zguess, iZ = 0.0, iZB = 0.0, v2 = 0.0;
+    if (refine && is_pos(Z))
+        Z = c2p_refine_f32(Z, S2, SB2, B2, Dc, Uen, gm1g);
     int tries = 0;
     bool ok = true;
     for (;;) {

@@ -128,12 +128,14 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             sg = mp->sg;
         }
         double B[3];
-        B[0] = 0.5 * ((double)A.U[5][id] + (double)A.U[5][id + 1]) * isg;
-        B[1] = 0.5 * ((double)A.U[6][id] + (double)A.U[6][id + g.px]) * isg;
-        B[2] = 0.5 * ((double)A.U[7][id] + (double)A.U[7][id + g.pxy]) * isg;
-        const double S[3] = {(double)A.U[1][id] * isg, (double)A.U[2][id] * isg, (double)A.U[3][id] * isg};
-        const double zg = guess_mode == 2 ? 0.0 : A.Z[id];
-        const double Dc = (double)A.U[0][id] * isg, tc = (double)A.U[4][id] * isg;
+        B[0] = 0.5 * (to_d(A.U[5][id]) + to_d(A.U[5][id + 1])) * isg;
+        B[1] = 0.5 * (to_d(A.U[6][id]) + to_d(A.U[6][id + g.px])) * isg;
+        B[2] = 0.5 * (to_d(A.U[7][id]) + to_d(A.U[7][id + g.pxy])) * isg;
+        const double S[3] = {to_d(A.U[1][id]) * isg, to_d(A.U[2][id]) * isg, to_d(A.U[3][id]) * isg};
+        const int src = guess_mode & 3;
+        const bool refine = (guess_mode & 4) != 0;
+        const double zg = src == 2 ? 0.0 : A.Z[id];
+        const double Dc = to_d(A.U[0][id]) * isg, tc = to_d(A.U[4][id]) * isg;
         C2PResult r;
         if constexpr (MLP) {
             float f[MLP_NI], o[MLP_NO];
@@ -145,9 +147,9 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             const double Wg = exp((double)o[0]), pD = exp((double)o[1]);
             const double z0 = Dc * Wg * (1.0 + ph.gr * pD * Wg);
             if constexpr (MK == 1)
-                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MKS<double>(*mp), 8);
+                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MKS<double>(*mp), 8, refine);
             else
-                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MFlat<double>(), 8);
+                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MFlat<double>(), 8, refine);
             if (!r.ok) {
                 const int first = r.iters;
                 if constexpr (MK == 1)
@@ -159,9 +161,9 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             }
         } else {
             if constexpr (MK == 1)
-                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp));
+                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp), NEWTON_MAXIT, refine);
             else
-                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>());
+                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>(), NEWTON_MAXIT, refine);
         }
         its = r.iters;
         calls = 1;
@@ -173,7 +175,7 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
                 bool reset = !r.ok;
                 if (reset)
                     for (int q = 0; q < 5; ++q)
-                        P8[q] = (double)A.P[q][id];
+                        P8[q] = to_d(A.P[q][id]);
                 const double rf = A.met.floors[2 * i], pf = A.met.floors[2 * i + 1];
                 if (!ile(rf, P8[0])) {
                     P8[0] = rf;
@@ -188,12 +190,12 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
                     double C5[5];
                     p2c_point(P8, ph.gr, MKS<double>(*mp), C5, Z);
                     for (int q = 0; q < 5; ++q)
-                        A.U[q][id] = (R)(C5[q] * sg);
+                        A.U[q][id] = from_d<R>(C5[q] * sg);
                 }
             }
         }
         for (int q = 0; q < 8; ++q)
-            A.P[q][id] = (R)P8[q];
+            A.P[q][id] = from_d<R>(P8[q]);
         A.Z[id] = Z;
         if (want_rate) {
             if constexpr (MK == 1)
@@ -439,12 +441,12 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     T FL[5], UL[5], FR[5], UR[5], lpL, lmL, lpR, lmR;
     if constexpr (MK == 1) {
         const MKS<T> m(*mp);
-        state_flux<D>(PL, (T)ph.gamma, (T)ph.gr, m, FL, UL, lpL, lmL);
-        state_flux<D>(PR, (T)ph.gamma, (T)ph.gr, m, FR, UR, lpR, lmR);
+        state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, lpL, lmL);
+        state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, lpR, lmR);
     } else {
         const MFlat<T> m;
-        state_flux<D>(PL, (T)ph.gamma, (T)ph.gr, m, FL, UL, lpL, lmL);
-        state_flux<D>(PR, (T)ph.gamma, (T)ph.gr, m, FR, UR, lpR, lmR);
+        state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, lpL, lmL);
+        state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, lpR, lmR);
     }
     const T ap = imax(T(0), imax(lpL, lpR));
     const T am = imax(T(0), imax(-lmL, -lmR));
@@ -698,6 +700,13 @@ __device__ __forceinline__ void ks_sources(const T P[8], T gr, const MetPt &mp, 
 // their axis; a face that is not evolved, e.g. on the polar axis, gets 0).
 // Body over the linear index t of the (n0+1)(n1+1)(n2+1) box of cells and
 // faces, x fastest.
+template <typename R>
+__device__ __forceinline__ R geom_idx(const Geom &g, int d);
+template <>
+__device__ __forceinline__ double geom_idx<double>(const Geom &g, int d) { return g.idx[d]; }
+template <>
+__device__ __forceinline__ float geom_idx<float>(const Geom &g, int d) { return g.idx_f[d]; }
+
 template <int MK, typename R>
 __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const Arrays<R> &A, int stage,
                                             double *Lout, long long t)
@@ -724,14 +733,14 @@ __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const
             for (int q = 0; q < 8; ++q)
                 P[q] = A.P[q][id];
             const int ti = j * A.met.np0 + i;
-            ks_sources(P, (R)ph.gr, A.met.C[ti], A.met.dC[ti], src);
+            ks_sources(P, phys_gr<R>(ph), A.met.C[ti], A.met.dC[ti], src);
         }
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             R r = R(0);
 #pragma unroll
             for (int d = 0; d < 3; ++d)
-                r -= (A.F[d][q][id + st[d]] - A.F[d][q][id]) * (R)g.idx[d];
+                r -= (A.F[d][q][id + st[d]] - A.F[d][q][id]) * geom_idx<R>(g, d);
             r += src[q];
             if (stage < 0) {
                 Lout[q * N + ((long long)tk * g.n[1] + tj) * g.n[0] + ti] = (double)r;
@@ -762,8 +771,8 @@ __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const
             R l = R(0);
             if (evolved) {
                 // dB~^d/dt = -(d_a E_b - d_b E_a)
-                const R dEb = (A.E[b][id + st[a]] - A.E[b][id]) * (R)g.idx[a];
-                const R dEa = (A.E[a][id + st[b]] - A.E[a][id]) * (R)g.idx[b];
+                const R dEb = (A.E[b][id + st[a]] - A.E[b][id]) * geom_idx<R>(g, a);
+                const R dEa = (A.E[a][id + st[b]] - A.E[a][id]) * geom_idx<R>(g, b);
                 l = -(dEb - dEa);
             }
             if (stage < 0) {
@@ -772,8 +781,8 @@ __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const
                     const bool dup = ijk[d] == NG + g.n[d] && g.bc[2 * d] == BC_PERIODIC;
                     R lo = l;
                     if (dup) {
-                        const R dEb = (A.E[b][id + st[a]] - A.E[b][id]) * (R)g.idx[a];
-                        const R dEa = (A.E[a][id + st[b]] - A.E[a][id]) * (R)g.idx[b];
+                        const R dEb = (A.E[b][id + st[a]] - A.E[b][id]) * geom_idx<R>(g, a);
+                        const R dEa = (A.E[a][id + st[b]] - A.E[a][id]) * geom_idx<R>(g, b);
                         lo = -(dEb - dEa);
                     }
                     Lout[off + ((long long)tk * e[1] + tj) * e[0] + ti] = (double)lo;

@@ -1,0 +1,72 @@
+// echo_selftest.cu -- self-check of device helpers that replace hardware
+// instructions: the integer-pipe float <-> double conversions must equal the
+// hardware casts bit for bit.
+#include "../../include/echo.h"
+#include "echo_device.cuh"
+
+namespace echo {
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x)
+{
+    x += 0x9e3779b97f4a7c15ULL;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebULL;
+    return x ^ (x >> 31);
+}
+
+// Thread i builds test values from a counter-based hash: random float bit
+// patterns (every class), doubles spread over and beyond the float range,
+// doubles exactly half-way between two floats, and signed zeros.
+__global__ void k_check_conversions(long long n, unsigned long long seed, unsigned long long *mismatch)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const unsigned long long h = mix64(seed ^ (unsigned long long)i);
+    unsigned long long bad = 0;
+    // float -> double on an arbitrary float pattern
+    {
+        const float f = __uint_as_float((unsigned)h);
+        const double a = f2d(f), b = (double)f;
+        if (!(f != f)) {
+            if (__double_as_longlong(a) != __double_as_longlong(b))
+                ++bad;
+        }
+    }
+    // double -> float: exponent near the float range, random mantissa
+    {
+        const unsigned long long e = 1023ULL - 160ULL + (h >> 52) % 320ULL;
+        const unsigned long long m = mix64(h) & 0xfffffffffffffULL;
+        const unsigned long long sgn = (h & 1ULL) << 63;
+        const double x = __longlong_as_double((long long)(sgn | (e << 52) | m));
+        if (__float_as_uint(d2f(x)) != __float_as_uint((float)x))
+            ++bad;
+        // exactly half-way between two floats (round-to-even case), and one ulp either side
+        const unsigned long long tie = (m & ~0x1fffffffULL) | 0x10000000ULL;
+        for (long long off = -1; off <= 1; ++off) {
+            const double y = __longlong_as_double((long long)(sgn | (e << 52) | (tie + off)));
+            if (__float_as_uint(d2f(y)) != __float_as_uint((float)y))
+                ++bad;
+        }
+    }
+    if (i == 0) {
+        const double z[4] = {0.0, -0.0, 3.4028234663852886e38, -1.1754943508222875e-38};
+        for (int k = 0; k < 4; ++k)
+            if (__float_as_uint(d2f(z[k])) != __float_as_uint((float)z[k]))
+                ++bad;
+    }
+    if (bad)
+        atomicAdd(mismatch, bad);
+}
+
+}  // namespace echo
+
+extern "C" int echo_selftest_conversions(long long n, unsigned long long seed, unsigned long long *dev_mismatch,
+                                         void *stream)
+{
+    if (n < 1 || !dev_mismatch)
+        return ECHO_EINVAL;
+    echo::k_check_conversions<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        n, seed, dev_mismatch);
+    return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
+}

@@ -1,7 +1,8 @@
-"""Batch of independent runs in one persistent cooperative kernel per RK
-stage: the same results as the runs advanced one at a time (the same
-device bodies compute the same arithmetic, so bitwise in FP64), for every
-scheduling configuration and with CUDA-graph replay."""
+"""Batch of independent runs under each schedule (persistent cooperative
+kernel per RK stage, one launch per phase, run-major with concurrent
+branches): the same results as the runs advanced one at a time (the same
+device bodies compute the same arithmetic, so bitwise in FP64), with and
+without CUDA-graph replay."""
 import numpy as np
 import pytest
 
@@ -29,8 +30,11 @@ def _tori(precision=64):
     return out
 
 
-@pytest.mark.parametrize("tile,dyn,graph", [(256, True, False), (128, False, False), (512, True, True)])
-def test_batch_equals_runs_one_at_a_time(tile, dyn, graph):
+@pytest.mark.parametrize("tile,dyn,graph,mode,branches", [
+    (256, True, False, 0, 1), (128, False, False, 0, 1), (512, True, True, 0, 1), (256, True, False, 1, 1),
+    (1024, True, True, 1, 1), (256, True, False, 2, 1), (256, True, True, 2, 1), (256, True, False, 2, 2),
+    (256, True, True, 2, 3)])
+def test_batch_equals_runs_one_at_a_time(tile, dyn, graph, mode, branches):
     from paper_1810_04597_gb300.batch import Batch
     single = _tori()
     for s in single:
@@ -39,7 +43,7 @@ def test_batch_equals_runs_one_at_a_time(tile, dyn, graph):
     ref = [s.get_state() for s in single]
     runs = _tori()
     b = Batch(runs)
-    b.configure(tile=tile, dynamic=dyn)
+    b.configure(tile=tile, dynamic=dyn, mode=mode, branches=branches)
     b.graph(graph)
     for _ in range(3):
         b.step()

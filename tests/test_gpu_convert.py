@@ -1,0 +1,42 @@
+"""Device helpers that stand in for hardware instructions, and the FP32
+guess refinement of the Newton solve."""
+import numpy as np
+import pytest
+
+from paper_1810_04597_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_integer_pipe_conversions_equal_hardware_casts():
+    import torch
+    from paper_1810_04597_gb300 import _lib
+    if not torch.cuda.is_available():
+        pytest.fail("needs a CUDA device")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for seed in (1, 2, 3):
+        _lib.echo_selftest_conversions(1 << 22, seed, cnt)
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == 0
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_fp32_refined_guess_converges_to_the_same_state(precision):
+    """Guess mode +4 (FP32 Newton pre-refinement): same converged state as the
+    plain previous-stage guess, with fewer FP64 iterations per call."""
+    from paper_1810_04597_gb300.echo import Solver
+    prob = inputs.sweep_box(32, seed=21)
+    res = {}
+    for mode in (0, 4):
+        s = Solver(prob, precision=precision)
+        s.set_prims()
+        s.set_c2p_guess(mode)
+        c0 = s.counters()
+        for _ in range(3):
+            s.step()
+        c1 = s.counters()
+        res[mode] = (s.get_state(), (c1["c2p_iters"] - c0["c2p_iters"]) / (c1["c2p_calls"] - c0["c2p_calls"]))
+    a, b = res[0][0], res[4][0]
+    tol = 1e-12 if precision == 64 else 1e-6
+    assert np.max(np.abs(a - b)) <= tol * np.max(np.abs(a))
+    assert res[4][1] < res[0][1], (res[0][1], res[4][1])
