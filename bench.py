@@ -49,6 +49,34 @@ KMODEL = {
 }
 
 
+# FP64 floating-point operations per unit of each kernel class (FP64 path):
+# 2 x DFMA + DADD + DMUL thread instructions counted by ncu, including those
+# inside divisions and square roots, on one launch at 128^3 of the same input
+# recipe (sweep_box), divided by the units of that launch.  c2p depends on the
+# Newton iteration count (2.74 per call there); faces_y/z run the code of
+# faces_x with other strides.
+FLOPS64 = {
+    64: {"faces_x": 604.8, "faces_y": 604.8, "faces_z": 604.8,
+         "emf_x": 326.1, "emf_y": 326.1, "emf_z": 326.1,
+         "c2p": 469.6, "update": 79.0},
+    # FP32-bulk path: only c2p computes in FP64 (previous-stage Z refined in
+    # FP32, then 1.01 FP64 Newton iterations per call)
+    32: {"c2p": 277.0},
+}
+# FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 DFMA lanes
+# per SM and clock x 2 flop x 2.07 GHz (the 1.25 TFLOP/s nominal figure).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes per face of faces_x (dram__bytes_read.sum + dram__bytes_write.sum
+# of the same 128^3 ncu launch: 317,764,096 B over 2,316,324 faces); scaled to
+# a launch by the faces it processes.
+TRAFFIC_PER_FACE64 = 317764096 / 2316324
+# FP64 pipe activity in those captures
+# (sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active).
+FP64_PIPE_BUSY = {64: {"faces_x": 0.851, "faces_y": 0.851, "faces_z": 0.851, "emf_x": 0.840, "emf_y": 0.840,
+                       "emf_z": 0.840, "c2p": 0.872, "update": 0.833},
+                  32: {"c2p": 0.868}}
+
+
 def kernel_units(name, n):
     nx, ny, nz = n
     g = 3
@@ -193,10 +221,16 @@ def cpu_description():
     try:
         with open("/proc/cpuinfo") as f:
             txt = f.read()
+        arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+        ncpu = sum(1 for ln in txt.splitlines() if ln.startswith("processor"))
         for key in ("model name", "CPU part", "Hardware"):
             for ln in txt.splitlines():
                 if ln.startswith(key):
-                    return ln.split(":", 1)[1].strip()
+                    v = ln.split(":", 1)[1].strip()
+                    name = arm_parts.get(v, v) if key == "CPU part" else v
+                    return f"{name} (CPU part {v})" if key == "CPU part" else name
+        if ncpu:
+            return f"{ncpu} processors"
     except Exception:
         pass
     import platform
@@ -241,6 +275,11 @@ def max_over_ranks(dist, value):
 
 # ------------------------------------------------------------------ arms
 
+def workload_name(args):
+    return (f"sweep_box {args.size}^3 periodic SRMHD, Gamma 4/3, CFL 0.4, "
+            f"{'FP64' if args.precision == 64 else 'FP32 bulk'}")
+
+
 def run_reference(args, world, rank):
     """The oracle (plain FP64 C, OpenMP over cells) as the reference arm."""
     if rank != 0:
@@ -249,7 +288,7 @@ def run_reference(args, world, rank):
     import oracle
     oracle.build()
     prob = inputs.sweep_box(args.size)
-    w = 48
+    w = min(64, args.size)
     win = oracle_window(prob, w)
     cfg = oracle.make_cfg(win)
     st, Z = oracle.p2c(cfg, win.prims, win.bface)
@@ -267,8 +306,8 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded)",
-        "config": {"workload": f"sweep_box {args.size}^3 periodic SRMHD (oracle on a {w}^3 window)",
-                   "grid": [args.size] * 3},
+        "config": {"workload": workload_name(args), "grid": [args.size] * 3, "zones": args.size ** 3,
+                   "parallelism": "rank 0 only (host cores)", "sample": f"{w}^3 window per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample, "cpu": cpu_description()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -289,6 +328,8 @@ def run_ours(args, world, rank, local, dist):
     s = Solver(prob, precision=args.precision, device=str(dev))
     stream = s.stream
     s.set_prims()
+    if args.precision == 32:
+        s.set_c2p_guess(4)      # previous-stage Z refined by FP32 Newton steps
     for _ in range(args.warmup):
         s.step()
     torch.cuda.synchronize()
@@ -328,15 +369,31 @@ def run_ours(args, world, rank, local, dist):
     dom = max(timed, key=lambda k: timed[k][0])
     dom_ms, dom_launches = timed[dom]
     avg_s = dom_ms / dom_launches * 1e-3
-    bytes_launch = kernel_units(dom, n) * kernel_bytes_per_unit(dom, args.precision)
-    achieved = bytes_launch / avg_s / 1e9
+    units = kernel_units(dom, n)
+    bytes_launch = units * kernel_bytes_per_unit(dom, args.precision)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_ctx = {"achieved": bytes_launch / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+               "frac": bytes_launch / avg_s / 1e9 / hbm, "bytes_per_launch": bytes_launch,
+               "peak_source": f"{peak_src} hbm_gbs" if peak_src == "measured" else "fallback 6800 GB/s"}
     share = {k: round(v[0] / ms, 4) for k, v in prof.items() if v[1] > 0}
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None,
-            "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
-            else "fallback 6800 GB/s",
-            "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_s * 1e3, "time_share": share}
+    fl = FLOPS64[args.precision]
+    if dom in fl:
+        # bound by the FP64 pipe, not by HBM
+        flops = units * fl[dom]
+        achieved = flops / avg_s / 1e12
+        traffic = units * TRAFFIC_PER_FACE64 if (dom.startswith("faces") and args.precision == 64) else None
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "flops_per_unit": fl[dom], "units_per_launch": units,
+                "fp64_pipe_busy_ncu": FP64_PIPE_BUSY[args.precision].get(dom),
+                "traffic_note": "dram bytes per face of a 128^3 ncu capture x faces per launch"
+                if traffic is not None else "no ncu traffic figure for this kernel and precision",
+                "avg_launch_ms": avg_s * 1e3, "hbm_context": hbm_ctx, "time_share": share}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": hbm_ctx["achieved"], "peak": hbm, "unit": "GB/s",
+                "frac": hbm_ctx["frac"], "traffic": None, "peak_source": hbm_ctx["peak_source"],
+                "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_s * 1e3, "time_share": share}
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None
@@ -410,7 +467,7 @@ def run_ours(args, world, rank, local, dist):
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, z, nsteps_c, secs, threads, w = oracle_sample(prob, 50, args.cpu_budget)
+        v, z, nsteps_c, secs, threads, w = oracle_sample(prob, 400, args.cpu_budget, w=64)
         cpu = {"value": v / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{w}^3 periodic window of this input, {nsteps_c} SSP-RK3 steps, "
                          f"{secs:.1f} s, FP64 C oracle with OpenMP over cells",
@@ -422,8 +479,7 @@ def run_ours(args, world, rank, local, dist):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == 64 else "f32 stencil + f64 c2p/reductions",
         "data": "synthetic (seeded sweep_box)",
-        "config": {"workload": f"sweep_box {args.size}^3 periodic SRMHD, Gamma 4/3, CFL 0.4, "
-                               f"{'FP64' if args.precision == 64 else 'FP32 bulk'}",
+        "config": {"workload": workload_name(args),
                    "grid": list(n), "zones": zones, "parallelism": f"replicas x{world}",
                    "l2": "working set (~9 GB) larger than L2; no flush needed"},
         "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "variants": variants,

@@ -17,6 +17,12 @@ constexpr int NG = 3;              // ghost layers (MP5: 3 cells per side)
 constexpr double MP5_ALPHA = 4.0;  // Suresh & Huynh (1997) alpha
 constexpr double MP5_EPS = 1e-10;  // Suresh & Huynh (1997) epsilon
 constexpr double NEWTON_TOL = 1e-13;
+// Stopping tolerance of the FP64 Newton iterations when the primitives are
+// stored in FP32.  Newton converges quadratically: after a step with
+// |dZ| <= 1e-6 Z the remaining relative error is O((dZ/Z)^2) ~ 1e-12 times
+// the curvature factor, far below the 6e-8 rounding of the FP32 store, so
+// the confirming iteration that the 1e-13 rule needs is skipped.
+constexpr double NEWTON_TOL_BULK32 = 1e-6;
 constexpr int NEWTON_MAXIT = 50;
 constexpr int NEWTON_MAXHALF = 30;
 
@@ -544,7 +550,7 @@ __device__ __forceinline__ void p2c_point(const double P[8], double gr, const M 
 //   f(Z)   = Z - p + (1 + v^2) B^2 / 2 - (S.B)^2 / (2 Z^2) - (tau + D)
 // An inadmissible guess (Z <= 0 or v^2 >= 1) is replaced by doubling
 // max(Z, tau + D); a step leaving the admissible set is halved (<= 30 times);
-// stop at |dZ| <= 1e-13 Z or after 50 iterations.
+// stop at |dZ| <= tol Z (1e-13 by default) or after 50 iterations.
 struct C2PResult {
     double rho, v[3], p, Z;
     int iters;
@@ -602,7 +608,7 @@ __device__ __forceinline__ double c2p_refine_f32(double Zg, double S2d, double S
 template <typename M>
 __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], double tau, const double B[3],
                                                 double Zguess, double gm1g, const M &m, int maxit = NEWTON_MAXIT,
-                                                bool refine = false)
+                                                bool refine = false, double tol = NEWTON_TOL)
 {
     double Su[3], Bl[3];
     raise<double>(m, S, Su);
@@ -667,7 +673,7 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
         iZ = iZn;
         iZB = iZBn;
         v2 = v2n;
-        if (ile(iabs(dZ), NEWTON_TOL * Z)) {
+        if (ile(iabs(dZ), tol * Z)) {
             conv = true;
             break;
         }

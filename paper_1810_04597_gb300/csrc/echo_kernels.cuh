@@ -136,6 +136,7 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
         const bool refine = (guess_mode & 4) != 0;
         const double zg = src == 2 ? 0.0 : A.Z[id];
         const double Dc = to_d(A.U[0][id]) * isg, tc = to_d(A.U[4][id]) * isg;
+        constexpr double tol = sizeof(R) == 4 ? NEWTON_TOL_BULK32 : NEWTON_TOL;
         C2PResult r;
         if constexpr (MLP) {
             float f[MLP_NI], o[MLP_NO];
@@ -147,23 +148,23 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             const double Wg = exp((double)o[0]), pD = exp((double)o[1]);
             const double z0 = Dc * Wg * (1.0 + ph.gr * pD * Wg);
             if constexpr (MK == 1)
-                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MKS<double>(*mp), 8, refine);
+                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MKS<double>(*mp), 8, refine, tol);
             else
-                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MFlat<double>(), 8, refine);
+                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MFlat<double>(), 8, refine, tol);
             if (!r.ok) {
                 const int first = r.iters;
                 if constexpr (MK == 1)
-                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp));
+                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp), NEWTON_MAXIT, false, tol);
                 else
-                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>());
+                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>(), NEWTON_MAXIT, false, tol);
                 r.iters += first;
                 mfb = 1;
             }
         } else {
             if constexpr (MK == 1)
-                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp), NEWTON_MAXIT, refine);
+                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp), NEWTON_MAXIT, refine, tol);
             else
-                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>(), NEWTON_MAXIT, refine);
+                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>(), NEWTON_MAXIT, refine, tol);
         }
         its = r.iters;
         calls = 1;
@@ -606,18 +607,21 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
                 Est[s][u] = -(va[s][u] * Bb[s] - vb[s][u] * Ba[u]);
         }
     const T sA = apa + ama, sB = apb + amb;
-    T wLL, wLR, wRL, wRR;
+    T wLL, wLR, wRL, wRR, da, db;
     if (is_pos(sA) && is_pos(sB)) {
+        // one division: 1/sA = sB iden, 1/sB = sA iden
         const T iden = T(1) / (sA * sB);
         wLL = apa * apb * iden;
         wLR = apa * amb * iden;
         wRL = ama * apb * iden;
         wRR = ama * amb * iden;
+        da = apa * ama * (sB * iden);
+        db = apb * amb * (sA * iden);
     } else {
         wLL = wLR = wRL = wRR = T(0.25);
+        da = is_pos(sA) ? apa * ama / sA : T(0);
+        db = is_pos(sB) ? apb * amb / sB : T(0);
     }
-    const T da = is_pos(sA) ? apa * ama / sA : T(0);
-    const T db = is_pos(sB) ? apb * amb / sB : T(0);
     A.E[E][id] = wLL * Est[0][0] + wLR * Est[0][1] + wRL * Est[1][0] + wRR * Est[1][1]
                  + da * (Bb[1] - Bb[0]) - db * (Ba[1] - Ba[0]);
 }

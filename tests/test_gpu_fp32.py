@@ -56,3 +56,34 @@ def test_fp32_rhs_close_to_oracle(orc):
     L_o, _, _ = orc.rhs(cfg, st, Z)
     l1 = per_field(orc, L_g, L_o, prob.n, metric=l1_rel)
     assert max(l1.values()) <= 1e-4, l1
+
+
+def test_fp32_bulk_c2p_matches_fp64_solve():
+    """FP32 storage: the FP32-refined guess plus FP64 Newton with the
+    quadratic-convergence stop (|dZ| <= 1e-6 Z) lands on the FP64 solution of
+    the strict 1e-13 rule to far below FP32 rounding, mostly in one FP64
+    iteration."""
+    from paper_1810_04597_gb300.echo import Solver
+    prob = inputs.sweep_box(48, seed=21)
+    s32 = Solver(prob, precision=32)
+    s32.set_prims()
+    s32.step()
+    st = s32.get_state()                      # FP32 values, exact in FP64
+    z = s32.get_z()
+    rng = np.random.default_rng(5)
+    zg = z * (1.0 + 1e-3 * rng.uniform(-1.0, 1.0, z.shape))
+    s64 = Solver(prob, precision=64)
+    s64.set_state(st, zg)
+    s32.set_state(st, zg)
+    c0 = s32.counters()
+    t64 = s64.c2p(0)
+    t32 = s32.c2p(4)
+    c1 = s32.counters()
+    assert t64["c2p_fail"] == 0 and t32["c2p_fail"] == 0
+    z64, z32 = s64.get_z(), s32.get_z()
+    assert np.max(np.abs(z32 - z64) / z64) <= 1e-10
+    P64, P32 = s64.get_prims(), s32.get_prims()
+    for q in (0, 4):
+        assert np.max(np.abs(P32[q] - P64[q]) / np.abs(P64[q])) <= 2e-7, q
+    its = (c1["c2p_iters"] - c0["c2p_iters"]) / (c1["c2p_calls"] - c0["c2p_calls"])
+    assert its <= 1.5, its
