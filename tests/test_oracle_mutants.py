@@ -1,0 +1,65 @@
+"""Planted mistakes: each one is a plausible error in the oracle (a dropped
+term, a wrong sign, a swapped index or operand); a copy of the oracle with
+the mistake is built and the oracle's pins are run against it -- at least
+one pin must fail for every mistake.  The mistakes are planted only in
+copies of the C source built under oracle/_build/mutants/, on the CPU."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+OUT = os.path.join(ORACLE, "_build", "mutants")
+PINS = ["tests/test_oracle_pointwise.py", "tests/test_oracle_scheme.py", "tests/test_golden.py"]
+MLP_PINS = ["tests/test_oracle_mlp.py"]
+
+# (name, file, original text, planted text, pin files)
+MUTANTS = [
+    ("uct_diffusion_sign", "echo_oracle.c", "+ da * (Bb[1] - Bb[0]) - db * (Ba[1] - Ba[0])",
+     "- da * (Bb[1] - Bb[0]) - db * (Ba[1] - Ba[0])", PINS),
+    ("uct_weight_swap", "echo_oracle.c", "wLR = apa * amb / den;", "wLR = ama * apb / den;", PINS),
+    ("c2p_dropped_sb_term", "echo_oracle.c", "- SB * SB / (2.0 * Z * Z) - U;", "- U;", PINS),
+    ("mp5_coefficient", "echo_oracle.c", "47.0 * u0", "46.0 * u0", PINS),
+    ("flux_dropped_magnetic_stress", "echo_oracle.c", "- bu[d] * bl[j];", ";", PINS),
+    ("ks_shift_scaling", "echo_oracle.c", "beta[0] = z / (1.0 + z) / r;", "beta[0] = z / (1.0 + z);", PINS),
+    ("emf_side_labels", "echo_oracle.c", "Est[s][t] = -(vta * Bb[s] - vtb * Ba[t]);",
+     "Est[s][t] = -(vta * Bb[t] - vtb * Ba[s]);", PINS),
+    ("source_index_swap", "echo_oracle.c", "st += Wij * dbe[j][i];", "st += Wij * dbe[i][j];", PINS),
+    ("source_dropped_lapse_term", "echo_oracle.c", "s -= U * dal[i];", ";", PINS),
+    ("fast_speed_dropped_cross_term", "echo_oracle.c", "double a2 = cs2 + ca2 - cs2 * ca2;",
+     "double a2 = cs2 + ca2;", PINS),
+    ("mlp_dropped_activation", "mlp_oracle.c", "a2[k] = tanh(s);", "a2[k] = s;", MLP_PINS),
+]
+
+
+def _build(name, fname, old, new):
+    srcs = {}
+    for f in ("echo_oracle.c", "mlp_oracle.c"):
+        with open(os.path.join(ORACLE, f)) as fh:
+            srcs[f] = fh.read()
+    assert srcs[fname].count(old) >= 1, f"anchor of {name} not found"
+    srcs[fname] = srcs[fname].replace(old, new, 1)
+    d = os.path.join(OUT, name)
+    os.makedirs(d, exist_ok=True)
+    paths = []
+    for f, txt in srcs.items():
+        p = os.path.join(d, f)
+        with open(p, "w") as fh:
+            fh.write(txt)
+        paths.append(p)
+    lib = os.path.join(d, "liboracle_mutant.so")
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp",
+                    "-std=c11", "-w", "-o", lib, *paths, "-lm"], check=True, capture_output=True, text=True)
+    return lib
+
+
+@pytest.mark.parametrize("name,fname,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(name, fname, old, new, pins):
+    lib = _build(name, fname, old, new)
+    env = dict(os.environ, ECHO_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", *pins, "-x", "-q", "-p", "no:cacheprovider",
+                        "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"{name}: no pin failed\n{r.stdout[-1500:]}"
+    assert " failed" in r.stdout, r.stdout[-1500:]

@@ -287,6 +287,27 @@ def test_speeds_velocity_addition_sound(orc):
             assert abs(lm - (v - cs) / (1 - v * cs)) < 1e-14
 
 
+def test_speeds_perpendicular_fast_wave(orc):
+    """Field transverse to d, v along d: in the fluid frame the wave vector is
+    perpendicular to the field, where the relativistic fast magnetosonic speed
+    is exact, a^2 = (G p + b^2)/(rho h + b^2) (total-enthalpy form of the
+    RMHD dispersion relation; b^2 = B^2/W^2 since v.B = 0), and the lab speeds
+    follow by velocity addition along d."""
+    cfg = flat_cfg(orc)
+    for rho, p, v, bmag in [(1.0, 0.5, 0.0, 0.8), (0.3, 2.0, 0.6, 1.5), (2.0, 0.05, -0.9, 0.4)]:
+        W2 = 1.0 / (1.0 - v * v)
+        b2 = bmag * bmag / W2
+        a = np.sqrt((GAM * p + b2) / (rho + GAM / (GAM - 1) * p + b2))
+        for d in range(3):
+            P = np.zeros(8)
+            P[0], P[4] = rho, p
+            P[1 + d] = v
+            P[5 + (d + 1) % 3] = bmag
+            lp, lm = orc.speeds_point(cfg, np.zeros(3), P, d)
+            assert abs(lp - (v + a) / (1 + v * a)) < 1e-14
+            assert abs(lm - (v - a) / (1 - v * a)) < 1e-14
+
+
 def test_speeds_cold_alfven_limit(orc):
     """p -> 0 with v = 0: a -> the relativistic Alfven speed
     B^2/(rho + B^2) (comoving field at rest)."""
