@@ -179,30 +179,13 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_window(prob, w=48):
-    """The w^3 corner of the workload's seeded input as a periodic problem
-    (the oracle's bounded sample)."""
-    import numpy as np
-    from paper_1810_04597_gb300 import inputs
-    N = prob.n
-    prims = np.ascontiguousarray(prob.prims[:, :w, :w, :w])
-    o = 0
-    bx = prob.bface[o:o + N[2] * N[1] * (N[0] + 1)].reshape(N[2], N[1], N[0] + 1)
-    o += bx.size
-    by = prob.bface[o:o + N[2] * (N[1] + 1) * N[0]].reshape(N[2], N[1] + 1, N[0])
-    o += by.size
-    bz = prob.bface[o:o + (N[2] + 1) * N[1] * N[0]].reshape(N[2] + 1, N[1], N[0])
-    return inputs.Problem(name="window", n=(w, w, w), x0=(0, 0, 0), dx=prob.dx, cfl=prob.cfl,
-                          prims=prims, bface=inputs.pack_faces(bx[:w, :w, :w + 1], by[:w, :w + 1, :w],
-                                                               bz[:w + 1, :w, :w]))
-
-
 def oracle_sample(prob, nsteps_hint, budget_s, w=48):
-    """Time oracle SSP-RK3 steps on a w^3 window of the workload's seeded
-    input for about budget_s seconds.  Returns (zones_per_s, zones, steps,
-    seconds, threads, w)."""
+    """Time oracle SSP-RK3 steps on the workload's recipe at w^3 (a periodic
+    sweep_box of the same seeded recipe) for about budget_s seconds.
+    Returns (zones_per_s, zones, steps, seconds, threads, w)."""
     import oracle
-    win = oracle_window(prob, w)
+    from paper_1810_04597_gb300 import inputs
+    win = inputs.sweep_box(w)
     cfg = oracle.make_cfg(win)
     st, Z = oracle.p2c(cfg, win.prims, win.bface)
     t0 = time.perf_counter()
@@ -287,9 +270,8 @@ def run_reference(args, world, rank):
     from paper_1810_04597_gb300 import inputs
     import oracle
     oracle.build()
-    prob = inputs.sweep_box(args.size)
     w = min(64, args.size)
-    win = oracle_window(prob, w)
+    win = inputs.sweep_box(w)
     cfg = oracle.make_cfg(win)
     st, Z = oracle.p2c(cfg, win.prims, win.bface)
     st, Z, _, _ = oracle.steps(cfg, st, Z, args.warmup)
@@ -299,7 +281,7 @@ def run_reference(args, world, rank):
     zones = w ** 3
     value = zones * args.steps / dt / 1e6
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = (f"{w}^3 periodic window of the {args.size}^3 sweep_box input, {args.steps} oracle "
+    sample = (f"sweep_box recipe at {w}^3 (periodic; the {args.size}^3 workload's statistics), {args.steps} oracle "
               f"SSP-RK3 steps (after {args.warmup} warm-up), FP64, OpenMP over cells")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -307,7 +289,7 @@ def run_reference(args, world, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded)",
         "config": {"workload": workload_name(args), "grid": [args.size] * 3, "zones": args.size ** 3,
-                   "parallelism": "rank 0 only (host cores)", "sample": f"{w}^3 window per step"},
+                   "parallelism": "rank 0 only (host cores)", "sample": f"{w}^3 box of the same recipe per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample, "cpu": cpu_description()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -328,8 +310,13 @@ def run_ours(args, world, rank, local, dist):
     s = Solver(prob, precision=args.precision, device=str(dev))
     stream = s.stream
     s.set_prims()
-    if args.precision == 32:
-        s.set_c2p_guess(4)      # previous-stage Z refined by FP32 Newton steps
+    guess = args.guess if args.guess is not None else (4 if args.precision == 32 else 0)
+    if guess & 1:
+        # the network guess: train the default network first (untimed)
+        from paper_1810_04597_gb300 import mlp
+        state = mlp.default_network(device=str(dev))[0]
+        s.mlp_load(state)
+    s.set_c2p_guess(guess)
     for _ in range(args.warmup):
         s.step()
     torch.cuda.synchronize()
@@ -467,9 +454,9 @@ def run_ours(args, world, rank, local, dist):
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, z, nsteps_c, secs, threads, w = oracle_sample(prob, 400, args.cpu_budget, w=64)
+        v, z, nsteps_c, secs, threads, w = oracle_sample(prob, 50, args.cpu_budget, w=80)
         cpu = {"value": v / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{w}^3 periodic window of this input, {nsteps_c} SSP-RK3 steps, "
+               "sample": f"sweep_box recipe at {w}^3 (periodic), {nsteps_c} SSP-RK3 steps, "
                          f"{secs:.1f} s, FP64 C oracle with OpenMP over cells",
                "cpu": cpu_description()}
 
@@ -480,7 +467,7 @@ def run_ours(args, world, rank, local, dist):
         "dtype": "f64" if args.precision == 64 else "f32 stencil + f64 c2p/reductions",
         "data": "synthetic (seeded sweep_box)",
         "config": {"workload": workload_name(args),
-                   "grid": list(n), "zones": zones, "parallelism": f"replicas x{world}",
+                   "grid": list(n), "zones": zones, "parallelism": f"replicas x{world}", "c2p_guess": guess,
                    "l2": "working set (~9 GB) larger than L2; no flush needed"},
         "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "variants": variants,
         "gpu_launches": launches,
@@ -622,6 +609,8 @@ def main():
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--guess", type=int, default=None, choices=(0, 1, 4, 5, 9, 13),
+                    help="c2p guess mode of the main line (default: 0 for FP64, 4 for FP32)")
     args = ap.parse_args()
     world, rank, local = dist_info()
     if args.impl == "reference":

@@ -139,7 +139,9 @@ int echo_get_z(echo_ctx *ctx, double *Z, int on_device);
 /* Conservative-to-primitive inversion of the current state on every owned
  * cell.  guess_mode: 0 = the stored Z of the cell (previous stage), 1 = the
  * c2p-guess network (see below), 2 = cold guess (Z = 0, replaced by the
- * admissibility rule); adding 4 refines the guess in FP32 first.  If stats is non-NULL
+ * admissibility rule); adding 4 refines the guess in FP32 first; adding 8 to
+ * mode 1 or 5 runs the network on the CUDA cores instead of the tensor
+ * cores.  Other values: ECHO_EINVAL.  If stats is non-NULL
  * the call synchronises and fills the counters and dt_cfl of stats (the
  * other fields are left untouched) and returns ECHO_EC2P if any cell failed. */
 int echo_c2p(echo_ctx *ctx, int guess_mode, echo_totals *stats);
@@ -205,6 +207,11 @@ int echo_mlp_grad(const float *dev_state, const float *X, const float *Y, long l
 
 /* Standardised network outputs (n x 3, device) of n feature rows. */
 int echo_mlp_forward(const float *dev_state, const float *X, long long n, float *out, void *cuda_stream);
+/* The same with the 64 x 64 hidden layer on the tensor cores (tcgen05 MMA,
+ * BF16 inputs, FP32 accumulation; layers 1 and 3 in FP32), as the c2p
+ * kernel evaluates the network.  Rows whose tensor-core result did not
+ * arrive within about a second get NaN. */
+int echo_mlp_forward_tc(const float *dev_state, const float *X, long long n, float *out, void *cuda_stream);
 
 /* Training rows from the current state: runs a c2p (previous-stage guess),
  * then writes for every owned cell its features and targets at row
@@ -219,7 +226,10 @@ int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
 /* Newton guess used by echo_step/echo_rhs: 0 previous-stage Z (default),
  * 1 network (requires echo_mlp_load); adding 4 first refines that guess by
  * up to four Newton steps of the same residual in FP32 (the FP64 iterations
- * that follow still decide convergence). */
+ * that follow still decide convergence).  The network's hidden layer runs on
+ * the tensor cores (as echo_mlp_forward_tc); adding 8 to a network mode
+ * evaluates it in FP32 on the CUDA cores instead (modes 9, 13).  Accepted:
+ * 0, 1, 4, 5, 9, 13; echo_c2p also takes 2 (cold guess) and 6. */
 int echo_set_c2p_guess(echo_ctx *ctx, int mode);
 
 /* Copy the cumulative counters (c2p_iters, c2p_calls, c2p_fail, floor_hits,
@@ -281,6 +291,11 @@ void echo_batch_destroy(echo_batch *batch);
  * number of mismatches to *dev_mismatch (device, caller-zeroed). */
 int echo_selftest_conversions(long long n, unsigned long long seed, unsigned long long *dev_mismatch,
                               void *cuda_stream);
+/* Self-check of the library's Newton-Raphson FP64 reciprocal (used in the
+ * c2p Newton solve in place of IEEE divisions) against the IEEE quotient on n
+ * hashed values (both signs, exponents -300..300): atomically maxes the
+ * largest distance in ulp into *dev_max_ulp (device, caller-zeroed). */
+int echo_selftest_recip(long long n, unsigned long long seed, unsigned long long *dev_max_ulp, void *cuda_stream);
 
 /* Kernel classes timed by the profiling facility below. */
 #define ECHO_K_FILL_FACES 0

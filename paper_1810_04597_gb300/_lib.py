@@ -94,6 +94,7 @@ _SIGS = {
     "echo_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "echo_counters": (ctypes.c_int, [_P, ctypes.POINTER(echo_totals)]),
     "echo_selftest_conversions": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
+    "echo_selftest_recip": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
     "echo_batch_workspace_bytes": (ctypes.c_size_t, [_P]),
     "echo_batch_bind": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
@@ -114,6 +115,7 @@ _SIGS = {
     "echo_mlp_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int,
                                      ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P]),
     "echo_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P]),
+    "echo_mlp_forward_tc": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P]),
     "echo_mlp_dataset": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong]),
     "echo_mlp_load": (ctypes.c_int, [_P, _P]),
     "echo_set_c2p_guess": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -352,6 +354,11 @@ def echo_mlp_forward(state, X, n, out, stream_handle: int = 0):
                                    _P(_dev_f32(out, "out")), _P(stream_handle)), "echo_mlp_forward")
 
 
+def echo_mlp_forward_tc(state, X, n, out, stream_handle: int = 0):
+    _plain(load().echo_mlp_forward_tc(_P(_dev_f32(state, "state")), _P(_dev_f32(X, "X")), int(n),
+                                      _P(_dev_f32(out, "out")), _P(stream_handle)), "echo_mlp_forward_tc")
+
+
 def echo_mlp_dataset(ctx, X, Y, capacity, offset, stride):
     _check(ctx, load().echo_mlp_dataset(ctx, _P(_dev_f32(X, "X")), _P(_dev_f32(Y, "Y")), int(capacity),
                                         int(offset), int(stride)))
@@ -420,6 +427,11 @@ def echo_batch_step(b, dt=0.0):
 
 def echo_batch_destroy(b):
     load().echo_batch_destroy(b)
+
+
+def echo_selftest_recip(n, seed, dev_max, stream_handle: int = 0):
+    _plain(load().echo_selftest_recip(int(n), ctypes.c_ulonglong(seed), _P(_dev_any(dev_max, "max")),
+                                      _P(stream_handle)), "echo_selftest_recip")
 
 
 def echo_selftest_conversions(n, seed, dev_counter, stream_handle: int = 0):

@@ -486,8 +486,9 @@ int echo_c2p(echo_ctx *c, int guess_mode, echo_totals *stats)
     int rc = require_bound(c, true);
     if (rc)
         return rc;
-    if (guess_mode < 0 || guess_mode > 6 || guess_mode == 3)
-        return fail(c, ECHO_EINVAL, "guess_mode: 0 previous Z, 1 network, 2 cold, +4 FP32 refinement");
+    if (guess_mode < 0 || guess_mode > 13 || (guess_mode & 3) == 3 || ((guess_mode & 8) && (guess_mode & 3) != 1))
+        return fail(c, ECHO_EINVAL,
+                    "guess_mode: 0 previous Z, 1 network, 2 cold, +4 FP32 refinement, +8 network on the CUDA cores");
     if ((guess_mode & 3) == 1 && !c->mlp_loaded)
         return fail(c, ECHO_ESTATE, "no c2p-guess network loaded: call echo_mlp_load first");
     rc = ECHO_DISPATCH(c, op_c2p, guess_mode);
@@ -631,8 +632,9 @@ int echo_set_c2p_guess(echo_ctx *c, int mode)
 {
     if (!c)
         return ECHO_EINVAL;
-    if (mode != 0 && mode != 1 && mode != 4 && mode != 5)
-        return fail(c, ECHO_EINVAL, "c2p guess mode: 0 previous Z, 1 network, +4 FP32 refinement");
+    if (mode != 0 && mode != 1 && mode != 4 && mode != 5 && mode != 9 && mode != 13)
+        return fail(c, ECHO_EINVAL,
+                    "c2p guess mode: 0 previous Z, 1 network, +4 FP32 refinement, +8 network on the CUDA cores");
     if ((mode & 3) == 1 && !c->mlp_loaded)
         return fail(c, ECHO_ESTATE, "no c2p-guess network loaded: call echo_mlp_load first");
     c->c2p_guess = mode;

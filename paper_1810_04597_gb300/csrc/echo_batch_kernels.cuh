@@ -56,7 +56,7 @@ template <int MK, typename R, bool MLP>
 __device__ __noinline__ void nl_c2p(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess, int rate, long long t,
                                     const float *sm)
 {
-    c2p_body<MK, R, MLP>(g, ph, A, guess, rate, t, sm);
+    c2p_body<MK, R, MLP ? 1 : 0>(g, ph, A, guess, rate, t, sm);
 }
 template <int D, int MK, typename R>
 __device__ __noinline__ void nl_faces(const Geom &g, const Phys &ph, const Arrays<R> &A, long long t,
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(128) k_bphase_c2p(const RunDesc<R> *__restrict
     const RunDesc<R> &rd = runs[sgm.run];
     const long long base = (tl - sgm.first_tile) * plan->tile;
     for (int c = 0; c < plan->tile; c += blockDim.x)
-        c2p_body<MK, R, MLP>(rd.g, ph, rd.A, guess_mode, want_rate, base + c + threadIdx.x, sm);
+        c2p_body<MK, R, MLP ? 1 : 0>(rd.g, ph, rd.A, guess_mode, want_rate, base + c + threadIdx.x, sm);
 }
 
 template <int MK, typename R>

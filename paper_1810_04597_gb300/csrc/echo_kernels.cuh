@@ -14,6 +14,7 @@
 #include "echo_device.cuh"
 #include "echo_launch.h"
 #include "echo_mlp.cuh"
+#include "echo_mlp_tc.cuh"
 
 namespace echo {
 
@@ -103,56 +104,112 @@ __global__ void k_fill(Geom g, int d, FillList<R> L)
 // Body over the linear index t of the owned cells (x fastest); every lane of
 // a warp must call it (warp-level counter reductions).  mlp_sm: the network
 // block in shared memory when MLP.
-template <int MK, typename R, bool MLP>
-__device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mode,
-                                         int want_rate, long long t, const float *mlp_sm)
+// Inputs of the inversion at owned cell t (x fastest): undensitised D, S_i,
+// tau, the cell-centre B (mean of the two faces), sqrt(gamma) and the metric
+// point.  Returns false for t beyond the owned cells.
+struct C2PCell {
+    long long id;
+    int i, j;
+    double B[3], S[3], Dc, tc, sg;
+    const MetPt *mp;
+};
+
+template <int MK, typename R>
+__device__ __forceinline__ bool c2p_cell(const Geom &g, const Arrays<R> &A, long long t, C2PCell &c)
 {
     const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
-    const bool live = t < ncell;
-    int i = NG, j = NG, k = NG;
-    if (live) {
-        i = NG + (int)(t % g.n[0]);
-        const long long r = t / g.n[0];
-        j = NG + (int)(r % g.n[1]);
-        k = NG + (int)(r / g.n[1]);
+    if (t >= ncell)
+        return false;
+    c.i = NG + (int)(t % g.n[0]);
+    const long long r = t / g.n[0];
+    c.j = NG + (int)(r % g.n[1]);
+    const int k = NG + (int)(r / g.n[1]);
+    const long long id = gidx(g, c.i, c.j, k);
+    c.id = id;
+    c.sg = 1.0;
+    c.mp = nullptr;
+    if constexpr (MK == 1) {
+        c.mp = &A.met.C[c.j * A.met.np0 + c.i];
+        const double isg = c.mp->isg;
+        c.sg = c.mp->sg;
+        c.B[0] = 0.5 * (to_d(A.U[5][id]) + to_d(A.U[5][id + 1])) * isg;
+        c.B[1] = 0.5 * (to_d(A.U[6][id]) + to_d(A.U[6][id + g.px])) * isg;
+        c.B[2] = 0.5 * (to_d(A.U[7][id]) + to_d(A.U[7][id + g.pxy])) * isg;
+        for (int q = 0; q < 3; ++q)
+            c.S[q] = to_d(A.U[1 + q][id]) * isg;
+        c.Dc = to_d(A.U[0][id]) * isg;
+        c.tc = to_d(A.U[4][id]) * isg;
+    } else {
+        c.B[0] = 0.5 * (to_d(A.U[5][id]) + to_d(A.U[5][id + 1]));
+        c.B[1] = 0.5 * (to_d(A.U[6][id]) + to_d(A.U[6][id + g.px]));
+        c.B[2] = 0.5 * (to_d(A.U[7][id]) + to_d(A.U[7][id + g.pxy]));
+        for (int q = 0; q < 3; ++q)
+            c.S[q] = to_d(A.U[1 + q][id]);
+        c.Dc = to_d(A.U[0][id]);
+        c.tc = to_d(A.U[4][id]);
     }
+    return true;
+}
+
+template <int MK>
+__device__ __forceinline__ void c2p_cell_features(const C2PCell &c, float f[MLP_NI])
+{
+    if constexpr (MK == 1)
+        mlp_features(c.Dc, c.S, c.tc, c.B, c.sg, MKS<double>(*c.mp), f);
+    else
+        mlp_features(c.Dc, c.S, c.tc, c.B, 1.0, MFlat<double>(), f);
+}
+
+// MLPK: 0 no network; 1 network evaluated here (CUDA cores, parameter block
+// mlp_sm in shared memory); 2 network outputs net[0..1] (log W, log(p/D))
+// computed by the caller, usable if net_ok.
+template <int MK, typename R, int MLPK>
+__device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mode,
+                                         int want_rate, long long t, const float *mlp_sm,
+                                         const float *net = nullptr, bool net_ok = false)
+{
+    C2PCell c;
+    const bool live = c2p_cell<MK, R>(g, A, t, c);
     double rate = 0.0;
     unsigned long long its = 0, calls = 0, fails = 0, floors = 0, mfb = 0;
     if (live) {
-        const long long id = gidx(g, i, j, k);
-        double isg = 1.0, sg = 1.0;
-        const MetPt *mp = nullptr;
-        if constexpr (MK == 1) {
-            mp = &A.met.C[j * A.met.np0 + i];
-            isg = mp->isg;
-            sg = mp->sg;
-        }
-        double B[3];
-        B[0] = 0.5 * (to_d(A.U[5][id]) + to_d(A.U[5][id + 1])) * isg;
-        B[1] = 0.5 * (to_d(A.U[6][id]) + to_d(A.U[6][id + g.px])) * isg;
-        B[2] = 0.5 * (to_d(A.U[7][id]) + to_d(A.U[7][id + g.pxy])) * isg;
-        const double S[3] = {to_d(A.U[1][id]) * isg, to_d(A.U[2][id]) * isg, to_d(A.U[3][id]) * isg};
+        const long long id = c.id;
+        const int i = c.i;
+        const MetPt *mp = c.mp;
+        const double sg = c.sg;
+        const double *B = c.B, *S = c.S;
+        const double Dc = c.Dc, tc = c.tc;
         const int src = guess_mode & 3;
         const bool refine = (guess_mode & 4) != 0;
         const double zg = src == 2 ? 0.0 : A.Z[id];
-        const double Dc = to_d(A.U[0][id]) * isg, tc = to_d(A.U[4][id]) * isg;
         constexpr double tol = sizeof(R) == 4 ? NEWTON_TOL_BULK32 : NEWTON_TOL;
         C2PResult r;
-        if constexpr (MLP) {
-            float f[MLP_NI], o[MLP_NO];
-            if constexpr (MK == 1)
-                mlp_features(Dc, S, tc, B, sg, MKS<double>(*mp), f);
-            else
-                mlp_features(Dc, S, tc, B, 1.0, MFlat<double>(), f);
-            mlp_infer(mlp_sm, f, o);
-            const double Wg = exp((double)o[0]), pD = exp((double)o[1]);
-            const double z0 = Dc * Wg * (1.0 + ph.gr * pD * Wg);
-            if constexpr (MK == 1)
-                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MKS<double>(*mp), 8, refine, tol);
-            else
-                r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MFlat<double>(), 8, refine, tol);
+        if constexpr (MLPK != 0) {
+            float o[MLP_NO];
+            bool have = true;
+            if constexpr (MLPK == 1) {
+                float f[MLP_NI];
+                c2p_cell_features<MK>(c, f);
+                mlp_infer(mlp_sm, f, o);
+            } else {
+                o[0] = net[0];
+                o[1] = net[1];
+                have = net_ok;
+            }
+            int first = 0;
+            r.ok = false;
+            if (have) {
+                // Z0 = D W (1 + G/(G-1) (p/D) W) in FP32: it is only the start
+                // of the Newton solve (the FP64 pipe is the scarce one)
+                const float Wg = expf(o[0]), pD = expf(o[1]);
+                const double z0 = f2d(d2f(Dc) * Wg * (1.0f + ph.gr_f * pD * Wg));
+                if constexpr (MK == 1)
+                    r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MKS<double>(*mp), 8, refine, tol);
+                else
+                    r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MFlat<double>(), 8, refine, tol);
+                first = r.iters;
+            }
             if (!r.ok) {
-                const int first = r.iters;
                 if constexpr (MK == 1)
                     r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp), NEWTON_MAXIT, false, tol);
                 else
@@ -243,7 +300,36 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
         __syncthreads();
         sm = Ps;
     }
-    c2p_body<MK, R, MLP>(g, ph, A, guess_mode, want_rate, (long long)blockIdx.x * blockDim.x + threadIdx.x, sm);
+    c2p_body<MK, R, MLP ? 1 : 0>(g, ph, A, guess_mode, want_rate, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                                 sm);
+}
+
+// c2p with the network guess, its hidden layer on the tensor cores
+// (echo_mlp_tc.cuh): persistent CTAs of 128 threads walk tiles of 128 cells;
+// per tile every thread computes its cell's features, the CTA runs the
+// network (one tcgen05 MMA group), then every thread inverts its cell.  A
+// tile whose tensor-core result did not arrive falls back to the previous-
+// stage guess (counted in mlp_fallback).
+template <int MK, typename R>
+__global__ void __launch_bounds__(128) k_c2p_tc(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate,
+                                                long long ntiles)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    TcMlp tm;
+    tc_setup(tm, tc_smem, A.mlp);
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long t = tile * 128 + threadIdx.x;
+        C2PCell c;
+        float f[MLP_NI], o[MLP_NO];
+        if (c2p_cell<MK, R>(g, A, t, c))
+            c2p_cell_features<MK>(c, f);
+        else
+            for (int q = 0; q < MLP_NI; ++q)
+                f[q] = tm.P[TP_NORM + q];
+        const bool ok = tc_tile(tm, f, o);
+        c2p_body<MK, R, 2>(g, ph, A, guess_mode, want_rate, t, nullptr, o, ok);
+    }
+    tc_teardown(tm);
 }
 
 // ------------------------------------------------------------------ limiter

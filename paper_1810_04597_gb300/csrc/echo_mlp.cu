@@ -11,6 +11,7 @@
 
 #include "../../include/echo.h"
 #include "echo_mlp.cuh"
+#include "echo_mlp_tc.cuh"
 
 namespace echo {
 
@@ -313,6 +314,30 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float *__restrict__ P
         out[r * 3 + q] = (o[q] - P[MLP_ONORM + 2 * MLP_NI + q]) / P[MLP_ONORM + 2 * MLP_NI + MLP_NO + q];
 }
 
+// Forward pass with the hidden layer on the tensor cores (persistent CTAs of
+// 128 rows); standardised outputs like k_mlp_forward, NaN where the
+// tensor-core result did not arrive.
+__global__ void __launch_bounds__(128) k_mlp_forward_tc(const float *__restrict__ P, const float *__restrict__ x,
+                                                        long long n, float *__restrict__ out, long long ntiles)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    TcMlp t;
+    tc_setup(t, tc_smem, P);
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long r = tile * 128 + threadIdx.x;
+        float f[MLP_NI], o[MLP_NO];
+#pragma unroll
+        for (int i = 0; i < MLP_NI; ++i)
+            f[i] = r < n ? x[r * 9 + i] : t.P[TP_NORM + i];
+        const bool ok = tc_tile(t, f, o);
+        if (r < n)
+            for (int q = 0; q < MLP_NO; ++q)
+                out[r * 3 + q] = ok ? (o[q] - t.P[TP_NORM + 2 * MLP_NI + q]) / t.P[TP_NORM + 2 * MLP_NI + MLP_NO + q]
+                                    : __int_as_float(0x7fc00000);
+    }
+    tc_teardown(t);
+}
+
 }  // namespace echo
 
 using namespace echo;
@@ -386,6 +411,21 @@ int echo_mlp_train(float *state, const float *x, const float *y, long long n, in
         const double c2 = 1.0 - pow(0.999, (double)(t + 1));
         k_mlp_adam<<<(MLP_NPAR + 127) / 128, 128, 0, s>>>(state, grad, lr, (float)c1, (float)c2);
     }
+    return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
+}
+
+int echo_mlp_forward_tc(const float *state, const float *x, long long n, float *out, void *stream)
+{
+    if (!state || !x || !out || n < 0)
+        return ECHO_EINVAL;
+    if (n == 0)
+        return ECHO_OK;
+    static int resident = 0;
+    if (resident == 0)
+        resident = tc_resident_ctas((const void *)k_mlp_forward_tc, TC_SMEM);
+    const long long ntiles = (n + 127) / 128;
+    const long long grid = ntiles < resident ? ntiles : resident;
+    k_mlp_forward_tc<<<(unsigned)grid, 128, TC_SMEM, static_cast<cudaStream_t>(stream)>>>(state, x, n, out, ntiles);
     return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
 }
 

@@ -1,6 +1,7 @@
 // echo_selftest.cu -- self-check of device helpers that replace hardware
 // instructions: the integer-pipe float <-> double conversions must equal the
-// hardware casts bit for bit.
+// hardware casts bit for bit; the Newton-Raphson reciprocal must stay within
+// 2 ulp of the IEEE quotient.
 #include "../../include/echo.h"
 #include "echo_device.cuh"
 
@@ -59,7 +60,32 @@ __global__ void k_check_conversions(long long n, unsigned long long seed, unsign
         atomicAdd(mismatch, bad);
 }
 
+// Largest distance in ulp between nr_recip(d) and the IEEE quotient 1/d over
+// hashed d of both signs with exponents across [-300, 300].
+__global__ void k_check_recip(long long n, unsigned long long seed, unsigned long long *max_ulp)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const unsigned long long h = mix64(seed ^ (unsigned long long)i);
+    const unsigned long long e = 1023ULL - 300ULL + (h >> 52) % 601ULL;
+    const unsigned long long m = mix64(h) & 0xfffffffffffffULL;
+    const double d = __longlong_as_double((long long)(((h & 1ULL) << 63) | (e << 52) | m));
+    const long long a = __double_as_longlong(nr_recip(d)), b = __double_as_longlong(1.0 / d);
+    const unsigned long long dist = (unsigned long long)(a > b ? a - b : b - a);
+    atomicMax(max_ulp, dist);
+}
+
 }  // namespace echo
+
+extern "C" int echo_selftest_recip(long long n, unsigned long long seed, unsigned long long *dev_max_ulp, void *stream)
+{
+    if (n < 1 || !dev_max_ulp)
+        return ECHO_EINVAL;
+    echo::k_check_recip<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, seed,
+                                                                                                 dev_max_ulp);
+    return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
+}
 
 extern "C" int echo_selftest_conversions(long long n, unsigned long long seed, unsigned long long *dev_mismatch,
                                          void *stream)

@@ -20,6 +20,20 @@ def test_integer_pipe_conversions_equal_hardware_casts():
     assert int(cnt.item()) == 0
 
 
+def test_newton_raphson_reciprocal_within_two_ulp():
+    """The c2p solve divides through a Newton-Raphson-refined reciprocal of
+    the hardware's approximate one; it must stay within 2 ulp of the IEEE
+    quotient."""
+    import torch
+    from paper_1810_04597_gb300 import _lib
+    mx = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for seed in (4, 5):
+        _lib.echo_selftest_recip(1 << 22, seed, mx)
+    torch.cuda.synchronize()
+    print("max ulp distance of the Newton-Raphson reciprocal:", int(mx.item()))
+    assert int(mx.item()) <= 2
+
+
 @pytest.mark.parametrize("precision", [64, 32])
 def test_fp32_refined_guess_converges_to_the_same_state(precision):
     """Guess mode +4 (FP32 Newton pre-refinement): same converged state as the

@@ -162,3 +162,75 @@ def test_gain_over_guesses_without_network(trained, torch):
     assert res["network"] < res["cold"]
     scale = np.max(np.abs(fin["previous"]))
     assert np.max(np.abs(fin["network"] - fin["previous"])) <= 1e-11 * scale
+
+
+def _bf16(a):
+    """Round to the nearest BF16 (ties to even), returned as float64."""
+    b = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _forward_bf16_hidden(st, x):
+    """FP64 forward pass with the tensor-core operands rounded as the GPU
+    rounds them: h1 (from FP32) and W2 to BF16; raw outputs."""
+    P = st.astype(np.float64)
+    mu, sd = P[4995:5004], P[5004:5013]
+    W1, b1 = P[0:576].reshape(64, 9), P[576:640]
+    W2, b2 = P[640:4736].reshape(64, 64), P[4736:4800]
+    W3, b3 = P[4800:4992].reshape(3, 64), P[4992:4995]
+    xs = (x.astype(np.float64) - mu) / sd
+    h1 = _bf16(np.tanh(xs @ W1.T + b1).astype(np.float32))
+    h2 = np.tanh(h1 @ _bf16(W2.astype(np.float32)).T + b2)
+    return h2 @ W3.T + b3
+
+
+def test_tensor_core_forward(orc, torch):
+    """The hidden layer on the tensor cores (tcgen05, BF16 operands, FP32
+    accumulation) equals the FP64 forward pass with the same BF16 roundings;
+    ragged last tile included."""
+    from paper_1810_04597_gb300 import _lib
+    rng = np.random.default_rng(3)
+    st = random_state(torch, rng)
+    n = 4099
+    x, _ = random_rows(rng, n)
+    dst, dx = torch.from_numpy(st).cuda(), torch.from_numpy(x).cuda()
+    out = torch.full((n, 3), -7.0, dtype=torch.float32, device="cuda")
+    _lib.echo_mlp_forward_tc(dst, dx, n, out)
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    emu = _forward_bf16_hidden(st[:4995 + 24], x)
+    d = np.abs(got - emu)
+    # FP32 layer 1 can flip a BF16 rounding of h1 in rare rows
+    assert np.median(d) <= 1e-5 and np.max(d) <= 2e-3, (np.median(d), np.max(d))
+    ref = orc.mlp_forward(st[:4995 + 24].astype(np.float64), x.astype(np.float64))
+    print("tensor-core forward: max |tc - fp64| =", np.max(np.abs(got - ref)), " max |tc - bf16 model| =", d.max())
+
+
+@pytest.mark.parametrize("precision,modes", [(64, (9, 1)), (32, (13, 5))])
+def test_tensor_core_guess_gives_the_same_inversion(trained, torch, precision, modes):
+    """c2p from the network guess evaluated on the tensor cores and on the CUDA
+    cores: Newton decides, so the primitives agree (FP64: to 1e-12; FP32
+    storage: to its rounding), with no fallback."""
+    from paper_1810_04597_gb300.echo import Solver
+    state, _, _ = trained
+    prob = inputs.sweep_box(41, seed=78)          # 68,921 cells: a ragged last tile
+    out = []
+    for m in modes:
+        s = Solver(prob, precision=precision)
+        s.set_prims()
+        s.mlp_load(state)
+        s.step()
+        c0 = s.counters()
+        s.c2p(m)
+        c1 = s.counters()
+        out.append((s.get_prims(), s.get_z(), c1["mlp_fallback"] - c0["mlp_fallback"],
+                    (c1["c2p_iters"] - c0["c2p_iters"]) / (c1["c2p_calls"] - c0["c2p_calls"])))
+    (Pa, Za, fa, ia), (Pb, Zb, fb, ib) = out
+    assert fb == 0 and fa == 0
+    assert np.max(np.abs(Za - Zb) / Za) <= (1e-12 if precision == 64 else 1e-10)
+    tol = 1e-12 if precision == 64 else 2.5e-7
+    for q in range(5):
+        assert np.max(np.abs(Pa[q] - Pb[q])) <= tol * max(np.max(np.abs(Pa[q])), 1e-300), q
+    print(f"precision {precision}: Newton iterations per call, CUDA-core guess {ia:.3f}, tensor-core guess {ib:.3f}")
+    assert abs(ia - ib) <= 0.5
