@@ -173,6 +173,17 @@ template <typename T>
 __device__ __forceinline__ bool ilt(T a, T b) { return okey(a) < okey(b); }
 template <typename T>
 __device__ __forceinline__ bool ile(T a, T b) { return okey(a) <= okey(b); }
+// FP32 has one-instruction min/max and comparisons on the fast pipes: use
+// them (the integer form would cost 3-6 integer instructions each).  They
+// differ from the integer forms only in the order of -0 and +0.
+template <>
+__device__ __forceinline__ float imin<float>(float a, float b) { return fminf(a, b); }
+template <>
+__device__ __forceinline__ float imax<float>(float a, float b) { return fmaxf(a, b); }
+template <>
+__device__ __forceinline__ bool ilt<float>(float a, float b) { return a < b; }
+template <>
+__device__ __forceinline__ bool ile<float>(float a, float b) { return a <= b; }
 __device__ __forceinline__ double with_sign_of(double mag, double s)
 {
     return __longlong_as_double(__double_as_longlong(mag)
@@ -182,6 +193,45 @@ __device__ __forceinline__ float with_sign_of(float mag, float s)
 {
     return __int_as_float(__float_as_int(mag) | (__float_as_int(s) & (int)0x80000000u));
 }
+
+// Reciprocal 1/d by Newton-Raphson refinement of the hardware's approximate
+// FP64 reciprocal (rcp.approx.ftz.f64): r <- r + r (1 - d r), two FMAs a
+// step; each step squares the relative error, two reach the last bits of
+// FP64 (within 2 ulp of the IEEE quotient, checked by
+// echo_selftest_recip).  For normal, finite, non-zero d: 4 DFMA where an
+// IEEE division costs about 8.6 DFMA slots on GB300.
+__device__ __forceinline__ double nr_recip(double d)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
+// n / d through nr_recip when |d| is safely normal, else the IEEE division.
+// The product is rounded on its own (__dmul_rn is never fused into a
+// neighbouring add), so, like a division, the result does not depend on how
+// the compiler contracts the code around it (kernels that share this code
+// stay bitwise equal).
+__device__ __forceinline__ double nr_div(double n, double d)
+{
+    const double a = iabs(d);
+    return (ilt(1e-200, a) && ilt(a, 1e200)) ? __dmul_rn(n, nr_recip(d)) : n / d;
+}
+
+// 1/x for the stencil: the IEEE division in FP64 (kernels that share the
+// stencil code -- single runs and the batched schedules -- then agree
+// bitwise); in FP32 the hardware reciprocal (MUFU, within 2 ulp for normal
+// x) -- FP32 results are compared in L1 at 1e-5.
+template <typename T>
+__device__ __forceinline__ T fast_recip(T x);
+template <>
+__device__ __forceinline__ double fast_recip<double>(double x) { return 1.0 / x; }
+template <>
+__device__ __forceinline__ float fast_recip<float>(float x) { return __fdividef(1.0f, x); }
+
 
 // ------------------------------------------------------------------ exact
 // float <-> double conversions on the integer pipe
@@ -246,9 +296,11 @@ template <typename T>
 struct MKS {
     static constexpr bool flat = false;
     T al, b1, g11, g13, g22, g33, i11, i13, i22, i33, sg;
+    // FP64 -> T through from_d (integer pipe for FP32)
     __device__ __forceinline__ explicit MKS(const MetPt &m)
-        : al((T)m.al), b1((T)m.b1), g11((T)m.g11), g13((T)m.g13), g22((T)m.g22), g33((T)m.g33),
-          i11((T)m.i11), i13((T)m.i13), i22((T)m.i22), i33((T)m.i33), sg((T)m.sg)
+        : al(from_d<T>(m.al)), b1(from_d<T>(m.b1)), g11(from_d<T>(m.g11)), g13(from_d<T>(m.g13)),
+          g22(from_d<T>(m.g22)), g33(from_d<T>(m.g33)), i11(from_d<T>(m.i11)), i13(from_d<T>(m.i13)),
+          i22(from_d<T>(m.i22)), i33(from_d<T>(m.i33)), sg(from_d<T>(m.sg))
     {
     }
 };
@@ -444,7 +496,7 @@ __device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m
     const T rmg = rhoh - gam * p;
     const T disc = Gs * iW2 * (Y * gup<D, T>(m) - rmg * vd * vd);
     const T sq = sqrt(is_pos(disc) ? disc : T(0));
-    const T iY = T(1) / Y;
+    const T iY = fast_recip(Y);
     const T base = vd * rmg;
     if constexpr (M::flat) {
         F[0] = Dn * vd;
@@ -478,38 +530,40 @@ __device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m
 }
 
 // Sum over directions of max(|lambda+|, |lambda-|)/dx (CFL rate) of a cell
-// (same eigenvalue form as state_flux), FP64.
-template <typename M>
-__device__ __forceinline__ double cfl_rate(const double P[8], double gam, double gr, const double idx[3], const M &m)
+// (same eigenvalue form as state_flux) in T: FP64 for FP64 storage; with
+// FP32 storage the speeds are evaluated in FP32 like the face speeds of that
+// path, and only their max over cells (the reduction) is FP64.
+template <typename M, typename T>
+__device__ __forceinline__ T cfl_rate(const T P[8], T gam, T gr, const T idx[3], const M &m)
 {
-    const double v[3] = {P[1], P[2], P[3]}, B[3] = {P[5], P[6], P[7]};
-    double vl[3], Bl[3];
-    lower<double>(m, v, vl);
-    lower<double>(m, B, Bl);
-    const double p = P[4];
-    const double v2 = vl[0] * v[0] + vl[1] * v[1] + vl[2] * v[2];
-    const double B2 = Bl[0] * B[0] + Bl[1] * B[1] + Bl[2] * B[2];
-    const double vB = vl[0] * B[0] + vl[1] * B[1] + vl[2] * B[2];
-    const double iW2 = 1.0 - v2;
-    const double rhoh = P[0] + gr * p;
-    const double b2 = B2 * iW2 + vB * vB;
-    const double Gs = gam * p + b2;
-    const double Y = (rhoh + b2) - v2 * Gs;
-    const double rmg = rhoh - gam * p;
-    const double iY = 1.0 / Y;
-    double s = 0.0;
+    const T v[3] = {P[1], P[2], P[3]}, B[3] = {P[5], P[6], P[7]};
+    T vl[3], Bl[3];
+    lower<T>(m, v, vl);
+    lower<T>(m, B, Bl);
+    const T p = P[4];
+    const T v2 = vl[0] * v[0] + vl[1] * v[1] + vl[2] * v[2];
+    const T B2 = Bl[0] * B[0] + Bl[1] * B[1] + Bl[2] * B[2];
+    const T vB = vl[0] * B[0] + vl[1] * B[1] + vl[2] * B[2];
+    const T iW2 = T(1) - v2;
+    const T rhoh = P[0] + gr * p;
+    const T b2 = B2 * iW2 + vB * vB;
+    const T Gs = gam * p + b2;
+    const T Y = (rhoh + b2) - v2 * Gs;
+    const T rmg = rhoh - gam * p;
+    const T iY = fast_recip(Y);
+    T s = T(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        double gdd = 1.0, al = 1.0, be = 0.0;
+        T gdd = T(1), al = T(1), be = T(0);
         if constexpr (!M::flat) {
             gdd = d == 0 ? m.i11 : (d == 1 ? m.i22 : m.i33);
             al = m.al;
-            be = d == 0 ? m.b1 : 0.0;
+            be = d == 0 ? m.b1 : T(0);
         }
-        const double disc = Gs * iW2 * (Y * gdd - rmg * v[d] * v[d]);
-        const double sq = sqrt(is_pos(disc) ? disc : 0.0);
-        const double base = v[d] * rmg;
-        double lp = (base + sq) * iY, lm = (base - sq) * iY;
+        const T disc = Gs * iW2 * (Y * gdd - rmg * v[d] * v[d]);
+        const T sq = sqrt(is_pos(disc) ? disc : T(0));
+        const T base = v[d] * rmg;
+        T lp = (base + sq) * iY, lm = (base - sq) * iY;
         if constexpr (!M::flat) {
             lp = al * lp - be;
             lm = al * lm - be;
@@ -556,29 +610,6 @@ struct C2PResult {
     int iters;
     bool ok;
 };
-
-// Reciprocal 1/d by Newton-Raphson refinement of the hardware's approximate
-// FP64 reciprocal (rcp.approx.ftz.f64): r <- r + r (1 - d r), two FMAs a
-// step; each step squares the relative error, two reach the last bits of
-// FP64 (within 2 ulp of the IEEE quotient, checked by
-// echo_selftest_recip).  For normal, finite, non-zero d: 4 DFMA where an
-// IEEE division costs about 8.6 DFMA slots on GB300.
-__device__ __forceinline__ double nr_recip(double d)
-{
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    return fma(r, e, r);
-}
-
-// n / d through nr_recip when |d| is safely normal, else the IEEE division.
-__device__ __forceinline__ double nr_div(double n, double d)
-{
-    const double a = iabs(d);
-    return (ilt(1e-200, a) && ilt(a, 1e200)) ? n * nr_recip(d) : n / d;
-}
 
 // v^2 at Z from the reciprocals iZ = 1/Z, iZB = 1/(Z + B^2).
 __device__ __forceinline__ double c2p_v2r(double Z, double iZ, double iZB, double S2, double SB2, double B2)

@@ -256,10 +256,23 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             A.P[q][id] = from_d<R>(P8[q]);
         A.Z[id] = Z;
         if (want_rate) {
-            if constexpr (MK == 1)
-                rate = cfl_rate(P8, ph.gamma, ph.gr, g.idx, MKS<double>(*mp));
-            else
-                rate = cfl_rate(P8, ph.gamma, ph.gr, g.idx, MFlat<double>());
+            if constexpr (sizeof(R) == 4) {
+                float Pf[8];
+                for (int q = 0; q < 8; ++q)
+                    Pf[q] = d2f(P8[q]);
+                const float idxf[3] = {d2f(g.idx[0]), d2f(g.idx[1]), d2f(g.idx[2])};
+                float rf;
+                if constexpr (MK == 1)
+                    rf = cfl_rate(Pf, ph.gamma_f, ph.gr_f, idxf, MKS<float>(*mp));
+                else
+                    rf = cfl_rate(Pf, ph.gamma_f, ph.gr_f, idxf, MFlat<float>());
+                rate = f2d(rf);
+            } else {
+                if constexpr (MK == 1)
+                    rate = cfl_rate(P8, ph.gamma, ph.gr, g.idx, MKS<double>(*mp));
+                else
+                    rate = cfl_rate(P8, ph.gamma, ph.gr, g.idx, MFlat<double>());
+            }
         }
     }
     // warp-aggregated counters
@@ -539,7 +552,7 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     const T am = imax(T(0), imax(-lmL, -lmR));
     const T ssum = ap + am;
     if (is_pos(ssum)) {
-        const T is = T(1) / ssum;
+        const T is = fast_recip(ssum);
         const T apam = ap * am;
 #pragma unroll
         for (int q = 0; q < 5; ++q)
@@ -696,7 +709,7 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
     T wLL, wLR, wRL, wRR, da, db;
     if (is_pos(sA) && is_pos(sB)) {
         // one division: 1/sA = sB iden, 1/sB = sA iden
-        const T iden = T(1) / (sA * sB);
+        const T iden = fast_recip(sA * sB);
         wLL = apa * apb * iden;
         wLR = apa * amb * iden;
         wRL = ama * apb * iden;
