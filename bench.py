@@ -314,7 +314,7 @@ def run_ours(args, world, rank, local, dist):
     if guess & 1:
         # the network guess: train the default network first (untimed)
         from paper_1810_04597_gb300 import mlp
-        state = mlp.default_network(device=str(dev))[0]
+        state = mlp.default_network(device=str(dev), torus=True)[0]
         s.mlp_load(state)
     s.set_c2p_guess(guess)
     for _ in range(args.warmup):
@@ -478,15 +478,15 @@ def run_ours(args, world, rank, local, dist):
 
 
 def run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms64):
-    """FP32 bulk with the c2p-guess network: train the default network on
-    FP64 runs of the 128^3 configs-1/2 boxes (untimed), then time W + K
+    """FP32 bulk with the c2p-guess network: train the network on FP64 runs
+    of the 128^3 periodic boxes and of four tori (untimed), then time W + K
     steps on the workload from the same input as the FP64 run."""
     import numpy as np
     import torch
     from paper_1810_04597_gb300 import mlp
     from paper_1810_04597_gb300.echo import Solver
     t0 = time.perf_counter()
-    state, losses, _, (Xte, Yte) = mlp.default_network(device=str(dev))
+    state, losses, _, (Xte, Yte) = mlp.default_network(device=str(dev), torus=True)
     err = mlp.guess_error(state, Xte, Yte).cpu().numpy()
     t_train = time.perf_counter() - t0
     s = Solver(prob, precision=32, device=str(dev))

@@ -19,7 +19,7 @@ def collect(problems_and_steps, device="cuda:0"):
     problems_and_steps: list of (problem, [steps at which to take a
     snapshot]).  In every run the last snapshot is held out for test, the one
     before it for validation, the others train (rows interleaved across the
-    training snapshots)."""
+    training snapshots, or shuffled when the snapshots differ in size)."""
     import torch
     train_s, val_s, test_s = [], [], []
     for prob, at in problems_and_steps:
@@ -40,9 +40,17 @@ def collect(problems_and_steps, device="cuda:0"):
         train_s += snaps[:-2]
         val_s.append(snaps[-2])
         test_s.append(snaps[-1])
-    n = min(x.shape[0] for x, _ in train_s)
-    Xtr = torch.stack([x[:n] for x, _ in train_s], dim=1).reshape(-1, 9).contiguous()
-    Ytr = torch.stack([y[:n] for _, y in train_s], dim=1).reshape(-1, 3).contiguous()
+    sizes = {x.shape[0] for x, _ in train_s}
+    if len(sizes) == 1:
+        Xtr = torch.stack([x for x, _ in train_s], dim=1).reshape(-1, 9).contiguous()
+        Ytr = torch.stack([y for _, y in train_s], dim=1).reshape(-1, 3).contiguous()
+    else:
+        # snapshots of different sizes: all rows, in a fixed pseudo-random order
+        Xtr = torch.cat([x for x, _ in train_s], dim=0)
+        Ytr = torch.cat([y for _, y in train_s], dim=0)
+        g = torch.Generator(device="cpu").manual_seed(12345)
+        perm = torch.randperm(Xtr.shape[0], generator=g).to(Xtr.device)
+        Xtr, Ytr = Xtr[perm].contiguous(), Ytr[perm].contiguous()
     cat = lambda xs: torch.cat(xs, dim=0).contiguous()  # noqa: E731
     return (Xtr, Ytr), (cat([x for x, _ in val_s]), cat([y for _, y in val_s])), \
         (cat([x for x, _ in test_s]), cat([y for _, y in test_s]))
@@ -84,11 +92,29 @@ def guess_error(state, X, Y, gamma=4.0 / 3.0):
     return (z0 - z).abs() / z
 
 
-def default_network(device="cuda:0", n=128, epochs=2, seed=1):
-    """The network used by the benchmarks: trained on snapshots of the
-    n^3 configs-2 (sweep_box) and configs-1-recipe (smooth_box) FP64 runs."""
-    runs = [(inputs.sweep_box(n), [0, 3, 6, 9, 12, 15]),
+def box_runs(n=128):
+    """Snapshots of FP64 runs of the two periodic boxes at n^3: the
+    throughput recipe (sweep_box) and the parity recipe (smooth_box)."""
+    return [(inputs.sweep_box(n), [0, 3, 6, 9, 12, 15]),
             (inputs.smooth_box(n), [0, 4, 8, 12])]
+
+
+def torus_runs(n=(96, 48, 48)):
+    """Snapshots of FP64 Fishbone-Moncrief torus runs on Kerr-Schild (spins
+    0 and 0.9, beta 10 and 100): the atmosphere at the floors and the
+    magnetised torus, where the box data do not reach."""
+    runs = []
+    for k, (spin, beta) in enumerate(((0.0, 10.0), (0.9, 100.0), (0.9, 10.0), (0.0, 100.0))):
+        prob = inputs.fm_torus(n, spin=spin, beta=beta, seed=inputs.SEED_BASE + 200 + k)
+        runs.append((prob, [0, 4, 8, 12, 16, 20]))
+    return runs
+
+
+def default_network(device="cuda:0", n=128, epochs=2, seed=1, torus=False):
+    """The network used by the benchmarks: trained on snapshots of the n^3
+    box runs (box_runs), and with torus=True also of the torus runs
+    (torus_runs)."""
+    runs = box_runs(n) + (torus_runs() if torus else [])
     (Xtr, Ytr), (Xva, Yva), (Xte, Yte) = collect(runs, device=device)
     state, losses = train(Xtr, Ytr, epochs=epochs, seed=seed, device=device)
     return state, losses, (Xva, Yva), (Xte, Yte)

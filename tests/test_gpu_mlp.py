@@ -234,3 +234,32 @@ def test_tensor_core_guess_gives_the_same_inversion(trained, torch, precision, m
         assert np.max(np.abs(Pa[q] - Pb[q])) <= tol * max(np.max(np.abs(Pa[q])), 1e-300), q
     print(f"precision {precision}: Newton iterations per call, CUDA-core guess {ia:.3f}, tensor-core guess {ib:.3f}")
     assert abs(ia - ib) <= 0.5
+
+
+def test_torus_training_reduces_fallbacks(torch):
+    """A network trained on the periodic boxes alone meets states it never saw
+    in a torus atmosphere (tiny density, high magnetisation); adding torus
+    snapshots to the training data must cut the fallbacks to the previous-
+    stage guess and the Newton iterations on a held-out torus (spin 0.5,
+    another seed).  Fallbacks are counted net of the cells whose inversion
+    fails from every guess (those end at the floors either way)."""
+    from paper_1810_04597_gb300 import mlp
+    from paper_1810_04597_gb300.echo import Solver
+    nets = {"box": mlp.default_network(n=64)[0], "box+torus": mlp.default_network(n=64, torus=True)[0]}
+    prob = inputs.fm_torus((96, 48, 48), spin=0.5, beta=30.0, seed=inputs.SEED_BASE + 299)
+    res = {}
+    for name, state in nets.items():
+        s = Solver(prob)
+        s.set_prims()
+        s.mlp_load(state)
+        s.set_c2p_guess(1)
+        c0 = s.counters()
+        for _ in range(6):
+            s.step()
+        c1 = s.counters()
+        calls = c1["c2p_calls"] - c0["c2p_calls"]
+        soft = (c1["mlp_fallback"] - c0["mlp_fallback"]) - (c1["c2p_fail"] - c0["c2p_fail"])
+        res[name] = (soft / calls, (c1["c2p_iters"] - c0["c2p_iters"]) / calls)
+    print("held-out torus: (fallbacks per call, Newton iterations per call):", res)
+    assert res["box+torus"][0] <= res["box"][0], res
+    assert res["box+torus"][1] < 0.9 * res["box"][1], res
