@@ -378,48 +378,39 @@ __device__ __forceinline__ T minmod4(T w, T x, T y, T z)
     return (pos || neg) ? with_sign_of(m, w) : T(0);
 }
 
-// Interface value between u0 = u_j and up1 = u_{j+1}, biased to u_j
-// (Suresh & Huynh 1997): fifth-order interpolant of cell averages, kept
-// inside the monotonicity/accuracy-preserving interval.
+// MP5 (Suresh & Huynh 1997): the interface value between u0 = u_j and
+// up1 = u_{j+1}, biased to u_j -- the fifth-order interpolant of cell
+// averages, kept inside the monotonicity- and accuracy-preserving interval.
+// The GPU splits it for divergence-free evaluation: mp5_try returns the
+// unlimited value and whether the Suresh & Huynh test accepts it; mp5_limit
+// returns the limited value for a rejected stencil (same uor).
+
+// (2 u_{j-2} - 13 u_{j-1} + 47 u_j + 27 u_{j+1} - 3 u_{j+2}) / 60 with the
+// 1/60 folded into the weights (5 FP64 operations).
 template <typename T>
-__device__ __forceinline__ T mp5(T um2, T um1, T u0, T up1, T up2)
+__device__ __forceinline__ T mp5_uor(T um2, T um1, T u0, T up1, T up2)
 {
-    const T uor = (T(2) * um2 - T(13) * um1 + T(47) * u0 + T(27) * up1 - T(3) * up2) * T(1.0 / 60.0);
-    const T a4 = T(MP5_ALPHA) * (u0 - um1);
-    const T ump = u0 + minmod2(up1 - u0, a4);
-    if (ile((uor - u0) * (uor - ump), T(MP5_EPS)))
-        return uor;
-    const T dm1 = um2 - T(2) * um1 + u0;
-    const T d0 = um1 - T(2) * u0 + up1;
-    const T dp1 = u0 - T(2) * up1 + up2;
-    const T dMp = minmod4(T(4) * d0 - dp1, T(4) * dp1 - d0, d0, dp1);
-    const T dMm = minmod4(T(4) * d0 - dm1, T(4) * dm1 - d0, d0, dm1);
-    const T uul = u0 + a4;
-    const T uav = T(0.5) * (u0 + up1);
-    const T umd = uav - T(0.5) * dMp;
-    const T ulc = u0 + T(0.5) * (u0 - um1) + T(4.0 / 3.0) * dMm;
-    const T umin = imax(imin(imin(u0, up1), umd), imin(imin(u0, uul), ulc));
-    const T umax = imin(imax(imax(u0, up1), umd), imax(imax(u0, uul), ulc));
-    return uor + minmod2(umin - uor, umax - uor);
+    return fma(T(2.0 / 60.0), um2,
+               fma(T(-13.0 / 60.0), um1, fma(T(47.0 / 60.0), u0, fma(T(27.0 / 60.0), up1, T(-3.0 / 60.0) * up2))));
 }
 
-// MP5 split for divergence-free evaluation on the GPU.  mp5_try returns the
-// unlimited value and whether it is accepted (the Suresh & Huynh test);
-// mp5_limit returns the limited value for a stencil whose unlimited value
-// was rejected.  mp5_try + (if rejected) mp5_limit == mp5 exactly.
+// Accept uor if (uor - u_j)(uor - u_mp) <= eps, u_mp = u_j + minmod(u_{j+1} - u_j,
+// alpha (u_j - u_{j-1})); written with d0 = uor - u_j so that
+// uor - u_mp = d0 - minmod(...).
 template <typename T>
 __device__ __forceinline__ T mp5_try(T um2, T um1, T u0, T up1, T up2, bool &accept)
 {
-    const T uor = (T(2) * um2 - T(13) * um1 + T(47) * u0 + T(27) * up1 - T(3) * up2) * T(1.0 / 60.0);
-    const T ump = u0 + minmod2(up1 - u0, T(MP5_ALPHA) * (u0 - um1));
-    accept = ile((uor - u0) * (uor - ump), T(MP5_EPS));
+    const T uor = mp5_uor(um2, um1, u0, up1, up2);
+    const T d0 = uor - u0;
+    const T mm = minmod2(up1 - u0, T(MP5_ALPHA) * (u0 - um1));
+    accept = ile(d0 * (d0 - mm), T(MP5_EPS));
     return uor;
 }
 
 template <typename T>
 __device__ __forceinline__ T mp5_limit(T um2, T um1, T u0, T up1, T up2)
 {
-    const T uor = (T(2) * um2 - T(13) * um1 + T(47) * u0 + T(27) * up1 - T(3) * up2) * T(1.0 / 60.0);
+    const T uor = mp5_uor(um2, um1, u0, up1, up2);
     const T a4 = T(MP5_ALPHA) * (u0 - um1);
     const T dm1 = um2 - T(2) * um1 + u0;
     const T d0 = um1 - T(2) * u0 + up1;
@@ -433,14 +424,6 @@ __device__ __forceinline__ T mp5_limit(T um2, T um1, T u0, T up1, T up2)
     const T umin = imax(imin(imin(u0, up1), umd), imin(imin(u0, uul), ulc));
     const T umax = imin(imax(imax(u0, up1), umd), imax(imax(u0, uul), ulc));
     return uor + minmod2(umin - uor, umax - uor);
-}
-
-// Left/right states at the face between q[2] and q[3] of q[0..5].
-template <typename T>
-__device__ __forceinline__ void mp5_lr(const T q[6], T &L, T &R)
-{
-    L = mp5(q[0], q[1], q[2], q[3], q[4]);
-    R = mp5(q[5], q[4], q[3], q[2], q[1]);
 }
 
 // ------------------------------------------------------------------ state
@@ -457,8 +440,12 @@ __device__ __forceinline__ void mp5_lr(const T q[6], T &L, T &R)
 //   a^2 = c_s^2 + c_A^2 - c_s^2 c_A^2 = (G p + b^2)/(rho h + b^2),
 //   lambda = alpha [v^d (1 - a^2) +- sqrt(a^2 (1-v^2)((1 - v^2 a^2) gamma^dd
 //            - (1 - a^2)(v^d)^2))] / (1 - v^2 a^2) - beta^d.
+// Returns the eigenvalues as lambda+- = np / Y, nm / Y (Y > 0 below), so
+// that the caller can take the reciprocals of both states' Y with one
+// division.
 template <int D, typename T, typename M>
-__device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m, T F[5], T U[5], T &lp, T &lm)
+__device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m, T F[5], T U[5], T &np, T &nm,
+                                           T &Yout)
 {
     const T rho = P[0], p = P[4];
     const T v[3] = {P[1], P[2], P[3]};
@@ -495,9 +482,10 @@ __device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m
     const T Y = (rhoh + b2) - v2 * Gs;
     const T rmg = rhoh - gam * p;
     const T disc = Gs * iW2 * (Y * gup<D, T>(m) - rmg * vd * vd);
-    const T sq = sqrt(is_pos(disc) ? disc : T(0));
-    const T iY = fast_recip(Y);
+    // sqrt(disc) = disc rsqrt(disc): one rsqrt is cheaper than a sqrt
+    const T sq = is_pos(disc) ? disc * rsqrt(disc) : T(0);
     const T base = vd * rmg;
+    Yout = Y;
     if constexpr (M::flat) {
         F[0] = Dn * vd;
 #pragma unroll
@@ -506,8 +494,8 @@ __device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m
             F[1 + j] = wt * vl[j] - bd * bj + (j == D ? p + T(0.5) * b2 : T(0));
         }
         F[4] = U[1 + D] - Dn * vd;
-        lp = (base + sq) * iY;
-        lm = (base - sq) * iY;
+        np = base + sq;
+        nm = base - sq;
     } else {
         const T al = m.al;
         const T be = D == 0 ? m.b1 : T(0);
@@ -519,8 +507,8 @@ __device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m
         }
         const T Su[3] = {U[1], U[2], U[3]};
         F[4] = al * (raise_c<D, T>(m, Su) - Dn * vd) - be * U[4];
-        lp = al * (base + sq) * iY - be;
-        lm = al * (base - sq) * iY - be;
+        np = al * (base + sq) - be * Y;
+        nm = al * (base - sq) - be * Y;
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             F[q] *= m.sg;
@@ -561,7 +549,7 @@ __device__ __forceinline__ T cfl_rate(const T P[8], T gam, T gr, const T idx[3],
             be = d == 0 ? m.b1 : T(0);
         }
         const T disc = Gs * iW2 * (Y * gdd - rmg * v[d] * v[d]);
-        const T sq = sqrt(is_pos(disc) ? disc : T(0));
+        const T sq = is_pos(disc) ? disc * rsqrt(disc) : T(0);
         const T base = v[d] * rmg;
         T lp = (base + sq) * iY, lm = (base - sq) * iY;
         if constexpr (!M::flat) {
@@ -732,8 +720,8 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
             break;
         }
     }
-    const double om = 1.0 - v2;
-    const double sq = sqrt(om);
+    const double om = 1.0 - v2;   // > 0: v2 < 1 on every accepted iterate
+    const double sq = om * rsqrt(om);
     const double p = gm1g * (Z * om - Dc * sq);
     const double sbz = SB * iZ;
     double vl[3];

@@ -538,16 +538,27 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
                 Ps[qs[m]] = A.P[qs[m]][c];
         }
     }
-    T FL[5], UL[5], FR[5], UR[5], lpL, lmL, lpR, lmR;
+    T FL[5], UL[5], FR[5], UR[5], npL, nmL, YL, npR, nmR, YR;
     if constexpr (MK == 1) {
         const MKS<T> m(*mp);
-        state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, lpL, lmL);
-        state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, lpR, lmR);
+        state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, npL, nmL, YL);
+        state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, npR, nmR, YR);
     } else {
         const MFlat<T> m;
-        state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, lpL, lmL);
-        state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, lpR, lmR);
+        state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, npL, nmL, YL);
+        state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, npR, nmR, YR);
     }
+    // both states' 1/Y from one division in FP64
+    T iYL, iYR;
+    if constexpr (sizeof(T) == 8) {
+        const T inv = T(1) / (YL * YR);
+        iYL = inv * YR;
+        iYR = inv * YL;
+    } else {
+        iYL = fast_recip(YL);
+        iYR = fast_recip(YR);
+    }
+    const T lpL = npL * iYL, lmL = nmL * iYL, lpR = npR * iYR, lmR = nmR * iYR;
     const T ap = imax(T(0), imax(lpL, lpR));
     const T am = imax(T(0), imax(-lmL, -lmR));
     const T ssum = ap + am;

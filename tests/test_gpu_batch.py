@@ -1,8 +1,9 @@
 """Batch of independent runs under each schedule (persistent cooperative
 kernel per RK stage, one launch per phase, run-major with concurrent
-branches): the same results as the runs advanced one at a time (the same
-device bodies compute the same arithmetic, so bitwise in FP64), with and
-without CUDA-graph replay."""
+branches): the same results as the runs advanced one at a time -- bitwise
+for run-major (the same kernels), to rounding for the other two (the same
+device bodies compiled into other kernels) -- with and without CUDA-graph
+replay."""
 import numpy as np
 import pytest
 
@@ -49,7 +50,14 @@ def test_batch_equals_runs_one_at_a_time(tile, dyn, graph, mode, branches):
         b.step()
     for r, s in zip(ref, runs):
         got = s.get_state()
-        assert np.array_equal(got, r), np.max(np.abs(got - r))
+        if mode == 2:
+            # run-major runs the single-run kernels themselves: bitwise
+            assert np.array_equal(got, r), np.max(np.abs(got - r))
+        else:
+            # the persistent and per-phase kernels compile the same device code
+            # in other kernels; ptxas may fuse a multiply and an add into one
+            # FMA differently there, so they agree to rounding, not bitwise
+            assert np.max(np.abs(got - r)) <= 1e-12 * np.max(np.abs(r)), np.max(np.abs(got - r))
 
 
 def test_batch_flat_fixed_dt_and_counters():
@@ -67,5 +75,6 @@ def test_batch_flat_fixed_dt_and_counters():
     b.step(1e-3)
     b.step(1e-3)
     for x, y in zip(a, c):
-        assert np.array_equal(x.get_state(), y.get_state())
+        sx, sy = x.get_state(), y.get_state()
+        assert np.max(np.abs(sx - sy)) <= 1e-12 * np.max(np.abs(sx))
         assert x.counters()["c2p_calls"] == y.counters()["c2p_calls"]
