@@ -381,7 +381,7 @@ __device__ __forceinline__ T minmod4(T w, T x, T y, T z)
 // MP5 (Suresh & Huynh 1997): the interface value between u0 = u_j and
 // up1 = u_{j+1}, biased to u_j -- the fifth-order interpolant of cell
 // averages, kept inside the monotonicity- and accuracy-preserving interval.
-// The GPU splits it for divergence-free evaluation: mp5_try returns the
+// The GPU splits it for warp-uniform evaluation: mp5_try returns the
 // unlimited value and whether the Suresh & Huynh test accepts it; mp5_limit
 // returns the limited value for a rejected stencil (same uor).
 
@@ -486,13 +486,14 @@ __device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m
     const T sq = is_pos(disc) ? disc * rsqrt(disc) : T(0);
     const T base = vd * rmg;
     Yout = Y;
+    // wt v_j - b^d b_j with b_j = B_j / W + W (v.B) v_j, regrouped as
+    // c1 v_j - c2 B_j
+    const T c1 = wt - bd * Wvb, c2 = bd * iW;
     if constexpr (M::flat) {
         F[0] = Dn * vd;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const T bj = Bl[j] * iW + Wvb * vl[j];
-            F[1 + j] = wt * vl[j] - bd * bj + (j == D ? p + T(0.5) * b2 : T(0));
-        }
+        for (int j = 0; j < 3; ++j)
+            F[1 + j] = c1 * vl[j] - c2 * Bl[j] + (j == D ? p + T(0.5) * b2 : T(0));
         F[4] = U[1 + D] - Dn * vd;
         np = base + sq;
         nm = base - sq;
@@ -501,10 +502,8 @@ __device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m
         const T be = D == 0 ? m.b1 : T(0);
         F[0] = Dn * (al * vd - be);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const T bj = Bl[j] * iW + Wvb * vl[j];
-            F[1 + j] = al * (wt * vl[j] - bd * bj + (j == D ? p + T(0.5) * b2 : T(0))) - be * U[1 + j];
-        }
+        for (int j = 0; j < 3; ++j)
+            F[1 + j] = al * (c1 * vl[j] - c2 * Bl[j] + (j == D ? p + T(0.5) * b2 : T(0))) - be * U[1 + j];
         const T Su[3] = {U[1], U[2], U[3]};
         F[4] = al * (raise_c<D, T>(m, Su) - Dn * vd) - be * U[4];
         np = al * (base + sq) - be * Y;

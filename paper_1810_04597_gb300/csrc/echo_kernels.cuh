@@ -564,10 +564,10 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     const T ssum = ap + am;
     if (is_pos(ssum)) {
         const T is = fast_recip(ssum);
-        const T apam = ap * am;
+        const T wL = ap * is, wR = am * is, wD = wL * am;
 #pragma unroll
         for (int q = 0; q < 5; ++q)
-            A.F[D][q][id] = (ap * FL[q] + am * FR[q] - apam * (UR[q] - UL[q])) * is;
+            A.F[D][q][id] = wL * FL[q] + wR * FR[q] - wD * (UR[q] - UL[q]);
     } else {
 #pragma unroll
         for (int q = 0; q < 5; ++q)
