@@ -46,6 +46,7 @@ class OCfg(ctypes.Structure):
         ("rho_floor_pow", ctypes.c_double),
         ("p_floor", ctypes.c_double),
         ("p_floor_pow", ctypes.c_double),
+        ("order", ctypes.c_int),
     ]
 
 
@@ -84,6 +85,12 @@ def lib():
         L.oracle_mp5_face.restype = d
         L.oracle_mp5_unlimited.argtypes = [pd]
         L.oracle_mp5_unlimited.restype = d
+        L.oracle_mp5_face_order.argtypes = [pd, i]
+        L.oracle_mp5_face_order.restype = d
+        L.oracle_ho_flux.argtypes = [pd]
+        L.oracle_ho_flux.restype = d
+        L.oracle_ho_center.argtypes = [pd]
+        L.oracle_ho_center.restype = d
         L.oracle_speeds_point.argtypes = [pc, pd, pd, i, pd, pd]
         L.oracle_flux_point.argtypes = [pc, pd, pd, i, pd, pd]
         L.oracle_hll.argtypes = [pd, pd, pd, pd, d, d, pd]
@@ -137,6 +144,7 @@ def make_cfg(problem) -> OCfg:
     c.rho_floor_pow = float(problem.rho_floor_pow)
     c.p_floor = float(problem.p_floor)
     c.p_floor_pow = float(problem.p_floor_pow)
+    c.order = int(getattr(problem, "order", 0))
     return c
 
 
@@ -182,6 +190,23 @@ def c2p_residual(cfg: OCfg, x, C5, B3, Z):
 
 def mp5_face(u5) -> float:
     return lib().oracle_mp5_face(_dp(_f64(u5)))
+
+
+def mp5_face_order(u5, order):
+    """MP5 interface value with the cell-average (order 0) or point-value
+    (order 1) interpolant."""
+    return lib().oracle_mp5_face_order(_dp(_f64(u5)), int(order))
+
+
+def ho_flux(f5):
+    """Flux-derivative correction F - D2/24 + 3 D4/640 at the middle of five
+    interface values."""
+    return lib().oracle_ho_flux(_dp(_f64(f5)))
+
+
+def ho_center(b6):
+    """Sixth-order midpoint interpolation of six equally spaced values."""
+    return lib().oracle_ho_center(_dp(_f64(b6)))
 
 
 def mp5_unlimited(u5) -> float:

@@ -44,7 +44,8 @@
 #include <string.h>
 #include <stdint.h>
 
-#define NG 3                 /* ghost layers: MP5 needs 3 cells on each side */
+#define NG 5                 /* ghost layers: MP5 needs 3 cells on each side, the
+                                high-order flux correction two more faces */
 #define MP5_ALPHA 4.0
 #define MP5_EPS 1e-10
 #define NEWTON_TOL 1e-13
@@ -67,6 +68,10 @@ typedef struct {
     double cfl;
     int floors;        /* 1: apply atmosphere floors after c2p */
     double rho_floor, rho_floor_pow, p_floor, p_floor_pow;  /* floor = f0 * r^pow */
+    int order;         /* 0: the scheme as read (cell-average MP5 weights, second-order
+                          cell-centre B, no flux correction); 1: high order (point-value
+                          MP5 weights, sixth-order cell-centre B, flux-derivative
+                          correction of the fluxes and the EMFs) */
 } ocfg;
 
 typedef struct {
@@ -313,11 +318,14 @@ static double minmod4(double w, double x, double y, double z)
 /* Interface value between u0 = u_j and u1 = u_{j+1}, biased towards u_j,
  * from the five values um2 = u_{j-2}, um1, u0, up1, up2 = u_{j+2}.
  * The unlimited value is the fifth-order interpolant of cell averages,
- * (2, -13, 47, 27, -3)/60; the limiter keeps it inside the monotonicity-
- * and accuracy-preserving interval of Suresh & Huynh. */
-static double mp5_face(double um2, double um1, double u0, double up1, double up2)
+ * (2, -13, 47, 27, -3)/60 (order 0), or the fifth-order Lagrange
+ * interpolant of point values at the interface, (3, -20, 90, 60, -5)/128
+ * (order 1); the limiter keeps it inside the monotonicity- and
+ * accuracy-preserving interval of Suresh & Huynh. */
+static double mp5_face(double um2, double um1, double u0, double up1, double up2, int order)
 {
-    double uor = (2.0 * um2 - 13.0 * um1 + 47.0 * u0 + 27.0 * up1 - 3.0 * up2) / 60.0;
+    double uor = order ? (3.0 * um2 - 20.0 * um1 + 90.0 * u0 + 60.0 * up1 - 5.0 * up2) / 128.0
+                       : (2.0 * um2 - 13.0 * um1 + 47.0 * u0 + 27.0 * up1 - 3.0 * up2) / 60.0;
     double ump = u0 + minmod2(up1 - u0, MP5_ALPHA * (u0 - um1));
     if ((uor - u0) * (uor - ump) <= MP5_EPS)
         return uor;
@@ -337,10 +345,33 @@ static double mp5_face(double um2, double um1, double u0, double up1, double up2
 
 /* Left and right states at the face between q[2] and q[3] of a 6-point
  * stencil q[0..5] = u_{f-3} .. u_{f+2}. */
-static void mp5_lr(const double q[6], double *L, double *R)
+static void mp5_lr(const double q[6], double *L, double *R, int order)
 {
-    *L = mp5_face(q[0], q[1], q[2], q[3], q[4]);
-    *R = mp5_face(q[5], q[4], q[3], q[2], q[1]);
+    *L = mp5_face(q[0], q[1], q[2], q[3], q[4], order);
+    *R = mp5_face(q[5], q[4], q[3], q[2], q[1], order);
+}
+
+/* ---- high-order flux-derivative correction ----
+ * For point values F_{j+1/2} of a flux at the interfaces, the corrected
+ * flux  Fhat = F - D2/24 + 3 D4/640,  D2 = F_{-1} - 2 F_0 + F_{+1},
+ * D4 = F_{-2} - 4 F_{-1} + 6 F_0 - 4 F_{+1} + F_{+2} (neighbouring
+ * interfaces), makes (Fhat_{i+1/2} - Fhat_{i-1/2}) / h the sixth-order
+ * derivative dF/dx at x_i: Fhat is the interface value of the function
+ * whose cell averages are the point values F (F - h^2 F''/24 +
+ * 7 h^4 F/5760), with F and F written as differences of the
+ * interface values.  f5 = F_{-2} .. F_{+2}. */
+static double ho_flux(const double f5[5])
+{
+    double d2 = f5[1] - 2.0 * f5[2] + f5[3];
+    double d4 = f5[0] - 4.0 * f5[1] + 6.0 * f5[2] - 4.0 * f5[3] + f5[4];
+    return f5[2] - d2 / 24.0 + 3.0 * d4 / 640.0;
+}
+
+/* Sixth-order Lagrange interpolation to the midpoint of six equally spaced
+ * values b6 = b_{-5/2} .. b_{+5/2}: (3, -25, 150, 150, -25, 3)/256. */
+static double ho_center(const double b6[6])
+{
+    return (3.0 * b6[0] - 25.0 * b6[1] + 150.0 * b6[2] + 150.0 * b6[3] - 25.0 * b6[4] + 3.0 * b6[5]) / 256.0;
 }
 
 /* ---- characteristic speeds (approximate fast magnetosonic speed) ----
@@ -445,6 +476,8 @@ typedef struct {
     double *ap[3], *am[3];
     double *vL[3][3], *vR[3][3];   /* [face dir][component] */
     double *E[3];       /* edge EMFs */
+    double *Fc[3][5];   /* order 1: corrected fluxes on the owned faces */
+    double *Ec[3][2];   /* order 1: E_e corrected along (e+1)%3 [0] and (e+2)%3 [1] */
     double *LU[5], *LB[3];
     double *cellspeed;  /* per cell sum_d max|lambda_d|/dx_d */
 } ogrid;
@@ -474,7 +507,8 @@ static int grid_alloc(ogrid *G, const int n[3])
     for (int q = 0; q < 5; ++q) { A(G->U[q]); A(G->LU[q]); }
     for (int d = 0; d < 3; ++d) {
         A(G->B[d]); A(G->LB[d]); A(G->E[d]); A(G->ap[d]); A(G->am[d]);
-        for (int q = 0; q < 5; ++q) A(G->F[d][q]);
+        for (int q = 0; q < 5; ++q) { A(G->F[d][q]); A(G->Fc[d][q]); }
+        A(G->Ec[d][0]); A(G->Ec[d][1]);
         for (int c = 0; c < 3; ++c) { A(G->vL[d][c]); A(G->vR[d][c]); }
     }
     for (int q = 0; q < 8; ++q) A(G->P[q]);
@@ -489,7 +523,8 @@ static void grid_free(ogrid *G)
     for (int q = 0; q < 5; ++q) { free(G->U[q]); free(G->LU[q]); }
     for (int d = 0; d < 3; ++d) {
         free(G->B[d]); free(G->LB[d]); free(G->E[d]); free(G->ap[d]); free(G->am[d]);
-        for (int q = 0; q < 5; ++q) free(G->F[d][q]);
+        for (int q = 0; q < 5; ++q) { free(G->F[d][q]); free(G->Fc[d][q]); }
+        free(G->Ec[d][0]); free(G->Ec[d][1]);
         for (int c = 0; c < 3; ++c) { free(G->vL[d][c]); free(G->vR[d][c]); }
     }
     for (int q = 0; q < 8; ++q) free(G->P[q]);
@@ -673,8 +708,29 @@ static double floor_value(double f0, double pw, const ocfg *c, double x1)
     return f0;
 }
 
-/* c2p over the owned cells.  Cell-centre B = average of the two faces
- * divided by the cell's sqrt(gamma).  With floors on, rho and p are raised
+/* Cell-centre B of cell (i,j,k): order 0 the mean of the two faces, order 1
+ * the sixth-order interpolation of the faces i-2 .. i+3 along each d; then
+ * divided by the cell's sqrt(gamma). */
+static void cell_centre_B(const ocfg *c, const ogrid *G, int i, int j, int k, double sqrtg, double Bc[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        if (c->order) {
+            double b6[6];
+            for (int s = 0; s < 6; ++s) {
+                int t[3] = {i, j, k};
+                t[d] += s - 2;
+                b6[s] = G->B[d][IDX(G, t[0], t[1], t[2])];
+            }
+            Bc[d] = ho_center(b6) / sqrtg;
+        } else {
+            int t[3] = {i, j, k};
+            t[d] += 1;
+            Bc[d] = 0.5 * (G->B[d][IDX(G, i, j, k)] + G->B[d][IDX(G, t[0], t[1], t[2])]) / sqrtg;
+        }
+    }
+}
+
+/* c2p over the owned cells.  Cell-centre B from cell_centre_B.  With floors on, rho and p are raised
  * to the atmosphere floors and the conserved state is reset from the
  * floored primitives; a failed inversion keeps the cell's previous
  * primitives (floored) and is counted.  Without floors a failure is an
@@ -691,9 +747,7 @@ static int c2p_grid(const ocfg *c, ogrid *G, ostats *st)
                 ometric m;
                 metric_eval(c, x, &m);
                 double Bc[3];
-                Bc[0] = 0.5 * (G->B[0][id] + G->B[0][IDX(G, i + 1, j, k)]) / m.sqrtg;
-                Bc[1] = 0.5 * (G->B[1][id] + G->B[1][IDX(G, i, j + 1, k)]) / m.sqrtg;
-                Bc[2] = 0.5 * (G->B[2][id] + G->B[2][IDX(G, i, j, k + 1)]) / m.sqrtg;
+                cell_centre_B(c, G, i, j, k, m.sqrtg, Bc);
                 double C[5];
                 for (int q = 0; q < 5; ++q)
                     C[q] = G->U[q][id] / m.sqrtg;
@@ -791,8 +845,9 @@ static double cfl_rate_max(const ocfg *c, ogrid *G)
 static void faces_dir(const ocfg *c, ogrid *G, int d, ostats *st)
 {
     int lo[3] = {0, 0, 0}, hi[3] = {G->np[0], G->np[1], G->np[2]};
-    lo[d] = NG;
-    hi[d] = NG + G->n[d] + 1;
+    /* order 1: two more faces on each side for the flux correction */
+    lo[d] = NG - 2 * c->order;
+    hi[d] = NG + G->n[d] + 1 + 2 * c->order;
     /* transverse: indices whose face stencil (along d) exists; all */
     long long fb = 0;
 #pragma omp parallel for collapse(2) reduction(+ : fb)
@@ -831,7 +886,7 @@ static void faces_dir(const ocfg *c, ogrid *G, int d, ostats *st)
                     double qq[6];
                     for (int s = 0; s < 6; ++s)
                         qq[s] = G->P[q][cid[s]];
-                    mp5_lr(qq, &PL[q], &PR[q]);
+                    mp5_lr(qq, &PL[q], &PR[q], c->order);
                 }
                 double Bn = G->B[d][id] / m.sqrtg;
                 PL[5 + d] = Bn;
@@ -896,6 +951,11 @@ static void emf_dir(const ocfg *c, ogrid *G, int e)
     }
     hi[a] += 1;
     hi[b] += 1;
+    /* order 1: two more edges on each side along a and b for the correction */
+    lo[a] -= 2 * c->order;
+    hi[a] += 2 * c->order;
+    lo[b] -= 2 * c->order;
+    hi[b] += 2 * c->order;
 #pragma omp parallel for collapse(2)
     for (int k = lo[2]; k < hi[2]; ++k)
         for (int j = lo[1]; j < hi[1]; ++j)
@@ -920,18 +980,18 @@ static void emf_dir(const ocfg *c, ogrid *G, int e)
                         qa[s] = vs[a][sb[s]];
                         qb[s] = vs[b][sb[s]];
                     }
-                    mp5_lr(qa, &va[sside][0], &va[sside][1]);
-                    mp5_lr(qb, &vb[sside][0], &vb[sside][1]);
+                    mp5_lr(qa, &va[sside][0], &va[sside][1], c->order);
+                    mp5_lr(qb, &vb[sside][0], &vb[sside][1], c->order);
                 }
                 double Bb[2], Ba[2];
                 {
                     double q[6];
                     for (int s = 0; s < 6; ++s)
                         q[s] = G->B[b][sa[s]];
-                    mp5_lr(q, &Bb[0], &Bb[1]);
+                    mp5_lr(q, &Bb[0], &Bb[1], c->order);
                     for (int s = 0; s < 6; ++s)
                         q[s] = G->B[a][sb[s]];
-                    mp5_lr(q, &Ba[0], &Ba[1]);
+                    mp5_lr(q, &Ba[0], &Ba[1], c->order);
                 }
                 size_t a0 = sb[2], a1 = sb[3];  /* a-faces at b-1, b */
                 size_t b0 = sa[2], b1 = sa[3];  /* b-faces at a-1, a */
@@ -1075,8 +1135,54 @@ static void owned_faces(const ocfg *c, int d, int *lo, int *hi)
         *hi = NG + c->n[d] - 1;
 }
 
+/* Order 1: the flux-derivative correction (ho_flux) of the fluxes along
+ * their own direction on the owned faces, and of each EMF E_e along each of
+ * its two half-integer directions (the induction equation differences E_e
+ * along both): Ec[e][0] along (e+1)%3, Ec[e][1] along (e+2)%3.  The 1-D
+ * corrections along different axes commute, so the discrete divergence
+ * built from the same corrected differences stays constant. */
+static void ho_correct(const ocfg *c, ogrid *G)
+{
+    for (int d = 0; d < 3; ++d) {
+#pragma omp parallel for collapse(2)
+        for (int k = NG; k < NG + G->n[2] + (d == 2); ++k)
+            for (int j = NG; j < NG + G->n[1] + (d == 1); ++j)
+                for (int i = NG; i < NG + G->n[0] + (d == 0); ++i) {
+                    size_t id = IDX(G, i, j, k);
+                    for (int q = 0; q < 5; ++q) {
+                        double f5[5];
+                        for (int s = 0; s < 5; ++s) {
+                            int t[3] = {i, j, k};
+                            t[d] += s - 2;
+                            f5[s] = G->F[d][q][IDX(G, t[0], t[1], t[2])];
+                        }
+                        G->Fc[d][q][id] = ho_flux(f5);
+                    }
+                }
+    }
+    for (int e = 0; e < 3; ++e)
+        for (int w = 0; w < 2; ++w) {
+            int dir = (e + 1 + w) % 3;
+            int hi[3] = {NG + G->n[0] + 1, NG + G->n[1] + 1, NG + G->n[2] + 1};
+            hi[e] -= 1;
+#pragma omp parallel for collapse(2)
+            for (int k = NG; k < hi[2]; ++k)
+                for (int j = NG; j < hi[1]; ++j)
+                    for (int i = NG; i < hi[0]; ++i) {
+                        double f5[5];
+                        for (int s = 0; s < 5; ++s) {
+                            int t[3] = {i, j, k};
+                            t[dir] += s - 2;
+                            f5[s] = G->E[e][IDX(G, t[0], t[1], t[2])];
+                        }
+                        G->Ec[e][w][IDX(G, i, j, k)] = ho_flux(f5);
+                    }
+        }
+}
+
 /* L(U): flux difference plus sources for the cell variables, minus the
- * curl of the edge EMFs for the face field. */
+ * curl of the edge EMFs for the face field (order 1: of the corrected
+ * fluxes and EMFs). */
 static void assemble(const ocfg *c, ogrid *G)
 {
 #pragma omp parallel for collapse(2)
@@ -1100,8 +1206,10 @@ static void assemble(const ocfg *c, ogrid *G)
                 }
                 for (int q = 0; q < 5; ++q) {
                     double r = 0.0;
-                    for (int d = 0; d < 3; ++d)
-                        r -= (G->F[d][q][nb[d]] - G->F[d][q][id]) / c->dx[d];
+                    for (int d = 0; d < 3; ++d) {
+                        const double *F = c->order ? G->Fc[d][q] : G->F[d][q];
+                        r -= (F[nb[d]] - F[id]) / c->dx[d];
+                    }
                     G->LU[q][id] = r + src[q];
                 }
             }
@@ -1123,9 +1231,12 @@ static void assemble(const ocfg *c, ogrid *G)
                     ta[a] += 1;
                     int tb[3] = {idx[0], idx[1], idx[2]};
                     tb[b] += 1;
-                    /* E_b varies along a: its edges at a+-1/2; E_a ... */
-                    double dEb_da = (G->E[b][IDX(G, ta[0], ta[1], ta[2])] - G->E[b][id]) / c->dx[a];
-                    double dEa_db = (G->E[a][IDX(G, tb[0], tb[1], tb[2])] - G->E[a][id]) / c->dx[b];
+                    /* E_b varies along a: its edges at a+-1/2; E_a along b.  Order 1:
+                     * E_b corrected along a = (b+2)%3, E_a along b = (a+1)%3 */
+                    const double *Eb = c->order ? G->Ec[b][1] : G->E[b];
+                    const double *Ea = c->order ? G->Ec[a][0] : G->E[a];
+                    double dEb_da = (Eb[IDX(G, ta[0], ta[1], ta[2])] - Eb[id]) / c->dx[a];
+                    double dEa_db = (Ea[IDX(G, tb[0], tb[1], tb[2])] - Ea[id]) / c->dx[b];
                     /* (curl E)^d = d_a E_b - d_b E_a */
                     G->LB[d][id] = -(dEb_da - dEa_db);
                 }
@@ -1153,6 +1264,8 @@ static int eval_rhs(const ocfg *c, ogrid *G, ostats *st, double *rate_max, doubl
         faces_dir(c, G, d, st);
     for (int e = 0; e < 3; ++e)
         emf_dir(c, G, e);
+    if (c->order)
+        ho_correct(c, G);
     assemble(c, G);
     return 0;
 }
@@ -1216,7 +1329,13 @@ void oracle_c2p_residual(const ocfg *c, const double *x, const double *C5, const
     *fp = 1.0 - dp + 0.5 * B2 * dv2 + SB * SB / (Z * Z * Z);
 }
 
-double oracle_mp5_face(const double *u5) { return mp5_face(u5[0], u5[1], u5[2], u5[3], u5[4]); }
+double oracle_mp5_face(const double *u5) { return mp5_face(u5[0], u5[1], u5[2], u5[3], u5[4], 0); }
+double oracle_mp5_face_order(const double *u5, int order)
+{
+    return mp5_face(u5[0], u5[1], u5[2], u5[3], u5[4], order);
+}
+double oracle_ho_flux(const double *f5) { return ho_flux(f5); }
+double oracle_ho_center(const double *b6) { return ho_center(b6); }
 
 /* Unlimited fifth-order value, for the polynomial-exactness pin. */
 double oracle_mp5_unlimited(const double *u5)
@@ -1282,9 +1401,7 @@ int oracle_p2c(const ocfg *c, const double *prims, const double *bface, double *
                 double P[8];
                 for (int q = 0; q < 5; ++q)
                     P[q] = prims[q * N + h];
-                P[5] = 0.5 * (G.B[0][id] + G.B[0][IDX(&G, i + 1, j, k)]) / m.sqrtg;
-                P[6] = 0.5 * (G.B[1][id] + G.B[1][IDX(&G, i, j + 1, k)]) / m.sqrtg;
-                P[7] = 0.5 * (G.B[2][id] + G.B[2][IDX(&G, i, j, k + 1)]) / m.sqrtg;
+                cell_centre_B(c, &G, i, j, k, m.sqrtg, P + 5);
                 double C[5];
                 p2c_point(&m, c->gamma, P, C);
                 for (int q = 0; q < 5; ++q)
@@ -1452,9 +1569,29 @@ int oracle_reduce(const ocfg *c, const double *state, double *out)
                 sT += G.U[4][id] * dV;
                 for (int q = 0; q < 3; ++q)
                     sS[q] += G.U[1 + q][id] * dV;
-                double dv = (G.B[0][IDX(&G, i + 1, j, k)] - G.B[0][id]) / c->dx[0]
-                            + (G.B[1][IDX(&G, i, j + 1, k)] - G.B[1][id]) / c->dx[1]
-                            + (G.B[2][IDX(&G, i, j, k + 1)] - G.B[2][id]) / c->dx[2];
+                double dv = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    /* order 0: B~(i+1) - B~(i); order 1: the same difference of
+                     * the corrected face values (the divergence that order 1
+                     * keeps constant) */
+                    double bf[2];
+                    for (int side = 0; side < 2; ++side) {
+                        int t[3] = {i, j, k};
+                        t[d] += side;
+                        if (c->order) {
+                            double f5[5];
+                            for (int s = 0; s < 5; ++s) {
+                                int u[3] = {t[0], t[1], t[2]};
+                                u[d] += s - 2;
+                                f5[s] = G.B[d][IDX(&G, u[0], u[1], u[2])];
+                            }
+                            bf[side] = ho_flux(f5);
+                        } else {
+                            bf[side] = G.B[d][IDX(&G, t[0], t[1], t[2])];
+                        }
+                    }
+                    dv += (bf[1] - bf[0]) / c->dx[d];
+                }
                 mdiv = fmax(mdiv, fabs(dv));
             }
     out[0] = sD;

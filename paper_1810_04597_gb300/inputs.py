@@ -44,6 +44,7 @@ class Problem:
     rho_floor_pow: float = 0.0
     p_floor: float = 0.0
     p_floor_pow: float = 0.0
+    order: int = 0           # 0 the scheme as read; 1 high order (flux-derivative correction)
     steps: int = 10
     seed: int = 0
     prims: np.ndarray = field(default=None, repr=False)   # (5, nz, ny, nx)
@@ -299,11 +300,13 @@ def permute_axes(prob: Problem) -> Problem:
                    bface=pack_faces(*nb))
 
 
-def alfven_wave_2d(n: int, t=0.0, rho=1.0, p=1.0, B0=1.0, eta=1.0, gamma=4.0 / 3.0) -> Problem:
+def alfven_wave_2d(n: int, t=0.0, rho=1.0, p=1.0, B0=1.0, eta=1.0, gamma=4.0 / 3.0, order=0) -> Problem:
     """The circularly polarised Alfven wave propagating along the diagonal
     of the periodic unit square (n x n x 1), wave vector k = 2 pi (1, 1).
-    The in-plane perpendicular field comes from the discrete curl of an
-    edge-centred A_z, so the discrete divergence vanishes."""
+    order 0: the in-plane perpendicular field comes from the discrete curl of
+    an edge-centred A_z, so the second-order discrete divergence vanishes;
+    order 1 (for the high-order scheme): the face field holds the exact
+    point values at the face centres."""
     vA = alfven_speed(rho, p, B0, eta, gamma)
     nn = (n, n, 1)
     dx = (1.0 / n, 1.0 / n, 1.0)
@@ -333,11 +336,17 @@ def alfven_wave_2d(n: int, t=0.0, rho=1.0, p=1.0, B0=1.0, eta=1.0, gamma=4.0 / 3
     XE, YE = np.meshgrid(xf, xf, indexing="xy")       # (ny+1, nx+1)
     Az = -(eta * B0 / kmag) * np.sin(phase(XE, YE))
     Azc = Az[None, :, :]
-    bx = (Azc[:, 1:, :] - Azc[:, :-1, :]) / dx[1] + B0 * nhat[0]     # (1, n, n+1)
-    by = -(Azc[:, :, 1:] - Azc[:, :, :-1]) / dx[0] + B0 * nhat[1]    # (1, n+1, n)
+    if order:
+        XFx, YFx = np.meshgrid(xf, xc, indexing="xy")     # x-faces (n, n+1)
+        XFy, YFy = np.meshgrid(xc, xf, indexing="xy")     # y-faces (n+1, n)
+        bx = (eta * B0 * np.cos(phase(XFx, YFx)) * that[0] + B0 * nhat[0])[None]
+        by = (eta * B0 * np.cos(phase(XFy, YFy)) * that[1] + B0 * nhat[1])[None]
+    else:
+        bx = (Azc[:, 1:, :] - Azc[:, :-1, :]) / dx[1] + B0 * nhat[0]     # (1, n, n+1)
+        by = -(Azc[:, :, 1:] - Azc[:, :, :-1]) / dx[0] + B0 * nhat[1]    # (1, n+1, n)
     bz = np.stack([Bzc, Bzc])                                          # (2, n, n)
     return Problem(name=f"alfven2d_{n}", n=nn, x0=(0.0, 0.0, 0.0), dx=dx, gamma=gamma, prims=prims,
-                   bface=pack_faces(bx, by, bz))
+                   bface=pack_faces(bx, by, bz), order=order)
 
 
 # ------------------------------------------------------------------ torus

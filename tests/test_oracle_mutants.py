@@ -14,6 +14,7 @@ ORACLE = os.path.join(ROOT, "oracle")
 OUT = os.path.join(ORACLE, "_build", "mutants")
 PINS = ["tests/test_oracle_pointwise.py", "tests/test_oracle_scheme.py", "tests/test_golden.py"]
 MLP_PINS = ["tests/test_oracle_mlp.py"]
+HO_PINS = ["tests/test_oracle_high_order.py"]
 
 # (name, file, original text, planted text, pin files)
 MUTANTS = [
@@ -31,6 +32,13 @@ MUTANTS = [
     ("fast_speed_dropped_cross_term", "echo_oracle.c", "double a2 = cs2 + ca2 - cs2 * ca2;",
      "double a2 = cs2 + ca2;", PINS),
     ("mlp_dropped_activation", "mlp_oracle.c", "a2[k] = tanh(s);", "a2[k] = s;", MLP_PINS),
+    ("ho_dropped_fourth_difference", "echo_oracle.c", "return f5[2] - d2 / 24.0 + 3.0 * d4 / 640.0;",
+     "return f5[2] - d2 / 24.0;", HO_PINS),
+    ("ho_emf_correction_direction", "echo_oracle.c", "const double *Eb = c->order ? G->Ec[b][1] : G->E[b];",
+     "const double *Eb = c->order ? G->Ec[b][0] : G->E[b];", HO_PINS),
+    ("ho_point_value_weight", "echo_oracle.c", "90.0 * u0", "91.0 * u0", HO_PINS),
+    ("ho_centre_weight", "echo_oracle.c", "150.0 * b6[2] + 150.0 * b6[3]", "150.0 * b6[2] + 149.0 * b6[3]",
+     HO_PINS),
 ]
 
 
