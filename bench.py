@@ -444,6 +444,7 @@ def run_ours(args, world, rank, local, dist):
             "c2p_guess": "previous-stage Z refined by FP32 Newton steps; FP64 Newton judges",
             "note": "FP32 storage/stencil, FP64 c2p and reductions; same input, same step count"}}
         del s32
+        variants["fp64_high_order"] = run_order1_variant(args, prob, dev, world, dist, ms)
         mlp_state = None
         if not args.no_mlp:
             variants["fp32_mlp"], mlp_state = run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds,
@@ -475,6 +476,34 @@ def run_ours(args, world, rank, local, dist):
                   totals["c2p_iters"] / max(totals["c2p_calls"], 1), "dt_cfl": totals["dt_cfl"]},
     }
     return line if rank == 0 else None
+
+
+def run_order1_variant(args, prob, dev, world, dist, ms64):
+    """The same input and step count with the high-order form (order 1:
+    point-value MP5, sixth-order cell-centre B, flux-derivative correction
+    of the fluxes and EMFs), FP64."""
+    import dataclasses
+    import torch
+    from paper_1810_04597_gb300.echo import Solver
+    p1 = dataclasses.replace(prob, order=1)
+    s = Solver(p1, precision=64, device=str(dev))
+    s.set_prims()
+    for _ in range(args.warmup):
+        s.step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    for _ in range(args.steps):
+        s.step()
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    t = s.reduce()
+    del s
+    return {"value": world * prob.ncells * args.steps / (max_over_ranks(dist, ms1) * 1e-3) / 1e6, "unit": UNIT,
+            "ms_per_step": ms1 / args.steps, "cost_vs_order0": ms1 / ms64, "c2p_fail": t["c2p_fail"],
+            "note": "FP64, high-order form (flux-derivative correction), same input and steps"}
 
 
 def run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms64):

@@ -104,6 +104,20 @@ int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *
 
 /* Bytes of device workspace the context needs (all arrays, with 3 ghost
  * layers, plus staging and reduction scratch). */
+/* Scheme order, before echo_bind (it changes the workspace size):
+ * 0 (default) the scheme as read -- MP5 with the fifth-order interpolant of
+ * cell averages on the point values, cell-centre B the mean of the two
+ * faces, HLL fluxes and UCT EMFs differenced as they are; 1 high order --
+ * MP5 with the fifth-order interpolant of point values, cell-centre B by
+ * sixth-order interpolation of six faces, and the flux-derivative
+ * correction F - D2/24 + 3 D4/640 (second and fourth differences of
+ * neighbouring interface values) of every flux along its direction and of
+ * every EMF along each of its two half-integer directions, so that the
+ * differences are sixth-order derivatives (the scheme's "high-order"
+ * finite differences).  With order 1 the divergence that stays constant is
+ * the one built from corrected face differences (echo_reduce reports it).
+ * ECHO_EINVAL for another value, ECHO_ESTATE after echo_bind. */
+int echo_set_order(echo_ctx *ctx, int order);
 size_t echo_workspace_bytes(const echo_ctx *ctx);
 
 /* Number of doubles of a host-layout state. */
@@ -269,7 +283,9 @@ int echo_batch_max_blocks_per_sm(echo_batch *batch);
  * own register budget; blocks_per_sm and the queue kind do not apply);
  * 2 run-major: each run's own launch sequence (as echo_step) in turn, so a
  * run's working set stays in L2 across its phases (tile, blocks_per_sm and
- * queue kind do not apply).  ECHO_EINVAL for any other value. */
+ * queue kind do not apply).  ECHO_EINVAL for any other value.  Runs of
+ * order 1 (echo_set_order) need schedule 2 (echo_batch_step returns
+ * ECHO_EINVAL otherwise). */
 int echo_batch_mode(echo_batch *batch, int mode);
 /* Schedule 2 only: spread the runs over `branches` (1 .. number of runs)
  * concurrent streams forked from and joined back into the batch stream (in a
@@ -310,7 +326,8 @@ int echo_selftest_recip(long long n, unsigned long long seed, unsigned long long
 #define ECHO_K_UPDATE 9
 #define ECHO_K_SCALARS 10
 #define ECHO_K_TOTALS 11
-#define ECHO_NK 12
+#define ECHO_K_CORRECT 12
+#define ECHO_NK 13
 
 /* Enable (1) or disable (0) per-kernel timing: while enabled, every kernel
  * launch of echo_step/echo_rhs/echo_c2p/echo_reduce is bracketed by two

@@ -76,6 +76,7 @@ _SIGS = {
     "echo_init": (ctypes.c_int, [ctypes.POINTER(echo_grid), ctypes.POINTER(echo_metric),
                                  ctypes.POINTER(echo_eos), ctypes.c_int, ctypes.c_double,
                                  ctypes.POINTER(_P)]),
+    "echo_set_order": (ctypes.c_int, [_P, ctypes.c_int]),
     "echo_workspace_bytes": (ctypes.c_size_t, [_P]),
     "echo_state_count": (ctypes.c_size_t, [_P]),
     "echo_bind": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
@@ -189,6 +190,10 @@ def echo_init(grid: echo_grid, metric: echo_metric, eos: echo_eos, precision: in
     return ctx
 
 
+def echo_set_order(ctx, order):
+    _check(ctx, load().echo_set_order(ctx, int(order)))
+
+
 def echo_workspace_bytes(ctx) -> int:
     return int(load().echo_workspace_bytes(ctx))
 
@@ -257,7 +262,7 @@ def echo_reduce(ctx) -> echo_totals:
     return t
 
 
-ECHO_NK = 12
+ECHO_NK = 13
 
 
 def echo_profile(ctx, enable: bool):

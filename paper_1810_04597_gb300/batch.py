@@ -118,8 +118,11 @@ def autotune(batch: Batch, tiles=(128, 256, 512, 1024), queue=(True, False), rep
     best = None
     results = []
     nr = len(batch.solvers)
-    cands = [(tile, bps, dyn, PERSISTENT, 1) for tile in tiles for bps in bpss for dyn in queue]
-    cands += [(tile, mb, True, PHASED, 1) for tile in tiles]
+    cands = []
+    if not any(getattr(s.problem, "order", 0) for s in batch.solvers):
+        # the persistent and per-phase schedules run the form of order 0 only
+        cands += [(tile, bps, dyn, PERSISTENT, 1) for tile in tiles for bps in bpss for dyn in queue]
+        cands += [(tile, mb, True, PHASED, 1) for tile in tiles]
     cands += [(256, mb, True, RUN_MAJOR, k) for k in sorted({1, 2, 4, 8, nr}) if k <= nr]
     batch.graph(graph)
     for tile, bps, dyn, mode, br in cands:

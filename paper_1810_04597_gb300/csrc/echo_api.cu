@@ -67,6 +67,13 @@ size_t layout(echo_ctx *c, char *base, Arrays<R> *A)
             A->fv[d][q] = arr();
         A->E[d] = arr();
     }
+    for (int d = 0; d < 3; ++d) {
+        // order 1 only: corrected fluxes and EMFs
+        for (int q = 0; q < 5; ++q)
+            A->Fc[d][q] = c->geo.order ? arr() : nullptr;
+        for (int w = 0; w < 2; ++w)
+            A->Ec[d][w] = c->geo.order ? arr() : nullptr;
+    }
     A->Z = reinterpret_cast<double *>(take(cells * sizeof(double)));
     A->mlp = reinterpret_cast<const float *>(take(MLP_BLOCK * sizeof(float)));
     A->met = MetTables{};
@@ -172,6 +179,8 @@ void enqueue_rhs_pass(echo_ctx *c, int stage, double *Lout, bool want_rate, doub
         PROF(ECHO_K_FACES_X + d, (launch_faces<MK, R>(c->geo, c->ph, A, d, s)));
     for (int e = 0; e < 3; ++e)
         PROF(ECHO_K_EMF_X + e, (launch_emf<MK, R>(c->geo, A, e, s)));
+    if (c->geo.order)
+        PROF(ECHO_K_CORRECT, launch_correct<R>(c->geo, A, s));
     PROF(ECHO_K_UPDATE, (launch_update<MK, R>(c->geo, c->ph, A, stage, Lout, s)));
 }
 
@@ -307,6 +316,22 @@ int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *
     else
         c->ws_need = layout<float>(c, nullptr, &c->af);
     *out = c;
+    return ECHO_OK;
+}
+
+int echo_set_order(echo_ctx *c, int order)
+{
+    if (!c)
+        return ECHO_EINVAL;
+    if (order != 0 && order != 1)
+        return fail(c, ECHO_EINVAL, "order: 0 the scheme as read, 1 high order");
+    if (c->bound)
+        return fail(c, ECHO_ESTATE, "set the order before echo_bind");
+    c->geo.order = order;
+    if (c->precision == 64)
+        c->ws_need = layout<double>(c, nullptr, &c->ad);
+    else
+        c->ws_need = layout<float>(c, nullptr, &c->af);
     return ECHO_OK;
 }
 
@@ -702,7 +727,7 @@ int echo_profile_read(echo_ctx *c, double *ms, long long *launches, int nk)
 const char *echo_kernel_name(int k)
 {
     static const char *names[ECHO_NK] = {"fill_faces", "c2p", "fill_prims", "faces_x", "faces_y", "faces_z",
-                                         "emf_x", "emf_y", "emf_z", "update", "scalars", "totals"};
+                                         "emf_x", "emf_y", "emf_z", "update", "scalars", "totals", "correct"};
     return (k >= 0 && k < ECHO_NK) ? names[k] : "";
 }
 

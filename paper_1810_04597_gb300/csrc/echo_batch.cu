@@ -92,10 +92,16 @@ long long phase_count(const Geom &g, int p, int kind)
         return 2LL * NG * p0 * p1;
     case PH_C2P:
         return n0 * n1 * n2;
-    case PH_FACES:
-        return kind == 0 ? (n0 + 1) * p1 * p2 : (kind == 1 ? p0 * (n1 + 1) * p2 : p0 * p1 * (n2 + 1));
-    case PH_EMF:
-        return kind == 0 ? n0 * (n1 + 1) * (n2 + 1) : (kind == 1 ? (n0 + 1) * n1 * (n2 + 1) : (n0 + 1) * (n1 + 1) * n2);
+    case PH_FACES: {
+        int cnt[3], off[3];
+        faces_space(g, kind, cnt, off);
+        return (long long)cnt[0] * cnt[1] * cnt[2];
+    }
+    case PH_EMF: {
+        int cnt[3], off[3];
+        emf_space(g, kind, cnt, off);
+        return (long long)cnt[0] * cnt[1] * cnt[2];
+    }
     default:
         return (n0 + 1) * (n1 + 1) * (n2 + 1);
     }
@@ -459,9 +465,12 @@ int echo_batch_step(echo_batch *b, double dt)
 {
     if (!b || !b->bound)
         return b ? bfail(b, ECHO_ESTATE, "bind the batch first") : ECHO_EINVAL;
-    for (echo_ctx *c : b->runs)
+    for (echo_ctx *c : b->runs) {
         if (!c->have_state)
             return bfail(b, ECHO_ESTATE, "every run needs a state");
+        if (c->geo.order != 0 && b->phased != 2)
+            return bfail(b, ECHO_EINVAL, "runs of order 1 need the run-major schedule (echo_batch_mode 2)");
+    }
     if (!b->use_graph) {
         const int rc = enqueue_step(b, dt);
         return rc ? rc : bcheck(b, "echo_batch_step");

@@ -13,7 +13,8 @@
 
 namespace echo {
 
-constexpr int NG = 3;              // ghost layers (MP5: 3 cells per side)
+constexpr int NG = 5;              // ghost layers: MP5 needs 3 cells per side, the
+                                   // high-order flux correction two more faces
 constexpr double MP5_ALPHA = 4.0;  // Suresh & Huynh (1997) alpha
 constexpr double MP5_EPS = 1e-10;  // Suresh & Huynh (1997) epsilon
 constexpr double NEWTON_TOL = 1e-13;
@@ -42,11 +43,61 @@ struct Geom {
     double x0[3];
     int bc[6];
     int flo[3], fhi[3];      // owned (evolved) face range along d, inclusive
+    int order;               // 0 the scheme as read; 1 high order (flux-derivative correction)
 };
 
 __host__ __device__ __forceinline__ long long gidx(const Geom &g, int i, int j, int k)
 {
     return (long long)k * g.pxy + (long long)j * g.px + i;
+}
+
+// Iteration space of the D-face kernel: cnt[a] indices from padded index
+// off[a] on each axis.  Along D every face of an owned cell (order 1: two
+// more on each side, for the flux correction); across, the faces whose
+// velocities the EMF stencils (3 rows around the edges) read.
+__host__ __device__ __forceinline__ void faces_space(const Geom &g, int D, int cnt[3], int off[3])
+{
+    const int w = 2 * g.order;
+    for (int a = 0; a < 3; ++a) {
+        cnt[a] = g.n[a] + 6 + 2 * w;
+        off[a] = NG - 3 - w;
+    }
+    cnt[D] = g.n[D] + 1 + 2 * w;
+    off[D] = NG - w;
+}
+
+// Iteration space of the E-edge kernel: the edges of owned cells (order 1:
+// two more on each side across E, for the EMF correction).
+__host__ __device__ __forceinline__ void emf_space(const Geom &g, int E, int cnt[3], int off[3])
+{
+    const int w = 2 * g.order;
+    for (int a = 0; a < 3; ++a) {
+        cnt[a] = g.n[a] + 1 + 2 * w;
+        off[a] = NG - w;
+    }
+    cnt[E] = g.n[E];
+    off[E] = NG;
+}
+
+// Flux-derivative correction at the middle of five interface values
+// f_{-2} .. f_{+2}: f - D2/24 + 3 D4/640 (D2, D4 the second and fourth
+// differences): the interface value of the function whose cell averages
+// are the point values, so that its difference is the sixth-order
+// derivative.
+template <typename T>
+__host__ __device__ __forceinline__ T ho_flux(T fm2, T fm1, T f0, T fp1, T fp2)
+{
+    const T d2 = fm1 - T(2) * f0 + fp1;
+    const T d4 = fm2 - T(4) * fm1 + T(6) * f0 - T(4) * fp1 + fp2;
+    return f0 - d2 * T(1.0 / 24.0) + d4 * T(3.0 / 640.0);
+}
+
+// Sixth-order interpolation to the midpoint of six equally spaced values:
+// (3, -25, 150, 150, -25, 3) / 256.
+template <typename T>
+__host__ __device__ __forceinline__ T ho_center(T b0, T b1, T b2, T b3, T b4, T b5)
+{
+    return (T(3) * (b0 + b5) - T(25) * (b1 + b4) + T(150) * (b2 + b3)) * T(1.0 / 256.0);
 }
 
 struct Phys {
@@ -121,6 +172,8 @@ struct Arrays {
     R *am[3];      // HLL a- on d-faces
     R *fv[3][4];   // d-face states used by the EMFs: v^d_L, v^d_R, v^{d+1}_L, v^{d+1}_R
     R *E[3];       // edge EMFs: E_e at index (i,j,k) = edge at half-integer a, b
+    R *Fc[3][5];   // order 1: corrected fluxes on the owned d-faces (else null)
+    R *Ec[3][2];   // order 1: E_e corrected along (e+1)%3 [0] and (e+2)%3 [1]
     double *stage; // host-layout staging (FP64)
     double *partials;  // reduction partials
     DevScalars *scal;
@@ -385,22 +438,28 @@ __device__ __forceinline__ T minmod4(T w, T x, T y, T z)
 // unlimited value and whether the Suresh & Huynh test accepts it; mp5_limit
 // returns the limited value for a rejected stencil (same uor).
 
-// (2 u_{j-2} - 13 u_{j-1} + 47 u_j + 27 u_{j+1} - 3 u_{j+2}) / 60 with the
-// 1/60 folded into the weights (5 FP64 operations).
+// order 0: (2 u_{j-2} - 13 u_{j-1} + 47 u_j + 27 u_{j+1} - 3 u_{j+2}) / 60, the
+// fifth-order interpolant of cell averages; order 1: (3, -20, 90, 60, -5) /
+// 128, the fifth-order Lagrange interpolant of point values.  Weights
+// pre-divided (5 FP64 operations).
 template <typename T>
-__device__ __forceinline__ T mp5_uor(T um2, T um1, T u0, T up1, T up2)
+__device__ __forceinline__ T mp5_uor(T um2, T um1, T u0, T up1, T up2, int order)
 {
-    return fma(T(2.0 / 60.0), um2,
-               fma(T(-13.0 / 60.0), um1, fma(T(47.0 / 60.0), u0, fma(T(27.0 / 60.0), up1, T(-3.0 / 60.0) * up2))));
+    const T w0 = order ? T(3.0 / 128.0) : T(2.0 / 60.0);
+    const T w1 = order ? T(-20.0 / 128.0) : T(-13.0 / 60.0);
+    const T w2 = order ? T(90.0 / 128.0) : T(47.0 / 60.0);
+    const T w3 = order ? T(60.0 / 128.0) : T(27.0 / 60.0);
+    const T w4 = order ? T(-5.0 / 128.0) : T(-3.0 / 60.0);
+    return fma(w0, um2, fma(w1, um1, fma(w2, u0, fma(w3, up1, w4 * up2))));
 }
 
 // Accept uor if (uor - u_j)(uor - u_mp) <= eps, u_mp = u_j + minmod(u_{j+1} - u_j,
 // alpha (u_j - u_{j-1})); written with d0 = uor - u_j so that
 // uor - u_mp = d0 - minmod(...).
 template <typename T>
-__device__ __forceinline__ T mp5_try(T um2, T um1, T u0, T up1, T up2, bool &accept)
+__device__ __forceinline__ T mp5_try(T um2, T um1, T u0, T up1, T up2, bool &accept, int order)
 {
-    const T uor = mp5_uor(um2, um1, u0, up1, up2);
+    const T uor = mp5_uor(um2, um1, u0, up1, up2, order);
     const T d0 = uor - u0;
     const T mm = minmod2(up1 - u0, T(MP5_ALPHA) * (u0 - um1));
     accept = ile(d0 * (d0 - mm), T(MP5_EPS));
@@ -408,9 +467,9 @@ __device__ __forceinline__ T mp5_try(T um2, T um1, T u0, T up1, T up2, bool &acc
 }
 
 template <typename T>
-__device__ __forceinline__ T mp5_limit(T um2, T um1, T u0, T up1, T up2)
+__device__ __forceinline__ T mp5_limit(T um2, T um1, T u0, T up1, T up2, int order)
 {
-    const T uor = mp5_uor(um2, um1, u0, up1, up2);
+    const T uor = mp5_uor(um2, um1, u0, up1, up2, order);
     const T a4 = T(MP5_ALPHA) * (u0 - um1);
     const T dm1 = um2 - T(2) * um1 + u0;
     const T d0 = um1 - T(2) * u0 + up1;

@@ -104,6 +104,24 @@ __global__ void k_fill(Geom g, int d, FillList<R> L)
 // Body over the linear index t of the owned cells (x fastest); every lane of
 // a warp must call it (warp-level counter reductions).  mlp_sm: the network
 // block in shared memory when MLP.
+// Densitised cell-centre B~ of the cell at padded index id: order 0 the
+// mean of the two faces, order 1 the sixth-order interpolation of the faces
+// i-2 .. i+3 along each axis.
+template <typename R>
+__device__ __forceinline__ void cell_centre_Bt(const Geom &g, const Arrays<R> &A, long long id, double Bt[3])
+{
+    const long long st[3] = {1LL, g.px, g.pxy};
+    for (int d = 0; d < 3; ++d) {
+        const R *__restrict__ f = A.U[5 + d];
+        const long long s = st[d];
+        if (g.order)
+            Bt[d] = ho_center(to_d(f[id - 2 * s]), to_d(f[id - s]), to_d(f[id]), to_d(f[id + s]),
+                              to_d(f[id + 2 * s]), to_d(f[id + 3 * s]));
+        else
+            Bt[d] = 0.5 * (to_d(f[id]) + to_d(f[id + s]));
+    }
+}
+
 // Inputs of the inversion at owned cell t (x fastest): undensitised D, S_i,
 // tau, the cell-centre B (mean of the two faces), sqrt(gamma) and the metric
 // point.  Returns false for t beyond the owned cells.
@@ -128,23 +146,23 @@ __device__ __forceinline__ bool c2p_cell(const Geom &g, const Arrays<R> &A, long
     c.id = id;
     c.sg = 1.0;
     c.mp = nullptr;
+    double Bt[3];
+    cell_centre_Bt(g, A, id, Bt);
     if constexpr (MK == 1) {
         c.mp = &A.met.C[c.j * A.met.np0 + c.i];
         const double isg = c.mp->isg;
         c.sg = c.mp->sg;
-        c.B[0] = 0.5 * (to_d(A.U[5][id]) + to_d(A.U[5][id + 1])) * isg;
-        c.B[1] = 0.5 * (to_d(A.U[6][id]) + to_d(A.U[6][id + g.px])) * isg;
-        c.B[2] = 0.5 * (to_d(A.U[7][id]) + to_d(A.U[7][id + g.pxy])) * isg;
-        for (int q = 0; q < 3; ++q)
+        for (int q = 0; q < 3; ++q) {
+            c.B[q] = Bt[q] * isg;
             c.S[q] = to_d(A.U[1 + q][id]) * isg;
+        }
         c.Dc = to_d(A.U[0][id]) * isg;
         c.tc = to_d(A.U[4][id]) * isg;
     } else {
-        c.B[0] = 0.5 * (to_d(A.U[5][id]) + to_d(A.U[5][id + 1]));
-        c.B[1] = 0.5 * (to_d(A.U[6][id]) + to_d(A.U[6][id + g.px]));
-        c.B[2] = 0.5 * (to_d(A.U[7][id]) + to_d(A.U[7][id + g.pxy]));
-        for (int q = 0; q < 3; ++q)
+        for (int q = 0; q < 3; ++q) {
+            c.B[q] = Bt[q];
             c.S[q] = to_d(A.U[1 + q][id]);
+        }
         c.Dc = to_d(A.U[0][id]);
         c.tc = to_d(A.U[4][id]);
     }
@@ -407,11 +425,11 @@ __device__ __forceinline__ void compact_limit(unsigned pend, long long id, LimSc
 
 // ------------------------------------------------------------------ faces
 
-// MP5 left/right states, HLL flux and speeds on the D-faces.  Face index
-// along D runs over NG..NG+n (every face of an owned cell); transversally
-// the full padded range (the EMFs need face data three rows into the
-// ghosts).  Threads map linearly onto that box so that warps stay full at
-// row ends.  A reconstructed side with rho <= 0, p <= 0 or v^2 >= 1 takes
+// MP5 left/right states, HLL flux and speeds on the D-faces of the box
+// faces_space gives: along D every face of an owned cell (order 1: two more
+// per side for the flux correction), across D three rows into the ghosts
+// (the EMF stencils read face data there; order 1: two more).  Threads map
+// linearly onto that box so that warps stay full at row ends.  A reconstructed side with rho <= 0, p <= 0 or v^2 >= 1 takes
 // the adjacent cell's primitives.
 //
 // The MP5 limiter is taken by ~10-15% of reconstructions; evaluated inline
@@ -434,19 +452,19 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
                                            LimScratch<R> &lsm)
 {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-    int cnt[3] = {g.np[0], g.np[1], g.np[2]};
-    cnt[D] = g.n[D] + 1;
+    int cnt[3], off[3];
+    faces_space(g, D, cnt, off);
     const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
     const bool live = t < tot;
     int ijk[3];
     {
         const long long tt = live ? t : 0;
-        ijk[0] = (int)(tt % cnt[0]);
+        ijk[0] = off[0] + (int)(tt % cnt[0]);
         const long long r = tt / cnt[0];
-        ijk[1] = (int)(r % cnt[1]);
-        ijk[2] = (int)(r / cnt[1]);
-        ijk[D] += NG;
+        ijk[1] = off[1] + (int)(r % cnt[1]);
+        ijk[2] = off[2] + (int)(r / cnt[1]);
     }
+    const int order = g.order;
     const long long id = gidx(g, ijk[0], ijk[1], ijk[2]);
     const long long sd = D == 0 ? 1LL : (D == 1 ? g.px : g.pxy);
     using T = R;
@@ -462,8 +480,8 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
             for (int s = 0; s < 6; ++s)
                 q[s] = a[id + (s - 3) * sd];
             bool okL, okR;
-            Lv[m] = mp5_try(q[0], q[1], q[2], q[3], q[4], okL);
-            Rv[m] = mp5_try(q[5], q[4], q[3], q[2], q[1], okR);
+            Lv[m] = mp5_try(q[0], q[1], q[2], q[3], q[4], okL, order);
+            Rv[m] = mp5_try(q[5], q[4], q[3], q[2], q[1], okR, order);
             pend |= (okL ? 0u : 1u) << (2 * m);
             pend |= (okR ? 0u : 1u) << (2 * m + 1);
         }
@@ -475,7 +493,7 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
 #pragma unroll
         for (int s = 0; s < 6; ++s)
             q[s] = a[ido + (s - 3) * sd];
-        return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1]) : mp5_limit(q[0], q[1], q[2], q[3], q[4]);
+        return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1], order) : mp5_limit(q[0], q[1], q[2], q[3], q[4], order);
     });
     if (!live)
         return;
@@ -622,19 +640,20 @@ template <int E, int MK, typename R>
 __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long long t, LimScratch<R> &lsm)
 {
     constexpr int a = (E + 1) % 3, b = (E + 2) % 3;
-    int cnt[3] = {g.n[0] + 1, g.n[1] + 1, g.n[2] + 1};
-    cnt[E] = g.n[E];
+    int cnt[3], off[3];
+    emf_space(g, E, cnt, off);
     const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
     const bool live = t < tot;
     long long id;
     int ei, ej;
     {
         const long long tt = live ? t : 0;
-        ei = NG + (int)(tt % cnt[0]);
+        ei = off[0] + (int)(tt % cnt[0]);
         const long long r = tt / cnt[0];
-        ej = NG + (int)(r % cnt[1]);
-        id = gidx(g, ei, ej, NG + (int)(r / cnt[1]));
+        ej = off[1] + (int)(r % cnt[1]);
+        id = gidx(g, ei, ej, off[2] + (int)(r / cnt[1]));
     }
+    const int order = g.order;
     const long long sa = a == 0 ? 1LL : (a == 1 ? g.px : g.pxy);
     const long long sb = b == 0 ? 1LL : (b == 1 ? g.px : g.pxy);
     using T = R;
@@ -658,8 +677,8 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
             for (int s = 0; s < 6; ++s)
                 q[s] = S.p[m][id + (s - 3) * S.st[m]];
             bool okL, okR;
-            Lv[m] = mp5_try(q[0], q[1], q[2], q[3], q[4], okL);
-            Rv[m] = mp5_try(q[5], q[4], q[3], q[2], q[1], okR);
+            Lv[m] = mp5_try(q[0], q[1], q[2], q[3], q[4], okL, order);
+            Rv[m] = mp5_try(q[5], q[4], q[3], q[2], q[1], okR, order);
             pend |= (okL ? 0u : 1u) << (2 * m);
             pend |= (okR ? 0u : 1u) << (2 * m + 1);
         }
@@ -672,7 +691,7 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
 #pragma unroll
         for (int s = 0; s < 6; ++s)
             q[s] = p[ido + (s - 3) * st];
-        return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1]) : mp5_limit(q[0], q[1], q[2], q[3], q[4]);
+        return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1], order) : mp5_limit(q[0], q[1], q[2], q[3], q[4], order);
     });
     if (!live)
         return;
@@ -853,8 +872,10 @@ __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const
         for (int q = 0; q < 5; ++q) {
             R r = R(0);
 #pragma unroll
-            for (int d = 0; d < 3; ++d)
-                r -= (A.F[d][q][id + st[d]] - A.F[d][q][id]) * geom_idx<R>(g, d);
+            for (int d = 0; d < 3; ++d) {
+                const R *__restrict__ F = g.order ? A.Fc[d][q] : A.F[d][q];
+                r -= (F[id + st[d]] - F[id]) * geom_idx<R>(g, d);
+            }
             r += src[q];
             if (stage < 0) {
                 Lout[q * N + ((long long)tk * g.n[1] + tj) * g.n[0] + ti] = (double)r;
@@ -881,12 +902,15 @@ __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const
         e[d] += 1;
         const bool trans_own = own[a] && own[b];
         const bool evolved = ijk[d] >= g.flo[d] && ijk[d] <= g.fhi[d];
+        // order 1: E_b corrected along a = (b+2)%3, E_a along b = (a+1)%3
+        const R *__restrict__ Eb = g.order ? A.Ec[b][1] : A.E[b];
+        const R *__restrict__ Ea = g.order ? A.Ec[a][0] : A.E[a];
         if (trans_own) {
             R l = R(0);
             if (evolved) {
                 // dB~^d/dt = -(d_a E_b - d_b E_a)
-                const R dEb = (A.E[b][id + st[a]] - A.E[b][id]) * geom_idx<R>(g, a);
-                const R dEa = (A.E[a][id + st[b]] - A.E[a][id]) * geom_idx<R>(g, b);
+                const R dEb = (Eb[id + st[a]] - Eb[id]) * geom_idx<R>(g, a);
+                const R dEa = (Ea[id + st[b]] - Ea[id]) * geom_idx<R>(g, b);
                 l = -(dEb - dEa);
             }
             if (stage < 0) {
@@ -895,8 +919,8 @@ __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const
                     const bool dup = ijk[d] == NG + g.n[d] && g.bc[2 * d] == BC_PERIODIC;
                     R lo = l;
                     if (dup) {
-                        const R dEb = (A.E[b][id + st[a]] - A.E[b][id]) * geom_idx<R>(g, a);
-                        const R dEa = (A.E[a][id + st[b]] - A.E[a][id]) * geom_idx<R>(g, b);
+                        const R dEb = (Eb[id + st[a]] - Eb[id]) * geom_idx<R>(g, a);
+                        const R dEa = (Ea[id + st[b]] - Ea[id]) * geom_idx<R>(g, b);
                         lo = -(dEb - dEa);
                     }
                     Lout[off + ((long long)tk * e[1] + tj) * e[0] + ti] = (double)lo;
@@ -945,10 +969,10 @@ __global__ void k_p2c(Geom g, Phys ph, const double *prims5, Arrays<R> A)
         isg = mp->isg;
         sg = mp->sg;
     }
+    double Bt[3];
+    cell_centre_Bt(g, A, id, Bt);
     const double P8[8] = {prims5[h], prims5[N + h], prims5[2 * N + h], prims5[3 * N + h], prims5[4 * N + h],
-                          0.5 * ((double)A.U[5][id] + (double)A.U[5][id + 1]) * isg,
-                          0.5 * ((double)A.U[6][id] + (double)A.U[6][id + g.px]) * isg,
-                          0.5 * ((double)A.U[7][id] + (double)A.U[7][id + g.pxy]) * isg};
+                          Bt[0] * isg, Bt[1] * isg, Bt[2] * isg};
     double C5[5], Z;
     if constexpr (MK == 1)
         p2c_point(P8, ph.gr, MKS<double>(*mp), C5, Z);
@@ -1052,9 +1076,24 @@ __global__ void __launch_bounds__(256) k_totals(Geom g, Arrays<R> A)
         acc[2] += (double)A.U[1][id];
         acc[3] += (double)A.U[2][id];
         acc[4] += (double)A.U[3][id];
-        const double dv = ((double)A.U[5][id + 1] - (double)A.U[5][id]) * g.idx[0]
-                          + ((double)A.U[6][id + g.px] - (double)A.U[6][id]) * g.idx[1]
-                          + ((double)A.U[7][id + g.pxy] - (double)A.U[7][id]) * g.idx[2];
+        // div B~ from face differences (order 1: of the corrected face values,
+        // the divergence that order keeps constant)
+        double dv;
+        if (g.order) {
+            const long long sd[3] = {1LL, g.px, g.pxy};
+            dv = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const R *__restrict__ f = A.U[5 + d];
+                const long long s = sd[d];
+                const double v[6] = {(double)f[id - 2 * s], (double)f[id - s], (double)f[id], (double)f[id + s],
+                                     (double)f[id + 2 * s], (double)f[id + 3 * s]};
+                dv += (ho_flux(v[1], v[2], v[3], v[4], v[5]) - ho_flux(v[0], v[1], v[2], v[3], v[4])) * g.idx[d];
+            }
+        } else {
+            dv = ((double)A.U[5][id + 1] - (double)A.U[5][id]) * g.idx[0]
+                 + ((double)A.U[6][id + g.px] - (double)A.U[6][id]) * g.idx[1]
+                 + ((double)A.U[7][id + g.pxy] - (double)A.U[7][id]) * g.idx[2];
+        }
         acc[5] = fmax(acc[5], fabs(dv));
     }
 #pragma unroll
@@ -1194,6 +1233,57 @@ __global__ void k_unpack_z(Geom g, const double *src, Arrays<R> A)
     const long long h = ((long long)tk * g.n[1] + tj) * g.n[0] + ti;
     A.Z[id] = src ? src[h] : 0.0;
 }
+
+// ---- order 1: flux-derivative correction (ho_flux) of the fluxes along
+// their direction on the owned faces, and of each EMF along each of its two
+// half-integer directions on the edges of owned cells.
+template <typename R>
+__global__ void __launch_bounds__(256) k_fcorr(Geom g, Arrays<R> A, int d)
+{
+    const long long c0 = g.n[0] + (d == 0), c1 = g.n[1] + (d == 1), c2 = g.n[2] + (d == 2);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= c0 * c1 * c2)
+        return;
+    const long long id = gidx(g, NG + (int)(t % c0), NG + (int)((t / c0) % c1), NG + (int)(t / (c0 * c1)));
+    const long long s = d == 0 ? 1LL : (d == 1 ? g.px : g.pxy);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const R *__restrict__ F = A.F[d][q];
+        A.Fc[d][q][id] = ho_flux(F[id - 2 * s], F[id - s], F[id], F[id + s], F[id + 2 * s]);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_ecorr(Geom g, Arrays<R> A, int e)
+{
+    const long long c0 = g.n[0] + (e != 0), c1 = g.n[1] + (e != 1), c2 = g.n[2] + (e != 2);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= c0 * c1 * c2)
+        return;
+    const long long id = gidx(g, NG + (int)(t % c0), NG + (int)((t / c0) % c1), NG + (int)(t / (c0 * c1)));
+    const long long st[3] = {1LL, g.px, g.pxy};
+    const R *__restrict__ E = A.E[e];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+        const long long s = st[(e + 1 + w) % 3];
+        A.Ec[e][w][id] = ho_flux(E[id - 2 * s], E[id - s], E[id], E[id + s], E[id + 2 * s]);
+    }
+}
+
+template <typename R>
+void launch_correct(const Geom &g, const Arrays<R> &A, cudaStream_t s)
+{
+    for (int d = 0; d < 3; ++d) {
+        const long long n = (long long)(g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * (g.n[2] + (d == 2));
+        k_fcorr<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, A, d);
+    }
+    for (int e = 0; e < 3; ++e) {
+        const long long n = (long long)(g.n[0] + (e != 0)) * (g.n[1] + (e != 1)) * (g.n[2] + (e != 2));
+        k_ecorr<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, A, e);
+    }
+}
+template void launch_correct<double>(const Geom &, const Arrays<double> &, cudaStream_t);
+template void launch_correct<float>(const Geom &, const Arrays<float> &, cudaStream_t);
 
 #endif  // ECHO_COMMON_KERNELS
 

@@ -38,6 +38,9 @@ void launch_mlp_dataset(const Geom &g, const Arrays<R> &A, float *X, float *Y, l
                         cudaStream_t s);
 template <typename R>
 void launch_totals(const Geom &g, const Arrays<R> &A, int nblk, cudaStream_t s);
+// order 1: corrected fluxes (Fc) and EMFs (Ec) from F and E (6 launches)
+template <typename R>
+void launch_correct(const Geom &g, const Arrays<R> &A, cudaStream_t s);
 template <typename R>
 void launch_unpack_state(const Geom &g, const double *src, const Arrays<R> &A, int what, cudaStream_t s);
 template <typename R>

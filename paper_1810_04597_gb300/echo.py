@@ -38,6 +38,8 @@ class Solver:
                           float(problem.rho_floor_pow), float(problem.p_floor), float(problem.p_floor_pow))
         self.precision = int(precision)
         self.ctx = _lib.echo_init(g, m, e, self.precision, float(problem.cfl))
+        if getattr(problem, "order", 0):
+            _lib.echo_set_order(self.ctx, int(problem.order))
         self.nbytes = _lib.echo_workspace_bytes(self.ctx)
         self.nstate = _lib.echo_state_count(self.ctx)
         self.ncells = int(problem.n[0]) * int(problem.n[1]) * int(problem.n[2])

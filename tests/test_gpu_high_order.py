@@ -1,0 +1,120 @@
+"""The high-order form (echo_set_order 1: point-value MP5, sixth-order
+cell-centre B, flux-derivative correction of the fluxes and EMFs) on the
+GPU against the oracle's order 1: the right-hand side on a ragged grid,
+steps in flat space and on the Kerr-Schild torus (FP64, max relative error
+per field <= 1e-11), the FP32-bulk form in relative L1, the divergence that
+order 1 keeps constant, and the batch schedules it runs under."""
+import numpy as np
+import pytest
+
+from paper_1810_04597_gb300 import inputs
+from gpu_util import gpu_run, l1_rel, oracle_run, per_field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def _order1(prob):
+    prob.order = 1
+    return prob
+
+
+def test_order1_rhs_parity_ragged(orc):
+    """L(U) on a ragged grid (not a multiple of any tile size)."""
+    from paper_1810_04597_gb300.echo import Solver
+    from test_gpu_parity import crop
+    prob = _order1(crop(inputs.sweep_box(40, seed=5), (37, 29, 23)))
+    s = Solver(prob)
+    s.set_prims()
+    L_g = s.rhs()
+    cfg = orc.make_cfg(prob)
+    st, Z = orc.p2c(cfg, prob.prims, prob.bface)
+    L_o, _, _ = orc.rhs(cfg, st, Z)
+    errs = per_field(orc, L_g, L_o, prob.n)
+    assert max(errs.values()) <= 1e-11, errs
+
+
+def test_order1_ragged_steps(orc):
+    from test_gpu_parity import crop
+    prob = _order1(crop(inputs.smooth_box(40, seed=11), (33, 21, 17)))
+    st_g, _ = gpu_run(prob, 3)
+    st_o, _, _, _ = oracle_run(orc, prob, 3)
+    errs = per_field(orc, st_g, st_o, prob.n)
+    assert max(errs.values()) <= 1e-11, errs
+
+
+@pytest.mark.parametrize("size", [32, 24])
+def test_order1_ten_steps_flat(orc, size):
+    prob = _order1(inputs.smooth_box(size, seed=40 + size))
+    st_g, s = gpu_run(prob, 10)
+    st_o, _, _, _ = oracle_run(orc, prob, 10)
+    errs = per_field(orc, st_g, st_o, prob.n)
+    assert max(errs.values()) <= 1e-11, errs
+
+
+def test_order1_steps_torus(orc):
+    """Five steps of the magnetised torus on Kerr-Schild (floors, polar axis).
+    The high-order form has no positivity safeguard: on this torus both
+    codes lose the same cells to NaN at step 7 (the atmosphere's failed
+    inversions grow every step), so the comparison stops at 5."""
+    prob = _order1(inputs.fm_torus((48, 24, 12), spin=0.9))
+    st_g, s = gpu_run(prob, 5)
+    st_o, _, _, ostats = oracle_run(orc, prob, 5)
+    assert np.all(np.isfinite(st_g)) and np.all(np.isfinite(st_o))
+    errs = per_field(orc, st_g, st_o, prob.n)
+    assert max(errs.values()) <= 1e-11, errs
+
+
+def test_order1_fp32_bulk(orc):
+    prob = _order1(inputs.smooth_box(32, seed=7))
+    st_g, _ = gpu_run(prob, 10, precision=32)
+    st_o, _, _, _ = oracle_run(orc, prob, 10)
+    l1 = per_field(orc, st_g, st_o, prob.n, metric=l1_rel)
+    assert max(l1.values()) <= 1e-5, l1
+
+
+def test_order1_keeps_its_divergence_and_conserves():
+    from paper_1810_04597_gb300.echo import Solver
+    prob = _order1(inputs.sweep_box(32, seed=9))
+    s = Solver(prob)
+    s.set_prims()
+    t0 = s.reduce()
+    for _ in range(10):
+        s.step()
+    t1 = s.reduce()
+    bmax = np.max(np.abs(s.get_state()[5 * prob.ncells:]))
+    assert abs(t1["max_divb"] - t0["max_divb"]) * prob.dx[0] <= 1e-12 * bmax
+    assert abs(t1["mass"] - t0["mass"]) <= 1e-13 * abs(t0["mass"])
+    assert abs(t1["energy"] - t0["energy"]) <= 1e-13 * abs(t0["energy"])
+
+
+def test_order1_batch_needs_run_major():
+    from paper_1810_04597_gb300 import _lib
+    from paper_1810_04597_gb300.batch import Batch, RUN_MAJOR, PERSISTENT
+    from paper_1810_04597_gb300.echo import Solver
+    probs = [_order1(inputs.smooth_box(16, seed=s)) for s in (1, 2)]
+    single = []
+    for p in probs:
+        x = Solver(p)
+        x.set_prims()
+        x.step()
+        single.append(x.get_state())
+    runs = []
+    for p in probs:
+        x = Solver(p)
+        x.set_prims()
+        runs.append(x)
+    b = Batch(runs)
+    b.configure(mode=PERSISTENT)
+    with pytest.raises(_lib.EchoError):
+        b.step()
+    b.configure(mode=RUN_MAJOR, branches=2)
+    b.step()
+    for r, x in zip(single, runs):
+        assert np.array_equal(x.get_state(), r)
