@@ -31,8 +31,15 @@
  *     Bz (nz+1, ny, nx), face i-1/2 at index i.  On a periodic axis the last
  *     face repeats the first (read: ignored; written: duplicated).
  *   - A pointer argument flagged "on_device" is a device pointer when the
- *     flag is 1 and a host pointer otherwise.  A host input buffer must stay
- *     unchanged until the next synchronising call.
+ *     flag is 1; a host pointer copied through the library's staging area
+ *     when it is 0; and, when it is 2, a host pointer into page-locked host
+ *     memory mapped into the device's address space (cudaHostAlloc, torch
+ *     pin_memory), which the library's kernels read or write directly over
+ *     the host link with no staging copy -- the library checks the mapping
+ *     with cudaPointerGetAttributes (ECHO_EINVAL if the memory is not
+ *     mapped page-locked memory) but not the buffer's length, which must be
+ *     the documented one.  A host input buffer must stay unchanged until the
+ *     next synchronising call.  Other flag values: ECHO_EINVAL.
  */
 #ifndef ECHO_H
 #define ECHO_H

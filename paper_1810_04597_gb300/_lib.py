@@ -160,7 +160,8 @@ def _check(ctx, rc):
 
 
 def _ptr(a, writable=False):
-    """(pointer, on_device) of a NumPy array or torch CUDA tensor (FP64)."""
+    """(pointer, on_device) of a NumPy array (0), a torch CUDA tensor (1) or
+    a page-locked torch CPU tensor (2), FP64."""
     if a is None:
         return None, 0
     if isinstance(a, np.ndarray):
@@ -177,7 +178,8 @@ def _ptr(a, writable=False):
         raise TypeError("tensors must be contiguous float64")
     if a.is_cuda:
         return a.data_ptr(), 1
-    return a.data_ptr(), 0
+    # page-locked host memory is read/written directly by the kernels (2)
+    return a.data_ptr(), (2 if a.is_pinned() else 0)
 
 
 # ---------------------------------------------------------------- entry points

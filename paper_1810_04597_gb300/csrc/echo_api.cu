@@ -365,12 +365,34 @@ int echo_bind(echo_ctx *c, void *ws, size_t bytes, void *stream)
     return cuda_check(c, "echo_bind");
 }
 
+// Device address of page-locked host memory mapped into the device's
+// address space, or null if p is not such memory.
+static void *mapped_host(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 static const double *stage_input(echo_ctx *c, const double *src, size_t count, size_t at, int on_device,
                                  int *rc)
 {
     *rc = ECHO_OK;
-    if (on_device)
+    if (on_device < 0 || on_device > 2) {
+        *rc = fail(c, ECHO_EINVAL, "on_device: 0 host (staged), 1 device, 2 mapped page-locked host memory");
+        return nullptr;
+    }
+    if (on_device == 1)
         return src;
+    if (on_device == 2) {
+        const double *d = static_cast<const double *>(mapped_host(src));
+        if (!d)
+            *rc = fail(c, ECHO_EINVAL, "on_device = 2 needs page-locked host memory mapped into the device");
+        return d;
+    }
     double *st = (c->precision == 64 ? c->ad.stage : c->af.stage) + at;
     if (cudaMemcpyAsync(st, src, count * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         *rc = cuda_check(c, "host to device copy");
@@ -445,9 +467,29 @@ int echo_set_state(echo_ctx *c, const double *state, const double *Z, int on_dev
     return rc;
 }
 
+// Where an output is written: the caller's device pointer (1), its mapped
+// host memory (2), or the staging area copied out afterwards (0).
+static double *output_target(echo_ctx *c, double *out, int on_device, int *rc)
+{
+    *rc = ECHO_OK;
+    if (on_device < 0 || on_device > 2) {
+        *rc = fail(c, ECHO_EINVAL, "on_device: 0 host (staged), 1 device, 2 mapped page-locked host memory");
+        return nullptr;
+    }
+    if (on_device == 1)
+        return out;
+    if (on_device == 2) {
+        double *d = static_cast<double *>(mapped_host(out));
+        if (!d)
+            *rc = fail(c, ECHO_EINVAL, "on_device = 2 needs page-locked host memory mapped into the device");
+        return d;
+    }
+    return c->precision == 64 ? c->ad.stage : c->af.stage;
+}
+
 static int finish_output(echo_ctx *c, double *dst, const double *staged, size_t count, int on_device)
 {
-    if (!on_device) {
+    if (on_device == 0) {
         if (cudaMemcpyAsync(dst, staged, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
             return cuda_check(c, "device to host copy");
     }
@@ -463,7 +505,9 @@ int echo_get_state(echo_ctx *c, double *out, int on_device)
         return rc;
     if (!out)
         return fail(c, ECHO_EINVAL, "null output");
-    double *dst = on_device ? out : (c->precision == 64 ? c->ad.stage : c->af.stage);
+    double *dst = output_target(c, out, on_device, &rc);
+    if (rc)
+        return rc;
     if (c->precision == 64) {
         launch_fill<double>(c->geo, face_list(c->ad), c->stream);
         launch_pack_state<double>(c->geo, c->ad, dst, c->stream);
@@ -482,7 +526,9 @@ int echo_get_prims(echo_ctx *c, double *out, int on_device)
     if (!out)
         return fail(c, ECHO_EINVAL, "null output");
     const size_t N = (size_t)c->geo.n[0] * c->geo.n[1] * c->geo.n[2];
-    double *dst = on_device ? out : (c->precision == 64 ? c->ad.stage : c->af.stage);
+    double *dst = output_target(c, out, on_device, &rc);
+    if (rc)
+        return rc;
     if (c->precision == 64)
         launch_pack_cells<double>(c->geo, c->ad, dst, 0, c->stream);
     else
@@ -498,7 +544,9 @@ int echo_get_z(echo_ctx *c, double *out, int on_device)
     if (!out)
         return fail(c, ECHO_EINVAL, "null output");
     const size_t N = (size_t)c->geo.n[0] * c->geo.n[1] * c->geo.n[2];
-    double *dst = on_device ? out : (c->precision == 64 ? c->ad.stage : c->af.stage);
+    double *dst = output_target(c, out, on_device, &rc);
+    if (rc)
+        return rc;
     if (c->precision == 64)
         launch_pack_cells<double>(c->geo, c->ad, dst, 1, c->stream);
     else
@@ -545,12 +593,14 @@ int echo_rhs(echo_ctx *c, double *L, int on_device)
         return rc;
     if (!L)
         return fail(c, ECHO_EINVAL, "null output");
-    double *dst = on_device ? L : (c->precision == 64 ? c->ad.stage : c->af.stage);
+    double *dst = output_target(c, L, on_device, &rc);
+    if (rc)
+        return rc;
     rc = ECHO_DISPATCH(c, op_rhs, dst);
     if (rc)
         return rc;
-    if (!on_device)
-        return finish_output(c, L, dst, c->nstate, 0);
+    if (on_device != 1)
+        return finish_output(c, L, dst, c->nstate, on_device);
     return ECHO_OK;
 }
 

@@ -79,17 +79,16 @@ size_t a256(size_t v) { return (v + 255) / 256 * 256; }
 long long phase_count(const Geom &g, int p, int kind)
 {
     const long long n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
-    const long long p0 = g.np[0], p1 = g.np[1], p2 = g.np[2];
     switch (p) {
     case PH_FILLF0:
     case PH_FILLP0:
-        return 2LL * NG * p1 * p2;
+        return fill_count(g, 0);
     case PH_FILLF1:
     case PH_FILLP1:
-        return 2LL * NG * p0 * p2;
+        return fill_count(g, 1);
     case PH_FILLF2:
     case PH_FILLP2:
-        return 2LL * NG * p0 * p1;
+        return fill_count(g, 2);
     case PH_C2P:
         return n0 * n1 * n2;
     case PH_FACES: {

@@ -51,6 +51,17 @@ __host__ __device__ __forceinline__ long long gidx(const Geom &g, int i, int j, 
     return (long long)k * g.pxy + (long long)j * g.px + i;
 }
 
+// Ghost layers the scheme reads: 3 (MP5 stencils), 5 for order 1.
+__host__ __device__ __forceinline__ int fill_layers(const Geom &g) { return 3 + 2 * g.order; }
+
+// Threads of one ghost-fill launch along axis d (fill_body).
+__host__ __device__ __forceinline__ long long fill_count(const Geom &g, int d)
+{
+    const int nl = fill_layers(g);
+    const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+    return 2LL * nl * (g.n[d1] + 2 * nl) * (g.n[d2] + 2 * nl);
+}
+
 // Iteration space of the D-face kernel: cnt[a] indices from padded index
 // off[a] on each axis.  Along D every face of an owned cell (order 1: two
 // more on each side, for the flux correction); across, the faces whose

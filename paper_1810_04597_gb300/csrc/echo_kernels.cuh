@@ -45,24 +45,28 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 
 // ------------------------------------------------------------------ ghost fill
 
-// Fill the ghost slab of axis d for a list of arrays.  Thread (s, t1, t2):
-// s in [0, 2 NG) selects the ghost layer (lower layers 0..NG-1, upper
-// n+NG..n+2NG-1), t1/t2 run over the full padded extent of the other axes.
+// Fill the ghost slab of axis d for a list of arrays, over the ghost layers
+// the scheme reads (fill_layers: 3, order 1: 5).  Thread (s, t1, t2): s in
+// [0, 2 L) selects the layer (lower NG-L..NG-1, upper NG+n..NG+n+L-1), t1/t2
+// run over the same extent of the other axes (so that edges and corners
+// are filled by the later axes).
 template <typename R>
 __device__ __forceinline__ void fill_body(const Geom &g, int d, const FillList<R> &L, long long t)
 {
     const int d1 = d == 0 ? 1 : 0;
     const int d2 = d == 2 ? 1 : 2;
-    if (t >= (long long)2 * NG * g.np[d1] * g.np[d2])
+    const int nl = fill_layers(g);
+    const int e1 = g.n[d1] + 2 * nl, e2 = g.n[d2] + 2 * nl;
+    if (t >= (long long)2 * nl * e1 * e2)
         return;
-    const int s = (int)(t % (2 * NG));
-    const int t1 = (int)((t / (2 * NG)) % g.np[d1]);
-    const int t2 = (int)(t / (2 * NG) / g.np[d1]);
-    const int id_d = s < NG ? s : g.n[d] + s;
+    const int s = (int)(t % (2 * nl));
+    const int t1 = (int)((t / (2 * nl)) % e1);
+    const int t2 = (int)(t / (2 * nl) / e1);
+    const int id_d = s < nl ? NG - nl + s : NG + g.n[d] + (s - nl);
     int ijk[3];
     ijk[d] = id_d;
-    ijk[d1] = t1;
-    ijk[d2] = t2;
+    ijk[d1] = NG - nl + t1;
+    ijk[d2] = NG - nl + t2;
     const long long dst = gidx(g, ijk[0], ijk[1], ijk[2]);
     const long long sd = d == 0 ? 1LL : (d == 1 ? g.px : g.pxy);
     for (int a = 0; a < L.count; ++a) {

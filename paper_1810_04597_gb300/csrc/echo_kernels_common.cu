@@ -16,8 +16,7 @@ template <typename R>
 void launch_fill(const Geom &g, const FillList<R> &L, cudaStream_t s)
 {
     for (int d = 0; d < 3; ++d) {
-        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
-        const long long tot = (long long)2 * NG * g.np[d1] * g.np[d2];
+        const long long tot = fill_count(g, d);
         k_fill<R><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, d, L);
     }
 }

@@ -198,3 +198,38 @@ def test_small_workspace_rejected():
         _lib.echo_bind(ctx, ws.data_ptr(), 1024, torch.cuda.current_stream().cuda_stream)
     assert e.value.code == _lib.ECHO_ENOMEM
     _lib.echo_destroy(ctx)
+
+
+def test_mapped_host_buffers_match_staged_copies():
+    """on_device = 2: page-locked host buffers read and written by the
+    kernels directly give the same state, primitives, Z and L(U) as the
+    staged copies of plain host arrays; pageable memory is refused."""
+    import ctypes
+    import torch
+    from paper_1810_04597_gb300 import _lib
+    from paper_1810_04597_gb300.echo import Solver
+    prob = inputs.smooth_box(20, seed=17)
+    a = Solver(prob)
+    a.set_prims()
+    a.step()
+    st = a.get_state()
+    z = a.get_z()
+    b = Solver(prob)
+    st_p = torch.from_numpy(st.copy()).pin_memory()
+    z_p = torch.from_numpy(z.copy()).pin_memory()
+    b.set_state(st_p, z_p)
+    out = torch.zeros(b.nstate, dtype=torch.float64).pin_memory()
+    b.get_state(out)
+    assert np.array_equal(out.numpy(), st)
+    zo = torch.zeros(prob.ncells, dtype=torch.float64).pin_memory()
+    b.get_z(zo)
+    assert np.array_equal(zo.numpy(), z)
+    L1 = a.rhs()
+    Lp = torch.zeros(a.nstate, dtype=torch.float64).pin_memory()
+    b.rhs(Lp)
+    assert np.array_equal(Lp.numpy(), L1)
+    plain = np.zeros(b.nstate)
+    rc = _lib.load().echo_get_state(b.ctx, ctypes.c_void_p(plain.ctypes.data), 2)
+    assert rc == _lib.ECHO_EINVAL
+    rc = _lib.load().echo_get_state(b.ctx, ctypes.c_void_p(plain.ctypes.data), 3)
+    assert rc == _lib.ECHO_EINVAL
