@@ -498,3 +498,64 @@ def fm_torus(n=(64, 32, 32), spin=0.9, beta=100.0, r_in=6.0, r_max=12.0, r_out=5
                    bc=(OUTFLOW, OUTFLOW, AXIS, AXIS, PERIODIC, PERIODIC), metric=1, spin=a, gamma=gam,
                    floors=True, rho_floor=rho_floor, rho_floor_pow=-1.5, p_floor=p_floor, p_floor_pow=-2.5,
                    steps=steps, seed=seed, prims=prims, bface=pack_faces(bx, by, bz))
+
+
+def michel_accretion(n_r: int, r_in=3.0, r_out=20.0, r_c=8.0, rho_c=1.0, gamma=4.0 / 3.0, order=0) -> Problem:
+    """Michel (1972) steady spherical accretion of a polytropic gas (p = K
+    rho^G) onto a Schwarzschild black hole (M = 1), transonic at r_c, on an
+    equatorial slab of the Kerr-Schild (ln r, theta, phi) grid: n_r cells in
+    ln r on [ln r_in, ln r_out], one cell in theta centred at pi/2 and one in
+    phi (periodic there), outflow in r, B = 0.
+
+    Along the radial inflow, rest-mass conservation rho u^r r^2 = C1 and the
+    Bernoulli integral h^2 (1 - 2/r + (u^r)^2) = C2 hold; at the sonic
+    radius (u^r)^2 = 1/(2 r_c) and c_s^2 = (u^r)^2 / (1 - 3 (u^r)^2), which
+    fixes K from rho_c.  At each cell the density is the root of the
+    Bernoulli relation on the subsonic branch outside r_c and the
+    supersonic branch inside.  u^r is the same in Boyer-Lindquist and
+    Kerr-Schild coordinates; u^t_KS = u^t_BL + (2/r)/(1 - 2/r) u^r, and the
+    Eulerian velocity is v^r = u^r/(alpha u^t) + beta^r/alpha (v^x1 = v^r/r)."""
+    from scipy.optimize import brentq, minimize_scalar
+    G = gamma
+    uc2 = 1.0 / (2.0 * r_c)
+    cs2 = uc2 / (1.0 - 3.0 * uc2)
+    x = cs2 / (G * (1.0 - cs2 / (G - 1.0)))          # K rho_c^(G-1)
+    K = x / rho_c ** (G - 1.0)
+    uc = -np.sqrt(uc2)
+    h = lambda rho: 1.0 + G / (G - 1.0) * K * rho ** (G - 1.0)  # noqa: E731
+    C1 = rho_c * uc * r_c * r_c
+    C2 = h(rho_c) ** 2 * (1.0 - 2.0 / r_c + uc2)
+
+    def F(lrho, r):
+        rho = np.exp(lrho)
+        u = C1 / (rho * r * r)
+        return h(rho) ** 2 * (1.0 - 2.0 / r + u * u) - C2
+
+    x0 = (np.log(r_in), np.pi / 2 - 0.05, 0.0)
+    dx = ((np.log(r_out) - np.log(r_in)) / n_r, 0.1, 2.0 * np.pi)
+    rc = np.exp(x0[0] + (np.arange(n_r) + 0.5) * dx[0])
+    rho = np.empty(n_r)
+    for i, r in enumerate(rc):
+        lo, hi = np.log(rho_c) - 30.0, np.log(rho_c) + 30.0
+        m = minimize_scalar(lambda l: F(l, r), bounds=(lo, hi), method="bounded",
+                            options={"xatol": 1e-12})
+        ls = m.x
+        if r > r_c:
+            rho[i] = np.exp(brentq(F, ls, hi, args=(r,), xtol=1e-15, rtol=1e-15))
+        else:
+            rho[i] = np.exp(brentq(F, lo, ls, args=(r,), xtol=1e-15, rtol=1e-15))
+    u = C1 / (rho * rc * rc)
+    f = 1.0 - 2.0 / rc
+    ut = np.sqrt(f + u * u) / f + (2.0 / rc) / f * u
+    alpha = 1.0 / np.sqrt(1.0 + 2.0 / rc)
+    betar = (2.0 / rc) / (1.0 + 2.0 / rc)
+    vr = u / (alpha * ut) + betar / alpha
+    prims = np.zeros((5, 1, 1, n_r))
+    prims[0, 0, 0] = rho
+    prims[1, 0, 0] = vr / rc
+    prims[4, 0, 0] = K * rho ** G
+    nn = (n_r, 1, 1)
+    bface = np.zeros((n_r + 1) + (1 + 1) * n_r + (1 + 1) * n_r)
+    return Problem(name=f"michel_{n_r}", n=nn, x0=x0, dx=dx, bc=(OUTFLOW, OUTFLOW, PERIODIC, PERIODIC, PERIODIC,
+                                                                PERIODIC),
+                   metric=1, spin=0.0, gamma=G, prims=prims, bface=bface, order=order)

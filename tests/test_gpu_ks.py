@@ -74,3 +74,19 @@ def test_ks_fp32_bulk(orc):
     l1 = per_field(orc, st_g, st_o, prob.n, metric=l1_rel)
     assert l1["D"] <= 1e-5 and l1["tau"] <= 1e-5, l1
     assert max(l1.values()) <= 1e-4, l1
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_michel_rhs_parity(orc, order):
+    """L(U) of the Michel accretion state (radial inflow through the
+    Kerr-Schild shift) on the GPU against the oracle, both orders."""
+    from paper_1810_04597_gb300.echo import Solver
+    prob = inputs.michel_accretion(96, order=order)
+    s = Solver(prob)
+    s.set_prims()
+    L_g = s.rhs()
+    cfg = orc.make_cfg(prob)
+    st, Z = orc.p2c(cfg, prob.prims, prob.bface)
+    L_o, _, _ = orc.rhs(cfg, st, Z)
+    errs = per_field(orc, L_g, L_o, prob.n)
+    assert max(errs[k] for k in ("D", "S_x", "tau")) <= 1e-11, errs

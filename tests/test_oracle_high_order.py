@@ -133,3 +133,13 @@ def test_high_order_state_matches_the_scheme_as_read_to_truncation(orc):
     (a0, a1), (b0, b1) = out
     change = np.max(np.abs(a1 - a0))
     assert np.max(np.abs(a1 - b1)) < 0.05 * change
+
+
+def test_michel_accretion_high_order(orc):
+    """The same stationary Michel flow with order 1: L(U) converges at
+    fifth order for D and at fourth order for S_r and tau, whose sources use
+    fourth-order differences of the metric."""
+    from test_oracle_scheme import _michel_residuals
+    res, orders = _michel_residuals(orc, 1, sizes=(64, 128, 256))
+    print("Michel residual orders, order 1:", orders)
+    assert np.all(orders[:, 0] >= 4.5) and np.all(orders[:, 1:] >= 3.7), (res, orders)

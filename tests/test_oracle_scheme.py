@@ -241,3 +241,30 @@ def test_torus_steps_conserve_in_the_bulk(orc):
     assert t1[5] * min(p.dx) / bmax < 1e-12
     assert abs(t1[0] - t0[0]) < 1e-3 * t0[0]
     assert np.all(dts > 0)
+
+
+def _michel_residuals(orc, order, sizes=(32, 64, 128)):
+    res = []
+    for n in sizes:
+        p = inputs.michel_accretion(n, order=order)
+        cfg = orc.make_cfg(p)
+        st, Z = orc.p2c(cfg, p.prims, p.bface)
+        L, _, _ = orc.rhs(cfg, st, Z)
+        N = p.ncells
+        cells = L[:5 * N].reshape(5, N)
+        U = st[:5 * N].reshape(5, N)
+        rc = np.exp(p.x0[0] + (np.arange(n) + 0.5) * p.dx[0])
+        core = (rc > 4.0) & (rc < 16.0)          # away from the outflow boundaries
+        res.append([np.sum(np.abs(cells[q][core])) / np.sum(np.abs(U[q][core])) for q in (0, 1, 4)])
+    res = np.array(res)
+    return res, np.log2(res[:-1] / res[1:])
+
+
+def test_michel_accretion_residual_converges(orc):
+    """Michel's transonic radial accretion onto a Schwarzschild hole is a
+    stationary solution: on the Kerr-Schild grid (radial inflow, non-zero
+    shift) L(U) of the exact state converges to zero at second order
+    (D, S_r, tau), which pins the radial fluxes, the shift terms and the
+    sources with a flow the torus does not have."""
+    res, orders = _michel_residuals(orc, 0)
+    assert np.all(orders >= 1.8), (res, orders)
