@@ -1033,7 +1033,7 @@ static void emf_dir(const ocfg *c, ogrid *G, int e)
  *   S(S_i) = 1/2 alpha W^jk d_i gamma_jk + S_j d_i beta^j - U d_i alpha
  *   S(tau) = 1/2 W^ik beta^j d_j gamma_ik + W_i^j d_j beta^i - S^j d_j alpha
  * (the second is alpha K_ij W^ij - S^j d_j alpha with d_t gamma_ij = 0).
- * Metric derivatives: fourth-order centred differences of the closed-form
+ * Metric derivatives: sixth-order centred differences of the closed-form
  * metric with step dx^d.  Zero in flat space. */
 static void sources_point(const ocfg *c, const double x[3], const ometric *m, const double *P,
                           double src[5])
@@ -1045,15 +1045,15 @@ static void sources_point(const ocfg *c, const double x[3], const ometric *m, co
     double dal[3], dbe[3][3], dg[3][3][3];
     for (int d = 0; d < 3; ++d) {
         double h = c->dx[d];
-        double wts[4] = {1.0, -8.0, 8.0, -1.0};
-        double offs[4] = {-2.0, -1.0, 1.0, 2.0};
+        double wts[6] = {-1.0, 9.0, -45.0, 45.0, -9.0, 1.0};
+        double offs[6] = {-3.0, -2.0, -1.0, 1.0, 2.0, 3.0};
         dal[d] = 0.0;
         for (int i = 0; i < 3; ++i) {
             dbe[d][i] = 0.0;
             for (int j = 0; j < 3; ++j)
                 dg[d][i][j] = 0.0;
         }
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < 6; ++s) {
             double y[3] = {x[0], x[1], x[2]};
             y[d] += offs[s] * h;
             double al, be[3], g[3][3];
@@ -1065,11 +1065,11 @@ static void sources_point(const ocfg *c, const double x[3], const ometric *m, co
                     dg[d][i][j] += wts[s] * g[i][j];
             }
         }
-        dal[d] /= 12.0 * h;
+        dal[d] /= 60.0 * h;
         for (int i = 0; i < 3; ++i) {
-            dbe[d][i] /= 12.0 * h;
+            dbe[d][i] /= 60.0 * h;
             for (int j = 0; j < 3; ++j)
-                dg[d][i][j] /= 12.0 * h;
+                dg[d][i][j] /= 60.0 * h;
         }
     }
     double v[3] = {P[1], P[2], P[3]}, B[3] = {P[5], P[6], P[7]};

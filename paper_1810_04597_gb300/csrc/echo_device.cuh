@@ -154,7 +154,7 @@ struct MetPt {
 };
 
 // d_1 and d_2 of alpha, beta^1, gamma_11, _13, _22, _33 at a cell centre
-// (fourth-order centred differences of the closed form, step dx^d).
+// (sixth-order centred differences of the closed form, step dx^d).
 struct MetDer {
     double dal[2], db1[2], dg11[2], dg13[2], dg22[2], dg33[2];
 };

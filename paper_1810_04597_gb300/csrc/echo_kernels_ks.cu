@@ -49,7 +49,7 @@ __device__ MetPt ks_point(double x1, double th, double a)
 }
 
 // One thread per (i, j) of the padded (x1, x2) plane: the four table
-// positions, fourth-order centred derivatives at the cell centre
+// positions, sixth-order centred derivatives at the cell centre
 // ((f(-2h) - 8 f(-h) + 8 f(h) - f(2h)) / (12 h), h = dx^d), and per i the
 // floors f0 r^pow at the cell centre.
 __global__ void k_metric_tables(Geom g, double a, MetTables T, double rho_floor, double rho_pow, double p_floor,
@@ -69,12 +69,13 @@ __global__ void k_metric_tables(Geom g, double a, MetTables T, double rho_floor,
     T.F2[id] = ks_point(xc, tf, a);
     T.K[id] = ks_point(xf, tf, a);
     MetDer dv;
-    const double w[4] = {1.0, -8.0, 8.0, -1.0};
-    const double o[4] = {-2.0, -1.0, 1.0, 2.0};
+    // sixth-order centred differences of the closed-form metric
+    const double w[6] = {-1.0, 9.0, -45.0, 45.0, -9.0, 1.0};
+    const double o[6] = {-3.0, -2.0, -1.0, 1.0, 2.0, 3.0};
     for (int d = 0; d < 2; ++d) {
         double acc[6] = {0, 0, 0, 0, 0, 0};
         const double h = g.dx[d];
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < 6; ++s) {
             double v[6];
             const double x1 = d == 0 ? xc + o[s] * h : xc;
             const double th = d == 1 ? tc + o[s] * h : tc;
@@ -82,12 +83,12 @@ __global__ void k_metric_tables(Geom g, double a, MetTables T, double rho_floor,
             for (int c = 0; c < 6; ++c)
                 acc[c] += w[s] * v[c];
         }
-        dv.dal[d] = acc[0] / (12.0 * h);
-        dv.db1[d] = acc[1] / (12.0 * h);
-        dv.dg11[d] = acc[2] / (12.0 * h);
-        dv.dg13[d] = acc[3] / (12.0 * h);
-        dv.dg22[d] = acc[4] / (12.0 * h);
-        dv.dg33[d] = acc[5] / (12.0 * h);
+        dv.dal[d] = acc[0] / (60.0 * h);
+        dv.db1[d] = acc[1] / (60.0 * h);
+        dv.dg11[d] = acc[2] / (60.0 * h);
+        dv.dg13[d] = acc[3] / (60.0 * h);
+        dv.dg22[d] = acc[4] / (60.0 * h);
+        dv.dg33[d] = acc[5] / (60.0 * h);
     }
     T.dC[id] = dv;
     if (j == 0) {
