@@ -453,6 +453,8 @@ def run_ours(args, world, rank, local, dist):
                                                               ms)
         if not args.no_sweep:
             variants["sweep_batch"] = run_sweep_variant(args, dev, world, dist, mlp_state)
+        if not args.no_512 and mlp_state is not None:
+            variants["box512_fp64_vs_fp32_mlp"] = run_box512_variant(args, dev, world, dist, mlp_state)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -557,6 +559,69 @@ def run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms64):
     return out, state
 
 
+def run_box512_variant(args, dev, world, dist, mlp_state):
+    """The 512^3 periodic box of the parity recipe (smooth_box): FP64 and FP32
+    bulk + network c2p guess (tensor cores) on the same input, W + K steps
+    each, and the relative L1 distance per field of the FP32 + network state
+    from the FP64 state."""
+    import numpy as np
+    import torch
+    from paper_1810_04597_gb300 import inputs
+    from paper_1810_04597_gb300.echo import Solver
+    prob = inputs.smooth_box(512)
+    out = {"zones": prob.ncells, "steps": args.steps}
+
+    def timed(s):
+        for _ in range(args.warmup):
+            s.step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for _ in range(args.steps):
+            s.step()
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(dist, e0.elapsed_time(e1))
+
+    s = Solver(prob, precision=64, device=str(dev))
+    s.set_prims()
+    ms64 = timed(s)
+    fin64 = s.get_state()
+    s.close()
+    del s
+    s = Solver(prob, precision=32, device=str(dev))
+    s.set_prims()
+    s.mlp_load(mlp_state)
+    s.set_c2p_guess(5)
+    c0 = s.counters()
+    ms32 = timed(s)
+    c1 = s.counters()
+    fin32 = s.get_state()
+    s.close()
+    del s
+    N = prob.ncells
+    nx, ny, nz = prob.n
+    bounds = [0, N, 2 * N, 3 * N, 4 * N, 5 * N, 5 * N + nz * ny * (nx + 1),
+              5 * N + nz * ny * (nx + 1) + nz * (ny + 1) * nx, len(fin64)]
+    names = ["D", "S_x", "S_y", "S_z", "tau", "Bx", "By", "Bz"]
+    l1 = {}
+    for name, a, b in zip(names, bounds[:-1], bounds[1:]):
+        den = float(np.sum(np.abs(fin64[a:b])))
+        l1[name] = float(np.sum(np.abs(fin32[a:b] - fin64[a:b])) / den) if den > 0 else 0.0
+    calls = max(c1["c2p_calls"] - c0["c2p_calls"], 1)
+    out.update({
+        "fp64": {"value": world * N * args.steps / (ms64 * 1e-3) / 1e6, "unit": UNIT,
+                 "ms_per_step": ms64 / args.steps},
+        "fp32_mlp": {"value": world * N * args.steps / (ms32 * 1e-3) / 1e6, "unit": UNIT,
+                     "ms_per_step": ms32 / args.steps, "speedup_vs_fp64": ms64 / ms32,
+                     "l1_rel_vs_fp64_gpu": l1, "max_l1": max(l1.values()),
+                     "mean_newton_iters": (c1["c2p_iters"] - c0["c2p_iters"]) / calls,
+                     "mlp_fallback_per_call": (c1["mlp_fallback"] - c0["mlp_fallback"]) / calls},
+        "note": "smooth_box recipe at 512^3 (|k| <= 3 modes), same input and step count for both"})
+    return out
+
+
 def run_sweep_variant(args, dev, world, dist, mlp_state):
     """The 16-run Fishbone-Moncrief torus sweep (uneven sizes 64x32x32 ..
     192x96x96, spins 0..0.98, beta 10/100), FP32 bulk + network c2p guess,
@@ -640,6 +705,7 @@ def main():
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-512", action="store_true", help="skip the 512^3 FP64 / FP32 + network variant")
     ap.add_argument("--guess", type=int, default=None, choices=(0, 1, 4, 5, 9, 13),
                     help="c2p guess mode of the main line (default: 0 for FP64, 4 for FP32)")
     args = ap.parse_args()

@@ -72,19 +72,18 @@ def _axes(n, x0, dx, off):
 
 def _mode_sum(modes, xs):
     """sum_m a_m cos(2 pi k_m . x + phi_m) on the tensor grid xs = (x, y, z);
-    returns an array (nz, ny, nx)."""
+    returns an array (nz, ny, nx).  cos(A + B) = cos A cos B - sin A sin B
+    with A along x and B on the (z, y) plane, summed over the modes as one
+    matrix product."""
     x, y, z = xs
-    acc = np.zeros((len(z), len(y), len(x)))
-    tmp = np.empty_like(acc)
+    left, right = [], []
     for (kx, ky, kz, amp, ph) in modes:
-        # cos(A + B) = cos A cos B - sin A sin B, A along x, B on the (z, y) plane
         A = 2 * np.pi * kx * x + ph
         B = 2 * np.pi * (kz * z[:, None] + ky * y[None, :])
-        np.multiply.outer(amp * np.cos(B), np.cos(A), out=tmp)
-        acc += tmp
-        np.multiply.outer(amp * np.sin(B), np.sin(A), out=tmp)
-        acc -= tmp
-    return acc
+        left += [amp * np.cos(B).reshape(-1), -amp * np.sin(B).reshape(-1)]
+        right += [np.cos(A), np.sin(A)]
+    acc = np.stack(left, axis=1) @ np.stack(right, axis=0)
+    return acc.reshape(len(z), len(y), len(x))
 
 
 def _random_k(rng, kmax):
@@ -105,16 +104,26 @@ def _random_modes(rng, count, kmax, amp_lo=0.5, amp_hi=1.0):
 
 def _lowpass_noise(rng, n, kmax, lo, hi):
     """White noise U[lo, hi] per cell, keeping only Fourier modes with
-    |k|_inf <= kmax (k in units of the box)."""
+    |k|_inf <= kmax (k in units of the box): the discrete Fourier
+    coefficients of those modes and their synthesis, both evaluated as
+    separable sums (small matrix products) since only (2 kmax + 1)^3 modes
+    survive."""
     w = rng.uniform(lo, hi, size=(n[2], n[1], n[0]))
-    f = np.fft.rfftn(w)
-    kz = np.fft.fftfreq(n[2]) * n[2]
-    ky = np.fft.fftfreq(n[1]) * n[1]
-    kx = np.fft.rfftfreq(n[0]) * n[0]
-    mask = ((np.abs(kz)[:, None, None] <= kmax) & (np.abs(ky)[None, :, None] <= kmax)
-            & (np.abs(kx)[None, None, :] <= kmax))
-    f = f * mask
-    return np.fft.irfftn(f, s=(n[2], n[1], n[0]), axes=(0, 1, 2))
+    ks = np.arange(-kmax, kmax + 1)
+
+    def basis(m):
+        return np.exp(-2j * np.pi * np.outer(ks, np.arange(m)) / m)
+
+    Ex, Ey, Ez = basis(n[0]), basis(n[1]), basis(n[2])
+    w2 = w.reshape(-1, n[0])
+    t = (w2 @ Ex.real.T + 1j * (w2 @ Ex.imag.T)).reshape(n[2], n[1], len(ks))
+    t = np.einsum("zyk,jy->zjk", t, Ey)
+    F = np.einsum("zjk,iz->ijk", t, Ez)                       # coefficients (kz, ky, kx)
+    h = np.einsum("ijk,kx->ijx", F, Ex.conj())
+    h = np.einsum("ijx,jy->iyx", h, Ey.conj()).reshape(len(ks), -1)
+    Ec = Ez.conj().T
+    g = Ec.real @ h.real - Ec.imag @ h.imag                   # real part of the synthesis
+    return g.reshape(n[2], n[1], n[0]) / (n[0] * n[1] * n[2])
 
 
 def curl_faces(n, dx, Ax, Ay, Az):
