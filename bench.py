@@ -447,6 +447,7 @@ def run_ours(args, world, rank, local, dist):
             "note": "FP32 storage/stencil, FP64 c2p and reductions; same input, same step count"}}
         del s32
         variants["fp64_high_order"] = run_order1_variant(args, prob, dev, world, dist, ms)
+        variants["torus_256x128x128"] = run_torus_variant(args, dev, world, dist)
         mlp_state = None
         if not args.no_mlp:
             variants["fp32_mlp"], mlp_state = run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds,
@@ -480,6 +481,58 @@ def run_ours(args, world, rank, local, dist):
                   totals["c2p_iters"] / max(totals["c2p_calls"], 1), "dt_cfl": totals["dt_cfl"]},
     }
     return line if rank == 0 else None
+
+
+def run_torus_variant(args, dev, world, dist, steps=50):
+    """Fishbone-Moncrief torus on the Kerr metric (a = 0.9, beta = 100, 2 %
+    pressure noise), 256 x 128 x 128 in (ln r, theta, phi) with atmosphere
+    floors: FP32 bulk (guess: previous Z refined in FP32) and FP64 on the same
+    input, W + 50 steps each; relative L1 per field of FP32 from FP64."""
+    import numpy as np
+    import torch
+    from paper_1810_04597_gb300 import inputs
+    from paper_1810_04597_gb300.echo import Solver
+    prob = inputs.fm_torus((256, 128, 128), spin=0.9, beta=100.0)
+    res = {"zones": prob.ncells, "steps": steps}
+    fin = {}
+    for prec in (64, 32):
+        s = Solver(prob, precision=prec, device=str(dev))
+        s.set_prims()
+        if prec == 32:
+            s.set_c2p_guess(4)
+        for _ in range(args.warmup):
+            s.step()
+        torch.cuda.synchronize()
+        c0 = s.counters()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for _ in range(steps):
+            s.step()
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(dist, e0.elapsed_time(e1))
+        c1 = s.counters()
+        calls = max(c1["c2p_calls"] - c0["c2p_calls"], 1)
+        fin[prec] = s.get_state()
+        res[f"fp{prec}"] = {"value": world * prob.ncells * steps / (ms * 1e-3) / 1e6, "unit": UNIT,
+                            "ms_per_step": ms / steps,
+                            "mean_newton_iters": (c1["c2p_iters"] - c0["c2p_iters"]) / calls,
+                            "c2p_fail_per_call": (c1["c2p_fail"] - c0["c2p_fail"]) / calls,
+                            "floor_hits_per_call": (c1["floor_hits"] - c0["floor_hits"]) / calls}
+        s.close()
+        del s
+    N = prob.ncells
+    a64, a32 = fin[64], fin[32]
+    l1 = {}
+    for q, name in enumerate(["D", "S_r", "S_theta", "S_phi", "tau"]):
+        seg = slice(q * N, (q + 1) * N)
+        den = float(np.sum(np.abs(a64[seg])))
+        l1[name] = float(np.sum(np.abs(a32[seg] - a64[seg])) / den) if den > 0 else 0.0
+    res["fp32"]["l1_rel_vs_fp64_gpu"] = l1
+    res["fp32"]["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res["fp32"]["ms_per_step"]
+    res["note"] = "Kerr-Schild, floors and fallbacks; FP32 bulk with FP64 c2p, metric and reductions"
+    return res
 
 
 def run_order1_variant(args, prob, dev, world, dist, ms64):
