@@ -105,12 +105,14 @@ typedef struct {
 /* Create a context.  precision: 64 (FP64 everywhere) or 32 (FP32 storage
  * and stencil arithmetic; c2p, metric and reductions in FP64).  cfl: the
  * Courant number of the CFL time step.  Validates the configuration;
- * returns ECHO_EINVAL (and *out = NULL) on a bad one. */
+ * returns ECHO_EINVAL (and *out = NULL) on a bad one, and also when the
+ * padded grid (n + 10 cells per axis, x rounded up to a multiple of 8) has
+ * 2^31 cells or more: the kernels index each array with 32-bit offsets
+ * (the limit is near 1278^3 cells, where the workspace of either
+ * precision is already larger than the 288 GB of one GPU). */
 int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *eos, int precision,
               double cfl, echo_ctx **out);
 
-/* Bytes of device workspace the context needs (all arrays, with 3 ghost
- * layers, plus staging and reduction scratch). */
 /* Scheme order, before echo_bind (it changes the workspace size):
  * 0 (default) the scheme as read -- MP5 with the fifth-order interpolant of
  * cell averages on the point values, cell-centre B the mean of the two
@@ -125,6 +127,9 @@ int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *
  * the one built from corrected face differences (echo_reduce reports it).
  * ECHO_EINVAL for another value, ECHO_ESTATE after echo_bind. */
 int echo_set_order(echo_ctx *ctx, int order);
+
+/* Bytes of device workspace the context needs (all arrays, with 5 ghost
+ * layers per side, plus staging and reduction scratch). */
 size_t echo_workspace_bytes(const echo_ctx *ctx);
 
 /* Number of doubles of a host-layout state. */

@@ -3,6 +3,7 @@
 // Host-side orchestration only: validation, workspace layout, and the
 // order of kernel launches for c2p, L(U) and one SSP-RK3 step.  Every
 // operation on the state runs in the kernels of echo_kernels.cu.
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -270,9 +271,15 @@ int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *
         return ECHO_EINVAL;
     if (!(eos->gamma > 1.0) || !(cfl > 0.0) || (precision != 64 && precision != 32))
         return ECHO_EINVAL;
-    const long long cells = (long long)grid->n[0] * grid->n[1] * grid->n[2];
-    if (cells > (1LL << 31))
-        return ECHO_EINVAL;
+    // padded cells (n + 2 NG per axis, x rounded up to 8) below 2^31: the
+    // kernels index every array with 32-bit offsets
+    {
+        long long padded = (long long)align_up((size_t)grid->n[0] + 2 * NG, 8);
+        for (int d = 1; d < 3 && padded <= INT_MAX; ++d)
+            padded *= (long long)grid->n[d] + 2 * NG;
+        if (padded > INT_MAX)
+            return ECHO_EINVAL;
+    }
 
     echo_ctx *c = new (std::nothrow) echo_ctx();
     if (!c)
@@ -295,9 +302,9 @@ int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *
         g.flo[d] = NG + (grid->bc[2 * d] == ECHO_BC_AXIS ? 1 : 0);
         g.fhi[d] = per ? NG + g.n[d] - 1 : NG + g.n[d] - (grid->bc[2 * d + 1] == ECHO_BC_AXIS ? 1 : 0);
     }
-    g.px = (long long)align_up((size_t)g.np[0], 8);
+    g.px = (int)align_up((size_t)g.np[0], 8);
     g.pxy = g.px * g.np[1];
-    g.cells_padded = g.pxy * g.np[2];
+    g.cells_padded = (long long)g.pxy * g.np[2];
     c->ph.gamma = eos->gamma;
     c->ph.gr = eos->gamma / (eos->gamma - 1.0);
     c->ph.gm1g = (eos->gamma - 1.0) / eos->gamma;
@@ -306,7 +313,7 @@ int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *
     c->ph.gr_f = (float)c->ph.gr;
     for (int d = 0; d < 3; ++d)
         g.idx_f[d] = (float)g.idx[d];
-    const size_t N = (size_t)cells;
+    const size_t N = (size_t)grid->n[0] * grid->n[1] * grid->n[2];
     c->nstate = 5 * N + (size_t)g.n[2] * g.n[1] * (g.n[0] + 1) + (size_t)g.n[2] * (g.n[1] + 1) * g.n[0]
                 + (size_t)(g.n[2] + 1) * g.n[1] * g.n[0];
     c->staging_count = c->nstate > 8 * N ? c->nstate : 8 * N;

@@ -35,7 +35,9 @@ enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_AXIS = 2 };
 struct Geom {
     int n[3];
     int np[3];
-    long long px, pxy;
+    // x and xy strides of the padded arrays; echo_init keeps cells_padded
+    // below 2^31, so every offset into one array is an int
+    int px, pxy;
     long long cells_padded;  // pxy * np2
     double dx[3];
     double idx[3];           // 1/dx
@@ -46,9 +48,9 @@ struct Geom {
     int order;               // 0 the scheme as read; 1 high order (flux-derivative correction)
 };
 
-__host__ __device__ __forceinline__ long long gidx(const Geom &g, int i, int j, int k)
+__host__ __device__ __forceinline__ int gidx(const Geom &g, int i, int j, int k)
 {
-    return (long long)k * g.pxy + (long long)j * g.px + i;
+    return k * g.pxy + j * g.px + i;
 }
 
 // Ghost layers the scheme reads: 3 (MP5 stencils), 5 for order 1.

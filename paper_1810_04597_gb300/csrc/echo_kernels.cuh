@@ -21,9 +21,9 @@ namespace echo {
 
 // ------------------------------------------------------------------ helpers
 
-__device__ __forceinline__ long long stride_of(const Geom &g, int d)
+__device__ __forceinline__ int stride_of(const Geom &g, int d)
 {
-    return d == 0 ? 1LL : (d == 1 ? g.px : g.pxy);
+    return d == 0 ? 1 : (d == 1 ? g.px : g.pxy);
 }
 
 template <typename T>
@@ -67,8 +67,8 @@ __device__ __forceinline__ void fill_body(const Geom &g, int d, const FillList<R
     ijk[d] = id_d;
     ijk[d1] = NG - nl + t1;
     ijk[d2] = NG - nl + t2;
-    const long long dst = gidx(g, ijk[0], ijk[1], ijk[2]);
-    const long long sd = d == 0 ? 1LL : (d == 1 ? g.px : g.pxy);
+    const int dst = gidx(g, ijk[0], ijk[1], ijk[2]);
+    const int sd = stride_of(g, d);
     for (int a = 0; a < L.count; ++a) {
         bool flip;
         const int face = L.face[a] == d ? 1 : 0;
@@ -77,7 +77,7 @@ __device__ __forceinline__ void fill_body(const Geom &g, int d, const FillList<R
             continue;
         R val = R(0);
         if (src >= 0) {
-            val = L.a[a][dst + (long long)(src - id_d) * sd];
+            val = L.a[a][dst + (src - id_d) * sd];
             if (flip && L.comp[a] == d)
                 val = -val;
         }
@@ -112,12 +112,12 @@ __global__ void k_fill(Geom g, int d, FillList<R> L)
 // mean of the two faces, order 1 the sixth-order interpolation of the faces
 // i-2 .. i+3 along each axis.
 template <typename R>
-__device__ __forceinline__ void cell_centre_Bt(const Geom &g, const Arrays<R> &A, long long id, double Bt[3])
+__device__ __forceinline__ void cell_centre_Bt(const Geom &g, const Arrays<R> &A, int id, double Bt[3])
 {
-    const long long st[3] = {1LL, g.px, g.pxy};
+    const int st[3] = {1, g.px, g.pxy};
     for (int d = 0; d < 3; ++d) {
         const R *__restrict__ f = A.U[5 + d];
-        const long long s = st[d];
+        const int s = st[d];
         if (g.order)
             Bt[d] = ho_center(to_d(f[id - 2 * s]), to_d(f[id - s]), to_d(f[id]), to_d(f[id + s]),
                               to_d(f[id + 2 * s]), to_d(f[id + 3 * s]));
@@ -130,7 +130,7 @@ __device__ __forceinline__ void cell_centre_Bt(const Geom &g, const Arrays<R> &A
 // tau, the cell-centre B (mean of the two faces), sqrt(gamma) and the metric
 // point.  Returns false for t beyond the owned cells.
 struct C2PCell {
-    long long id;
+    int id;
     int i, j;
     double B[3], S[3], Dc, tc, sg;
     const MetPt *mp;
@@ -142,11 +142,14 @@ __device__ __forceinline__ bool c2p_cell(const Geom &g, const Arrays<R> &A, long
     const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
     if (t >= ncell)
         return false;
-    c.i = NG + (int)(t % g.n[0]);
-    const long long r = t / g.n[0];
-    c.j = NG + (int)(r % g.n[1]);
-    const int k = NG + (int)(r / g.n[1]);
-    const long long id = gidx(g, c.i, c.j, k);
+    // 32-bit decomposition: t < ncell < 2^31
+    const unsigned u = (unsigned)t, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    const unsigned r = u / n0;
+    c.i = NG + (int)(u - r * n0);
+    const unsigned k0 = r / n1;
+    c.j = NG + (int)(r - k0 * n1);
+    const int k = NG + (int)k0;
+    const int id = gidx(g, c.i, c.j, k);
     c.id = id;
     c.sg = 1.0;
     c.mp = nullptr;
@@ -195,7 +198,7 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
     double rate = 0.0;
     unsigned long long its = 0, calls = 0, fails = 0, floors = 0, mfb = 0;
     if (live) {
-        const long long id = c.id;
+        const int id = c.id;
         const int i = c.i;
         const MetPt *mp = c.mp;
         const double sg = c.sg;
@@ -387,7 +390,7 @@ struct LimScratch {
 
 // limited(id_of_owner, m, side) -> T
 template <typename T, typename F>
-__device__ __forceinline__ void compact_limit(unsigned pend, long long id, LimScratch<T> &sm, F limited)
+__device__ __forceinline__ void compact_limit(unsigned pend, int id, LimScratch<T> &sm, F limited)
 {
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
@@ -418,7 +421,7 @@ __device__ __forceinline__ void compact_limit(unsigned pend, long long id, LimSc
         const bool act = item < total;
         const unsigned d = act ? sm.desc[w][item] : (unsigned)(lane << 4);
         const int o = (int)(d >> 4);
-        const long long ido = __shfl_sync(0xffffffffu, id, o);
+        const int ido = __shfl_sync(0xffffffffu, id, o);
         if (act) {
             const int b = (int)(d & 15);
             sm.res[w][o][b] = limited(ido, b >> 1, b & 1);
@@ -462,15 +465,16 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     const bool live = t < tot;
     int ijk[3];
     {
-        const long long tt = live ? t : 0;
-        ijk[0] = off[0] + (int)(tt % cnt[0]);
-        const long long r = tt / cnt[0];
-        ijk[1] = off[1] + (int)(r % cnt[1]);
-        ijk[2] = off[2] + (int)(r / cnt[1]);
+        // 32-bit decomposition: the face box lies inside the padded array
+        const unsigned tt = live ? (unsigned)t : 0u, c0 = (unsigned)cnt[0], c1 = (unsigned)cnt[1];
+        const unsigned r = tt / c0, r2 = r / c1;
+        ijk[0] = off[0] + (int)(tt - r * c0);
+        ijk[1] = off[1] + (int)(r - r2 * c1);
+        ijk[2] = off[2] + (int)r2;
     }
     const int order = g.order;
-    const long long id = gidx(g, ijk[0], ijk[1], ijk[2]);
-    const long long sd = D == 0 ? 1LL : (D == 1 ? g.px : g.pxy);
+    const int id = gidx(g, ijk[0], ijk[1], ijk[2]);
+    const int sd = stride_of(g, D);
     using T = R;
     const int qs[7] = {0, 1, 2, 3, 4, 5 + T1, 5 + T2};
     T Lv[7], Rv[7];
@@ -491,7 +495,7 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
         }
     }
     // limiter on the rejected items, compacted across the warp
-    compact_limit<T>(pend, id, lsm, [&](long long ido, int m, int side) -> T {
+    compact_limit<T>(pend, id, lsm, [&](int ido, int m, int side) -> T {
         const R *__restrict__ a = pick7(A, qs, m);
         T q[6];
 #pragma unroll
@@ -554,7 +558,7 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
             v2 = Ps[1] * Ps[1] + Ps[2] * Ps[2] + Ps[3] * Ps[3];
         }
         if (!is_pos(Ps[0]) || !is_pos(Ps[4]) || !ilt(v2, T(1))) {
-            const long long c = id + (side == 0 ? -sd : 0);
+            const int c = id + (side == 0 ? -sd : 0);
 #pragma unroll
             for (int m = 0; m < 7; ++m)
                 Ps[qs[m]] = A.P[qs[m]][c];
@@ -624,11 +628,11 @@ __global__ void __launch_bounds__(128) k_faces(Geom g, Phys ph, Arrays<R> A)
 template <typename R>
 struct EmfSrc {
     const R *p[6];      // v^a_L, v^a_R, v^b_L, v^b_R (a-faces, along b), B~b (along a), B~a (along b)
-    long long st[6];    // stencil stride of each source
+    int st[6];          // stencil stride of each source
 };
 
 template <typename R>
-__device__ __forceinline__ void emf_pick(const EmfSrc<R> &S, int m, const R *&p, long long &st)
+__device__ __forceinline__ void emf_pick(const EmfSrc<R> &S, int m, const R *&p, int &st)
 {
     p = S.p[0];
     st = S.st[0];
@@ -648,18 +652,19 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
     emf_space(g, E, cnt, off);
     const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
     const bool live = t < tot;
-    long long id;
+    int id;
     int ei, ej;
     {
-        const long long tt = live ? t : 0;
-        ei = off[0] + (int)(tt % cnt[0]);
-        const long long r = tt / cnt[0];
-        ej = off[1] + (int)(r % cnt[1]);
-        id = gidx(g, ei, ej, off[2] + (int)(r / cnt[1]));
+        // 32-bit decomposition: the edge box lies inside the padded array
+        const unsigned tt = live ? (unsigned)t : 0u, c0 = (unsigned)cnt[0], c1 = (unsigned)cnt[1];
+        const unsigned r = tt / c0, r2 = r / c1;
+        ei = off[0] + (int)(tt - r * c0);
+        ej = off[1] + (int)(r - r2 * c1);
+        id = gidx(g, ei, ej, off[2] + (int)r2);
     }
     const int order = g.order;
-    const long long sa = a == 0 ? 1LL : (a == 1 ? g.px : g.pxy);
-    const long long sb = b == 0 ? 1LL : (b == 1 ? g.px : g.pxy);
+    const int sa = stride_of(g, a);
+    const int sb = stride_of(g, b);
     using T = R;
     EmfSrc<R> S;
     S.p[0] = A.fv[a][0];
@@ -687,9 +692,9 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
             pend |= (okR ? 0u : 1u) << (2 * m + 1);
         }
     }
-    compact_limit<T>(pend, id, lsm, [&](long long ido, int m, int side) -> T {
+    compact_limit<T>(pend, id, lsm, [&](int ido, int m, int side) -> T {
         const R *p;
-        long long st;
+        int st;
         emf_pick(S, m, p, st);
         T q[6];
 #pragma unroll
@@ -851,12 +856,14 @@ __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const
     const long long e0 = g.n[0] + 1, e1 = g.n[1] + 1;
     if (t >= e0 * e1 * (g.n[2] + 1))
         return;
-    const int ti = (int)(t % e0);
-    const int tj = (int)((t / e0) % e1);
-    const int tk = (int)(t / (e0 * e1));
+    // 32-bit decomposition: the box lies inside the padded array
+    const unsigned u = (unsigned)t, r = u / (unsigned)e0, r2 = r / (unsigned)e1;
+    const int ti = (int)(u - r * (unsigned)e0);
+    const int tj = (int)(r - r2 * (unsigned)e1);
+    const int tk = (int)r2;
     const int i = NG + ti, j = NG + tj, k = NG + tk;
-    const long long id = gidx(g, i, j, k);
-    const long long st[3] = {1LL, g.px, g.pxy};
+    const int id = gidx(g, i, j, k);
+    const int st[3] = {1, g.px, g.pxy};
     const int own[3] = {ti < g.n[0], tj < g.n[1], tk < g.n[2]};
     const int ijk[3] = {i, j, k};
     const R dt = stage >= 0 ? (R)A.scal->dt : R(0);
@@ -1074,7 +1081,7 @@ __global__ void __launch_bounds__(256) k_totals(Geom g, Arrays<R> A)
         const long long r = t / g.n[0];
         const int tj = (int)(r % g.n[1]);
         const int tk = (int)(r / g.n[1]);
-        const long long id = gidx(g, NG + ti, NG + tj, NG + tk);
+        const int id = gidx(g, NG + ti, NG + tj, NG + tk);
         acc[0] += (double)A.U[0][id];
         acc[1] += (double)A.U[4][id];
         acc[2] += (double)A.U[1][id];
@@ -1084,11 +1091,11 @@ __global__ void __launch_bounds__(256) k_totals(Geom g, Arrays<R> A)
         // the divergence that order keeps constant)
         double dv;
         if (g.order) {
-            const long long sd[3] = {1LL, g.px, g.pxy};
+            const int sd[3] = {1, g.px, g.pxy};
             dv = 0.0;
             for (int d = 0; d < 3; ++d) {
                 const R *__restrict__ f = A.U[5 + d];
-                const long long s = sd[d];
+                const int s = sd[d];
                 const double v[6] = {(double)f[id - 2 * s], (double)f[id - s], (double)f[id], (double)f[id + s],
                                      (double)f[id + 2 * s], (double)f[id + 3 * s]};
                 dv += (ho_flux(v[1], v[2], v[3], v[4], v[5]) - ho_flux(v[0], v[1], v[2], v[3], v[4])) * g.idx[d];
@@ -1248,8 +1255,8 @@ __global__ void __launch_bounds__(256) k_fcorr(Geom g, Arrays<R> A, int d)
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= c0 * c1 * c2)
         return;
-    const long long id = gidx(g, NG + (int)(t % c0), NG + (int)((t / c0) % c1), NG + (int)(t / (c0 * c1)));
-    const long long s = d == 0 ? 1LL : (d == 1 ? g.px : g.pxy);
+    const int id = gidx(g, NG + (int)(t % c0), NG + (int)((t / c0) % c1), NG + (int)(t / (c0 * c1)));
+    const int s = stride_of(g, d);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const R *__restrict__ F = A.F[d][q];
@@ -1264,12 +1271,12 @@ __global__ void __launch_bounds__(256) k_ecorr(Geom g, Arrays<R> A, int e)
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= c0 * c1 * c2)
         return;
-    const long long id = gidx(g, NG + (int)(t % c0), NG + (int)((t / c0) % c1), NG + (int)(t / (c0 * c1)));
-    const long long st[3] = {1LL, g.px, g.pxy};
+    const int id = gidx(g, NG + (int)(t % c0), NG + (int)((t / c0) % c1), NG + (int)(t / (c0 * c1)));
+    const int st[3] = {1, g.px, g.pxy};
     const R *__restrict__ E = A.E[e];
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
-        const long long s = st[(e + 1 + w) % 3];
+        const int s = st[(e + 1 + w) % 3];
         A.Ec[e][w][id] = ho_flux(E[id - 2 * s], E[id - s], E[id], E[id + s], E[id + 2 * s]);
     }
 }

@@ -74,6 +74,20 @@ def test_init_rejects_bad_grids(lib, kw):
     assert e.value.code == _lib.ECHO_EINVAL
 
 
+def test_init_limits_padded_arrays_to_32_bit_offsets(lib):
+    """The kernels index each padded array (n + 10 per axis, x rounded up to
+    8) with int offsets: echo_init takes 1278^3 (1288^3 padded < 2^31) and
+    rejects 1279^3 and grids whose product would overflow."""
+    eos = _lib.echo_eos(4.0 / 3.0, 0, 0, 0, 0, 0)
+    flat = _lib.echo_metric(0, 0.0)
+    ctx = _lib.echo_init(_grid((1278, 1278, 1278)), flat, eos, 32, 0.4)
+    _lib.echo_destroy(ctx)
+    for n in [(1279, 1279, 1279), (2 ** 30, 2 ** 30, 1), (1, 1, 2 ** 31 - 1), (2 ** 31 - 1, 2 ** 31 - 1, 2 ** 31 - 1)]:
+        with pytest.raises(_lib.EchoError) as e:
+            _lib.echo_init(_grid(n), flat, eos, 32, 0.4)
+        assert e.value.code == _lib.ECHO_EINVAL, n
+
+
 def test_init_rejects_bad_physics(lib):
     g = _grid()
     with pytest.raises(_lib.EchoError):
