@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
 // tile whose tensor-core result did not arrive falls back to the previous-
 // stage guess (counted in mlp_fallback).
 template <int MK, typename R>
-__global__ void __launch_bounds__(128) k_c2p_tc(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate,
+__global__ void __launch_bounds__(128, 6) k_c2p_tc(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate,
                                                 long long ntiles)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];

@@ -68,6 +68,18 @@ __device__ __forceinline__ uint32_t tc_pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+// tanh of the hidden layers: the hardware approximation (tanh.approx.f32,
+// one SFU instruction, relative error about 2^-11 by the PTX ISA) instead
+// of the accurate library tanhf (two SFU instructions and a dozen FMAs).
+// The network only supplies the Newton start; its outputs move by ~1e-3,
+// well inside the guess's own error.
+__device__ __forceinline__ float tc_tanh(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -143,7 +155,9 @@ __device__ __forceinline__ void tc_setup(TcMlp &t, unsigned char *smem, const fl
             src = MLP_OB2 + (q - TP_B2);                // b2, W3, b3 (contiguous)
         else
             src = MLP_ONORM + (q - TP_NORM);
-        Ps[q] = gP[src];
+        // the feature standard deviations are only divided by: keep 1/std
+        const bool fstd = q >= TP_NORM + MLP_NI && q < TP_NORM + 2 * MLP_NI;
+        Ps[q] = fstd ? 1.0f / gP[src] : gP[src];
     }
     // B = W2^T as a K-major operand: row n (hidden-2 unit) holds W2[n][0..63]
     for (int idx = threadIdx.x; idx < 64 * 8; idx += blockDim.x) {
@@ -191,7 +205,7 @@ __device__ __forceinline__ bool tc_tile(TcMlp &t, const float f[MLP_NI], float o
     float x[MLP_NI];
 #pragma unroll
     for (int i = 0; i < MLP_NI; ++i)
-        x[i] = (f[i] - P[TP_NORM + i]) / P[TP_NORM + MLP_NI + i];
+        x[i] = (f[i] - P[TP_NORM + i]) * P[TP_NORM + MLP_NI + i];   // (f - mean) / std
     const int r = threadIdx.x;
 #pragma unroll 1
     for (int kg = 0; kg < 8; ++kg) {
@@ -203,7 +217,7 @@ __device__ __forceinline__ bool tc_tile(TcMlp &t, const float f[MLP_NI], float o
 #pragma unroll
             for (int i = 0; i < MLP_NI; ++i)
                 s = fmaf(P[TP_W1 + j * MLP_NI + i], x[i], s);
-            h[u] = tanhf(s);
+            h[u] = tc_tanh(s);
         }
         uint4 v;
         v.x = tc_pack_bf16(h[0], h[1]);
@@ -244,7 +258,7 @@ __device__ __forceinline__ bool tc_tile(TcMlp &t, const float f[MLP_NI], float o
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
             const int n = c * 32 + u;
-            const float h2 = tanhf(__uint_as_float(v[u]) + P[TP_B2 + n]);
+            const float h2 = tc_tanh(__uint_as_float(v[u]) + P[TP_B2 + n]);
             o0 = fmaf(P[TP_W3 + n], h2, o0);
             o1 = fmaf(P[TP_W3 + MLP_NH + n], h2, o1);
             o2 = fmaf(P[TP_W3 + 2 * MLP_NH + n], h2, o2);
