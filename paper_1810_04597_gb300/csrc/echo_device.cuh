@@ -444,6 +444,26 @@ __device__ __forceinline__ T minmod4(T w, T x, T y, T z)
     return (pos || neg) ? with_sign_of(m, w) : T(0);
 }
 
+// FP32 forms from one-instruction min/max (the integer sign tests above cost
+// about a dozen integer instructions per call, and the FP32 stencil kernels
+// are bound by the integer pipe): minmod of two is the median of (a, b, 0);
+// minmod of four is max(min, 0) + min(max, 0), of which at most one term is
+// non-zero.  Both select an argument exactly; only the sign of a zero result
+// can differ from the forms above.
+template <>
+__device__ __forceinline__ float minmod2<float>(float a, float b)
+{
+    return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));
+}
+
+template <>
+__device__ __forceinline__ float minmod4<float>(float w, float x, float y, float z)
+{
+    const float lo = fminf(fminf(w, x), fminf(y, z));
+    const float hi = fmaxf(fmaxf(w, x), fmaxf(y, z));
+    return fmaxf(lo, 0.0f) + fminf(hi, 0.0f);
+}
+
 // MP5 (Suresh & Huynh 1997): the interface value between u0 = u_j and
 // up1 = u_{j+1}, biased to u_j -- the fifth-order interpolant of cell
 // averages, kept inside the monotonicity- and accuracy-preserving interval.
@@ -469,14 +489,24 @@ __device__ __forceinline__ T mp5_uor(T um2, T um1, T u0, T up1, T up2, int order
 // Accept uor if (uor - u_j)(uor - u_mp) <= eps, u_mp = u_j + minmod(u_{j+1} - u_j,
 // alpha (u_j - u_{j-1})); written with d0 = uor - u_j so that
 // uor - u_mp = d0 - minmod(...).
+// dp = u_{j+1} - u_j and dm = u_j - u_{j-1} come from the caller, which
+// shares them between the two states of a face: the right state's
+// differences are the left stencil's negated (exact in IEEE arithmetic up to
+// the sign of a zero, which minmod2 maps to 0 either way).
 template <typename T>
-__device__ __forceinline__ T mp5_try(T um2, T um1, T u0, T up1, T up2, bool &accept, int order)
+__device__ __forceinline__ T mp5_try_d(T um2, T um1, T u0, T up1, T up2, T dp, T dm, bool &accept, int order)
 {
     const T uor = mp5_uor(um2, um1, u0, up1, up2, order);
     const T d0 = uor - u0;
-    const T mm = minmod2(up1 - u0, T(MP5_ALPHA) * (u0 - um1));
+    const T mm = minmod2(dp, T(MP5_ALPHA) * dm);
     accept = ile(d0 * (d0 - mm), T(MP5_EPS));
     return uor;
+}
+
+template <typename T>
+__device__ __forceinline__ T mp5_try(T um2, T um1, T u0, T up1, T up2, bool &accept, int order)
+{
+    return mp5_try_d(um2, um1, u0, up1, up2, up1 - u0, u0 - um1, accept, order);
 }
 
 template <typename T>
@@ -765,6 +795,21 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
         const double dp = gm1g * (om - Z * dv2 + 0.5 * Dc * dv2 * isq);
         const double fp = 1.0 - dp + 0.5 * B2 * dv2 + SB2 * iZ2 * iZ;
         double dZ = nr_div(f, fp);
+        // A step within the tolerance ends the iteration: Z, 1/Z, 1/(Z + B^2)
+        // and v^2 move along their first derivatives instead of being
+        // evaluated again at Z - dZ (one division and the v^2 formula fewer);
+        // the neglected terms are of relative size (dZ/Z)^2 <= tol^2.
+        if (ile(iabs(dZ), tol * Z)) {
+            const double Zl = Z - dZ, v2l = v2 - dv2 * dZ;
+            if (is_pos(Zl) && ilt(v2l, 1.0)) {
+                iZ = fma(iZ * dZ, iZ, iZ);
+                iZB = fma(iZB * dZ, iZB, iZB);
+                Z = Zl;
+                v2 = v2l;
+                conv = true;
+                break;
+            }
+        }
         double Zn = Z - dZ, iZn = 0.0, iZBn = 0.0, v2n = 2.0;
         int h = 0;
         for (;;) {

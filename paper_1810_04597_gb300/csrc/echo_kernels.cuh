@@ -488,8 +488,9 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
             for (int s = 0; s < 6; ++s)
                 q[s] = a[id + (s - 3) * sd];
             bool okL, okR;
-            Lv[m] = mp5_try(q[0], q[1], q[2], q[3], q[4], okL, order);
-            Rv[m] = mp5_try(q[5], q[4], q[3], q[2], q[1], okR, order);
+            const T d1 = q[2] - q[1], d2 = q[3] - q[2], d3 = q[4] - q[3];
+            Lv[m] = mp5_try_d(q[0], q[1], q[2], q[3], q[4], d2, d1, okL, order);
+            Rv[m] = mp5_try_d(q[5], q[4], q[3], q[2], q[1], -d2, -d3, okR, order);
             pend |= (okL ? 0u : 1u) << (2 * m);
             pend |= (okR ? 0u : 1u) << (2 * m + 1);
         }
@@ -686,8 +687,9 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
             for (int s = 0; s < 6; ++s)
                 q[s] = S.p[m][id + (s - 3) * S.st[m]];
             bool okL, okR;
-            Lv[m] = mp5_try(q[0], q[1], q[2], q[3], q[4], okL, order);
-            Rv[m] = mp5_try(q[5], q[4], q[3], q[2], q[1], okR, order);
+            const T d1 = q[2] - q[1], d2 = q[3] - q[2], d3 = q[4] - q[3];
+            Lv[m] = mp5_try_d(q[0], q[1], q[2], q[3], q[4], d2, d1, okL, order);
+            Rv[m] = mp5_try_d(q[5], q[4], q[3], q[2], q[1], -d2, -d3, okR, order);
             pend |= (okL ? 0u : 1u) << (2 * m);
             pend |= (okR ? 0u : 1u) << (2 * m + 1);
         }
