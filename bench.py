@@ -574,6 +574,7 @@ def run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms64):
     t0 = time.perf_counter()
     state, losses, _, (Xte, Yte) = mlp.default_network(device=str(dev), torus=True)
     err = mlp.guess_error(state, Xte, Yte).cpu().numpy()
+    err_tc = mlp.guess_error(state, Xte, Yte, tensor_cores=True).cpu().numpy()
     t_train = time.perf_counter() - t0
     s = Solver(prob, precision=32, device=str(dev))
     s.set_prims()
@@ -605,6 +606,8 @@ def run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms64):
            "mlp_fallback_per_call": (c1["mlp_fallback"] - c0["mlp_fallback"]) / calls,
            "guess_rel_err_median_heldout": float(np.median(err)),
            "guess_rel_err_p99_heldout": float(np.quantile(err, 0.99)),
+           "guess_rel_err_median_heldout_tensor_cores": float(np.median(err_tc)),
+           "guess_rel_err_p99_heldout_tensor_cores": float(np.quantile(err_tc, 0.99)),
            "train_seconds": t_train, "train_final_loss": float(losses[-50:].mean().item()),
            "c2p_guess": "network (trained on the GPU, untimed) refined by FP32 Newton steps; FP64 Newton judges",
            "note": "FP32 bulk"}

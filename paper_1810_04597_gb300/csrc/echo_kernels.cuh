@@ -443,17 +443,6 @@ __device__ __forceinline__ void compact_limit(unsigned pend, int id, LimScratch<
 // it would run for the whole warp at every one of the 14 calls.  Instead
 // all unlimited values are computed first, a bitmask records the rejected
 // ones, and compact_limit evaluates them packed 32 per warp round.
-template <typename R>
-__device__ __forceinline__ const R *pick7(const Arrays<R> &A, const int qs[7], int m)
-{
-    const R *p = A.P[qs[0]];
-#pragma unroll
-    for (int u = 1; u < 7; ++u)
-        if (m == u)
-            p = A.P[qs[u]];
-    return p;
-}
-
 template <int D, int MK, typename R>
 __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const Arrays<R> &A, long long t,
                                            LimScratch<R> &lsm)
@@ -497,7 +486,7 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     }
     // limiter on the rejected items, compacted across the warp
     compact_limit<T>(pend, id, lsm, [&](int ido, int m, int side) -> T {
-        const R *__restrict__ a = pick7(A, qs, m);
+        const R *__restrict__ a = A.P[qs[m]];
         T q[6];
 #pragma unroll
         for (int s = 0; s < 6; ++s)

@@ -3,19 +3,25 @@
 // each own one row (one cell or one feature row).
 //
 // Per tile of 128 rows:
-//   1. every thread standardises its 9 features and evaluates layer 1
-//      (9 -> 64, tanh) in FP32, and writes h1 as BF16 into row `threadIdx.x`
-//      of the A operand in shared memory;
-//   2. one thread issues four tcgen05.mma (M = 128, N = 64, K = 16 each,
-//      BF16 inputs, FP32 accumulation) of A (128 x 64) by W2^T (64 x 64) into
-//      64 TMEM columns, and commits them to an mbarrier;
+//   1. every thread standardises its 9 features in FP32 and writes them as
+//      BF16 (K padded to 16 with zeros) into row `threadIdx.x` of the layer-1
+//      A operand in shared memory;
+//   2. one thread issues one tcgen05.mma (M = 128, N = 64, K = 16, BF16
+//      inputs, FP32 accumulation) of X (128 x 16) by W1^T (16 x 64) into 64
+//      TMEM columns and commits it to an mbarrier;
 //   3. every thread waits for the mbarrier (bounded), reads its own TMEM lane
 //      (row = thread: warp w owns lanes 32w..32w+31) with tcgen05.ld, adds
-//      b2, applies tanh and evaluates layer 3 (64 -> 3) in FP32.
+//      b1, applies tanh and writes h1 as BF16 into its row of the layer-2 A
+//      operand;
+//   4. one thread issues four tcgen05.mma (K = 16 each) of H1 (128 x 64) by
+//      W2^T (64 x 64) into the same TMEM columns and commits them;
+//   5. every thread waits, reads its lane, adds b2, applies tanh and
+//      evaluates layer 3 (64 -> 3) in FP32.
 // Operands use the no-swizzle K-major layout: 8 x 8 BF16 core matrices of
 // 128 contiguous bytes, core matrix (row group, k group) at
-// (row_group * 8 + k_group) * 128 bytes, so the leading-dimension (K) byte
-// offset is 128 and the stride (M/N) byte offset is 1024.
+// (row_group * KG + k_group) * 128 bytes with KG = K / 8, so the
+// leading-dimension (K) byte offset is 128 and the stride (M/N) byte offset
+// is KG * 128 (1024 for the 64-wide operands, 256 for the 16-wide ones).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -27,14 +33,16 @@
 
 namespace echo {
 
-// FP32 parameters the CUDA cores need, packed (W2 lives only as BF16):
-// W1 (64x9), b1 (64), b2 (64), W3 (3x64), b3 (3), feature mean/std (9+9),
-// target mean/std (3+3).
-constexpr int TP_W1 = 0, TP_B1 = TP_W1 + MLP_NH * MLP_NI, TP_B2 = TP_B1 + MLP_NH, TP_W3 = TP_B2 + MLP_NH,
+// FP32 parameters the CUDA cores need, packed (W1 and W2 live only as BF16):
+// b1 (64), b2 (64), W3 (3x64), b3 (3), feature mean/std (9+9), target
+// mean/std (3+3).
+constexpr int TP_B1 = 0, TP_B2 = TP_B1 + MLP_NH, TP_W3 = TP_B2 + MLP_NH,
               TP_B3 = TP_W3 + MLP_NO * MLP_NH, TP_NORM = TP_B3 + MLP_NO, TP_COUNT = TP_NORM + MLP_NNORM;
-constexpr int TC_A_BYTES = 128 * 64 * 2;            // h1 of 128 rows, BF16
-constexpr int TC_B_BYTES = 64 * 64 * 2;             // W2, BF16
-constexpr int TC_P_OFF = TC_A_BYTES + TC_B_BYTES;   // packed FP32 parameters
+constexpr int TC_A_BYTES = 128 * 64 * 2;            // h1 of 128 rows, BF16 (layer-2 A)
+constexpr int TC_B_BYTES = 64 * 64 * 2;             // W2, BF16 (layer-2 B)
+constexpr int TC_X_OFF = TC_A_BYTES + TC_B_BYTES;   // features of 128 rows, BF16, K = 16 (layer-1 A)
+constexpr int TC_W1_OFF = TC_X_OFF + 128 * 16 * 2;  // W1, BF16, K = 16 (layer-1 B)
+constexpr int TC_P_OFF = TC_W1_OFF + 64 * 16 * 2;   // packed FP32 parameters
 constexpr int TC_BAR_OFF = TC_P_OFF + ((TP_COUNT * 4 + 15) / 16) * 16;
 constexpr int TC_SMEM = TC_BAR_OFF + 16;            // + mbarrier (8 B) + TMEM address slot
 constexpr uint32_t TC_TMEM_COLS = 64;
@@ -53,12 +61,18 @@ __device__ __forceinline__ int tc_off(int r, int k)
     return ((r >> 3) * 8 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
+// The same for a 16-column operand (two core matrices per row group).
+__device__ __forceinline__ int tc_off16(int r, int k)
+{
+    return ((r >> 3) * 2 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
 // Shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading
 // byte offset >> 4 (bits 16-29), stride byte offset >> 4 (bits 32-45), the
 // fixed version field 1 (bits 46-47), base offset 0, no swizzle (bits 61-63 = 0).
-__device__ __forceinline__ uint64_t tc_desc(uint32_t addr)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t sbo = 1024)
 {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32)
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32)
            | (1ull << 46);
 }
 
@@ -135,14 +149,14 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32])
 }
 
 struct TcMlp {
-    unsigned char *base;   // A operand at offset 0, B at TC_A_BYTES
+    unsigned char *base;   // layer-2 A operand at offset 0, B at TC_A_BYTES, layer-1 A and B at TC_X_OFF, TC_W1_OFF
     const float *P;        // packed FP32 parameters (TP_*) in shared memory
-    uint32_t a_addr, b_addr, bar, tmem, phase;
+    uint32_t a_addr, b_addr, x_addr, w1_addr, bar, tmem, phase;
     bool ok;               // false after a wait gave up: no further MMA is issued
     bool pending;          // a commit that never arrived (waited for again at teardown)
 };
 
-// Copy the parameters, build W2 as the BF16 B operand, initialise the
+// Copy the parameters, build W1 and W2 as BF16 B operands, initialise the
 // mbarrier and allocate the TMEM columns.  All threads of the CTA call it.
 __device__ __forceinline__ void tc_setup(TcMlp &t, unsigned char *smem, const float *__restrict__ gP)
 {
@@ -150,7 +164,7 @@ __device__ __forceinline__ void tc_setup(TcMlp &t, unsigned char *smem, const fl
     for (int q = threadIdx.x; q < TP_COUNT; q += blockDim.x) {
         int src;
         if (q < TP_B2)
-            src = MLP_OW1 + q;                          // W1, b1 (contiguous in the block)
+            src = MLP_OB1 + q;                          // b1
         else if (q < TP_NORM)
             src = MLP_OB2 + (q - TP_B2);                // b2, W3, b3 (contiguous)
         else
@@ -169,6 +183,22 @@ __device__ __forceinline__ void tc_setup(TcMlp &t, unsigned char *smem, const fl
         v.z = tc_pack_bf16(w[4], w[5]);
         v.w = tc_pack_bf16(w[6], w[7]);
         *reinterpret_cast<uint4 *>(smem + TC_A_BYTES + tc_off(n, kg * 8)) = v;
+    }
+    // layer-1 B = W1^T, K-major: row n holds W1[n][0..8], zeros up to K = 16
+    for (int idx = threadIdx.x; idx < 64 * 2; idx += blockDim.x) {
+        const int n = idx >> 1, kg = idx & 1;
+        float w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = kg * 8 + u;
+            w[u] = k < MLP_NI ? gP[MLP_OW1 + n * MLP_NI + k] : 0.0f;
+        }
+        uint4 v;
+        v.x = tc_pack_bf16(w[0], w[1]);
+        v.y = tc_pack_bf16(w[2], w[3]);
+        v.z = tc_pack_bf16(w[4], w[5]);
+        v.w = tc_pack_bf16(w[6], w[7]);
+        *reinterpret_cast<uint4 *>(smem + TC_W1_OFF + tc_off16(n, kg * 8)) = v;
     }
     uint32_t *slot = reinterpret_cast<uint32_t *>(smem + TC_BAR_OFF + 8);
     t.bar = tc_smem_addr(smem + TC_BAR_OFF);
@@ -191,50 +221,27 @@ __device__ __forceinline__ void tc_setup(TcMlp &t, unsigned char *smem, const fl
     t.P = Ps;
     t.a_addr = tc_smem_addr(smem);
     t.b_addr = tc_smem_addr(smem + TC_A_BYTES);
+    t.x_addr = tc_smem_addr(smem + TC_X_OFF);
+    t.w1_addr = tc_smem_addr(smem + TC_W1_OFF);
     t.phase = 0;
     t.ok = true;
     t.pending = false;
 }
 
-// One tile: every thread of the CTA passes its 9 features and receives the
-// de-standardised outputs (log W, log(p/D), log10 guess error).  Returns
-// false (the same on every thread) if the tensor-core result did not arrive.
-__device__ __forceinline__ bool tc_tile(TcMlp &t, const float f[MLP_NI], float out[MLP_NO])
+// One round of MMAs: make the CTA's operand writes visible to the tensor
+// core, let thread 0 issue `issue()` and commit it, and wait (bounded) for
+// the commit.  Returns false on every thread if the result did not arrive
+// (then no further MMA is issued and the commit is waited for again at
+// teardown).
+template <typename Issue>
+__device__ __forceinline__ bool tc_round(TcMlp &t, Issue issue)
 {
-    const float *__restrict__ P = t.P;
-    float x[MLP_NI];
-#pragma unroll
-    for (int i = 0; i < MLP_NI; ++i)
-        x[i] = (f[i] - P[TP_NORM + i]) * P[TP_NORM + MLP_NI + i];   // (f - mean) / std
-    const int r = threadIdx.x;
-#pragma unroll 1
-    for (int kg = 0; kg < 8; ++kg) {
-        float h[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int j = kg * 8 + u;
-            float s = P[TP_B1 + j];
-#pragma unroll
-            for (int i = 0; i < MLP_NI; ++i)
-                s = fmaf(P[TP_W1 + j * MLP_NI + i], x[i], s);
-            h[u] = tc_tanh(s);
-        }
-        uint4 v;
-        v.x = tc_pack_bf16(h[0], h[1]);
-        v.y = tc_pack_bf16(h[2], h[3]);
-        v.z = tc_pack_bf16(h[4], h[5]);
-        v.w = tc_pack_bf16(h[6], h[7]);
-        *reinterpret_cast<uint4 *>(t.base + tc_off(r, kg * 8)) = v;
-    }
-    // make the generic-proxy writes of A visible to the tensor core
     tc_fence_async_smem();
     tc_fence_before();
     __syncthreads();
     if (threadIdx.x == 0 && t.ok) {
         tc_fence_after();
-#pragma unroll
-        for (int kb = 0; kb < 4; ++kb)
-            tc_mma(t.tmem, tc_desc(t.a_addr + kb * 256), tc_desc(t.b_addr + kb * 256), kb > 0 ? 1u : 0u);
+        issue();
         tc_commit(t.bar);
     }
     bool got = false;
@@ -249,7 +256,63 @@ __device__ __forceinline__ bool tc_tile(TcMlp &t, const float f[MLP_NI], float o
     }
     t.phase ^= 1u;
     tc_fence_after();
+    return true;
+}
+
+// One tile: every thread of the CTA passes its 9 features and receives the
+// de-standardised outputs (log W, log(p/D), log10 guess error).  Returns
+// false (the same on every thread) if a tensor-core result did not arrive.
+__device__ __forceinline__ bool tc_tile(TcMlp &t, const float f[MLP_NI], float out[MLP_NO])
+{
+    const float *__restrict__ P = t.P;
+    const int r = threadIdx.x;
+    {
+        float x[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            x[i] = i < MLP_NI ? (f[i] - P[TP_NORM + i]) * P[TP_NORM + MLP_NI + i] : 0.0f;   // (f - mean) / std
+#pragma unroll
+        for (int kg = 0; kg < 2; ++kg) {
+            uint4 v;
+            v.x = tc_pack_bf16(x[kg * 8 + 0], x[kg * 8 + 1]);
+            v.y = tc_pack_bf16(x[kg * 8 + 2], x[kg * 8 + 3]);
+            v.z = tc_pack_bf16(x[kg * 8 + 4], x[kg * 8 + 5]);
+            v.w = tc_pack_bf16(x[kg * 8 + 6], x[kg * 8 + 7]);
+            *reinterpret_cast<uint4 *>(t.base + TC_X_OFF + tc_off16(r, kg * 8)) = v;
+        }
+    }
+    // layer 1: X (128 x 16) W1^T -> TMEM
+    if (!tc_round(t, [&] { tc_mma(t.tmem, tc_desc(t.x_addr, 256), tc_desc(t.w1_addr, 256), 0u); }))
+        return false;
     const uint32_t lane = t.tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+        uint32_t v[32];
+        tc_ld32(lane + (uint32_t)(c * 32), v);
+#pragma unroll
+        for (int kg = 0; kg < 4; ++kg) {
+            float h[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int n = c * 32 + kg * 8 + u;
+                h[u] = tc_tanh(__uint_as_float(v[kg * 8 + u]) + P[TP_B1 + n]);
+            }
+            uint4 w;
+            w.x = tc_pack_bf16(h[0], h[1]);
+            w.y = tc_pack_bf16(h[2], h[3]);
+            w.z = tc_pack_bf16(h[4], h[5]);
+            w.w = tc_pack_bf16(h[6], h[7]);
+            *reinterpret_cast<uint4 *>(t.base + tc_off(r, c * 32 + kg * 8)) = w;
+        }
+    }
+    // layer 2: H1 (128 x 64) W2^T -> the same TMEM columns (every lane's
+    // tcgen05.ld above completed before the barrier in tc_round)
+    if (!tc_round(t, [&] {
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb)
+                tc_mma(t.tmem, tc_desc(t.a_addr + kb * 256), tc_desc(t.b_addr + kb * 256), kb > 0 ? 1u : 0u);
+        }))
+        return false;
     float o0 = P[TP_B3], o1 = P[TP_B3 + 1], o2 = P[TP_B3 + 2];
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {

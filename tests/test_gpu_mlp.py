@@ -106,6 +106,10 @@ def test_training_reduces_loss_and_error(trained, torch):
     assert L[-50:].mean() < 0.05 * L[:20].mean(), (L[:20].mean(), L[-50:].mean())
     err = mlp.guess_error(state, Xte, Yte).cpu().numpy()
     assert np.median(err) < 1e-2, np.median(err)
+    # the tensor-core forward c2p uses (BF16 operands, hardware tanh)
+    err_tc = mlp.guess_error(state, Xte, Yte, tensor_cores=True).cpu().numpy()
+    print("held-out guess error, median: FP32", np.median(err), "tensor cores", np.median(err_tc))
+    assert np.median(err_tc) < 1.5e-2, np.median(err_tc)
 
 
 def test_network_guess_gives_the_same_inversion(trained, torch):
@@ -173,21 +177,23 @@ def _bf16(a):
 
 def _forward_bf16_hidden(st, x):
     """FP64 forward pass with the tensor-core operands rounded as the GPU
-    rounds them: h1 (from FP32) and W2 to BF16; raw outputs."""
+    rounds them: the standardised features (FP32, times 1/std in FP32), W1,
+    h1 (from FP32) and W2 to BF16; raw outputs."""
     P = st.astype(np.float64)
     mu, sd = P[4995:5004], P[5004:5013]
     W1, b1 = P[0:576].reshape(64, 9), P[576:640]
     W2, b2 = P[640:4736].reshape(64, 64), P[4736:4800]
     W3, b3 = P[4800:4992].reshape(3, 64), P[4992:4995]
-    xs = (x.astype(np.float64) - mu) / sd
-    h1 = _bf16(np.tanh(xs @ W1.T + b1).astype(np.float32))
+    isd = (np.float32(1.0) / sd.astype(np.float32)).astype(np.float32)
+    xs = _bf16((x.astype(np.float32) - mu.astype(np.float32)) * isd)
+    h1 = _bf16(np.tanh(xs @ _bf16(W1.astype(np.float32)).T + b1).astype(np.float32))
     h2 = np.tanh(h1 @ _bf16(W2.astype(np.float32)).T + b2)
     return h2 @ W3.T + b3
 
 
 def test_tensor_core_forward(orc, torch):
-    """The hidden layer on the tensor cores (tcgen05, BF16 operands, FP32
-    accumulation) matches the FP64 forward pass with the same BF16 roundings
+    """Both hidden layers on the tensor cores (tcgen05, BF16 operands, FP32
+    accumulation) match the FP64 forward pass with the same BF16 roundings
     to the accuracy of the hardware tanh; ragged last tile included."""
     from paper_1810_04597_gb300 import _lib
     rng = np.random.default_rng(3)
