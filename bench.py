@@ -58,23 +58,23 @@ KMODEL = {
 FLOPS64 = {
     64: {"faces_x": 549.0, "faces_y": 549.0, "faces_z": 549.0,
          "emf_x": 299.2, "emf_y": 299.2, "emf_z": 299.2,
-         "c2p": 432.5, "update": 79.0},
+         "c2p": 420.5, "update": 79.0},
     # FP32-bulk path: only c2p computes in FP64 (previous-stage Z refined in
     # FP32, then 1.01 FP64 Newton iterations per call)
-    32: {"c2p": 159.0},
+    32: {"c2p": 145.0},
 }
 # FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 DFMA lanes
 # per SM and clock x 2 flop x 2.07 GHz (the 1.25 TFLOP/s nominal figure).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per face of faces_x (dram__bytes_read.sum + dram__bytes_write.sum
-# of the same 128^3 ncu launch: 317,747,712 B over 2,316,324 faces); scaled to a
+# of the same 128^3 ncu launch: 336,887,040 B over 2,316,324 faces); scaled to a
 # launch by the faces it processes.
-TRAFFIC_PER_FACE64 = 317747712 / 2316324
+TRAFFIC_PER_FACE64 = 336887040 / 2316324
 # FP64 pipe activity in those captures
 # (sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active).
-FP64_PIPE_BUSY = {64: {"faces_x": 0.861, "faces_y": 0.861, "faces_z": 0.861, "emf_x": 0.852, "emf_y": 0.852,
-                       "emf_z": 0.852, "c2p": 0.863, "update": 0.834},
-                  32: {"c2p": 0.855}}
+FP64_PIPE_BUSY = {64: {"faces_x": 0.862, "faces_y": 0.862, "faces_z": 0.862, "emf_x": 0.854, "emf_y": 0.854,
+                       "emf_z": 0.854, "c2p": 0.862, "update": 0.834},
+                  32: {"c2p": 0.854}}
 
 
 def kernel_units(name, n):
