@@ -346,8 +346,11 @@ def run_ours(args, world, rank, local, dist):
     totals = s.reduce()
     fin64 = s.get_state() if (args.precision == 64 and not args.no_variants) else None
 
-    # kernels launched in the timed region (a fill call launches 3 kernels)
+    # kernels launched in the timed region (a fill call launches 3 kernels; a
+    # c2p with the network guess in its own pass 2)
     per_call = {"fill_faces": 3, "fill_prims": 3}
+    if (guess & 3) == 1 and not (guess & 24):
+        per_call["c2p"] = 2
     launches = int(sum(cnt * per_call.get(k, 1) for k, (_, cnt) in prof.items()))
 
     # ---- roofline of the dominant kernel (live CUDA-event times)
@@ -452,6 +455,7 @@ def run_ours(args, world, rank, local, dist):
         if not args.no_mlp:
             variants["fp32_mlp"], mlp_state = run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds,
                                                               ms)
+            variants["c2p_guess_gain"] = run_guess_gain(prob, dev, mlp_state)
         if not args.no_sweep:
             variants["sweep_batch"] = run_sweep_variant(args, dev, world, dist, mlp_state)
         if not args.no_512 and mlp_state is not None:
@@ -615,6 +619,58 @@ def run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms64):
     return out, state
 
 
+def run_guess_gain(prob, dev, mlp_state, warm=2, steps=3):
+    """What the network guess gains: the workload's c2p with the previous-
+    stage Z, the network (tensor cores) and the cold guess as start, in FP64
+    (plain Newton from the guess) and in the FP32-bulk form (guess refined in
+    FP32, one FP64 judging step): c2p kernel time per call (the library's
+    per-kernel CUDA events), mean and 99th-percentile Newton iterations per
+    inversion (from the iteration histogram), network restarts.  Each guess
+    runs `steps` steps from the same state (`warm` steps with the previous-Z
+    guess first)."""
+    import numpy as np
+    import torch
+    from paper_1810_04597_gb300.echo import Solver
+    out = {}
+    for prec, modes in ((64, {"previous": 0, "network": 1, "network_inside_c2p": 17, "cold": 2}),
+                        (32, {"previous": 4, "network": 5, "network_inside_c2p": 21, "cold": 6})):
+        res = {}
+        for name, mode in modes.items():
+            s = Solver(prob, precision=prec, device=str(dev))
+            s.set_prims()
+            s.mlp_load(mlp_state)
+            if prec == 32:
+                s.set_c2p_guess(4)
+            for _ in range(warm):
+                s.step()
+            s.set_c2p_guess(mode)
+            torch.cuda.synchronize()
+            c0 = s.counters()
+            s.profile(True)
+            s.profile_read()
+            for _ in range(steps):
+                s.step()
+            prof = s.profile_read()
+            s.profile(False)
+            c1 = s.counters()
+            calls = max(c1["c2p_calls"] - c0["c2p_calls"], 1)
+            h = np.array(c1["c2p_iter_hist"]) - np.array(c0["c2p_iter_hist"])
+            cum = np.cumsum(h) / max(int(h.sum()), 1)
+            ms, nl = prof["c2p"]
+            res[name] = {"c2p_ms_per_call": ms / max(nl, 1),
+                         "mean_newton_iters": (c1["c2p_iters"] - c0["c2p_iters"]) / calls,
+                         "p99_newton_iters": int(np.searchsorted(cum, 0.99)),
+                         "mlp_fallback_per_call": (c1["mlp_fallback"] - c0["mlp_fallback"]) / calls}
+            del s
+        out[f"fp{prec}"] = res
+    out["note"] = ("c2p on the workload from each start: FP64 plain Newton, FP32 bulk with FP32 refinement and "
+                   "one FP64 judging step; iterations are FP64 Newton iterations (network attempt and restart "
+                   "together); the previous-stage Z is the plain method's guess; network: tensor-core pass "
+                   "writing the starts, then the c2p kernel; network_inside_c2p: the same network fused into "
+                   "the c2p kernel")
+    return out
+
+
 def run_box512_variant(args, dev, world, dist, mlp_state):
     """The 512^3 periodic box of the parity recipe (smooth_box): FP64 and FP32
     bulk + network c2p guess (tensor cores) on the same input, W + K steps
@@ -762,7 +818,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-512", action="store_true", help="skip the 512^3 FP64 / FP32 + network variant")
-    ap.add_argument("--guess", type=int, default=None, choices=(0, 1, 4, 5, 9, 13),
+    ap.add_argument("--guess", type=int, default=None, choices=(0, 1, 2, 4, 5, 6, 9, 13, 17, 21),
                     help="c2p guess mode of the main line (default: 0 for FP64, 4 for FP32)")
     args = ap.parse_args()
     world, rank, local = dist_info()

@@ -68,6 +68,9 @@ extern "C" {
 #define ECHO_METRIC_FLAT 0
 #define ECHO_METRIC_KERR_SCHILD 1 /* coordinates (ln r, theta, phi), M = 1 */
 
+/* buckets of the Newton-iteration histogram in echo_totals */
+#define ECHO_C2P_HIST 16
+
 typedef struct echo_ctx echo_ctx; /* opaque, library-owned host object */
 
 typedef struct {
@@ -100,6 +103,10 @@ typedef struct {
     long long floor_hits; /* cells reset by floors since bind */
     long long fallback_faces; /* reserved (first-order face fallbacks) */
     long long mlp_fallback;   /* network guesses that needed the previous-Z restart */
+    /* cell inversions since bind by their Newton iterations: [k] took k
+     * iterations (network attempt and restart together), [ECHO_C2P_HIST - 1]
+     * that many or more; the entries sum to c2p_calls */
+    long long c2p_iter_hist[ECHO_C2P_HIST];
 } echo_totals;
 
 /* Create a context.  precision: 64 (FP64 everywhere) or 32 (FP32 storage
@@ -165,9 +172,12 @@ int echo_get_z(echo_ctx *ctx, double *Z, int on_device);
 /* Conservative-to-primitive inversion of the current state on every owned
  * cell.  guess_mode: 0 = the stored Z of the cell (previous stage), 1 = the
  * c2p-guess network (see below), 2 = cold guess (Z = 0, replaced by the
- * admissibility rule); adding 4 refines the guess in FP32 first; adding 8 to
- * mode 1 or 5 runs the network on the CUDA cores instead of the tensor
- * cores.  Other values: ECHO_EINVAL.  If stats is non-NULL
+ * admissibility rule); adding 4 refines the guess in FP32 first.  The
+ * network (modes 1, 5) runs on the tensor cores in a pass of its own that
+ * writes every cell's Newton start, followed by the plain c2p kernel; adding
+ * 8 runs it in FP32 on the CUDA cores inside the c2p kernel instead, adding
+ * 16 on the tensor cores inside the c2p kernel (the same starts, so the
+ * same result as modes 1, 5).  Other values: ECHO_EINVAL.  If stats is non-NULL
  * the call synchronises and fills the counters and dt_cfl of stats (the
  * other fields are left untouched) and returns ECHO_EC2P if any cell failed. */
 int echo_c2p(echo_ctx *ctx, int guess_mode, echo_totals *stats);
@@ -250,12 +260,15 @@ int echo_mlp_dataset(echo_ctx *ctx, float *X, float *Y, long long capacity, long
 int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
 
 /* Newton guess used by echo_step/echo_rhs: 0 previous-stage Z (default),
- * 1 network (requires echo_mlp_load); adding 4 first refines that guess by
- * up to four Newton steps of the same residual in FP32 (the FP64 iterations
- * that follow still decide convergence).  The network's hidden layer runs on
- * the tensor cores (as echo_mlp_forward_tc); adding 8 to a network mode
- * evaluates it in FP32 on the CUDA cores instead (modes 9, 13).  Accepted:
- * 0, 1, 4, 5, 9, 13; echo_c2p also takes 2 (cold guess) and 6. */
+ * 1 network (requires echo_mlp_load), 2 cold (the guess of echo_c2p mode 2,
+ * for measuring what the other guesses gain); adding 4 first refines that
+ * guess by up to four Newton steps of the same residual in FP32 (the FP64
+ * iterations that follow still decide convergence).  The network's hidden
+ * layers run on the tensor cores (as echo_mlp_forward_tc) in a pass before
+ * the c2p kernel; adding 8 to a network mode evaluates it in FP32 on the
+ * CUDA cores inside the c2p kernel (modes 9, 13), adding 16 on the tensor
+ * cores inside the c2p kernel (modes 17, 21).  Accepted: 0, 1, 2, 4, 5, 6,
+ * 9, 13, 17, 21. */
 int echo_set_c2p_guess(echo_ctx *ctx, int mode);
 
 /* Copy the cumulative counters (c2p_iters, c2p_calls, c2p_fail, floor_hits,

@@ -28,6 +28,7 @@ ECHO_ETIMEOUT = -5
 ECHO_ESTATE = -6
 ECHO_ERANGE = -7
 ECHO_STATIC_MAX_ROWS = 65536
+ECHO_C2P_HIST = 16
 _NAMES = {0: "ECHO_OK", -1: "ECHO_EINVAL", -2: "ECHO_ECUDA", -3: "ECHO_ENOMEM", -4: "ECHO_EC2P",
           -5: "ECHO_ETIMEOUT", -6: "ECHO_ESTATE", -7: "ECHO_ERANGE"}
 
@@ -61,13 +62,15 @@ class echo_totals(ctypes.Structure):
                 ("mom", ctypes.c_double * 3), ("max_divb", ctypes.c_double),
                 ("c2p_iters", ctypes.c_longlong), ("c2p_calls", ctypes.c_longlong),
                 ("c2p_fail", ctypes.c_longlong), ("floor_hits", ctypes.c_longlong),
-                ("fallback_faces", ctypes.c_longlong), ("mlp_fallback", ctypes.c_longlong)]
+                ("fallback_faces", ctypes.c_longlong), ("mlp_fallback", ctypes.c_longlong),
+                ("c2p_iter_hist", ctypes.c_longlong * ECHO_C2P_HIST)]
 
     def as_dict(self):
         return dict(dt_cfl=self.dt_cfl, mass=self.mass, energy=self.energy, mom=list(self.mom),
                     max_divb=self.max_divb, c2p_iters=self.c2p_iters, c2p_calls=self.c2p_calls,
                     c2p_fail=self.c2p_fail, floor_hits=self.floor_hits,
-                    fallback_faces=self.fallback_faces, mlp_fallback=self.mlp_fallback)
+                    fallback_faces=self.fallback_faces, mlp_fallback=self.mlp_fallback,
+                    c2p_iter_hist=list(self.c2p_iter_hist))
 
 
 # Exported entry points and their C signatures.

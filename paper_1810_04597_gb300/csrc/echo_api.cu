@@ -76,6 +76,7 @@ size_t layout(echo_ctx *c, char *base, Arrays<R> *A)
             A->Ec[d][w] = c->geo.order ? arr() : nullptr;
     }
     A->Z = reinterpret_cast<double *>(take(cells * sizeof(double)));
+    A->zg = reinterpret_cast<float *>(take(cells * sizeof(float)));
     A->mlp = reinterpret_cast<const float *>(take(MLP_BLOCK * sizeof(float)));
     A->met = MetTables{};
     A->met.np0 = c->geo.np[0];
@@ -230,6 +231,22 @@ int read_scalars(echo_ctx *c, DevScalars *hs)
         return cuda_check(c, "synchronize");
     return ECHO_OK;
 }
+
+// Guess modes: 0 previous Z, 1 network, 2 cold; +4 FP32 refinement; for the
+// network +8 (FP32 on the CUDA cores) or +16 (tensor cores inside the c2p
+// kernel) -- not both.
+bool valid_guess(int mode)
+{
+    if (mode < 0 || mode > 31 || (mode & 3) == 3)
+        return false;
+    if ((mode & 24) && (mode & 3) != 1)
+        return false;
+    return (mode & 24) != 24;
+}
+
+const char *const kGuessModes =
+    "guess mode: 0 previous Z, 1 network, 2 cold; +4 FP32 refinement; for the network +8 on the CUDA cores or +16 "
+    "inside the c2p kernel";
 
 int require_bound(echo_ctx *c, bool need_state)
 {
@@ -566,9 +583,8 @@ int echo_c2p(echo_ctx *c, int guess_mode, echo_totals *stats)
     int rc = require_bound(c, true);
     if (rc)
         return rc;
-    if (guess_mode < 0 || guess_mode > 13 || (guess_mode & 3) == 3 || ((guess_mode & 8) && (guess_mode & 3) != 1))
-        return fail(c, ECHO_EINVAL,
-                    "guess_mode: 0 previous Z, 1 network, 2 cold, +4 FP32 refinement, +8 network on the CUDA cores");
+    if (!valid_guess(guess_mode))
+        return fail(c, ECHO_EINVAL, kGuessModes);
     if ((guess_mode & 3) == 1 && !c->mlp_loaded)
         return fail(c, ECHO_ESTATE, "no c2p-guess network loaded: call echo_mlp_load first");
     rc = ECHO_DISPATCH(c, op_c2p, guess_mode);
@@ -584,6 +600,8 @@ int echo_c2p(echo_ctx *c, int guess_mode, echo_totals *stats)
     stats->c2p_fail = (long long)hs.c2p_fail;
     stats->floor_hits = (long long)hs.floor_hits;
     stats->mlp_fallback = (long long)hs.mlp_fallback;
+    for (int k = 0; k < ECHO_C2P_HIST; ++k)
+        stats->c2p_iter_hist[k] = (long long)hs.c2p_hist[k];
     if (hs.fail_since_check) {
         DevScalars *ds = c->precision == 64 ? c->ad.scal : c->af.scal;
         cudaMemsetAsync(&ds->fail_since_check, 0, sizeof(unsigned long long), c->stream);
@@ -667,6 +685,8 @@ int echo_reduce(echo_ctx *c, echo_totals *out)
     out->floor_hits = (long long)hs.floor_hits;
     out->fallback_faces = 0;
     out->mlp_fallback = (long long)hs.mlp_fallback;
+    for (int k = 0; k < ECHO_C2P_HIST; ++k)
+        out->c2p_iter_hist[k] = (long long)hs.c2p_hist[k];
     if (hs.fail_since_check) {
         DevScalars *ds = c->precision == 64 ? c->ad.scal : c->af.scal;
         cudaMemsetAsync(&ds->fail_since_check, 0, sizeof(unsigned long long), c->stream);
@@ -692,6 +712,8 @@ int echo_counters(echo_ctx *c, echo_totals *out)
     out->c2p_fail = (long long)hs.c2p_fail;
     out->floor_hits = (long long)hs.floor_hits;
     out->mlp_fallback = (long long)hs.mlp_fallback;
+    for (int k = 0; k < ECHO_C2P_HIST; ++k)
+        out->c2p_iter_hist[k] = (long long)hs.c2p_hist[k];
     return ECHO_OK;
 }
 
@@ -714,9 +736,8 @@ int echo_set_c2p_guess(echo_ctx *c, int mode)
 {
     if (!c)
         return ECHO_EINVAL;
-    if (mode != 0 && mode != 1 && mode != 4 && mode != 5 && mode != 9 && mode != 13)
-        return fail(c, ECHO_EINVAL,
-                    "c2p guess mode: 0 previous Z, 1 network, +4 FP32 refinement, +8 network on the CUDA cores");
+    if (!valid_guess(mode))
+        return fail(c, ECHO_EINVAL, kGuessModes);
     if ((mode & 3) == 1 && !c->mlp_loaded)
         return fail(c, ECHO_ESTATE, "no c2p-guess network loaded: call echo_mlp_load first");
     c->c2p_guess = mode;

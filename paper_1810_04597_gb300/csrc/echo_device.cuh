@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "echo.h"   // ECHO_C2P_HIST, the boundary's constants
+
 namespace echo {
 
 constexpr int NG = 5;              // ghost layers: MP5 needs 3 cells per side, the
@@ -145,6 +147,7 @@ struct DevScalars {
     unsigned long long fail_since_check;
     unsigned long long mlp_fallback;
     double totals[8];            // mass, energy, mom x3, max divB, rate, spare
+    unsigned long long c2p_hist[ECHO_C2P_HIST];   // inversions by Newton iterations (last: that many or more)
 };
 
 // Metric at one point of the axisymmetric (x1, x2) plane, FP64: lapse,
@@ -179,6 +182,7 @@ struct Arrays {
     R *U[8];       // conserved: D, S_x, S_y, S_z, tau (cell), B~x, B~y, B~z (faces)
     R *U0[8];      // RK base state
     double *Z;     // Newton memory (cell)
+    float *zg;     // network Newton start per cell (0: none), written by k_mlp_guess_tc
     R *P[8];       // primitives rho, v^x, v^y, v^z, p, B^x, B^y, B^z (cell)
     R *F[3][5];    // HLL fluxes on d-faces
     R *ap[3];      // HLL a+ on d-faces

@@ -185,9 +185,20 @@ __device__ __forceinline__ void c2p_cell_features(const C2PCell &c, float f[MLP_
         mlp_features(c.Dc, c.S, c.tc, c.B, 1.0, MFlat<double>(), f);
 }
 
+// Newton start from the network outputs (log W, log(p/D)) of a cell with
+// undensitised D: Z0 = D W (1 + G/(G-1) (p/D) W), in FP32.
+__device__ __forceinline__ float net_z0(const float o[MLP_NO], double Dc, float gr_f)
+{
+    const float Wg = expf(o[0]), pD = expf(o[1]);
+    return d2f(Dc) * Wg * (1.0f + gr_f * pD * Wg);
+}
+
 // MLPK: 0 no network; 1 network evaluated here (CUDA cores, parameter block
 // mlp_sm in shared memory); 2 network outputs net[0..1] (log W, log(p/D))
-// computed by the caller, usable if net_ok.
+// computed by the caller, usable if net_ok; 3 the network's Newton start
+// A.zg written by k_mlp_guess_tc (0: none).  Every network start is
+// Z0 = D W (1 + G/(G-1) (p/D) W) in FP32 (net_z0): it only starts the Newton
+// solve, and the FP64 pipe is the scarce one.
 template <int MK, typename R, int MLPK>
 __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mode,
                                          int want_rate, long long t, const float *mlp_sm,
@@ -210,24 +221,28 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
         constexpr double tol = sizeof(R) == 4 ? NEWTON_TOL_BULK32 : NEWTON_TOL;
         C2PResult r;
         if constexpr (MLPK != 0) {
-            float o[MLP_NO];
             bool have = true;
-            if constexpr (MLPK == 1) {
-                float f[MLP_NI];
-                c2p_cell_features<MK>(c, f);
-                mlp_infer(mlp_sm, f, o);
+            float z0f = 0.0f;
+            if constexpr (MLPK == 3) {
+                z0f = A.zg[id];
+                have = z0f > 0.0f;
             } else {
-                o[0] = net[0];
-                o[1] = net[1];
-                have = net_ok;
+                float o[MLP_NO];
+                if constexpr (MLPK == 1) {
+                    float f[MLP_NI];
+                    c2p_cell_features<MK>(c, f);
+                    mlp_infer(mlp_sm, f, o);
+                } else {
+                    o[0] = net[0];
+                    o[1] = net[1];
+                    have = net_ok;
+                }
+                z0f = net_z0(o, Dc, ph.gr_f);
             }
             int first = 0;
             r.ok = false;
             if (have) {
-                // Z0 = D W (1 + G/(G-1) (p/D) W) in FP32: it is only the start
-                // of the Newton solve (the FP64 pipe is the scarce one)
-                const float Wg = expf(o[0]), pD = expf(o[1]);
-                const double z0 = f2d(d2f(Dc) * Wg * (1.0f + ph.gr_f * pD * Wg));
+                const double z0 = f2d(z0f);
                 if constexpr (MK == 1)
                     r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MKS<double>(*mp), 8, refine, tol);
                 else
@@ -300,6 +315,16 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             }
         }
     }
+    // histogram of the iteration counts: one atomic per distinct count in the warp
+    {
+        const unsigned lmask = __ballot_sync(0xffffffffu, live);
+        if (live) {
+            const int b = its < (unsigned long long)(ECHO_C2P_HIST - 1) ? (int)its : ECHO_C2P_HIST - 1;
+            const unsigned same = __match_any_sync(lmask, b);
+            if ((int)(threadIdx.x & 31) == __ffs(same) - 1)
+                atomicAdd(&A.scal->c2p_hist[b], (unsigned long long)__popc(same));
+        }
+    }
     // warp-aggregated counters
     its = warp_sum_u64(its);
     calls = warp_sum_u64(calls);
@@ -326,24 +351,130 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
     }
 }
 
-template <int MK, typename R, bool MLP>
+// NET: 0 no network; 1 the FP32 network on the CUDA cores (parameter block
+// staged in shared memory); 3 the Newton starts k_mlp_guess_tc wrote.
+template <int MK, typename R, int NET>
 __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate)
 {
     extern __shared__ float4 mlp_smem4[];
     const float *sm = nullptr;
-    if constexpr (MLP) {
+    if constexpr (NET == 1) {
         float *Ps = reinterpret_cast<float *>(mlp_smem4);
         for (int q = threadIdx.x; q < MLP_BLOCK; q += blockDim.x)
             Ps[q] = A.mlp[q];
         __syncthreads();
         sm = Ps;
     }
-    c2p_body<MK, R, MLP ? 1 : 0>(g, ph, A, guess_mode, want_rate, (long long)blockIdx.x * blockDim.x + threadIdx.x,
-                                 sm);
+    c2p_body<MK, R, NET>(g, ph, A, guess_mode, want_rate, (long long)blockIdx.x * blockDim.x + threadIdx.x, sm);
 }
 
-// c2p with the network guess, its hidden layer on the tensor cores
-// (echo_mlp_tc.cuh): persistent CTAs of 128 threads walk tiles of 128 cells;
+// Inputs of one cell's network features, loaded one tile ahead of their use
+// by k_mlp_guess_tc (the loads are in flight during the MMA round trips).
+template <typename R>
+struct CellIn {
+    R u[5];          // D, S_i, tau (densitised)
+    R bf[3][2];      // the two faces of each B~ component
+    int id, i, j;
+    bool live;
+};
+
+template <typename R>
+__device__ __forceinline__ void cell_in_load(const Geom &g, const Arrays<R> &A, long long t, CellIn<R> &x)
+{
+    const long long ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+    x.live = t < ncell;
+    const unsigned u = x.live ? (unsigned)t : 0u, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    const unsigned r = u / n0, k0 = r / n1;
+    x.i = NG + (int)(u - r * n0);
+    x.j = NG + (int)(r - k0 * n1);
+    x.id = gidx(g, x.i, x.j, NG + (int)k0);
+    const int st[3] = {1, g.px, g.pxy};
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        x.u[q] = A.U[q][x.id];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        x.bf[d][0] = A.U[5 + d][x.id];
+        x.bf[d][1] = A.U[5 + d][x.id + st[d]];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ float to_f(R x);
+template <>
+__device__ __forceinline__ float to_f<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float to_f<double>(double x) { return d2f(x); }
+
+// The network features of a loaded cell, in FP32 (cell-centre B the mean of
+// the two faces, which the training pairs also use for the scheme of order
+// 0; for order 1 the start changes by the difference of the two centre
+// values, a few 1e-3 at most, and Newton decides as before); returns the
+// undensitised D.
+template <int MK, typename R>
+__device__ __forceinline__ float cell_in_features(const Arrays<R> &A, const CellIn<R> &x, float f[MLP_NI])
+{
+    float isg = 1.0f, sg = 1.0f;
+    float S[3], B[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        B[d] = 0.5f * (to_f(x.bf[d][0]) + to_f(x.bf[d][1]));
+    if constexpr (MK == 1) {
+        const MetPt &mp = A.met.C[x.j * A.met.np0 + x.i];
+        isg = d2f(mp.isg);
+        sg = d2f(mp.sg);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            B[d] *= isg;
+    }
+    const float D = to_f(x.u[0]) * isg, tau = to_f(x.u[4]) * isg;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        S[q] = to_f(x.u[1 + q]) * isg;
+    if constexpr (MK == 1)
+        mlp_features_f(D, S, tau, B, sg, MKS<double>(A.met.C[x.j * A.met.np0 + x.i]), f);
+    else
+        mlp_features_f(D, S, tau, B, 1.0f, MFlat<float>(), f);
+    return D;
+}
+
+// The network's Newton start of every owned cell, both hidden layers on the
+// tensor cores (echo_mlp_tc.cuh), for the c2p kernel that follows (NET 3):
+// persistent CTAs of 128 threads walk tiles of 128 cells.  A tile whose
+// tensor-core result did not arrive writes 0: its cells start from the
+// previous-stage Z (counted in mlp_fallback).  Keeping the network out of
+// the c2p kernel leaves that FP64-bound kernel at full occupancy and free of
+// the per-tile barriers of the MMA round trips.
+template <int MK, typename R>
+__global__ void __launch_bounds__(128, 6) k_mlp_guess_tc(Geom g, Arrays<R> A, float gr_f, long long ntiles)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    TcMlp tm;
+    tc_setup(tm, tc_smem, A.mlp);
+    CellIn<R> x;
+    long long tile = blockIdx.x;
+    if (tile < ntiles)
+        cell_in_load(g, A, tile * 128 + threadIdx.x, x);
+    for (; tile < ntiles; tile += gridDim.x) {
+        float f[MLP_NI], o[MLP_NO];
+        const float D = cell_in_features<MK, R>(A, x, f);   // a lane past the end: its clamped cell's values
+        const int id = x.id;
+        const bool live = x.live;
+        const long long next = tile + gridDim.x;
+        if (next < ntiles)
+            cell_in_load(g, A, next * 128 + threadIdx.x, x);
+        const bool ok = tc_tile(tm, f, o);
+        if (live) {
+            const float Wg = expf(o[0]), pD = expf(o[1]);
+            A.zg[id] = ok ? D * Wg * (1.0f + gr_f * pD * Wg) : 0.0f;
+        }
+    }
+    tc_teardown(tm);
+}
+
+// c2p with the network evaluated inside it (guess mode +16), both hidden
+// layers on the tensor cores (echo_mlp_tc.cuh): persistent CTAs of 128
+// threads walk tiles of 128 cells;
 // per tile every thread computes its cell's features, the CTA runs the
 // network (one tcgen05 MMA group), then every thread inverts its cell.  A
 // tile whose tensor-core result did not arrive falls back to the previous-

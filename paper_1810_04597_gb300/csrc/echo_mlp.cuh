@@ -31,14 +31,15 @@ constexpr int MLP_STATE = 3 * MLP_BLOCK;
 // contravariant B and the metric:  log(tau/D), log(1 + S^2/D^2),
 // log(1 + B^2/D), (S.B)^2 / (S^2 B^2), alpha, log sqrt(gamma), beta_i beta^i,
 // (gamma^11 + gamma^22 + gamma^33)/3, log(D)/10.
+// FP32 inputs; the metric's members are FP32 or FP64 (converted on the
+// integer pipe).
+__device__ __forceinline__ float as_f(float x) { return x; }
+__device__ __forceinline__ float as_f(double x) { return d2f(x); }
+
 template <typename M>
-__device__ __forceinline__ void mlp_features(double Dc, const double S[3], double tau, const double B[3], double sqrtg,
-                                             const M &m, float f[9])
+__device__ __forceinline__ void mlp_features_f(float D, const float Sf[3], float tauf, const float Bf[3],
+                                               float sqrtgf, const M &m, float f[9])
 {
-    // FP64 -> FP32 on the integer pipe (d2f): the FP64 pipe is the scarce one
-    const float D = d2f(Dc);
-    const float Sf[3] = {d2f(S[0]), d2f(S[1]), d2f(S[2])};
-    const float Bf[3] = {d2f(B[0]), d2f(B[1]), d2f(B[2])};
     float Su[3], Bl[3];
     float al = 1.0f, bb = 0.0f, tr = 1.0f;
     if constexpr (M::flat) {
@@ -49,16 +50,16 @@ __device__ __forceinline__ void mlp_features(double Dc, const double S[3], doubl
         Bl[1] = Bf[1];
         Bl[2] = Bf[2];
     } else {
-        const float i11 = d2f(m.i11), i13 = d2f(m.i13), i22 = d2f(m.i22), i33 = d2f(m.i33);
-        const float g11 = d2f(m.g11), g13 = d2f(m.g13), g22 = d2f(m.g22), g33 = d2f(m.g33);
-        const float b1 = d2f(m.b1);
+        const float i11 = as_f(m.i11), i13 = as_f(m.i13), i22 = as_f(m.i22), i33 = as_f(m.i33);
+        const float g11 = as_f(m.g11), g13 = as_f(m.g13), g22 = as_f(m.g22), g33 = as_f(m.g33);
+        const float b1 = as_f(m.b1);
         Su[0] = i11 * Sf[0] + i13 * Sf[2];
         Su[1] = i22 * Sf[1];
         Su[2] = i13 * Sf[0] + i33 * Sf[2];
         Bl[0] = g11 * Bf[0] + g13 * Bf[2];
         Bl[1] = g22 * Bf[1];
         Bl[2] = g13 * Bf[0] + g33 * Bf[2];
-        al = d2f(m.al);
+        al = as_f(m.al);
         bb = g11 * b1 * b1;
         tr = (i11 + i22 + i33) * (1.0f / 3.0f);
     }
@@ -66,15 +67,26 @@ __device__ __forceinline__ void mlp_features(double Dc, const double S[3], doubl
     const float B2 = Bl[0] * Bf[0] + Bl[1] * Bf[1] + Bl[2] * Bf[2];
     const float SB = Sf[0] * Bf[0] + Sf[1] * Bf[1] + Sf[2] * Bf[2];
     const float iD = 1.0f / D;
-    f[0] = logf(fmaxf(d2f(tau) * iD, 1e-30f));
+    f[0] = logf(fmaxf(tauf * iD, 1e-30f));
     f[1] = log1pf(S2 * iD * iD);
     f[2] = log1pf(B2 * iD);
     f[3] = SB * SB / (S2 * B2 + 1e-30f);
     f[4] = al;
-    f[5] = logf(d2f(sqrtg));
+    f[5] = logf(sqrtgf);
     f[6] = bb;
     f[7] = tr;
     f[8] = fminf(fmaxf(logf(D), -30.0f), 30.0f) * 0.1f;
+}
+
+// FP64 inputs, converted to FP32 on the integer pipe (d2f): the FP64 pipe
+// is the scarce one.
+template <typename M>
+__device__ __forceinline__ void mlp_features(double Dc, const double S[3], double tau, const double B[3], double sqrtg,
+                                             const M &m, float f[9])
+{
+    const float Sf[3] = {d2f(S[0]), d2f(S[1]), d2f(S[2])};
+    const float Bf[3] = {d2f(B[0]), d2f(B[1]), d2f(B[2])};
+    mlp_features_f(d2f(Dc), Sf, d2f(tau), Bf, d2f(sqrtg), m, f);
 }
 
 // Forward pass with the parameter block in shared memory; returns the

@@ -109,6 +109,19 @@ def test_calls_out_of_order_are_rejected(lib):
         _lib.echo_destroy(ctx)
 
 
+def test_totals_struct_matches_the_header(lib):
+    """The binding's echo_totals has the header's members in order (the
+    iteration histogram last, ECHO_C2P_HIST long longs)."""
+    import ctypes
+    src = open(os.path.join(ROOT, "include", "echo.h")).read()
+    body = re.search(r"typedef struct \{([^{}]*)\} echo_totals;", src).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\b([a-z_0-9]+)(?:\[[A-Z_0-9]+\])?;", body)
+    assert names == [f[0] for f in _lib.echo_totals._fields_], names
+    assert int(re.search(r"#define ECHO_C2P_HIST (\d+)", src).group(1)) == _lib.ECHO_C2P_HIST
+    assert ctypes.sizeof(_lib.echo_totals) == 8 * (7 + 6 + _lib.ECHO_C2P_HIST)
+
+
 def test_kernel_names(lib):
     names = [_lib.echo_kernel_name(k) for k in range(_lib.ECHO_NK)]
     assert names[1] == "c2p" and names[3] == "faces_x" and len(set(names)) == _lib.ECHO_NK

@@ -48,6 +48,13 @@ def test_c2p_parity(orc):
     # and the input primitives are recovered
     for q in range(5):
         assert max_rel(P_g[q], prob.prims[q].reshape(-1)) <= 1e-13, q
+    # the iteration histogram covers every inversion and sums to the
+    # iteration count, which matches the oracle's (a cell whose last step
+    # lands on the stopping threshold may take one iteration more or less)
+    h = np.array(stats["c2p_iter_hist"])
+    assert h.sum() == stats["c2p_calls"] == prob.ncells
+    assert h[-1] == 0 and int(np.dot(np.arange(h.size), h)) == stats["c2p_iters"]
+    assert abs(stats["c2p_iters"] - ostats["iters"]) <= 0.002 * prob.ncells, (stats["c2p_iters"], ostats["iters"])
 
 
 def test_rhs_parity_ragged(orc):
