@@ -786,6 +786,8 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
     }
     int it = 0;
     bool conv = false;
+    bool lin = false;       // the last step was taken to first order
+    double sq_fin = 0.0;    // sqrt(1 - v^2) from that step
     while (ok && it < maxit) {
         ++it;
         const double om = 1.0 - v2;
@@ -799,17 +801,21 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
         const double dp = gm1g * (om - Z * dv2 + 0.5 * Dc * dv2 * isq);
         const double fp = 1.0 - dp + 0.5 * B2 * dv2 + SB2 * iZ2 * iZ;
         double dZ = nr_div(f, fp);
-        // A step within the tolerance ends the iteration: Z, 1/Z, 1/(Z + B^2)
-        // and v^2 move along their first derivatives instead of being
-        // evaluated again at Z - dZ (one division and the v^2 formula fewer);
-        // the neglected terms are of relative size (dZ/Z)^2 <= tol^2.
+        // A step within the tolerance ends the iteration: Z, 1/Z, 1/(Z + B^2),
+        // v^2 and sqrt(1 - v^2) move along their first derivatives instead of
+        // being evaluated again at Z - dZ (one division, the v^2 formula and a
+        // reciprocal square root fewer); the neglected terms are second order
+        // in the step, below the error the stopping tolerance itself leaves.
         if (ile(iabs(dZ), tol * Z)) {
-            const double Zl = Z - dZ, v2l = v2 - dv2 * dZ;
+            const double dv = dv2 * dZ;
+            const double Zl = Z - dZ, v2l = v2 - dv;
             if (is_pos(Zl) && ilt(v2l, 1.0)) {
                 iZ = fma(iZ * dZ, iZ, iZ);
                 iZB = fma(iZB * dZ, iZB, iZB);
                 Z = Zl;
                 v2 = v2l;
+                sq_fin = fma(0.5 * isq, dv, sq);   // d sqrt(om) = d om / (2 sqrt(om)), d om = dv
+                lin = true;
                 conv = true;
                 break;
             }
@@ -841,7 +847,7 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
         }
     }
     const double om = 1.0 - v2;   // > 0: v2 < 1 on every accepted iterate
-    const double sq = om * rsqrt(om);
+    const double sq = lin ? sq_fin : om * rsqrt(om);
     const double p = gm1g * (Z * om - Dc * sq);
     const double sbz = SB * iZ;
     double vl[3];
