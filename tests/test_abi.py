@@ -122,6 +122,27 @@ def test_totals_struct_matches_the_header(lib):
     assert ctypes.sizeof(_lib.echo_totals) == 8 * (7 + 6 + _lib.ECHO_C2P_HIST)
 
 
+def test_guess_modes_are_validated(lib):
+    """Newton-start modes: 0 previous Z, 1 network, 2 cold; +4 FP32
+    refinement; +8 / +16 (network on the CUDA cores / fused on the tensor
+    cores) only for the network and not both.  A network mode needs a loaded
+    network (ECHO_ESTATE), anything else is ECHO_EINVAL."""
+    ctx = _lib.echo_init(_grid(), _lib.echo_metric(0, 0.0), _lib.echo_eos(4 / 3, 0, 0, 0, 0, 0), 64, 0.4)
+    try:
+        for mode in (0, 2, 4, 6):
+            _lib.echo_set_c2p_guess(ctx, mode)
+        for mode in (1, 5, 9, 13, 17, 21):
+            with pytest.raises(_lib.EchoError) as e:
+                _lib.echo_set_c2p_guess(ctx, mode)
+            assert e.value.code == _lib.ECHO_ESTATE, mode
+        for mode in (-1, 3, 7, 8, 10, 12, 16, 18, 25, 29, 32):
+            with pytest.raises(_lib.EchoError) as e:
+                _lib.echo_set_c2p_guess(ctx, mode)
+            assert e.value.code == _lib.ECHO_EINVAL, mode
+    finally:
+        _lib.echo_destroy(ctx)
+
+
 def test_kernel_names(lib):
     names = [_lib.echo_kernel_name(k) for k in range(_lib.ECHO_NK)]
     assert names[1] == "c2p" and names[3] == "faces_x" and len(set(names)) == _lib.ECHO_NK

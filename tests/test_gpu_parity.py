@@ -131,6 +131,31 @@ def test_fixed_dt_matches(orc):
     assert max(errs.values()) <= 1e-12, errs
 
 
+def test_steps_from_any_start_match_the_oracle(orc):
+    """Newton decides the inversion: five steps with the cold start in every
+    c2p (mode 2) match the oracle (which starts from the previous-stage Z)
+    like the default start does, with more iterations per inversion; the
+    iteration histogram accounts for every inversion."""
+    from paper_1810_04597_gb300.echo import Solver
+    prob = inputs.smooth_box(20, seed=21)
+    st_o, _, _, _ = oracle_run(orc, prob, 5)
+    mean = {}
+    for mode in (0, 2):
+        s = Solver(prob)
+        s.set_prims()
+        s.set_c2p_guess(mode)
+        for _ in range(5):
+            s.step()
+        c = s.counters()
+        errs = per_field(orc, s.get_state(), st_o, prob.n)
+        assert max(errs.values()) <= 1e-11, (mode, errs)
+        h = np.array(c["c2p_iter_hist"])
+        assert h.sum() == c["c2p_calls"] and int(np.dot(np.arange(h.size), h)) == c["c2p_iters"]
+        mean[mode] = c["c2p_iters"] / c["c2p_calls"]
+    print("mean Newton iterations per inversion, previous Z / cold:", mean)
+    assert mean[2] > mean[0] + 0.5, mean
+
+
 def test_uniform_state_is_exact():
     prob = inputs.uniform_box((16, 8, 4))
     st0, _ = gpu_run(prob, 0)
