@@ -58,10 +58,10 @@ KMODEL = {
 FLOPS64 = {
     64: {"faces_x": 549.0, "faces_y": 549.0, "faces_z": 549.0,
          "emf_x": 299.2, "emf_y": 299.2, "emf_z": 299.2,
-         "c2p": 420.5, "update": 79.0},
+         "c2p": 412.5, "update": 79.0},
     # FP32-bulk path: only c2p computes in FP64 (previous-stage Z refined in
     # FP32, then 1.01 FP64 Newton iterations per call)
-    32: {"c2p": 145.0},
+    32: {"c2p": 139.0},
 }
 # FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 DFMA lanes
 # per SM and clock x 2 flop x 2.07 GHz (the 1.25 TFLOP/s nominal figure).
@@ -73,8 +73,8 @@ TRAFFIC_PER_FACE64 = 336887040 / 2316324
 # FP64 pipe activity in those captures
 # (sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active).
 FP64_PIPE_BUSY = {64: {"faces_x": 0.862, "faces_y": 0.862, "faces_z": 0.862, "emf_x": 0.854, "emf_y": 0.854,
-                       "emf_z": 0.854, "c2p": 0.862, "update": 0.834},
-                  32: {"c2p": 0.854}}
+                       "emf_z": 0.854, "c2p": 0.861, "update": 0.834},
+                  32: {"c2p": 0.850}}
 
 
 def kernel_units(name, n):
