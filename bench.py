@@ -424,12 +424,16 @@ def run_ours(args, world, rank, local, dist):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        s32.profile(True)
+        s32.profile_read()
         e0.record(s32.stream)
         for _ in range(args.steps):
             s32.step()
         e1.record(s32.stream)
         torch.cuda.synchronize()
         ms32 = e0.elapsed_time(e1)
+        prof32 = s32.profile_read()
+        s32.profile(False)
         fin32 = s32.get_state()
         t32 = s32.reduce()
         N = zones
@@ -447,6 +451,7 @@ def run_ours(args, world, rank, local, dist):
             "l1_rel_vs_fp64_gpu": l1, "max_l1": max(l1.values()),
             "mean_newton_iters": t32["c2p_iters"] / max(t32["c2p_calls"], 1),
             "c2p_guess": "previous-stage Z refined by FP32 Newton steps; FP64 Newton judges",
+            "roofline": fp32_c2p_roofline(prof32, ms32, zones),
             "note": "FP32 storage/stencil, FP64 c2p and reductions; same input, same step count"}}
         del s32
         variants["fp64_high_order"] = run_order1_variant(args, prob, dev, world, dist, ms)
@@ -617,6 +622,19 @@ def run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms64):
            "note": "FP32 bulk"}
     del s
     return out, state
+
+
+def fp32_c2p_roofline(prof, ms, zones):
+    """The FP32-bulk path's dominant kernel is c2p, bound by the FP64 pipe:
+    FP64 flop per cell (ncu, FLOPS64[32]) x cells per launch / its live
+    CUDA-event launch time, against the FP64 peak."""
+    c_ms, c_n = prof["c2p"]
+    avg_s = c_ms / max(c_n, 1) * 1e-3
+    achieved = zones * FLOPS64[32]["c2p"] / avg_s / 1e12
+    return {"kernel": "c2p", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_unit": FLOPS64[32]["c2p"], "units_per_launch": zones,
+            "fp64_pipe_busy_ncu": FP64_PIPE_BUSY[32]["c2p"], "avg_launch_ms": avg_s * 1e3,
+            "time_share": {k: round(v[0] / ms, 4) for k, v in prof.items() if v[1] > 0}}
 
 
 def run_guess_gain(prob, dev, mlp_state, warm=2, steps=3):

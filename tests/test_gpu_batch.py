@@ -78,3 +78,40 @@ def test_batch_flat_fixed_dt_and_counters():
         sx, sy = x.get_state(), y.get_state()
         assert np.max(np.abs(sx - sy)) <= 1e-12 * np.max(np.abs(sx))
         assert x.counters()["c2p_calls"] == y.counters()["c2p_calls"]
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_batch_with_network_guess(mode):
+    """FP32 tori with the network Newton start (guess 5) under each schedule.
+    Run-major runs the single-run kernels (the network's tensor-core pass):
+    bitwise.  The persistent and per-phase schedules evaluate the network on
+    the CUDA cores inside their c2p body: other starts, the same converged
+    inversions, so the states agree to the FP32 store's rounding."""
+    import torch
+    from paper_1810_04597_gb300.batch import Batch
+    rng = np.random.default_rng(77)
+    from test_gpu_mlp import random_state
+    state = torch.from_numpy(random_state(torch, rng)).cuda()
+    single = _tori(32)
+    runs = _tori(32)
+    for s in single + runs:
+        s.mlp_load(state)
+        s.set_c2p_guess(5)
+    for s in single:
+        for _ in range(2):
+            s.step()
+    b = Batch(runs)
+    b.configure(mode=mode, branches=2 if mode == 2 else 1)
+    for _ in range(2):
+        b.step()
+    for s, r in zip(runs, single):
+        got, ref = s.get_state(), r.get_state()
+        assert np.all(np.isfinite(got))
+        if mode == 2:
+            assert np.array_equal(got, ref), np.max(np.abs(got - ref))
+        else:
+            # a floor decision can flip with the last FP32 bit of a cell: L1
+            # to the store's rounding, max loosely
+            l1 = np.sum(np.abs(got - ref)) / np.sum(np.abs(ref))
+            assert l1 <= 1e-6, l1
+            assert np.max(np.abs(got - ref)) <= 1e-3 * np.max(np.abs(ref)), np.max(np.abs(got - ref))
