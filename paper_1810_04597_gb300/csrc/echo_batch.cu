@@ -163,7 +163,9 @@ const void *stage_kernel(const echo_batch *b)
     return b->precision == 64 ? batch_stage_kernel<double>(b->mk, b->mlp) : batch_stage_kernel<float>(b->mk, b->mlp);
 }
 
-size_t dyn_smem(const echo_batch *b) { return b->mlp ? MLP_BLOCK * sizeof(float) : 0; }
+// the network's starts come from a pass of their own: no parameter block in
+// the stage kernel's shared memory
+size_t dyn_smem(const echo_batch *) { return 0; }
 
 int occupancy(const echo_batch *b)
 {
@@ -221,6 +223,16 @@ int launch_stage(echo_batch *b, int stage, double dt)
     Phys ph = b->ph;
     double cfl = b->cfl;
     int guess = b->guess;
+    if (b->mlp) {
+        // the network's Newton starts of this stage, before the persistent
+        // kernel (its features read the face field before the stage's own
+        // ghost fill: a cell next to a periodic seam may start from a field
+        // one stage old; Newton decides the result either way)
+        if (b->precision == 64)
+            batch_enqueue_guess<double>(b->mk, descs, planp, b->plan, ph.gr_f, b->stream);
+        else
+            batch_enqueue_guess<float>(b->mk, descs, planp, b->plan, ph.gr_f, b->stream);
+    }
     void *args[] = {&descs, &planp, &qctr, &ph, &stage, &dt, &cfl, &guess};
     cudaError_t e = cudaLaunchCooperativeKernel(stage_kernel(b), dim3(b->grid_blocks), dim3(128), args, dyn_smem(b),
                                                 b->stream);

@@ -7,8 +7,31 @@ template <>
 const void *batch_stage_kernel<double>(int mk, bool mlp)
 {
     if (mk == 1)
-        return mlp ? (const void *)k_batch_stage<1, double, true, 4> : (const void *)k_batch_stage<1, double, false, 4>;
-    return mlp ? (const void *)k_batch_stage<0, double, true, 4> : (const void *)k_batch_stage<0, double, false, 4>;
+        return mlp ? (const void *)k_batch_stage<1, double, 3, 4> : (const void *)k_batch_stage<1, double, 0, 4>;
+    return mlp ? (const void *)k_batch_stage<0, double, 3, 4> : (const void *)k_batch_stage<0, double, 0, 4>;
+}
+
+template <int MK>
+static void guess_pass(const RunDesc<double> *descs, const BatchPlan *planp, const BatchPlan &P, float gr_f, cudaStream_t s)
+{
+    static int resident = 0;
+    if (resident == 0)
+        resident = tc_resident_ctas((const void *)k_bphase_guess_tc<MK, double>, TC_SMEM);
+    const long long nch = P.ntiles[PH_C2P] * (P.tile / 128);
+    const long long grid = nch < resident ? nch : resident;
+    if (grid > 0)
+        k_bphase_guess_tc<MK, double><<<(unsigned)grid, 128, TC_SMEM, s>>>(descs, planp, gr_f);
+}
+
+template <>
+void batch_enqueue_guess<double>(int mk, const void *descs, const BatchPlan *plan_dev, const BatchPlan &plan, float gr_f,
+                            cudaStream_t s)
+{
+    const RunDesc<double> *d = static_cast<const RunDesc<double> *>(descs);
+    if (mk == 1)
+        guess_pass<1>(d, plan_dev, plan, gr_f, s);
+    else
+        guess_pass<0>(d, plan_dev, plan, gr_f, s);
 }
 
 template <int MK>
@@ -19,12 +42,12 @@ static void phased(bool mlp, const RunDesc<double> *descs, const BatchPlan *plan
     for (int st = 0; st < 3; ++st) {
         for (int p = PH_FILLF0; p <= PH_FILLF2; ++p)
             k_bphase_fill<double><<<(unsigned)P.ntiles[p], 128, 0, s>>>(descs, planp, p);
-        if (mlp)
-            k_bphase_c2p<MK, double, true><<<(unsigned)P.ntiles[PH_C2P], 128, MLP_BLOCK * sizeof(float), s>>>(
-                descs, planp, ph, guess, st == 0 ? 1 : 0);
-        else
-            k_bphase_c2p<MK, double, false><<<(unsigned)P.ntiles[PH_C2P], 128, 0, s>>>(descs, planp, ph, guess,
-                                                                                   st == 0 ? 1 : 0);
+        if (mlp) {
+            guess_pass<MK>(descs, planp, P, ph.gr_f, s);
+            k_bphase_c2p<MK, double, 3><<<(unsigned)P.ntiles[PH_C2P], 128, 0, s>>>(descs, planp, ph, guess, st == 0 ? 1 : 0);
+        } else {
+            k_bphase_c2p<MK, double, 0><<<(unsigned)P.ntiles[PH_C2P], 128, 0, s>>>(descs, planp, ph, guess, st == 0 ? 1 : 0);
+        }
         if (st == 0)
             k_bphase_scalars<double><<<1, 32, 0, s>>>(descs, nruns, 1, dt, cfl);
         for (int p = PH_FILLP0; p <= PH_FILLP2; ++p)

@@ -52,11 +52,10 @@ __device__ __noinline__ void nl_fill(const Geom &g, int d, const FillList<R> &L,
 {
     fill_body<R>(g, d, L, t);
 }
-template <int MK, typename R, bool MLP>
-__device__ __noinline__ void nl_c2p(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess, int rate, long long t,
-                                    const float *sm)
+template <int MK, typename R, int NET>
+__device__ __noinline__ void nl_c2p(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess, int rate, long long t)
 {
-    c2p_body<MK, R, MLP ? 1 : 0>(g, ph, A, guess, rate, t, sm);
+    c2p_body<MK, R, NET>(g, ph, A, guess, rate, t, nullptr);
 }
 template <int D, int MK, typename R>
 __device__ __noinline__ void nl_faces(const Geom &g, const Phys &ph, const Arrays<R> &A, long long t,
@@ -75,7 +74,9 @@ __device__ __noinline__ void nl_update(const Geom &g, const Phys &ph, const Arra
     update_body<MK, R>(g, ph, A, stage, nullptr, t);
 }
 
-template <int MK, typename R, bool MLP, int MINB>
+// NET: 0 no network; 3 the network's Newton starts, written by
+// k_bphase_guess_tc before the stage.
+template <int MK, typename R, int NET, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_batch_stage(const RunDesc<R> *__restrict__ runs, const BatchPlan *__restrict__ plan,
                                                      unsigned long long *qctr, Phys ph, int stage, double dt_fixed,
                                                      double cfl, int guess_mode)
@@ -83,18 +84,8 @@ __global__ void __launch_bounds__(128, MINB) k_batch_stage(const RunDesc<R> *__r
     cg::grid_group grid = cg::this_grid();
     __shared__ LimScratch<R> lsm;
     __shared__ long long s_tile;
-    extern __shared__ float4 mlp_smem4[];
     const int nruns = plan->nruns;
     const int tile = plan->tile;
-    const float *sm = nullptr;
-    if constexpr (MLP) {
-        float *Ps = reinterpret_cast<float *>(mlp_smem4);
-        const float *src = runs[0].A.mlp;
-        for (int q = threadIdx.x; q < MLP_BLOCK; q += blockDim.x)
-            Ps[q] = src[q];
-        __syncthreads();
-        sm = Ps;
-    }
     if (stage == 0 && blockIdx.x == 0 && (int)threadIdx.x < nruns) {
         DevScalars *sc = runs[threadIdx.x].A.scal;
         sc->rate_bits = 0ULL;
@@ -139,7 +130,7 @@ __global__ void __launch_bounds__(128, MINB) k_batch_stage(const RunDesc<R> *__r
                     nl_fill<R>(rd.g, p - PH_FILLF0, rd.ff, t);
                     break;
                 case PH_C2P:
-                    nl_c2p<MK, R, MLP>(rd.g, ph, rd.A, guess_mode, stage == 0 ? 1 : 0, t, sm);
+                    nl_c2p<MK, R, NET>(rd.g, ph, rd.A, guess_mode, stage == 0 ? 1 : 0, t);
                     break;
                 case PH_FILLP0:
                 case PH_FILLP1:
@@ -200,25 +191,64 @@ __global__ void __launch_bounds__(128) k_bphase_fill(const RunDesc<R> *__restric
         fill_body<R>(rd.g, d, p < PH_C2P ? rd.ff : rd.fp, base + c + threadIdx.x);
 }
 
-template <int MK, typename R, bool MLP>
+template <int MK, typename R, int NET>
 __global__ void __launch_bounds__(128) k_bphase_c2p(const RunDesc<R> *__restrict__ runs, const BatchPlan *__restrict__ plan,
                                                     Phys ph, int guess_mode, int want_rate)
 {
-    extern __shared__ float4 mlp_smem4[];
-    const float *sm = nullptr;
-    if constexpr (MLP) {
-        float *Ps = reinterpret_cast<float *>(mlp_smem4);
-        for (int q = threadIdx.x; q < MLP_BLOCK; q += blockDim.x)
-            Ps[q] = runs[0].A.mlp[q];
-        __syncthreads();
-        sm = Ps;
-    }
     const long long tl = blockIdx.x;
     const Segment sgm = plan->seg[PH_C2P][find_segment(plan, PH_C2P, tl)];
     const RunDesc<R> &rd = runs[sgm.run];
     const long long base = (tl - sgm.first_tile) * plan->tile;
     for (int c = 0; c < plan->tile; c += blockDim.x)
-        c2p_body<MK, R, MLP ? 1 : 0>(rd.g, ph, rd.A, guess_mode, want_rate, base + c + threadIdx.x, sm);
+        c2p_body<MK, R, NET>(rd.g, ph, rd.A, guess_mode, want_rate, base + c + threadIdx.x, nullptr);
+}
+
+// The network's Newton starts for the cells of every run (tensor cores,
+// echo_mlp_tc.cuh), as k_mlp_guess_tc does for one run: persistent CTAs walk
+// the c2p phase's tiles in chunks of 128 cells (the plan's tile is a
+// multiple of 128), loading the next chunk's inputs during the current
+// chunk's MMA round trips.  All runs use runs[0]'s network.
+template <int MK, typename R>
+__global__ void __launch_bounds__(128, 6) k_bphase_guess_tc(const RunDesc<R> *__restrict__ runs,
+                                                         const BatchPlan *__restrict__ plan, float gr_f)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    TcMlp tm;
+    tc_setup(tm, tc_smem, runs[0].A.mlp);
+    const long long cpt = plan->tile / 128;
+    const long long nch = plan->ntiles[PH_C2P] * cpt;
+    // run of chunk ch and the run-local index of its first cell
+    auto locate = [&](long long ch, int &run) -> long long {
+        const long long tl = ch / cpt;
+        const Segment sgm = plan->seg[PH_C2P][find_segment(plan, PH_C2P, tl)];
+        run = sgm.run;
+        return (tl - sgm.first_tile) * plan->tile + (ch % cpt) * 128;
+    };
+    CellIn<R> x;
+    int run = 0;
+    long long ch = blockIdx.x;
+    if (ch < nch) {
+        const long long b = locate(ch, run);
+        cell_in_load(runs[run].g, runs[run].A, b + threadIdx.x, x);
+    }
+    for (; ch < nch; ch += gridDim.x) {
+        float f[MLP_NI], o[MLP_NO];
+        const int cur = run;
+        const float D = cell_in_features<MK, R>(runs[cur].A, x, f);
+        const int id = x.id;
+        const bool live = x.live;
+        const long long next = ch + gridDim.x;
+        if (next < nch) {
+            const long long b = locate(next, run);
+            cell_in_load(runs[run].g, runs[run].A, b + threadIdx.x, x);
+        }
+        const bool ok = tc_tile(tm, f, o);
+        if (live) {
+            const float Wg = expf(o[0]), pD = expf(o[1]);
+            runs[cur].A.zg[id] = ok ? D * Wg * (1.0f + gr_f * pD * Wg) : 0.0f;
+        }
+    }
+    tc_teardown(tm);
 }
 
 template <int MK, typename R>
@@ -296,9 +326,19 @@ __global__ void k_bphase_scalars(const RunDesc<R> *__restrict__ runs, int nruns,
 // Host-side entry points of one storage type R (defined in the per-type units).
 template <typename R>
 const void *batch_stage_kernel(int mk, bool mlp);
+// the network's Newton starts of every run (guess modes 1, 5), before a stage
+template <typename R>
+void batch_enqueue_guess(int mk, const void *descs, const BatchPlan *plan_dev, const BatchPlan &plan, float gr_f,
+                         cudaStream_t s);
 template <typename R>
 void batch_enqueue_phased(int mk, bool mlp, const void *descs, const BatchPlan *plan_dev, const BatchPlan &plan,
                           int nruns, const Phys &ph, int guess, double dt, double cfl, cudaStream_t s);
+template <>
+void batch_enqueue_guess<double>(int mk, const void *descs, const BatchPlan *plan_dev, const BatchPlan &plan,
+                                 float gr_f, cudaStream_t s);
+template <>
+void batch_enqueue_guess<float>(int mk, const void *descs, const BatchPlan *plan_dev, const BatchPlan &plan,
+                                float gr_f, cudaStream_t s);
 template <>
 const void *batch_stage_kernel<double>(int mk, bool mlp);
 template <>

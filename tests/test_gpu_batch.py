@@ -83,10 +83,12 @@ def test_batch_flat_fixed_dt_and_counters():
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_with_network_guess(mode):
     """FP32 tori with the network Newton start (guess 5) under each schedule.
-    Run-major runs the single-run kernels (the network's tensor-core pass):
-    bitwise.  The persistent and per-phase schedules evaluate the network on
-    the CUDA cores inside their c2p body: other starts, the same converged
-    inversions, so the states agree to the FP32 store's rounding."""
+    Run-major runs the single-run kernels: bitwise.  The persistent and
+    per-phase schedules take the starts from their own tensor-core pass over
+    all runs (the persistent one before the stage's ghost fill, so a cell at
+    a periodic seam may start from a field one stage old) and compile c2p
+    into other kernels: the same converged inversions, states equal to the
+    FP32 store's rounding."""
     import torch
     from paper_1810_04597_gb300.batch import Batch
     rng = np.random.default_rng(77)
