@@ -243,10 +243,11 @@ int echo_mlp_grad(const float *dev_state, const float *X, const float *Y, long l
 
 /* Standardised network outputs (n x 3, device) of n feature rows. */
 int echo_mlp_forward(const float *dev_state, const float *X, long long n, float *out, void *cuda_stream);
-/* The same with the 64 x 64 hidden layer on the tensor cores (tcgen05 MMA,
- * BF16 inputs, FP32 accumulation; layers 1 and 3 in FP32), as the c2p
- * kernel evaluates the network.  Rows whose tensor-core result did not
- * arrive within about a second get NaN. */
+/* The same with the products of layers 1 and 2 on the tensor cores
+ * (tcgen05 MMA, BF16 inputs, FP32 accumulation; standardisation, tanh.approx
+ * activations and layer 3 in FP32), as the network guess of c2p evaluates
+ * it.  Rows whose tensor-core result did not arrive within about a second
+ * get NaN. */
 int echo_mlp_forward_tc(const float *dev_state, const float *X, long long n, float *out, void *cuda_stream);
 
 /* Training rows from the current state: runs a c2p (previous-stage guess),
@@ -272,8 +273,8 @@ int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
 int echo_set_c2p_guess(echo_ctx *ctx, int mode);
 
 /* Copy the cumulative counters (c2p_iters, c2p_calls, c2p_fail, floor_hits,
- * mlp_fallback) to *out without running anything; other fields untouched.
- * Synchronises. */
+ * mlp_fallback, c2p_iter_hist) to *out without running anything; other
+ * fields untouched.  Synchronises. */
 int echo_counters(echo_ctx *ctx, echo_totals *out);
 
 /* ---- batch of independent runs (parameter sweeps) ----
@@ -287,8 +288,9 @@ int echo_counters(echo_ctx *ctx, echo_totals *out);
  * block resident, so they cannot deadlock).  Every run keeps its own CFL dt.
  * The runs must be bound contexts with a state; their workspaces and
  * counters are the runs' own.  In schedules 0 and 1, if run 0 uses the
- * network guess, all runs use run 0's guess mode and network; schedule 2
- * uses each run's own. */
+ * network guess, all runs use run 0's guess mode and network, evaluated on
+ * the tensor cores in a pass over all runs before each stage's c2p; schedule
+ * 2 uses each run's own. */
 #define ECHO_BATCH_MAXRUNS 32
 typedef struct echo_batch echo_batch;
 
@@ -338,7 +340,8 @@ int echo_selftest_conversions(long long n, unsigned long long seed, unsigned lon
  * largest distance in ulp into *dev_max_ulp (device, caller-zeroed). */
 int echo_selftest_recip(long long n, unsigned long long seed, unsigned long long *dev_max_ulp, void *cuda_stream);
 
-/* Kernel classes timed by the profiling facility below. */
+/* Kernel classes timed by the profiling facility below (ECHO_K_C2P includes
+ * the network's own pass when the guess mode runs one). */
 #define ECHO_K_FILL_FACES 0
 #define ECHO_K_C2P 1
 #define ECHO_K_FILL_PRIMS 2
