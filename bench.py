@@ -366,6 +366,15 @@ def run_ours(args, world, rank, local, dist):
                "frac": bytes_launch / avg_s / 1e9 / hbm, "bytes_per_launch": bytes_launch,
                "peak_source": f"{peak_src} hbm_gbs" if peak_src == "measured" else "fallback 6800 GB/s"}
     share = {k: round(v[0] / ms, 4) for k, v in prof.items() if v[1] > 0}
+    # whole-step HBM figure: the algorithmic bytes of every modelled kernel
+    # launched in the timed region (each field read or written once per
+    # launch) over the step time
+    step_bytes = sum(kernel_units(k, n) * kernel_bytes_per_unit(k, args.precision) * v[1] for k, v in timed.items())
+    hbm_step = {"bytes_per_zone_step": step_bytes / (zones * args.steps),
+                "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
+                "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm, "peak_gbs": hbm,
+                "note": "algorithmic bytes of c2p, faces, EMFs and update per step / step time (fills and scalars "
+                        "not counted)"}
     fl = FLOPS64[args.precision]
     if dom in fl:
         # bound by the FP64 pipe, not by HBM
@@ -484,7 +493,8 @@ def run_ours(args, world, rank, local, dist):
         "config": {"workload": workload_name(args),
                    "grid": list(n), "zones": zones, "parallelism": f"replicas x{world}", "c2p_guess": guess,
                    "l2": "working set (~9 GB) larger than L2; no flush needed"},
-        "clocks": clocks, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "variants": variants,
+        "clocks": clocks, "roofline": roof, "hbm_step": hbm_step, "cpu_baseline": cpu, "e2e": e2e,
+        "variants": variants,
         "gpu_launches": launches,
         "check": {"c2p_fail": totals["c2p_fail"], "mean_newton_iters":
                   totals["c2p_iters"] / max(totals["c2p_calls"], 1), "dt_cfl": totals["dt_cfl"]},

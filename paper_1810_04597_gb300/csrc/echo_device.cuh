@@ -513,10 +513,10 @@ __device__ __forceinline__ T mp5_try(T um2, T um1, T u0, T up1, T up2, bool &acc
     return mp5_try_d(um2, um1, u0, up1, up2, up1 - u0, u0 - um1, accept, order);
 }
 
+// The limited value given the unlimited one (uor = mp5_uor of the same stencil).
 template <typename T>
-__device__ __forceinline__ T mp5_limit(T um2, T um1, T u0, T up1, T up2, int order)
+__device__ __forceinline__ T mp5_limit_u(T um2, T um1, T u0, T up1, T up2, T uor)
 {
-    const T uor = mp5_uor(um2, um1, u0, up1, up2, order);
     const T a4 = T(MP5_ALPHA) * (u0 - um1);
     const T dm1 = um2 - T(2) * um1 + u0;
     const T d0 = um1 - T(2) * u0 + up1;
@@ -530,6 +530,12 @@ __device__ __forceinline__ T mp5_limit(T um2, T um1, T u0, T up1, T up2, int ord
     const T umin = imax(imin(imin(u0, up1), umd), imin(imin(u0, uul), ulc));
     const T umax = imin(imax(imax(u0, up1), umd), imax(imax(u0, uul), ulc));
     return uor + minmod2(umin - uor, umax - uor);
+}
+
+template <typename T>
+__device__ __forceinline__ T mp5_limit(T um2, T um1, T u0, T up1, T up2, int order)
+{
+    return mp5_limit_u(um2, um1, u0, up1, up2, mp5_uor(um2, um1, u0, up1, up2, order));
 }
 
 // ------------------------------------------------------------------ state

@@ -519,8 +519,11 @@ struct LimScratch {
     unsigned short desc[kWarpsPerBlock][32 * 16];
 };
 
-// limited(id_of_owner, m, side) -> T
-template <typename T, typename F>
+// limited(id_of_owner, m, side, uor) -> T.  With PRE the owners have stored
+// every unlimited value in their res slots before the call (uor passes the
+// rejected item's one, so the limiter need not recompute it; FP64, where that
+// saves five FP64-pipe instructions per item), else uor is 0.
+template <bool PRE, typename T, typename F>
 __device__ __forceinline__ void compact_limit(unsigned pend, int id, LimScratch<T> &sm, F limited)
 {
     const int lane = threadIdx.x & 31;
@@ -555,7 +558,7 @@ __device__ __forceinline__ void compact_limit(unsigned pend, int id, LimScratch<
         const int ido = __shfl_sync(0xffffffffu, id, o);
         if (act) {
             const int b = (int)(d & 15);
-            sm.res[w][o][b] = limited(ido, b >> 1, b & 1);
+            sm.res[w][o][b] = limited(ido, b >> 1, b & 1, PRE ? sm.res[w][o][b] : T(0));
         }
     }
     __syncwarp();
@@ -597,7 +600,7 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     const int sd = stride_of(g, D);
     using T = R;
     const int qs[7] = {0, 1, 2, 3, 4, 5 + T1, 5 + T2};
-    T Lv[7], Rv[7];
+    T Lv[7] = {}, Rv[7] = {};
     unsigned pend = 0;
     if (live) {
 #pragma unroll
@@ -616,25 +619,34 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
         }
     }
     // limiter on the rejected items, compacted across the warp
-    compact_limit<T>(pend, id, lsm, [&](int ido, int m, int side) -> T {
+    constexpr bool PRE = sizeof(T) == 8;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if constexpr (PRE) {
+#pragma unroll
+        for (int m = 0; m < 7; ++m) {
+            lsm.res[w][lane][2 * m] = Lv[m];
+            lsm.res[w][lane][2 * m + 1] = Rv[m];
+        }
+    }
+    compact_limit<PRE, T>(pend, id, lsm, [&](int ido, int m, int side, T uor) -> T {
         const R *__restrict__ a = A.P[qs[m]];
         T q[6];
 #pragma unroll
         for (int s = 0; s < 6; ++s)
             q[s] = a[ido + (s - 3) * sd];
-        return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1], order) : mp5_limit(q[0], q[1], q[2], q[3], q[4], order);
+        if constexpr (PRE)
+            return side ? mp5_limit_u(q[5], q[4], q[3], q[2], q[1], uor) : mp5_limit_u(q[0], q[1], q[2], q[3], q[4], uor);
+        else
+            return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1], order) : mp5_limit(q[0], q[1], q[2], q[3], q[4], order);
     });
     if (!live)
         return;
-    {
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-        for (int m = 0; m < 7; ++m) {
-            if (pend & (1u << (2 * m)))
-                Lv[m] = lsm.res[w][lane][2 * m];
-            if (pend & (1u << (2 * m + 1)))
-                Rv[m] = lsm.res[w][lane][2 * m + 1];
-        }
+    for (int m = 0; m < 7; ++m) {
+        if (PRE || (pend & (1u << (2 * m))))
+            Lv[m] = lsm.res[w][lane][2 * m];
+        if (PRE || (pend & (1u << (2 * m + 1))))
+            Rv[m] = lsm.res[w][lane][2 * m + 1];
     }
     // face metric (x1-faces: F1, x2-faces: F2, x3-faces: the cell-centre table)
     const MetPt *mp = nullptr;
@@ -797,7 +809,7 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
     S.st[0] = S.st[1] = S.st[2] = S.st[3] = sb;
     S.st[4] = sa;
     S.st[5] = sb;
-    T Lv[6], Rv[6];
+    T Lv[6] = {}, Rv[6] = {};
     unsigned pend = 0;
     if (live) {
 #pragma unroll
@@ -814,7 +826,16 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
             pend |= (okR ? 0u : 1u) << (2 * m + 1);
         }
     }
-    compact_limit<T>(pend, id, lsm, [&](int ido, int m, int side) -> T {
+    constexpr bool PRE = sizeof(T) == 8;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if constexpr (PRE) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            lsm.res[w][lane][2 * m] = Lv[m];
+            lsm.res[w][lane][2 * m + 1] = Rv[m];
+        }
+    }
+    compact_limit<PRE, T>(pend, id, lsm, [&](int ido, int m, int side, T uor) -> T {
         const R *p;
         int st;
         emf_pick(S, m, p, st);
@@ -822,19 +843,19 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
 #pragma unroll
         for (int s = 0; s < 6; ++s)
             q[s] = p[ido + (s - 3) * st];
-        return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1], order) : mp5_limit(q[0], q[1], q[2], q[3], q[4], order);
+        if constexpr (PRE)
+            return side ? mp5_limit_u(q[5], q[4], q[3], q[2], q[1], uor) : mp5_limit_u(q[0], q[1], q[2], q[3], q[4], uor);
+        else
+            return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1], order) : mp5_limit(q[0], q[1], q[2], q[3], q[4], order);
     });
     if (!live)
         return;
-    {
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            if (pend & (1u << (2 * m)))
-                Lv[m] = lsm.res[w][lane][2 * m];
-            if (pend & (1u << (2 * m + 1)))
-                Rv[m] = lsm.res[w][lane][2 * m + 1];
-        }
+    for (int m = 0; m < 6; ++m) {
+        if (PRE || (pend & (1u << (2 * m))))
+            Lv[m] = lsm.res[w][lane][2 * m];
+        if (PRE || (pend & (1u << (2 * m + 1))))
+            Rv[m] = lsm.res[w][lane][2 * m + 1];
     }
     // va[s][t]: a-face side s (0 L, 1 R), reconstructed along b to side t
     const T va[2][2] = {{Lv[0], Rv[0]}, {Lv[1], Rv[1]}};
