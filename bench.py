@@ -56,8 +56,8 @@ KMODEL = {
 # Newton iteration count (2.74 per call there); faces_y/z run the code of
 # faces_x with other strides.
 FLOPS64 = {
-    64: {"faces_x": 549.0, "faces_y": 549.0, "faces_z": 549.0,
-         "emf_x": 299.2, "emf_y": 299.2, "emf_z": 299.2,
+    64: {"faces_x": 540.5, "faces_y": 540.5, "faces_z": 540.5,
+         "emf_x": 290.7, "emf_y": 290.7, "emf_z": 290.7,
          "c2p": 412.5, "update": 79.0},
     # FP32-bulk path: only c2p computes in FP64 (previous-stage Z refined in
     # FP32, then 1.01 FP64 Newton iterations per call)
@@ -67,13 +67,13 @@ FLOPS64 = {
 # per SM and clock x 2 flop x 2.07 GHz (the 1.25 TFLOP/s nominal figure).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per face of faces_x (dram__bytes_read.sum + dram__bytes_write.sum
-# of the same 128^3 ncu launch: 336,887,040 B over 2,316,324 faces); scaled to a
+# of the same 128^3 ncu launch: 338,365,440 B over 2,316,324 faces); scaled to a
 # launch by the faces it processes.
-TRAFFIC_PER_FACE64 = 336887040 / 2316324
+TRAFFIC_PER_FACE64 = 338365440 / 2316324
 # FP64 pipe activity in those captures
 # (sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active).
-FP64_PIPE_BUSY = {64: {"faces_x": 0.862, "faces_y": 0.862, "faces_z": 0.862, "emf_x": 0.854, "emf_y": 0.854,
-                       "emf_z": 0.854, "c2p": 0.861, "update": 0.834},
+FP64_PIPE_BUSY = {64: {"faces_x": 0.859, "faces_y": 0.859, "faces_z": 0.859, "emf_x": 0.849, "emf_y": 0.849,
+                       "emf_z": 0.849, "c2p": 0.861, "update": 0.832},
                   32: {"c2p": 0.850}}
 
 
