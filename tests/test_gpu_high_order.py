@@ -118,3 +118,23 @@ def test_order1_batch_needs_run_major():
     b.step()
     for r, x in zip(single, runs):
         assert np.array_equal(x.get_state(), r)
+
+
+def test_order1_with_network_guess_matches():
+    """The network's Newton start (its features take the two-face mean of B
+    also under order 1) only moves the start: three order-1 steps with it
+    equal the steps from the previous-stage Z to rounding."""
+    import torch
+    from paper_1810_04597_gb300.echo import Solver
+    from test_gpu_mlp import random_state
+    state = torch.from_numpy(random_state(torch, np.random.default_rng(5))).cuda()
+    out = []
+    for mode in (0, 1):
+        s = Solver(_order1(inputs.smooth_box(20, seed=13)))
+        s.set_prims()
+        s.mlp_load(state)
+        s.set_c2p_guess(mode)
+        for _ in range(3):
+            s.step()
+        out.append(s.get_state())
+    assert np.max(np.abs(out[0] - out[1])) <= 1e-12 * np.max(np.abs(out[0])), np.max(np.abs(out[0] - out[1]))
