@@ -109,3 +109,42 @@ def test_full_size_steps_conserve(full):
     bmax = np.max(np.abs(st[5 * full.ncells:]))
     assert t1["max_divb"] * full.dx[0] / bmax <= 1e-12
     assert t1["dt_cfl"] > 0.0
+
+
+@pytest.mark.parametrize("guess", [4, 5])
+def test_full_size_fp32_bulk_against_fp64(full, guess):
+    """The FP32-bulk form at 256^3 (previous-Z start, and the network start
+    from a briefly trained network) against the FP64 path (pinned to the
+    oracle above) after three steps: relative L1 per field well inside 1e-5,
+    mass and energy conserved to the FP32 store's rounding."""
+    import torch
+    from paper_1810_04597_gb300 import mlp
+    from paper_1810_04597_gb300.echo import Solver
+    s64 = Solver(full)
+    s64.set_prims()
+    for _ in range(3):
+        s64.step()
+    ref = s64.get_state()
+    del s64
+    s = Solver(full, precision=32)
+    s.set_prims()
+    if guess & 1:
+        runs = [(inputs.sweep_box(48, seed=91), [0, 2, 4])]
+        (Xtr, Ytr), _, _ = mlp.collect(runs)
+        state, _ = mlp.train(Xtr, Ytr, epochs=2, batch=4096, lr=2e-3)
+        s.mlp_load(state)
+    s.set_c2p_guess(guess)
+    t0 = s.reduce()
+    for _ in range(3):
+        s.step()
+    t1 = s.reduce()
+    got = s.get_state()
+    N = full.ncells
+    bounds = [0, N, 2 * N, 3 * N, 4 * N, 5 * N, len(ref)]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        l1 = np.sum(np.abs(got[a:b] - ref[a:b])) / np.sum(np.abs(ref[a:b]))
+        assert l1 <= 2e-6, (a, l1)
+    assert t1["c2p_fail"] == 0
+    assert abs(t1["mass"] - t0["mass"]) <= 1e-6 * abs(t0["mass"])
+    assert abs(t1["energy"] - t0["energy"]) <= 1e-6 * abs(t0["energy"])
+    torch.cuda.empty_cache()
