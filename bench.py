@@ -63,6 +63,15 @@ FLOPS64 = {
     # FP32, then 1.01 FP64 Newton iterations per call)
     32: {"c2p": 139.0},
 }
+# FP64 arithmetic instructions (DFMA + DADD + DMUL thread instructions) per
+# unit from the same captures: each takes one FP64-pipe slot, so these over
+# the pipe's 2 slots per SM and clock give the pipe-time view beside the flop
+# roofline (DADD and DMUL are one flop for a full slot).
+FP64_INSTR = {
+    64: {"faces_x": 391.9, "faces_y": 391.9, "faces_z": 391.9, "emf_x": 222.0, "emf_y": 222.0, "emf_z": 222.0,
+         "c2p": 298.4, "update": 53.0},
+    32: {"c2p": 102.0},
+}
 # FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 DFMA lanes
 # per SM and clock x 2 flop x 2.07 GHz (the 1.25 TFLOP/s nominal figure).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -386,6 +395,7 @@ def run_ours(args, world, rank, local, dist):
                 "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "flops_per_unit": fl[dom], "units_per_launch": units,
                 "fp64_pipe_busy_ncu": FP64_PIPE_BUSY[args.precision].get(dom),
+                "fp64_instr_frac": units * FP64_INSTR[args.precision][dom] / avg_s / (FP64_PEAK_TFLOPS * 1e12 / 2),
                 "traffic_note": "dram bytes per face of a 128^3 ncu capture x faces per launch"
                 if traffic is not None else "no ncu traffic figure for this kernel and precision",
                 "avg_launch_ms": avg_s * 1e3, "hbm_context": hbm_ctx, "time_share": share}
@@ -644,6 +654,7 @@ def fp32_c2p_roofline(prof, ms, zones):
     return {"kernel": "c2p", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_unit": FLOPS64[32]["c2p"], "units_per_launch": zones,
             "fp64_pipe_busy_ncu": FP64_PIPE_BUSY[32]["c2p"], "avg_launch_ms": avg_s * 1e3,
+            "fp64_instr_frac": zones * FP64_INSTR[32]["c2p"] / avg_s / (FP64_PEAK_TFLOPS * 1e12 / 2),
             "time_share": {k: round(v[0] / ms, 4) for k, v in prof.items() if v[1] > 0}}
 
 
