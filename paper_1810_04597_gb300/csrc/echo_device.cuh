@@ -493,6 +493,23 @@ __device__ __forceinline__ T mp5_uor(T um2, T um1, T u0, T up1, T up2, int order
 // Accept uor if (uor - u_j)(uor - u_mp) <= eps, u_mp = u_j + minmod(u_{j+1} - u_j,
 // alpha (u_j - u_{j-1})); written with d0 = uor - u_j so that
 // uor - u_mp = d0 - minmod(...).
+// alpha x for the MP5 test (alpha = 4 = 2^2).  FP64: on the integer pipe, by
+// adding 2 to the exponent field -- the same bits as the FP64 product for
+// zero and every normal x below 2^1021; a subnormal x (|x| < 2^-1022, which
+// a difference of two stencil values never is) gives a signed zero.  The
+// product feeds a min/max, so it cannot fuse into an FMA, and on GB300 an
+// FP64 multiply takes a slot of the scarce FP64 pipe.  FP32: the multiply.
+static_assert(MP5_ALPHA == 4.0, "alpha_times assumes alpha = 4");
+template <typename T>
+__device__ __forceinline__ T alpha_times(T x) { return T(MP5_ALPHA) * x; }
+template <>
+__device__ __forceinline__ double alpha_times<double>(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const bool tiny = (b & 0x7ff0000000000000LL) == 0;
+    return __longlong_as_double(tiny ? (b & (long long)0x8000000000000000ULL) : b + (2LL << 52));
+}
+
 // dp = u_{j+1} - u_j and dm = u_j - u_{j-1} come from the caller, which
 // shares them between the two states of a face: the right state's
 // differences are the left stencil's negated (exact in IEEE arithmetic up to
@@ -502,7 +519,7 @@ __device__ __forceinline__ T mp5_try_d(T um2, T um1, T u0, T up1, T up2, T dp, T
 {
     const T uor = mp5_uor(um2, um1, u0, up1, up2, order);
     const T d0 = uor - u0;
-    const T mm = minmod2(dp, T(MP5_ALPHA) * dm);
+    const T mm = minmod2(dp, alpha_times(dm));
     accept = ile(d0 * (d0 - mm), T(MP5_EPS));
     return uor;
 }
