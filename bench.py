@@ -56,8 +56,8 @@ KMODEL = {
 # Newton iteration count (2.74 per call there); faces_y/z run the code of
 # faces_x with other strides.
 FLOPS64 = {
-    64: {"faces_x": 540.5, "faces_y": 540.5, "faces_z": 540.5,
-         "emf_x": 290.7, "emf_y": 290.7, "emf_z": 290.7,
+    64: {"faces_x": 520.2, "faces_y": 520.2, "faces_z": 520.2,
+         "emf_x": 273.4, "emf_y": 273.4, "emf_z": 273.4,
          "c2p": 412.5, "update": 79.0},
     # FP32-bulk path: only c2p computes in FP64 (previous-stage Z refined in
     # FP32, then 1.01 FP64 Newton iterations per call)
@@ -68,7 +68,7 @@ FLOPS64 = {
 # the pipe's 2 slots per SM and clock give the pipe-time view beside the flop
 # roofline (DADD and DMUL are one flop for a full slot).
 FP64_INSTR = {
-    64: {"faces_x": 391.9, "faces_y": 391.9, "faces_z": 391.9, "emf_x": 222.0, "emf_y": 222.0, "emf_z": 222.0,
+    64: {"faces_x": 371.6, "faces_y": 371.6, "faces_z": 371.6, "emf_x": 204.7, "emf_y": 204.7, "emf_z": 204.7,
          "c2p": 298.4, "update": 53.0},
     32: {"c2p": 102.0},
 }
@@ -76,13 +76,13 @@ FP64_INSTR = {
 # per SM and clock x 2 flop x 2.07 GHz (the 1.25 TFLOP/s nominal figure).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per face of faces_x (dram__bytes_read.sum + dram__bytes_write.sum
-# of the same 128^3 ncu launch: 338,365,440 B over 2,316,324 faces); scaled to a
+# of the same 128^3 ncu launch: 338,767,872 B over 2,316,324 faces); scaled to a
 # launch by the faces it processes.
-TRAFFIC_PER_FACE64 = 338365440 / 2316324
+TRAFFIC_PER_FACE64 = 338767872 / 2316324
 # FP64 pipe activity in those captures
 # (sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active).
-FP64_PIPE_BUSY = {64: {"faces_x": 0.859, "faces_y": 0.859, "faces_z": 0.859, "emf_x": 0.849, "emf_y": 0.849,
-                       "emf_z": 0.849, "c2p": 0.861, "update": 0.832},
+FP64_PIPE_BUSY = {64: {"faces_x": 0.864, "faces_y": 0.864, "faces_z": 0.864, "emf_x": 0.854, "emf_y": 0.854,
+                       "emf_z": 0.854, "c2p": 0.861, "update": 0.834},
                   32: {"c2p": 0.850}}
 
 
