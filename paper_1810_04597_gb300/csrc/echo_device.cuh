@@ -493,22 +493,32 @@ __device__ __forceinline__ T mp5_uor(T um2, T um1, T u0, T up1, T up2, int order
 // Accept uor if (uor - u_j)(uor - u_mp) <= eps, u_mp = u_j + minmod(u_{j+1} - u_j,
 // alpha (u_j - u_{j-1})); written with d0 = uor - u_j so that
 // uor - u_mp = d0 - minmod(...).
-// alpha x for the MP5 test (alpha = 4 = 2^2).  FP64: on the integer pipe, by
-// adding 2 to the exponent field -- the same bits as the FP64 product for
-// zero and every normal x below 2^1021; a subnormal x (|x| < 2^-1022, which
-// a difference of two stencil values never is) gives a signed zero.  The
-// product feeds a min/max, so it cannot fuse into an FMA, and on GB300 an
-// FP64 multiply takes a slot of the scarce FP64 pipe.  FP32: the multiply.
+// x 2^E for FP64 on the integer pipe, by adding E to the exponent field:
+// the same bits as the FP64 product for zero and every normal x whose
+// product is normal; a subnormal x (below 2^-1022 in magnitude, which none
+// of the quantities scaled here ever is) gives a signed zero.  On GB300 an
+// FP64 multiply takes a slot of the scarce FP64 pipe; where the product
+// cannot fuse into an FMA this saves that slot.
+template <int E>
+__device__ __forceinline__ double scale2(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const bool tiny = (b & 0x7ff0000000000000LL) == 0;
+    long long r;
+    if constexpr (E >= 0)
+        r = b + ((long long)E << 52);
+    else
+        r = b - ((long long)(-E) << 52);
+    return __longlong_as_double(tiny ? (b & (long long)0x8000000000000000ULL) : r);
+}
+
+// alpha x for the MP5 test (alpha = 4 = 2^2): the product feeds a min/max,
+// so it cannot fuse into an FMA.  FP64: scale2; FP32: the multiply.
 static_assert(MP5_ALPHA == 4.0, "alpha_times assumes alpha = 4");
 template <typename T>
 __device__ __forceinline__ T alpha_times(T x) { return T(MP5_ALPHA) * x; }
 template <>
-__device__ __forceinline__ double alpha_times<double>(double x)
-{
-    const long long b = __double_as_longlong(x);
-    const bool tiny = (b & 0x7ff0000000000000LL) == 0;
-    return __longlong_as_double(tiny ? (b & (long long)0x8000000000000000ULL) : b + (2LL << 52));
-}
+__device__ __forceinline__ double alpha_times<double>(double x) { return scale2<2>(x); }
 
 // dp = u_{j+1} - u_j and dm = u_j - u_{j-1} come from the caller, which
 // shares them between the two states of a face: the right state's
@@ -788,6 +798,8 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
     const double SB2 = SB * SB;
     const double B2 = Bl[0] * B[0] + Bl[1] * B[1] + Bl[2] * B[2];
     const double Uen = tau + Dc;
+    // halves used every iteration, exact on the integer pipe
+    const double hB2 = scale2<-1>(B2), hSB2 = scale2<-1>(SB2), hD = scale2<-1>(Dc);
     C2PResult r;
     double Z = Zguess, iZ = 0.0, iZB = 0.0, v2 = 0.0;
     if (refine && is_pos(Z))
@@ -818,11 +830,12 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
         const double sq = om * isq;
         const double p = gm1g * (Z * om - Dc * sq);
         const double iZ2 = iZ * iZ;
-        const double f = Z - p + 0.5 * (1.0 + v2) * B2 - 0.5 * SB2 * iZ2 - Uen;
+        const double f = Z - p + (1.0 + v2) * hB2 - hSB2 * iZ2 - Uen;
         const double iZB3 = iZB * iZB * iZB;
-        const double dv2 = -2.0 * (S2 * Z * Z * Z + SB2 * (3.0 * Z * Z + 3.0 * Z * B2 + B2 * B2)) * iZ2 * iZ * iZB3;
-        const double dp = gm1g * (om - Z * dv2 + 0.5 * Dc * dv2 * isq);
-        const double fp = 1.0 - dp + 0.5 * B2 * dv2 + SB2 * iZ2 * iZ;
+        // dv^2/dZ = -2 (S^2 Z^3 + (S.B)^2 (3 Z^2 + 3 Z B^2 + B^4)) / (Z^3 (Z + B^2)^3)
+        const double dv2 = -(scale2<1>(S2 * Z * Z * Z + SB2 * (3.0 * Z * Z + 3.0 * Z * B2 + B2 * B2)) * iZ2 * iZ * iZB3);
+        const double dp = gm1g * (om - Z * dv2 + hD * dv2 * isq);
+        const double fp = 1.0 - dp + hB2 * dv2 + SB2 * iZ2 * iZ;
         double dZ = nr_div(f, fp);
         // A step within the tolerance ends the iteration: Z, 1/Z, 1/(Z + B^2),
         // v^2 and sqrt(1 - v^2) move along their first derivatives instead of
