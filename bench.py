@@ -58,10 +58,10 @@ KMODEL = {
 FLOPS64 = {
     64: {"faces_x": 520.2, "faces_y": 520.2, "faces_z": 520.2,
          "emf_x": 273.4, "emf_y": 273.4, "emf_z": 273.4,
-         "c2p": 412.5, "update": 79.0},
+         "c2p": 403.5, "update": 79.0},
     # FP32-bulk path: only c2p computes in FP64 (previous-stage Z refined in
     # FP32, then 1.01 FP64 Newton iterations per call)
-    32: {"c2p": 139.0},
+    32: {"c2p": 134.0},
 }
 # FP64 arithmetic instructions (DFMA + DADD + DMUL thread instructions) per
 # unit from the same captures: each takes one FP64-pipe slot, so these over
@@ -69,8 +69,8 @@ FLOPS64 = {
 # roofline (DADD and DMUL are one flop for a full slot).
 FP64_INSTR = {
     64: {"faces_x": 371.6, "faces_y": 371.6, "faces_z": 371.6, "emf_x": 204.7, "emf_y": 204.7, "emf_z": 204.7,
-         "c2p": 298.4, "update": 53.0},
-    32: {"c2p": 102.0},
+         "c2p": 289.4, "update": 53.0},
+    32: {"c2p": 97.0},
 }
 # FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 DFMA lanes
 # per SM and clock x 2 flop x 2.07 GHz (the 1.25 TFLOP/s nominal figure).
@@ -82,8 +82,8 @@ TRAFFIC_PER_FACE64 = 338767872 / 2316324
 # FP64 pipe activity in those captures
 # (sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active).
 FP64_PIPE_BUSY = {64: {"faces_x": 0.864, "faces_y": 0.864, "faces_z": 0.864, "emf_x": 0.854, "emf_y": 0.854,
-                       "emf_z": 0.854, "c2p": 0.861, "update": 0.834},
-                  32: {"c2p": 0.850}}
+                       "emf_z": 0.854, "c2p": 0.863, "update": 0.834},
+                  32: {"c2p": 0.852}}
 
 
 def kernel_units(name, n):
