@@ -339,6 +339,13 @@ int echo_selftest_conversions(long long n, unsigned long long seed, unsigned lon
  * hashed values (both signs, exponents -300..300): atomically maxes the
  * largest distance in ulp into *dev_max_ulp (device, caller-zeroed). */
 int echo_selftest_recip(long long n, unsigned long long seed, unsigned long long *dev_max_ulp, void *cuda_stream);
+/* Self-check of the library's integer-pipe scaling by powers of two (the
+ * exponent-field add the FP64 kernels use for alpha times a difference in
+ * the MP5 test and for the halves and doublings of the c2p Newton step)
+ * against the FP64 products x*4, x*2, x*0.5 on n hashed values (both signs,
+ * exponents -1000..1000, and signed zeros): adds the number of bit-pattern
+ * mismatches to *dev_mismatch (device, caller-zeroed). */
+int echo_selftest_scale2(long long n, unsigned long long seed, unsigned long long *dev_mismatch, void *cuda_stream);
 
 /* Kernel classes timed by the profiling facility below (ECHO_K_C2P includes
  * the network's own pass when the guess mode runs one). */

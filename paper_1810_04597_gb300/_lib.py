@@ -99,6 +99,7 @@ _SIGS = {
     "echo_counters": (ctypes.c_int, [_P, ctypes.POINTER(echo_totals)]),
     "echo_selftest_conversions": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_selftest_recip": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
+    "echo_selftest_scale2": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
     "echo_batch_workspace_bytes": (ctypes.c_size_t, [_P]),
     "echo_batch_bind": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
@@ -437,6 +438,11 @@ def echo_batch_step(b, dt=0.0):
 
 def echo_batch_destroy(b):
     load().echo_batch_destroy(b)
+
+
+def echo_selftest_scale2(n, seed, dev_mismatch, stream_handle: int = 0):
+    _plain(load().echo_selftest_scale2(int(n), ctypes.c_ulonglong(seed), _P(_dev_any(dev_mismatch, "mismatch")),
+                                       _P(stream_handle)), "echo_selftest_scale2")
 
 
 def echo_selftest_recip(n, seed, dev_max, stream_handle: int = 0):

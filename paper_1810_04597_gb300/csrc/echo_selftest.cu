@@ -76,7 +76,44 @@ __global__ void k_check_recip(long long n, unsigned long long seed, unsigned lon
     atomicMax(max_ulp, dist);
 }
 
+// scale2<E>(x) against the FP64 product x * 2^E for E = 2, 1, -1 on hashed
+// x of both signs with exponents across [-1000, 1000] (products normal) and
+// on signed zeros; counts the mismatching bit patterns.
+__global__ void k_check_scale2(long long n, unsigned long long seed, unsigned long long *mismatch)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const unsigned long long h = mix64(seed ^ (unsigned long long)i);
+    const unsigned long long e = 1023ULL - 1000ULL + (h >> 52) % 2001ULL;
+    const unsigned long long m = mix64(h) & 0xfffffffffffffULL;
+    const unsigned long long sign = (h & 1ULL) << 63;
+    const double x = (i & 1023) == 0 ? __longlong_as_double((long long)sign)
+                                      : __longlong_as_double((long long)(sign | (e << 52) | m));
+    unsigned long long bad = 0;
+    if (__double_as_longlong(scale2<2>(x)) != __double_as_longlong(x * 4.0))
+        ++bad;
+    if (__double_as_longlong(scale2<1>(x)) != __double_as_longlong(x * 2.0))
+        ++bad;
+    if (__double_as_longlong(scale2<-1>(x)) != __double_as_longlong(x * 0.5))
+        ++bad;
+    if (__double_as_longlong(alpha_times(x)) != __double_as_longlong(MP5_ALPHA * x))
+        ++bad;
+    if (bad)
+        atomicAdd(mismatch, bad);
+}
+
 }  // namespace echo
+
+extern "C" int echo_selftest_scale2(long long n, unsigned long long seed, unsigned long long *dev_mismatch,
+                                    void *stream)
+{
+    if (n < 1 || !dev_mismatch)
+        return ECHO_EINVAL;
+    echo::k_check_scale2<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, seed,
+                                                                                                   dev_mismatch);
+    return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
+}
 
 extern "C" int echo_selftest_recip(long long n, unsigned long long seed, unsigned long long *dev_max_ulp, void *stream)
 {

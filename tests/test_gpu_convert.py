@@ -34,6 +34,18 @@ def test_newton_raphson_reciprocal_within_two_ulp():
     assert int(mx.item()) <= 2
 
 
+def test_integer_pipe_scaling_matches_fp64_products():
+    """scale2 / alpha_times (exponent-field adds on the integer pipe) give
+    the bit patterns of the FP64 products x*4, x*2, x*0.5 on 8 M values."""
+    import torch
+    from paper_1810_04597_gb300 import _lib
+    bad = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for seed in (6, 7):
+        _lib.echo_selftest_scale2(1 << 22, seed, bad)
+    torch.cuda.synchronize()
+    assert int(bad.item()) == 0
+
+
 @pytest.mark.parametrize("precision", [64, 32])
 def test_fp32_refined_guess_converges_to_the_same_state(precision):
     """Guess mode +4 (FP32 Newton pre-refinement): same converged state as the
