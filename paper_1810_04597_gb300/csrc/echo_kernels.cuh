@@ -888,23 +888,21 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
                 Est[s][u] = -(va[s][u] * Bb[s] - vb[s][u] * Ba[u]);
         }
     const T sA = apa + ama, sB = apb + amb;
-    T wLL, wLR, wRL, wRR, da, db;
     if (is_pos(sA) && is_pos(sB)) {
-        // one division: 1/sA = sB iden, 1/sB = sA iden
-        const T iden = fast_recip(sA * sB);
-        wLL = apa * apb * iden;
-        wLR = apa * amb * iden;
-        wRL = ama * apb * iden;
-        wRR = ama * amb * iden;
-        da = apa * ama * (sB * iden);
-        db = apb * amb * (sA * iden);
+        // the whole expression over the common denominator sA sB, nested so
+        // that the weights are never formed: one division, one final product
+        const T t0 = fma(apb, Est[0][0], amb * Est[0][1]);
+        const T t1 = fma(apb, Est[1][0], amb * Est[1][1]);
+        T u = fma(apa, t0, ama * t1);
+        u = fma(apa * ama * sB, Bb[1] - Bb[0], u);
+        u = fma(-(apb * amb * sA), Ba[1] - Ba[0], u);
+        A.E[E][id] = u * fast_recip(sA * sB);
     } else {
-        wLL = wLR = wRL = wRR = T(0.25);
-        da = is_pos(sA) ? apa * ama / sA : T(0);
-        db = is_pos(sB) ? apb * amb / sB : T(0);
+        const T da = is_pos(sA) ? apa * ama / sA : T(0);
+        const T db = is_pos(sB) ? apb * amb / sB : T(0);
+        A.E[E][id] = T(0.25) * (Est[0][0] + Est[0][1] + Est[1][0] + Est[1][1]) + da * (Bb[1] - Bb[0])
+                     - db * (Ba[1] - Ba[0]);
     }
-    A.E[E][id] = wLL * Est[0][0] + wLR * Est[0][1] + wRL * Est[1][0] + wRR * Est[1][1]
-                 + da * (Bb[1] - Bb[0]) - db * (Ba[1] - Ba[0]);
 }
 
 template <int E, int MK, typename R>
