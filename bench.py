@@ -57,7 +57,7 @@ KMODEL = {
 # faces_x with other strides.
 FLOPS64 = {
     64: {"faces_x": 520.2, "faces_y": 520.2, "faces_z": 520.2,
-         "emf_x": 273.4, "emf_y": 273.4, "emf_z": 273.4,
+         "emf_x": 266.4, "emf_y": 266.4, "emf_z": 266.4,
          "c2p": 403.5, "update": 79.0},
     # FP32-bulk path: only c2p computes in FP64 (previous-stage Z refined in
     # FP32, then 1.01 FP64 Newton iterations per call)
@@ -68,7 +68,7 @@ FLOPS64 = {
 # the pipe's 2 slots per SM and clock give the pipe-time view beside the flop
 # roofline (DADD and DMUL are one flop for a full slot).
 FP64_INSTR = {
-    64: {"faces_x": 371.6, "faces_y": 371.6, "faces_z": 371.6, "emf_x": 204.7, "emf_y": 204.7, "emf_z": 204.7,
+    64: {"faces_x": 371.6, "faces_y": 371.6, "faces_z": 371.6, "emf_x": 197.7, "emf_y": 197.7, "emf_z": 197.7,
          "c2p": 289.4, "update": 53.0},
     32: {"c2p": 97.0},
 }
