@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float *__restrict__ P
         out[r * 3 + q] = (o[q] - P[MLP_ONORM + 2 * MLP_NI + q]) / P[MLP_ONORM + 2 * MLP_NI + MLP_NO + q];
 }
 
-// Forward pass with the hidden layer on the tensor cores (persistent CTAs of
-// 128 rows); standardised outputs like k_mlp_forward, NaN where the
+// Forward pass with both hidden layers on the tensor cores (persistent CTAs
+// of 128 rows); standardised outputs like k_mlp_forward, NaN where the
 // tensor-core result did not arrive.
 __global__ void __launch_bounds__(128) k_mlp_forward_tc(const float *__restrict__ P, const float *__restrict__ x,
                                                         long long n, float *__restrict__ out, long long ntiles)

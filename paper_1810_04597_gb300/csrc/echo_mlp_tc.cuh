@@ -1,6 +1,7 @@
-// echo_mlp_tc.cuh -- the c2p-guess network with its 64x64 hidden layer on
-// the 5th-generation tensor cores (tcgen05), for CTAs of 128 threads that
-// each own one row (one cell or one feature row).
+// echo_mlp_tc.cuh -- the c2p-guess network with the products of both
+// hidden layers (9 -> 64 and 64 -> 64) on the 5th-generation tensor cores
+// (tcgen05), for CTAs of 128 threads that each own one row (one cell or one
+// feature row).
 //
 // Per tile of 128 rows:
 //   1. every thread standardises its 9 features in FP32 and writes them as
