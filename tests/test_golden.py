@@ -21,3 +21,10 @@ def test_alfven_speed_closed_form():
 def test_mp5_jump_values(orc):
     for row in _rows("mp5_steps.txt"):
         assert orc.mp5_face(row[:5]) == row[5]
+
+
+def test_mp5_bound_values(orc):
+    """The limited value where u_UL, u_LC and u_MD in turn bound the
+    interval; the result is u_or + (bound - u_or), one rounding each."""
+    for row in _rows("mp5_bounds.txt"):
+        assert abs(orc.mp5_face(row[:5]) - row[5]) <= 4e-16 * max(1.0, abs(row[5]))

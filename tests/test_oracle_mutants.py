@@ -12,11 +12,14 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 OUT = os.path.join(ORACLE, "_build", "mutants")
-PINS = ["tests/test_oracle_pointwise.py", "tests/test_oracle_scheme.py", "tests/test_golden.py"]
+PINS = ["tests/test_golden.py", "tests/test_oracle_pointwise.py", "tests/test_oracle_scheme.py"]
 MLP_PINS = ["tests/test_oracle_mlp.py"]
 HO_PINS = ["tests/test_oracle_high_order.py"]
 
-# (name, file, original text, planted text, pin files)
+# (name, file, original text, planted text, pin files).  Not listed: a
+# change to the sign factors of minmod4's last two arguments, which is an
+# equivalent mistake for the arguments MP5 passes (4a - b and 4b - a of one
+# sign force a and b to that sign).
 MUTANTS = [
     ("uct_diffusion_sign", "echo_oracle.c", "+ da * (Bb[1] - Bb[0]) - db * (Ba[1] - Ba[0])",
      "- da * (Bb[1] - Bb[0]) - db * (Ba[1] - Ba[0])", PINS),
@@ -39,6 +42,28 @@ MUTANTS = [
     ("ho_point_value_weight", "echo_oracle.c", "90.0 * u0", "91.0 * u0", HO_PINS),
     ("ho_centre_weight", "echo_oracle.c", "150.0 * b6[2] + 150.0 * b6[3]", "150.0 * b6[2] + 149.0 * b6[3]",
      HO_PINS),
+    ("c2p_derivative_factor", "echo_oracle.c", "double dv2 = -2.0 * (S2", "double dv2 = -1.0 * (S2", PINS),
+    ("c2p_recovery_sign", "echo_oracle.c", "vl[j] = (S[j] + SB * Bl[j] / Z) / (Z + B2);",
+     "vl[j] = (S[j] - SB * Bl[j] / Z) / (Z + B2);", PINS),
+    ("rk3_stage_weights", "echo_oracle.c", "u[id] = 0.75 * u0[id] + 0.25 * (u[id] + dt * l[id]);",
+     "u[id] = 0.25 * u0[id] + 0.75 * (u[id] + dt * l[id]);", PINS),
+    ("ct_curl_sign", "echo_oracle.c", "G->LB[d][id] = -(dEb_da - dEa_db);", "G->LB[d][id] = (dEb_da - dEa_db);",
+     PINS),
+    ("cfl_max_instead_of_sum", "echo_oracle.c", "s += fmax(fabs(lp), fabs(lm)) / c->dx[d];",
+     "s = fmax(s, fmax(fabs(lp), fabs(lm)) / c->dx[d]);", PINS),
+    ("hll_diffusion_sign", "echo_oracle.c", "- ap * am * (UR[q] - UL[q])) / s;", "+ ap * am * (UR[q] - UL[q])) / s;",
+     PINS),
+    ("mp5_limiter_alpha", "echo_oracle.c", "double uul = u0 + MP5_ALPHA * (u0 - um1);",
+     "double uul = u0 + 2.0 * (u0 - um1);", PINS),
+    ("mp5_lc_coefficient", "echo_oracle.c", "4.0 / 3.0 * dMm", "3.0 / 4.0 * dMm", PINS),
+    ("mp5_curvature_side", "echo_oracle.c", "double dMp = minmod4(4.0 * d0 - dp1, 4.0 * dp1 - d0, d0, dp1);",
+     "double dMp = minmod4(4.0 * d0 - dm1, 4.0 * dm1 - d0, d0, dm1);", PINS),
+    ("mp5_minmod4_dropped_operand", "echo_oracle.c", "fmin(fmin(fabs(w), fabs(x)), fmin(fabs(y), fabs(z)))",
+     "fmin(fmin(fabs(w), fabs(x)), fabs(y))", PINS),
+    ("mp5_bounds_min_max", "echo_oracle.c", "double umin = fmax(fmin(fmin(u0, up1), umd)",
+     "double umin = fmin(fmin(fmin(u0, up1), umd)", PINS),
+    ("mp5_test_direction", "echo_oracle.c", "if ((uor - u0) * (uor - ump) <= MP5_EPS)",
+     "if ((uor - u0) * (uor - ump) >= MP5_EPS)", PINS),
 ]
 
 
