@@ -91,6 +91,8 @@ def lib():
         L.oracle_ho_flux.restype = d
         L.oracle_ho_center.argtypes = [pd]
         L.oracle_ho_center.restype = d
+        L.oracle_ghosts.restype = i
+        L.oracle_fill_padded.argtypes = [pc, pd, i, i]
         L.oracle_speeds_point.argtypes = [pc, pd, pd, i, pd, pd]
         L.oracle_flux_point.argtypes = [pc, pd, pd, i, pd, pd]
         L.oracle_hll.argtypes = [pd, pd, pd, pd, d, d, pd]
@@ -207,6 +209,23 @@ def ho_flux(f5):
 def ho_center(b6):
     """Sixth-order midpoint interpolation of six equally spaced values."""
     return lib().oracle_ho_center(_dp(_f64(b6)))
+
+
+def ghosts() -> int:
+    """Ghost layers per side of the oracle's padded arrays."""
+    return int(lib().oracle_ghosts())
+
+
+def fill_padded(cfg: OCfg, a: np.ndarray, comp: int, face: int) -> np.ndarray:
+    """The oracle's ghost fill applied to a copy of a padded array of shape
+    (n2 + 2g, n1 + 2g, n0 + 2g); comp = the vector component it holds (-1
+    for a scalar), face = its face direction (-1 for a cell array)."""
+    g = ghosts()
+    shape = tuple(cfg.n[2 - k] + 2 * g for k in range(3))
+    out = _f64(a).copy()
+    assert out.shape == shape, (out.shape, shape)
+    lib().oracle_fill_padded(ctypes.byref(cfg), _dp(out), int(comp), int(face))
+    return out
 
 
 def mp5_unlimited(u5) -> float:

@@ -1337,6 +1337,25 @@ double oracle_mp5_face_order(const double *u5, int order)
 double oracle_ho_flux(const double *f5) { return ho_flux(f5); }
 double oracle_ho_center(const double *b6) { return ho_center(b6); }
 
+/* Ghost layers per side of every padded array. */
+int oracle_ghosts(void) { return NG; }
+
+/* Ghost fill of one padded array (n[d] + 2 NG entries along each d, x
+ * fastest; a face array holds face i-1/2 at index i) with the grid's
+ * boundary conditions: the routine every step uses, exposed for the
+ * boundary-condition pins.  comp and face as in fill_array. */
+void oracle_fill_padded(const ocfg *c, double *a, int comp, int face)
+{
+    ogrid G;
+    memset(&G, 0, sizeof(G));
+    for (int d = 0; d < 3; ++d) {
+        G.n[d] = c->n[d];
+        G.np[d] = c->n[d] + 2 * NG;
+    }
+    G.ncell = (size_t)G.np[0] * G.np[1] * G.np[2];
+    fill_array(c, &G, a, comp, face);
+}
+
 /* Unlimited fifth-order value, for the polynomial-exactness pin. */
 double oracle_mp5_unlimited(const double *u5)
 {

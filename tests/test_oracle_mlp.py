@@ -70,3 +70,18 @@ def test_adam_first_step_is_signed_learning_rate(orc):
     v = np.zeros(4995)
     orc.mlp_adam(P, m, v, g, 1, lr=1e-2, eps=1e-8)
     assert np.allclose(P - P0, -1e-2 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+
+
+def test_adam_steps_under_constant_gradient(orc):
+    """With a constant gradient the bias-corrected moments are exactly g and
+    g^2 at every t (m_t = (1 - b1^t) g, v_t = (1 - b2^t) g^2), so each of the
+    first steps is again -lr g / (|g| + eps)."""
+    rng = np.random.default_rng(3)
+    P = rng.normal(size=4995)
+    g = rng.normal(size=4995)
+    m = np.zeros(4995)
+    v = np.zeros(4995)
+    for t in range(1, 6):
+        P0 = P.copy()
+        orc.mlp_adam(P, m, v, g, t, lr=1e-2, eps=1e-8)
+        assert np.allclose(P - P0, -1e-2 * g / (np.abs(g) + 1e-8), rtol=1e-9, atol=1e-15), t

@@ -12,7 +12,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 OUT = os.path.join(ORACLE, "_build", "mutants")
-PINS = ["tests/test_golden.py", "tests/test_oracle_pointwise.py", "tests/test_oracle_scheme.py"]
+PINS = ["tests/test_golden.py", "tests/test_oracle_boundaries.py", "tests/test_oracle_pointwise.py",
+        "tests/test_oracle_scheme.py"]
 MLP_PINS = ["tests/test_oracle_mlp.py"]
 HO_PINS = ["tests/test_oracle_high_order.py"]
 
@@ -64,6 +65,23 @@ MUTANTS = [
      "double umin = fmin(fmin(fmin(u0, up1), umd)", PINS),
     ("mp5_test_direction", "echo_oracle.c", "if ((uor - u0) * (uor - ump) <= MP5_EPS)",
      "if ((uor - u0) * (uor - ump) >= MP5_EPS)", PINS),
+    ("adam_bias_correction_constant", "mlp_oracle.c", "double c1 = 1.0 - pow(b1, t), c2", "double c1 = 1.0 - b1, c2",
+     MLP_PINS),
+    ("bc_outflow_offset", "echo_oracle.c", "return side == 0 ? lo : hi;", "return side == 0 ? lo + 1 : hi;", PINS),
+    ("bc_axis_mirror_offset", "echo_oracle.c", "return side == 0 ? 2 * NG - 1 - i : 2 * (NG + n) - 1 - i;",
+     "return side == 0 ? 2 * NG - i : 2 * (NG + n) - 1 - i;", PINS),
+    ("bc_axis_no_flip", "echo_oracle.c", "if (flip && comp == d)", "if (flip && comp == -2)", PINS),
+    ("coord_centre_shift", "echo_oracle.c", "+ 0.5 + off) * c->dx[d];", "+ off) * c->dx[d];", PINS),
+    ("floor_power_sign", "echo_oracle.c", "return f0 * pow(exp(x1), pw);", "return f0 * pow(exp(x1), -pw);", PINS),
+    ("c2p_v2_term", "echo_oracle.c", "SB * SB * (2.0 * Z + B2)) / (Z * Z * ZB * ZB)",
+     "SB * SB * (Z + B2)) / (Z * Z * ZB * ZB)", PINS),
+    ("p2c_dropped_vb", "echo_oracle.c", "0.5 * (B2 + B2 * v2 - vB * vB)", "0.5 * (B2 + B2 * v2)", PINS),
+    ("speeds_shift_sign", "echo_oracle.c", "*lp = m->alpha / den * (vd * (1.0 - a2) + sq) - m->beta[d];",
+     "*lp = m->alpha / den * (vd * (1.0 - a2) + sq) + m->beta[d];", PINS),
+    ("flux_tau_shift_sign", "echo_oracle.c", "F[4] = m->alpha * (Su[d] - C[0] * v[d]) - m->beta[d] * C[4];",
+     "F[4] = m->alpha * (Su[d] - C[0] * v[d]) + m->beta[d] * C[4];", PINS),
+    ("c2p_pressure_dropped_root", "echo_oracle.c", "double p = gg * (Z * (1.0 - v2) - D * sq);",
+     "double p = gg * (Z * (1.0 - v2) - D);", PINS),
 ]
 
 

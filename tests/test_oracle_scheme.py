@@ -39,6 +39,78 @@ def test_cfl_dt_at_rest(orc):
     assert abs(dts[0] - 0.4 * prob.dx[0] / (3 * cs)) <= 1e-15
 
 
+def test_ssp_rk3_is_third_order_in_time(orc):
+    """Fixed grid, fixed end time: halving dt shrinks the difference to a
+    fine-dt solution eight-fold (Shu & Osher's scheme is third order)."""
+    prob = inputs.linear_wave(16)
+    cfg, st0, Z0 = setup(orc, prob)
+    T = 3.2 * prob.dx[0]
+
+    def run(m):
+        s, _, _, _ = orc.steps(cfg, st0.copy(), Z0.copy(), m, T / m)
+        return s
+
+    ref = run(64)
+    e = [np.max(np.abs(run(m) - ref)) for m in (4, 8, 16)]
+    for r in (e[0] / e[1], e[1] / e[2]):
+        assert 7.0 <= r <= 9.5, e
+
+
+def _ks_patch(orc, n=(4, 3, 2), floors=0):
+    c = orc.OCfg()
+    for d, (x0, dx) in enumerate(((np.log(4.0), 0.15), (1.0, 0.2), (0.3, 0.3))):
+        c.n[d] = n[d]
+        c.x0[d] = x0
+        c.dx[d] = dx
+    for k, b in enumerate((1, 1, 2, 2, 0, 0)):
+        c.bc[k] = b
+    c.metric, c.spin, c.gamma, c.cfl = 1, 0.9, 4.0 / 3.0, 0.4
+    c.floors, c.rho_floor, c.rho_floor_pow, c.p_floor, c.p_floor_pow = floors, 1e-4, -1.5, 1e-6, -2.5
+    return c
+
+
+def test_cell_centres_of_the_grid(orc):
+    """Cell (i, j, k) holds the state at x0 + (i + 1/2, j + 1/2, k + 1/2) dx:
+    the grid's conserved state on a Kerr-Schild patch is the pointwise map
+    at those coordinates, times sqrt(gamma) there."""
+    cfg = _ks_patch(orc)
+    n = list(cfg.n)
+    N = n[0] * n[1] * n[2]
+    rng = np.random.default_rng(41)
+    prims = np.zeros((5, n[2], n[1], n[0]))
+    prims[0] = rng.uniform(0.5, 1.5, prims[0].shape)
+    prims[1:4] = rng.uniform(-0.01, 0.01, prims[1:4].shape)
+    prims[4] = rng.uniform(0.1, 1.0, prims[4].shape)
+    st, _ = orc.p2c(cfg, prims, np.zeros(orc.state_count(n) - 5 * N))
+    for k in range(n[2]):
+        for j in range(n[1]):
+            for i in range(n[0]):
+                x = [cfg.x0[d] + (idx + 0.5) * cfg.dx[d] for d, idx in enumerate((i, j, k))]
+                P8 = np.concatenate([prims[:, k, j, i], np.zeros(3)])
+                C = orc.p2c_point(cfg, x, P8) * orc.metric_point(cfg, x)["sqrtg"]
+                h = (k * n[1] + j) * n[0] + i
+                got = st[np.arange(5) * N + h]
+                assert np.allclose(got, C, rtol=1e-14, atol=0.0), (i, j, k)
+
+
+def test_floor_law(orc):
+    """Atmosphere floors rho_0 r^k_rho and p_0 r^k_p at each cell's radius
+    r = exp(x1): a state far below both comes out of the inversion on them."""
+    cfg = _ks_patch(orc, floors=1)
+    n = list(cfg.n)
+    N = n[0] * n[1] * n[2]
+    prims = np.zeros((5, n[2], n[1], n[0]))
+    prims[0] = 1e-9
+    prims[4] = 1e-12
+    st, Z = orc.p2c(cfg, prims, np.zeros(orc.state_count(n) - 5 * N))
+    P, _, stats, _ = orc.c2p(cfg, st, Z)
+    r = np.exp(cfg.x0[0] + (np.arange(n[0]) + 0.5) * cfg.dx[0])
+    r = np.broadcast_to(r[None, None, :], (n[2], n[1], n[0])).reshape(-1)
+    assert np.allclose(P[0], 1e-4 * r ** -1.5, rtol=1e-14, atol=0.0)
+    assert np.allclose(P[4], 1e-6 * r ** -2.5, rtol=1e-14, atol=0.0)
+    assert stats["floors"] == N
+
+
 @pytest.fixture(scope="module")
 def box32(orc):
     prob = inputs.smooth_box(32)
