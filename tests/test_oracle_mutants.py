@@ -80,6 +80,9 @@ MUTANTS = [
      "*lp = m->alpha / den * (vd * (1.0 - a2) + sq) + m->beta[d];", PINS),
     ("flux_tau_shift_sign", "echo_oracle.c", "F[4] = m->alpha * (Su[d] - C[0] * v[d]) - m->beta[d] * C[4];",
      "F[4] = m->alpha * (Su[d] - C[0] * v[d]) + m->beta[d] * C[4];", PINS),
+    ("divb_spacing", "echo_oracle.c", "dv += (bf[1] - bf[0]) / c->dx[d];", "dv += (bf[1] - bf[0]) / c->dx[0];",
+     PINS),
+    ("energy_total_component", "echo_oracle.c", "sT += G.U[4][id] * dV;", "sT += G.U[3][id] * dV;", PINS),
     ("c2p_pressure_dropped_root", "echo_oracle.c", "double p = gg * (Z * (1.0 - v2) - D * sq);",
      "double p = gg * (Z * (1.0 - v2) - D);", PINS),
 ]

@@ -111,6 +111,34 @@ def test_floor_law(orc):
     assert stats["floors"] == N
 
 
+def test_reduce_totals_and_divergence(orc):
+    """The totals are the volume sums of the stored conserved arrays; the
+    face field B~ = (2x, -y, 3z) at the face centres (outflow box, every
+    face owned) has the discrete divergence 2 - 1 + 3 = 4 in every cell
+    (the spacings differ, so no other pairing of differences and spacings
+    gives 4)."""
+    n = (5, 4, 3)
+    c = orc.OCfg()
+    for d, (x0, dx) in enumerate(((0.3, 0.1), (-0.2, 0.2), (0.1, 0.3))):
+        c.n[d], c.x0[d], c.dx[d] = n[d], x0, dx
+    for k in range(6):
+        c.bc[k] = 1
+    c.gamma = 4.0 / 3.0
+    rng = np.random.default_rng(42)
+    cells = rng.normal(size=(5, n[2], n[1], n[0]))
+    xf = [c.x0[d] + np.arange(n[d] + 1) * c.dx[d] for d in range(3)]
+    bx = np.broadcast_to(2.0 * xf[0][None, None, :], (n[2], n[1], n[0] + 1))
+    by = np.broadcast_to(-xf[1][None, :, None], (n[2], n[1] + 1, n[0]))
+    bz = np.broadcast_to(3.0 * xf[2][:, None, None], (n[2] + 1, n[1], n[0]))
+    st = np.concatenate([cells.reshape(-1), inputs.pack_faces(bx, by, bz)])
+    t = orc.reduce(c, st)
+    dV = c.dx[0] * c.dx[1] * c.dx[2]
+    sums = cells.reshape(5, -1).sum(axis=1) * dV
+    assert np.allclose(t[:2], [sums[0], sums[4]], rtol=1e-13, atol=1e-15)
+    assert np.allclose(t[2:5], sums[1:4], rtol=1e-13, atol=1e-15)
+    assert abs(t[5] - 4.0) <= 1e-13
+
+
 @pytest.fixture(scope="module")
 def box32(orc):
     prob = inputs.smooth_box(32)
