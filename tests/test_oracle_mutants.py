@@ -83,6 +83,13 @@ MUTANTS = [
     ("divb_spacing", "echo_oracle.c", "dv += (bf[1] - bf[0]) / c->dx[d];", "dv += (bf[1] - bf[0]) / c->dx[0];",
      PINS),
     ("energy_total_component", "echo_oracle.c", "sT += G.U[4][id] * dV;", "sT += G.U[3][id] * dV;", PINS),
+    ("source_derivative_weight", "echo_oracle.c", "double wts[6] = {-1.0, 9.0, -45.0, 45.0, -9.0, 1.0};",
+     "double wts[6] = {-1.0, 9.0, -45.0, 45.0, -9.0, 0.0};", PINS),
+    ("source_tau_lapse_sign", "echo_oracle.c", "st -= Su[j] * dal[j];", "st += Su[j] * dal[j];", PINS),
+    ("source_magnetic_pressure", "echo_oracle.c", "(p + 0.5 * b2) * m->gi[i][j]", "(p + b2) * m->gi[i][j]", PINS),
+    ("emf_transport_shift_sign", "echo_oracle.c", "double vta = alpha * va[s][t] - beta[a];",
+     "double vta = alpha * va[s][t] + beta[a];", PINS),
+    ("ks_polar_metric", "echo_oracle.c", "g[1][1] = sig;", "g[1][1] = r * r;", PINS),
     ("c2p_pressure_dropped_root", "echo_oracle.c", "double p = gg * (Z * (1.0 - v2) - D * sq);",
      "double p = gg * (Z * (1.0 - v2) - D);", PINS),
 ]
