@@ -90,6 +90,10 @@ MUTANTS = [
     ("emf_transport_shift_sign", "echo_oracle.c", "double vta = alpha * va[s][t] - beta[a];",
      "double vta = alpha * va[s][t] + beta[a];", PINS),
     ("ks_polar_metric", "echo_oracle.c", "g[1][1] = sig;", "g[1][1] = r * r;", PINS),
+    ("face_fallback_dropped", "echo_oracle.c", "if (!(Ps[0] > 0.0) || !(Ps[4] > 0.0) || !(v2 < 1.0)) {",
+     "if (0) {", PINS),
+    ("face_fallback_wrong_cell", "echo_oracle.c", "size_t src = cid[side == 0 ? 2 : 3];", "size_t src = cid[3];",
+     PINS),
     ("c2p_pressure_dropped_root", "echo_oracle.c", "double p = gg * (Z * (1.0 - v2) - D * sq);",
      "double p = gg * (Z * (1.0 - v2) - D);", PINS),
 ]
