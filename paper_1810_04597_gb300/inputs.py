@@ -235,6 +235,33 @@ def uniform_box(n=(8, 8, 8), rho=1.0, v=(0.2, -0.1, 0.05), p=0.7, B=(0.3, 0.2, -
                    bface=pack_faces(bx, by, bz))
 
 
+def relativistic_shear(n: int = 16, speed: float = 0.99, B=(0.0, 0.0, 0.0), mirror: bool = False) -> Problem:
+    """1-D periodic flow at |v| = speed whose direction turns from x to y
+    over two cells in the middle (rho = p = 1, uniform face field B):
+    reconstructing v^x and v^y separately gives face states with v^2 >= 1
+    there.  mirror: the image under x -> -x (cells reversed, v^x negated).
+    A test case for L(U) and one step: without floors the inversion fails
+    within the second step (the periodic seam turns v by 90 degrees in one
+    jump)."""
+    ang = np.zeros(n)
+    ang[n // 2:] = np.pi / 2
+    ang[n // 2 - 1] = np.pi / 4
+    ang[n // 2] = 3 * np.pi / 8
+    prims = np.zeros((5, 1, 1, n))
+    prims[0] = 1.0
+    prims[4] = 1.0
+    prims[1, 0, 0] = speed * np.cos(ang)
+    prims[2, 0, 0] = speed * np.sin(ang)
+    if mirror:
+        prims = prims[..., ::-1].copy()
+        prims[1] = -prims[1]
+    bx = np.full((1, 1, n + 1), B[0])
+    by = np.full((1, 2, n), B[1])
+    bz = np.full((2, 1, n), B[2])
+    return Problem(name=f"relativistic_shear_{n}", n=(n, 1, 1), x0=(0.0, 0.0, 0.0), dx=(1.0 / n, 1.0, 1.0),
+                   prims=prims, bface=pack_faces(bx, by, bz))
+
+
 def linear_wave(n: int, amp=0.1, v0=0.3, p0=1.0, B0=(0.2, 0.1, 0.05), t=0.0) -> Problem:
     """1-D density wave along x: rho = 1 + amp sin(2 pi (x - v0 t)), uniform
     v = (v0, 0, 0), p and B.  An exact solution of ideal (S)RMHD."""

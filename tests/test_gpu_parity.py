@@ -123,6 +123,20 @@ def test_parity_low_dimensional(orc, kind):
     assert max(errs.values()) <= 1e-11, errs
 
 
+def test_parity_relativistic_shear(orc):
+    """Face states with v^2 >= 1 (a flow at |v| = 0.99 turning over two
+    cells) fall back to their own side's cell on both paths; the face
+    velocities after the fallback also feed the edge EMFs (B != 0).  One
+    step: the inversion of this state fails within the second without
+    floors."""
+    prob = inputs.relativistic_shear(32, B=(0.1, 0.05, 0.02))
+    st_g, _ = gpu_run(prob, 1)
+    st_o, _, _, stats = oracle_run(orc, prob, 1)
+    assert stats["fallback_faces"] > 0
+    errs = per_field(orc, st_g, st_o, prob.n)
+    assert max(errs.values()) <= 1e-11, errs
+
+
 def test_fixed_dt_matches(orc):
     prob = inputs.smooth_box(16, seed=3)
     st_g, _ = gpu_run(prob, 4, dt=1e-3)

@@ -224,37 +224,17 @@ def test_induction_converges_on_kerr_schild(orc):
     assert np.all(e32 / e64 >= 3.5), (e32, e64)
 
 
-def _shear(n, mirror=False):
-    """1-D periodic flow at |v| = 0.99 whose direction turns from x to y
-    over two cells (B = 0): reconstructing v^x and v^y separately gives
-    face states with v^2 >= 1 there."""
-    ang = np.zeros(n)
-    ang[n // 2:] = np.pi / 2
-    ang[n // 2 - 1] = np.pi / 4
-    ang[n // 2] = 3 * np.pi / 8
-    prims = np.zeros((5, 1, 1, n))
-    prims[0] = prims[4] = 1.0
-    prims[1, 0, 0] = 0.99 * np.cos(ang)
-    prims[2, 0, 0] = 0.99 * np.sin(ang)
-    if mirror:
-        prims = prims[..., ::-1].copy()
-        prims[1] = -prims[1]
-    faces = inputs.pack_faces(np.zeros((1, 1, n + 1)), np.zeros((1, 2, n)), np.zeros((2, 1, n)))
-    return inputs.Problem(name="shear", n=(n, 1, 1), x0=(0.0, 0.0, 0.0), dx=(1.0 / n, 1.0, 1.0),
-                          prims=prims, bface=faces)
-
-
 def test_unphysical_face_states_fall_back_to_the_cell(orc):
     """Face states with v^2 >= 1 are replaced by their own side's cell: the
     step stays finite, the replacements are counted, and the rate keeps the
     mirror symmetry x -> -x (v^x -> -v^x) of the equations."""
     n = 16
-    prob = _shear(n)
+    prob = inputs.relativistic_shear(n)
     cfg, st, Z = setup(orc, prob)
     st1, _, _, stats = orc.steps(cfg, st, Z, 1)
     assert stats["fallback_faces"] > 0 and np.all(np.isfinite(st1))
     L, _, _ = orc.rhs(cfg, st, Z)
-    cfgm, stm, Zm = setup(orc, _shear(n, mirror=True))
+    cfgm, stm, Zm = setup(orc, inputs.relativistic_shear(n, mirror=True))
     Lm, _, _ = orc.rhs(cfgm, stm, Zm)
     cells = L[:5 * n].reshape(5, n)
     cellsm = Lm[:5 * n].reshape(5, n)[:, ::-1].copy()
