@@ -94,6 +94,10 @@ MUTANTS = [
      "if (0) {", PINS),
     ("face_fallback_wrong_cell", "echo_oracle.c", "size_t src = cid[side == 0 ? 2 : 3];", "size_t src = cid[3];",
      PINS),
+    ("ho_second_difference_sign", "echo_oracle.c", "double d2 = f5[1] - 2.0 * f5[2] + f5[3];",
+     "double d2 = f5[1] - 2.0 * f5[2] - f5[3];", HO_PINS),
+    ("ho_flux_stencil_offset", "echo_oracle.c", "                            t[d] += s - 2;\n                            f5[s] = G->F[d][q]",
+     "                            t[d] += s - 1;\n                            f5[s] = G->F[d][q]", HO_PINS),
     ("c2p_pressure_dropped_root", "echo_oracle.c", "double p = gg * (Z * (1.0 - v2) - D * sq);",
      "double p = gg * (Z * (1.0 - v2) - D);", PINS),
 ]
