@@ -93,6 +93,31 @@ def sweep_runs(scale=1, precision=32, device="cuda:0", steps=100):
     return sol
 
 
+def candidates(runs: int, max_blocks_per_sm: int, tiles=(128, 256, 512, 1024), queue=(True, False),
+               high_order: bool = False):
+    """The schedules the autotuner times, as (tile, blocks per SM, dynamic
+    queue, mode, branches): persistent with each tile, blocks-per-SM choice
+    and queue kind, per-phase with each tile (both for the form of order 0
+    only), and run-major with 1, 2, 4, 8 and all-runs graph branches (never
+    more branches than runs)."""
+    mb = max_blocks_per_sm
+    bpss = sorted({mb, max(1, mb // 2), min(mb, 2), min(mb, 3)})
+    cands = []
+    if not high_order:
+        cands += [(tile, bps, dyn, PERSISTENT, 1) for tile in tiles for bps in bpss for dyn in queue]
+        cands += [(tile, mb, True, PHASED, 1) for tile in tiles]
+    cands += [(256, mb, True, RUN_MAJOR, k) for k in sorted({1, 2, 4, 8, runs}) if k <= runs]
+    return cands
+
+
+def _load_cache():
+    try:
+        with open(TUNE_CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def autotune(batch: Batch, tiles=(128, 256, 512, 1024), queue=(True, False), reps=2, key=None, cache=True,
              graph=True):
     """Time `reps` steps (replayed from a graph when `graph`) for every
@@ -101,29 +126,20 @@ def autotune(batch: Batch, tiles=(128, 256, 512, 1024), queue=(True, False), rep
     per device and batch signature.  The runs' states advance while tuning."""
     import torch
     mb = _lib.echo_batch_max_blocks_per_sm(batch.b)
-    bpss = sorted({mb, max(1, mb // 2), min(mb, 2), min(mb, 3)})
     dev = torch.cuda.get_device_name(batch.solvers[0].device)
     sig = key or "|".join("x".join(str(v) for v in s.problem.n) for s in batch.solvers)
     ck = f"{dev}|p{batch.solvers[0].precision}|g{int(graph)}|{sig}"
-    if cache and os.path.exists(TUNE_CACHE):
-        try:
-            db = json.load(open(TUNE_CACHE))
-            if ck in db:
-                c = db[ck]
-                batch.configure(c["tile"], c["blocks_per_sm"], c["dynamic"], c["mode"], c["branches"])
-                batch.graph(graph)
-                return dict(c, cached=True)
-        except Exception:
-            pass
+    if cache:
+        c = _load_cache().get(ck)
+        if c is not None:
+            batch.configure(c["tile"], c["blocks_per_sm"], c["dynamic"], c["mode"], c["branches"])
+            batch.graph(graph)
+            return dict(c, cached=True)
     best = None
     results = []
-    nr = len(batch.solvers)
-    cands = []
-    if not any(getattr(s.problem, "order", 0) for s in batch.solvers):
-        # the persistent and per-phase schedules run the form of order 0 only
-        cands += [(tile, bps, dyn, PERSISTENT, 1) for tile in tiles for bps in bpss for dyn in queue]
-        cands += [(tile, mb, True, PHASED, 1) for tile in tiles]
-    cands += [(256, mb, True, RUN_MAJOR, k) for k in sorted({1, 2, 4, 8, nr}) if k <= nr]
+    # the persistent and per-phase schedules run the form of order 0 only
+    high = any(getattr(s.problem, "order", 0) for s in batch.solvers)
+    cands = candidates(len(batch.solvers), mb, tiles, queue, high)
     batch.graph(graph)
     for tile, bps, dyn, mode, br in cands:
         batch.configure(tile, bps, dyn, mode, br)
@@ -143,12 +159,8 @@ def autotune(batch: Batch, tiles=(128, 256, 512, 1024), queue=(True, False), rep
     out = dict(best, cached=False, candidates=results)
     if cache:
         os.makedirs(os.path.dirname(TUNE_CACHE), exist_ok=True)
-        db = {}
-        if os.path.exists(TUNE_CACHE):
-            try:
-                db = json.load(open(TUNE_CACHE))
-            except Exception:
-                db = {}
+        db = _load_cache()
         db[ck] = {k: best[k] for k in ("tile", "blocks_per_sm", "dynamic", "mode", "branches", "ms")}
-        json.dump(db, open(TUNE_CACHE, "w"), indent=1)
+        with open(TUNE_CACHE, "w") as f:
+            json.dump(db, f, indent=1)
     return out
