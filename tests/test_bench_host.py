@@ -1,0 +1,70 @@
+"""Host logic of the benchmark (no GPU): the per-launch unit counts and
+algorithmic bytes behind the roofline, the peaks file and its fallback, and
+the parsing of the clock samples that decides whether a run is kept."""
+import json
+
+import bench
+
+
+def test_units_per_launch():
+    n = (128, 96, 64)
+    nx, ny, nz = n
+    assert bench.kernel_units("c2p", n) == nx * ny * nz == bench.kernel_units("update", n)
+    # faces: every face along d, over the cells and 3 ghost layers across
+    assert bench.kernel_units("faces_x", n) == (nx + 1) * (ny + 6) * (nz + 6)
+    assert bench.kernel_units("faces_z", n) == (nx + 6) * (ny + 6) * (nz + 1)
+    # edges along e: one per owned edge, faces + 1 across
+    assert bench.kernel_units("emf_y", n) == (nx + 1) * ny * (nz + 1)
+    # the 128^3 capture the traffic per face is taken from
+    assert bench.kernel_units("faces_x", (128, 128, 128)) == 2316324
+
+
+def test_bytes_per_unit():
+    # FP64: every value 8 B; FP32: 4 B except the Newton unknown Z (FP64)
+    assert bench.kernel_bytes_per_unit("c2p", 64) == 18 * 8
+    assert bench.kernel_bytes_per_unit("c2p", 32) == 16 * 4 + 2 * 8
+    assert bench.kernel_bytes_per_unit("faces_y", 32) == 19 * 4
+    assert bench.kernel_bytes_per_unit("update", 64) == 42 * 8
+
+
+def test_peaks_file_and_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peaks, src = bench.load_peaks()
+    assert src == "fallback" and peaks["hbm_gbs"] == 6800.0 and peaks["bf16_tflops"] == 1900.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 7000.0}))
+    peaks, src = bench.load_peaks()
+    assert src == "measured" and peaks["hbm_gbs"] == 7000.0
+
+
+class _Proc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _row(gpu, sm, mx, w, *reasons):
+    flags = ["Active" if r else "Not Active" for r in reasons]
+    return f"{gpu}, {sm} MHz, {mx} MHz, {w} W, 0x0, " + ", ".join(flags)
+
+
+def test_clock_samples_parsed():
+    s = bench.ClockSampler(gpu_index=1)
+    s.proc = _Proc()
+    s.lines = [_row(0, 900, 2070, 100.0, 1, 1, 0, 0),
+               _row(1, 2070, 2070, 300.0, 0, 0, 0, 0),
+               _row(1, 2055, 2070, 320.5, 0, 0, 0, 1),
+               _row(1, 2070, 2070, 310.0, 0, 0, 0, 0),
+               "garbage"]
+    out = s.stop()
+    # only the selected GPU's rows; the other GPU's slowdown is not ours
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    assert out["power_w_max"] == 320.5
+
+
+def test_clock_sampler_without_nvidia_smi():
+    out = bench.ClockSampler().stop()
+    assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
