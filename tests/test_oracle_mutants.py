@@ -98,6 +98,14 @@ MUTANTS = [
      "double d2 = f5[1] - 2.0 * f5[2] - f5[3];", HO_PINS),
     ("ho_flux_stencil_offset", "echo_oracle.c", "                            t[d] += s - 2;\n                            f5[s] = G->F[d][q]",
      "                            t[d] += s - 1;\n                            f5[s] = G->F[d][q]", HO_PINS),
+    ("cell_centre_field_one_face", "echo_oracle.c",
+     "Bc[d] = 0.5 * (G->B[d][IDX(G, i, j, k)] + G->B[d][IDX(G, t[0], t[1], t[2])]) / sqrtg;",
+     "Bc[d] = G->B[d][IDX(G, i, j, k)] / sqrtg;", PINS),
+    ("floor_reset_skipped", "echo_oracle.c", "                if (reset) {", "                if (0) {", PINS),
+    ("p2c_momentum_sign", "echo_oracle.c", "C[1 + j] = (Zw + B2) * vl[j] - vB * Bl[j];",
+     "C[1 + j] = (Zw + B2) * vl[j] + vB * Bl[j];", PINS),
+    ("speeds_root_metric_term", "echo_oracle.c", "((1.0 - v2 * a2) * m->gi[d][d] - (1.0 - a2) * vd * vd)",
+     "((1.0 - v2 * a2) - (1.0 - a2) * vd * vd)", PINS),
     ("c2p_pressure_dropped_root", "echo_oracle.c", "double p = gg * (Z * (1.0 - v2) - D * sq);",
      "double p = gg * (Z * (1.0 - v2) - D);", PINS),
 ]

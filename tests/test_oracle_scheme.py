@@ -111,6 +111,60 @@ def test_floor_law(orc):
     assert stats["floors"] == N
 
 
+def test_floors_reset_the_conserved_state(orc):
+    """A cell raised to the floors gets the conserved state of its floored
+    primitives: one step of negligible length from a state far below them
+    ends on p2c of the floor values (the RK base is taken after the first
+    stage's inversion)."""
+    cfg = _ks_patch(orc, floors=1)
+    n = list(cfg.n)
+    N = n[0] * n[1] * n[2]
+    prims = np.zeros((5, n[2], n[1], n[0]))
+    prims[0] = 1e-9
+    prims[4] = 1e-12
+    nf = orc.state_count(n) - 5 * N
+    st, Z = orc.p2c(cfg, prims, np.zeros(nf))
+    st1, _, _, _ = orc.steps(cfg, st, Z, 1, 1e-12)
+    r = np.exp(cfg.x0[0] + (np.arange(n[0]) + 0.5) * cfg.dx[0])
+    fl = np.zeros_like(prims)
+    fl[0] = 1e-4 * r[None, None, :] ** -1.5
+    fl[4] = 1e-6 * r[None, None, :] ** -2.5
+    want, _ = orc.p2c(cfg, fl, np.zeros(nf))
+    got, want = st1[:5 * N].reshape(5, N), want[:5 * N].reshape(5, N)
+    assert np.allclose(got[[0, 4]], want[[0, 4]], rtol=1e-8, atol=0.0)
+    # at rest: the momenta are the step's own dt L(U), far below D
+    assert np.max(np.abs(got[1:4])) <= 1e-10 * np.max(want[0])
+
+
+def test_cell_centre_field_exact_for_linear_faces(orc):
+    """The cell-centre field interpolated from the two faces is exact for a
+    face field linear along its own direction (flat box): the grid's energy
+    is the pointwise map's with B at the centre."""
+    n = (4, 3, 2)
+    c = orc.OCfg()
+    for d, (x0, dx) in enumerate(((0.2, 0.1), (-0.3, 0.2), (0.0, 0.25))):
+        c.n[d], c.x0[d], c.dx[d] = n[d], x0, dx
+    for k in range(6):
+        c.bc[k] = 1
+    c.gamma = 4.0 / 3.0
+    lin = [(0.3, 0.5), (-0.2, 0.4), (0.1, -0.6)]          # B^d = a_d + b_d x^d
+    xf = [c.x0[d] + np.arange(n[d] + 1) * c.dx[d] for d in range(3)]
+    xc = [c.x0[d] + (np.arange(n[d]) + 0.5) * c.dx[d] for d in range(3)]
+    bx = np.broadcast_to((lin[0][0] + lin[0][1] * xf[0])[None, None, :], (n[2], n[1], n[0] + 1))
+    by = np.broadcast_to((lin[1][0] + lin[1][1] * xf[1])[None, :, None], (n[2], n[1] + 1, n[0]))
+    bz = np.broadcast_to((lin[2][0] + lin[2][1] * xf[2])[:, None, None], (n[2] + 1, n[1], n[0]))
+    prims = np.zeros((5, n[2], n[1], n[0]))
+    prims[0], prims[1], prims[2], prims[4] = 1.0, 0.2, -0.1, 0.5
+    st, _ = orc.p2c(c, prims, inputs.pack_faces(bx, by, bz))
+    N = n[0] * n[1] * n[2]
+    for k, j, i in np.ndindex(n[2], n[1], n[0]):
+        x = [xc[0][i], xc[1][j], xc[2][k]]
+        B = [lin[d][0] + lin[d][1] * x[d] for d in range(3)]
+        C = orc.p2c_point(c, x, np.concatenate([prims[:, k, j, i], B]))
+        h = (k * n[1] + j) * n[0] + i
+        assert np.allclose(st[np.arange(5) * N + h], C, rtol=1e-13, atol=1e-15), (i, j, k)
+
+
 def test_reduce_totals_and_divergence(orc):
     """The totals are the volume sums of the stored conserved arrays; the
     face field B~ = (2x, -y, 3z) at the face centres (outflow box, every
