@@ -202,12 +202,21 @@ def _induction_fields(x):
     return v, B
 
 
-def _induction_rate(orc, cfg, x, i):
+def _axis_fields(x):
+    """An axisymmetric magnetised flow smooth across the pole: the theta
+    components odd in theta, the others even."""
+    r, th = np.exp(x[0]), x[1]
+    v = np.array([0.05 * np.cos(th) / r, 0.02 * np.sin(th) * np.cos(th) / r, 0.01 / r])
+    B = np.array([0.1 * (1 + 0.5 * np.cos(th)) / r**2, 0.05 * np.sin(th) / r**2, 0.08 / r**2])
+    return v, B
+
+
+def _induction_rate(orc, cfg, x, i, fields=_induction_fields):
     """d_t B~^i = d_j (vt^i B~^j - vt^j B~^i), vt = alpha v - beta, B~ = sqrt(gamma) B,
     by fourth-order differences of the exact fields."""
     def G(y):
         m = orc.metric_point(cfg, y)
-        v, B = _induction_fields(y)
+        v, B = fields(y)
         vt = m["alpha"] * v - m["beta"]
         Bt = m["sqrtg"] * B
         return vt[i] * Bt - Bt[i] * vt
@@ -222,18 +231,20 @@ def _induction_rate(orc, cfg, x, i):
     return s
 
 
-def _induction_error(orc, N):
+def _induction_error(orc, N, fields=_induction_fields, theta=(0.9, 1.3), bc=(1, 1, 1, 1, 0, 0), rows=None):
+    """Max |L(B~) - d_t B~| over the r- and theta-faces of the central half
+    in r and, unless rows lists theta rows, in theta."""
     c = _ks_patch(orc, n=(N, N, 4))
-    for d, (x0, ext) in enumerate(((np.log(4.0), 1.0), (0.9, 1.3), (0.0, 0.4))):
+    for d, (x0, ext) in enumerate(((np.log(4.0), 1.0), theta, (0.0, 0.4))):
         c.x0[d], c.dx[d] = x0, ext / c.n[d]
-    for k, b in enumerate((1, 1, 1, 1, 0, 0)):
+    for k, b in enumerate(bc):
         c.bc[k] = b
     n = list(c.n)
     xc = [c.x0[d] + (np.arange(n[d]) + 0.5) * c.dx[d] for d in range(3)]
     prims = np.zeros((5, n[2], n[1], n[0]))
     prims[0] = prims[4] = 1.0
     for k, j, i in np.ndindex(n[2], n[1], n[0]):
-        prims[1:4, k, j, i] = _induction_fields([xc[0][i], xc[1][j], xc[2][k]])[0]
+        prims[1:4, k, j, i] = fields([xc[0][i], xc[1][j], xc[2][k]])[0]
 
     def face_x(d, idx):
         k, j, i = idx
@@ -248,7 +259,7 @@ def _induction_error(orc, N):
         a = np.zeros(shp)
         for idx in np.ndindex(*shp):
             x = face_x(d, idx)
-            a[idx] = orc.metric_point(c, x)["sqrtg"] * _induction_fields(x)[1][d]
+            a[idx] = orc.metric_point(c, x)["sqrtg"] * fields(x)[1][d]
         faces.append(a)
         shapes.append(shp)
     st, Z = orc.p2c(c, prims, inputs.pack_faces(*faces))
@@ -260,8 +271,9 @@ def _induction_error(orc, N):
         off += int(np.prod(shp))
         e = 0.0
         for idx in np.ndindex(*shp):
-            if M <= idx[2] < shp[2] - M and M <= idx[1] < shp[1] - M:
-                e = max(e, abs(Ld[idx] - _induction_rate(orc, c, face_x(d, idx), d)))
+            in_theta = (M <= idx[1] < shp[1] - M) if rows is None else (idx[1] in rows)
+            if M <= idx[2] < shp[2] - M and in_theta:
+                e = max(e, abs(Ld[idx] - _induction_rate(orc, c, face_x(d, idx), d, fields)))
         errs.append(e)
     return np.array(errs)
 
@@ -275,6 +287,20 @@ def test_induction_converges_on_kerr_schild(orc):
     e32 = _induction_error(orc, 32)
     e64 = _induction_error(orc, 64)
     assert np.all(e32 <= 5e-6), e32
+    assert np.all(e32 / e64 >= 3.5), (e32, e64)
+
+
+@pytest.mark.xfail(strict=True, reason="the axis rule continues the densitised face field B~ evenly "
+                   "across the pole, but B~ = sqrt(gamma) B carries sqrt(gamma) ~ sin(theta): the EMFs "
+                   "reconstruct B~^r across a kink and the rate of B~^r is off by O(1) within three rows "
+                   "of the axis; continuing the r- and phi-face arrays oddly restores convergence")
+def test_induction_next_to_the_axis(orc):
+    """The same pin on the rows next to the polar axis (theta from 0, axis
+    boundary), for an axisymmetric flow smooth across the pole."""
+    kw = dict(fields=_axis_fields, theta=(0.0, 1.0), bc=(1, 1, 2, 1, 0, 0), rows=(0, 1, 2, 3))
+    e32 = _induction_error(orc, 32, **kw)
+    e64 = _induction_error(orc, 64, **kw)
+    assert np.all(e32 <= 1e-5), e32
     assert np.all(e32 / e64 >= 3.5), (e32, e64)
 
 
