@@ -211,6 +211,17 @@ def _axis_fields(x):
     return v, B
 
 
+def _phi_fields(x):
+    """The flow of _induction_fields modulated along phi: one period over
+    the patch's phi extent (0.4)."""
+    r, th = np.exp(x[0]), x[1]
+    c, s = np.cos(2 * np.pi * x[2] / 0.4), np.sin(2 * np.pi * x[2] / 0.4)
+    v = np.array([0.05 * np.sin(th) / r * (1 + 0.2 * c), 0.02 * np.cos(th) / r, 0.01 / r * (1 + 0.3 * s)])
+    B = np.array([0.1 * (1 + 0.5 * np.cos(th)) / r**2 * (1 + 0.2 * s), 0.05 * np.sin(th) / r**2 * (1 + 0.1 * c),
+                  0.08 / r**2 * (1 + 0.2 * c)])
+    return v, B
+
+
 def _induction_rate(orc, cfg, x, i, fields=_induction_fields):
     """d_t B~^i = d_j (vt^i B~^j - vt^j B~^i), vt = alpha v - beta, B~ = sqrt(gamma) B,
     by fourth-order differences of the exact fields."""
@@ -221,7 +232,7 @@ def _induction_rate(orc, cfg, x, i, fields=_induction_fields):
         Bt = m["sqrtg"] * B
         return vt[i] * Bt - Bt[i] * vt
     h, s = 1e-4, 0.0
-    for j in range(2):
+    for j in range(3):
         acc = 0.0
         for w, o in ((1, -2), (-8, -1), (8, 1), (-1, 2)):
             y = np.array(x, float)
@@ -232,10 +243,10 @@ def _induction_rate(orc, cfg, x, i, fields=_induction_fields):
 
 
 def _induction_error(orc, N, fields=_induction_fields, theta=(0.9, 1.3), bc=(1, 1, 1, 1, 0, 0), rows=None,
-                     order=0):
+                     order=0, n_phi=4, sample=1):
     """Max |L(B~) - d_t B~| over the r- and theta-faces of the central half
     in r and, unless rows lists theta rows, in theta."""
-    c = _ks_patch(orc, n=(N, N, 4))
+    c = _ks_patch(orc, n=(N, N, n_phi))
     c.order = order
     for d, (x0, ext) in enumerate(((np.log(4.0), 1.0), theta, (0.0, 0.4))):
         c.x0[d], c.dx[d] = x0, ext / c.n[d]
@@ -274,6 +285,8 @@ def _induction_error(orc, N, fields=_induction_fields, theta=(0.9, 1.3), bc=(1, 
         e = 0.0
         for idx in np.ndindex(*shp):
             in_theta = (M <= idx[1] < shp[1] - M) if rows is None else (idx[1] in rows)
+            if sample > 1 and (idx[0] % sample or idx[1] % sample):
+                continue
             if M <= idx[2] < shp[2] - M and in_theta:
                 e = max(e, abs(Ld[idx] - _induction_rate(orc, c, face_x(d, idx), d, fields)))
         errs.append(e)
@@ -289,6 +302,16 @@ def test_induction_converges_on_kerr_schild(orc):
     e32 = _induction_error(orc, 32)
     e64 = _induction_error(orc, 64)
     assert np.all(e32 <= 5e-6), e32
+    assert np.all(e32 / e64 >= 3.5), (e32, e64)
+
+
+def test_induction_with_phi_dependence(orc):
+    """The same pin for a flow that varies along phi as well (the phi-edge
+    EMFs and the spin's r-phi metric coupling), phi resolved like r and
+    theta; measured ratios 4.2 per halving."""
+    e32 = _induction_error(orc, 32, fields=_phi_fields, n_phi=16, sample=4)
+    e64 = _induction_error(orc, 64, fields=_phi_fields, n_phi=32, sample=4)
+    assert np.all(e32 <= 1e-3), e32
     assert np.all(e32 / e64 >= 3.5), (e32, e64)
 
 
