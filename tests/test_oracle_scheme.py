@@ -315,6 +315,72 @@ def test_induction_with_phi_dependence(orc):
     assert np.all(e32 / e64 >= 3.5), (e32, e64)
 
 
+def _fluid_prims(x):
+    """rho, v^i, p, B^i of a smooth magnetised flow varying in r, theta and
+    phi (v and B those of _phi_fields)."""
+    v, B = _phi_fields(x)
+    rho = 1.0 + 0.1 * np.sin(x[1]) * np.cos(2 * np.pi * x[2] / 0.4)
+    p = 0.5 * (1.0 + 0.1 * np.cos(x[1]))
+    return np.concatenate([[rho], v, [p], B])
+
+
+def _fluid_error(orc, N, sample=4):
+    """Max |L(U) - d_t U| per conserved variable over the central half of a
+    spinning Kerr-Schild patch, d_t U = -d_j F^j + S with the pointwise
+    (sqrt(gamma)-weighted) flux and sources of the exact state, the flux
+    divergence by fourth-order differences."""
+    c = _ks_patch(orc, n=(N, N, N // 2))
+    for d, (x0, ext) in enumerate(((np.log(4.0), 1.0), (0.9, 1.3), (0.0, 0.4))):
+        c.x0[d], c.dx[d] = x0, ext / c.n[d]
+    for k, b in enumerate((1, 1, 1, 1, 0, 0)):
+        c.bc[k] = b
+    n = list(c.n)
+    xc = [c.x0[d] + (np.arange(n[d]) + 0.5) * c.dx[d] for d in range(3)]
+    prims = np.zeros((5, n[2], n[1], n[0]))
+    for k, j, i in np.ndindex(n[2], n[1], n[0]):
+        prims[:, k, j, i] = _fluid_prims([xc[0][i], xc[1][j], xc[2][k]])[:5]
+    faces = []
+    for d in range(3):
+        shp = [n[2], n[1], n[0]]
+        shp[2 - d] += 1
+        a = np.zeros(shp)
+        for idx in np.ndindex(*shp):
+            k, j, i = idx
+            x = [xc[0][min(i, n[0] - 1)], xc[1][min(j, n[1] - 1)], xc[2][min(k, n[2] - 1)]]
+            x[d] = c.x0[d] + idx[2 - d] * c.dx[d]
+            a[idx] = orc.metric_point(c, x)["sqrtg"] * _fluid_prims(x)[5 + d]
+        faces.append(a)
+    st, Z = orc.p2c(c, prims, inputs.pack_faces(*faces))
+    L, _, _ = orc.rhs(c, st, Z)
+    Lc = L[:5 * n[0] * n[1] * n[2]].reshape(5, n[2], n[1], n[0])
+    M, h, e = N // 4, 1e-4, np.zeros(5)
+    for k, j, i in np.ndindex(n[2], n[1], n[0]):
+        if k % sample or j % sample or not (M <= i < n[0] - M and M <= j < n[1] - M):
+            continue
+        x = [xc[0][i], xc[1][j], xc[2][k]]
+        rate = orc.sources_point(c, x, _fluid_prims(x))
+        for dd in range(3):
+            acc = np.zeros(5)
+            for w, o in ((1, -2), (-8, -1), (8, 1), (-1, 2)):
+                y = np.array(x, float)
+                y[dd] += o * h
+                acc += w * orc.flux_point(c, y, _fluid_prims(y), dd)[0]
+            rate = rate - acc / (12 * h)
+        e = np.maximum(e, np.abs(Lc[:, k, j, i] - rate))
+    return e
+
+
+def test_fluid_converges_on_spinning_kerr_schild(orc):
+    """L(U) of a smooth magnetised flow varying in r, theta and phi on a
+    Kerr-Schild patch (a = 0.9) converges at second order or better to the
+    continuum rate built from the pointwise flux and sources (measured
+    ratios 3.5-9.1 per halving), pinning the grid's flux differences and
+    source assembly in all three directions."""
+    e32 = _fluid_error(orc, 32)
+    e64 = _fluid_error(orc, 64)
+    assert np.all(e32 / e64 >= 3.0), (e32, e64)
+
+
 def test_induction_high_order_form_fifth_order(orc):
     """The high-order form (flux-derivative correction of fluxes and EMFs,
     point values at the faces) on the same Kerr-Schild patch: the face-field
