@@ -193,106 +193,6 @@ def test_reduce_totals_and_divergence(orc):
     assert abs(t[5] - 4.0) <= 1e-13
 
 
-def _induction_fields(x):
-    """A smooth magnetised flow on a Kerr-Schild patch (contravariant
-    coordinate components; no phi dependence)."""
-    r, th = np.exp(x[0]), x[1]
-    v = np.array([0.05 * np.sin(th) / r, 0.02 * np.cos(th) / r, 0.01 / r])
-    B = np.array([0.1 * (1 + 0.5 * np.cos(th)) / r**2, 0.05 * np.sin(th) / r**2, 0.08 / r**2])
-    return v, B
-
-
-def _axis_fields(x):
-    """An axisymmetric magnetised flow smooth across the pole: the theta
-    components odd in theta, the others even."""
-    r, th = np.exp(x[0]), x[1]
-    v = np.array([0.05 * np.cos(th) / r, 0.02 * np.sin(th) * np.cos(th) / r, 0.01 / r])
-    B = np.array([0.1 * (1 + 0.5 * np.cos(th)) / r**2, 0.05 * np.sin(th) / r**2, 0.08 / r**2])
-    return v, B
-
-
-def _phi_fields(x):
-    """The flow of _induction_fields modulated along phi: one period over
-    the patch's phi extent (0.4)."""
-    r, th = np.exp(x[0]), x[1]
-    c, s = np.cos(2 * np.pi * x[2] / 0.4), np.sin(2 * np.pi * x[2] / 0.4)
-    v = np.array([0.05 * np.sin(th) / r * (1 + 0.2 * c), 0.02 * np.cos(th) / r, 0.01 / r * (1 + 0.3 * s)])
-    B = np.array([0.1 * (1 + 0.5 * np.cos(th)) / r**2 * (1 + 0.2 * s), 0.05 * np.sin(th) / r**2 * (1 + 0.1 * c),
-                  0.08 / r**2 * (1 + 0.2 * c)])
-    return v, B
-
-
-def _induction_rate(orc, cfg, x, i, fields=_induction_fields):
-    """d_t B~^i = d_j (vt^i B~^j - vt^j B~^i), vt = alpha v - beta, B~ = sqrt(gamma) B,
-    by fourth-order differences of the exact fields."""
-    def G(y):
-        m = orc.metric_point(cfg, y)
-        v, B = fields(y)
-        vt = m["alpha"] * v - m["beta"]
-        Bt = m["sqrtg"] * B
-        return vt[i] * Bt - Bt[i] * vt
-    h, s = 1e-4, 0.0
-    for j in range(3):
-        acc = 0.0
-        for w, o in ((1, -2), (-8, -1), (8, 1), (-1, 2)):
-            y = np.array(x, float)
-            y[j] += o * h
-            acc += w * G(y)[j]
-        s += acc / (12 * h)
-    return s
-
-
-def _induction_error(orc, N, fields=_induction_fields, theta=(0.9, 1.3), bc=(1, 1, 1, 1, 0, 0), rows=None,
-                     order=0, n_phi=4, sample=1):
-    """Max |L(B~) - d_t B~| over the r- and theta-faces of the central half
-    in r and, unless rows lists theta rows, in theta."""
-    c = _ks_patch(orc, n=(N, N, n_phi))
-    c.order = order
-    for d, (x0, ext) in enumerate(((np.log(4.0), 1.0), theta, (0.0, 0.4))):
-        c.x0[d], c.dx[d] = x0, ext / c.n[d]
-    for k, b in enumerate(bc):
-        c.bc[k] = b
-    n = list(c.n)
-    xc = [c.x0[d] + (np.arange(n[d]) + 0.5) * c.dx[d] for d in range(3)]
-    prims = np.zeros((5, n[2], n[1], n[0]))
-    prims[0] = prims[4] = 1.0
-    for k, j, i in np.ndindex(n[2], n[1], n[0]):
-        prims[1:4, k, j, i] = fields([xc[0][i], xc[1][j], xc[2][k]])[0]
-
-    def face_x(d, idx):
-        k, j, i = idx
-        x = [xc[0][min(i, n[0] - 1)], xc[1][min(j, n[1] - 1)], xc[2][min(k, n[2] - 1)]]
-        x[d] = c.x0[d] + idx[2 - d] * c.dx[d]
-        return x
-
-    faces, shapes = [], []
-    for d in range(3):
-        shp = [n[2], n[1], n[0]]
-        shp[2 - d] += 1
-        a = np.zeros(shp)
-        for idx in np.ndindex(*shp):
-            x = face_x(d, idx)
-            a[idx] = orc.metric_point(c, x)["sqrtg"] * fields(x)[1][d]
-        faces.append(a)
-        shapes.append(shp)
-    st, Z = orc.p2c(c, prims, inputs.pack_faces(*faces))
-    L, _, _ = orc.rhs(c, st, Z)
-    off, M, errs = 5 * n[0] * n[1] * n[2], N // 4, []
-    for d in range(2):
-        shp = shapes[d]
-        Ld = L[off:off + int(np.prod(shp))].reshape(shp)
-        off += int(np.prod(shp))
-        e = 0.0
-        for idx in np.ndindex(*shp):
-            in_theta = (M <= idx[1] < shp[1] - M) if rows is None else (idx[1] in rows)
-            if sample > 1 and (idx[0] % sample or idx[1] % sample):
-                continue
-            if M <= idx[2] < shp[2] - M and in_theta:
-                e = max(e, abs(Ld[idx] - _induction_rate(orc, c, face_x(d, idx), d, fields)))
-        errs.append(e)
-    return np.array(errs)
-
-
 def test_induction_converges_on_kerr_schild(orc):
     """The face-field rate of a smooth magnetised flow on a Kerr-Schild patch
     (a = 0.9, away from the axis) converges at second order to the
@@ -302,106 +202,6 @@ def test_induction_converges_on_kerr_schild(orc):
     e32 = _induction_error(orc, 32)
     e64 = _induction_error(orc, 64)
     assert np.all(e32 <= 5e-6), e32
-    assert np.all(e32 / e64 >= 3.5), (e32, e64)
-
-
-def test_induction_with_phi_dependence(orc):
-    """The same pin for a flow that varies along phi as well (the phi-edge
-    EMFs and the spin's r-phi metric coupling), phi resolved like r and
-    theta; measured ratios 4.2 per halving."""
-    e32 = _induction_error(orc, 32, fields=_phi_fields, n_phi=16, sample=4)
-    e64 = _induction_error(orc, 64, fields=_phi_fields, n_phi=32, sample=4)
-    assert np.all(e32 <= 1e-3), e32
-    assert np.all(e32 / e64 >= 3.5), (e32, e64)
-
-
-def _fluid_prims(x):
-    """rho, v^i, p, B^i of a smooth magnetised flow varying in r, theta and
-    phi (v and B those of _phi_fields)."""
-    v, B = _phi_fields(x)
-    rho = 1.0 + 0.1 * np.sin(x[1]) * np.cos(2 * np.pi * x[2] / 0.4)
-    p = 0.5 * (1.0 + 0.1 * np.cos(x[1]))
-    return np.concatenate([[rho], v, [p], B])
-
-
-def _fluid_error(orc, N, sample=4):
-    """Max |L(U) - d_t U| per conserved variable over the central half of a
-    spinning Kerr-Schild patch, d_t U = -d_j F^j + S with the pointwise
-    (sqrt(gamma)-weighted) flux and sources of the exact state, the flux
-    divergence by fourth-order differences."""
-    c = _ks_patch(orc, n=(N, N, N // 2))
-    for d, (x0, ext) in enumerate(((np.log(4.0), 1.0), (0.9, 1.3), (0.0, 0.4))):
-        c.x0[d], c.dx[d] = x0, ext / c.n[d]
-    for k, b in enumerate((1, 1, 1, 1, 0, 0)):
-        c.bc[k] = b
-    n = list(c.n)
-    xc = [c.x0[d] + (np.arange(n[d]) + 0.5) * c.dx[d] for d in range(3)]
-    prims = np.zeros((5, n[2], n[1], n[0]))
-    for k, j, i in np.ndindex(n[2], n[1], n[0]):
-        prims[:, k, j, i] = _fluid_prims([xc[0][i], xc[1][j], xc[2][k]])[:5]
-    faces = []
-    for d in range(3):
-        shp = [n[2], n[1], n[0]]
-        shp[2 - d] += 1
-        a = np.zeros(shp)
-        for idx in np.ndindex(*shp):
-            k, j, i = idx
-            x = [xc[0][min(i, n[0] - 1)], xc[1][min(j, n[1] - 1)], xc[2][min(k, n[2] - 1)]]
-            x[d] = c.x0[d] + idx[2 - d] * c.dx[d]
-            a[idx] = orc.metric_point(c, x)["sqrtg"] * _fluid_prims(x)[5 + d]
-        faces.append(a)
-    st, Z = orc.p2c(c, prims, inputs.pack_faces(*faces))
-    L, _, _ = orc.rhs(c, st, Z)
-    Lc = L[:5 * n[0] * n[1] * n[2]].reshape(5, n[2], n[1], n[0])
-    M, h, e = N // 4, 1e-4, np.zeros(5)
-    for k, j, i in np.ndindex(n[2], n[1], n[0]):
-        if k % sample or j % sample or not (M <= i < n[0] - M and M <= j < n[1] - M):
-            continue
-        x = [xc[0][i], xc[1][j], xc[2][k]]
-        rate = orc.sources_point(c, x, _fluid_prims(x))
-        for dd in range(3):
-            acc = np.zeros(5)
-            for w, o in ((1, -2), (-8, -1), (8, 1), (-1, 2)):
-                y = np.array(x, float)
-                y[dd] += o * h
-                acc += w * orc.flux_point(c, y, _fluid_prims(y), dd)[0]
-            rate = rate - acc / (12 * h)
-        e = np.maximum(e, np.abs(Lc[:, k, j, i] - rate))
-    return e
-
-
-def test_fluid_converges_on_spinning_kerr_schild(orc):
-    """L(U) of a smooth magnetised flow varying in r, theta and phi on a
-    Kerr-Schild patch (a = 0.9) converges at second order or better to the
-    continuum rate built from the pointwise flux and sources (measured
-    ratios 3.5-9.1 per halving), pinning the grid's flux differences and
-    source assembly in all three directions."""
-    e32 = _fluid_error(orc, 32)
-    e64 = _fluid_error(orc, 64)
-    assert np.all(e32 / e64 >= 3.0), (e32, e64)
-
-
-def test_induction_high_order_form_fifth_order(orc):
-    """The high-order form (flux-derivative correction of fluxes and EMFs,
-    point values at the faces) on the same Kerr-Schild patch: the face-field
-    rate converges at fifth order (measured ratios 31 per halving)."""
-    e32 = _induction_error(orc, 32, order=1)
-    e64 = _induction_error(orc, 64, order=1)
-    assert np.all(e32 <= 2e-9), e32
-    assert np.all(e32 / e64 >= 20.0), (e32, e64)
-
-
-@pytest.mark.xfail(strict=True, reason="the axis rule continues the densitised face field B~ evenly "
-                   "across the pole, but B~ = sqrt(gamma) B carries sqrt(gamma) ~ sin(theta): the EMFs "
-                   "reconstruct B~^r across a kink and the rate of B~^r is off by O(1) within three rows "
-                   "of the axis; continuing the r- and phi-face arrays oddly restores convergence")
-def test_induction_next_to_the_axis(orc):
-    """The same pin on the rows next to the polar axis (theta from 0, axis
-    boundary), for an axisymmetric flow smooth across the pole."""
-    kw = dict(fields=_axis_fields, theta=(0.0, 1.0), bc=(1, 1, 2, 1, 0, 0), rows=(0, 1, 2, 3))
-    e32 = _induction_error(orc, 32, **kw)
-    e64 = _induction_error(orc, 64, **kw)
-    assert np.all(e32 <= 1e-5), e32
     assert np.all(e32 / e64 >= 3.5), (e32, e64)
 
 
@@ -681,3 +481,205 @@ def test_michel_accretion_residual_converges(orc):
     sources with a flow the torus does not have."""
     res, orders = _michel_residuals(orc, 0)
     assert np.all(orders >= 1.8), (res, orders)
+
+
+# ---- convergence to the continuum equations on Kerr-Schild patches (slowest pins last)
+
+def _induction_fields(x):
+    """A smooth magnetised flow on a Kerr-Schild patch (contravariant
+    coordinate components; no phi dependence)."""
+    r, th = np.exp(x[0]), x[1]
+    v = np.array([0.05 * np.sin(th) / r, 0.02 * np.cos(th) / r, 0.01 / r])
+    B = np.array([0.1 * (1 + 0.5 * np.cos(th)) / r**2, 0.05 * np.sin(th) / r**2, 0.08 / r**2])
+    return v, B
+
+
+def _axis_fields(x):
+    """An axisymmetric magnetised flow smooth across the pole: the theta
+    components odd in theta, the others even."""
+    r, th = np.exp(x[0]), x[1]
+    v = np.array([0.05 * np.cos(th) / r, 0.02 * np.sin(th) * np.cos(th) / r, 0.01 / r])
+    B = np.array([0.1 * (1 + 0.5 * np.cos(th)) / r**2, 0.05 * np.sin(th) / r**2, 0.08 / r**2])
+    return v, B
+
+
+def _phi_fields(x):
+    """The flow of _induction_fields modulated along phi: one period over
+    the patch's phi extent (0.4)."""
+    r, th = np.exp(x[0]), x[1]
+    c, s = np.cos(2 * np.pi * x[2] / 0.4), np.sin(2 * np.pi * x[2] / 0.4)
+    v = np.array([0.05 * np.sin(th) / r * (1 + 0.2 * c), 0.02 * np.cos(th) / r, 0.01 / r * (1 + 0.3 * s)])
+    B = np.array([0.1 * (1 + 0.5 * np.cos(th)) / r**2 * (1 + 0.2 * s), 0.05 * np.sin(th) / r**2 * (1 + 0.1 * c),
+                  0.08 / r**2 * (1 + 0.2 * c)])
+    return v, B
+
+
+def _induction_rate(orc, cfg, x, i, fields=_induction_fields):
+    """d_t B~^i = d_j (vt^i B~^j - vt^j B~^i), vt = alpha v - beta, B~ = sqrt(gamma) B,
+    by fourth-order differences of the exact fields."""
+    def G(y):
+        m = orc.metric_point(cfg, y)
+        v, B = fields(y)
+        vt = m["alpha"] * v - m["beta"]
+        Bt = m["sqrtg"] * B
+        return vt[i] * Bt - Bt[i] * vt
+    h, s = 1e-4, 0.0
+    for j in range(3):
+        acc = 0.0
+        for w, o in ((1, -2), (-8, -1), (8, 1), (-1, 2)):
+            y = np.array(x, float)
+            y[j] += o * h
+            acc += w * G(y)[j]
+        s += acc / (12 * h)
+    return s
+
+
+def _induction_error(orc, N, fields=_induction_fields, theta=(0.9, 1.3), bc=(1, 1, 1, 1, 0, 0), rows=None,
+                     order=0, n_phi=4, sample=1):
+    """Max |L(B~) - d_t B~| over the r- and theta-faces of the central half
+    in r and, unless rows lists theta rows, in theta."""
+    c = _ks_patch(orc, n=(N, N, n_phi))
+    c.order = order
+    for d, (x0, ext) in enumerate(((np.log(4.0), 1.0), theta, (0.0, 0.4))):
+        c.x0[d], c.dx[d] = x0, ext / c.n[d]
+    for k, b in enumerate(bc):
+        c.bc[k] = b
+    n = list(c.n)
+    xc = [c.x0[d] + (np.arange(n[d]) + 0.5) * c.dx[d] for d in range(3)]
+    prims = np.zeros((5, n[2], n[1], n[0]))
+    prims[0] = prims[4] = 1.0
+    for k, j, i in np.ndindex(n[2], n[1], n[0]):
+        prims[1:4, k, j, i] = fields([xc[0][i], xc[1][j], xc[2][k]])[0]
+
+    def face_x(d, idx):
+        k, j, i = idx
+        x = [xc[0][min(i, n[0] - 1)], xc[1][min(j, n[1] - 1)], xc[2][min(k, n[2] - 1)]]
+        x[d] = c.x0[d] + idx[2 - d] * c.dx[d]
+        return x
+
+    faces, shapes = [], []
+    for d in range(3):
+        shp = [n[2], n[1], n[0]]
+        shp[2 - d] += 1
+        a = np.zeros(shp)
+        for idx in np.ndindex(*shp):
+            x = face_x(d, idx)
+            a[idx] = orc.metric_point(c, x)["sqrtg"] * fields(x)[1][d]
+        faces.append(a)
+        shapes.append(shp)
+    st, Z = orc.p2c(c, prims, inputs.pack_faces(*faces))
+    L, _, _ = orc.rhs(c, st, Z)
+    off, M, errs = 5 * n[0] * n[1] * n[2], N // 4, []
+    for d in range(2):
+        shp = shapes[d]
+        Ld = L[off:off + int(np.prod(shp))].reshape(shp)
+        off += int(np.prod(shp))
+        e = 0.0
+        for idx in np.ndindex(*shp):
+            in_theta = (M <= idx[1] < shp[1] - M) if rows is None else (idx[1] in rows)
+            if sample > 1 and (idx[0] % sample or idx[1] % sample):
+                continue
+            if M <= idx[2] < shp[2] - M and in_theta:
+                e = max(e, abs(Ld[idx] - _induction_rate(orc, c, face_x(d, idx), d, fields)))
+        errs.append(e)
+    return np.array(errs)
+
+
+def test_induction_with_phi_dependence(orc):
+    """The same pin for a flow that varies along phi as well (the phi-edge
+    EMFs and the spin's r-phi metric coupling), phi resolved like r and
+    theta; measured ratios 4.2 per halving."""
+    e32 = _induction_error(orc, 32, fields=_phi_fields, n_phi=16, sample=4)
+    e64 = _induction_error(orc, 64, fields=_phi_fields, n_phi=32, sample=4)
+    assert np.all(e32 <= 1e-3), e32
+    assert np.all(e32 / e64 >= 3.5), (e32, e64)
+
+
+def _fluid_prims(x):
+    """rho, v^i, p, B^i of a smooth magnetised flow varying in r, theta and
+    phi (v and B those of _phi_fields)."""
+    v, B = _phi_fields(x)
+    rho = 1.0 + 0.1 * np.sin(x[1]) * np.cos(2 * np.pi * x[2] / 0.4)
+    p = 0.5 * (1.0 + 0.1 * np.cos(x[1]))
+    return np.concatenate([[rho], v, [p], B])
+
+
+def _fluid_error(orc, N, sample=4):
+    """Max |L(U) - d_t U| per conserved variable over the central half of a
+    spinning Kerr-Schild patch, d_t U = -d_j F^j + S with the pointwise
+    (sqrt(gamma)-weighted) flux and sources of the exact state, the flux
+    divergence by fourth-order differences."""
+    c = _ks_patch(orc, n=(N, N, N // 2))
+    for d, (x0, ext) in enumerate(((np.log(4.0), 1.0), (0.9, 1.3), (0.0, 0.4))):
+        c.x0[d], c.dx[d] = x0, ext / c.n[d]
+    for k, b in enumerate((1, 1, 1, 1, 0, 0)):
+        c.bc[k] = b
+    n = list(c.n)
+    xc = [c.x0[d] + (np.arange(n[d]) + 0.5) * c.dx[d] for d in range(3)]
+    prims = np.zeros((5, n[2], n[1], n[0]))
+    for k, j, i in np.ndindex(n[2], n[1], n[0]):
+        prims[:, k, j, i] = _fluid_prims([xc[0][i], xc[1][j], xc[2][k]])[:5]
+    faces = []
+    for d in range(3):
+        shp = [n[2], n[1], n[0]]
+        shp[2 - d] += 1
+        a = np.zeros(shp)
+        for idx in np.ndindex(*shp):
+            k, j, i = idx
+            x = [xc[0][min(i, n[0] - 1)], xc[1][min(j, n[1] - 1)], xc[2][min(k, n[2] - 1)]]
+            x[d] = c.x0[d] + idx[2 - d] * c.dx[d]
+            a[idx] = orc.metric_point(c, x)["sqrtg"] * _fluid_prims(x)[5 + d]
+        faces.append(a)
+    st, Z = orc.p2c(c, prims, inputs.pack_faces(*faces))
+    L, _, _ = orc.rhs(c, st, Z)
+    Lc = L[:5 * n[0] * n[1] * n[2]].reshape(5, n[2], n[1], n[0])
+    M, h, e = N // 4, 1e-4, np.zeros(5)
+    for k, j, i in np.ndindex(n[2], n[1], n[0]):
+        if k % sample or j % sample or not (M <= i < n[0] - M and M <= j < n[1] - M):
+            continue
+        x = [xc[0][i], xc[1][j], xc[2][k]]
+        rate = orc.sources_point(c, x, _fluid_prims(x))
+        for dd in range(3):
+            acc = np.zeros(5)
+            for w, o in ((1, -2), (-8, -1), (8, 1), (-1, 2)):
+                y = np.array(x, float)
+                y[dd] += o * h
+                acc += w * orc.flux_point(c, y, _fluid_prims(y), dd)[0]
+            rate = rate - acc / (12 * h)
+        e = np.maximum(e, np.abs(Lc[:, k, j, i] - rate))
+    return e
+
+
+def test_fluid_converges_on_spinning_kerr_schild(orc):
+    """L(U) of a smooth magnetised flow varying in r, theta and phi on a
+    Kerr-Schild patch (a = 0.9) converges at second order or better to the
+    continuum rate built from the pointwise flux and sources (measured
+    ratios 3.5-9.1 per halving), pinning the grid's flux differences and
+    source assembly in all three directions."""
+    e32 = _fluid_error(orc, 32)
+    e64 = _fluid_error(orc, 64)
+    assert np.all(e32 / e64 >= 3.0), (e32, e64)
+
+
+def test_induction_high_order_form_fifth_order(orc):
+    """The high-order form (flux-derivative correction of fluxes and EMFs,
+    point values at the faces) on the same Kerr-Schild patch: the face-field
+    rate converges at fifth order (measured ratios 31 per halving)."""
+    e32 = _induction_error(orc, 32, order=1)
+    e64 = _induction_error(orc, 64, order=1)
+    assert np.all(e32 <= 2e-9), e32
+    assert np.all(e32 / e64 >= 20.0), (e32, e64)
+
+
+@pytest.mark.xfail(strict=True, reason="the axis rule continues the densitised face field B~ evenly "
+                   "across the pole, but B~ = sqrt(gamma) B carries sqrt(gamma) ~ sin(theta): the EMFs "
+                   "reconstruct B~^r across a kink and the rate of B~^r is off by O(1) within three rows "
+                   "of the axis; continuing the r- and phi-face arrays oddly restores convergence")
+def test_induction_next_to_the_axis(orc):
+    """The same pin on the rows next to the polar axis (theta from 0, axis
+    boundary), for an axisymmetric flow smooth across the pole."""
+    kw = dict(fields=_axis_fields, theta=(0.0, 1.0), bc=(1, 1, 2, 1, 0, 0), rows=(0, 1, 2, 3))
+    e32 = _induction_error(orc, 32, **kw)
+    e64 = _induction_error(orc, 64, **kw)
+    assert np.all(e32 <= 1e-5), e32
+    assert np.all(e32 / e64 >= 3.5), (e32, e64)
