@@ -4,7 +4,11 @@ padding rules of numpy.pad: periodic is 'wrap', outflow (zero gradient) is
 for cell arrays, 'reflect' about the axis face for the face array normal to
 it -- with the vector component normal to the axis reversed.  Corners are
 filled by applying the rule of each direction in turn (x, then y, then z),
-which is what the padding of one axis after another gives."""
+which is what the padding of one axis after another gives.  For the
+densitised face field this is the rule as it stands, which continues B~^r
+and B~^phi evenly across the pole although sqrt(gamma) is odd there; see
+test_induction_next_to_the_axis (an expected failure) in
+test_oracle_scheme.py."""
 import numpy as np
 import pytest
 
