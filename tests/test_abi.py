@@ -147,3 +147,12 @@ def test_kernel_names(lib):
     names = [_lib.echo_kernel_name(k) for k in range(_lib.ECHO_NK)]
     assert names[1] == "c2p" and names[3] == "faces_x" and len(set(names)) == _lib.ECHO_NK
     assert _lib.echo_kernel_name(99) == ""
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without the built library the binding raises
+    instead of running anything."""
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "libecho_missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load(build_if_needed=False)
