@@ -85,3 +85,17 @@ def test_adam_steps_under_constant_gradient(orc):
         P0 = P.copy()
         orc.mlp_adam(P, m, v, g, t, lr=1e-2, eps=1e-8)
         assert np.allclose(P - P0, -1e-2 * g / (np.abs(g) + 1e-8), rtol=1e-9, atol=1e-15), t
+
+
+def test_loss_is_the_weighted_mean_square(orc):
+    """The loss is the mean over samples of the squared standardised
+    residuals, the third output's weighted by w2 (the first two by 1)."""
+    rng = np.random.default_rng(4)
+    P = random_net(rng)
+    x, y = random_data(rng, 12)
+    o = orc.mlp_forward(P, x)
+    t = orc.mlp_targets(P, x, y)
+    for w2 in (0.5, 0.1):
+        loss, _ = orc.mlp_loss_grad(P, x, y, w2=w2)
+        want = np.mean(np.sum((o - t) ** 2 * np.array([1.0, 1.0, w2]), axis=1))
+        assert abs(loss - want) <= 1e-13 * want

@@ -106,6 +106,8 @@ MUTANTS = [
      "C[1 + j] = (Zw + B2) * vl[j] + vB * Bl[j];", PINS),
     ("speeds_root_metric_term", "echo_oracle.c", "((1.0 - v2 * a2) * m->gi[d][d] - (1.0 - a2) * vd * vd)",
      "((1.0 - v2 * a2) - (1.0 - a2) * vd * vd)", PINS),
+    ("mlp_loss_weight", "mlp_oracle.c", "double wgt[NO] = {1.0, 1.0, w2};", "double wgt[NO] = {1.0, 1.0, 1.0};",
+     MLP_PINS),
     ("c2p_pressure_dropped_root", "echo_oracle.c", "double p = gg * (Z * (1.0 - v2) - D * sq);",
      "double p = gg * (Z * (1.0 - v2) - D);", PINS),
 ]
