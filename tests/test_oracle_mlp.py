@@ -99,3 +99,22 @@ def test_loss_is_the_weighted_mean_square(orc):
         loss, _ = orc.mlp_loss_grad(P, x, y, w2=w2)
         want = np.mean(np.sum((o - t) ** 2 * np.array([1.0, 1.0, w2]), axis=1))
         assert abs(loss - want) <= 1e-13 * want
+
+
+def test_forward_is_the_layered_network(orc):
+    """The forward pass is the 9 -> 64 -> 64 -> 3 tanh network of the
+    parameter layout W1 (64x9) | b1 | W2 (64x64) | b2 | W3 (3x64) | b3, on
+    features standardised by the stored mean and std (numpy products)."""
+    rng = np.random.default_rng(5)
+    P = random_net(rng)
+    x, _ = random_data(rng, 10)
+    o1 = 64 * 9
+    W1, b1 = P[:o1].reshape(64, 9), P[o1:o1 + 64]
+    o2 = o1 + 64
+    W2, b2 = P[o2:o2 + 4096].reshape(64, 64), P[o2 + 4096:o2 + 4160]
+    o3 = o2 + 4160
+    W3, b3 = P[o3:o3 + 192].reshape(3, 64), P[o3 + 192:o3 + 195]
+    mu, sd = P[4995:4995 + 9], P[4995 + 9:4995 + 18]
+    h1 = np.tanh((x - mu) / sd @ W1.T + b1)
+    h2 = np.tanh(h1 @ W2.T + b2)
+    assert np.allclose(orc.mlp_forward(P, x), h2 @ W3.T + b3, rtol=1e-12, atol=1e-13)

@@ -108,6 +108,8 @@ MUTANTS = [
      "((1.0 - v2 * a2) - (1.0 - a2) * vd * vd)", PINS),
     ("mlp_loss_weight", "mlp_oracle.c", "double wgt[NO] = {1.0, 1.0, w2};", "double wgt[NO] = {1.0, 1.0, 1.0};",
      MLP_PINS),
+    ("mlp_standardisation", "mlp_oracle.c", "xs[i] = (x[i] - mu[i]) / sd[i];", "xs[i] = (x[i] - mu[i]) * sd[i];",
+     MLP_PINS),
     ("c2p_pressure_dropped_root", "echo_oracle.c", "double p = gg * (Z * (1.0 - v2) - D * sq);",
      "double p = gg * (Z * (1.0 - v2) - D);", PINS),
 ]
