@@ -385,22 +385,30 @@ const char *echo_kernel_name(int k);
  * monitoring hook that must not change the device's memory footprint while
  * a large run sits near the HBM limit.
  *   state: device pointer, FP64 host layout of an n[0] x n[1] x n[2] grid
- *          (as written by echo_get_state with on_device = 1).
+ *          (as written by echo_get_state with on_device = 1); its length
+ *          (echo_state_count of such a grid) is not checked and must be
+ *          the documented one.
  *   n, dx: host arrays of 3 (cells > 0, widths > 0).
  *   out6:  device pointer to 6 doubles, written with sum D dV, sum tau dV,
  *          sum S_x dV, sum S_y dV, sum S_z dV and max |div B~| (dV = dx dy dz),
  *          the same quantities echo_reduce reports.
  *   cuda_stream: stream to enqueue on (cudaStream_t, NULL = legacy stream).
+ * state and out6 must be device (or managed) memory of the current device;
+ * a host pointer or memory of another device returns ECHO_EINVAL with
+ * nothing launched.  An error pending from earlier work on this thread is
+ * reported as ECHO_ECUDA and left pending (not cleared), with nothing
+ * launched.
  * The per-row partial sums live in one file-scope device array of
  * ECHO_STATIC_MAX_ROWS x 6 doubles (3 MiB) that every GPU loading the
  * library holds until the process exits; calls allocate nothing (no
  * cudaMalloc, no library allocator).  Rows = n[1] * n[2] above
  * ECHO_STATIC_MAX_ROWS return ECHO_ERANGE; bad arguments ECHO_EINVAL.  The
  * first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race,
- * so order them on one stream.  Asynchronous: out6 is valid once the stream
- * reaches the call. */
+ * device, with that device current) and caches it for the life of the
+ * process -- the cached address does not survive a cudaDeviceReset of that
+ * device; make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race, so order them on one
+ * stream.  Asynchronous: out6 is valid once the stream reaches the call. */
 #define ECHO_STATIC_MAX_ROWS 65536
 int echo_totals_static(const double *state, const int *n, const double *dx, double *out6, void *cuda_stream);
 

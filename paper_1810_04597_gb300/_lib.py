@@ -287,14 +287,37 @@ def echo_kernel_name(k: int) -> str:
     return (load().echo_kernel_name(int(k)) or b"").decode()
 
 
+def static_state_count(n) -> int:
+    """Doubles of a host-layout state of an n[0] x n[1] x n[2] grid (the
+    length echo_totals_static reads)."""
+    nx, ny, nz = (int(v) for v in n)
+    return 5 * nx * ny * nz + nz * ny * (nx + 1) + nz * (ny + 1) * nx + (nz + 1) * ny * nx
+
+
 def echo_totals_static(state, n, dx, out6, stream_handle: int = 0):
     """Totals of a device state (torch CUDA tensor, FP64 host layout) into
     the device tensor out6 (6 doubles), allocating nothing.  For callers
-    that cannot allocate device memory; see include/echo.h."""
+    that cannot allocate device memory; see include/echo.h.
+
+    The C entry point cannot see the tensors' lengths or devices, so they
+    are checked here before anything is called: a state shorter than the
+    grid's host layout, an out6 of fewer than 6 doubles, or a tensor on
+    another device than the current one raise ValueError."""
+    if len(n) != 3 or len(dx) != 3 or any(int(v) < 1 for v in n):
+        raise ValueError("n and dx need 3 entries, n >= 1")
+    need = static_state_count(n)
+    if state.numel() < need:
+        raise ValueError(f"state holds {state.numel()} doubles, the {tuple(n)} grid needs {need}")
+    if out6.numel() < 6:
+        raise ValueError(f"out6 holds {out6.numel()} doubles, needs 6")
     s, ds = _ptr(state)
     o, do = _ptr(out6, writable=True)
-    if not (ds and do):
+    if not (ds == 1 and do == 1):
         raise TypeError("echo_totals_static takes device arrays")
+    import torch
+    cur = torch.cuda.current_device()
+    if state.device.index != cur or out6.device.index != cur:
+        raise ValueError(f"state and out6 must be on the current device cuda:{cur}")
     nn = (ctypes.c_int * 3)(*[int(v) for v in n])
     dd = (ctypes.c_double * 3)(*[float(v) for v in dx])
     rc = load().echo_totals_static(_P(s), nn, dd, _P(o), _P(stream_handle))

@@ -103,11 +103,12 @@ __global__ void __launch_bounds__(1024) k_rows_final(const double *rows, int nro
 }
 
 // Device address of the scratch array on the current device, looked up
-// once per device (cudaGetSymbolAddress with that device current).
-int scratch_for_current_device(double **out)
+// once per device (cudaGetSymbolAddress with that device current) and
+// cached for the life of the process; the cache does not survive a
+// cudaDeviceReset of that device.
+int scratch_for_current_device(int dev, double **out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    if (dev < 0 || dev >= kMaxDevices)
         return ECHO_ECUDA;
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_scratch[dev]) {
@@ -118,6 +119,21 @@ int scratch_for_current_device(double **out)
     }
     *out = g_scratch[dev];
     return ECHO_OK;
+}
+
+// True if p is device memory (or managed memory) of device dev: the kernels
+// below dereference it, so pageable or page-locked host memory and memory
+// of another device are rejected before anything is launched.
+bool on_device(const void *p, int dev)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the error this query raised
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged)
+        return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -133,8 +149,19 @@ extern "C" int echo_totals_static(const double *state, const int *n, const doubl
     const long long rows = (long long)n[1] * n[2];
     if (rows > ECHO_STATIC_MAX_ROWS)
         return ECHO_ERANGE;
+    // an error left pending by earlier work belongs to its owner: report it
+    // without clearing it and launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess)
+        return ECHO_ECUDA;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return ECHO_ECUDA;
+    }
+    if (!on_device(state, dev) || !on_device(out6, dev))
+        return ECHO_EINVAL;
     double *scratch = nullptr;
-    const int rc = scratch_for_current_device(&scratch);
+    const int rc = scratch_for_current_device(dev, &scratch);
     if (rc != ECHO_OK) {
         cudaGetLastError();
         return rc;
@@ -142,6 +169,8 @@ extern "C" int echo_totals_static(const double *state, const int *n, const doubl
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const unsigned blocks = (unsigned)((rows * 32 + 255) / 256);
     k_row_totals<<<blocks, 256, 0, s>>>(state, n[0], n[1], n[2], 1.0 / dx[0], 1.0 / dx[1], 1.0 / dx[2], scratch);
+    if (cudaGetLastError() != cudaSuccess)
+        return ECHO_ECUDA;
     k_rows_final<<<1, 1024, 0, s>>>(scratch, (int)rows, dx[0] * dx[1] * dx[2], out6);
     return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
 }

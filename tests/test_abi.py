@@ -156,3 +156,24 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(build, "LIB", str(tmp_path / "libecho_missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         _lib.load(build_if_needed=False)
+
+
+def test_static_totals_binding_checks_lengths_before_any_call():
+    """echo_totals_static reads a state whose length follows from n and
+    writes 6 doubles; the C entry point cannot see the buffers' lengths, so
+    the binding rejects short ones before it loads or calls anything (these
+    are CPU tensors: the length checks come first)."""
+    import torch
+    n = (4, 3, 2)
+    need = _lib.static_state_count(n)
+    assert need == 5 * 24 + 2 * 3 * 5 + 2 * 4 * 4 + 3 * 3 * 4
+    out6 = torch.zeros(6, dtype=torch.float64)
+    with pytest.raises(ValueError, match="state holds"):
+        _lib.echo_totals_static(torch.zeros(need - 1, dtype=torch.float64), n, (1.0, 1.0, 1.0), out6)
+    with pytest.raises(ValueError, match="out6 holds"):
+        _lib.echo_totals_static(torch.zeros(need, dtype=torch.float64), n, (1.0, 1.0, 1.0),
+                                torch.zeros(5, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        _lib.echo_totals_static(torch.zeros(need, dtype=torch.float64), (4, 3), (1.0, 1.0, 1.0), out6)
+    with pytest.raises(TypeError, match="device arrays"):
+        _lib.echo_totals_static(torch.zeros(need, dtype=torch.float64), n, (1.0, 1.0, 1.0), out6)
