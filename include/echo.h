@@ -101,7 +101,9 @@ typedef struct {
     long long c2p_calls;  /* cell inversions since bind */
     long long c2p_fail;   /* failed inversions since bind */
     long long floor_hits; /* cells reset by floors since bind */
-    long long fallback_faces; /* reserved (first-order face fallbacks) */
+    long long fallback_faces; /* reconstructed face sides replaced by their cell
+                               * (rho <= 0, p <= 0 or v^2 >= 1) since bind, on
+                               * the faces that bound owned cells, each once */
     long long mlp_fallback;   /* network guesses that needed the previous-Z restart */
     /* cell inversions since bind by their Newton iterations: [k] took k
      * iterations (network attempt and restart together), [ECHO_C2P_HIST - 1]
@@ -109,7 +111,10 @@ typedef struct {
     long long c2p_iter_hist[ECHO_C2P_HIST];
 } echo_totals;
 
-/* Create a context.  precision: 64 (FP64 everywhere) or 32 (FP32 storage
+/* Method: the grid and equations of the paper's solver (introduction: a 3-D
+ * finite-difference GRMHD code), read as the 3+1 Valencia form of ideal
+ * GRMHD on a stationary metric (Banyuls et al. 1997; Del Zanna et al. 2007).
+ * Create a context.  precision: 64 (FP64 everywhere) or 32 (FP32 storage
  * and stencil arithmetic; c2p, metric and reductions in FP64).  cfl: the
  * Courant number of the CFL time step.  Validates the configuration;
  * returns ECHO_EINVAL (and *out = NULL) on a bad one, and also when the
@@ -120,7 +125,10 @@ typedef struct {
 int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *eos, int precision,
               double cfl, echo_ctx **out);
 
-/* Scheme order, before echo_bind (it changes the workspace size):
+/* Method: the paper's "high-order reconstruction" (introduction), read as the
+ * point-value finite-difference form with a flux-derivative correction
+ * (Del Zanna et al. 2007).
+ * Scheme order, before echo_bind (it changes the workspace size):
  * 0 (default) the scheme as read -- MP5 with the fifth-order interpolant of
  * cell averages on the point values, cell-centre B the mean of the two
  * faces, HLL fluxes and UCT EMFs differenced as they are; 1 high order --
@@ -148,7 +156,8 @@ size_t echo_state_count(const echo_ctx *ctx);
  * ECHO_ENOMEM if the workspace is too small, ECHO_EINVAL if misaligned. */
 int echo_bind(echo_ctx *ctx, void *dev_workspace, size_t bytes, void *cuda_stream);
 
-/* Initial data: cell primitives (5, nz, ny, nx) = rho, v^x, v^y, v^z, p
+/* Method: primitive -> conserved map of the Valencia form (Anton et al. 2006).
+ * Initial data: cell primitives (5, nz, ny, nx) = rho, v^x, v^y, v^z, p
  * (contravariant v) and the face field B~ in host face layout.  Converts
  * them to the conserved state on the device (cell-centre B = mean of the two
  * faces over sqrt(gamma)) and sets the Newton memory Z = rho h W^2. */
@@ -169,7 +178,9 @@ int echo_get_prims(echo_ctx *ctx, double *prims8, int on_device);
 /* Copy the Newton memory Z (nz*ny*nx doubles) out.  Synchronises. */
 int echo_get_z(echo_ctx *ctx, double *Z, int on_device);
 
-/* Conservative-to-primitive inversion of the current state on every owned
+/* Method: conservative-to-primitive inversion, a 1-D Newton iteration on
+ * Z = rho h W^2 (as in Noble et al. 2006, one-dimensional form).
+ * Conservative-to-primitive inversion of the current state on every owned
  * cell.  guess_mode: 0 = the stored Z of the cell (previous stage), 1 = the
  * c2p-guess network (see below), 2 = cold guess (Z = 0, replaced by the
  * admissibility rule); adding 4 refines the guess in FP32 first.  The
@@ -182,16 +193,25 @@ int echo_get_z(echo_ctx *ctx, double *Z, int on_device);
  * other fields are left untouched) and returns ECHO_EC2P if any cell failed. */
 int echo_c2p(echo_ctx *ctx, int guess_mode, echo_totals *stats);
 
-/* L(U) of the current state: c2p, ghost fill, reconstruction, HLL fluxes,
+/* Method: the semi-discrete right-hand side of the finite-difference scheme:
+ * MP5 reconstruction (Suresh & Huynh 1997), HLL fluxes (Harten, Lax & van
+ * Leer 1983), UCT-HLL edge EMFs (Londrillo & Del Zanna 2004), Valencia
+ * sources on a stationary metric.
+ * L(U) of the current state: c2p, ghost fill, reconstruction, HLL fluxes,
  * UCT EMFs, flux difference + sources, and minus the curl of the EMFs for the
  * face field.  Written in host layout (state_count doubles) to L. */
 int echo_rhs(echo_ctx *ctx, double *L, int on_device);
 
-/* One SSP-RK3 step.  dt > 0: that step size; dt <= 0: the CFL step
+/* Method: the three-stage SSP Runge-Kutta scheme (Shu & Osher 1988) with the
+ * CFL time step of the fastest characteristic speeds.
+ * One SSP-RK3 step.  dt > 0: that step size; dt <= 0: the CFL step
  * cfl / max_cells sum_d max|lambda_d|/dx^d from the first-stage primitives. */
 int echo_step(echo_ctx *ctx, double dt);
 
-/* Totals of the current state (runs a c2p for dt_cfl), copied to *out.
+/* Method: volume sums of the conserved variables (conserved to rounding on
+ * periodic grids by the flux form) and the discrete divergence of the
+ * constrained-transport face field (Evans & Hawley 1988).
+ * Totals of the current state (runs a c2p for dt_cfl), copied to *out.
  * Synchronises.  Returns ECHO_EC2P if an inversion failed since the last
  * call and floors are off. */
 int echo_reduce(echo_ctx *ctx, echo_totals *out);
@@ -214,7 +234,8 @@ int echo_reduce(echo_ctx *ctx, echo_totals *out);
 #define ECHO_MLP_BLOCK 5024
 #define ECHO_MLP_STATE (3 * ECHO_MLP_BLOCK)
 
-/* Glorot-uniform weights (counter-based generator seeded by seed), zero
+/* Method: Glorot & Bengio 2010 initialisation; splitmix64 generator.
+ * Glorot-uniform weights (counter-based generator seeded by seed), zero
  * biases and moments, identity standardisation. */
 int echo_mlp_init(float *dev_state, unsigned long long seed, void *cuda_stream);
 
@@ -227,7 +248,8 @@ size_t echo_mlp_work_bytes(int batch);
 int echo_mlp_normalize(float *dev_state, const float *X, const float *Y, long long n, void *dev_work,
                        size_t work_bytes, void *cuda_stream);
 
-/* nsteps Adam steps (lr; b1 0.9, b2 0.999, eps 1e-8) on minibatches of
+/* Method: Adam (Kingma & Ba 2015) on the squared-error loss of the network.
+ * nsteps Adam steps (lr; b1 0.9, b2 0.999, eps 1e-8) on minibatches of
  * `batch` consecutive rows, step t (from step0) starting at row
  * (t * batch) mod n.  losses (device, may be NULL) receives each step's
  * mean batch loss. */
@@ -235,7 +257,8 @@ int echo_mlp_train(float *dev_state, const float *X, const float *Y, long long n
                    long long step0, float lr, double gamma, void *dev_work, size_t work_bytes, float *losses,
                    void *cuda_stream);
 
-/* Gradient (ECHO_MLP_NPARAM floats, device) and mean loss (device float, may
+/* Method: reverse-mode differentiation (backpropagation) of that loss.
+ * Gradient (ECHO_MLP_NPARAM floats, device) and mean loss (device float, may
  * be NULL) of the batch loss over rows row0 .. row0+batch-1 (mod n). */
 int echo_mlp_grad(const float *dev_state, const float *X, const float *Y, long long n, long long row0, int batch,
                   double gamma, float *dev_grad, float *dev_loss, void *dev_work, size_t work_bytes,
@@ -250,7 +273,18 @@ int echo_mlp_forward(const float *dev_state, const float *X, long long n, float 
  * get NaN. */
 int echo_mlp_forward_tc(const float *dev_state, const float *X, long long n, float *out, void *cuda_stream);
 
-/* Training rows from the current state: runs a c2p (previous-stage guess),
+/* Relative error |Z0 - Z| / Z of the network's Newton start Z0 on n rows
+ * (features X, targets Y), for judging a trained network: the forward pass
+ * (tensor_cores 0: echo_mlp_forward, 1: echo_mlp_forward_tc) writes the
+ * standardised outputs to out (n x 3, device), then err (n floats, device)
+ * receives the error of Z0 = D W (1 + G/(G-1) (p/D) W) against the target
+ * Z = D exp(Y[:, 2]), evaluated in FP64 (gamma the adiabatic index). */
+int echo_mlp_guess_error(const float *dev_state, const float *X, const float *Y, long long n, double gamma,
+                         int tensor_cores, float *out, float *err, void *cuda_stream);
+
+/* Method: training pairs that the inversion itself produces (the network
+ * learns the Newton solve's converged answer).
+ * Training rows from the current state: runs a c2p (previous-stage guess),
  * then writes for every owned cell its features and targets at row
  * offset + perm(cell) * stride of X/Y (perm: a fixed permutation of the
  * cells).  offset + (cells-1) * stride must be below capacity (rows). */
@@ -260,7 +294,9 @@ int echo_mlp_dataset(echo_ctx *ctx, float *X, float *Y, long long capacity, long
  * the context. */
 int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
 
-/* Newton guess used by echo_step/echo_rhs: 0 previous-stage Z (default),
+/* Method: the initial guess of the Newton iteration (the iteration, not the
+ * guess, decides the converged result).
+ * Newton guess used by echo_step/echo_rhs: 0 previous-stage Z (default),
  * 1 network (requires echo_mlp_load), 2 cold (the guess of echo_c2p mode 2,
  * for measuring what the other guesses gain); adding 4 first refines that
  * guess by up to four Newton steps of the same residual in FP32 (the FP64
@@ -273,12 +309,13 @@ int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
 int echo_set_c2p_guess(echo_ctx *ctx, int mode);
 
 /* Copy the cumulative counters (c2p_iters, c2p_calls, c2p_fail, floor_hits,
- * mlp_fallback, c2p_iter_hist) to *out without running anything; other
+ * mlp_fallback, fallback_faces, c2p_iter_hist) to *out without running anything; other
  * fields untouched.  Synchronises. */
 int echo_counters(echo_ctx *ctx, echo_totals *out);
 
 /* ---- batch of independent runs (parameter sweeps) ----
- * The paper motivates the cost of exploring many parameters; a batch advances
+ * Method: independent runs of the scheme above, one time step of each per
+ * call.  The paper motivates the cost of exploring many parameters; a batch advances
  * up to ECHO_BATCH_MAXRUNS independent runs (same metric kind, precision,
  * adiabatic index and CFL number; sizes may differ), by default with ONE
  * persistent cooperative kernel per SSP-RK3 stage.  Each stage's phases (ghost fills,
@@ -328,24 +365,38 @@ int echo_batch_step(echo_batch *batch, double dt);
 const char *echo_batch_last_error(const echo_batch *batch);
 void echo_batch_destroy(echo_batch *batch);
 
-/* Self-check of the library's integer-pipe float <-> double conversions
+/* Method: IEEE 754 round-to-nearest-even binary64 -> binary32 conversion.
+ * Self-check of the library's integer-pipe float <-> double conversions
  * against the hardware casts on n hashed test values (all float classes,
  * doubles over and beyond the float range, exact rounding ties): adds the
  * number of mismatches to *dev_mismatch (device, caller-zeroed). */
 int echo_selftest_conversions(long long n, unsigned long long seed, unsigned long long *dev_mismatch,
                               void *cuda_stream);
-/* Self-check of the library's Newton-Raphson FP64 reciprocal (used in the
+/* Method: Newton-Raphson refinement r <- r + r (1 - d r) of a reciprocal.
+ * Self-check of the library's Newton-Raphson FP64 reciprocal (used in the
  * c2p Newton solve in place of IEEE divisions) against the IEEE quotient on n
  * hashed values (both signs, exponents -300..300): atomically maxes the
  * largest distance in ulp into *dev_max_ulp (device, caller-zeroed). */
 int echo_selftest_recip(long long n, unsigned long long seed, unsigned long long *dev_max_ulp, void *cuda_stream);
-/* Self-check of the library's integer-pipe scaling by powers of two (the
+/* Method: IEEE 754 binary64 exponent arithmetic (exact scaling by 2^k).
+ * Self-check of the library's integer-pipe scaling by powers of two (the
  * exponent-field add the FP64 kernels use for alpha times a difference in
  * the MP5 test and for the halves and doublings of the c2p Newton step)
  * against the FP64 products x*4, x*2, x*0.5 on n hashed values (both signs,
  * exponents -1000..1000, and signed zeros): adds the number of bit-pattern
  * mismatches to *dev_mismatch (device, caller-zeroed). */
 int echo_selftest_scale2(long long n, unsigned long long seed, unsigned long long *dev_mismatch, void *cuda_stream);
+
+/* Method: a register-only throughput probe (no counterpart in the paper).
+ * FP64 fused multiply-add throughput probe: echo_selftest_dfma_blocks()
+ * blocks of 256 threads (4 per SM of the current device; -1 if the device
+ * cannot be queried), each thread running 8 independent chains of `iters`
+ * FMAs in registers, then writing one double per thread to dev_out (device,
+ * at least 256 * blocks doubles, caller-owned).  *flops (host, may be NULL)
+ * receives the launch's floating-point operations (2 per FMA), so that the
+ * caller's event time around the launch gives the device's FP64 rate. */
+int echo_selftest_dfma_blocks(void);
+int echo_selftest_dfma(long long iters, double *dev_out, double *flops, void *cuda_stream);
 
 /* Kernel classes timed by the profiling facility below (ECHO_K_C2P includes
  * the network's own pass when the guess mode runs one). */

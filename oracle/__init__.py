@@ -92,7 +92,7 @@ def lib():
         L.oracle_ho_center.argtypes = [pd]
         L.oracle_ho_center.restype = d
         L.oracle_ghosts.restype = i
-        L.oracle_fill_padded.argtypes = [pc, pd, i, i]
+        L.oracle_fill_padded.argtypes = [pc, pd, i, i, i]
         L.oracle_speeds_point.argtypes = [pc, pd, pd, i, pd, pd]
         L.oracle_flux_point.argtypes = [pc, pd, pd, i, pd, pd]
         L.oracle_hll.argtypes = [pd, pd, pd, pd, d, d, pd]
@@ -216,15 +216,17 @@ def ghosts() -> int:
     return int(lib().oracle_ghosts())
 
 
-def fill_padded(cfg: OCfg, a: np.ndarray, comp: int, face: int) -> np.ndarray:
+def fill_padded(cfg: OCfg, a: np.ndarray, comp: int, face: int, dens: int = 0) -> np.ndarray:
     """The oracle's ghost fill applied to a copy of a padded array of shape
     (n2 + 2g, n1 + 2g, n0 + 2g); comp = the vector component it holds (-1
-    for a scalar), face = its face direction (-1 for a cell array)."""
+    for a scalar), face = its face direction (-1 for a cell array), dens = 1
+    for an array carrying the factor sqrt(gamma) (the densitised face
+    field), which is odd about a polar axis."""
     g = ghosts()
     shape = tuple(cfg.n[2 - k] + 2 * g for k in range(3))
     out = _f64(a).copy()
     assert out.shape == shape, (out.shape, shape)
-    lib().oracle_fill_padded(ctypes.byref(cfg), _dp(out), int(comp), int(face))
+    lib().oracle_fill_padded(ctypes.byref(cfg), _dp(out), int(comp), int(face), int(dens))
     return out
 
 

@@ -649,10 +649,13 @@ static int bc_source(const ocfg *c, int d, int i, int face, int *flip)
 }
 
 /* Fill the ghost layers of one padded array.  comp = the vector component
- * the array holds (0..2) or -1 for a scalar; a component along an axis
- * dimension changes sign under reflection.  face = -1 for a cell array,
- * else the face direction. */
-static void fill_array(const ocfg *c, const ogrid *G, double *a, int comp, int face)
+ * the array holds (0..2) or -1 for a scalar; face = -1 for a cell array,
+ * else the face direction; dens = 1 if the array carries the factor
+ * sqrt(gamma) (the densitised face field B~ = sqrt(gamma) B).  Under the
+ * reflection across a polar axis along d the component along d changes
+ * sign, and so does sqrt(gamma) ~ sin(theta), which is odd about the pole:
+ * the ghost value is negated when exactly one of the two holds. */
+static void fill_array(const ocfg *c, const ogrid *G, double *a, int comp, int face, int dens)
 {
     for (int d = 0; d < 3; ++d) {
         int isface = face == d;
@@ -673,7 +676,7 @@ static void fill_array(const ocfg *c, const ogrid *G, double *a, int comp, int f
                         int sidx[3] = {i, j, k};
                         sidx[d] = s;
                         val = a[IDX(G, sidx[0], sidx[1], sidx[2])];
-                        if (flip && comp == d)
+                        if (flip && ((comp == d) != (dens != 0)))
                             val = -val;
                     }
                     a[IDX(G, i, j, k)] = val;
@@ -683,18 +686,21 @@ static void fill_array(const ocfg *c, const ogrid *G, double *a, int comp, int f
 
 static void fill_prims(const ocfg *c, ogrid *G)
 {
-    fill_array(c, G, G->P[0], -1, -1);
+    fill_array(c, G, G->P[0], -1, -1, 0);
     for (int q = 0; q < 3; ++q)
-        fill_array(c, G, G->P[1 + q], q, -1);
-    fill_array(c, G, G->P[4], -1, -1);
+        fill_array(c, G, G->P[1 + q], q, -1, 0);
+    fill_array(c, G, G->P[4], -1, -1, 0);
     for (int q = 0; q < 3; ++q)
-        fill_array(c, G, G->P[5 + q], q, -1);
+        fill_array(c, G, G->P[5 + q], q, -1, 0);
 }
 
+/* The face field B~^d = sqrt(gamma) B^d: across a polar axis along theta the
+ * theta-face array is even (B^theta and sqrt(gamma) both odd) and the r- and
+ * phi-face arrays are odd. */
 static void fill_faces(const ocfg *c, ogrid *G)
 {
     for (int d = 0; d < 3; ++d)
-        fill_array(c, G, G->B[d], d, d);
+        fill_array(c, G, G->B[d], d, d, 1);
 }
 
 /* ------------------------------------------------------------------ */
@@ -841,7 +847,8 @@ static double cfl_rate_max(const ocfg *c, ogrid *G)
  * cell-centre B components; the normal component is the staggered B~^d
  * divided by the face sqrt(gamma).  If a reconstructed side has rho <= 0,
  * p <= 0 or v^2 >= 1, that side takes the adjacent cell's primitives
- * (first order). */
+ * (first order); fallback_faces counts those replacements on the faces
+ * that bound owned cells (each face once, both sides). */
 static void faces_dir(const ocfg *c, ogrid *G, int d, ostats *st)
 {
     int lo[3] = {0, 0, 0}, hi[3] = {G->np[0], G->np[1], G->np[2]};
@@ -871,6 +878,16 @@ static void faces_dir(const ocfg *c, ogrid *G, int d, ostats *st)
                         G->vR[d][cc][id] = 0.0;
                     }
                     continue;
+                }
+                /* counted fallbacks: faces that bound owned cells, each once (on a
+                 * periodic axis the face NG+n repeats NG) */
+                int owned = 1;
+                for (int a = 0; a < 3; ++a) {
+                    int top = NG + G->n[a] - 1;
+                    if (a == d && c->bc[2 * d] != BC_PERIODIC)
+                        top += 1;
+                    if (idx[a] < NG || idx[a] > top)
+                        owned = 0;
                 }
                 double PL[8], PR[8];
                 /* gather stencil cells f-3..f+2 along d */
@@ -902,7 +919,7 @@ static void faces_dir(const ocfg *c, ogrid *G, int d, ostats *st)
                         for (int q = 0; q < 8; ++q)
                             if (q != 5 + d)
                                 Ps[q] = G->P[q][src];
-                        fb += 1;
+                        fb += owned;
                     }
                 }
                 double FL[5], FR[5], UL[5], UR[5];
@@ -1343,8 +1360,8 @@ int oracle_ghosts(void) { return NG; }
 /* Ghost fill of one padded array (n[d] + 2 NG entries along each d, x
  * fastest; a face array holds face i-1/2 at index i) with the grid's
  * boundary conditions: the routine every step uses, exposed for the
- * boundary-condition pins.  comp and face as in fill_array. */
-void oracle_fill_padded(const ocfg *c, double *a, int comp, int face)
+ * boundary-condition pins.  comp, face and dens as in fill_array. */
+void oracle_fill_padded(const ocfg *c, double *a, int comp, int face, int dens)
 {
     ogrid G;
     memset(&G, 0, sizeof(G));
@@ -1353,7 +1370,7 @@ void oracle_fill_padded(const ocfg *c, double *a, int comp, int face)
         G.np[d] = c->n[d] + 2 * NG;
     }
     G.ncell = (size_t)G.np[0] * G.np[1] * G.np[2];
-    fill_array(c, &G, a, comp, face);
+    fill_array(c, &G, a, comp, face, dens);
 }
 
 /* Unlimited fifth-order value, for the polynomial-exactness pin. */
@@ -1482,7 +1499,7 @@ int oracle_rhs(const ocfg *c, const double *state, double *Z, double *L, double 
     if (rc == 0) {
         /* periodic axes: the duplicate last face repeats the first */
         for (int d = 0; d < 3; ++d)
-            fill_array(c, &G, G.LB[d], d, d);
+            fill_array(c, &G, G.LB[d], d, d, 1);
         pack_arrays(&G, G.LU, G.LB, L);
         pack_cell(&G, G.Z, Z);
     }

@@ -100,6 +100,8 @@ _SIGS = {
     "echo_selftest_conversions": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_selftest_recip": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_selftest_scale2": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
+    "echo_selftest_dfma_blocks": (ctypes.c_int, []),
+    "echo_selftest_dfma": (ctypes.c_int, [ctypes.c_longlong, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "echo_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
     "echo_batch_workspace_bytes": (ctypes.c_size_t, [_P]),
     "echo_batch_bind": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
@@ -121,6 +123,8 @@ _SIGS = {
                                      ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P]),
     "echo_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P]),
     "echo_mlp_forward_tc": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P]),
+    "echo_mlp_guess_error": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_double, ctypes.c_int, _P, _P,
+                                            _P]),
     "echo_mlp_dataset": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong]),
     "echo_mlp_load": (ctypes.c_int, [_P, _P]),
     "echo_set_c2p_guess": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -393,6 +397,12 @@ def echo_mlp_forward_tc(state, X, n, out, stream_handle: int = 0):
                                       _P(_dev_f32(out, "out")), _P(stream_handle)), "echo_mlp_forward_tc")
 
 
+def echo_mlp_guess_error(state, X, Y, n, gamma, tensor_cores, out, err, stream_handle: int = 0):
+    _plain(load().echo_mlp_guess_error(_P(_dev_f32(state, "state")), _P(_dev_f32(X, "X")), _P(_dev_f32(Y, "Y")),
+                                       int(n), float(gamma), 1 if tensor_cores else 0, _P(_dev_f32(out, "out")),
+                                       _P(_dev_f32(err, "err")), _P(stream_handle)), "echo_mlp_guess_error")
+
+
 def echo_mlp_dataset(ctx, X, Y, capacity, offset, stride):
     _check(ctx, load().echo_mlp_dataset(ctx, _P(_dev_f32(X, "X")), _P(_dev_f32(Y, "Y")), int(capacity),
                                         int(offset), int(stride)))
@@ -461,6 +471,23 @@ def echo_batch_step(b, dt=0.0):
 
 def echo_batch_destroy(b):
     load().echo_batch_destroy(b)
+
+
+def echo_selftest_dfma_blocks() -> int:
+    return int(load().echo_selftest_dfma_blocks())
+
+
+def echo_selftest_dfma(iters, dev_out, stream_handle: int = 0) -> float:
+    """Launch the FP64 FMA throughput probe; returns the launch's flop count.
+    dev_out: a device tensor of at least 256 * echo_selftest_dfma_blocks()
+    doubles."""
+    need = 256 * echo_selftest_dfma_blocks()
+    if dev_out.numel() < need or dev_out.element_size() != 8:
+        raise ValueError(f"dev_out needs {need} doubles")
+    f = ctypes.c_double(0.0)
+    _plain(load().echo_selftest_dfma(int(iters), _P(_dev_any(dev_out, "out")), ctypes.byref(f), _P(stream_handle)),
+           "echo_selftest_dfma")
+    return f.value
 
 
 def echo_selftest_scale2(n, seed, dev_mismatch, stream_handle: int = 0):

@@ -139,6 +139,7 @@ FillList<R> face_list(const Arrays<R> &A)
         L.a[d] = A.U[5 + d];
         L.comp[d] = d;
         L.face[d] = d;
+        L.dens[d] = 1;
     }
     L.count = 3;
     return L;
@@ -153,6 +154,7 @@ FillList<R> prim_list(const Arrays<R> &A)
         L.a[q] = A.P[q];
         L.comp[q] = comps[q];
         L.face[q] = -1;
+        L.dens[q] = 0;
     }
     L.count = 8;
     return L;
@@ -683,7 +685,7 @@ int echo_reduce(echo_ctx *c, echo_totals *out)
     out->c2p_calls = (long long)hs.c2p_calls;
     out->c2p_fail = (long long)hs.c2p_fail;
     out->floor_hits = (long long)hs.floor_hits;
-    out->fallback_faces = 0;
+    out->fallback_faces = (long long)hs.fallback_faces;
     out->mlp_fallback = (long long)hs.mlp_fallback;
     for (int k = 0; k < ECHO_C2P_HIST; ++k)
         out->c2p_iter_hist[k] = (long long)hs.c2p_hist[k];
@@ -712,6 +714,7 @@ int echo_counters(echo_ctx *c, echo_totals *out)
     out->c2p_fail = (long long)hs.c2p_fail;
     out->floor_hits = (long long)hs.floor_hits;
     out->mlp_fallback = (long long)hs.mlp_fallback;
+    out->fallback_faces = (long long)hs.fallback_faces;
     for (int k = 0; k < ECHO_C2P_HIST; ++k)
         out->c2p_iter_hist[k] = (long long)hs.c2p_hist[k];
     return ECHO_OK;

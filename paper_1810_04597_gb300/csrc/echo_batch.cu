@@ -136,6 +136,7 @@ FillList<R> faces_fill(const Arrays<R> &A)
         L.a[d] = A.U[5 + d];
         L.comp[d] = d;
         L.face[d] = d;
+        L.dens[d] = 1;
     }
     L.count = 3;
     return L;
@@ -150,6 +151,7 @@ FillList<R> prims_fill(const Arrays<R> &A)
         L.a[q] = A.P[q];
         L.comp[q] = comps[q];
         L.face[q] = -1;
+        L.dens[q] = 0;
     }
     L.count = 8;
     return L;

@@ -148,6 +148,7 @@ struct DevScalars {
     unsigned long long mlp_fallback;
     double totals[8];            // mass, energy, mom x3, max divB, rate, spare
     unsigned long long c2p_hist[ECHO_C2P_HIST];   // inversions by Newton iterations (last: that many or more)
+    unsigned long long fallback_faces;  // first-order face fallbacks on faces bounding owned cells (sides)
 };
 
 // Metric at one point of the axisymmetric (x1, x2) plane, FP64: lapse,

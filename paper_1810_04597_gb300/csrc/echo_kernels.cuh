@@ -78,7 +78,9 @@ __device__ __forceinline__ void fill_body(const Geom &g, int d, const FillList<R
         R val = R(0);
         if (src >= 0) {
             val = L.a[a][dst + (src - id_d) * sd];
-            if (flip && L.comp[a] == d)
+            // across a polar axis the component along d and the factor
+            // sqrt(gamma) ~ sin(theta) are odd: negate if exactly one applies
+            if (flip && ((L.comp[a] == d) != (L.dens[a] != 0)))
                 val = -val;
         }
         L.a[a][dst] = val;
@@ -695,6 +697,15 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
 #pragma unroll
             for (int m = 0; m < 7; ++m)
                 Ps[qs[m]] = A.P[qs[m]][c];
+            // counted on the faces that bound owned cells, each face once
+            bool owned = true;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int top = NG + g.n[a] - 1 + ((a == D && g.bc[2 * D] != BC_PERIODIC) ? 1 : 0);
+                owned = owned && ijk[a] >= NG && ijk[a] <= top;
+            }
+            if (owned)
+                atomicAdd(&A.scal->fallback_faces, 1ULL);
         }
     }
     T FL[5], UL[5], FR[5], UR[5], npL, nmL, YL, npR, nmR, YR;

@@ -12,12 +12,15 @@ template <typename R>
 struct Arrays;
 
 // Arrays whose ghost layers one fill pass updates.  comp: vector component
-// held (-1 scalar), face: face direction of a face-centred array (-1 cell).
+// held (-1 scalar), face: face direction of a face-centred array (-1 cell),
+// dens: 1 if the array carries the factor sqrt(gamma) (the densitised face
+// field), which is odd about a polar axis like the component normal to it.
 template <typename R>
 struct FillList {
     R *a[12];
     int comp[12];
     int face[12];
+    int dens[12];
     int count;
 };
 

@@ -338,6 +338,24 @@ __global__ void __launch_bounds__(128) k_mlp_forward_tc(const float *__restrict_
     tc_teardown(t);
 }
 
+// Relative error |Z0 - Z| / Z of the network's Newton start on each row,
+// from its standardised outputs `out` (n x 3, as the forward kernels write
+// them) and the rows' targets Y (log Z/D in column 2), in FP64:
+// Z0 / D = W (1 + G/(G-1) (p/D) W) with the de-standardised log W, log(p/D).
+__global__ void k_mlp_guess_error(const float *__restrict__ P, const float *__restrict__ out,
+                                  const float *__restrict__ y, long long n, double gr, float *__restrict__ err)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n)
+        return;
+    const double lw = (double)out[r * 3] * P[MLP_ONORM + 2 * MLP_NI + MLP_NO] + P[MLP_ONORM + 2 * MLP_NI];
+    const double lp = (double)out[r * 3 + 1] * P[MLP_ONORM + 2 * MLP_NI + MLP_NO + 1] + P[MLP_ONORM + 2 * MLP_NI + 1];
+    const double W = exp(lw);
+    const double z0 = W * (1.0 + gr * exp(lp) * W);
+    const double z = exp((double)y[r * 3 + 2]);
+    err[r] = (float)(fabs(z0 - z) / z);
+}
+
 }  // namespace echo
 
 using namespace echo;
@@ -426,6 +444,23 @@ int echo_mlp_forward_tc(const float *state, const float *x, long long n, float *
     const long long ntiles = (n + 127) / 128;
     const long long grid = ntiles < resident ? ntiles : resident;
     k_mlp_forward_tc<<<(unsigned)grid, 128, TC_SMEM, static_cast<cudaStream_t>(stream)>>>(state, x, n, out, ntiles);
+    return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
+}
+
+int echo_mlp_forward(const float *state, const float *x, long long n, float *out, void *stream);
+
+int echo_mlp_guess_error(const float *state, const float *x, const float *y, long long n, double gamma,
+                         int tensor_cores, float *out, float *err, void *stream)
+{
+    if (!state || !x || !y || !out || !err || n < 0 || !(gamma > 1.0) || (tensor_cores != 0 && tensor_cores != 1))
+        return ECHO_EINVAL;
+    if (n == 0)
+        return ECHO_OK;
+    const int rc = tensor_cores ? echo_mlp_forward_tc(state, x, n, out, stream) : echo_mlp_forward(state, x, n, out, stream);
+    if (rc != ECHO_OK)
+        return rc;
+    k_mlp_guess_error<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        state, out, y, n, gamma / (gamma - 1.0), err);
     return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
 }
 

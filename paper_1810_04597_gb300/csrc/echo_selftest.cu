@@ -1,7 +1,9 @@
 // echo_selftest.cu -- self-check of device helpers that replace hardware
 // instructions: the integer-pipe float <-> double conversions must equal the
 // hardware casts bit for bit; the Newton-Raphson reciprocal must stay within
-// 2 ulp of the IEEE quotient.
+// 2 ulp of the IEEE quotient.  Also a register-only FP64 FMA throughput probe
+// whose measured rate is the FP64 roofline peak the benchmark reports
+// against.
 #include "../../include/echo.h"
 #include "echo_device.cuh"
 
@@ -103,7 +105,55 @@ __global__ void k_check_scale2(long long n, unsigned long long seed, unsigned lo
         atomicAdd(mismatch, bad);
 }
 
+// FP64 fused multiply-add throughput: every thread runs 8 independent
+// chains c <- c * b + a for `iters` rounds in registers (no memory traffic
+// inside the loop) and writes one sum, so the compiler cannot drop the work.
+// a and b come from the arguments; with b slightly below 1 and a small the
+// chains stay finite.
+constexpr int kDfmaChains = 8;
+
+__global__ void __launch_bounds__(256) k_dfma_throughput(long long iters, double a, double b, double *out)
+{
+    double c[kDfmaChains];
+#pragma unroll
+    for (int q = 0; q < kDfmaChains; ++q)
+        c[q] = (double)(threadIdx.x + q);
+    for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < kDfmaChains; ++q)
+            c[q] = fma(c[q], b, a);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kDfmaChains; ++q)
+        s += c[q];
+    out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace echo
+
+extern "C" int echo_selftest_dfma_blocks(void)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)
+                                                   != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return 4 * sms;
+}
+
+extern "C" int echo_selftest_dfma(long long iters, double *dev_out, double *flops, void *stream)
+{
+    const int blocks = echo_selftest_dfma_blocks();
+    if (iters < 1 || !dev_out || blocks < 1)
+        return ECHO_EINVAL;
+    echo::k_dfma_throughput<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        iters, 1e-3, 0.999999, dev_out);
+    if (flops)
+        *flops = 2.0 * echo::kDfmaChains * (double)iters * 256.0 * (double)blocks;
+    return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
+}
 
 extern "C" int echo_selftest_scale2(long long n, unsigned long long seed, unsigned long long *dev_mismatch,
                                     void *stream)

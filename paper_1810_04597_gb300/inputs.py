@@ -536,6 +536,40 @@ def fm_torus(n=(64, 32, 32), spin=0.9, beta=100.0, r_in=6.0, r_max=12.0, r_out=5
                    steps=steps, seed=seed, prims=prims, bface=pack_faces(bx, by, bz))
 
 
+def polar_cap(n=(24, 24, 8), spin=0.9, theta_max=1.0) -> Problem:
+    """A magnetised flow through the polar axis on a Kerr-Schild patch:
+    ln r in [ln 4, ln 4 + 1], theta in [0, theta_max] (the axis at theta = 0,
+    outflow at theta_max), phi periodic over [0, 2 pi).  Everything is smooth
+    across the pole: rho = 1 + 0.1 sin^2(theta) cos(phi), p = 1, coordinate
+    velocities v^1 = 0.05 cos(theta)/r, v^theta = 0.02 sin(theta) cos(theta)/r,
+    v^phi = 0.01/r; the face field is the discrete coordinate curl of edge
+    potentials A_phi = 0.02 sin^2(theta)/r, A_theta = 0.01 sin(theta)/r^2
+    (B~^r odd in theta, B~^theta even, B~^phi odd, with div B~ = 0 to
+    rounding and B~^theta = 0 on the axis faces).  No floors."""
+    nr, nt, nph = (int(v) for v in n)
+    x0 = (np.log(4.0), 0.0, 0.0)
+    dx = (1.0 / nr, theta_max / nt, 2.0 * np.pi / nph)
+    x1c, thc, phc = (x0[d] + (np.arange(n[d]) + 0.5) * dx[d] for d in range(3))
+    PH, TH, X1 = np.meshgrid(phc, thc, x1c, indexing="ij")     # (nph, nt, nr)
+    r = np.exp(X1)
+    prims = np.zeros((5, nph, nt, nr))
+    prims[0] = 1.0 + 0.1 * np.sin(TH) ** 2 * np.cos(PH)
+    prims[1] = 0.05 * np.cos(TH) / r
+    prims[2] = 0.02 * np.sin(TH) * np.cos(TH) / r
+    prims[3] = 0.01 / r
+    prims[4] = 1.0
+    x1f = x0[0] + np.arange(nr + 1) * dx[0]
+    thf = np.arange(nt + 1) * dx[1]
+    Ax = np.zeros((nph + 1, nt + 1, nr))
+    # A_theta at (i-1/2, j, k-1/2), A_phi at (i-1/2, j-1/2, k)
+    Ay = np.broadcast_to((0.01 * np.sin(thc)[:, None] / np.exp(x1f)[None, :] ** 2)[None], (nph + 1, nt, nr + 1))
+    Az = np.broadcast_to((0.02 * np.sin(thf)[:, None] ** 2 / np.exp(x1f)[None, :])[None], (nph, nt + 1, nr + 1))
+    bx, by, bz = curl_faces((nr, nt, nph), dx, Ax, Ay, Az)
+    return Problem(name=f"polar_cap_{nr}x{nt}x{nph}", n=(nr, nt, nph), x0=x0, dx=dx,
+                   bc=(OUTFLOW, OUTFLOW, AXIS, OUTFLOW, PERIODIC, PERIODIC), metric=1, spin=float(spin),
+                   steps=10, prims=prims, bface=pack_faces(bx, by, bz))
+
+
 def michel_accretion(n_r: int, r_in=3.0, r_out=20.0, r_c=8.0, rho_c=1.0, gamma=4.0 / 3.0, order=0) -> Problem:
     """Michel (1972) steady spherical accretion of a polytropic gas (p = K
     rho^G) onto a Schwarzschild black hole (M = 1), transonic at r_c, on an

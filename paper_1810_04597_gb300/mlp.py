@@ -77,22 +77,16 @@ def train(X, Y, epochs=2, batch=8192, lr=1e-3, seed=1, gamma=4.0 / 3.0, device="
 
 def guess_error(state, X, Y, gamma=4.0 / 3.0, tensor_cores=False):
     """Relative error |Z0 - Z| / Z of the network guess on rows (X, Y),
-    from the standardised outputs the library's forward kernel returns:
-    the FP32 CUDA-core forward, or with tensor_cores the BF16 tensor-core
-    forward that c2p uses."""
+    computed by the library (``echo_mlp_guess_error``): the FP32 CUDA-core
+    forward, or with tensor_cores the BF16 tensor-core forward that c2p
+    uses."""
     import torch
     n = X.shape[0]
     out = torch.empty((n, 3), dtype=torch.float32, device=X.device)
-    fwd = _lib.echo_mlp_forward_tc if tensor_cores else _lib.echo_mlp_forward
-    fwd(state, X, n, out, torch.cuda.current_stream(X.device).cuda_stream)
-    blk = state[:_lib.ECHO_MLP_BLOCK].double()
-    ym, ys = blk[4995 + 18:4995 + 21], blk[4995 + 21:4995 + 24]
-    o = out.double() * ys + ym
-    gr = gamma / (gamma - 1.0)
-    W = torch.exp(o[:, 0])
-    z0 = W * (1.0 + gr * torch.exp(o[:, 1]) * W)
-    z = torch.exp(Y[:, 2].double())
-    return (z0 - z).abs() / z
+    err = torch.empty(n, dtype=torch.float32, device=X.device)
+    _lib.echo_mlp_guess_error(state, X, Y, n, gamma, tensor_cores, out, err,
+                              torch.cuda.current_stream(X.device).cuda_stream)
+    return err
 
 
 def box_runs(n=128):

@@ -60,6 +60,25 @@ def test_batch_equals_runs_one_at_a_time(tile, dyn, graph, mode, branches):
             assert np.max(np.abs(got - r)) <= 1e-12 * np.max(np.abs(r)), np.max(np.abs(got - r))
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_batch_matches_the_oracle(orc, mode):
+    """Each of the three uneven tori advanced by the batch (FP64) under each
+    schedule matches the oracle's own run of that torus after 10 steps to
+    1e-11 per field (CFL dt per run)."""
+    from paper_1810_04597_gb300.batch import Batch
+    from gpu_util import oracle_run, per_field
+    runs = _tori()
+    probs = [s.problem for s in runs]
+    b = Batch(runs)
+    b.configure(mode=mode, branches=2 if mode == 2 else 1)
+    for _ in range(10):
+        b.step()
+    for s, p in zip(runs, probs):
+        st_o, _, _, _ = oracle_run(orc, p, 10)
+        errs = per_field(orc, s.get_state(), st_o, p.n)
+        assert max(errs.values()) <= 1e-11, (p.n, errs)
+
+
 def test_batch_flat_fixed_dt_and_counters():
     from paper_1810_04597_gb300.batch import Batch
     from paper_1810_04597_gb300.echo import Solver

@@ -66,3 +66,25 @@ def test_fp32_refined_guess_converges_to_the_same_state(precision):
     tol = 1e-12 if precision == 64 else 1e-6
     assert np.max(np.abs(a - b)) <= tol * np.max(np.abs(a))
     assert res[4][1] < res[0][1], (res[0][1], res[4][1])
+
+
+def test_fp64_throughput_probe():
+    """The FP64 FMA probe whose rate bench.py takes as the FP64 roofline
+    peak: the chains stay finite and the measured rate lies between a
+    quarter of and just above GB300's nominal FP64 peak (152 SMs x 2 FMA x 2
+    flop x 2.07 GHz = 1.26 TFLOP/s)."""
+    import torch
+    from paper_1810_04597_gb300 import _lib
+    blocks = _lib.echo_selftest_dfma_blocks()
+    out = torch.empty(256 * blocks, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+    _lib.echo_selftest_dfma(1000, out, s.cuda_stream)          # warm-up
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    flops = _lib.echo_selftest_dfma(20000, out, s.cuda_stream)
+    b.record(s)
+    torch.cuda.synchronize()
+    rate = flops / (a.elapsed_time(b) * 1e-3)
+    print(f"FP64 FMA probe: {rate / 1e12:.3f} TFLOP/s")
+    assert torch.isfinite(out).all()
+    assert 0.3e12 <= rate <= 1.4e12, rate

@@ -130,9 +130,12 @@ def test_parity_relativistic_shear(orc):
     step: the inversion of this state fails within the second without
     floors."""
     prob = inputs.relativistic_shear(32, B=(0.1, 0.05, 0.02))
-    st_g, _ = gpu_run(prob, 1)
+    st_g, s = gpu_run(prob, 1)
     st_o, _, _, stats = oracle_run(orc, prob, 1)
     assert stats["fallback_faces"] > 0
+    # the same face sides were replaced on both paths (counted on the faces
+    # that bound owned cells)
+    assert s.counters()["fallback_faces"] == stats["fallback_faces"]
     errs = per_field(orc, st_g, st_o, prob.n)
     assert max(errs.values()) <= 1e-11, errs
 
@@ -279,3 +282,44 @@ def test_mapped_host_buffers_match_staged_copies():
     assert rc == _lib.ECHO_EINVAL
     rc = _lib.load().echo_get_state(b.ctx, ctypes.c_void_p(plain.ctypes.data), 3)
     assert rc == _lib.ECHO_EINVAL
+
+
+def _inadmissible(orc, prob, cell):
+    """The p2c state of prob with tau = -10 D in one cell: tau + D < 0 admits
+    no Z > 0, so that inversion fails on both paths."""
+    cfg = orc.make_cfg(prob)
+    st, Z = orc.p2c(cfg, prob.prims, prob.bface)
+    N = prob.ncells
+    bad = st.copy()
+    bad[4 * N + cell] = -10.0 * bad[cell]
+    return cfg, bad, Z
+
+
+def test_inadmissible_state_returns_ec2p(orc):
+    """Floors off: a host-built state with one inadmissible cell makes
+    echo_c2p return ECHO_EC2P with that one failure counted (the oracle
+    fails on the same cell), and a step followed by echo_reduce reports it
+    too."""
+    from paper_1810_04597_gb300 import _lib
+    from paper_1810_04597_gb300.echo import Solver
+    prob = inputs.smooth_box(12, seed=5)
+    cfg, bad, Z = _inadmissible(orc, prob, cell=123)
+    _, _, ostats, orc_rc = orc.c2p(cfg, bad, Z, check=False)
+    assert orc_rc != 0 and ostats["fails"] == 1
+    s = Solver(prob)
+    s.set_state(bad, Z)
+    t = _lib.echo_totals()
+    with pytest.raises(_lib.EchoError) as e:
+        _lib.echo_c2p(s.ctx, 0, t)
+    assert e.value.code == _lib.ECHO_EC2P
+    assert t.c2p_fail == 1 and t.c2p_calls == prob.ncells
+    s2 = Solver(prob)
+    s2.set_state(bad, Z)
+    s2.step(1e-4)
+    with pytest.raises(_lib.EchoError) as e:
+        s2.reduce()
+    assert e.value.code == _lib.ECHO_EC2P
+    # the error is reported once: a clean state afterwards reduces normally
+    st, _ = orc.p2c(cfg, prob.prims, prob.bface)
+    s2.set_state(st, Z)
+    assert s2.reduce()["c2p_fail"] >= 1

@@ -2,13 +2,12 @@
 padding rules of numpy.pad: periodic is 'wrap', outflow (zero gradient) is
 'edge', and the polar axis is a mirror image -- 'symmetric' about the axis
 for cell arrays, 'reflect' about the axis face for the face array normal to
-it -- with the vector component normal to the axis reversed.  Corners are
-filled by applying the rule of each direction in turn (x, then y, then z),
-which is what the padding of one axis after another gives.  For the
-densitised face field this is the rule as it stands, which continues B~^r
-and B~^phi evenly across the pole although sqrt(gamma) is odd there; see
-test_induction_next_to_the_axis (an expected failure) in
-test_oracle_scheme.py."""
+it -- with the sign reversed for the vector component normal to the axis
+and, independently, for an array that carries the factor sqrt(gamma) (odd
+about the pole): the densitised face field B~ = sqrt(gamma) B is even in its
+theta component and odd in the others.  Corners are filled by applying the
+rule of each direction in turn (x, then y, then z), which is what the
+padding of one axis after another gives."""
 import numpy as np
 import pytest
 
@@ -35,7 +34,7 @@ def owned(n, g, bc_lo, d, face):
     return g, g + n
 
 
-def expected_fill(a, n, g, bc, comp, face):
+def expected_fill(a, n, g, bc, comp, face, dens=0):
     out = a.copy()
     for d in range(3):
         ax = 2 - d                       # x is the fastest (last numpy) axis
@@ -57,7 +56,7 @@ def expected_fill(a, n, g, bc, comp, face):
             take = [slice(None)] * 3
             take[ax] = slice(0, width) if side == 0 else slice(padded.shape[ax] - width, None)
             ghost = padded[tuple(take)]
-            if kind == AXIS and comp == d:
+            if kind == AXIS and ((comp == d) != bool(dens)):
                 ghost = -ghost
             parts.append(ghost)
         out = np.concatenate([parts[0], own, parts[1]], axis=ax)
@@ -82,14 +81,15 @@ def test_ghost_fill_is_numpy_padding(orc, setup):
     shape = tuple(n[2 - k] + 2 * g for k in range(3))
     for face in (-1, 0, 1, 2):
         for comp in (-1, 0, 1, 2):
-            a = np.full(shape, np.nan)
-            lo = [owned(n[d], g, bc[2 * d], d, face) for d in range(3)]
-            inner = (slice(*lo[2]), slice(*lo[1]), slice(*lo[0]))
-            a[inner] = rng.normal(size=a[inner].shape)
-            got = orc.fill_padded(cfg, a, comp, face)
-            want = expected_fill(a, n, g, bc, comp, face)
-            assert not np.isnan(got).any(), (setup, face, comp)
-            assert np.array_equal(got, want), (setup, face, comp)
+            for dens in (0, 1):
+                a = np.full(shape, np.nan)
+                lo = [owned(n[d], g, bc[2 * d], d, face) for d in range(3)]
+                inner = (slice(*lo[2]), slice(*lo[1]), slice(*lo[0]))
+                a[inner] = rng.normal(size=a[inner].shape)
+                got = orc.fill_padded(cfg, a, comp, face, dens)
+                want = expected_fill(a, n, g, bc, comp, face, dens)
+                assert not np.isnan(got).any(), (setup, face, comp, dens)
+                assert np.array_equal(got, want), (setup, face, comp, dens)
 
 
 def test_axis_keeps_a_smooth_field_smooth(orc):
@@ -113,3 +113,29 @@ def test_axis_keeps_a_smooth_field_smooth(orc):
         col = got[g, :, g]
         # the continuation of the profile past both poles is the profile itself
         assert np.allclose(col, prof, rtol=0, atol=1e-14), comp
+
+
+def test_axis_continues_the_densitised_face_field(orc):
+    """Independent of numpy: the face field of an axisymmetric field smooth
+    across the pole, B~^i = sqrt(gamma) B^i with sqrt(gamma) ~ sin(theta),
+    continues past both poles as its own profile: B~^r ~ sin(theta) f(theta)
+    with f even (odd in theta), B~^theta ~ sin(theta) sin(2 theta) (even),
+    B~^phi like B~^r.  r- and phi-face arrays sit at cell-centre theta, the
+    theta-face array at the faces (the axis faces hold 0)."""
+    n = (6, 12, 6)
+    g = orc.ghosts()
+    bc = SETUPS["kerr_schild"]
+    cfg = cfg_of(orc, n, bc)
+    dth = np.pi / n[1]
+    thc = (np.arange(n[1] + 2 * g) - g + 0.5) * dth
+    thf = (np.arange(n[1] + 2 * g) - g) * dth
+    shape = tuple(n[2 - k] + 2 * g for k in range(3))
+    cases = ((0, np.sin(thc) * np.cos(2 * thc), n[1]), (2, np.sin(thc) * (1.0 + np.cos(thc) ** 2), n[1]),
+             (1, np.sin(thf) * np.sin(2 * thf), n[1] + 1))
+    for face, prof, nown in cases:
+        a = np.full(shape, np.nan)
+        inner = (slice(g, g + n[2]), slice(g, g + nown), slice(g, g + n[0] + (face == 0)))
+        a[inner] = np.broadcast_to(prof[None, g:g + nown, None], a[inner].shape)
+        got = orc.fill_padded(cfg, a, face, face, 1)
+        col = got[g, :, g]
+        assert np.allclose(col, prof, rtol=0, atol=1e-14), face

@@ -70,7 +70,8 @@ MUTANTS = [
     ("bc_outflow_offset", "echo_oracle.c", "return side == 0 ? lo : hi;", "return side == 0 ? lo + 1 : hi;", PINS),
     ("bc_axis_mirror_offset", "echo_oracle.c", "return side == 0 ? 2 * NG - 1 - i : 2 * (NG + n) - 1 - i;",
      "return side == 0 ? 2 * NG - i : 2 * (NG + n) - 1 - i;", PINS),
-    ("bc_axis_no_flip", "echo_oracle.c", "if (flip && comp == d)", "if (flip && comp == -2)", PINS),
+    ("bc_axis_no_flip", "echo_oracle.c", "if (flip && ((comp == d) != (dens != 0)))", "if (flip && comp == -2)", PINS),
+    ("bc_axis_density_even", "echo_oracle.c", "if (flip && ((comp == d) != (dens != 0)))", "if (flip && comp == d)", PINS),
     ("coord_centre_shift", "echo_oracle.c", "+ 0.5 + off) * c->dx[d];", "+ off) * c->dx[d];", PINS),
     ("floor_power_sign", "echo_oracle.c", "return f0 * pow(exp(x1), pw);", "return f0 * pow(exp(x1), -pw);", PINS),
     ("c2p_v2_term", "echo_oracle.c", "SB * SB * (2.0 * Z + B2)) / (Z * Z * ZB * ZB)",

@@ -671,15 +671,15 @@ def test_induction_high_order_form_fifth_order(orc):
     assert np.all(e32 / e64 >= 20.0), (e32, e64)
 
 
-@pytest.mark.xfail(strict=True, reason="the axis rule continues the densitised face field B~ evenly "
-                   "across the pole, but B~ = sqrt(gamma) B carries sqrt(gamma) ~ sin(theta): the EMFs "
-                   "reconstruct B~^r across a kink and the rate of B~^r is off by O(1) within three rows "
-                   "of the axis; continuing the r- and phi-face arrays oddly restores convergence")
 def test_induction_next_to_the_axis(orc):
     """The same pin on the rows next to the polar axis (theta from 0, axis
-    boundary), for an axisymmetric flow smooth across the pole."""
+    boundary), for an axisymmetric flow smooth across the pole: with the
+    densitised face field continued as it is smooth (B~^r, B~^phi odd and
+    B~^theta even about the pole, since sqrt(gamma) ~ sin(theta)) the rate
+    of the face field converges there at third order (measured ratios 7.9
+    and 17 per halving)."""
     kw = dict(fields=_axis_fields, theta=(0.0, 1.0), bc=(1, 1, 2, 1, 0, 0), rows=(0, 1, 2, 3))
     e32 = _induction_error(orc, 32, **kw)
     e64 = _induction_error(orc, 64, **kw)
     assert np.all(e32 <= 1e-5), e32
-    assert np.all(e32 / e64 >= 3.5), (e32, e64)
+    assert np.all(e32 / e64 >= 6.0), (e32, e64)
