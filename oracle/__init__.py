@@ -65,6 +65,113 @@ def build(force: bool = False) -> str:
         return _LIB
 
 
+_COUNT_SRC = os.path.join(_HERE, "op_count.cpp")
+_COUNT_LIB = os.path.join(_BUILD, "libecho_oracle_count.so")
+_count_lib = None
+COUNT_PHASES = ("c2p", "cfl", "faces", "emf", "correct", "assemble", "ct", "rk", "other")
+COUNT_OPS = ("add", "mul", "div", "sqrt", "fn")
+
+
+def build_count(force: bool = False) -> str:
+    """Compile the operation-counting build (op_count.cpp: echo_oracle.c as
+    C++ with a counting number type, OpenMP as the plain build) into
+    ``oracle/_build/libecho_oracle_count.so``."""
+    with _lock:
+        os.makedirs(_BUILD, exist_ok=True)
+        if (not force and os.path.exists(_COUNT_LIB)
+                and all(os.path.getmtime(_COUNT_LIB) >= os.path.getmtime(f) for f in (_SRC, _COUNT_SRC))):
+            return _COUNT_LIB
+        tmp = _COUNT_LIB + f".{os.getpid()}.tmp"
+        cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c++17", "-fopenmp",
+               "-Wall", "-Wno-unused-variable", "-o", tmp, _COUNT_SRC]
+        subprocess.run(cmd, check=True, capture_output=True, text=True)
+        os.replace(tmp, _COUNT_LIB)
+        return _COUNT_LIB
+
+
+def count_lib():
+    """The counting build, with the entry points the counts need."""
+    global _count_lib
+    if _count_lib is None:
+        L = ctypes.CDLL(build_count())
+        P = ctypes.POINTER
+        d, i, ll = ctypes.c_double, ctypes.c_int, ctypes.c_longlong
+        pc, pd = P(OCfg), P(d)
+        L.oracle_p2c.argtypes = [pc, pd, pd, pd, pd]
+        L.oracle_p2c.restype = i
+        L.oracle_steps.argtypes = [pc, pd, pd, i, d, pd, P(ll)]
+        L.oracle_steps.restype = i
+        L.oracle_c2p.argtypes = [pc, pd, pd, pd, pd, P(ll)]
+        L.oracle_c2p.restype = i
+        L.oracle_mp5_face.argtypes = [pd]
+        L.oracle_mp5_face.restype = d
+        L.oracle_count_reset.argtypes = [i, i]
+        L.oracle_count_read.argtypes = [P(ll), P(ll), P(ll)]
+        L.oracle_count_nphase.restype = i
+        _count_lib = L
+    return _count_lib
+
+
+def count_read() -> dict:
+    """Counts since the last count_reset: {phase: {op: n, ..., "flops",
+    "units", "sampled", "per_unit"}} (per_unit: flops over the sampled
+    units)."""
+    L = count_lib()
+    nph = L.oracle_count_nphase()
+    c = (ctypes.c_longlong * (nph * len(COUNT_OPS)))()
+    u = (ctypes.c_longlong * nph)()
+    sm = (ctypes.c_longlong * nph)()
+    L.oracle_count_read(c, u, sm)
+    out = {}
+    for p in range(nph):
+        row = {op: int(c[p * len(COUNT_OPS) + k]) for k, op in enumerate(COUNT_OPS)}
+        row["flops"] = row["add"] + row["mul"] + row["div"] + row["sqrt"]
+        row["units"] = int(u[p])
+        row["sampled"] = int(sm[p])
+        row["per_unit"] = row["flops"] / row["sampled"] if sm[p] else None
+        out[COUNT_PHASES[p]] = row
+    return out
+
+
+def count_reset(sample_every: int = 1, cse: bool = False):
+    count_lib().oracle_count_reset(int(sample_every), 1 if cse else 0)
+
+
+def count_mp5_face(u5, cse: bool = False) -> tuple:
+    """(value, counts) of one MP5 interface value in the counting build:
+    the operations of a single reconstruction (outside any step)."""
+    count_reset(1, cse)
+    v = count_lib().oracle_mp5_face(_dp(_f64(u5)))
+    return v, count_read()["other"]
+
+
+def count_steps(cfg: OCfg, prims5: np.ndarray, bface: np.ndarray, nsteps: int, dt: float = 0.0,
+                sample_every: int = 1, cse: bool = False, state=None, Z=None):
+    """Operation counts of nsteps SSP-RK3 steps of the counting build, from
+    the primitives (the initial p2c is not counted) or, if given, from the
+    conserved state and Newton memory (state, Z); returns (counts per phase
+    as count_read gives them, c2p stats: iterations, calls, fails, floors,
+    fallback faces)."""
+    L = count_lib()
+    n = list(cfg.n)
+    N = n[0] * n[1] * n[2]
+    if state is None:
+        state = np.zeros(state_count(n))
+        Z = np.zeros(N)
+        count_reset(1, False)
+        _check(L.oracle_p2c(ctypes.byref(cfg), _dp(_f64(prims5)), _dp(_f64(bface)), _dp(state), _dp(Z)), "p2c")
+    else:
+        state = _f64(state).copy()
+        Z = _f64(Z).copy()
+    count_reset(sample_every, cse)
+    dts = np.zeros(max(int(nsteps), 1))
+    stats = (ctypes.c_longlong * 6)()
+    _check(L.oracle_steps(ctypes.byref(cfg), _dp(state), _dp(Z), int(nsteps), float(dt), _dp(dts), stats),
+           "steps")
+    return count_read(), dict(iters=stats[0], calls=stats[1], fails=stats[2], floors=stats[3],
+                              fallback_faces=stats[4], guard_faces=stats[5])
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -311,16 +418,17 @@ def rhs(cfg: OCfg, state: np.ndarray, Z: np.ndarray):
 
 def steps(cfg: OCfg, state: np.ndarray, Z: np.ndarray, nsteps: int, dt: float = 0.0):
     """nsteps SSP-RK3 steps; dt <= 0 selects the CFL dt.  Returns
-    (state, Z, dts, stats dict)."""
+    (state, Z, dts, stats dict: c2p iterations, calls, fails, floors,
+    first-order face fallbacks, faces the order-1 safeguard replaced)."""
     state = _f64(state).copy()
     Z = _f64(Z).copy()
     dts = np.zeros(max(int(nsteps), 1))
-    stats = (ctypes.c_longlong * 5)()
+    stats = (ctypes.c_longlong * 6)()
     rc = lib().oracle_steps(ctypes.byref(cfg), _dp(state), _dp(Z), int(nsteps), float(dt), _dp(dts),
                             stats)
     _check(rc, "steps")
     return state, Z, dts[:nsteps], dict(iters=stats[0], calls=stats[1], fails=stats[2],
-                                        floors=stats[3], fallback_faces=stats[4])
+                                        floors=stats[3], fallback_faces=stats[4], guard_faces=stats[5])
 
 
 def reduce(cfg: OCfg, state: np.ndarray):

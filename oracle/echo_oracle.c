@@ -44,6 +44,21 @@
 #include <string.h>
 #include <stdint.h>
 
+/* Hooks of the operation-counting build (op_count.cpp compiles this file as
+ * C++ with a number type that counts its arithmetic): OPC_PHASE(k) assigns
+ * the operations that follow to step k of the scheme, OPC_UNIT() counts one
+ * unit of that step (a cell, a face, an edge), OPC_UNCOUNTED opens a scope
+ * whose arithmetic is not the method's own: evaluating the closed-form
+ * metric and its derivatives (tabulated once for a fixed metric),
+ * coordinates of grid points, and selections (min, max, minmod, which
+ * return one of their arguments).  In this C build they do nothing. */
+#ifndef OPC_PHASE
+#define OPC_PHASE(k)
+#define OPC_UNIT()
+#define OPC_UNCOUNTED
+#endif
+enum { OPC_C2P, OPC_CFL, OPC_FACES, OPC_EMF, OPC_CORRECT, OPC_ASSEMBLE, OPC_CT, OPC_RK, OPC_OTHER, OPC_NPHASE };
+
 #define NG 5                 /* ghost layers: MP5 needs 3 cells on each side, the
                                 high-order flux correction two more faces */
 #define MP5_ALPHA 4.0
@@ -88,6 +103,7 @@ typedef struct {
     long long c2p_fail;
     long long floor_hits;
     long long fallback_faces;
+    long long guard_faces;    /* order 1: faces whose corrected fluxes the safeguard replaced */
 } ostats;
 
 /* ------------------------------------------------------------------ */
@@ -97,6 +113,7 @@ typedef struct {
 /* Inverse and determinant of a symmetric 3x3 matrix by cofactors. */
 static double inv3(const double m[3][3], double out[3][3])
 {
+    OPC_UNCOUNTED;
     double c00 = m[1][1] * m[2][2] - m[1][2] * m[2][1];
     double c01 = m[1][2] * m[2][0] - m[1][0] * m[2][2];
     double c02 = m[1][0] * m[2][1] - m[1][1] * m[2][0];
@@ -131,6 +148,7 @@ static double inv3(const double m[3][3], double out[3][3])
 static void metric_components(const ocfg *c, const double x[3], double *alpha,
                               double beta[3], double g[3][3])
 {
+    OPC_UNCOUNTED;
     memset(g, 0, 9 * sizeof(double));
     beta[0] = beta[1] = beta[2] = 0.0;
     if (c->metric == 0) {
@@ -155,6 +173,7 @@ static void metric_components(const ocfg *c, const double x[3], double *alpha,
 
 static void metric_eval(const ocfg *c, const double x[3], ometric *m)
 {
+    OPC_UNCOUNTED;
     metric_components(c, x, &m->alpha, m->beta, m->g);
     double det = inv3(m->g, m->gi);
     m->sqrtg = det > 0.0 ? sqrt(det) : 0.0;
@@ -164,6 +183,7 @@ static void metric_eval(const ocfg *c, const double x[3], ometric *m)
  * from padded indices. */
 static double coord(const ocfg *c, int d, int ipad, double off)
 {
+    OPC_UNCOUNTED;
     return c->x0[d] + ((double)(ipad - NG) + 0.5 + off) * c->dx[d];
 }
 
@@ -306,11 +326,13 @@ static double sgn(double a) { return (a > 0.0) - (a < 0.0); }
 
 static double minmod2(double a, double b)
 {
+    OPC_UNCOUNTED;
     return 0.5 * (sgn(a) + sgn(b)) * fmin(fabs(a), fabs(b));
 }
 
 static double minmod4(double w, double x, double y, double z)
 {
+    OPC_UNCOUNTED;
     double s = 0.125 * (sgn(w) + sgn(x)) * fabs((sgn(w) + sgn(y)) * (sgn(w) + sgn(z)));
     return s * fmin(fmin(fabs(w), fabs(x)), fmin(fabs(y), fabs(z)));
 }
@@ -480,6 +502,7 @@ typedef struct {
     double *Ec[3][2];   /* order 1: E_e corrected along (e+1)%3 [0] and (e+2)%3 [1] */
     double *LU[5], *LB[3];
     double *cellspeed;  /* per cell sum_d max|lambda_d|/dx_d */
+    double *mark;       /* order 1: 1 for a cell the positivity safeguard flags */
 } ogrid;
 
 static size_t IDX(const ogrid *G, int i, int j, int k)
@@ -514,6 +537,7 @@ static int grid_alloc(ogrid *G, const int n[3])
     for (int q = 0; q < 8; ++q) A(G->P[q]);
     A(G->Z);
     A(G->cellspeed);
+    A(G->mark);
 #undef A
     return ok ? 0 : -1;
 }
@@ -530,6 +554,7 @@ static void grid_free(ogrid *G)
     for (int q = 0; q < 8; ++q) free(G->P[q]);
     free(G->Z);
     free(G->cellspeed);
+    free(G->mark);
 }
 
 /* Number of doubles in a host state. */
@@ -709,6 +734,7 @@ static void fill_faces(const ocfg *c, ogrid *G)
 
 static double floor_value(double f0, double pw, const ocfg *c, double x1)
 {
+    OPC_UNCOUNTED;
     if (c->metric == 1)
         return f0 * pow(exp(x1), pw);
     return f0;
@@ -744,10 +770,12 @@ static void cell_centre_B(const ocfg *c, const ogrid *G, int i, int j, int k, do
 static int c2p_grid(const ocfg *c, ogrid *G, ostats *st)
 {
     long long iters = 0, fails = 0, floors = 0, calls = 0;
+    OPC_PHASE(OPC_C2P);
 #pragma omp parallel for collapse(2) reduction(+ : iters, fails, floors, calls)
     for (int k = NG; k < NG + G->n[2]; ++k)
         for (int j = NG; j < NG + G->n[1]; ++j)
             for (int i = NG; i < NG + G->n[0]; ++i) {
+                OPC_UNIT();
                 size_t id = IDX(G, i, j, k);
                 double x[3] = {coord(c, 0, i, 0), coord(c, 1, j, 0), coord(c, 2, k, 0)};
                 ometric m;
@@ -811,10 +839,12 @@ static int c2p_grid(const ocfg *c, ogrid *G, ostats *st)
 /* Per-cell CFL rate sum_d max(|l+_d|, |l-_d|) / dx_d from cell primitives. */
 static double cfl_rate_max(const ocfg *c, ogrid *G)
 {
+    OPC_PHASE(OPC_CFL);
 #pragma omp parallel for collapse(2)
     for (int k = NG; k < NG + G->n[2]; ++k)
         for (int j = NG; j < NG + G->n[1]; ++j)
             for (int i = NG; i < NG + G->n[0]; ++i) {
+                OPC_UNIT();
                 size_t id = IDX(G, i, j, k);
                 double x[3] = {coord(c, 0, i, 0), coord(c, 1, j, 0), coord(c, 2, k, 0)};
                 ometric m;
@@ -857,6 +887,7 @@ static void faces_dir(const ocfg *c, ogrid *G, int d, ostats *st)
     hi[d] = NG + G->n[d] + 1 + 2 * c->order;
     /* transverse: indices whose face stencil (along d) exists; all */
     long long fb = 0;
+    OPC_PHASE(OPC_FACES);
 #pragma omp parallel for collapse(2) reduction(+ : fb)
     for (int k = lo[2]; k < hi[2]; ++k)
         for (int j = lo[1]; j < hi[1]; ++j)
@@ -879,6 +910,7 @@ static void faces_dir(const ocfg *c, ogrid *G, int d, ostats *st)
                     }
                     continue;
                 }
+                OPC_UNIT();
                 /* counted fallbacks: faces that bound owned cells, each once (on a
                  * periodic axis the face NG+n repeats NG) */
                 int owned = 1;
@@ -973,10 +1005,12 @@ static void emf_dir(const ocfg *c, ogrid *G, int e)
     hi[a] += 2 * c->order;
     lo[b] -= 2 * c->order;
     hi[b] += 2 * c->order;
+    OPC_PHASE(OPC_EMF);
 #pragma omp parallel for collapse(2)
     for (int k = lo[2]; k < hi[2]; ++k)
         for (int j = lo[1]; j < hi[1]; ++j)
             for (int i = lo[0]; i < hi[0]; ++i) {
+                OPC_UNIT();
                 int idx[3] = {i, j, k};
                 size_t id = IDX(G, i, j, k);
                 /* stencils: along b on a-faces, along a on b-faces */
@@ -1061,6 +1095,7 @@ static void sources_point(const ocfg *c, const double x[3], const ometric *m, co
         return;
     double dal[3], dbe[3][3], dg[3][3][3];
     for (int d = 0; d < 3; ++d) {
+        OPC_UNCOUNTED;
         double h = c->dx[d];
         double wts[6] = {-1.0, 9.0, -45.0, 45.0, -9.0, 1.0};
         double offs[6] = {-3.0, -2.0, -1.0, 1.0, 2.0, 3.0};
@@ -1160,6 +1195,7 @@ static void owned_faces(const ocfg *c, int d, int *lo, int *hi)
  * built from the same corrected differences stays constant. */
 static void ho_correct(const ocfg *c, ogrid *G)
 {
+    OPC_PHASE(OPC_CORRECT);
     for (int d = 0; d < 3; ++d) {
 #pragma omp parallel for collapse(2)
         for (int k = NG; k < NG + G->n[2] + (d == 2); ++k)
@@ -1202,10 +1238,12 @@ static void ho_correct(const ocfg *c, ogrid *G)
  * fluxes and EMFs). */
 static void assemble(const ocfg *c, ogrid *G)
 {
+    OPC_PHASE(OPC_ASSEMBLE);
 #pragma omp parallel for collapse(2)
     for (int k = NG; k < NG + G->n[2]; ++k)
         for (int j = NG; j < NG + G->n[1]; ++j)
             for (int i = NG; i < NG + G->n[0]; ++i) {
+                OPC_UNIT();
                 size_t id = IDX(G, i, j, k);
                 size_t nb[3] = {IDX(G, i + 1, j, k), IDX(G, i, j + 1, k), IDX(G, i, j, k + 1)};
                 double x[3] = {coord(c, 0, i, 0), coord(c, 1, j, 0), coord(c, 2, k, 0)};
@@ -1231,6 +1269,7 @@ static void assemble(const ocfg *c, ogrid *G)
                 }
             }
     /* face field: dB~^x/dt = -(dE_z/dy - dE_y/dz), cyclic */
+    OPC_PHASE(OPC_CT);
     for (int d = 0; d < 3; ++d) {
         int a = (d + 1) % 3, b = (d + 2) % 3;
         int flo, fhi;
@@ -1242,6 +1281,7 @@ static void assemble(const ocfg *c, ogrid *G)
         for (int k = lo[2]; k <= hi[2]; ++k)
             for (int j = lo[1]; j <= hi[1]; ++j)
                 for (int i = lo[0]; i <= hi[0]; ++i) {
+                    OPC_UNIT();
                     int idx[3] = {i, j, k};
                     size_t id = IDX(G, i, j, k);
                     int ta[3] = {idx[0], idx[1], idx[2]};
@@ -1260,11 +1300,124 @@ static void assemble(const ocfg *c, ogrid *G)
     }
 }
 
+/* Order 1: admissibility safeguard of the flux-derivative correction, in up
+ * to GUARD_PASSES passes after assemble has formed L(U) with the corrected
+ * fluxes.  A pass forms every owned cell's stage result as the SSP-RK3
+ * stage would form it (stage 0: U + dt L; 1: 3/4 U0 + 1/4 (U + dt L);
+ * 2: 1/3 U0 + 2/3 (U + dt L)) for the five cell variables, with the
+ * cell-centre field of the current state, and flags (for good) every cell
+ * whose result the inversion (c2p_point, from the cell's Z) cannot invert;
+ * every face of a flagged cell then takes the uncorrected flux (the scheme
+ * of order 0) in place of the corrected one -- the same value for both
+ * cells sharing it, a periodic axis pairing the faces across the seam with
+ * the cells they bound -- and L(U) is assembled again.  A face replaced
+ * changes the result of the neighbouring cell too, hence the further
+ * passes; they stop when one flags no new cell.  U0: the stage base (the
+ * state after the first stage's inversion).  Returns the faces replaced,
+ * counted once each. */
+#define GUARD_PASSES 3
+
+static long long guard_mark(const ocfg *c, ogrid *G, double dt, int stage, double *const *U0)
+{
+    long long added = 0;
+    const double wa = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
+    const double wb = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+#pragma omp parallel for collapse(2) reduction(+ : added)
+    for (int k = NG; k < NG + G->n[2]; ++k)
+        for (int j = NG; j < NG + G->n[1]; ++j)
+            for (int i = NG; i < NG + G->n[0]; ++i) {
+                size_t id = IDX(G, i, j, k);
+                if (G->mark[id] != 0.0)
+                    continue;
+                double x[3] = {coord(c, 0, i, 0), coord(c, 1, j, 0), coord(c, 2, k, 0)};
+                ometric m;
+                metric_eval(c, x, &m);
+                double C[5];
+                for (int q = 0; q < 5; ++q) {
+                    double fe = G->U[q][id] + dt * G->LU[q][id];
+                    double u = stage == 0 ? fe : wa * U0[q][id] + wb * fe;
+                    C[q] = u / m.sqrtg;
+                }
+                double Bc[3] = {G->P[5][id], G->P[6][id], G->P[7][id]};
+                double P5[5], Zc;
+                int its;
+                if (c2p_point(&m, c->gamma, C, Bc, G->Z[id], P5, &Zc, &its)) {
+                    G->mark[id] = 1.0;
+                    added += 1;
+                }
+            }
+    return added;
+}
+
+/* Faces bounding a flagged cell take the uncorrected flux; returns the
+ * owned faces that now differ from their corrected value, counted once. */
+static long long guard_revert(const ocfg *c, ogrid *G)
+{
+    long long replaced = 0;
+    for (int d = 0; d < 3; ++d) {
+        int per = c->bc[2 * d] == BC_PERIODIC;
+        int hi[3] = {NG + G->n[0] - 1, NG + G->n[1] - 1, NG + G->n[2] - 1};
+        hi[d] = NG + G->n[d];
+#pragma omp parallel for collapse(2) reduction(+ : replaced)
+        for (int k = NG; k <= hi[2]; ++k)
+            for (int j = NG; j <= hi[1]; ++j)
+                for (int i = NG; i <= hi[0]; ++i) {
+                    int idx[3] = {i, j, k};
+                    /* the cells on the two sides of face idx along d */
+                    int lo_c[3] = {i, j, k}, hi_c[3] = {i, j, k};
+                    lo_c[d] -= 1;
+                    int f = 0;
+                    for (int side = 0; side < 2; ++side) {
+                        int *t = side == 0 ? lo_c : hi_c;
+                        if (t[d] < NG || t[d] >= NG + G->n[d]) {
+                            if (!per)
+                                continue;
+                            t[d] = NG + ((t[d] - NG) % G->n[d] + G->n[d]) % G->n[d];
+                        }
+                        if (G->mark[IDX(G, t[0], t[1], t[2])] != 0.0)
+                            f = 1;
+                    }
+                    if (!f)
+                        continue;
+                    size_t id = IDX(G, idx[0], idx[1], idx[2]);
+                    int changed = 0;
+                    for (int q = 0; q < 5; ++q) {
+                        changed |= G->Fc[d][q][id] != G->F[d][q][id];
+                        G->Fc[d][q][id] = G->F[d][q][id];
+                    }
+                    /* the periodic duplicate face NG + n is the face NG */
+                    if (changed && !(per && idx[d] == NG + G->n[d]))
+                        replaced += 1;
+                }
+    }
+    return replaced;
+}
+
+static long long ho_guard(const ocfg *c, ogrid *G, double dt, int stage, double *const *U0)
+{
+    OPC_PHASE(OPC_CORRECT);
+    memset(G->mark, 0, G->ncell * sizeof(double));
+    long long replaced = 0;
+    for (int pass = 0; pass < GUARD_PASSES; ++pass) {
+        if (!guard_mark(c, G, dt, stage, U0))
+            break;
+        replaced += guard_revert(c, G);
+        assemble(c, G);
+    }
+    return replaced;
+}
+
 /* One evaluation of L(U) on the grid G (U, B, Z set on owned cells).
  * save (may be NULL): 8 arrays that receive U and B~ right after the c2p,
- * i.e. after floors and failure fallbacks have reset the conserved state. */
-static int eval_rhs(const ocfg *c, ogrid *G, ostats *st, double *rate_max, double *const *save)
+ * i.e. after floors and failure fallbacks have reset the conserved state.
+ * dt: the step the stage takes, for the safeguard of order 1 (ho_guard):
+ * > 0 that step; < 0 the CFL step cfl / rate_max of this evaluation (rate_max
+ * then non-NULL); 0 no safeguard (L(U) alone, with no step to check).
+ * stage, U0: the SSP-RK3 stage (0..2) and its base state, for the same. */
+static int eval_rhs(const ocfg *c, ogrid *G, ostats *st, double *rate_max, double *const *save, double dt,
+                    int stage, double *const *U0)
 {
+    OPC_PHASE(OPC_OTHER);
     fill_faces(c, G);
     if (c2p_grid(c, G, st))
         return -1;
@@ -1284,6 +1437,10 @@ static int eval_rhs(const ocfg *c, ogrid *G, ostats *st, double *rate_max, doubl
     if (c->order)
         ho_correct(c, G);
     assemble(c, G);
+    if (c->order && dt != 0.0) {
+        double h = dt > 0.0 ? dt : c->cfl / *rate_max;
+        st->guard_faces += ho_guard(c, G, h, stage, stage == 0 ? save : U0);
+    }
     return 0;
 }
 
@@ -1467,7 +1624,7 @@ int oracle_c2p(const ocfg *c, const double *state, const double *Zguess, double 
     if (Zguess)
         unpack_cell(&G, Zguess, G.Z);
     fill_faces(c, &G);
-    ostats st = {0, 0, 0, 0, 0};
+    ostats st = {0, 0, 0, 0, 0, 0};
     int rc = c2p_grid(c, &G, &st);
     size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
     for (int q = 0; q < 8; ++q)
@@ -1494,8 +1651,8 @@ int oracle_rhs(const ocfg *c, const double *state, double *Z, double *L, double 
         return -2;
     unpack_state(&G, state);
     unpack_cell(&G, Z, G.Z);
-    ostats st = {0, 0, 0, 0, 0};
-    int rc = eval_rhs(c, &G, &st, rate_max, NULL);
+    ostats st = {0, 0, 0, 0, 0, 0};
+    int rc = eval_rhs(c, &G, &st, rate_max, NULL, 0.0, 0, NULL);
     if (rc == 0) {
         /* periodic axes: the duplicate last face repeats the first */
         for (int d = 0; d < 3; ++d)
@@ -1515,18 +1672,19 @@ int oracle_rhs(const ocfg *c, const double *state, double *Z, double *L, double 
  * (floors and failure fallbacks reset the conserved variables there).
  * dt_in > 0: fixed dt; otherwise dt = cfl / max_cells sum_d max|lambda_d|/dx_d
  * from the primitives of the first stage of each step.  dts (may be NULL)
- * receives the dt of each step; stats5 (may be NULL): c2p iterations, c2p
- * calls, c2p failures, floor hits, first-order fallback faces.
+ * receives the dt of each step; stats6 (may be NULL): c2p iterations, c2p
+ * calls, c2p failures, floor hits, first-order fallback faces, faces the
+ * order-1 safeguard replaced.
  * The state (host layout) and Z are updated in place. */
 int oracle_steps(const ocfg *c, double *state, double *Z, int nsteps, double dt_in, double *dts,
-                 long long *stats5)
+                 long long *stats6)
 {
     ogrid G;
     if (grid_alloc(&G, c->n))
         return -2;
     unpack_state(&G, state);
     unpack_cell(&G, Z, G.Z);
-    ostats st = {0, 0, 0, 0, 0};
+    ostats st = {0, 0, 0, 0, 0, 0};
     size_t N = G.ncell;
     double *U0[8];
     for (int q = 0; q < 8; ++q)
@@ -1538,11 +1696,13 @@ int oracle_steps(const ocfg *c, double *state, double *Z, int nsteps, double dt_
         double dt = dt_in;
         for (int s = 0; s < 3 && rc == 0; ++s) {
             double rmax = 0.0;
-            rc = eval_rhs(c, &G, &st, s == 0 && dt_in <= 0.0 ? &rmax : NULL, s == 0 ? U0 : NULL);
+            rc = eval_rhs(c, &G, &st, s == 0 && dt_in <= 0.0 ? &rmax : NULL, s == 0 ? U0 : NULL,
+                          s == 0 && dt_in <= 0.0 ? -1.0 : dt, s, U0);
             if (rc)
                 break;
             if (s == 0 && dt_in <= 0.0)
                 dt = c->cfl / rmax;
+            OPC_PHASE(OPC_RK);
             for (int q = 0; q < 8; ++q) {
                 int isface = q >= 5;
                 int d = q - 5;
@@ -1553,6 +1713,7 @@ int oracle_steps(const ocfg *c, double *state, double *Z, int nsteps, double dt_
                 for (int k = lo[2]; k <= hi[2]; ++k)
                     for (int j = lo[1]; j <= hi[1]; ++j)
                         for (int i = lo[0]; i <= hi[0]; ++i) {
+                            OPC_UNIT();
                             size_t id = IDX(&G, i, j, k);
                             if (s == 0)
                                 u[id] = u0[id] + dt * l[id];
@@ -1572,12 +1733,13 @@ int oracle_steps(const ocfg *c, double *state, double *Z, int nsteps, double dt_
         pack_arrays(&G, G.U, G.B, state);
         pack_cell(&G, G.Z, Z);
     }
-    if (stats5) {
-        stats5[0] = st.c2p_iters;
-        stats5[1] = st.c2p_calls;
-        stats5[2] = st.c2p_fail;
-        stats5[3] = st.floor_hits;
-        stats5[4] = st.fallback_faces;
+    if (stats6) {
+        stats6[0] = st.c2p_iters;
+        stats6[1] = st.c2p_calls;
+        stats6[2] = st.c2p_fail;
+        stats6[3] = st.floor_hits;
+        stats6[4] = st.fallback_faces;
+        stats6[5] = st.guard_faces;
     }
     for (int q = 0; q < 8; ++q)
         free(U0[q]);

@@ -36,6 +36,12 @@ MUTANTS = [
     ("fast_speed_dropped_cross_term", "echo_oracle.c", "double a2 = cs2 + ca2 - cs2 * ca2;",
      "double a2 = cs2 + ca2;", PINS),
     ("mlp_dropped_activation", "mlp_oracle.c", "a2[k] = tanh(s);", "a2[k] = s;", MLP_PINS),
+    ("guard_lower_cell_only", "echo_oracle.c", "for (int side = 0; side < 2; ++side) {\n                        int *t = side",
+     "for (int side = 0; side < 1; ++side) {\n                        int *t = side", HO_PINS),
+    ("guard_without_reassembly", "echo_oracle.c", "replaced += guard_revert(c, G);\n        assemble(c, G);",
+     "replaced += guard_revert(c, G);", HO_PINS),
+    ("guard_stage_weight", "echo_oracle.c", "(stage == 1 ? 0.75 : 1.0 / 3.0)", "(stage == 1 ? 0.25 : 1.0 / 3.0)",
+     HO_PINS),
     ("ho_dropped_fourth_difference", "echo_oracle.c", "return f5[2] - d2 / 24.0 + 3.0 * d4 / 640.0;",
      "return f5[2] - d2 / 24.0;", HO_PINS),
     ("ho_emf_correction_direction", "echo_oracle.c", "const double *Eb = c->order ? G->Ec[b][1] : G->E[b];",
