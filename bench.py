@@ -49,12 +49,42 @@ KMODEL = {
 }
 
 
-# FP64 floating-point operations per unit of each kernel class (FP64 path):
-# 2 x DFMA + DADD + DMUL thread instructions counted by ncu, including those
-# inside divisions and square roots, on one launch at 128^3 of the same input
-# recipe (sweep_box), divided by the units of that launch.  c2p depends on the
-# Newton iteration count (2.74 per call there); faces_y/z run the code of
-# faces_x with other strides.
+# The method's own FP64 operations per unit (the roofline numerator): read
+# from oracle/op_counts.json, which the oracle's operation-counting build
+# writes (oracle/count_ops.py: one step of this workload at 256^3 after the
+# warm-up steps; +, -, *, / and sqrt each one operation, every distinct
+# operation once per unit).  Read as data; nothing of the oracle runs here.
+OP_COUNTS_PATH = os.path.join(ROOT, "oracle", "op_counts.json")
+
+
+def load_op_counts(path=None):
+    with open(path or OP_COUNTS_PATH) as f:
+        return json.load(f)
+
+
+def algorithmic_flops(counts, kernel, newton_iters):
+    """The method's FP64 operations per unit of a kernel class: faces per
+    face, EMFs per edge, update per cell (flux differences, CT curl, RK
+    combination), c2p per cell at the inversion's Newton iterations (the
+    oracle's count split into a part per cell and a part per iteration)."""
+    f = counts["flops_per_unit"]
+    if kernel.startswith("faces"):
+        return f["faces"]
+    if kernel.startswith("emf"):
+        return f["emf"]
+    if kernel == "update":
+        return counts["update_per_cell"]
+    if kernel == "c2p":
+        return counts["c2p_per_cell_fixed"] + counts["c2p_per_newton_iteration"] * newton_iters
+    return None
+
+
+# The kernels' own FP64 floating-point operations per unit (context beside
+# the algorithmic count): 2 x DFMA + DADD + DMUL thread instructions counted
+# by ncu, including those inside divisions and square roots, on one launch at
+# 128^3 of the same input recipe (sweep_box), divided by the units of that
+# launch.  c2p depends on the Newton iteration count (2.74 per call there);
+# faces_y/z run the code of faces_x with other strides.
 FLOPS64 = {
     64: {"faces_x": 520.2, "faces_y": 520.2, "faces_z": 520.2,
          "emf_x": 266.4, "emf_y": 266.4, "emf_z": 266.4,
@@ -72,9 +102,35 @@ FP64_INSTR = {
          "c2p": 289.4, "update": 53.0},
     32: {"c2p": 97.0},
 }
-# FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 DFMA lanes
-# per SM and clock x 2 flop x 2.07 GHz (the 1.25 TFLOP/s nominal figure).
+# Nominal FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2
+# DFMA lanes per SM and clock x 2 flop x 2.07 GHz (the 1.25 TFLOP/s figure);
+# the roofline uses the rate measured by the library's FP64 FMA probe
+# (measure_fp64_peak), this only if the probe cannot run.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def measure_fp64_peak(dev, repeats=3, iters=20000):
+    """FP64 rate of the library's register-only FMA probe
+    (echo_selftest_dfma), best of `repeats` launches timed with CUDA events:
+    (TFLOP/s, source)."""
+    import torch
+    from paper_1810_04597_gb300 import _lib
+    try:
+        blocks = _lib.echo_selftest_dfma_blocks()
+        out = torch.empty(256 * blocks, dtype=torch.float64, device=dev)
+        st = torch.cuda.current_stream(dev)
+        _lib.echo_selftest_dfma(1000, out, st.cuda_stream)
+        best = 0.0
+        for _ in range(repeats):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            flops = _lib.echo_selftest_dfma(iters, out, st.cuda_stream)
+            b.record(st)
+            torch.cuda.synchronize()
+            best = max(best, flops / (a.elapsed_time(b) * 1e-3) / 1e12)
+        return best, "measured: FP64 FMA throughput probe (echo_selftest_dfma), best of %d launches" % repeats
+    except Exception as exc:   # keep the bench line; say which peak it is
+        return FP64_PEAK_TFLOPS, f"nominal (probe failed: {exc})"
 # DRAM bytes per face of faces_x (dram__bytes_read.sum + dram__bytes_write.sum
 # of the same 128^3 ncu launch: 338,767,872 B over 2,316,324 faces); scaled to a
 # launch by the faces it processes.
@@ -305,6 +361,15 @@ def run_reference(args, world, rank):
     }
 
 
+OPS = load_op_counts() if os.path.exists(OP_COUNTS_PATH) else None
+
+
+def totals_c2p_iters(pair):
+    """Mean Newton iterations per inversion between two counter reads."""
+    a, b = pair
+    return (b["c2p_iters"] - a["c2p_iters"]) / max(b["c2p_calls"] - a["c2p_calls"], 1)
+
+
 def run_ours(args, world, rank, local, dist):
     import numpy as np
     import torch
@@ -329,6 +394,9 @@ def run_ours(args, world, rank, local, dist):
     for _ in range(args.warmup):
         s.step()
     torch.cuda.synchronize()
+    # the FP64 roofline peak: this GPU's rate on the library's FMA probe
+    fp64_peak, fp64_src = measure_fp64_peak(dev)
+    c_before = s.counters()
 
     # ---- timed region: K steps, device-resident inputs
     sampler = ClockSampler(gpu_index=None)
@@ -352,6 +420,8 @@ def run_ours(args, world, rank, local, dist):
     clocks = sampler.stop()
     ms_max = max_over_ranks(dist, ms)
     value = world * zones * args.steps / (ms_max * 1e-3) / 1e6
+    c_after = s.counters()
+    totals_run = (c_before, c_after)
     totals = s.reduce()
     fin64 = s.get_state() if (args.precision == 64 and not args.no_variants) else None
 
@@ -386,16 +456,22 @@ def run_ours(args, world, rank, local, dist):
                         "not counted)"}
     fl = FLOPS64[args.precision]
     if dom in fl:
-        # bound by the FP64 pipe, not by HBM
-        flops = units * fl[dom]
-        achieved = flops / avg_s / 1e12
+        # bound by the FP64 pipe, not by HBM: the method's operations (the
+        # oracle's count) per launch over the launch time, against the FP64
+        # rate the probe measures on this GPU
+        c_all = totals_c2p_iters(totals_run)
+        alg = algorithmic_flops(OPS, dom, c_all)
+        achieved = units * alg / avg_s / 1e12
+        kernel_achieved = units * fl[dom] / avg_s / 1e12
         traffic = units * TRAFFIC_PER_FACE64 if (dom.startswith("faces") and args.precision == 64) else None
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                "flops_per_unit": fl[dom], "units_per_launch": units,
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": traffic, "peak_source": fp64_src,
+                "flops_per_unit": alg, "flops_source": "the method's operations per unit, oracle counting build "
+                                                       "(oracle/op_counts.json)",
+                "units_per_launch": units,
+                "kernel_flops_per_unit_ncu": fl[dom], "kernel_flops_frac": kernel_achieved / fp64_peak,
                 "fp64_pipe_busy_ncu": FP64_PIPE_BUSY[args.precision].get(dom),
-                "fp64_instr_frac": units * FP64_INSTR[args.precision][dom] / avg_s / (FP64_PEAK_TFLOPS * 1e12 / 2),
+                "fp64_instr_frac": units * FP64_INSTR[args.precision][dom] / avg_s / (fp64_peak * 1e12 / 2),
                 "traffic_note": "dram bytes per face of a 128^3 ncu capture x faces per launch"
                 if traffic is not None else "no ncu traffic figure for this kernel and precision",
                 "avg_launch_ms": avg_s * 1e3, "hbm_context": hbm_ctx, "time_share": share}
@@ -470,7 +546,8 @@ def run_ours(args, world, rank, local, dist):
             "l1_rel_vs_fp64_gpu": l1, "max_l1": max(l1.values()),
             "mean_newton_iters": t32["c2p_iters"] / max(t32["c2p_calls"], 1),
             "c2p_guess": "previous-stage Z refined by FP32 Newton steps; FP64 Newton judges",
-            "roofline": fp32_c2p_roofline(prof32, ms32, zones),
+            "roofline": fp32_c2p_roofline(prof32, ms32, zones, t32["c2p_iters"] / max(t32["c2p_calls"], 1),
+                                          fp64_peak, fp64_src),
             "note": "FP32 storage/stencil, FP64 c2p and reductions; same input, same step count"}}
         del s32
         variants["fp64_high_order"] = run_order1_variant(args, prob, dev, world, dist, ms)
@@ -644,17 +721,25 @@ def run_mlp_variant(args, prob, dev, world, dist, fin64, names, bounds, ms64):
     return out, state
 
 
-def fp32_c2p_roofline(prof, ms, zones):
+def fp32_c2p_roofline(prof, ms, zones, newton_iters, fp64_peak, fp64_src):
     """The FP32-bulk path's dominant kernel is c2p, bound by the FP64 pipe:
-    FP64 flop per cell (ncu, FLOPS64[32]) x cells per launch / its live
-    CUDA-event launch time, against the FP64 peak."""
+    the method's FP64 operations per cell (the oracle's count at the FP64
+    Newton iterations this path takes; its FP32 refinement is not counted)
+    x cells per launch / its live CUDA-event launch time, against the
+    measured FP64 peak; the kernel's own ncu count beside it."""
     c_ms, c_n = prof["c2p"]
     avg_s = c_ms / max(c_n, 1) * 1e-3
-    achieved = zones * FLOPS64[32]["c2p"] / avg_s / 1e12
-    return {"kernel": "c2p", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_unit": FLOPS64[32]["c2p"], "units_per_launch": zones,
+    alg = algorithmic_flops(OPS, "c2p", newton_iters)
+    achieved = zones * alg / avg_s / 1e12
+    return {"kernel": "c2p", "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak, "peak_source": fp64_src, "flops_per_unit": alg,
+            "flops_source": "the method's FP64 operations per cell at %.2f FP64 Newton iterations, oracle counting "
+                            "build (oracle/op_counts.json)" % newton_iters,
+            "units_per_launch": zones,
+            "kernel_flops_per_unit_ncu": FLOPS64[32]["c2p"],
+            "kernel_flops_frac": zones * FLOPS64[32]["c2p"] / avg_s / 1e12 / fp64_peak,
             "fp64_pipe_busy_ncu": FP64_PIPE_BUSY[32]["c2p"], "avg_launch_ms": avg_s * 1e3,
-            "fp64_instr_frac": zones * FP64_INSTR[32]["c2p"] / avg_s / (FP64_PEAK_TFLOPS * 1e12 / 2),
+            "fp64_instr_frac": zones * FP64_INSTR[32]["c2p"] / avg_s / (fp64_peak * 1e12 / 2),
             "time_share": {k: round(v[0] / ms, 4) for k, v in prof.items() if v[1] > 0}}
 
 
@@ -699,14 +784,66 @@ def run_guess_gain(prob, dev, mlp_state, warm=2, steps=3):
             res[name] = {"c2p_ms_per_call": ms / max(nl, 1),
                          "mean_newton_iters": (c1["c2p_iters"] - c0["c2p_iters"]) / calls,
                          "p99_newton_iters": int(np.searchsorted(cum, 0.99)),
-                         "mlp_fallback_per_call": (c1["mlp_fallback"] - c0["mlp_fallback"]) / calls}
+                         "mlp_fallback_per_call": (c1["mlp_fallback"] - c0["mlp_fallback"]) / calls,
+                         "network_starts_per_call": (c1["mlp_used"] - c0["mlp_used"]) / calls}
+            del s
+        # a cold restart (state without its Newton memory): one inversion
+        for name, mode in (("restart_cold", modes["cold"]), ("restart_network", modes["network"])):
+            s = Solver(prob, precision=prec, device=str(dev))
+            s.set_prims()
+            s.mlp_load(mlp_state)
+            for _ in range(warm):
+                s.step()
+            s.set_state(s.get_state())
+            c0 = s.counters()
+            s.profile(True)
+            s.profile_read()
+            s.c2p(mode, stats=False)
+            prof = s.profile_read()
+            s.profile(False)
+            c1 = s.counters()
+            calls = max(c1["c2p_calls"] - c0["c2p_calls"], 1)
+            ms, nl = prof["c2p"]
+            res[name] = {"c2p_ms_per_call": ms / max(nl, 1),
+                         "mean_newton_iters": (c1["c2p_iters"] - c0["c2p_iters"]) / calls,
+                         "mlp_fallback_per_call": (c1["mlp_fallback"] - c0["mlp_fallback"]) / calls,
+                         "network_starts_per_call": (c1["mlp_used"] - c0["mlp_used"]) / calls}
             del s
         out[f"fp{prec}"] = res
+    # the torus atmosphere (held-out torus, FP64, 6 steps): the previous-stage
+    # Z against the per-cell choice
+    from paper_1810_04597_gb300 import inputs
+    tprob = inputs.fm_torus((96, 48, 48), spin=0.5, beta=30.0, seed=inputs.SEED_BASE + 299)
+    res = {}
+    for name, mode in (("previous", 0), ("network", 1)):
+        s = Solver(tprob, precision=64, device=str(dev))
+        s.set_prims()
+        s.mlp_load(mlp_state)
+        s.set_c2p_guess(mode)
+        c0 = s.counters()
+        s.profile(True)
+        s.profile_read()
+        for _ in range(6):
+            s.step()
+        prof = s.profile_read()
+        s.profile(False)
+        c1 = s.counters()
+        calls = max(c1["c2p_calls"] - c0["c2p_calls"], 1)
+        ms, nl = prof["c2p"]
+        res[name] = {"c2p_ms_per_call": ms / max(nl, 1),
+                     "mean_newton_iters": (c1["c2p_iters"] - c0["c2p_iters"]) / calls,
+                     "mlp_fallback_per_call": (c1["mlp_fallback"] - c0["mlp_fallback"]) / calls,
+                     "network_starts_per_call": (c1["mlp_used"] - c0["mlp_used"]) / calls,
+                     "c2p_fail_per_call": (c1["c2p_fail"] - c0["c2p_fail"]) / calls}
+        del s
+    out["torus_fp64"] = res
     out["note"] = ("c2p on the workload from each start: FP64 plain Newton, FP32 bulk with FP32 refinement and "
                    "one FP64 judging step; iterations are FP64 Newton iterations (network attempt and restart "
-                   "together); the previous-stage Z is the plain method's guess; network: tensor-core pass "
-                   "writing the starts, then the c2p kernel; network_inside_c2p: the same network fused into "
-                   "the c2p kernel")
+                   "together); the previous-stage Z is the plain method's guess; network: per-cell choice "
+                   "between the network start and the previous Z (tensor-core pass over the flagged tiles, "
+                   "then the c2p kernel); network_inside_c2p: the same choice with the network fused into the "
+                   "c2p kernel; restart_*: one inversion of the state without its Newton memory; torus_fp64: "
+                   "a held-out 96x48x48 torus (spin 0.5, beta 30), 6 steps")
     return out
 
 

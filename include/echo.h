@@ -109,6 +109,7 @@ typedef struct {
      * iterations (network attempt and restart together), [ECHO_C2P_HIST - 1]
      * that many or more; the entries sum to c2p_calls */
     long long c2p_iter_hist[ECHO_C2P_HIST];
+    long long mlp_used;   /* inversions since bind started from the network's Newton start */
 } echo_totals;
 
 /* Method: the grid and equations of the paper's solver (introduction: a 3-D
@@ -188,7 +189,8 @@ int echo_get_z(echo_ctx *ctx, double *Z, int on_device);
  * writes every cell's Newton start, followed by the plain c2p kernel; adding
  * 8 runs it in FP32 on the CUDA cores inside the c2p kernel instead, adding
  * 16 on the tensor cores inside the c2p kernel (the same starts, so the
- * same result as modes 1, 5).  Other values: ECHO_EINVAL.  If stats is non-NULL
+ * same result as modes 1, 5).  The network modes choose the start per cell
+ * as echo_set_c2p_guess describes.  Other values: ECHO_EINVAL.  If stats is non-NULL
  * the call synchronises and fills the counters and dt_cfl of stats (the
  * other fields are left untouched) and returns ECHO_EC2P if any cell failed. */
 int echo_c2p(echo_ctx *ctx, int guess_mode, echo_totals *stats);
@@ -224,6 +226,8 @@ int echo_reduce(echo_ctx *ctx, echo_totals *out);
  * relative error of its guess Z0 = D W (1 + G/(G-1) (p/D) W).  The Newton
  * solve in FP64 stays the judge: from the network guess it may take at most
  * 8 iterations, else it restarts from the previous-stage Z (counted).
+ * Float ECHO_MLP_GATE of the block (after the standardisation) holds the
+ * network's gate (echo_mlp_calibrate).
  * A network "state" is ECHO_MLP_STATE floats of device memory: parameters
  * and standardisation block (ECHO_MLP_BLOCK floats: W1 64x9, b1, W2 64x64,
  * b2, W3 3x64, b3, feature mean/std (9+9), target mean/std (3+3)), then
@@ -290,6 +294,17 @@ int echo_mlp_guess_error(const float *dev_state, const float *X, const float *Y,
  * cells).  offset + (cells-1) * stride must be below capacity (rows). */
 int echo_mlp_dataset(echo_ctx *ctx, float *X, float *Y, long long capacity, long long offset, long long stride);
 
+/* The network's gate: writes to the state's block (float ECHO_MLP_GATE)
+ * the mean over n rows (features X, targets Y, device) of log10 of its
+ * Newton-start error, the network's typical error, below which a cell's
+ * previous-stage Z is not expected to lose to it (see echo_set_c2p_guess).
+ * out (n x 3) and err (n) are caller-owned device work arrays, as for
+ * echo_mlp_guess_error (the tensor-core forward that c2p uses).  The gate
+ * is 0 (an error of 1: only cold starts consult the network) until set. */
+#define ECHO_MLP_GATE 5019
+int echo_mlp_calibrate(float *dev_state, const float *X, const float *Y, long long n, double gamma, float *out,
+                       float *err, void *cuda_stream);
+
 /* Copy a trained network (the first ECHO_MLP_BLOCK floats of a state) into
  * the context. */
 int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
@@ -300,9 +315,18 @@ int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
  * 1 network (requires echo_mlp_load), 2 cold (the guess of echo_c2p mode 2,
  * for measuring what the other guesses gain); adding 4 first refines that
  * guess by up to four Newton steps of the same residual in FP32 (the FP64
- * iterations that follow still decide convergence).  The network's hidden
- * layers run on the tensor cores (as echo_mlp_forward_tc) in a pass before
- * the c2p kernel; adding 8 to a network mode evaluates it in FP32 on the
+ * iterations that follow still decide convergence).  In the network modes
+ * the start is chosen per cell: every inversion records how far each cell's
+ * Z moved (an estimate of the error of the previous-stage Z as the next
+ * start) and flags the tiles of 128 cells where some cell moved at least as
+ * much as the network's calibrated typical error (echo_mlp_calibrate); the
+ * network is evaluated in flagged tiles only, and a cell there starts from
+ * it only where its predicted log10 error (third output) beats the previous
+ * Z's; all other cells start from the previous-stage Z (not counted as a
+ * fallback).  After echo_set_prims, or echo_set_state with Z, no tile is
+ * flagged; after echo_set_state without Z (a cold start) every tile is.
+ * The network's hidden layers run on the tensor cores (as
+ * echo_mlp_forward_tc) in a pass before the c2p kernel; adding 8 to a network mode evaluates it in FP32 on the
  * CUDA cores inside the c2p kernel (modes 9, 13), adding 16 on the tensor
  * cores inside the c2p kernel (modes 17, 21).  Accepted: 0, 1, 2, 4, 5, 6,
  * 9, 13, 17, 21. */

@@ -63,14 +63,14 @@ class echo_totals(ctypes.Structure):
                 ("c2p_iters", ctypes.c_longlong), ("c2p_calls", ctypes.c_longlong),
                 ("c2p_fail", ctypes.c_longlong), ("floor_hits", ctypes.c_longlong),
                 ("fallback_faces", ctypes.c_longlong), ("mlp_fallback", ctypes.c_longlong),
-                ("c2p_iter_hist", ctypes.c_longlong * ECHO_C2P_HIST)]
+                ("c2p_iter_hist", ctypes.c_longlong * ECHO_C2P_HIST), ("mlp_used", ctypes.c_longlong)]
 
     def as_dict(self):
         return dict(dt_cfl=self.dt_cfl, mass=self.mass, energy=self.energy, mom=list(self.mom),
                     max_divb=self.max_divb, c2p_iters=self.c2p_iters, c2p_calls=self.c2p_calls,
                     c2p_fail=self.c2p_fail, floor_hits=self.floor_hits,
                     fallback_faces=self.fallback_faces, mlp_fallback=self.mlp_fallback,
-                    c2p_iter_hist=list(self.c2p_iter_hist))
+                    c2p_iter_hist=list(self.c2p_iter_hist), mlp_used=self.mlp_used)
 
 
 # Exported entry points and their C signatures.
@@ -125,6 +125,7 @@ _SIGS = {
     "echo_mlp_forward_tc": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P]),
     "echo_mlp_guess_error": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_double, ctypes.c_int, _P, _P,
                                             _P]),
+    "echo_mlp_calibrate": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_double, _P, _P, _P]),
     "echo_mlp_dataset": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong]),
     "echo_mlp_load": (ctypes.c_int, [_P, _P]),
     "echo_set_c2p_guess": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -401,6 +402,15 @@ def echo_mlp_guess_error(state, X, Y, n, gamma, tensor_cores, out, err, stream_h
     _plain(load().echo_mlp_guess_error(_P(_dev_f32(state, "state")), _P(_dev_f32(X, "X")), _P(_dev_f32(Y, "Y")),
                                        int(n), float(gamma), 1 if tensor_cores else 0, _P(_dev_f32(out, "out")),
                                        _P(_dev_f32(err, "err")), _P(stream_handle)), "echo_mlp_guess_error")
+
+
+ECHO_MLP_GATE = 5019
+
+
+def echo_mlp_calibrate(state, X, Y, n, gamma, out, err, stream_handle: int = 0):
+    _plain(load().echo_mlp_calibrate(_P(_dev_f32(state, "state")), _P(_dev_f32(X, "X")), _P(_dev_f32(Y, "Y")),
+                                     int(n), float(gamma), _P(_dev_f32(out, "out")), _P(_dev_f32(err, "err")),
+                                     _P(stream_handle)), "echo_mlp_calibrate")
 
 
 def echo_mlp_dataset(ctx, X, Y, capacity, offset, stride):

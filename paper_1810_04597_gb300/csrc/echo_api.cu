@@ -77,6 +77,8 @@ size_t layout(echo_ctx *c, char *base, Arrays<R> *A)
     }
     A->Z = reinterpret_cast<double *>(take(cells * sizeof(double)));
     A->zg = reinterpret_cast<float *>(take(cells * sizeof(float)));
+    A->ze = reinterpret_cast<unsigned char *>(take(cells));
+    A->tflag = reinterpret_cast<unsigned char *>(take((size_t)c->ntiles));
     A->mlp = reinterpret_cast<const float *>(take(MLP_BLOCK * sizeof(float)));
     A->met = MetTables{};
     A->met.np0 = c->geo.np[0];
@@ -169,6 +171,33 @@ Arrays<float> &arrays<float>(echo_ctx *c) { return c->af; }
 
 // ---- operations, templated on the storage type
 
+// The previous-Z error codes and tile flags of the network modes' per-cell
+// choice: after a new state an exact Newton memory (from p2c, or a Z the
+// caller passed) needs no network start; a cold one (no Z) flags every tile.
+int reset_start_memory(echo_ctx *c, bool exact, cudaStream_t s)
+{
+    unsigned char *ze = c->precision == 64 ? c->ad.ze : c->af.ze;
+    unsigned char *tf = c->precision == 64 ? c->ad.tflag : c->af.tflag;
+    if (cudaMemsetAsync(ze, exact ? ZE_EXACT : 0, (size_t)c->geo.cells_padded, s) != cudaSuccess
+        || cudaMemsetAsync(tf, exact ? 0 : 1, (size_t)c->ntiles, s) != cudaSuccess)
+        return cuda_check(c, "start memory");
+    c->ze_valid = true;
+    return ECHO_OK;
+}
+
+// Only the network modes' inversions keep the codes up to date: before one
+// of them, codes left stale by plain-mode inversions are reset to "previous
+// Z exact" (the plain method's start everywhere until the next inversion
+// has measured the cells again).
+int prepare_start(echo_ctx *c, int mode, cudaStream_t s)
+{
+    if ((mode & 3) != 1) {
+        c->ze_valid = false;
+        return ECHO_OK;
+    }
+    return c->ze_valid ? ECHO_OK : reset_start_memory(c, true, s);
+}
+
 template <int MK, typename R>
 void enqueue_rhs_pass(echo_ctx *c, int stage, double *Lout, bool want_rate, double dt_fixed)
 {
@@ -192,6 +221,8 @@ template <int MK, typename R>
 int op_step(echo_ctx *c, double dt)
 {
     Arrays<R> &A = arrays<R>(c);
+    if (const int rc = prepare_start(c, c->c2p_guess, c->stream))
+        return rc;
     PROF(ECHO_K_SCALARS, launch_step_begin(A.scal, dt > 0.0 ? dt : 0.0, c->stream));
     for (int st = 0; st < 3; ++st)
         enqueue_rhs_pass<MK, R>(c, st, nullptr, st == 0, dt);
@@ -202,6 +233,8 @@ template <int MK, typename R>
 int op_rhs(echo_ctx *c, double *Lout)
 {
     Arrays<R> &A = arrays<R>(c);
+    if (const int rc = prepare_start(c, c->c2p_guess, c->stream))
+        return rc;
     launch_step_begin(A.scal, 0.0, c->stream);
     enqueue_rhs_pass<MK, R>(c, -1, Lout, true, 0.0);
     return cuda_check(c, "echo_rhs");
@@ -211,6 +244,8 @@ template <int MK, typename R>
 int op_c2p(echo_ctx *c, int guess_mode)
 {
     Arrays<R> &A = arrays<R>(c);
+    if (const int rc = prepare_start(c, guess_mode, c->stream))
+        return rc;
     PROF(ECHO_K_SCALARS, launch_step_begin(A.scal, 0.0, c->stream));
     PROF(ECHO_K_FILL_FACES, launch_fill<R>(c->geo, face_list(A), c->stream));
     PROF(ECHO_K_C2P, (launch_c2p<MK, R>(c->geo, c->ph, A, guess_mode, 1, c->stream)));
@@ -333,6 +368,7 @@ int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *
     for (int d = 0; d < 3; ++d)
         g.idx_f[d] = (float)g.idx[d];
     const size_t N = (size_t)grid->n[0] * grid->n[1] * grid->n[2];
+    c->ntiles = (long long)((N + 127) / 128);
     c->nstate = 5 * N + (size_t)g.n[2] * g.n[1] * (g.n[0] + 1) + (size_t)g.n[2] * (g.n[1] + 1) * g.n[0]
                 + (size_t)(g.n[2] + 1) * g.n[1] * g.n[0];
     c->staging_count = c->nstate > 8 * N ? c->nstate : 8 * N;
@@ -457,6 +493,8 @@ int echo_set_prims(echo_ctx *c, const double *prims5, const double *bface, int o
     }
     rc = cuda_check(c, "echo_set_prims");
     if (rc == ECHO_OK)
+        rc = reset_start_memory(c, true, c->stream);
+    if (rc == ECHO_OK)
         c->have_state = true;
     return rc;
 }
@@ -488,6 +526,8 @@ int echo_set_state(echo_ctx *c, const double *state, const double *Z, int on_dev
     else
         launch_unpack_z<float>(c->geo, dz, c->af, c->stream);
     rc = cuda_check(c, "echo_set_state");
+    if (rc == ECHO_OK)
+        rc = reset_start_memory(c, Z != nullptr, c->stream);
     if (rc == ECHO_OK)
         c->have_state = true;
     return rc;
@@ -602,6 +642,7 @@ int echo_c2p(echo_ctx *c, int guess_mode, echo_totals *stats)
     stats->c2p_fail = (long long)hs.c2p_fail;
     stats->floor_hits = (long long)hs.floor_hits;
     stats->mlp_fallback = (long long)hs.mlp_fallback;
+    stats->mlp_used = (long long)hs.mlp_used;
     for (int k = 0; k < ECHO_C2P_HIST; ++k)
         stats->c2p_iter_hist[k] = (long long)hs.c2p_hist[k];
     if (hs.fail_since_check) {
@@ -638,6 +679,8 @@ int echo_step(echo_ctx *c, double dt)
         return rc;
     return ECHO_DISPATCH(c, op_step, dt);
 }
+
+int echo_internal_prepare_start(echo_ctx *c, int mode, cudaStream_t s) { return prepare_start(c, mode, s); }
 
 // Enqueue one step of context c on another stream (used by the run-major
 // batch schedule); per-kernel timing is off while the batch records.
@@ -687,6 +730,7 @@ int echo_reduce(echo_ctx *c, echo_totals *out)
     out->floor_hits = (long long)hs.floor_hits;
     out->fallback_faces = (long long)hs.fallback_faces;
     out->mlp_fallback = (long long)hs.mlp_fallback;
+    out->mlp_used = (long long)hs.mlp_used;
     for (int k = 0; k < ECHO_C2P_HIST; ++k)
         out->c2p_iter_hist[k] = (long long)hs.c2p_hist[k];
     if (hs.fail_since_check) {
@@ -714,6 +758,7 @@ int echo_counters(echo_ctx *c, echo_totals *out)
     out->c2p_fail = (long long)hs.c2p_fail;
     out->floor_hits = (long long)hs.floor_hits;
     out->mlp_fallback = (long long)hs.mlp_fallback;
+    out->mlp_used = (long long)hs.mlp_used;
     out->fallback_faces = (long long)hs.fallback_faces;
     for (int k = 0; k < ECHO_C2P_HIST; ++k)
         out->c2p_iter_hist[k] = (long long)hs.c2p_hist[k];

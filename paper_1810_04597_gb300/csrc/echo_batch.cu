@@ -484,6 +484,15 @@ int echo_batch_step(echo_batch *b, double dt)
         if (c->geo.order != 0 && b->phased != 2)
             return bfail(b, ECHO_EINVAL, "runs of order 1 need the run-major schedule (echo_batch_mode 2)");
     }
+    // the runs' per-cell start codes, on the batch stream and outside any
+    // capture: run-major inverts with each run's own guess mode, the other
+    // schedules with the batch's (the network for every run, or none)
+    for (echo_ctx *c : b->runs) {
+        const int mode = b->phased == 2 ? c->c2p_guess : (b->mlp ? 1 : 0);
+        const int rc = echo_internal_prepare_start(c, mode, b->stream);
+        if (rc)
+            return bfail(b, rc, std::string("start codes: ") + c->err);
+    }
     if (!b->use_graph) {
         const int rc = enqueue_step(b, dt);
         return rc ? rc : bcheck(b, "echo_batch_step");

@@ -206,15 +206,17 @@ __global__ void __launch_bounds__(128) k_bphase_c2p(const RunDesc<R> *__restrict
 // The network's Newton starts for the cells of every run (tensor cores,
 // echo_mlp_tc.cuh), as k_mlp_guess_tc does for one run: persistent CTAs walk
 // the c2p phase's tiles in chunks of 128 cells (the plan's tile is a
-// multiple of 128), loading the next chunk's inputs during the current
-// chunk's MMA round trips.  All runs use runs[0]'s network.
+// multiple of 128, so a chunk is one of the run's own 128-cell tiles), skip
+// the chunks its last inversion did not flag, choose per cell between the
+// network start and the previous-stage Z, and load the next flagged chunk's
+// inputs during the current chunk's MMA round trips.  All runs use runs[0]'s
+// network.
 template <int MK, typename R>
 __global__ void __launch_bounds__(128, 6) k_bphase_guess_tc(const RunDesc<R> *__restrict__ runs,
                                                          const BatchPlan *__restrict__ plan, float gr_f)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    TcMlp tm;
-    tc_setup(tm, tc_smem, runs[0].A.mlp);
+    __shared__ int s_first;
     const long long cpt = plan->tile / 128;
     const long long nch = plan->ntiles[PH_C2P] * cpt;
     // run of chunk ch and the run-local index of its first cell
@@ -224,29 +226,44 @@ __global__ void __launch_bounds__(128, 6) k_bphase_guess_tc(const RunDesc<R> *__
         run = sgm.run;
         return (tl - sgm.first_tile) * plan->tile + (ch % cpt) * 128;
     };
+    auto flagged = [&](long long ch) {
+        int r = 0;
+        const long long b = locate(ch, r);
+        const Geom &g = runs[r].g;
+        return b < (long long)g.n[0] * g.n[1] * g.n[2] && runs[r].A.tflag[b >> 7] != 0;
+    };
+    long long ch = next_flagged(blockIdx.x, nch, gridDim.x, flagged, &s_first);
+    if (ch >= nch)
+        return;   // block-uniform: nothing flagged for this CTA (nothing allocated yet)
+    TcMlp tm;
+    tc_setup(tm, tc_smem, runs[0].A.mlp);
     CellIn<R> x;
     int run = 0;
-    long long ch = blockIdx.x;
-    if (ch < nch) {
+    {
         const long long b = locate(ch, run);
         cell_in_load(runs[run].g, runs[run].A, b + threadIdx.x, x);
     }
-    for (; ch < nch; ch += gridDim.x) {
+    while (ch < nch) {
         float f[MLP_NI], o[MLP_NO];
         const int cur = run;
         const float D = cell_in_features<MK, R>(runs[cur].A, x, f);
         const int id = x.id;
         const bool live = x.live;
-        const long long next = ch + gridDim.x;
+        const long long next = next_flagged(ch + gridDim.x, nch, gridDim.x, flagged, &s_first);
         if (next < nch) {
             const long long b = locate(next, run);
             cell_in_load(runs[run].g, runs[run].A, b + threadIdx.x, x);
         }
         const bool ok = tc_tile(tm, f, o);
         if (live) {
-            const float Wg = expf(o[0]), pD = expf(o[1]);
-            runs[cur].A.zg[id] = ok ? D * Wg * (1.0f + gr_f * pD * Wg) : 0.0f;
+            float z0 = -1.0f;
+            if (ok) {
+                const float Wg = expf(o[0]), pD = expf(o[1]);
+                z0 = net_beats(o[2], runs[cur].A.ze[id]) ? D * Wg * (1.0f + gr_f * pD * Wg) : 0.0f;
+            }
+            runs[cur].A.zg[id] = z0;
         }
+        ch = next;
     }
     tc_teardown(tm);
 }

@@ -149,6 +149,7 @@ struct DevScalars {
     double totals[8];            // mass, energy, mom x3, max divB, rate, spare
     unsigned long long c2p_hist[ECHO_C2P_HIST];   // inversions by Newton iterations (last: that many or more)
     unsigned long long fallback_faces;  // first-order face fallbacks on faces bounding owned cells (sides)
+    unsigned long long mlp_used;        // inversions started from the network's Newton start
 };
 
 // Metric at one point of the axisymmetric (x1, x2) plane, FP64: lapse,
@@ -183,7 +184,10 @@ struct Arrays {
     R *U[8];       // conserved: D, S_x, S_y, S_z, tau (cell), B~x, B~y, B~z (faces)
     R *U0[8];      // RK base state
     double *Z;     // Newton memory (cell)
-    float *zg;     // network Newton start per cell (0: none), written by k_mlp_guess_tc
+    float *zg;     // network Newton start per cell (> 0), or 0: the previous-stage Z chosen, < 0: the
+                   // tensor-core result missing (previous Z, counted); written by k_mlp_guess_tc
+    unsigned char *ze;     // per cell: code of the previous-Z error at the last inversion (ze_code)
+    unsigned char *tflag;  // per tile of 128 owned cells: 1 if a cell's code reached the network's gate
     R *P[8];       // primitives rho, v^x, v^y, v^z, p, B^x, B^y, B^z (cell)
     R *F[3][5];    // HLL fluxes on d-faces
     R *ap[3];      // HLL a+ on d-faces

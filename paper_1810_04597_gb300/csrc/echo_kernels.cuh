@@ -196,20 +196,34 @@ __device__ __forceinline__ float net_z0(const float o[MLP_NO], double Dc, float 
 }
 
 // MLPK: 0 no network; 1 network evaluated here (CUDA cores, parameter block
-// mlp_sm in shared memory); 2 network outputs net[0..1] (log W, log(p/D))
-// computed by the caller, usable if net_ok; 3 the network's Newton start
-// A.zg written by k_mlp_guess_tc (0: none).  Every network start is
+// mlp_sm in shared memory); 2 network outputs net[0..2] (log W, log(p/D),
+// predicted log10 error) computed by the caller, usable if net_ok; 3 the
+// Newton starts A.zg written by k_mlp_guess_tc.  Every network start is
 // Z0 = D W (1 + G/(G-1) (p/D) W) in FP32 (net_z0): it only starts the Newton
 // solve, and the FP64 pipe is the scarce one.
+//
+// Per-cell choice (network modes): the network is consulted only in tiles
+// of 128 cells that the last inversion flagged (A.tflag: a cell's previous-Z
+// error code reached the network's gate), and a cell takes the network start
+// only where the network's predicted error beats its previous Z's (net_beats
+// on the code A.ze); every other cell starts from the previous-stage Z.
+// tile_flag: the flag of t's tile for MLPK 2 (read here otherwise).
+//
+// Every inversion of the network modes writes the cell's new code A.ze and,
+// through a block-wide vote, the flag of its tile for the next inversion:
+// then all 128 threads of the block must call this with t in one 128-aligned
+// tile of owned cells.  The plain modes (MLPK 0) write neither; the host
+// resets the codes before a network-mode inversion that follows them.
 template <int MK, typename R, int MLPK>
 __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mode,
                                          int want_rate, long long t, const float *mlp_sm,
-                                         const float *net = nullptr, bool net_ok = false)
+                                         const float *net = nullptr, bool net_ok = false, bool tile_flag = false)
 {
     C2PCell c;
     const bool live = c2p_cell<MK, R>(g, A, t, c);
     double rate = 0.0;
-    unsigned long long its = 0, calls = 0, fails = 0, floors = 0, mfb = 0;
+    unsigned long long its = 0, calls = 0, fails = 0, floors = 0, mfb = 0, used = 0;
+    bool want_net = false;
     if (live) {
         const int id = c.id;
         const int i = c.i;
@@ -219,45 +233,65 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
         const double Dc = c.Dc, tc = c.tc;
         const int src = guess_mode & 3;
         const bool refine = (guess_mode & 4) != 0;
-        const double zg = src == 2 ? 0.0 : A.Z[id];
+        const double zold = (MLPK != 0 || src != 2) ? A.Z[id] : 0.0;
+        const double zg = src == 2 ? 0.0 : zold;
         constexpr double tol = sizeof(R) == 4 ? NEWTON_TOL_BULK32 : NEWTON_TOL;
         C2PResult r;
         if constexpr (MLPK != 0) {
-            bool have = true;
+            // pick: 1 the network start z0f, 0 the previous-stage Z, -1 the
+            // previous-stage Z because the network's result is missing (counted)
+            int pick = 0;
             float z0f = 0.0f;
-            if constexpr (MLPK == 3) {
-                z0f = A.zg[id];
-                have = z0f > 0.0f;
-            } else {
-                float o[MLP_NO];
-                if constexpr (MLPK == 1) {
-                    float f[MLP_NI];
-                    c2p_cell_features<MK>(c, f);
-                    mlp_infer(mlp_sm, f, o);
+            const bool flagged = MLPK == 2 ? tile_flag : A.tflag[t >> 7] != 0;
+            if (flagged) {
+                if constexpr (MLPK == 3) {
+                    z0f = A.zg[id];
+                    pick = z0f > 0.0f ? 1 : (z0f < 0.0f ? -1 : 0);
                 } else {
-                    o[0] = net[0];
-                    o[1] = net[1];
-                    have = net_ok;
+                    float o[MLP_NO];
+                    bool ok = true;
+                    if constexpr (MLPK == 1) {
+                        float f[MLP_NI];
+                        c2p_cell_features<MK>(c, f);
+                        mlp_infer(mlp_sm, f, o);
+                    } else {
+                        o[0] = net[0];
+                        o[1] = net[1];
+                        o[2] = net[2];
+                        ok = net_ok;
+                    }
+                    if (!ok) {
+                        pick = -1;
+                    } else if (net_beats(o[2], A.ze[id])) {
+                        pick = 1;
+                        z0f = net_z0(o, Dc, ph.gr_f);
+                    }
                 }
-                z0f = net_z0(o, Dc, ph.gr_f);
             }
-            int first = 0;
             r.ok = false;
-            if (have) {
+            int first = 0;
+            if (pick == 1) {
+                used = 1;
                 const double z0 = f2d(z0f);
                 if constexpr (MK == 1)
                     r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MKS<double>(*mp), 8, refine, tol);
                 else
                     r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MFlat<double>(), 8, refine, tol);
                 first = r.iters;
+                if (!r.ok)
+                    mfb = 1;
+            } else if (pick == -1) {
+                mfb = 1;
             }
             if (!r.ok) {
+                // previous-stage Z: the chosen start, or the restart after the
+                // network start failed (no FP32 refinement then)
+                const bool ref = pick == 1 ? false : refine;
                 if constexpr (MK == 1)
-                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp), NEWTON_MAXIT, false, tol);
+                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp), NEWTON_MAXIT, ref, tol);
                 else
-                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>(), NEWTON_MAXIT, false, tol);
+                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>(), NEWTON_MAXIT, ref, tol);
                 r.iters += first;
-                mfb = 1;
             }
         } else {
             if constexpr (MK == 1)
@@ -297,6 +331,13 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
         for (int q = 0; q < 8; ++q)
             A.P[q][id] = from_d<R>(P8[q]);
         A.Z[id] = Z;
+        if constexpr (MLPK != 0) {
+            // the previous-Z error code for the next inversion, and whether
+            // this cell may gain from the network there
+            const unsigned char code = ze_code(Z, zold);
+            A.ze[id] = code;
+            want_net = (int)code <= ze_gate(A.mlp[MLP_OGATE]);
+        }
         if (want_rate) {
             if constexpr (sizeof(R) == 4) {
                 float Pf[8];
@@ -317,6 +358,13 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             }
         }
     }
+    // the tile's flag for the next inversion (block vote; the tile lies in
+    // the owned cells when its first cell does)
+    if constexpr (MLPK != 0) {
+        const int any = __syncthreads_or(want_net ? 1 : 0);
+        if ((threadIdx.x & 127) == 0 && t < (long long)g.n[0] * g.n[1] * g.n[2])
+            A.tflag[t >> 7] = (unsigned char)any;
+    }
     // histogram of the iteration counts: one atomic per distinct count in the warp
     {
         const unsigned lmask = __ballot_sync(0xffffffffu, live);
@@ -333,6 +381,7 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
     fails = warp_sum_u64(fails);
     floors = warp_sum_u64(floors);
     mfb = warp_sum_u64(mfb);
+    used = warp_sum_u64(used);
     if (want_rate)
         rate = warp_max(rate);
     if ((threadIdx.x & 31) == 0) {
@@ -348,6 +397,8 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             atomicAdd(&A.scal->floor_hits, floors);
         if (mfb)
             atomicAdd(&A.scal->mlp_fallback, mfb);
+        if (used)
+            atomicAdd(&A.scal->mlp_used, used);
         if (want_rate && rate > 0.0)
             atomicMax(&A.scal->rate_bits, (unsigned long long)__double_as_longlong(rate));
     }
@@ -440,47 +491,61 @@ __device__ __forceinline__ float cell_in_features(const Arrays<R> &A, const Cell
     return D;
 }
 
-// The network's Newton start of every owned cell, both hidden layers on the
-// tensor cores (echo_mlp_tc.cuh), for the c2p kernel that follows (NET 3):
-// persistent CTAs of 128 threads walk tiles of 128 cells.  A tile whose
-// tensor-core result did not arrive writes 0: its cells start from the
-// previous-stage Z (counted in mlp_fallback).  Keeping the network out of
-// the c2p kernel leaves that FP64-bound kernel at full occupancy and free of
-// the per-tile barriers of the MMA round trips.
+// The network's Newton starts for the c2p kernel that follows (NET 3), both
+// hidden layers on the tensor cores (echo_mlp_tc.cuh): persistent CTAs of
+// 128 threads walk the tiles of 128 cells that the last inversion flagged
+// (A.tflag) and skip the others, whose cells keep the previous-stage Z.  In
+// a flagged tile a cell gets the start Z0 > 0 only where the network's
+// predicted error beats its previous Z's (net_beats), else 0; a tile whose
+// tensor-core result did not arrive writes -1 (previous-stage Z, counted in
+// mlp_fallback).  The next flagged tile's inputs load during the current
+// tile's MMA round trips.  Keeping the network out of the c2p kernel leaves
+// that FP64-bound kernel at full occupancy and free of the per-tile
+// barriers of the MMA round trips.
 template <int MK, typename R>
 __global__ void __launch_bounds__(128, 6) k_mlp_guess_tc(Geom g, Arrays<R> A, float gr_f, long long ntiles)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ int s_first;
+    const unsigned char *__restrict__ flag = A.tflag;
+    auto flagged = [&](long long tl) { return flag[tl] != 0; };
+    long long tile = next_flagged(blockIdx.x, ntiles, gridDim.x, flagged, &s_first);
+    if (tile >= ntiles)
+        return;   // block-uniform: no flagged tile for this CTA (nothing allocated yet)
     TcMlp tm;
     tc_setup(tm, tc_smem, A.mlp);
     CellIn<R> x;
-    long long tile = blockIdx.x;
-    if (tile < ntiles)
-        cell_in_load(g, A, tile * 128 + threadIdx.x, x);
-    for (; tile < ntiles; tile += gridDim.x) {
+    cell_in_load(g, A, tile * 128 + threadIdx.x, x);
+    while (tile < ntiles) {
         float f[MLP_NI], o[MLP_NO];
         const float D = cell_in_features<MK, R>(A, x, f);   // a lane past the end: its clamped cell's values
         const int id = x.id;
         const bool live = x.live;
-        const long long next = tile + gridDim.x;
+        const long long next = next_flagged(tile + gridDim.x, ntiles, gridDim.x, flagged, &s_first);
         if (next < ntiles)
             cell_in_load(g, A, next * 128 + threadIdx.x, x);
         const bool ok = tc_tile(tm, f, o);
         if (live) {
-            const float Wg = expf(o[0]), pD = expf(o[1]);
-            A.zg[id] = ok ? D * Wg * (1.0f + gr_f * pD * Wg) : 0.0f;
+            float z0 = -1.0f;
+            if (ok) {
+                const float Wg = expf(o[0]), pD = expf(o[1]);
+                z0 = net_beats(o[2], A.ze[id]) ? D * Wg * (1.0f + gr_f * pD * Wg) : 0.0f;
+            }
+            A.zg[id] = z0;
         }
+        tile = next;
     }
     tc_teardown(tm);
 }
 
 // c2p with the network evaluated inside it (guess mode +16), both hidden
 // layers on the tensor cores (echo_mlp_tc.cuh): persistent CTAs of 128
-// threads walk tiles of 128 cells;
-// per tile every thread computes its cell's features, the CTA runs the
-// network (one tcgen05 MMA group), then every thread inverts its cell.  A
-// tile whose tensor-core result did not arrive falls back to the previous-
-// stage guess (counted in mlp_fallback).
+// threads walk tiles of 128 cells; in a tile the last inversion flagged
+// every thread computes its cell's features, the CTA runs the network (one
+// tcgen05 MMA group), then every thread inverts its cell, from the network
+// start where its predicted error beats the previous Z's.  Unflagged tiles
+// skip the network.  A tile whose tensor-core result did not arrive falls
+// back to the previous-stage guess (counted in mlp_fallback).
 template <int MK, typename R>
 __global__ void __launch_bounds__(128, 6) k_c2p_tc(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate,
                                                 long long ntiles)
@@ -490,15 +555,19 @@ __global__ void __launch_bounds__(128, 6) k_c2p_tc(Geom g, Phys ph, Arrays<R> A,
     tc_setup(tm, tc_smem, A.mlp);
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long t = tile * 128 + threadIdx.x;
+        const bool flagged = A.tflag[tile] != 0;   // block-uniform
         C2PCell c;
-        float f[MLP_NI], o[MLP_NO];
-        if (c2p_cell<MK, R>(g, A, t, c))
-            c2p_cell_features<MK>(c, f);
-        else
-            for (int q = 0; q < MLP_NI; ++q)
-                f[q] = tm.P[TP_NORM + q];
-        const bool ok = tc_tile(tm, f, o);
-        c2p_body<MK, R, 2>(g, ph, A, guess_mode, want_rate, t, nullptr, o, ok);
+        float f[MLP_NI], o[MLP_NO] = {0.0f, 0.0f, 0.0f};
+        bool ok = false;
+        if (flagged) {
+            if (c2p_cell<MK, R>(g, A, t, c))
+                c2p_cell_features<MK>(c, f);
+            else
+                for (int q = 0; q < MLP_NI; ++q)
+                    f[q] = tm.P[TP_NORM + q];
+            ok = tc_tile(tm, f, o);
+        }
+        c2p_body<MK, R, 2>(g, ph, A, guess_mode, want_rate, t, nullptr, o, ok, flagged);
     }
     tc_teardown(tm);
 }

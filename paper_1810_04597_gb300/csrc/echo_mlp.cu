@@ -15,6 +15,10 @@
 
 namespace echo {
 
+static_assert(MLP_BLOCK == ECHO_MLP_BLOCK && MLP_STATE == ECHO_MLP_STATE && MLP_NPAR == ECHO_MLP_NPARAM,
+              "network block layout of echo.h");
+static_assert(MLP_OGATE == ECHO_MLP_GATE, "gate slot of echo.h");
+
 constexpr int WS = 272;   // per-sample work floats
 constexpr int W_XS = 0, W_H1 = 9, W_H2 = 73, W_D1 = 137, W_D2 = 201, W_D3 = 265, W_LOSS = 268;
 constexpr float LOSS_W2 = 0.1f;
@@ -356,6 +360,25 @@ __global__ void k_mlp_guess_error(const float *__restrict__ P, const float *__re
     err[r] = (float)(fabs(z0 - z) / z);
 }
 
+// Mean of log10 of the rows' errors (clamped below at 1e-30) in FP64, one
+// block in a fixed order, into the block's gate slot.
+__global__ void __launch_bounds__(1024) k_mlp_gate(const float *__restrict__ err, long long n, float *S)
+{
+    __shared__ double sh[1024];
+    double acc = 0.0;
+    for (long long r = threadIdx.x; r < n; r += blockDim.x)
+        acc += log10(fmax((double)err[r], 1e-30));
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        S[MLP_OGATE] = (float)(sh[0] / (double)n);
+}
+
 }  // namespace echo
 
 using namespace echo;
@@ -461,6 +484,18 @@ int echo_mlp_guess_error(const float *state, const float *x, const float *y, lon
         return rc;
     k_mlp_guess_error<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         state, out, y, n, gamma / (gamma - 1.0), err);
+    return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
+}
+
+int echo_mlp_calibrate(float *state, const float *x, const float *y, long long n, double gamma, float *out, float *err,
+                       void *stream)
+{
+    if (n < 1)
+        return ECHO_EINVAL;
+    const int rc = echo_mlp_guess_error(state, x, y, n, gamma, 1, out, err, stream);
+    if (rc != ECHO_OK)
+        return rc;
+    k_mlp_gate<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>(err, n, state);
     return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
 }
 

@@ -23,7 +23,10 @@ constexpr int MLP_OB3 = MLP_OW3 + MLP_NO * MLP_NH;
 constexpr int MLP_NPAR = MLP_OB3 + MLP_NO;   // 4995
 constexpr int MLP_ONORM = MLP_NPAR;
 constexpr int MLP_NNORM = 2 * MLP_NI + 2 * MLP_NO;   // 24
-constexpr int MLP_BLOCK = 5024;                      // params + norm, padded to 32
+// log10 of the network's typical guess error (its gate), written by
+// echo_mlp_calibrate; 0 (an error of 1) until calibrated
+constexpr int MLP_OGATE = MLP_ONORM + MLP_NNORM;     // 5019
+constexpr int MLP_BLOCK = 5024;                      // params + norm + gate, padded to 32
 // training state: [params+norm (MLP_BLOCK) | Adam m (MLP_BLOCK) | Adam v (MLP_BLOCK)]
 constexpr int MLP_STATE = 3 * MLP_BLOCK;
 
@@ -127,6 +130,68 @@ __device__ __forceinline__ void mlp_infer(const float *__restrict__ P, const flo
 #pragma unroll
     for (int q = 0; q < MLP_NO; ++q)
         out[q] = o[q] * P[MLP_ONORM + 2 * MLP_NI + MLP_NO + q] + P[MLP_ONORM + 2 * MLP_NI + q];
+}
+
+// ---- per-cell choice of the Newton start
+//
+// The previous-stage Z of a cell is a good start when the state moved
+// little since the last inversion.  Every inversion records, per cell, the
+// code q of that movement: q = e(Z) - e(|Z - Z_prev|) from the binary
+// exponents e of the new Z and of its change, i.e. -log2 of the relative
+// change within one (0: a change of order one, 254: a change below 2^-254,
+// 255: no change; a cold start, Z_prev = 0, gives 0).  It estimates the
+// error of the previous Z as the next start.  The network's third output is
+// its own predicted log10 relative error o2; a cell takes the network start
+// iff -o2 log2(10) > q + 1/2, i.e. the network predicts a smaller error.
+constexpr unsigned char ZE_EXACT = 255;
+
+__device__ __forceinline__ unsigned char ze_code(double Z, double zprev)
+{
+    const long long bd = __double_as_longlong(Z - zprev) & 0x7fffffffffffffffLL;
+    if (bd == 0)
+        return ZE_EXACT;
+    const int ez = (int)((__double_as_longlong(Z) >> 52) & 0x7ff);
+    const int ed = (int)(bd >> 52);
+    const int q = ez - ed;
+    return (unsigned char)(q < 0 ? 0 : (q > 254 ? 254 : q));
+}
+
+// A cell whose previous Z is at least as far off as the network's typical
+// error (gate, log10) may gain from the network: q <= floor(-gate log2 10).
+__device__ __forceinline__ int ze_gate(float gate_log10)
+{
+    const float g = -gate_log10 * 3.32192809f;
+    return g <= 0.0f ? 0 : (g >= 254.0f ? 254 : (int)g);
+}
+
+__device__ __forceinline__ bool net_beats(float o2, unsigned char q)
+{
+    return q != ZE_EXACT && -o2 * 3.32192809f > (float)q + 0.5f;
+}
+
+// The first index t + k stride (k = 0, 1, ...) below n whose flagged(index)
+// holds, or n: the 128 threads of the block test 128 candidates at once.
+// Every thread of the block calls it (block-uniform result).
+template <typename F>
+__device__ __forceinline__ long long next_flagged(long long t, long long n, long long stride, F flagged, int *s_first)
+{
+    for (;;) {
+        if (t >= n)
+            return n;
+        const long long mine = t + (long long)threadIdx.x * stride;
+        const bool f = mine < n && flagged(mine);
+        if (threadIdx.x == 0)
+            *s_first = 1 << 30;
+        __syncthreads();
+        if (f)
+            atomicMin(s_first, (int)threadIdx.x);
+        __syncthreads();
+        const int k = *s_first;
+        __syncthreads();
+        if (k != 1 << 30)
+            return t + (long long)k * stride;
+        t += (long long)blockDim.x * stride;
+    }
 }
 
 }  // namespace echo

@@ -56,9 +56,22 @@ def collect(problems_and_steps, device="cuda:0"):
         (cat([x for x, _ in test_s]), cat([y for _, y in test_s]))
 
 
+def calibrate(state, X, Y, gamma=4.0 / 3.0):
+    """Set the network's gate (the mean log10 error of its Newton starts on
+    rows (X, Y), ``echo_mlp_calibrate``): cells whose previous-stage Z moved
+    less than that do not consult the network."""
+    import torch
+    n = X.shape[0]
+    out = torch.empty((n, 3), dtype=torch.float32, device=X.device)
+    err = torch.empty(n, dtype=torch.float32, device=X.device)
+    _lib.echo_mlp_calibrate(state, X, Y, n, gamma, out, err, torch.cuda.current_stream(X.device).cuda_stream)
+    return float(state[_lib.ECHO_MLP_GATE].item())
+
+
 def train(X, Y, epochs=2, batch=8192, lr=1e-3, seed=1, gamma=4.0 / 3.0, device="cuda:0"):
     """Train a fresh network on (X, Y); returns (state tensor, per-step
-    losses tensor)."""
+    losses tensor).  The gate is left at 0 (only cold starts consult the
+    network) until ``calibrate``."""
     import torch
     n = X.shape[0]
     state = torch.empty(_lib.ECHO_MLP_STATE, dtype=torch.float32, device=device)
@@ -110,8 +123,9 @@ def torus_runs(n=(96, 48, 48)):
 def default_network(device="cuda:0", n=128, epochs=2, seed=1, torus=False):
     """The network used by the benchmarks: trained on snapshots of the n^3
     box runs (box_runs), and with torus=True also of the torus runs
-    (torus_runs)."""
+    (torus_runs); its gate calibrated on the validation snapshots."""
     runs = box_runs(n) + (torus_runs() if torus else [])
     (Xtr, Ytr), (Xva, Yva), (Xte, Yte) = collect(runs, device=device)
     state, losses = train(Xtr, Ytr, epochs=epochs, seed=seed, device=device)
+    calibrate(state, Xva, Yva)
     return state, losses, (Xva, Yva), (Xte, Yte)

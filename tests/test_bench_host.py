@@ -68,3 +68,20 @@ def test_clock_samples_parsed():
 def test_clock_sampler_without_nvidia_smi():
     out = bench.ClockSampler().stop()
     assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_algorithmic_flops_from_the_oracle_counts(tmp_path):
+    """The roofline numerator: per unit, the counts the oracle's counting
+    build wrote; c2p's per-cell part plus its per-iteration part times the
+    iterations the inversion took."""
+    counts = {"flops_per_unit": {"faces": 480.0, "emf": 250.0}, "update_per_cell": 87.0,
+              "c2p_per_cell_fixed": 49.0, "c2p_per_newton_iteration": 55.0}
+    assert bench.algorithmic_flops(counts, "faces_y", 3.0) == 480.0
+    assert bench.algorithmic_flops(counts, "emf_z", 3.0) == 250.0
+    assert bench.algorithmic_flops(counts, "update", 3.0) == 87.0
+    assert bench.algorithmic_flops(counts, "c2p", 3.0) == 49.0 + 3 * 55.0
+    # the committed file has every figure the numerator needs
+    got = bench.load_op_counts()
+    for key in ("faces", "emf", "c2p", "assemble", "ct", "rk"):
+        assert got["flops_per_unit"][key] > 0.0, key
+    assert got["c2p_per_newton_iteration"] > 0.0 and got["update_per_cell"] > 0.0

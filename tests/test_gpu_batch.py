@@ -101,7 +101,8 @@ def test_batch_flat_fixed_dt_and_counters():
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_with_network_guess(mode):
-    """FP32 tori with the network Newton start (guess 5) under each schedule.
+    """FP32 tori from cold restarts with the network Newton start (guess 5)
+    under each schedule.
     Run-major runs the single-run kernels: bitwise.  The persistent and
     per-phase schedules take the starts from their own tensor-core pass over
     all runs (the persistent one before the stage's ghost fill, so a cell at
@@ -116,6 +117,7 @@ def test_batch_with_network_guess(mode):
     single = _tori(32)
     runs = _tori(32)
     for s in single + runs:
+        s.set_state(s.get_state())    # cold restarts: every tile consults the network first
         s.mlp_load(state)
         s.set_c2p_guess(5)
     for s in single:

@@ -122,8 +122,9 @@ def test_order1_batch_needs_run_major():
 
 def test_order1_with_network_guess_matches():
     """The network's Newton start (its features take the two-face mean of B
-    also under order 1) only moves the start: three order-1 steps with it
-    equal the steps from the previous-stage Z to rounding."""
+    also under order 1) only moves the start: three order-1 steps from a
+    cold restart with it equal the steps from the previous-stage Z (the cold
+    start first) to rounding."""
     import torch
     from paper_1810_04597_gb300.echo import Solver
     from test_gpu_mlp import random_state
@@ -132,6 +133,7 @@ def test_order1_with_network_guess_matches():
     for mode in (0, 1):
         s = Solver(_order1(inputs.smooth_box(20, seed=13)))
         s.set_prims()
+        s.set_state(s.get_state())     # a cold restart: every tile consults the network first
         s.mlp_load(state)
         s.set_c2p_guess(mode)
         for _ in range(3):
