@@ -425,11 +425,10 @@ def run_ours(args, world, rank, local, dist):
     totals = s.reduce()
     fin64 = s.get_state() if (args.precision == 64 and not args.no_variants) else None
 
-    # kernels launched in the timed region (a fill call launches 3 kernels; a
-    # c2p with the network guess in its own pass 2)
-    per_call = {"fill_faces": 3, "fill_prims": 3}
-    if (guess & 3) == 1 and not (guess & 24):
-        per_call["c2p"] = 2
+    # kernels launched in the timed region (a fill call launches 3 kernels,
+    # the order-1 correction and its safeguard 6 each; the network's own pass
+    # is a class of its own)
+    per_call = {"fill_faces": 3, "fill_prims": 3, "correct": 6}
     launches = int(sum(cnt * per_call.get(k, 1) for k, (_, cnt) in prof.items()))
 
     # ---- roofline of the dominant kernel (live CUDA-event times)
@@ -781,7 +780,9 @@ def run_guess_gain(prob, dev, mlp_state, warm=2, steps=3):
             h = np.array(c1["c2p_iter_hist"]) - np.array(c0["c2p_iter_hist"])
             cum = np.cumsum(h) / max(int(h.sum()), 1)
             ms, nl = prof["c2p"]
+            ms += prof["network"][0]   # the network's own pass, per c2p call
             res[name] = {"c2p_ms_per_call": ms / max(nl, 1),
+                         "network_pass_ms_per_call": prof["network"][0] / max(nl, 1),
                          "mean_newton_iters": (c1["c2p_iters"] - c0["c2p_iters"]) / calls,
                          "p99_newton_iters": int(np.searchsorted(cum, 0.99)),
                          "mlp_fallback_per_call": (c1["mlp_fallback"] - c0["mlp_fallback"]) / calls,
@@ -804,7 +805,9 @@ def run_guess_gain(prob, dev, mlp_state, warm=2, steps=3):
             c1 = s.counters()
             calls = max(c1["c2p_calls"] - c0["c2p_calls"], 1)
             ms, nl = prof["c2p"]
+            ms += prof["network"][0]
             res[name] = {"c2p_ms_per_call": ms / max(nl, 1),
+                         "network_pass_ms_per_call": prof["network"][0] / max(nl, 1),
                          "mean_newton_iters": (c1["c2p_iters"] - c0["c2p_iters"]) / calls,
                          "mlp_fallback_per_call": (c1["mlp_fallback"] - c0["mlp_fallback"]) / calls,
                          "network_starts_per_call": (c1["mlp_used"] - c0["mlp_used"]) / calls}
@@ -830,7 +833,9 @@ def run_guess_gain(prob, dev, mlp_state, warm=2, steps=3):
         c1 = s.counters()
         calls = max(c1["c2p_calls"] - c0["c2p_calls"], 1)
         ms, nl = prof["c2p"]
+        ms += prof["network"][0]
         res[name] = {"c2p_ms_per_call": ms / max(nl, 1),
+                     "network_pass_ms_per_call": prof["network"][0] / max(nl, 1),
                      "mean_newton_iters": (c1["c2p_iters"] - c0["c2p_iters"]) / calls,
                      "mlp_fallback_per_call": (c1["mlp_fallback"] - c0["mlp_fallback"]) / calls,
                      "network_starts_per_call": (c1["mlp_used"] - c0["mlp_used"]) / calls,

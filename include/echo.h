@@ -110,6 +110,7 @@ typedef struct {
      * that many or more; the entries sum to c2p_calls */
     long long c2p_iter_hist[ECHO_C2P_HIST];
     long long mlp_used;   /* inversions since bind started from the network's Newton start */
+    long long guard_faces; /* order 1: faces the safeguard returned to the uncorrected flux since bind */
 } echo_totals;
 
 /* Method: the grid and equations of the paper's solver (introduction: a 3-D
@@ -141,6 +142,14 @@ int echo_init(const echo_grid *grid, const echo_metric *metric, const echo_eos *
  * differences are sixth-order derivatives (the scheme's "high-order"
  * finite differences).  With order 1 the divergence that stays constant is
  * the one built from corrected face differences (echo_reduce reports it).
+ * Order 1 also runs a safeguard in every stage of echo_step: a cell whose
+ * stage result (formed from L(U) with the corrected fluxes as the stage
+ * forms it, with the current cell-centre field) the FP64 Newton inversion
+ * cannot invert is flagged, every face of a flagged cell takes the
+ * uncorrected flux (the same for both cells sharing it), and the check
+ * repeats on the cells not yet flagged, three passes at most; the faces it
+ * changed are counted (echo_totals.guard_faces).  echo_rhs has no step and
+ * no safeguard.
  * ECHO_EINVAL for another value, ECHO_ESTATE after echo_bind. */
 int echo_set_order(echo_ctx *ctx, int order);
 
@@ -306,7 +315,7 @@ int echo_mlp_calibrate(float *dev_state, const float *X, const float *Y, long lo
                        float *err, void *cuda_stream);
 
 /* Copy a trained network (the first ECHO_MLP_BLOCK floats of a state) into
- * the context. */
+ * the context; the Newton starts of an earlier network are discarded. */
 int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
 
 /* Method: the initial guess of the Newton iteration (the iteration, not the
@@ -318,13 +327,15 @@ int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
  * iterations that follow still decide convergence).  In the network modes
  * the start is chosen per cell: every inversion records how far each cell's
  * Z moved (an estimate of the error of the previous-stage Z as the next
- * start) and flags the tiles of 128 cells where some cell moved at least as
- * much as the network's calibrated typical error (echo_mlp_calibrate); the
- * network is evaluated in flagged tiles only, and a cell there starts from
- * it only where its predicted log10 error (third output) beats the previous
- * Z's; all other cells start from the previous-stage Z (not counted as a
- * fallback).  After echo_set_prims, or echo_set_state with Z, no tile is
- * flagged; after echo_set_state without Z (a cold start) every tile is.
+ * start) and lists the cells that moved at least as much as the network's
+ * calibrated typical error (echo_mlp_calibrate); the next inversion
+ * evaluates the network for the listed cells only (packed into tiles of
+ * 128), and a listed cell starts from it only where its predicted log10
+ * error (third output) beats the previous Z's; all other cells start from
+ * the previous-stage Z (not counted as a fallback).  After echo_set_prims,
+ * or echo_set_state with Z, no cell is listed; after echo_set_state without
+ * Z (a cold start) every cell is.  Inversions in the other modes keep no
+ * record: the first network-mode inversion after them lists no cell.
  * The network's hidden layers run on the tensor cores (as
  * echo_mlp_forward_tc) in a pass before the c2p kernel; adding 8 to a network mode evaluates it in FP32 on the
  * CUDA cores inside the c2p kernel (modes 9, 13), adding 16 on the tensor
@@ -333,7 +344,7 @@ int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
 int echo_set_c2p_guess(echo_ctx *ctx, int mode);
 
 /* Copy the cumulative counters (c2p_iters, c2p_calls, c2p_fail, floor_hits,
- * mlp_fallback, fallback_faces, c2p_iter_hist) to *out without running anything; other
+ * mlp_fallback, fallback_faces, mlp_used, guard_faces, c2p_iter_hist) to *out without running anything; other
  * fields untouched.  Synchronises. */
 int echo_counters(echo_ctx *ctx, echo_totals *out);
 
@@ -422,8 +433,8 @@ int echo_selftest_scale2(long long n, unsigned long long seed, unsigned long lon
 int echo_selftest_dfma_blocks(void);
 int echo_selftest_dfma(long long iters, double *dev_out, double *flops, void *cuda_stream);
 
-/* Kernel classes timed by the profiling facility below (ECHO_K_C2P includes
- * the network's own pass when the guess mode runs one). */
+/* Kernel classes timed by the profiling facility below (ECHO_K_NETWORK: the
+ * network's own pass before c2p in guess modes 1 and 5). */
 #define ECHO_K_FILL_FACES 0
 #define ECHO_K_C2P 1
 #define ECHO_K_FILL_PRIMS 2
@@ -437,7 +448,8 @@ int echo_selftest_dfma(long long iters, double *dev_out, double *flops, void *cu
 #define ECHO_K_SCALARS 10
 #define ECHO_K_TOTALS 11
 #define ECHO_K_CORRECT 12
-#define ECHO_NK 13
+#define ECHO_K_NETWORK 13
+#define ECHO_NK 14
 
 /* Enable (1) or disable (0) per-kernel timing: while enabled, every kernel
  * launch of echo_step/echo_rhs/echo_c2p/echo_reduce is bracketed by two

@@ -63,14 +63,16 @@ class echo_totals(ctypes.Structure):
                 ("c2p_iters", ctypes.c_longlong), ("c2p_calls", ctypes.c_longlong),
                 ("c2p_fail", ctypes.c_longlong), ("floor_hits", ctypes.c_longlong),
                 ("fallback_faces", ctypes.c_longlong), ("mlp_fallback", ctypes.c_longlong),
-                ("c2p_iter_hist", ctypes.c_longlong * ECHO_C2P_HIST), ("mlp_used", ctypes.c_longlong)]
+                ("c2p_iter_hist", ctypes.c_longlong * ECHO_C2P_HIST), ("mlp_used", ctypes.c_longlong),
+                ("guard_faces", ctypes.c_longlong)]
 
     def as_dict(self):
         return dict(dt_cfl=self.dt_cfl, mass=self.mass, energy=self.energy, mom=list(self.mom),
                     max_divb=self.max_divb, c2p_iters=self.c2p_iters, c2p_calls=self.c2p_calls,
                     c2p_fail=self.c2p_fail, floor_hits=self.floor_hits,
                     fallback_faces=self.fallback_faces, mlp_fallback=self.mlp_fallback,
-                    c2p_iter_hist=list(self.c2p_iter_hist), mlp_used=self.mlp_used)
+                    c2p_iter_hist=list(self.c2p_iter_hist), mlp_used=self.mlp_used,
+                    guard_faces=self.guard_faces)
 
 
 # Exported entry points and their C signatures.
@@ -273,7 +275,7 @@ def echo_reduce(ctx) -> echo_totals:
     return t
 
 
-ECHO_NK = 13
+ECHO_NK = 14
 
 
 def echo_profile(ctx, enable: bool):

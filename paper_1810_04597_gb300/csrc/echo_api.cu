@@ -78,7 +78,8 @@ size_t layout(echo_ctx *c, char *base, Arrays<R> *A)
     A->Z = reinterpret_cast<double *>(take(cells * sizeof(double)));
     A->zg = reinterpret_cast<float *>(take(cells * sizeof(float)));
     A->ze = reinterpret_cast<unsigned char *>(take(cells));
-    A->tflag = reinterpret_cast<unsigned char *>(take((size_t)c->ntiles));
+    A->nlist = reinterpret_cast<int *>(take((size_t)(c->ntiles * 128) * sizeof(int)));
+    A->gmark = c->geo.order ? reinterpret_cast<unsigned char *>(take(cells)) : nullptr;
     A->mlp = reinterpret_cast<const float *>(take(MLP_BLOCK * sizeof(float)));
     A->met = MetTables{};
     A->met.np0 = c->geo.np[0];
@@ -171,18 +172,27 @@ Arrays<float> &arrays<float>(echo_ctx *c) { return c->af; }
 
 // ---- operations, templated on the storage type
 
-// The previous-Z error codes and tile flags of the network modes' per-cell
-// choice: after a new state an exact Newton memory (from p2c, or a Z the
-// caller passed) needs no network start; a cold one (no Z) flags every tile.
+// The previous-Z error codes and the network-start list of the network
+// modes' per-cell choice: after a new state an exact Newton memory (from p2c,
+// or a Z the caller passed) needs no network start (codes "no change", list
+// empty); a cold one (no Z) lists every cell with the code of an error of
+// order one.
 int reset_start_memory(echo_ctx *c, bool exact, cudaStream_t s)
 {
     unsigned char *ze = c->precision == 64 ? c->ad.ze : c->af.ze;
-    unsigned char *tf = c->precision == 64 ? c->ad.tflag : c->af.tflag;
-    if (cudaMemsetAsync(ze, exact ? ZE_EXACT : 0, (size_t)c->geo.cells_padded, s) != cudaSuccess
-        || cudaMemsetAsync(tf, exact ? 0 : 1, (size_t)c->ntiles, s) != cudaSuccess)
+    if (cudaMemsetAsync(ze, exact ? ZE_EXACT : 0, (size_t)c->geo.cells_padded, s) != cudaSuccess)
         return cuda_check(c, "start memory");
+    if (exact) {
+        DevScalars *ds = c->precision == 64 ? c->ad.scal : c->af.scal;
+        if (cudaMemsetAsync(&ds->nlist_count, 0, sizeof(ds->nlist_count), s) != cudaSuccess)
+            return cuda_check(c, "start memory");
+    } else if (c->precision == 64) {
+        launch_list_all<double>(c->geo, c->ad, s);
+    } else {
+        launch_list_all<float>(c->geo, c->af, s);
+    }
     c->ze_valid = true;
-    return ECHO_OK;
+    return cuda_check(c, "start memory");
 }
 
 // Only the network modes' inversions keep the codes up to date: before one
@@ -204,6 +214,7 @@ void enqueue_rhs_pass(echo_ctx *c, int stage, double *Lout, bool want_rate, doub
     Arrays<R> &A = arrays<R>(c);
     cudaStream_t s = c->stream;
     PROF(ECHO_K_FILL_FACES, launch_fill<R>(c->geo, face_list(A), s));
+    PROF(ECHO_K_NETWORK, (launch_net_pass<MK, R>(c->geo, c->ph, A, c->c2p_guess, s)));
     PROF(ECHO_K_C2P, (launch_c2p<MK, R>(c->geo, c->ph, A, c->c2p_guess, want_rate ? 1 : 0, s)));
     if (want_rate)
         PROF(ECHO_K_SCALARS, launch_set_dt(A.scal, c->cfl, dt_fixed <= 0.0 ? 1 : 0, s));
@@ -212,8 +223,11 @@ void enqueue_rhs_pass(echo_ctx *c, int stage, double *Lout, bool want_rate, doub
         PROF(ECHO_K_FACES_X + d, (launch_faces<MK, R>(c->geo, c->ph, A, d, s)));
     for (int e = 0; e < 3; ++e)
         PROF(ECHO_K_EMF_X + e, (launch_emf<MK, R>(c->geo, A, e, s)));
-    if (c->geo.order)
+    if (c->geo.order) {
         PROF(ECHO_K_CORRECT, launch_correct<R>(c->geo, A, s));
+        if (stage >= 0)
+            PROF(ECHO_K_CORRECT, (launch_guard<MK, R>(c->geo, c->ph, A, stage, s)));
+    }
     PROF(ECHO_K_UPDATE, (launch_update<MK, R>(c->geo, c->ph, A, stage, Lout, s)));
 }
 
@@ -248,6 +262,7 @@ int op_c2p(echo_ctx *c, int guess_mode)
         return rc;
     PROF(ECHO_K_SCALARS, launch_step_begin(A.scal, 0.0, c->stream));
     PROF(ECHO_K_FILL_FACES, launch_fill<R>(c->geo, face_list(A), c->stream));
+    PROF(ECHO_K_NETWORK, (launch_net_pass<MK, R>(c->geo, c->ph, A, guess_mode, c->stream)));
     PROF(ECHO_K_C2P, (launch_c2p<MK, R>(c->geo, c->ph, A, guess_mode, 1, c->stream)));
     PROF(ECHO_K_SCALARS, launch_set_dt(A.scal, c->cfl, 1, c->stream));
     return cuda_check(c, "echo_c2p");
@@ -731,6 +746,7 @@ int echo_reduce(echo_ctx *c, echo_totals *out)
     out->fallback_faces = (long long)hs.fallback_faces;
     out->mlp_fallback = (long long)hs.mlp_fallback;
     out->mlp_used = (long long)hs.mlp_used;
+    out->guard_faces = (long long)hs.guard_faces;
     for (int k = 0; k < ECHO_C2P_HIST; ++k)
         out->c2p_iter_hist[k] = (long long)hs.c2p_hist[k];
     if (hs.fail_since_check) {
@@ -759,6 +775,7 @@ int echo_counters(echo_ctx *c, echo_totals *out)
     out->floor_hits = (long long)hs.floor_hits;
     out->mlp_fallback = (long long)hs.mlp_fallback;
     out->mlp_used = (long long)hs.mlp_used;
+    out->guard_faces = (long long)hs.guard_faces;
     out->fallback_faces = (long long)hs.fallback_faces;
     for (int k = 0; k < ECHO_C2P_HIST; ++k)
         out->c2p_iter_hist[k] = (long long)hs.c2p_hist[k];
@@ -775,6 +792,12 @@ int echo_mlp_load(echo_ctx *c, const float *dev_state)
     float *dst = const_cast<float *>(c->precision == 64 ? c->ad.mlp : c->af.mlp);
     if (cudaMemcpyAsync(dst, dev_state, MLP_BLOCK * sizeof(float), cudaMemcpyDeviceToDevice, c->stream)
         != cudaSuccess)
+        return cuda_check(c, "echo_mlp_load");
+    // no Newton start of an earlier network survives: a cell the next
+    // inversion consults under this network's gate, but that the list (made
+    // under the old gate) did not hold, starts from its previous Z
+    float *zg = c->precision == 64 ? c->ad.zg : c->af.zg;
+    if (cudaMemsetAsync(zg, 0, (size_t)c->geo.cells_padded * sizeof(float), c->stream) != cudaSuccess)
         return cuda_check(c, "echo_mlp_load");
     c->mlp_loaded = true;
     return cuda_check(c, "echo_mlp_load");
@@ -853,7 +876,8 @@ int echo_profile_read(echo_ctx *c, double *ms, long long *launches, int nk)
 const char *echo_kernel_name(int k)
 {
     static const char *names[ECHO_NK] = {"fill_faces", "c2p", "fill_prims", "faces_x", "faces_y", "faces_z",
-                                         "emf_x", "emf_y", "emf_z", "update", "scalars", "totals", "correct"};
+                                         "emf_x", "emf_y", "emf_z", "update", "scalars", "totals", "correct",
+                                         "network"};
     return (k >= 0 && k < ECHO_NK) ? names[k] : "";
 }
 

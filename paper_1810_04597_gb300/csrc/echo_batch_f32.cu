@@ -19,13 +19,12 @@ const void *batch_stage_kernel<float>(int mk, bool mlp)
 template <int MK>
 static void guess_pass(const RunDesc<float> *descs, const BatchPlan *planp, const BatchPlan &P, float gr_f, cudaStream_t s)
 {
+    // the grid is sized for the whole GPU: the lists' lengths are on the device
     static int resident = 0;
     if (resident == 0)
         resident = tc_resident_ctas((const void *)k_bphase_guess_tc<MK, float>, TC_SMEM);
-    const long long nch = P.ntiles[PH_C2P] * (P.tile / 128);
-    const long long grid = nch < resident ? nch : resident;
-    if (grid > 0)
-        k_bphase_guess_tc<MK, float><<<(unsigned)grid, 128, TC_SMEM, s>>>(descs, planp, gr_f);
+    k_bphase_guess_tc<MK, float><<<(unsigned)resident, 128, TC_SMEM, s>>>(descs, planp, gr_f);
+    k_bphase_clear_lists<float><<<1, 32, 0, s>>>(descs, P.nruns);
 }
 
 template <>

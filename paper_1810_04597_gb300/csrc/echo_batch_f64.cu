@@ -14,13 +14,12 @@ const void *batch_stage_kernel<double>(int mk, bool mlp)
 template <int MK>
 static void guess_pass(const RunDesc<double> *descs, const BatchPlan *planp, const BatchPlan &P, float gr_f, cudaStream_t s)
 {
+    // the grid is sized for the whole GPU: the lists' lengths are on the device
     static int resident = 0;
     if (resident == 0)
         resident = tc_resident_ctas((const void *)k_bphase_guess_tc<MK, double>, TC_SMEM);
-    const long long nch = P.ntiles[PH_C2P] * (P.tile / 128);
-    const long long grid = nch < resident ? nch : resident;
-    if (grid > 0)
-        k_bphase_guess_tc<MK, double><<<(unsigned)grid, 128, TC_SMEM, s>>>(descs, planp, gr_f);
+    k_bphase_guess_tc<MK, double><<<(unsigned)resident, 128, TC_SMEM, s>>>(descs, planp, gr_f);
+    k_bphase_clear_lists<double><<<1, 32, 0, s>>>(descs, P.nruns);
 }
 
 template <>

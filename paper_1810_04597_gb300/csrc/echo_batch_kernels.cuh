@@ -203,57 +203,55 @@ __global__ void __launch_bounds__(128) k_bphase_c2p(const RunDesc<R> *__restrict
         c2p_body<MK, R, NET>(rd.g, ph, rd.A, guess_mode, want_rate, base + c + threadIdx.x, nullptr);
 }
 
-// The network's Newton starts for the cells of every run (tensor cores,
-// echo_mlp_tc.cuh), as k_mlp_guess_tc does for one run: persistent CTAs walk
-// the c2p phase's tiles in chunks of 128 cells (the plan's tile is a
-// multiple of 128, so a chunk is one of the run's own 128-cell tiles), skip
-// the chunks its last inversion did not flag, choose per cell between the
-// network start and the previous-stage Z, and load the next flagged chunk's
-// inputs during the current chunk's MMA round trips.  All runs use runs[0]'s
-// network.
+// The network's Newton starts for the cells every run's last inversion
+// listed (tensor cores, echo_mlp_tc.cuh), as k_mlp_guess_tc does for one
+// run: persistent CTAs walk the runs' lists in tiles of 128 cells, run after
+// run (each CTA forms the tiles' prefix sums over the runs' list lengths),
+// choose per cell between the network start and the previous-stage Z, and
+// load the next tile's inputs during the current tile's MMA round trips.
+// All runs use runs[0]'s network.
 template <int MK, typename R>
 __global__ void __launch_bounds__(128, 6) k_bphase_guess_tc(const RunDesc<R> *__restrict__ runs,
                                                          const BatchPlan *__restrict__ plan, float gr_f)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    __shared__ int s_first;
-    const long long cpt = plan->tile / 128;
-    const long long nch = plan->ntiles[PH_C2P] * cpt;
-    // run of chunk ch and the run-local index of its first cell
-    auto locate = [&](long long ch, int &run) -> long long {
-        const long long tl = ch / cpt;
-        const Segment sgm = plan->seg[PH_C2P][find_segment(plan, PH_C2P, tl)];
-        run = sgm.run;
-        return (tl - sgm.first_tile) * plan->tile + (ch % cpt) * 128;
+    __shared__ long long s_first_tile[ECHO_BATCH_MAXRUNS + 1];
+    const int nruns = plan->nruns;
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int r = 0; r < nruns; ++r) {
+            s_first_tile[r] = acc;
+            acc += ((long long)runs[r].A.scal->nlist_count + 127) / 128;
+        }
+        s_first_tile[nruns] = acc;
+    }
+    __syncthreads();
+    const long long ntiles = s_first_tile[nruns];
+    long long tile = blockIdx.x;
+    if (tile >= ntiles)
+        return;   // block-uniform: nothing listed for this CTA (nothing allocated yet)
+    auto load = [&](long long tl, int &run, CellIn<R> &x) {
+        run = 0;
+        while (run + 1 < nruns && s_first_tile[run + 1] <= tl)
+            ++run;
+        const long long cnt = (long long)runs[run].A.scal->nlist_count;
+        const long long r = (tl - s_first_tile[run]) * 128 + threadIdx.x;
+        listed_cell_load<MK, R>(runs[run].g, runs[run].A, runs[run].A.nlist, cnt, r, x);
     };
-    auto flagged = [&](long long ch) {
-        int r = 0;
-        const long long b = locate(ch, r);
-        const Geom &g = runs[r].g;
-        return b < (long long)g.n[0] * g.n[1] * g.n[2] && runs[r].A.tflag[b >> 7] != 0;
-    };
-    long long ch = next_flagged(blockIdx.x, nch, gridDim.x, flagged, &s_first);
-    if (ch >= nch)
-        return;   // block-uniform: nothing flagged for this CTA (nothing allocated yet)
     TcMlp tm;
     tc_setup(tm, tc_smem, runs[0].A.mlp);
     CellIn<R> x;
     int run = 0;
-    {
-        const long long b = locate(ch, run);
-        cell_in_load(runs[run].g, runs[run].A, b + threadIdx.x, x);
-    }
-    while (ch < nch) {
+    load(tile, run, x);
+    for (; tile < ntiles; tile += gridDim.x) {
         float f[MLP_NI], o[MLP_NO];
         const int cur = run;
         const float D = cell_in_features<MK, R>(runs[cur].A, x, f);
         const int id = x.id;
         const bool live = x.live;
-        const long long next = next_flagged(ch + gridDim.x, nch, gridDim.x, flagged, &s_first);
-        if (next < nch) {
-            const long long b = locate(next, run);
-            cell_in_load(runs[run].g, runs[run].A, b + threadIdx.x, x);
-        }
+        const long long next = tile + gridDim.x;
+        if (next < ntiles)
+            load(next, run, x);
         const bool ok = tc_tile(tm, f, o);
         if (live) {
             float z0 = -1.0f;
@@ -263,9 +261,17 @@ __global__ void __launch_bounds__(128, 6) k_bphase_guess_tc(const RunDesc<R> *__
             }
             runs[cur].A.zg[id] = z0;
         }
-        ch = next;
     }
     tc_teardown(tm);
+}
+
+// Empty every run's network-start list (after the network's pass, before
+// the inversion that lists the cells again).
+template <typename R>
+__global__ void k_bphase_clear_lists(const RunDesc<R> *__restrict__ runs, int nruns)
+{
+    if ((int)threadIdx.x < nruns)
+        runs[threadIdx.x].A.scal->nlist_count = 0ULL;
 }
 
 template <int MK, typename R>

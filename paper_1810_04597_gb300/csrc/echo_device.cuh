@@ -150,6 +150,9 @@ struct DevScalars {
     unsigned long long c2p_hist[ECHO_C2P_HIST];   // inversions by Newton iterations (last: that many or more)
     unsigned long long fallback_faces;  // first-order face fallbacks on faces bounding owned cells (sides)
     unsigned long long mlp_used;        // inversions started from the network's Newton start
+    unsigned long long nlist_count;     // entries of Arrays::nlist
+    unsigned long long guard_faces;     // order 1: faces the safeguard returned to the uncorrected flux
+    unsigned long long guard_new[4];    // order 1: cells each safeguard pass of the running stage flagged
 };
 
 // Metric at one point of the axisymmetric (x1, x2) plane, FP64: lapse,
@@ -187,7 +190,9 @@ struct Arrays {
     float *zg;     // network Newton start per cell (> 0), or 0: the previous-stage Z chosen, < 0: the
                    // tensor-core result missing (previous Z, counted); written by k_mlp_guess_tc
     unsigned char *ze;     // per cell: code of the previous-Z error at the last inversion (ze_code)
-    unsigned char *tflag;  // per tile of 128 owned cells: 1 if a cell's code reached the network's gate
+    int *nlist;            // padded indices of the cells whose code reached the network's gate at the
+                           // last inversion (the cells the next one may start from the network)
+    unsigned char *gmark;  // order 1: cells the safeguard flagged in the running stage
     R *P[8];       // primitives rho, v^x, v^y, v^z, p, B^x, B^y, B^z (cell)
     R *F[3][5];    // HLL fluxes on d-faces
     R *ap[3];      // HLL a+ on d-faces

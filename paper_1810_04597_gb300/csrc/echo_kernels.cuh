@@ -202,28 +202,31 @@ __device__ __forceinline__ float net_z0(const float o[MLP_NO], double Dc, float 
 // Z0 = D W (1 + G/(G-1) (p/D) W) in FP32 (net_z0): it only starts the Newton
 // solve, and the FP64 pipe is the scarce one.
 //
-// Per-cell choice (network modes): the network is consulted only in tiles
-// of 128 cells that the last inversion flagged (A.tflag: a cell's previous-Z
-// error code reached the network's gate), and a cell takes the network start
-// only where the network's predicted error beats its previous Z's (net_beats
-// on the code A.ze); every other cell starts from the previous-stage Z.
-// tile_flag: the flag of t's tile for MLPK 2 (read here otherwise).
+// Per-cell choice (network modes): only a cell the last inversion listed
+// (its previous-Z error code A.ze within the network's gate) consults the
+// network, and it takes the network start only where the network's
+// predicted error beats its previous Z's (net_beats); every other cell
+// starts from the previous-stage Z.
 //
-// Every inversion of the network modes writes the cell's new code A.ze and,
-// through a block-wide vote, the flag of its tile for the next inversion:
-// then all 128 threads of the block must call this with t in one 128-aligned
-// tile of owned cells.  The plain modes (MLPK 0) write neither; the host
-// resets the codes before a network-mode inversion that follows them.
+// Every inversion of the network modes writes the cell's new code A.ze and
+// appends the cell to A.nlist when the new code is within the gate (the
+// list the network's pass before the next inversion walks; the host empties
+// it between that pass and the inversion).  The plain modes (MLPK 0) write
+// neither; the host resets the codes before a network-mode inversion that
+// follows them.  Every lane of a warp must call this.
 template <int MK, typename R, int MLPK>
 __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mode,
                                          int want_rate, long long t, const float *mlp_sm,
-                                         const float *net = nullptr, bool net_ok = false, bool tile_flag = false)
+                                         const float *net = nullptr, bool net_ok = false)
 {
     C2PCell c;
     const bool live = c2p_cell<MK, R>(g, A, t, c);
     double rate = 0.0;
     unsigned long long its = 0, calls = 0, fails = 0, floors = 0, mfb = 0, used = 0;
     bool want_net = false;
+    int gate = 0;
+    if constexpr (MLPK != 0)
+        gate = ze_gate(A.mlp[MLP_OGATE]);
     if (live) {
         const int id = c.id;
         const int i = c.i;
@@ -242,8 +245,8 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             // previous-stage Z because the network's result is missing (counted)
             int pick = 0;
             float z0f = 0.0f;
-            const bool flagged = MLPK == 2 ? tile_flag : A.tflag[t >> 7] != 0;
-            if (flagged) {
+            const unsigned char code = A.ze[id];
+            if ((int)code <= gate) {
                 if constexpr (MLPK == 3) {
                     z0f = A.zg[id];
                     pick = z0f > 0.0f ? 1 : (z0f < 0.0f ? -1 : 0);
@@ -262,36 +265,40 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
                     }
                     if (!ok) {
                         pick = -1;
-                    } else if (net_beats(o[2], A.ze[id])) {
+                    } else if (net_beats(o[2], code)) {
                         pick = 1;
                         z0f = net_z0(o, Dc, ph.gr_f);
                     }
                 }
             }
-            r.ok = false;
-            int first = 0;
+            // one Newton call site: the chosen start, and after a network
+            // start that did not converge in 8 iterations the restart from
+            // the previous-stage Z (no FP32 refinement then)
+            double start = zg;
+            int maxit = NEWTON_MAXIT;
+            bool ref = refine;
             if (pick == 1) {
                 used = 1;
-                const double z0 = f2d(z0f);
-                if constexpr (MK == 1)
-                    r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MKS<double>(*mp), 8, refine, tol);
-                else
-                    r = c2p_newton(Dc, S, tc, B, z0, ph.gm1g, MFlat<double>(), 8, refine, tol);
-                first = r.iters;
-                if (!r.ok)
-                    mfb = 1;
+                start = f2d(z0f);
+                maxit = 8;
             } else if (pick == -1) {
                 mfb = 1;
             }
-            if (!r.ok) {
-                // previous-stage Z: the chosen start, or the restart after the
-                // network start failed (no FP32 refinement then)
-                const bool ref = pick == 1 ? false : refine;
+            int first = 0;
+#pragma unroll 1
+            for (int attempt = 0;; ++attempt) {
                 if constexpr (MK == 1)
-                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp), NEWTON_MAXIT, ref, tol);
+                    r = c2p_newton(Dc, S, tc, B, start, ph.gm1g, MKS<double>(*mp), maxit, ref, tol);
                 else
-                    r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>(), NEWTON_MAXIT, ref, tol);
+                    r = c2p_newton(Dc, S, tc, B, start, ph.gm1g, MFlat<double>(), maxit, ref, tol);
                 r.iters += first;
+                if (r.ok || pick != 1 || attempt == 1)
+                    break;
+                mfb = 1;
+                first = r.iters;
+                start = zg;
+                maxit = NEWTON_MAXIT;
+                ref = false;
             }
         } else {
             if constexpr (MK == 1)
@@ -336,7 +343,7 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             // this cell may gain from the network there
             const unsigned char code = ze_code(Z, zold);
             A.ze[id] = code;
-            want_net = (int)code <= ze_gate(A.mlp[MLP_OGATE]);
+            want_net = (int)code <= gate;
         }
         if (want_rate) {
             if constexpr (sizeof(R) == 4) {
@@ -358,13 +365,9 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             }
         }
     }
-    // the tile's flag for the next inversion (block vote; the tile lies in
-    // the owned cells when its first cell does)
-    if constexpr (MLPK != 0) {
-        const int any = __syncthreads_or(want_net ? 1 : 0);
-        if ((threadIdx.x & 127) == 0 && t < (long long)g.n[0] * g.n[1] * g.n[2])
-            A.tflag[t >> 7] = (unsigned char)any;
-    }
+    // the cells the next inversion may start from the network
+    if constexpr (MLPK != 0)
+        list_append(want_net, live ? c.id : 0, A.nlist, &A.scal->nlist_count);
     // histogram of the iteration counts: one atomic per distinct count in the warp
     {
         const unsigned lmask = __ballot_sync(0xffffffffu, live);
@@ -380,8 +383,10 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
     calls = warp_sum_u64(calls);
     fails = warp_sum_u64(fails);
     floors = warp_sum_u64(floors);
-    mfb = warp_sum_u64(mfb);
-    used = warp_sum_u64(used);
+    if constexpr (MLPK != 0) {
+        mfb = warp_sum_u64(mfb);
+        used = warp_sum_u64(used);
+    }
     if (want_rate)
         rate = warp_max(rate);
     if ((threadIdx.x & 31) == 0) {
@@ -395,17 +400,20 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
         }
         if (floors)
             atomicAdd(&A.scal->floor_hits, floors);
-        if (mfb)
-            atomicAdd(&A.scal->mlp_fallback, mfb);
-        if (used)
-            atomicAdd(&A.scal->mlp_used, used);
+        if constexpr (MLPK != 0) {
+            if (mfb)
+                atomicAdd(&A.scal->mlp_fallback, mfb);
+            if (used)
+                atomicAdd(&A.scal->mlp_used, used);
+        }
         if (want_rate && rate > 0.0)
             atomicMax(&A.scal->rate_bits, (unsigned long long)__double_as_longlong(rate));
     }
 }
 
 // NET: 0 no network; 1 the FP32 network on the CUDA cores (parameter block
-// staged in shared memory); 3 the Newton starts k_mlp_guess_tc wrote.
+// staged in shared memory); 3 the Newton starts k_mlp_guess_tc wrote (that
+// form through k_c2p_listed).
 template <int MK, typename R, int NET>
 __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate)
 {
@@ -419,6 +427,15 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
         sm = Ps;
     }
     c2p_body<MK, R, NET>(g, ph, A, guess_mode, want_rate, (long long)blockIdx.x * blockDim.x + threadIdx.x, sm);
+}
+
+// c2p from the Newton starts k_mlp_guess_tc wrote for the listed cells
+// (NET 3), held to the plain kernel's occupancy (7 blocks of 128 threads per
+// SM): the FP64-bound solve needs the warps more than the registers.
+template <int MK, typename R>
+__global__ void __launch_bounds__(128, 7) k_c2p_listed(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate)
+{
+    c2p_body<MK, R, 3>(g, ph, A, guess_mode, want_rate, (long long)blockIdx.x * blockDim.x + threadIdx.x, nullptr);
 }
 
 // Inputs of one cell's network features, loaded one tile ahead of their use
@@ -492,38 +509,50 @@ __device__ __forceinline__ float cell_in_features(const Arrays<R> &A, const Cell
 }
 
 // The network's Newton starts for the c2p kernel that follows (NET 3), both
-// hidden layers on the tensor cores (echo_mlp_tc.cuh): persistent CTAs of
-// 128 threads walk the tiles of 128 cells that the last inversion flagged
-// (A.tflag) and skip the others, whose cells keep the previous-stage Z.  In
-// a flagged tile a cell gets the start Z0 > 0 only where the network's
-// predicted error beats its previous Z's (net_beats), else 0; a tile whose
-// tensor-core result did not arrive writes -1 (previous-stage Z, counted in
-// mlp_fallback).  The next flagged tile's inputs load during the current
-// tile's MMA round trips.  Keeping the network out of the c2p kernel leaves
-// that FP64-bound kernel at full occupancy and free of the per-tile
-// barriers of the MMA round trips.
+// hidden layers on the tensor cores (echo_mlp_tc.cuh), for the cells the
+// last inversion listed (A.nlist, A.scal->nlist_count entries): persistent
+// CTAs of 128 threads walk the list in tiles of 128 cells.  A listed cell
+// gets the start Z0 > 0 where the network's predicted error beats its
+// previous Z's (net_beats), else 0; a tile whose tensor-core result did not
+// arrive writes -1 (previous-stage Z, counted in mlp_fallback).  Unlisted
+// cells are not touched (c2p does not read their start).  The next tile's
+// inputs load during the current tile's MMA round trips.  Keeping the
+// network out of the c2p kernel leaves that FP64-bound kernel at full
+// occupancy and free of the per-tile barriers of the MMA round trips.
 template <int MK, typename R>
-__global__ void __launch_bounds__(128, 6) k_mlp_guess_tc(Geom g, Arrays<R> A, float gr_f, long long ntiles)
+__device__ __forceinline__ void listed_cell_load(const Geom &g, const Arrays<R> &A, const int *list, long long cnt,
+                                                 long long r, CellIn<R> &x)
+{
+    const int id = list[r < cnt ? r : cnt - 1];
+    // padded index -> (i, j, k); a lane past the end repeats the last cell
+    const int k = id / g.pxy, rem = id - k * g.pxy;
+    const int j = rem / g.px, i = rem - j * g.px;
+    const long long t = ((long long)(k - NG) * g.n[1] + (j - NG)) * g.n[0] + (i - NG);
+    cell_in_load(g, A, t, x);
+    x.live = r < cnt;
+}
+
+template <int MK, typename R>
+__global__ void __launch_bounds__(128, 6) k_mlp_guess_tc(Geom g, Arrays<R> A, float gr_f)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    __shared__ int s_first;
-    const unsigned char *__restrict__ flag = A.tflag;
-    auto flagged = [&](long long tl) { return flag[tl] != 0; };
-    long long tile = next_flagged(blockIdx.x, ntiles, gridDim.x, flagged, &s_first);
+    const long long cnt = (long long)A.scal->nlist_count;
+    const long long ntiles = (cnt + 127) / 128;
+    long long tile = blockIdx.x;
     if (tile >= ntiles)
-        return;   // block-uniform: no flagged tile for this CTA (nothing allocated yet)
+        return;   // block-uniform: nothing listed for this CTA (nothing allocated yet)
     TcMlp tm;
     tc_setup(tm, tc_smem, A.mlp);
     CellIn<R> x;
-    cell_in_load(g, A, tile * 128 + threadIdx.x, x);
-    while (tile < ntiles) {
+    listed_cell_load<MK, R>(g, A, A.nlist, cnt, tile * 128 + threadIdx.x, x);
+    for (; tile < ntiles; tile += gridDim.x) {
         float f[MLP_NI], o[MLP_NO];
-        const float D = cell_in_features<MK, R>(A, x, f);   // a lane past the end: its clamped cell's values
+        const float D = cell_in_features<MK, R>(A, x, f);
         const int id = x.id;
         const bool live = x.live;
-        const long long next = next_flagged(tile + gridDim.x, ntiles, gridDim.x, flagged, &s_first);
+        const long long next = tile + gridDim.x;
         if (next < ntiles)
-            cell_in_load(g, A, next * 128 + threadIdx.x, x);
+            listed_cell_load<MK, R>(g, A, A.nlist, cnt, next * 128 + threadIdx.x, x);
         const bool ok = tc_tile(tm, f, o);
         if (live) {
             float z0 = -1.0f;
@@ -533,19 +562,18 @@ __global__ void __launch_bounds__(128, 6) k_mlp_guess_tc(Geom g, Arrays<R> A, fl
             }
             A.zg[id] = z0;
         }
-        tile = next;
     }
     tc_teardown(tm);
 }
 
 // c2p with the network evaluated inside it (guess mode +16), both hidden
 // layers on the tensor cores (echo_mlp_tc.cuh): persistent CTAs of 128
-// threads walk tiles of 128 cells; in a tile the last inversion flagged
-// every thread computes its cell's features, the CTA runs the network (one
-// tcgen05 MMA group), then every thread inverts its cell, from the network
-// start where its predicted error beats the previous Z's.  Unflagged tiles
-// skip the network.  A tile whose tensor-core result did not arrive falls
-// back to the previous-stage guess (counted in mlp_fallback).
+// threads walk tiles of 128 cells; where a cell of the tile was listed by the
+// last inversion, every thread computes its cell's features, the CTA runs the
+// network (one tcgen05 MMA group), and the listed cells start from it where
+// its predicted error beats the previous Z's; other tiles skip the network.
+// A tile whose tensor-core result did not arrive falls back to the
+// previous-stage guess (counted in mlp_fallback).
 template <int MK, typename R>
 __global__ void __launch_bounds__(128, 6) k_c2p_tc(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate,
                                                 long long ntiles)
@@ -553,21 +581,23 @@ __global__ void __launch_bounds__(128, 6) k_c2p_tc(Geom g, Phys ph, Arrays<R> A,
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     TcMlp tm;
     tc_setup(tm, tc_smem, A.mlp);
+    const int gate = ze_gate(A.mlp[MLP_OGATE]);
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long t = tile * 128 + threadIdx.x;
-        const bool flagged = A.tflag[tile] != 0;   // block-uniform
         C2PCell c;
         float f[MLP_NI], o[MLP_NO] = {0.0f, 0.0f, 0.0f};
+        const bool have = c2p_cell<MK, R>(g, A, t, c);
+        const bool listed = have && (int)A.ze[c.id] <= gate;
         bool ok = false;
-        if (flagged) {
-            if (c2p_cell<MK, R>(g, A, t, c))
+        if (__syncthreads_or(listed ? 1 : 0)) {   // block-uniform
+            if (have)
                 c2p_cell_features<MK>(c, f);
             else
                 for (int q = 0; q < MLP_NI; ++q)
                     f[q] = tm.P[TP_NORM + q];
             ok = tc_tile(tm, f, o);
         }
-        c2p_body<MK, R, 2>(g, ph, A, guess_mode, want_rate, t, nullptr, o, ok, flagged);
+        c2p_body<MK, R, 2>(g, ph, A, guess_mode, want_rate, t, nullptr, o, ok);
     }
     tc_teardown(tm);
 }
@@ -1070,6 +1100,35 @@ __device__ __forceinline__ double geom_idx<double>(const Geom &g, int d) { retur
 template <>
 __device__ __forceinline__ float geom_idx<float>(const Geom &g, int d) { return g.idx_f[d]; }
 
+// L(U) of the five cell variables of owned cell (i, j, k) at padded index
+// id: minus the flux differences (order 1: of the corrected fluxes) plus the
+// sources.
+template <int MK, typename R>
+__device__ __forceinline__ void cell_rate(const Geom &g, const Phys &ph, const Arrays<R> &A, int id, int i, int j,
+                                          R rate[5])
+{
+    const int st[3] = {1, g.px, g.pxy};
+    R src[5] = {R(0), R(0), R(0), R(0), R(0)};
+    if constexpr (MK == 1) {
+        R P[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            P[q] = A.P[q][id];
+        const int ti = j * A.met.np0 + i;
+        ks_sources(P, phys_gr<R>(ph), A.met.C[ti], A.met.dC[ti], src);
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        R r = R(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const R *__restrict__ F = g.order ? A.Fc[d][q] : A.F[d][q];
+            r -= (F[id + st[d]] - F[id]) * geom_idx<R>(g, d);
+        }
+        rate[q] = r + src[q];
+    }
+}
+
 template <int MK, typename R>
 __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const Arrays<R> &A, int stage,
                                             double *Lout, long long t)
@@ -1091,24 +1150,11 @@ __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const
     const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
 
     if (own[0] && own[1] && own[2]) {
-        R src[5] = {R(0), R(0), R(0), R(0), R(0)};
-        if constexpr (MK == 1) {
-            R P[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                P[q] = A.P[q][id];
-            const int ti = j * A.met.np0 + i;
-            ks_sources(P, phys_gr<R>(ph), A.met.C[ti], A.met.dC[ti], src);
-        }
+        R rate[5];
+        cell_rate<MK, R>(g, ph, A, id, i, j, rate);
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            R r = R(0);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const R *__restrict__ F = g.order ? A.Fc[d][q] : A.F[d][q];
-                r -= (F[id + st[d]] - F[id]) * geom_idx<R>(g, d);
-            }
-            r += src[q];
+            const R r = rate[q];
             if (stage < 0) {
                 Lout[q * N + ((long long)tk * g.n[1] + tj) * g.n[0] + ti] = (double)r;
             } else {
@@ -1179,6 +1225,122 @@ template <int MK, typename R>
 __global__ void __launch_bounds__(256) k_update(Geom g, Phys ph, Arrays<R> A, int stage, double *Lout)
 {
     update_body<MK, R>(g, ph, A, stage, Lout, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---- order 1: admissibility safeguard of the flux-derivative correction
+//
+// Pass `pass` (0 .. GUARD_PASSES-1) of a stage: every owned cell not yet
+// flagged forms its stage result as k_update will (stage 0: U + dt L;
+// 1: 3/4 U0 + 1/4 (U + dt L); 2: 1/3 U0 + 2/3 (U + dt L)) from L(U) with the
+// current (corrected, or already returned) fluxes, with the cell-centre
+// field of the current state, and is flagged if the FP64 Newton inversion
+// from its Z cannot invert it; k_guard_revert then gives every face of a
+// flagged cell its uncorrected flux.  A pass after one that flagged nothing
+// returns at once.  The stage step dt is the device's.
+constexpr int GUARD_PASSES = 3;
+
+template <int MK, typename R>
+__global__ void __launch_bounds__(128) k_guard_mark(Geom g, Phys ph, Arrays<R> A, int stage, int pass)
+{
+    if (pass > 0 && A.scal->guard_new[pass - 1] == 0ULL)
+        return;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    C2PCell c;
+    if (!c2p_cell<MK, R>(g, A, t, c) || A.gmark[c.id])
+        return;
+    const int id = c.id;
+    R rate[5];
+    cell_rate<MK, R>(g, ph, A, id, c.i, c.j, rate);
+    const R dt = (R)A.scal->dt;
+    const R wa = stage == 0 ? R(0) : (stage == 1 ? R(0.75) : R(1.0 / 3.0));
+    const R wb = stage == 0 ? R(1) : (stage == 1 ? R(0.25) : R(2.0 / 3.0));
+    double u[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const R fe = A.U[q][id] + dt * rate[q];
+        u[q] = to_d(stage == 0 ? fe : wa * A.U0[q][id] + wb * fe);
+    }
+    // undensitised, with the cell-centre field of the current state
+    double S[3], B[3], Dc = u[0], tc = u[4];
+    if constexpr (MK == 1) {
+        const double isg = c.mp->isg;
+        Dc *= isg;
+        tc *= isg;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            S[q] = u[1 + q] * isg;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            S[q] = u[1 + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        B[q] = to_d(A.P[5 + q][id]);
+    constexpr double tol = sizeof(R) == 4 ? NEWTON_TOL_BULK32 : NEWTON_TOL;
+    C2PResult r;
+    if constexpr (MK == 1)
+        r = c2p_newton(Dc, S, tc, B, A.Z[id], ph.gm1g, MKS<double>(*c.mp), NEWTON_MAXIT, false, tol);
+    else
+        r = c2p_newton(Dc, S, tc, B, A.Z[id], ph.gm1g, MFlat<double>(), NEWTON_MAXIT, false, tol);
+    if (!r.ok) {
+        A.gmark[id] = 1;
+        atomicAdd(&A.scal->guard_new[pass], 1ULL);
+    }
+}
+
+// Faces bounding a flagged cell (of the (n0+1)(n1+1)(n2+1) box, each
+// direction's owned faces) take the uncorrected flux; a periodic axis pairs
+// the faces across the seam with the cells they bound.  Counts the faces
+// whose flux changed, the periodic duplicate face not again.
+template <typename R>
+__global__ void __launch_bounds__(256) k_guard_revert(Geom g, Arrays<R> A, int pass)
+{
+    if (A.scal->guard_new[pass] == 0ULL)
+        return;
+    const long long e0 = g.n[0] + 1, e1 = g.n[1] + 1;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= e0 * e1 * (g.n[2] + 1))
+        return;
+    const int tt[3] = {(int)(t % e0), (int)((t / e0) % e1), (int)(t / (e0 * e1))};
+    unsigned long long changed = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        bool owned = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (a != d && tt[a] >= g.n[a])
+                owned = false;
+        if (!owned)
+            continue;
+        const bool per = g.bc[2 * d] == BC_PERIODIC;
+        bool f = false;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            int c[3] = {tt[0], tt[1], tt[2]};
+            c[d] -= side == 0 ? 1 : 0;
+            if (c[d] < 0 || c[d] >= g.n[d]) {
+                if (!per)
+                    continue;
+                c[d] = (c[d] % g.n[d] + g.n[d]) % g.n[d];
+            }
+            f = f || A.gmark[gidx(g, NG + c[0], NG + c[1], NG + c[2])] != 0;
+        }
+        if (!f)
+            continue;
+        const int id = gidx(g, NG + tt[0], NG + tt[1], NG + tt[2]);
+        bool ch = false;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const R v = A.F[d][q][id];
+            ch = ch || A.Fc[d][q][id] != v;
+            A.Fc[d][q][id] = v;
+        }
+        if (ch && !(per && tt[d] == g.n[d]))
+            ++changed;
+    }
+    if (changed)
+        atomicAdd(&A.scal->guard_faces, changed);
 }
 
 // Primitives (host layout, 5 arrays) + face B~ (already in U, ghosts
@@ -1451,6 +1613,20 @@ __global__ void k_pack_cells(Geom g, Arrays<R> A, double *dst, int what)
     } else {
         dst[h] = A.Z[id];
     }
+}
+
+// The network-start list of a cold start: every owned cell, in order.
+template <typename R>
+__global__ void k_list_all(Geom g, Arrays<R> A)
+{
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0)
+        A.scal->nlist_count = (unsigned long long)N;
+    if (t >= N)
+        return;
+    const int i = (int)(t % g.n[0]), j = (int)((t / g.n[0]) % g.n[1]), k = (int)(t / ((long long)g.n[0] * g.n[1]));
+    A.nlist[t] = gidx(g, NG + i, NG + j, NG + k);
 }
 
 template <typename R>

@@ -66,7 +66,15 @@ void launch_unpack_z(const Geom &g, const double *src, const Arrays<R> &A, cudaS
     k_unpack_z<R><<<grid3(g.n[0], g.n[1], g.n[2], blk), blk, 0, s>>>(g, src, A);
 }
 
+template <typename R>
+void launch_list_all(const Geom &g, const Arrays<R> &A, cudaStream_t s)
+{
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    k_list_all<R><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(g, A);
+}
+
 #define ECHO_INSTANTIATE_COMMON(R)                                                                          \
+    template void launch_list_all<R>(const Geom &, const Arrays<R> &, cudaStream_t);                       \
     template void launch_fill<R>(const Geom &, const FillList<R> &, cudaStream_t);                         \
     template void launch_totals<R>(const Geom &, const Arrays<R> &, int, cudaStream_t);                    \
     template void launch_unpack_state<R>(const Geom &, const double *, const Arrays<R> &, int, cudaStream_t); \

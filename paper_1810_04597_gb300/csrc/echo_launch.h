@@ -28,6 +28,9 @@ template <typename R>
 void launch_fill(const Geom &g, const FillList<R> &L, cudaStream_t s);
 template <int MK, typename R>
 void launch_c2p(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mode, int want_rate, cudaStream_t s);
+// guess modes 1, 5: the network's pass writing the listed cells' Newton starts (before launch_c2p)
+template <int MK, typename R>
+void launch_net_pass(const Geom &g, const Phys &ph, const Arrays<R> &A, int guess_mode, cudaStream_t s);
 template <int MK, typename R>
 void launch_faces(const Geom &g, const Phys &ph, const Arrays<R> &A, int d, cudaStream_t s);
 template <int MK, typename R>
@@ -44,6 +47,12 @@ void launch_totals(const Geom &g, const Arrays<R> &A, int nblk, cudaStream_t s);
 // order 1: corrected fluxes (Fc) and EMFs (Ec) from F and E (6 launches)
 template <typename R>
 void launch_correct(const Geom &g, const Arrays<R> &A, cudaStream_t s);
+// order 1: the admissibility safeguard of stage `stage` (2 memsets, 6 launches)
+template <int MK, typename R>
+void launch_guard(const Geom &g, const Phys &ph, const Arrays<R> &A, int stage, cudaStream_t s);
+// the network-start list of a cold start (every owned cell)
+template <typename R>
+void launch_list_all(const Geom &g, const Arrays<R> &A, cudaStream_t s);
 template <typename R>
 void launch_unpack_state(const Geom &g, const double *src, const Arrays<R> &A, int what, cudaStream_t s);
 template <typename R>

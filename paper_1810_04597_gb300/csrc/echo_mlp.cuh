@@ -135,8 +135,8 @@ __device__ __forceinline__ void mlp_infer(const float *__restrict__ P, const flo
 // ---- per-cell choice of the Newton start
 //
 // The previous-stage Z of a cell is a good start when the state moved
-// little since the last inversion.  Every inversion records, per cell, the
-// code q of that movement: q = e(Z) - e(|Z - Z_prev|) from the binary
+// little since the last inversion.  Every network-mode inversion records,
+// per cell, the code q of that movement: q = e(Z) - e(|Z - Z_prev|) from the binary
 // exponents e of the new Z and of its change, i.e. -log2 of the relative
 // change within one (0: a change of order one, 254: a change below 2^-254,
 // 255: no change; a cold start, Z_prev = 0, gives 0).  It estimates the
@@ -157,7 +157,9 @@ __device__ __forceinline__ unsigned char ze_code(double Z, double zprev)
 }
 
 // A cell whose previous Z is at least as far off as the network's typical
-// error (gate, log10) may gain from the network: q <= floor(-gate log2 10).
+// error (gate, log10) may gain from the network: q <= floor(-gate log2 10);
+// the inversion lists those cells (Arrays::nlist) for the network's pass
+// before the next one, and only they consult the network there.
 __device__ __forceinline__ int ze_gate(float gate_log10)
 {
     const float g = -gate_log10 * 3.32192809f;
@@ -169,29 +171,20 @@ __device__ __forceinline__ bool net_beats(float o2, unsigned char q)
     return q != ZE_EXACT && -o2 * 3.32192809f > (float)q + 0.5f;
 }
 
-// The first index t + k stride (k = 0, 1, ...) below n whose flagged(index)
-// holds, or n: the 128 threads of the block test 128 candidates at once.
-// Every thread of the block calls it (block-uniform result).
-template <typename F>
-__device__ __forceinline__ long long next_flagged(long long t, long long n, long long stride, F flagged, int *s_first)
+// Append the padded index id of every lane with `want` to a list (one
+// atomic per warp, lanes in lane order); every lane of the warp calls this.
+__device__ __forceinline__ void list_append(bool want, int id, int *list, unsigned long long *count)
 {
-    for (;;) {
-        if (t >= n)
-            return n;
-        const long long mine = t + (long long)threadIdx.x * stride;
-        const bool f = mine < n && flagged(mine);
-        if (threadIdx.x == 0)
-            *s_first = 1 << 30;
-        __syncthreads();
-        if (f)
-            atomicMin(s_first, (int)threadIdx.x);
-        __syncthreads();
-        const int k = *s_first;
-        __syncthreads();
-        if (k != 1 << 30)
-            return t + (long long)k * stride;
-        t += (long long)blockDim.x * stride;
-    }
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m)
+        return;
+    const int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == __ffs(m) - 1)
+        base = atomicAdd(count, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (want)
+        list[base + __popc(m & ((1u << lane) - 1u))] = id;
 }
 
 }  // namespace echo

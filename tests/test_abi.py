@@ -111,8 +111,8 @@ def test_calls_out_of_order_are_rejected(lib):
 
 def test_totals_struct_matches_the_header(lib):
     """The binding's echo_totals has the header's members in order (the
-    iteration histogram of ECHO_C2P_HIST long longs, then the count of
-    network starts)."""
+    iteration histogram of ECHO_C2P_HIST long longs, then the counts of
+    network starts and of faces the order-1 safeguard changed)."""
     import ctypes
     src = open(os.path.join(ROOT, "include", "echo.h")).read()
     body = re.search(r"typedef struct \{([^{}]*)\} echo_totals;", src).group(1)
@@ -120,7 +120,7 @@ def test_totals_struct_matches_the_header(lib):
     names = re.findall(r"\b([a-z_0-9]+)(?:\[[A-Z_0-9]+\])?;", body)
     assert names == [f[0] for f in _lib.echo_totals._fields_], names
     assert int(re.search(r"#define ECHO_C2P_HIST (\d+)", src).group(1)) == _lib.ECHO_C2P_HIST
-    assert ctypes.sizeof(_lib.echo_totals) == 8 * (7 + 6 + _lib.ECHO_C2P_HIST + 1)
+    assert ctypes.sizeof(_lib.echo_totals) == 8 * (7 + 6 + _lib.ECHO_C2P_HIST + 2)
 
 
 def test_guess_modes_are_validated(lib):
