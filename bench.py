@@ -244,15 +244,13 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_sample(prob, nsteps_hint, budget_s, w=48):
-    """Time oracle SSP-RK3 steps on the workload's recipe at w^3 (a periodic
-    sweep_box of the same seeded recipe) for about budget_s seconds.
-    Returns (zones_per_s, zones, steps, seconds, threads, w)."""
+def oracle_rate(prob, nsteps_hint, budget_s):
+    """Time oracle SSP-RK3 steps of problem `prob` (FP64 C oracle, OpenMP
+    over cells) for about budget_s seconds after one untimed step.
+    Returns (zones_per_s, steps, seconds, threads)."""
     import oracle
-    from paper_1810_04597_gb300 import inputs
-    win = inputs.sweep_box(w)
-    cfg = oracle.make_cfg(win)
-    st, Z = oracle.p2c(cfg, win.prims, win.bface)
+    cfg = oracle.make_cfg(prob)
+    st, Z = oracle.p2c(cfg, prob.prims, prob.bface)
     t0 = time.perf_counter()
     st, Z, _, _ = oracle.steps(cfg, st, Z, 1)
     t1 = time.perf_counter() - t0
@@ -260,9 +258,45 @@ def oracle_sample(prob, nsteps_hint, budget_s, w=48):
     t0 = time.perf_counter()
     oracle.steps(cfg, st, Z, steps)
     dt = time.perf_counter() - t0
-    zones = w ** 3
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return zones * steps / dt, zones, steps, dt, threads, w
+    return prob.ncells * steps / dt, steps, dt, oracle.get_threads()
+
+
+def oracle_sample(prob, nsteps_hint, budget_s, w=48):
+    """Time oracle SSP-RK3 steps on the workload's recipe at w^3 (a periodic
+    sweep_box of the same seeded recipe) for about budget_s seconds.
+    Returns (zones_per_s, zones, steps, seconds, threads, w)."""
+    from paper_1810_04597_gb300 import inputs
+    v, steps, dt, threads = oracle_rate(inputs.sweep_box(w), nsteps_hint, budget_s)
+    return v, w ** 3, steps, dt, threads, w
+
+
+def cpu_baseline_rows(budget_s):
+    """The oracle on the host cores: the workload's recipe (sweep_box) on all
+    cores at 80^3 and on one thread at 48^3, and the torus recipe
+    (Fishbone-Moncrief, a = 0.9, beta 100, the 256x128x128 workload's
+    recipe at 64x32x32) on all cores."""
+    import oracle
+    from paper_1810_04597_gb300 import inputs
+    oracle.build()
+    cores = oracle.get_threads()
+    v, z, nsteps_c, secs, threads, w = oracle_sample(None, 50, budget_s, w=80)
+    out = {"value": v / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"sweep_box recipe at {w}^3 (periodic), {nsteps_c} SSP-RK3 steps, "
+                     f"{secs:.1f} s, FP64 C oracle with OpenMP over cells",
+           "cpu": cpu_description()}
+    oracle.set_threads(1)
+    try:
+        v1, s1, d1, t1 = oracle_rate(inputs.sweep_box(48), 20, budget_s / 3)
+    finally:
+        oracle.set_threads(cores)
+    out["one_thread"] = {"value": v1 / 1e6, "unit": UNIT, "cores": t1,
+                         "sample": f"sweep_box recipe at 48^3, {s1} steps, {d1:.1f} s, one thread"}
+    tor = inputs.fm_torus((64, 32, 32), spin=0.9, beta=100.0)
+    vt, st_, dtt, tt = oracle_rate(tor, 20, budget_s / 3)
+    out["torus"] = {"value": vt / 1e6, "unit": UNIT, "cores": tt,
+                    "sample": f"Fishbone-Moncrief torus (a = 0.9, beta 100, floors) at 64x32x32, {st_} steps, "
+                              f"{dtt:.1f} s, all cores"}
+    return out
 
 
 def cpu_description():
@@ -353,7 +387,8 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded)",
-        "config": {"workload": workload_name(args), "grid": [args.size] * 3, "zones": args.size ** 3,
+        "config": {"workload": f"{workload_name(args)}, timed on a {w}^3 sample of the same recipe per step",
+                   "grid": [args.size] * 3, "zones": args.size ** 3, "sample_grid": [w] * 3,
                    "parallelism": "rank 0 only (host cores)", "sample": f"{w}^3 box of the same recipe per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample, "cpu": cpu_description()},
@@ -564,11 +599,7 @@ def run_ours(args, world, rank, local, dist):
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, z, nsteps_c, secs, threads, w = oracle_sample(prob, 50, args.cpu_budget, w=80)
-        cpu = {"value": v / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"sweep_box recipe at {w}^3 (periodic), {nsteps_c} SSP-RK3 steps, "
-                         f"{secs:.1f} s, FP64 C oracle with OpenMP over cells",
-               "cpu": cpu_description()}
+        cpu = cpu_baseline_rows(args.cpu_budget)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

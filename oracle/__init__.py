@@ -199,6 +199,8 @@ def lib():
         L.oracle_ho_center.argtypes = [pd]
         L.oracle_ho_center.restype = d
         L.oracle_ghosts.restype = i
+        L.oracle_set_threads.argtypes = [i]
+        L.oracle_get_threads.restype = i
         L.oracle_fill_padded.argtypes = [pc, pd, i, i, i]
         L.oracle_speeds_point.argtypes = [pc, pd, pd, i, pd, pd]
         L.oracle_flux_point.argtypes = [pc, pd, pd, i, pd, pd]
@@ -316,6 +318,15 @@ def ho_flux(f5):
 def ho_center(b6):
     """Sixth-order midpoint interpolation of six equally spaced values."""
     return lib().oracle_ho_center(_dp(_f64(b6)))
+
+
+def set_threads(n: int):
+    """Threads of the oracle's OpenMP loops from now on."""
+    lib().oracle_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().oracle_get_threads())
 
 
 def ghosts() -> int:

@@ -1514,6 +1514,30 @@ double oracle_ho_center(const double *b6) { return ho_center(b6); }
 /* Ghost layers per side of every padded array. */
 int oracle_ghosts(void) { return NG; }
 
+/* Threads of the OpenMP loops from now on (n >= 1; no effect in a build
+ * without OpenMP), for timing the oracle on a chosen number of cores. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1)
+        omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int oracle_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 /* Ghost fill of one padded array (n[d] + 2 NG entries along each d, x
  * fastest; a face array holds face i-1/2 at index i) with the grid's
  * boundary conditions: the routine every step uses, exposed for the

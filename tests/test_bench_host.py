@@ -85,3 +85,15 @@ def test_algorithmic_flops_from_the_oracle_counts(tmp_path):
     for key in ("faces", "emf", "c2p", "assemble", "ct", "rk"):
         assert got["flops_per_unit"][key] > 0.0, key
     assert got["c2p_per_newton_iteration"] > 0.0 and got["update_per_cell"] > 0.0
+
+
+def test_reference_arm_labels_what_it_times():
+    """The reference arm (the oracle on the host cores) names the workload of
+    the GPU arm and, in the same label, the sample it actually times."""
+    import argparse
+    args = argparse.Namespace(size=12, precision=64, steps=1, warmup=1, gpus=1)
+    line = bench.run_reference(args, 1, 0)
+    assert line["impl"] == "reference" and line["value"] > 0.0
+    assert "12^3" in line["config"]["workload"] and "sample" in line["config"]["workload"]
+    assert line["config"]["sample_grid"] == [12, 12, 12]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
