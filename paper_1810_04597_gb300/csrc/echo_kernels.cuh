@@ -236,8 +236,7 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
         const double Dc = c.Dc, tc = c.tc;
         const int src = guess_mode & 3;
         const bool refine = (guess_mode & 4) != 0;
-        const double zold = (MLPK != 0 || src != 2) ? A.Z[id] : 0.0;
-        const double zg = src == 2 ? 0.0 : zold;
+        const double zg = src == 2 ? 0.0 : A.Z[id];
         constexpr double tol = sizeof(R) == 4 ? NEWTON_TOL_BULK32 : NEWTON_TOL;
         C2PResult r;
         if constexpr (MLPK != 0) {
@@ -271,9 +270,10 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
                     }
                 }
             }
-            // one Newton call site: the chosen start, and after a network
-            // start that did not converge in 8 iterations the restart from
-            // the previous-stage Z (no FP32 refinement then)
+            // the chosen start; after a network start that did not converge
+            // in 8 iterations, the restart from the previous-stage Z (no FP32
+            // refinement then; reloaded, so that no register holds it across
+            // the first solve)
             double start = zg;
             int maxit = NEWTON_MAXIT;
             bool ref = refine;
@@ -284,21 +284,19 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             } else if (pick == -1) {
                 mfb = 1;
             }
-            int first = 0;
-#pragma unroll 1
-            for (int attempt = 0;; ++attempt) {
-                if constexpr (MK == 1)
-                    r = c2p_newton(Dc, S, tc, B, start, ph.gm1g, MKS<double>(*mp), maxit, ref, tol);
-                else
-                    r = c2p_newton(Dc, S, tc, B, start, ph.gm1g, MFlat<double>(), maxit, ref, tol);
-                r.iters += first;
-                if (r.ok || pick != 1 || attempt == 1)
-                    break;
+            if constexpr (MK == 1)
+                r = c2p_newton(Dc, S, tc, B, start, ph.gm1g, MKS<double>(*mp), maxit, ref, tol);
+            else
+                r = c2p_newton(Dc, S, tc, B, start, ph.gm1g, MFlat<double>(), maxit, ref, tol);
+            if (!r.ok && pick == 1) {
                 mfb = 1;
-                first = r.iters;
-                start = zg;
-                maxit = NEWTON_MAXIT;
-                ref = false;
+                const int first = r.iters;
+                const double z1 = src == 2 ? 0.0 : __ldcg(&A.Z[id]);
+                if constexpr (MK == 1)
+                    r = c2p_newton(Dc, S, tc, B, z1, ph.gm1g, MKS<double>(*mp), NEWTON_MAXIT, false, tol);
+                else
+                    r = c2p_newton(Dc, S, tc, B, z1, ph.gm1g, MFlat<double>(), NEWTON_MAXIT, false, tol);
+                r.iters += first;
             }
         } else {
             if constexpr (MK == 1)
@@ -311,6 +309,10 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
         fails = r.ok ? 0 : 1;
         double P8[8] = {r.rho, r.v[0], r.v[1], r.v[2], r.p, B[0], B[1], B[2]};
         double Z = r.Z;
+        // the previous-stage Z again from memory, not held across the solve
+        double zold = 0.0;
+        if constexpr (MLPK != 0)
+            zold = __ldcg(&A.Z[id]);
         if constexpr (MK == 1) {
             if (A.met.use_floors) {
                 bool reset = !r.ok;
@@ -343,7 +345,7 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             // this cell may gain from the network there
             const unsigned char code = ze_code(Z, zold);
             A.ze[id] = code;
-            want_net = (int)code <= gate;
+            want_net = (int)code <= ze_gate(__ldg(&A.mlp[MLP_OGATE]));
         }
         if (want_rate) {
             if constexpr (sizeof(R) == 4) {
@@ -430,10 +432,11 @@ __global__ void __launch_bounds__(128) k_c2p(Geom g, Phys ph, Arrays<R> A, int g
 }
 
 // c2p from the Newton starts k_mlp_guess_tc wrote for the listed cells
-// (NET 3), held to the plain kernel's occupancy (7 blocks of 128 threads per
-// SM): the FP64-bound solve needs the warps more than the registers.
+// (NET 3), held to the plain kernel's occupancy (flat: 7 blocks of 128
+// threads per SM; Kerr-Schild: 4): the FP64-bound solve needs the warps more
+// than the registers, and the Kerr-Schild solve spills below ~110.
 template <int MK, typename R>
-__global__ void __launch_bounds__(128, 7) k_c2p_listed(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate)
+__global__ void __launch_bounds__(128, MK == 0 ? 7 : 4) k_c2p_listed(Geom g, Phys ph, Arrays<R> A, int guess_mode, int want_rate)
 {
     c2p_body<MK, R, 3>(g, ph, A, guess_mode, want_rate, (long long)blockIdx.x * blockDim.x + threadIdx.x, nullptr);
 }
