@@ -876,7 +876,7 @@ def run_guess_gain(prob, dev, mlp_state, warm=2, steps=3):
     out["note"] = ("c2p on the workload from each start: FP64 plain Newton, FP32 bulk with FP32 refinement and "
                    "one FP64 judging step; iterations are FP64 Newton iterations (network attempt and restart "
                    "together); the previous-stage Z is the plain method's guess; network: per-cell choice "
-                   "between the network start and the previous Z (tensor-core pass over the flagged tiles, "
+                   "between the network start and the previous Z (tensor-core pass over the listed cells, "
                    "then the c2p kernel); network_inside_c2p: the same choice with the network fused into the "
                    "c2p kernel; restart_*: one inversion of the state without its Newton memory; torus_fp64: "
                    "a held-out 96x48x48 torus (spin 0.5, beta 30), 6 steps")

@@ -328,14 +328,17 @@ int echo_mlp_load(echo_ctx *ctx, const float *dev_state);
  * the start is chosen per cell: every inversion records how far each cell's
  * Z moved (an estimate of the error of the previous-stage Z as the next
  * start) and lists the cells that moved at least as much as the network's
- * calibrated typical error (echo_mlp_calibrate); the next inversion
+ * calibrated typical error (echo_mlp_calibrate) -- with the FP32 refinement
+ * (+4) only those that also moved by about 1/8 or more, since the refinement
+ * brings any closer start to the same single FP64 iteration; the next inversion
  * evaluates the network for the listed cells only (packed into tiles of
  * 128), and a listed cell starts from it only where its predicted log10
  * error (third output) beats the previous Z's; all other cells start from
  * the previous-stage Z (not counted as a fallback).  After echo_set_prims,
  * or echo_set_state with Z, no cell is listed; after echo_set_state without
  * Z (a cold start) every cell is.  Inversions in the other modes keep no
- * record: the first network-mode inversion after them lists no cell.
+ * record: the first network-mode inversion after them lists no cell; so
+ * does one whose refinement flag (+4) differs from the previous one's.
  * The network's hidden layers run on the tensor cores (as
  * echo_mlp_forward_tc) in a pass before the c2p kernel; adding 8 to a network mode evaluates it in FP32 on the
  * CUDA cores inside the c2p kernel (modes 9, 13), adding 16 on the tensor

@@ -192,20 +192,30 @@ int reset_start_memory(echo_ctx *c, bool exact, cudaStream_t s)
         launch_list_all<float>(c->geo, c->af, s);
     }
     c->ze_valid = true;
+    c->ze_refine = -1;
     return cuda_check(c, "start memory");
 }
 
 // Only the network modes' inversions keep the codes up to date: before one
 // of them, codes left stale by plain-mode inversions are reset to "previous
 // Z exact" (the plain method's start everywhere until the next inversion
-// has measured the cells again).
+// has measured the cells again).  So are the codes of a list made under the
+// other gate (with or without the FP32 refinement): a cell consults the
+// network's start only if the last inversion listed it.
 int prepare_start(echo_ctx *c, int mode, cudaStream_t s)
 {
     if ((mode & 3) != 1) {
         c->ze_valid = false;
         return ECHO_OK;
     }
-    return c->ze_valid ? ECHO_OK : reset_start_memory(c, true, s);
+    const int rf = (mode & 4) ? 1 : 0;
+    if (c->ze_valid && (c->ze_refine < 0 || c->ze_refine == rf)) {
+        c->ze_refine = rf;
+        return ECHO_OK;
+    }
+    const int rc = reset_start_memory(c, true, s);
+    c->ze_refine = rf;
+    return rc;
 }
 
 template <int MK, typename R>

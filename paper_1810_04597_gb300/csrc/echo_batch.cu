@@ -488,7 +488,7 @@ int echo_batch_step(echo_batch *b, double dt)
     // capture: run-major inverts with each run's own guess mode, the other
     // schedules with the batch's (the network for every run, or none)
     for (echo_ctx *c : b->runs) {
-        const int mode = b->phased == 2 ? c->c2p_guess : (b->mlp ? 1 : 0);
+        const int mode = b->phased == 2 ? c->c2p_guess : b->guess;
         const int rc = echo_internal_prepare_start(c, mode, b->stream);
         if (rc)
             return bfail(b, rc, std::string("start codes: ") + c->err);

@@ -34,7 +34,8 @@ struct echo_ctx {
     std::string err;
     int c2p_guess = 0;        // 0 previous-stage Z, 1 c2p-guess network
     bool mlp_loaded = false;
-    bool ze_valid = false;    // the per-cell start codes and tile flags describe the current Newton memory
+    bool ze_valid = false;    // the per-cell start codes and the list describe the current Newton memory
+    int ze_refine = -1;       // the FP32-refinement flag (mode +4) of the gate that made the list; -1 either
     // per-kernel timing (echo_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev;      // pool, pairs (start, end)

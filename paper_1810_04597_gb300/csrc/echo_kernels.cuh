@@ -226,7 +226,7 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
     bool want_net = false;
     int gate = 0;
     if constexpr (MLPK != 0)
-        gate = ze_gate(A.mlp[MLP_OGATE]);
+        gate = ze_gate_mode(A.mlp[MLP_OGATE], guess_mode);
     if (live) {
         const int id = c.id;
         const int i = c.i;
@@ -345,7 +345,7 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             // this cell may gain from the network there
             const unsigned char code = ze_code(Z, zold);
             A.ze[id] = code;
-            want_net = (int)code <= ze_gate(__ldg(&A.mlp[MLP_OGATE]));
+            want_net = (int)code <= ze_gate_mode(__ldg(&A.mlp[MLP_OGATE]), guess_mode);
         }
         if (want_rate) {
             if constexpr (sizeof(R) == 4) {
@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(128, 6) k_c2p_tc(Geom g, Phys ph, Arrays<R> A,
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     TcMlp tm;
     tc_setup(tm, tc_smem, A.mlp);
-    const int gate = ze_gate(A.mlp[MLP_OGATE]);
+    const int gate = ze_gate_mode(A.mlp[MLP_OGATE], guess_mode);
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long t = tile * 128 + threadIdx.x;
         C2PCell c;

@@ -166,6 +166,19 @@ __device__ __forceinline__ int ze_gate(float gate_log10)
     return g <= 0.0f ? 0 : (g >= 254.0f ? 254 : (int)g);
 }
 
+// With the FP32 refinement (guess mode +4) every start that the four FP32
+// Newton steps bring to FP32 accuracy costs the same one FP64 iteration, so
+// only a previous Z that moved by about 1/8 or more (q <= 2) may gain from
+// the network: from a relative error e the refinement leaves about e^16,
+// which is below FP32 rounding for e < 1/4.
+constexpr int ZE_REFINE_GATE = 2;
+
+__device__ __forceinline__ int ze_gate_mode(float gate_log10, int guess_mode)
+{
+    const int g = ze_gate(gate_log10);
+    return (guess_mode & 4) && g > ZE_REFINE_GATE ? ZE_REFINE_GATE : g;
+}
+
 __device__ __forceinline__ bool net_beats(float o2, unsigned char q)
 {
     return q != ZE_EXACT && -o2 * 3.32192809f > (float)q + 0.5f;

@@ -220,6 +220,50 @@ def test_gain_over_guesses_without_network(trained, torch):
     assert np.max(np.abs(fin["network"] - fin["previous"])) <= 1e-11 * scale
 
 
+def test_refined_gate_lists_only_large_moves(trained, torch):
+    """With the FP32 refinement (mode 5) a cell is listed only where its Z
+    moved by about 1/8 or more, since the refinement brings any closer start
+    to the same single FP64 iteration: in a smooth FP32 run far fewer cells
+    start from the network than without the refinement (mode 1, the plain
+    gate), the FP64 iterations stay at those of the previous-Z start, and the
+    state equals the previous-Z run's to FP32 rounding (relative L1).  Changing the
+    refinement flag empties the list: the first inversion after the change
+    starts no cell from the network."""
+    from paper_1810_04597_gb300.echo import Solver
+    state, _, _ = trained
+    prob = inputs.sweep_box(48, seed=93)
+    res, fin = {}, {}
+    for mode in (4, 5, 1):
+        s = Solver(prob, precision=32)
+        s.set_prims()
+        s.mlp_load(state)
+        s.set_c2p_guess(mode)
+        for _ in range(2):
+            s.step()
+        c0 = s.counters()
+        for _ in range(3):
+            s.step()
+        c1 = s.counters()
+        calls = c1["c2p_calls"] - c0["c2p_calls"]
+        res[mode] = ((c1["c2p_iters"] - c0["c2p_iters"]) / calls, (c1["mlp_used"] - c0["mlp_used"]) / calls,
+                     c1["mlp_fallback"] - c0["mlp_fallback"])
+        fin[mode] = s.get_state()
+        if mode == 5:
+            # the refinement flag changes: the list made under the refined gate is dropped
+            c2 = s.counters()
+            s.c2p(1)
+            c3 = s.counters()
+            res["switch"] = c3["mlp_used"] - c2["mlp_used"]
+    print("FP32 (mean FP64 its, network starts per cell, fallbacks): previous Z", res[4], "refined gate", res[5],
+          "plain gate", res[1], "starts after the switch", res["switch"])
+    assert res[1][1] > 0.0, res
+    assert res[5][1] <= 0.2 * res[1][1], res
+    assert res[5][0] <= res[4][0] + 0.005, res
+    assert res[5][2] == 0 and res["switch"] == 0, res
+    # Newton decides: the same state to FP32 rounding (relative L1)
+    assert np.sum(np.abs(fin[5] - fin[4])) <= 1e-6 * np.sum(np.abs(fin[4]))
+
+
 def _bf16(a):
     """Round to the nearest BF16 (ties to even), returned as float64."""
     b = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
