@@ -734,14 +734,17 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     }
     compact_limit<PRE, T>(pend, id, lsm, [&](int ido, int m, int side, T uor) -> T {
         const R *__restrict__ a = A.P[qs[m]];
-        T q[6];
+        // the item's own five-point stencil, oriented towards its face (the
+        // right state's is the left one's mirror): one limiter evaluation
+        const int s0 = side ? 2 * sd : -3 * sd, ds = side ? -sd : sd;
+        T q[5];
 #pragma unroll
-        for (int s = 0; s < 6; ++s)
-            q[s] = a[ido + (s - 3) * sd];
+        for (int s = 0; s < 5; ++s)
+            q[s] = a[ido + s0 + s * ds];
         if constexpr (PRE)
-            return side ? mp5_limit_u(q[5], q[4], q[3], q[2], q[1], uor) : mp5_limit_u(q[0], q[1], q[2], q[3], q[4], uor);
+            return mp5_limit_u(q[0], q[1], q[2], q[3], q[4], uor);
         else
-            return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1], order) : mp5_limit(q[0], q[1], q[2], q[3], q[4], order);
+            return mp5_limit(q[0], q[1], q[2], q[3], q[4], order);
     });
     if (!live)
         return;
@@ -952,14 +955,15 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
         const R *p;
         int st;
         emf_pick(S, m, p, st);
-        T q[6];
+        const int s0 = side ? 2 * st : -3 * st, ds = side ? -st : st;
+        T q[5];
 #pragma unroll
-        for (int s = 0; s < 6; ++s)
-            q[s] = p[ido + (s - 3) * st];
+        for (int s = 0; s < 5; ++s)
+            q[s] = p[ido + s0 + s * ds];
         if constexpr (PRE)
-            return side ? mp5_limit_u(q[5], q[4], q[3], q[2], q[1], uor) : mp5_limit_u(q[0], q[1], q[2], q[3], q[4], uor);
+            return mp5_limit_u(q[0], q[1], q[2], q[3], q[4], uor);
         else
-            return side ? mp5_limit(q[5], q[4], q[3], q[2], q[1], order) : mp5_limit(q[0], q[1], q[2], q[3], q[4], order);
+            return mp5_limit(q[0], q[1], q[2], q[3], q[4], order);
     });
     if (!live)
         return;
