@@ -86,21 +86,23 @@ def algorithmic_flops(counts, kernel, newton_iters):
 # launch.  c2p depends on the Newton iteration count (2.74 per call there);
 # faces_y/z run the code of faces_x with other strides.
 FLOPS64 = {
-    64: {"faces_x": 520.2, "faces_y": 520.2, "faces_z": 520.2,
-         "emf_x": 266.4, "emf_y": 266.4, "emf_z": 266.4,
-         "c2p": 403.5, "update": 79.0},
+    64: {"faces_x": 500.3, "faces_y": 500.3, "faces_z": 500.3,
+         "emf_x": 248.4, "emf_y": 248.4, "emf_z": 248.4,
+         "c2p": 386.5, "update": 79.0},
     # FP32-bulk path: only c2p computes in FP64 (previous-stage Z refined in
     # FP32, then 1.01 FP64 Newton iterations per call)
-    32: {"c2p": 134.0},
+    32: {"c2p": 131.0},
 }
-# FP64 arithmetic instructions (DFMA + DADD + DMUL thread instructions) per
-# unit from the same captures: each takes one FP64-pipe slot, so these over
-# the pipe's 2 slots per SM and clock give the pipe-time view beside the flop
-# roofline (DADD and DMUL are one flop for a full slot).
+# FP64-pipe thread instructions (DFMA + DADD + DMUL; ncu counts 64-bit
+# integer adds, compares and masks with the DADDs, and the kernels keep
+# those on 32-bit words) per unit from the same captures: each takes one
+# lane slot of the FP64 pipe, so these over the pipe's nominal 2 lanes per
+# SM and clock give the pipe-time view beside the flop roofline (DADD and
+# DMUL are one flop for a full slot).
 FP64_INSTR = {
-    64: {"faces_x": 371.6, "faces_y": 371.6, "faces_z": 371.6, "emf_x": 197.7, "emf_y": 197.7, "emf_z": 197.7,
-         "c2p": 289.4, "update": 53.0},
-    32: {"c2p": 97.0},
+    64: {"faces_x": 351.6, "faces_y": 351.6, "faces_z": 351.6, "emf_x": 179.7, "emf_y": 179.7, "emf_z": 179.7,
+         "c2p": 272.4, "update": 53.0},
+    32: {"c2p": 93.0},
 }
 # Nominal FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2
 # DFMA lanes per SM and clock x 2 flop x 2.07 GHz (the 1.25 TFLOP/s figure);
@@ -132,14 +134,18 @@ def measure_fp64_peak(dev, repeats=3, iters=20000):
     except Exception as exc:   # keep the bench line; say which peak it is
         return FP64_PEAK_TFLOPS, f"nominal (probe failed: {exc})"
 # DRAM bytes per face of faces_x (dram__bytes_read.sum + dram__bytes_write.sum
-# of the same 128^3 ncu launch: 338,767,872 B over 2,316,324 faces); scaled to a
+# of the same 128^3 ncu launch: 336,666,880 B over 2,316,324 faces); scaled to a
 # launch by the faces it processes.
-TRAFFIC_PER_FACE64 = 338767872 / 2316324
+TRAFFIC_PER_FACE64 = 336666880 / 2316324
 # FP64 pipe activity in those captures
 # (sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active).
-FP64_PIPE_BUSY = {64: {"faces_x": 0.864, "faces_y": 0.864, "faces_z": 0.864, "emf_x": 0.854, "emf_y": 0.854,
-                       "emf_z": 0.854, "c2p": 0.863, "update": 0.834},
-                  32: {"c2p": 0.852}}
+FP64_PIPE_BUSY = {64: {"faces_x": 0.878, "faces_y": 0.878, "faces_z": 0.878, "emf_x": 0.870, "emf_y": 0.870,
+                       "emf_z": 0.870, "c2p": 0.869, "update": 0.828},
+                  32: {"c2p": 0.858}}
+# The FP64 pipe's nominal lane rate (thread instructions per second): 152 SMs
+# x 2 lanes per SM and clock x 2.07 GHz.  The FMA probe reaches ~84 % of it
+# (three 64-bit operands per FMA); DADD/DMUL-rich kernels can issue faster.
+FP64_PIPE_LANES_PER_S = 152 * 2 * 2.07e9
 
 
 def kernel_units(name, n):
@@ -505,7 +511,8 @@ def run_ours(args, world, rank, local, dist):
                 "units_per_launch": units,
                 "kernel_flops_per_unit_ncu": fl[dom], "kernel_flops_frac": kernel_achieved / fp64_peak,
                 "fp64_pipe_busy_ncu": FP64_PIPE_BUSY[args.precision].get(dom),
-                "fp64_instr_frac": units * FP64_INSTR[args.precision][dom] / avg_s / (fp64_peak * 1e12 / 2),
+                "fp64_instr_frac": units * FP64_INSTR[args.precision][dom] / avg_s / FP64_PIPE_LANES_PER_S,
+                "fp64_instr_frac_of": "the FP64 pipe's nominal lane rate (152 SMs x 2 per clock x 2.07 GHz)",
                 "traffic_note": "dram bytes per face of a 128^3 ncu capture x faces per launch"
                 if traffic is not None else "no ncu traffic figure for this kernel and precision",
                 "avg_launch_ms": avg_s * 1e3, "hbm_context": hbm_ctx, "time_share": share}
@@ -769,7 +776,8 @@ def fp32_c2p_roofline(prof, ms, zones, newton_iters, fp64_peak, fp64_src):
             "kernel_flops_per_unit_ncu": FLOPS64[32]["c2p"],
             "kernel_flops_frac": zones * FLOPS64[32]["c2p"] / avg_s / 1e12 / fp64_peak,
             "fp64_pipe_busy_ncu": FP64_PIPE_BUSY[32]["c2p"], "avg_launch_ms": avg_s * 1e3,
-            "fp64_instr_frac": zones * FP64_INSTR[32]["c2p"] / avg_s / (fp64_peak * 1e12 / 2),
+            "fp64_instr_frac": zones * FP64_INSTR[32]["c2p"] / avg_s / FP64_PIPE_LANES_PER_S,
+            "fp64_instr_frac_of": "the FP64 pipe's nominal lane rate (152 SMs x 2 per clock x 2.07 GHz)",
             "time_share": {k: round(v[0] / ms, 4) for k, v in prof.items() if v[1] > 0}}
 
 

@@ -216,7 +216,11 @@ struct Arrays {
 // the IEEE-754 bit patterns instead (integer pipe).  For non-NaN values
 // the map key(x) = bits ^ ((bits >> 63) & 0x7ff..f) is strictly monotonic
 // in x (IEEE 754 total order of bit patterns), so every result below equals
-// the floating-point comparison it replaces.
+// the floating-point comparison it replaces.  The FP64 forms work on the
+// two 32-bit halves of the pattern (high word signed, low word unsigned,
+// compared in that order): 64-bit integer compares, adds and masks issue on
+// the FP64 pipe as well (ncu counts them with the DADDs), 32-bit ones on
+// the integer ALU.
 
 __device__ __forceinline__ long long bits_of(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ int bits_of(float x) { return __float_as_int(x); }
@@ -231,17 +235,36 @@ __device__ __forceinline__ int okey(float x)
     const int b = __float_as_int(x);
     return b ^ ((b >> 31) & 0x7fffffff);
 }
+// key(x) as its two halves: (hi, lo), hi signed, lo unsigned
+struct Key2 {
+    int h;
+    unsigned l;
+};
+__device__ __forceinline__ Key2 okey2(double x)
+{
+    const int h = __double2hiint(x);
+    const unsigned l = (unsigned)__double2loint(x);
+    const int s = h >> 31;
+    return Key2{h ^ (s & 0x7fffffff), l ^ (unsigned)s};
+}
+__device__ __forceinline__ bool k2_lt(Key2 a, Key2 b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+__device__ __forceinline__ bool k2_le(Key2 a, Key2 b) { return a.h < b.h || (a.h == b.h && a.l <= b.l); }
 // x > 0 and x < 0 (strict; +0 and -0 are neither)
-__device__ __forceinline__ bool is_pos(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool is_pos(double x)
+{
+    const int h = __double2hiint(x);
+    return h > 0 || (h == 0 && __double2loint(x) != 0);
+}
 __device__ __forceinline__ bool is_pos(float x) { return __float_as_int(x) > 0; }
 __device__ __forceinline__ bool is_neg(double x)
 {
-    return (__double_as_longlong(x) ^ (long long)0x8000000000000000ULL) > 0;
+    const int h = __double2hiint(x) ^ (int)0x80000000u;
+    return h > 0 || (h == 0 && __double2loint(x) != 0);
 }
 __device__ __forceinline__ bool is_neg(float x) { return (__float_as_int(x) ^ (int)0x80000000u) > 0; }
 __device__ __forceinline__ double iabs(double x)
 {
-    return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+    return __hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x));
 }
 __device__ __forceinline__ float iabs(float x) { return __int_as_float(__float_as_int(x) & 0x7fffffff); }
 template <typename T>
@@ -264,10 +287,17 @@ template <>
 __device__ __forceinline__ bool ilt<float>(float a, float b) { return a < b; }
 template <>
 __device__ __forceinline__ bool ile<float>(float a, float b) { return a <= b; }
+template <>
+__device__ __forceinline__ double imin<double>(double a, double b) { return k2_lt(okey2(a), okey2(b)) ? a : b; }
+template <>
+__device__ __forceinline__ double imax<double>(double a, double b) { return k2_lt(okey2(a), okey2(b)) ? b : a; }
+template <>
+__device__ __forceinline__ bool ilt<double>(double a, double b) { return k2_lt(okey2(a), okey2(b)); }
+template <>
+__device__ __forceinline__ bool ile<double>(double a, double b) { return k2_le(okey2(a), okey2(b)); }
 __device__ __forceinline__ double with_sign_of(double mag, double s)
 {
-    return __longlong_as_double(__double_as_longlong(mag)
-                                | (__double_as_longlong(s) & (long long)0x8000000000000000ULL));
+    return __hiloint2double(__double2hiint(mag) | (__double2hiint(s) & (int)0x80000000u), __double2loint(mag));
 }
 __device__ __forceinline__ float with_sign_of(float mag, float s)
 {
@@ -320,7 +350,10 @@ __device__ __forceinline__ float fast_recip<float>(float x) { return __fdividef(
 // binary64 / binary32 encodings directly (sign, re-biased exponent, shifted
 // mantissa; round to nearest even when narrowing) and hand only zero-exponent
 // (zero / subnormal), overflowing and non-finite values to the hardware
-// conversion, so every result equals the hardware cast.
+// conversion, so every result equals the hardware cast.  They work on the
+// two 32-bit words of the binary64 encoding (64-bit integer operations
+// would take the FP64 pipe too): the high word holds the sign, the exponent
+// and the top 20 mantissa bits, the low word the other 32.
 
 __device__ __forceinline__ double f2d(float x)
 {
@@ -328,29 +361,29 @@ __device__ __forceinline__ double f2d(float x)
     const unsigned e = (b >> 23) & 0xffu;
     if (e == 0u || e == 0xffu) {
         if ((b & 0x7fffffffu) == 0u)
-            return __longlong_as_double((long long)((unsigned long long)(b & 0x80000000u) << 32));
+            return __hiloint2double((int)(b & 0x80000000u), 0);
         return (double)x;   // subnormal, inf, nan
     }
-    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32)
-                                 | ((unsigned long long)(e + (1023u - 127u)) << 52)
-                                 | ((unsigned long long)(b & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)d);
+    // the 23 mantissa bits, shifted up by 29: the top 20 end the high word,
+    // the low 3 start the low word
+    const unsigned hi = (b & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
 }
 
 __device__ __forceinline__ float d2f(double x)
 {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
     if (e >= 1 && e <= 254) {
-        const unsigned long long m = b & 0xfffffffffffffULL;
-        unsigned r = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)e << 23) | (unsigned)(m >> 29);
-        const unsigned long long rem = m & 0x1fffffffULL;
-        const unsigned long long half = 0x10000000ULL;
+        // the top 23 of the 52 mantissa bits: 20 from the high word, 3 from the low
+        unsigned r = (hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const unsigned rem = lo & 0x1fffffffu;   // the 29 bits rounded away
+        const unsigned half = 0x10000000u;
         r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;   // carry may raise the exponent (to inf)
         return __uint_as_float(r);
     }
-    if ((b & 0x7fffffffffffffffULL) == 0ULL)
-        return __uint_as_float((unsigned)(b >> 32) & 0x80000000u);
+    if (((hi & 0x7fffffffu) | lo) == 0u)
+        return __uint_as_float(hi & 0x80000000u);
     return (float)x;   // subnormal result, overflow, inf, nan
 }
 
@@ -512,14 +545,12 @@ __device__ __forceinline__ T mp5_uor(T um2, T um1, T u0, T up1, T up2, int order
 template <int E>
 __device__ __forceinline__ double scale2(double x)
 {
-    const long long b = __double_as_longlong(x);
-    const bool tiny = (b & 0x7ff0000000000000LL) == 0;
-    long long r;
-    if constexpr (E >= 0)
-        r = b + ((long long)E << 52);
-    else
-        r = b - ((long long)(-E) << 52);
-    return __longlong_as_double(tiny ? (b & (long long)0x8000000000000000ULL) : r);
+    // on the high word only: the exponent field lies in it
+    const int h = __double2hiint(x);
+    const int l = __double2loint(x);
+    const bool tiny = (h & 0x7ff00000) == 0;
+    const int r = h + E * (1 << 20);
+    return tiny ? __hiloint2double(h & (int)0x80000000u, 0) : __hiloint2double(r, l);
 }
 
 // alpha x for the MP5 test (alpha = 4 = 2^2): the product feeds a min/max,

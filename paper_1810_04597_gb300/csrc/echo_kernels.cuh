@@ -35,7 +35,9 @@ __device__ __forceinline__ T warp_max(T v)
     return v;
 }
 
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+// Warp sum of small per-lane counts (32-bit: a 64-bit add issues on the
+// FP64 pipe on GB300; the totals here stay far below 2^32).
+__device__ __forceinline__ unsigned warp_sum_u32(unsigned v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -222,7 +224,7 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
     C2PCell c;
     const bool live = c2p_cell<MK, R>(g, A, t, c);
     double rate = 0.0;
-    unsigned long long its = 0, calls = 0, fails = 0, floors = 0, mfb = 0, used = 0;
+    unsigned its = 0, calls = 0, fails = 0, floors = 0, mfb = 0, used = 0;
     bool want_net = false;
     int gate = 0;
     if constexpr (MLPK != 0)
@@ -374,39 +376,39 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
     {
         const unsigned lmask = __ballot_sync(0xffffffffu, live);
         if (live) {
-            const int b = its < (unsigned long long)(ECHO_C2P_HIST - 1) ? (int)its : ECHO_C2P_HIST - 1;
+            const int b = its < (unsigned)(ECHO_C2P_HIST - 1) ? (int)its : ECHO_C2P_HIST - 1;
             const unsigned same = __match_any_sync(lmask, b);
             if ((int)(threadIdx.x & 31) == __ffs(same) - 1)
                 atomicAdd(&A.scal->c2p_hist[b], (unsigned long long)__popc(same));
         }
     }
     // warp-aggregated counters
-    its = warp_sum_u64(its);
-    calls = warp_sum_u64(calls);
-    fails = warp_sum_u64(fails);
-    floors = warp_sum_u64(floors);
+    its = warp_sum_u32(its);
+    calls = warp_sum_u32(calls);
+    fails = warp_sum_u32(fails);
+    floors = warp_sum_u32(floors);
     if constexpr (MLPK != 0) {
-        mfb = warp_sum_u64(mfb);
-        used = warp_sum_u64(used);
+        mfb = warp_sum_u32(mfb);
+        used = warp_sum_u32(used);
     }
     if (want_rate)
         rate = warp_max(rate);
     if ((threadIdx.x & 31) == 0) {
         if (calls) {
-            atomicAdd(&A.scal->c2p_iters, its);
-            atomicAdd(&A.scal->c2p_calls, calls);
+            atomicAdd(&A.scal->c2p_iters, (unsigned long long)its);
+            atomicAdd(&A.scal->c2p_calls, (unsigned long long)calls);
         }
         if (fails) {
-            atomicAdd(&A.scal->c2p_fail, fails);
-            atomicAdd(&A.scal->fail_since_check, fails);
+            atomicAdd(&A.scal->c2p_fail, (unsigned long long)fails);
+            atomicAdd(&A.scal->fail_since_check, (unsigned long long)fails);
         }
         if (floors)
-            atomicAdd(&A.scal->floor_hits, floors);
+            atomicAdd(&A.scal->floor_hits, (unsigned long long)floors);
         if constexpr (MLPK != 0) {
             if (mfb)
-                atomicAdd(&A.scal->mlp_fallback, mfb);
+                atomicAdd(&A.scal->mlp_fallback, (unsigned long long)mfb);
             if (used)
-                atomicAdd(&A.scal->mlp_used, used);
+                atomicAdd(&A.scal->mlp_used, (unsigned long long)used);
         }
         if (want_rate && rate > 0.0)
             atomicMax(&A.scal->rate_bits, (unsigned long long)__double_as_longlong(rate));

@@ -147,11 +147,13 @@ constexpr unsigned char ZE_EXACT = 255;
 
 __device__ __forceinline__ unsigned char ze_code(double Z, double zprev)
 {
-    const long long bd = __double_as_longlong(Z - zprev) & 0x7fffffffffffffffLL;
-    if (bd == 0)
+    // binary exponents from the high words (32-bit integer work)
+    const double dz = Z - zprev;
+    const unsigned dh = (unsigned)__double2hiint(dz) & 0x7fffffffu;
+    if ((dh | (unsigned)__double2loint(dz)) == 0u)
         return ZE_EXACT;
-    const int ez = (int)((__double_as_longlong(Z) >> 52) & 0x7ff);
-    const int ed = (int)(bd >> 52);
+    const int ez = (int)(((unsigned)__double2hiint(Z) >> 20) & 0x7ffu);
+    const int ed = (int)(dh >> 20);
     const int q = ez - ed;
     return (unsigned char)(q < 0 ? 0 : (q > 254 ? 254 : q));
 }

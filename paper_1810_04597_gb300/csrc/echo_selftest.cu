@@ -112,13 +112,15 @@ __global__ void k_check_scale2(long long n, unsigned long long seed, unsigned lo
 // chains stay finite.
 constexpr int kDfmaChains = 8;
 
-__global__ void __launch_bounds__(256) k_dfma_throughput(long long iters, double a, double b, double *out)
+// The loop counter is 32-bit (64-bit integer adds and compares can take
+// FP64-pipe slots on GB300).
+__global__ void __launch_bounds__(256) k_dfma_throughput(int iters, double a, double b, double *out)
 {
     double c[kDfmaChains];
 #pragma unroll
     for (int q = 0; q < kDfmaChains; ++q)
         c[q] = (double)(threadIdx.x + q);
-    for (long long it = 0; it < iters; ++it) {
+    for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int q = 0; q < kDfmaChains; ++q)
             c[q] = fma(c[q], b, a);
@@ -146,10 +148,10 @@ extern "C" int echo_selftest_dfma_blocks(void)
 extern "C" int echo_selftest_dfma(long long iters, double *dev_out, double *flops, void *stream)
 {
     const int blocks = echo_selftest_dfma_blocks();
-    if (iters < 1 || !dev_out || blocks < 1)
+    if (iters < 1 || iters > 0x7fffffffLL || !dev_out || blocks < 1)
         return ECHO_EINVAL;
     echo::k_dfma_throughput<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        iters, 1e-3, 0.999999, dev_out);
+        (int)iters, 1e-3, 0.999999, dev_out);
     if (flops)
         *flops = 2.0 * echo::kDfmaChains * (double)iters * 256.0 * (double)blocks;
     return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
