@@ -1230,8 +1230,11 @@ __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const
     }
 }
 
+// Flat metric: 8 blocks of 256 per SM (32 registers, full occupancy; the
+// FP32 form streams and needs the warps in flight); Kerr-Schild (sources):
+// 3 blocks, the occupancy its registers give anyway.
 template <int MK, typename R>
-__global__ void __launch_bounds__(256) k_update(Geom g, Phys ph, Arrays<R> A, int stage, double *Lout)
+__global__ void __launch_bounds__(256, MK == 0 ? 8 : 3) k_update(Geom g, Phys ph, Arrays<R> A, int stage, double *Lout)
 {
     update_body<MK, R>(g, ph, A, stage, Lout, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
