@@ -611,24 +611,31 @@ __global__ void __launch_bounds__(128, 6) k_c2p_tc(Geom g, Phys ph, Arrays<R> A,
 // compaction
 //
 // Each lane holds up to 16 reconstructions (slot = 2 m + side); `pend` marks
-// those whose unlimited MP5 value was rejected.  The warp packs all pending
-// items of its 32 lanes into a shared list (warp prefix sum of the counts),
-// processes the list 32 items per round -- lane L takes item r*32 + L, loads
-// the owning lane's stencil itself and evaluates the limited value -- and
-// returns the results through shared memory.  Rounds per warp drop from the
-// max over lanes of their pending count to ceil(total / 32).
+// those whose unlimited MP5 value was rejected.  The pending items are packed
+// into a shared list (prefix sum of the counts: over the warp in FP32, over
+// the block in FP64), processed 32 items per warp round -- a lane takes an
+// item, loads the owning thread's stencil itself and evaluates the limited
+// value -- and the results return through shared memory.  Rounds drop from
+// the max over lanes of their pending count to ceil(total / 32).
 constexpr int kWarpsPerBlock = 4;   // kernels using this run 128 threads
 
 template <typename T>
 struct LimScratch {
     T res[kWarpsPerBlock][32][16];
-    unsigned short desc[kWarpsPerBlock][32 * 16];
+    unsigned short desc[kWarpsPerBlock * 32 * 16];
+    int ids[kWarpsPerBlock * 32];   // FP64: each thread's unit, for items taken by another warp
+    int wtot[kWarpsPerBlock];
 };
 
 // limited(id_of_owner, m, side, uor) -> T.  With PRE the owners have stored
 // every unlimited value in their res slots before the call (uor passes the
 // rejected item's one, so the limiter need not recompute it; FP64, where that
 // saves five FP64-pipe instructions per item), else uor is 0.
+//
+// FP64 (PRE) packs the items of the whole block (128 threads): the last,
+// partly filled round then occurs once per block rather than once per warp,
+// which on the FP64 pipe is worth the block's three barriers.  Every thread
+// of the block must call it then; the callers' units are block-uniform.
 template <bool PRE, typename T, typename F>
 __device__ __forceinline__ void compact_limit(unsigned pend, int id, LimScratch<T> &sm, F limited)
 {
@@ -642,32 +649,70 @@ __device__ __forceinline__ void compact_limit(unsigned pend, int id, LimScratch<
         if (lane >= o)
             excl += v;
     }
-    const int total = __shfl_sync(0xffffffffu, excl, 31);
-    if (total == 0)
-        return;
+    const int wtotal = __shfl_sync(0xffffffffu, excl, 31);
     excl -= cnt;
-    {
-        unsigned m = pend;
-        int k = excl;
-        while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            sm.desc[w][k++] = (unsigned short)((lane << 4) | b);
+    if constexpr (PRE) {
+        sm.ids[threadIdx.x] = id;
+        if (lane == 0)
+            sm.wtot[w] = wtotal;
+        __syncthreads();
+        int wbase = 0, total = 0;
+#pragma unroll
+        for (int q = 0; q < kWarpsPerBlock; ++q) {
+            const int v = sm.wtot[q];
+            wbase += q < w ? v : 0;
+            total += v;
         }
-    }
-    __syncwarp();
-    for (int base = 0; base < total; base += 32) {
-        const int item = base + lane;
-        const bool act = item < total;
-        const unsigned d = act ? sm.desc[w][item] : (unsigned)(lane << 4);
-        const int o = (int)(d >> 4);
-        const int ido = __shfl_sync(0xffffffffu, id, o);
-        if (act) {
-            const int b = (int)(d & 15);
-            sm.res[w][o][b] = limited(ido, b >> 1, b & 1, PRE ? sm.res[w][o][b] : T(0));
+        if (total == 0)
+            return;   // block-uniform
+        {
+            unsigned m = pend;
+            int k = wbase + excl;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                sm.desc[k++] = (unsigned short)((threadIdx.x << 4) | b);
+            }
         }
+        __syncthreads();
+        for (int base = w * 32; base < total; base += 32 * kWarpsPerBlock) {
+            const int item = base + lane;
+            if (item < total) {
+                const unsigned d = sm.desc[item];
+                const int o = (int)(d >> 4), b = (int)(d & 15);
+                T &slot = sm.res[o >> 5][o & 31][b];
+                slot = limited(sm.ids[o], b >> 1, b & 1, slot);
+            }
+        }
+        __syncthreads();
+    } else {
+        const int total = wtotal;
+        if (total == 0)
+            return;
+        unsigned short *desc = sm.desc + w * (32 * 16);
+        {
+            unsigned m = pend;
+            int k = excl;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                desc[k++] = (unsigned short)((lane << 4) | b);
+            }
+        }
+        __syncwarp();
+        for (int base = 0; base < total; base += 32) {
+            const int item = base + lane;
+            const bool act = item < total;
+            const unsigned d = act ? desc[item] : (unsigned)(lane << 4);
+            const int o = (int)(d >> 4);
+            const int ido = __shfl_sync(0xffffffffu, id, o);
+            if (act) {
+                const int b = (int)(d & 15);
+                sm.res[w][o][b] = limited(ido, b >> 1, b & 1, T(0));
+            }
+        }
+        __syncwarp();
     }
-    __syncwarp();
 }
 
 // ------------------------------------------------------------------ faces
