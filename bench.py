@@ -134,13 +134,13 @@ def measure_fp64_peak(dev, repeats=3, iters=20000):
     except Exception as exc:   # keep the bench line; say which peak it is
         return FP64_PEAK_TFLOPS, f"nominal (probe failed: {exc})"
 # DRAM bytes per face of faces_x (dram__bytes_read.sum + dram__bytes_write.sum
-# of the same 128^3 ncu launch: 336,666,880 B over 2,316,324 faces); scaled to a
+# of the same 128^3 ncu launch: 336,267,776 B over 2,316,324 faces); scaled to a
 # launch by the faces it processes.
-TRAFFIC_PER_FACE64 = 336666880 / 2316324
+TRAFFIC_PER_FACE64 = 336267776 / 2316324
 # FP64 pipe activity in those captures
 # (sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active).
-FP64_PIPE_BUSY = {64: {"faces_x": 0.878, "faces_y": 0.878, "faces_z": 0.878, "emf_x": 0.870, "emf_y": 0.870,
-                       "emf_z": 0.870, "c2p": 0.869, "update": 0.828},
+FP64_PIPE_BUSY = {64: {"faces_x": 0.879, "faces_y": 0.879, "faces_z": 0.879, "emf_x": 0.872, "emf_y": 0.872,
+                       "emf_z": 0.872, "c2p": 0.869, "update": 0.827},
                   32: {"c2p": 0.858}}
 # The FP64 pipe's nominal lane rate (thread instructions per second): 152 SMs
 # x 2 lanes per SM and clock x 2.07 GHz.  The FMA probe reaches ~84 % of it
