@@ -424,6 +424,15 @@ int echo_selftest_recip(long long n, unsigned long long seed, unsigned long long
  * exponents -1000..1000, and signed zeros): adds the number of bit-pattern
  * mismatches to *dev_mismatch (device, caller-zeroed). */
 int echo_selftest_scale2(long long n, unsigned long long seed, unsigned long long *dev_mismatch, void *cuda_stream);
+/* Method: the MP5 monotonicity test of Suresh & Huynh (1997), a b <= eps.
+ * Self-check of the FP64 kernels' form of that test, decided from the signs
+ * and binary exponents of a and b and multiplied out only near eps, against
+ * the product test itself on n hashed pairs (exponent sums concentrated
+ * around eps, both signs, zeros, subnormals, huge and infinite operands):
+ * adds the number of differing decisions to *dev_mismatch (device,
+ * caller-zeroed). */
+int echo_selftest_mp5_accept(long long n, unsigned long long seed, unsigned long long *dev_mismatch,
+                             void *cuda_stream);
 
 /* Method: a register-only throughput probe (no counterpart in the paper).
  * FP64 fused multiply-add throughput probe: echo_selftest_dfma_blocks()

@@ -102,6 +102,7 @@ _SIGS = {
     "echo_selftest_conversions": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_selftest_recip": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_selftest_scale2": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
+    "echo_selftest_mp5_accept": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_selftest_dfma_blocks": (ctypes.c_int, []),
     "echo_selftest_dfma": (ctypes.c_int, [ctypes.c_longlong, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "echo_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
@@ -505,6 +506,11 @@ def echo_selftest_dfma(iters, dev_out, stream_handle: int = 0) -> float:
 def echo_selftest_scale2(n, seed, dev_mismatch, stream_handle: int = 0):
     _plain(load().echo_selftest_scale2(int(n), ctypes.c_ulonglong(seed), _P(_dev_any(dev_mismatch, "mismatch")),
                                        _P(stream_handle)), "echo_selftest_scale2")
+
+
+def echo_selftest_mp5_accept(n, seed, dev_mismatch, stream_handle: int = 0):
+    _plain(load().echo_selftest_mp5_accept(int(n), ctypes.c_ulonglong(seed), _P(_dev_any(dev_mismatch, "mismatch")),
+                                           _P(stream_handle)), "echo_selftest_mp5_accept")
 
 
 def echo_selftest_recip(n, seed, dev_max, stream_handle: int = 0):

@@ -565,13 +565,42 @@ __device__ __forceinline__ double alpha_times<double>(double x) { return scale2<
 // shares them between the two states of a face: the right state's
 // differences are the left stencil's negated (exact in IEEE arithmetic up to
 // the sign of a zero, which minmod2 maps to 0 either way).
+// The MP5 test a b <= eps with a = uor - u_j, b = a - minmod(...).  FP32:
+// the product.  FP64: decided from the signs and binary exponents of a and b
+// where that is exact -- a zero or opposite signs give a product <= 0; with
+// unbiased exponents summing to s, |a b| lies in [2^s, 2^(s+2)), below eps
+// (1e-10 > 2^-34) for s <= -36 and above it (2^-33 > 1e-10) for s >= -33 --
+// and from the product itself only for s in {-35, -34} and non-normal
+// operands, so the decision is the product's in every case.
+template <typename T>
+__device__ __forceinline__ bool mp5_accept(T a, T b) { return ile(a * b, T(MP5_EPS)); }
+template <>
+__device__ __forceinline__ bool mp5_accept<double>(double a, double b)
+{
+    static_assert(MP5_EPS == 1e-10, "the exponent bounds below assume eps = 1e-10");
+    const int ha = __double2hiint(a), hb = __double2hiint(b);
+    const bool za = ((ha & 0x7fffffff) | __double2loint(a)) == 0;
+    const bool zb = ((hb & 0x7fffffff) | __double2loint(b)) == 0;
+    if ((ha ^ hb) < 0 || za || zb)
+        return true;
+    const int ea = (ha >> 20) & 0x7ff, eb = (hb >> 20) & 0x7ff;
+    if (ea != 0 && eb != 0 && ea != 0x7ff && eb != 0x7ff) {
+        const int s = ea + eb - 2046;
+        if (s <= -36)
+            return true;
+        if (s >= -33)
+            return false;
+    }
+    return ile(a * b, MP5_EPS);
+}
+
 template <typename T>
 __device__ __forceinline__ T mp5_try_d(T um2, T um1, T u0, T up1, T up2, T dp, T dm, bool &accept, int order)
 {
     const T uor = mp5_uor(um2, um1, u0, up1, up2, order);
     const T d0 = uor - u0;
     const T mm = minmod2(dp, alpha_times(dm));
-    accept = ile(d0 * (d0 - mm), T(MP5_EPS));
+    accept = mp5_accept(d0, d0 - mm);
     return uor;
 }
 

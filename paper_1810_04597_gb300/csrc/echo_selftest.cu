@@ -1,7 +1,8 @@
 // echo_selftest.cu -- self-check of device helpers that replace hardware
 // instructions: the integer-pipe float <-> double conversions must equal the
 // hardware casts bit for bit; the Newton-Raphson reciprocal must stay within
-// 2 ulp of the IEEE quotient.  Also a register-only FP64 FMA throughput probe
+// 2 ulp of the IEEE quotient; the MP5 test decided from signs and exponents
+// must agree with the product test.  Also a register-only FP64 FMA throughput probe
 // whose measured rate is the FP64 roofline peak the benchmark reports
 // against.
 #include "../../include/echo.h"
@@ -105,6 +106,37 @@ __global__ void k_check_scale2(long long n, unsigned long long seed, unsigned lo
         atomicAdd(mismatch, bad);
 }
 
+// mp5_accept<double>(a, b) (the MP5 test from signs and exponents) against
+// the product test a * b <= eps on hashed pairs: exponent sums spread over
+// [-60, 20] and concentrated on the band [-38, -31] around eps, both signs,
+// random mantissas, and every 64th pair with a zero, a subnormal, a huge or
+// a non-finite operand; counts the differing decisions.
+__global__ void k_check_mp5_accept(long long n, unsigned long long seed, unsigned long long *mismatch)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const unsigned long long h = mix64(seed ^ (unsigned long long)i), g = mix64(h);
+    const long long ea = -60 + (long long)((h >> 40) % 81ULL);
+    const long long s = (h & 2ULL) ? -38 + (long long)((h >> 20) % 8ULL) : -60 + (long long)((h >> 20) % 81ULL);
+    long long eb = s - ea;
+    eb = eb < -1000 ? -1000 : (eb > 1000 ? 1000 : eb);
+    const unsigned long long ma = g & 0xfffffffffffffULL, mb = mix64(g) & 0xfffffffffffffULL;
+    double a = __longlong_as_double((long long)(((h & 1ULL) << 63) | ((unsigned long long)(1023 + ea) << 52) | ma));
+    double b = __longlong_as_double((long long)(((h & 4ULL) << 61) | ((unsigned long long)(1023 + eb) << 52) | mb));
+    if ((i & 63) == 0) {
+        const int k = (int)((h >> 8) % 6ULL);
+        const double sp[6] = {0.0, -0.0, 4.9e-324, 1e300, __longlong_as_double(0x7ff0000000000000LL),
+                              __longlong_as_double((long long)0xfff0000000000000ULL)};
+        if (h & 8ULL)
+            a = sp[k];
+        else
+            b = sp[k];
+    }
+    if (mp5_accept<double>(a, b) != ile(a * b, MP5_EPS))
+        atomicAdd(mismatch, 1ULL);
+}
+
 // FP64 fused multiply-add throughput: every thread runs 8 independent
 // chains c <- c * b + a for `iters` rounds in registers (no memory traffic
 // inside the loop) and writes one sum, so the compiler cannot drop the work.
@@ -164,6 +196,16 @@ extern "C" int echo_selftest_scale2(long long n, unsigned long long seed, unsign
         return ECHO_EINVAL;
     echo::k_check_scale2<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, seed,
                                                                                                    dev_mismatch);
+    return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
+}
+
+extern "C" int echo_selftest_mp5_accept(long long n, unsigned long long seed, unsigned long long *dev_mismatch,
+                                        void *stream)
+{
+    if (n < 1 || !dev_mismatch)
+        return ECHO_EINVAL;
+    echo::k_check_mp5_accept<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        n, seed, dev_mismatch);
     return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
 }
 

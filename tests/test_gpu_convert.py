@@ -46,6 +46,20 @@ def test_integer_pipe_scaling_matches_fp64_products():
     assert int(bad.item()) == 0
 
 
+def test_mp5_test_from_exponents_matches_the_product():
+    """The FP64 kernels decide the MP5 test a b <= eps from signs and binary
+    exponents, multiplying only near eps: the same decision as the product
+    test on 8 M hashed pairs (most with exponent sums at and around eps's,
+    plus zeros, subnormals, huge and infinite operands)."""
+    import torch
+    from paper_1810_04597_gb300 import _lib
+    bad = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for seed in (8, 9):
+        _lib.echo_selftest_mp5_accept(1 << 22, seed, bad)
+    torch.cuda.synchronize()
+    assert int(bad.item()) == 0
+
+
 @pytest.mark.parametrize("precision", [64, 32])
 def test_fp32_refined_guess_converges_to_the_same_state(precision):
     """Guess mode +4 (FP32 Newton pre-refinement): same converged state as the
