@@ -654,7 +654,7 @@ __device__ __forceinline__ T mp5_limit(T um2, T um1, T u0, T up1, T up2, int ord
 // division.
 template <int D, typename T, typename M>
 __device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m, T F[5], T U[5], T &np, T &nm,
-                                           T &Yout)
+                                           T &Yout, const T *v2_known = nullptr)
 {
     const T rho = P[0], p = P[4];
     const T v[3] = {P[1], P[2], P[3]};
@@ -662,7 +662,8 @@ __device__ __forceinline__ void state_flux(const T P[8], T gam, T gr, const M &m
     T vl[3], Bl[3];
     lower<T>(m, v, vl);
     lower<T>(m, B, Bl);
-    const T v2 = vl[0] * v[0] + vl[1] * v[1] + vl[2] * v[2];
+    // v^2 as v_i v^i, or the caller's value of that same expression
+    const T v2 = v2_known ? *v2_known : vl[0] * v[0] + vl[1] * v[1] + vl[2] * v[2];
     const T B2 = Bl[0] * B[0] + Bl[1] * B[1] + Bl[2] * B[2];
     const T vB = vl[0] * B[0] + vl[1] * B[1] + vl[2] * B[2];
     const T iW2 = T(1) - v2;

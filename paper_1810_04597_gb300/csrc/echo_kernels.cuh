@@ -831,24 +831,31 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     const T Bn = A.U[5 + D][id] * isgf;
     PL[5 + D] = Bn;
     PR[5 + D] = Bn;
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-        T *Ps = side == 0 ? PL : PR;
-        T v2;
+    // v^2 of each side, written as state_flux writes it (v_i v^i), which
+    // then takes it instead of forming it again
+    auto side_v2 = [&](const T *Ps) -> T {
         if constexpr (MK == 1) {
             const MKS<T> m(*mp);
             const T vv[3] = {Ps[1], Ps[2], Ps[3]};
             T vl[3];
             lower<T>(m, vv, vl);
-            v2 = vl[0] * vv[0] + vl[1] * vv[1] + vl[2] * vv[2];
+            return vl[0] * vv[0] + vl[1] * vv[1] + vl[2] * vv[2];
         } else {
-            v2 = Ps[1] * Ps[1] + Ps[2] * Ps[2] + Ps[3] * Ps[3];
+            const T vv[3] = {Ps[1], Ps[2], Ps[3]};
+            return vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2];
         }
+    };
+    T v2s[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        T *Ps = side == 0 ? PL : PR;
+        T v2 = side_v2(Ps);
         if (!is_pos(Ps[0]) || !is_pos(Ps[4]) || !ilt(v2, T(1))) {
             const int c = id + (side == 0 ? -sd : 0);
 #pragma unroll
             for (int m = 0; m < 7; ++m)
                 Ps[qs[m]] = A.P[qs[m]][c];
+            v2 = side_v2(Ps);
             // counted on the faces that bound owned cells, each face once
             bool owned = true;
 #pragma unroll
@@ -859,16 +866,17 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
             if (owned)
                 atomicAdd(&A.scal->fallback_faces, 1ULL);
         }
+        v2s[side] = v2;
     }
     T FL[5], UL[5], FR[5], UR[5], npL, nmL, YL, npR, nmR, YR;
     if constexpr (MK == 1) {
         const MKS<T> m(*mp);
-        state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, npL, nmL, YL);
-        state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, npR, nmR, YR);
+        state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, npL, nmL, YL, &v2s[0]);
+        state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, npR, nmR, YR, &v2s[1]);
     } else {
         const MFlat<T> m;
-        state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, npL, nmL, YL);
-        state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, npR, nmR, YR);
+        state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, npL, nmL, YL, &v2s[0]);
+        state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, npR, nmR, YR, &v2s[1]);
     }
     // both states' 1/Y from one division in FP64
     T iYL, iYR;
