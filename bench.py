@@ -86,8 +86,8 @@ def algorithmic_flops(counts, kernel, newton_iters):
 # launch.  c2p depends on the Newton iteration count (2.74 per call there);
 # faces_y/z run the code of faces_x with other strides.
 FLOPS64 = {
-    64: {"faces_x": 500.3, "faces_y": 500.3, "faces_z": 500.3,
-         "emf_x": 248.4, "emf_y": 248.4, "emf_z": 248.4,
+    64: {"faces_x": 476.3, "faces_y": 476.3, "faces_z": 476.3,
+         "emf_x": 236.4, "emf_y": 236.4, "emf_z": 236.4,
          "c2p": 386.5, "update": 79.0},
     # FP32-bulk path: only c2p computes in FP64 (previous-stage Z refined in
     # FP32, then 1.01 FP64 Newton iterations per call)
@@ -100,7 +100,7 @@ FLOPS64 = {
 # SM and clock give the pipe-time view beside the flop roofline (DADD and
 # DMUL are one flop for a full slot).
 FP64_INSTR = {
-    64: {"faces_x": 351.6, "faces_y": 351.6, "faces_z": 351.6, "emf_x": 179.7, "emf_y": 179.7, "emf_z": 179.7,
+    64: {"faces_x": 331.7, "faces_y": 331.7, "faces_z": 331.7, "emf_x": 167.8, "emf_y": 167.8, "emf_z": 167.8,
          "c2p": 272.4, "update": 53.0},
     32: {"c2p": 93.0},
 }
@@ -134,13 +134,13 @@ def measure_fp64_peak(dev, repeats=3, iters=20000):
     except Exception as exc:   # keep the bench line; say which peak it is
         return FP64_PEAK_TFLOPS, f"nominal (probe failed: {exc})"
 # DRAM bytes per face of faces_x (dram__bytes_read.sum + dram__bytes_write.sum
-# of the same 128^3 ncu launch: 336,267,776 B over 2,316,324 faces); scaled to a
+# of the same 128^3 ncu launch: 337,239,040 B over 2,316,324 faces); scaled to a
 # launch by the faces it processes.
-TRAFFIC_PER_FACE64 = 336267776 / 2316324
+TRAFFIC_PER_FACE64 = 337239040 / 2316324
 # FP64 pipe activity in those captures
 # (sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active).
-FP64_PIPE_BUSY = {64: {"faces_x": 0.879, "faces_y": 0.879, "faces_z": 0.879, "emf_x": 0.872, "emf_y": 0.872,
-                       "emf_z": 0.872, "c2p": 0.869, "update": 0.827},
+FP64_PIPE_BUSY = {64: {"faces_x": 0.880, "faces_y": 0.880, "faces_z": 0.880, "emf_x": 0.874, "emf_y": 0.874,
+                       "emf_z": 0.874, "c2p": 0.869, "update": 0.827},
                   32: {"c2p": 0.858}}
 # The FP64 pipe's nominal lane rate (thread instructions per second): 152 SMs
 # x 2 lanes per SM and clock x 2.07 GHz.  The FMA probe reaches ~84 % of it
