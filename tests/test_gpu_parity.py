@@ -90,6 +90,32 @@ def crop(prob, n):
     return inputs.Problem(name=prob.name + "_crop", n=n, x0=prob.x0, dx=prob.dx, prims=prims, bface=bf)
 
 
+def test_parity_noise_box(orc):
+    """Seeded white noise in every primitive: most MP5 reconstructions fail
+    the monotonicity test, so the limiter's packed lists run long (in FP64
+    up to 16 items per thread, 2048 per block of 128) -- L(U) on a ragged
+    grid to 1e-12 and two steps to 1e-11 against the oracle."""
+    from paper_1810_04597_gb300.echo import Solver
+    base = crop(inputs.smooth_box(40, seed=13), (37, 29, 23))
+    rng = np.random.default_rng(2024)
+    shape = (base.n[2], base.n[1], base.n[0])
+    prims = np.stack([rng.uniform(0.5, 1.5, shape), rng.uniform(-0.3, 0.3, shape), rng.uniform(-0.3, 0.3, shape),
+                      rng.uniform(-0.3, 0.3, shape), rng.uniform(0.5, 1.5, shape)])
+    prob = inputs.Problem(name="noise_box", n=base.n, x0=base.x0, dx=base.dx, prims=prims, bface=base.bface)
+    s = Solver(prob)
+    s.set_prims()
+    L_g = s.rhs()
+    cfg = orc.make_cfg(prob)
+    st, Z = orc.p2c(cfg, prob.prims, prob.bface)
+    L_o, _, _ = orc.rhs(cfg, st, Z)
+    errs = per_field(orc, L_g, L_o, prob.n)
+    assert max(errs.values()) <= 1e-12, errs
+    st_g, _ = gpu_run(prob, 2)
+    st_o, _, _, _ = oracle_run(orc, prob, 2)
+    errs = per_field(orc, st_g, st_o, prob.n)
+    assert max(errs.values()) <= 1e-11, errs
+
+
 def test_ten_step_parity_32(orc):
     """The FP64 target: 10 steps of the 32^3 box, max-relative error per
     field <= 1e-11, CFL dt from each side's own state."""
