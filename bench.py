@@ -673,9 +673,40 @@ def run_torus_variant(args, dev, world, dist, steps=50):
         den = float(np.sum(np.abs(a64[seg])))
         l1[name] = float(np.sum(np.abs(a32[seg] - a64[seg])) / den) if den > 0 else 0.0
     res["fp32"]["l1_rel_vs_fp64_gpu"] = l1
+    res["fp32"]["l1_frame_vs_fp64_gpu"] = torus_frame_l1(prob, a64, a32)
     res["fp32"]["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res["fp32"]["ms_per_step"]
     res["note"] = "Kerr-Schild, floors and fallbacks; FP32 bulk with FP64 c2p, metric and reductions"
     return res
+
+
+def torus_frame_l1(prob, ref, got):
+    """Relative L1 distances of the torus state `got` from `ref` that stay
+    well conditioned where a component is near zero (S_theta in an
+    equilibrium torus): D and tau as sum|d| / sum|ref|; each covariant
+    momentum component in the local orthonormal frame,
+    sum |dS_i| sqrt(gamma^ii) / sum |S| with |S| = sqrt(gamma^ij S_i S_j),
+    the Kerr-Schild spatial metric at the cell centres (inputs.ks_metric_arrays)."""
+    import numpy as np
+    from paper_1810_04597_gb300 import inputs
+    nx, ny, nz = prob.n
+    N = nx * ny * nz
+    x1 = prob.x0[0] + (np.arange(nx) + 0.5) * prob.dx[0]
+    th = prob.x0[1] + (np.arange(ny) + 0.5) * prob.dx[1]
+    X1, TH = np.meshgrid(x1, th)                       # (ny, nx)
+    _, _, g11, g13, g22, g33 = inputs.ks_metric_arrays(X1, TH, prob.spin)
+    det = g11 * g33 - g13 * g13
+    gi11, gi22, gi33, gi13 = g33 / det, 1.0 / g22, g11 / det, -g13 / det
+    cell = lambda st, q: st[q * N:(q + 1) * N].reshape(nz, ny, nx)
+    S = [cell(ref, 1 + q) for q in range(3)]
+    Smag = np.sqrt(gi11 * S[0] ** 2 + gi22 * S[1] ** 2 + gi33 * S[2] ** 2 + 2.0 * gi13 * S[0] * S[2])
+    den = float(np.sum(Smag))
+    out = {}
+    for q, name in ((0, "D"), (4, "tau")):
+        r = cell(ref, q)
+        out[name] = float(np.sum(np.abs(cell(got, q) - r)) / max(float(np.sum(np.abs(r))), 1e-300))
+    for q, (name, gii) in enumerate((("S_r", gi11), ("S_theta", gi22), ("S_phi", gi33))):
+        out[name] = float(np.sum(np.abs(cell(got, 1 + q) - S[q]) * np.sqrt(gii)) / max(den, 1e-300))
+    return out
 
 
 def run_order1_variant(args, prob, dev, world, dist, ms64):

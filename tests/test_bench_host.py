@@ -97,3 +97,36 @@ def test_reference_arm_labels_what_it_times():
     assert "12^3" in line["config"]["workload"] and "sample" in line["config"]["workload"]
     assert line["config"]["sample_grid"] == [12, 12, 12]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_torus_frame_l1_measure():
+    """The torus FP32 line's frame-based L1: zero for equal states; a change
+    in one momentum component moves only that component's figure (and not D
+    or tau); invariant under a common scale of both states; an S_theta
+    change of d in one cell reads d sqrt(gamma^thth) / sum |S| there."""
+    import numpy as np
+    import bench
+    from paper_1810_04597_gb300 import inputs
+    prob = inputs.fm_torus((12, 6, 4))
+    N = prob.ncells
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=8 * N + 50)
+    assert all(v == 0.0 for v in bench.torus_frame_l1(prob, a, a).values())
+    b = a.copy()
+    cell = 1 * prob.n[0] * prob.n[1] + 3 * prob.n[0] + 7        # (k, j, i) = (1, 3, 7)
+    b[2 * N + cell] += 1e-3                                     # S_theta of that cell
+    m = bench.torus_frame_l1(prob, a, b)
+    assert m["D"] == 0.0 and m["tau"] == 0.0 and m["S_r"] == 0.0 and m["S_phi"] == 0.0
+    x1 = prob.x0[0] + 7.5 * prob.dx[0]
+    th = prob.x0[1] + 3.5 * prob.dx[1]
+    _, _, g11, g13, g22, g33 = inputs.ks_metric_arrays(np.array([[x1]]), np.array([[th]]), prob.spin)
+    X1, TH = np.meshgrid(prob.x0[0] + (np.arange(prob.n[0]) + 0.5) * prob.dx[0],
+                         prob.x0[1] + (np.arange(prob.n[1]) + 0.5) * prob.dx[1])
+    _, _, G11, G13, G22, G33 = inputs.ks_metric_arrays(X1, TH, prob.spin)
+    det = G11 * G33 - G13 ** 2
+    S = [a[(1 + q) * N:(2 + q) * N].reshape(prob.n[2], prob.n[1], prob.n[0]) for q in range(3)]
+    Smag = np.sqrt(G33 / det * S[0] ** 2 + S[1] ** 2 / G22 + G11 / det * S[2] ** 2 - 2 * G13 / det * S[0] * S[2])
+    want = 1e-3 / np.sqrt(g22[0, 0]) / np.sum(Smag)
+    assert abs(m["S_theta"] - want) <= 1e-12 * want
+    s = bench.torus_frame_l1(prob, 3.0 * a, 3.0 * b)
+    assert all(abs(s[k] - m[k]) <= 1e-14 + 1e-12 * m[k] for k in m)
