@@ -416,6 +416,17 @@ struct MKS {
           i22(from_d<T>(m.i22)), i33(from_d<T>(m.i33)), sg(from_d<T>(m.sg))
     {
     }
+    // FP64 -> T by the hardware conversion: one issue slot each on the FP64
+    // pipe, which the FP32 face kernels (bound by issue slots) leave idle --
+    // faster there than from_d's integer sequence; kernels bound by the FP64
+    // pipe, or by latency at low occupancy, use the constructor above
+    struct HwCast {
+    };
+    __device__ __forceinline__ MKS(const MetPt &m, HwCast)
+        : al((T)m.al), b1((T)m.b1), g11((T)m.g11), g13((T)m.g13), g22((T)m.g22), g33((T)m.g33), i11((T)m.i11),
+          i13((T)m.i13), i22((T)m.i22), i33((T)m.i33), sg((T)m.sg)
+    {
+    }
 };
 
 template <typename T, typename M>

@@ -835,7 +835,7 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     // then takes it instead of forming it again
     auto side_v2 = [&](const T *Ps) -> T {
         if constexpr (MK == 1) {
-            const MKS<T> m(*mp);
+            const MKS<T> m(*mp, typename MKS<T>::HwCast{});
             const T vv[3] = {Ps[1], Ps[2], Ps[3]};
             T vl[3];
             lower<T>(m, vv, vl);
@@ -870,7 +870,7 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     }
     T FL[5], UL[5], FR[5], UR[5], npL, nmL, YL, npR, nmR, YR;
     if constexpr (MK == 1) {
-        const MKS<T> m(*mp);
+        const MKS<T> m(*mp, typename MKS<T>::HwCast{});
         state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, npL, nmL, YL, &v2s[0]);
         state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, npR, nmR, YR, &v2s[1]);
     } else {
