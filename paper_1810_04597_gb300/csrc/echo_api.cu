@@ -92,6 +92,13 @@ size_t layout(echo_ctx *c, char *base, Arrays<R> *A)
         A->met.K = reinterpret_cast<MetPt *>(take(plane * sizeof(MetPt)));
         A->met.dC = reinterpret_cast<MetDer *>(take(plane * sizeof(MetDer)));
         A->met.floors = reinterpret_cast<double *>(take((size_t)c->geo.np[0] * 2 * sizeof(double)));
+        if (sizeof(R) == 4) {
+            A->met.Cf = reinterpret_cast<MetPtF *>(take(plane * sizeof(MetPtF)));
+            A->met.F1f = reinterpret_cast<MetPtF *>(take(plane * sizeof(MetPtF)));
+            A->met.F2f = reinterpret_cast<MetPtF *>(take(plane * sizeof(MetPtF)));
+            A->met.Kf = reinterpret_cast<MetPtF *>(take(plane * sizeof(MetPtF)));
+            A->met.dCf = reinterpret_cast<MetDerF *>(take(plane * sizeof(MetDerF)));
+        }
     }
     A->stage = reinterpret_cast<double *>(take(c->staging_count * sizeof(double)));
     A->partials = reinterpret_cast<double *>(take((size_t)c->nblk_red * 6 * sizeof(double)));

@@ -8,6 +8,8 @@
 // transcription only by rounding order.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -162,11 +164,19 @@ struct DevScalars {
 struct MetPt {
     double al, b1, g11, g13, g22, g33, i11, i13, i22, i33, sg, isg;
 };
+// The same in FP32, for the FP32 kernels (rounded once when the tables are
+// made, so that no kernel converts a metric value per cell).
+struct MetPtF {
+    float al, b1, g11, g13, g22, g33, i11, i13, i22, i33, sg, isg;
+};
 
 // d_1 and d_2 of alpha, beta^1, gamma_11, _13, _22, _33 at a cell centre
 // (sixth-order centred differences of the closed form, step dx^d).
 struct MetDer {
     double dal[2], db1[2], dg11[2], dg13[2], dg22[2], dg33[2];
+};
+struct MetDerF {
+    float dal[2], db1[2], dg11[2], dg13[2], dg22[2], dg33[2];
 };
 
 // Tables over the padded (x1, x2) plane, index j * np0 + i: cell centres C,
@@ -176,6 +186,8 @@ struct MetDer {
 struct MetTables {
     MetPt *C, *F1, *F2, *K;
     MetDer *dC;
+    MetPtF *Cf, *F1f, *F2f, *Kf;   // FP32 copies (FP32 storage only, else null)
+    MetDerF *dCf;
     double *floors;   // 2 * np0
     int np0;
     int use_floors;
@@ -416,16 +428,39 @@ struct MKS {
           i22(from_d<T>(m.i22)), i33(from_d<T>(m.i33)), sg(from_d<T>(m.sg))
     {
     }
-    // FP64 -> T by the hardware conversion: one issue slot each on the FP64
-    // pipe, which the FP32 face kernels (bound by issue slots) leave idle --
-    // faster there than from_d's integer sequence; kernels bound by the FP64
-    // pipe, or by latency at low occupancy, use the constructor above
-    struct HwCast {
-    };
-    __device__ __forceinline__ MKS(const MetPt &m, HwCast)
-        : al((T)m.al), b1((T)m.b1), g11((T)m.g11), g13((T)m.g13), g22((T)m.g22), g33((T)m.g33), i11((T)m.i11),
-          i13((T)m.i13), i22((T)m.i22), i33((T)m.i33), sg((T)m.sg)
+    // from the FP32 copy of the table (no conversion in an FP32 kernel)
+    __device__ __forceinline__ explicit MKS(const MetPtF &m)
+        : al(m.al), b1(m.b1), g11(m.g11), g13(m.g13), g22(m.g22), g33(m.g33), i11(m.i11), i13(m.i13), i22(m.i22),
+          i33(m.i33), sg(m.sg)
     {
+    }
+};
+
+// The metric tables of storage type R: FP64 points for FP64 kernels, the
+// FP32 copies for FP32 ones.
+template <typename R>
+using MetPtOf = std::conditional_t<sizeof(R) == 4, MetPtF, MetPt>;
+template <typename R>
+using MetDerOf = std::conditional_t<sizeof(R) == 4, MetDerF, MetDer>;
+template <typename R>
+struct MetOf {
+    const MetPtOf<R> *C, *F1, *F2, *K;
+    const MetDerOf<R> *dC;
+    __device__ __forceinline__ explicit MetOf(const MetTables &T)
+    {
+        if constexpr (sizeof(R) == 4) {
+            C = T.Cf;
+            F1 = T.F1f;
+            F2 = T.F2f;
+            K = T.Kf;
+            dC = T.dCf;
+        } else {
+            C = T.C;
+            F1 = T.F1;
+            F2 = T.F2;
+            K = T.K;
+            dC = T.dC;
+        }
     }
 };
 

@@ -357,7 +357,7 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
                 const float idxf[3] = {d2f(g.idx[0]), d2f(g.idx[1]), d2f(g.idx[2])};
                 float rf;
                 if constexpr (MK == 1)
-                    rf = cfl_rate(Pf, ph.gamma_f, ph.gr_f, idxf, MKS<float>(*mp));
+                    rf = cfl_rate(Pf, ph.gamma_f, ph.gr_f, idxf, MKS<float>(A.met.Cf[mp - A.met.C]));
                 else
                     rf = cfl_rate(Pf, ph.gamma_f, ph.gr_f, idxf, MFlat<float>());
                 rate = f2d(rf);
@@ -803,12 +803,13 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
             Rv[m] = lsm.res[w][lane][2 * m + 1];
     }
     // face metric (x1-faces: F1, x2-faces: F2, x3-faces: the cell-centre table)
-    const MetPt *mp = nullptr;
+    const MetPtOf<T> *mp = nullptr;   // the table of the storage type: no conversion
     T isgf = T(1);
     if constexpr (MK == 1) {
         const int ti = ijk[1] * A.met.np0 + ijk[0];
-        mp = D == 0 ? &A.met.F1[ti] : (D == 1 ? &A.met.F2[ti] : &A.met.C[ti]);
-        if (!(mp->sg > 0.0)) {
+        const MetOf<T> M(A.met);
+        mp = D == 0 ? &M.F1[ti] : (D == 1 ? &M.F2[ti] : &M.C[ti]);
+        if (!(mp->sg > T(0))) {
             // polar-axis face: zero area, no flux
 #pragma unroll
             for (int q = 0; q < 5; ++q)
@@ -820,7 +821,7 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
                 A.fv[D][q][id] = T(0);
             return;
         }
-        isgf = (T)mp->isg;
+        isgf = mp->isg;
     }
     T PL[8], PR[8];
 #pragma unroll
@@ -835,7 +836,7 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     // then takes it instead of forming it again
     auto side_v2 = [&](const T *Ps) -> T {
         if constexpr (MK == 1) {
-            const MKS<T> m(*mp, typename MKS<T>::HwCast{});
+            const MKS<T> m(*mp);
             const T vv[3] = {Ps[1], Ps[2], Ps[3]};
             T vl[3];
             lower<T>(m, vv, vl);
@@ -870,7 +871,7 @@ __device__ __forceinline__ void faces_body(const Geom &g, const Phys &ph, const 
     }
     T FL[5], UL[5], FR[5], UR[5], npL, nmL, YL, npR, nmR, YR;
     if constexpr (MK == 1) {
-        const MKS<T> m(*mp, typename MKS<T>::HwCast{});
+        const MKS<T> m(*mp);
         state_flux<D>(PL, phys_gamma<T>(ph), phys_gr<T>(ph), m, FL, UL, npL, nmL, YL, &v2s[0]);
         state_flux<D>(PR, phys_gamma<T>(ph), phys_gr<T>(ph), m, FR, UR, npR, nmR, YR, &v2s[1]);
     } else {
@@ -1044,10 +1045,11 @@ __device__ __forceinline__ void emf_body(const Geom &g, const Arrays<R> &A, long
     T al = T(1), bea = T(0), beb = T(0);
     if constexpr (MK == 1) {
         const int ti = ej * A.met.np0 + ei;
-        const MetPt &mp = E == 0 ? A.met.F2[ti] : (E == 1 ? A.met.F1[ti] : A.met.K[ti]);
-        al = (T)mp.al;
-        bea = a == 0 ? (T)mp.b1 : T(0);
-        beb = b == 0 ? (T)mp.b1 : T(0);
+        const MetOf<T> M(A.met);
+        const MetPtOf<T> &mp = E == 0 ? M.F2[ti] : (E == 1 ? M.F1[ti] : M.K[ti]);
+        al = mp.al;
+        bea = a == 0 ? mp.b1 : T(0);
+        beb = b == 0 ? mp.b1 : T(0);
     }
     T Est[2][2];
 #pragma unroll
@@ -1092,8 +1094,8 @@ __global__ void __launch_bounds__(128) k_emf(Geom g, Arrays<R> A)
 //   S(S_i) = 1/2 alpha W^jk d_i gamma_jk + S_1 d_i beta^1 - U d_i alpha     (i = 1, 2)
 //   S(tau) = 1/2 beta^1 W^ik d_1 gamma_ik + W_1^j d_j beta^1 - S^j d_j alpha
 // with W^jk = (rho h + b^2) W^2 v^j v^k + (p + b^2/2) gamma^jk - b^j b^k.
-template <typename T>
-__device__ __forceinline__ void ks_sources(const T P[8], T gr, const MetPt &mp, const MetDer &md, T src[5])
+template <typename T, typename MP, typename MD>
+__device__ __forceinline__ void ks_sources(const T P[8], T gr, const MP &mp, const MD &md, T src[5])
 {
     const MKS<T> m(mp);
     const T v[3] = {P[1], P[2], P[3]}, B[3] = {P[5], P[6], P[7]};
@@ -1129,16 +1131,16 @@ __device__ __forceinline__ void ks_sources(const T P[8], T gr, const MetPt &mp, 
     T s[2];
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-        const T wdg = W11 * (T)md.dg11[d] + T(2) * W13 * (T)md.dg13[d] + W22 * (T)md.dg22[d] + W33 * (T)md.dg33[d];
-        s[d] = T(0.5) * m.al * wdg + Sl[0] * (T)md.db1[d] - Uen * (T)md.dal[d];
+        const T wdg = W11 * md.dg11[d] + T(2) * W13 * md.dg13[d] + W22 * md.dg22[d] + W33 * md.dg33[d];
+        s[d] = T(0.5) * m.al * wdg + Sl[0] * md.db1[d] - Uen * md.dal[d];
     }
-    const T wdg1 = W11 * (T)md.dg11[0] + T(2) * W13 * (T)md.dg13[0] + W22 * (T)md.dg22[0] + W33 * (T)md.dg33[0];
+    const T wdg1 = W11 * md.dg11[0] + T(2) * W13 * md.dg13[0] + W22 * md.dg22[0] + W33 * md.dg33[0];
     const T W1_1 = m.g11 * W11 + m.g13 * W13;
     const T W1_2 = m.g11 * W12 + m.g13 * W32;
     const T Su1 = m.i11 * Sl[0] + m.i13 * Sl[2];
     const T Su2 = m.i22 * Sl[1];
-    const T st = T(0.5) * m.b1 * wdg1 + W1_1 * (T)md.db1[0] + W1_2 * (T)md.db1[1] - Su1 * (T)md.dal[0]
-                 - Su2 * (T)md.dal[1];
+    const T st = T(0.5) * m.b1 * wdg1 + W1_1 * md.db1[0] + W1_2 * md.db1[1] - Su1 * md.dal[0]
+                 - Su2 * md.dal[1];
     src[0] = T(0);
     src[1] = s[0] * m.sg;
     src[2] = s[1] * m.sg;
@@ -1177,7 +1179,8 @@ __device__ __forceinline__ void cell_rate(const Geom &g, const Phys &ph, const A
         for (int q = 0; q < 8; ++q)
             P[q] = A.P[q][id];
         const int ti = j * A.met.np0 + i;
-        ks_sources(P, phys_gr<R>(ph), A.met.C[ti], A.met.dC[ti], src);
+        const MetOf<R> M(A.met);
+        ks_sources(P, phys_gr<R>(ph), M.C[ti], M.dC[ti], src);
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {

@@ -91,6 +91,26 @@ __global__ void k_metric_tables(Geom g, double a, MetTables T, double rho_floor,
         dv.dg33[d] = acc[5] / (60.0 * h);
     }
     T.dC[id] = dv;
+    if (T.Cf) {
+        // the FP32 copies, rounded once here
+        const MetPt *src[4] = {&T.C[id], &T.F1[id], &T.F2[id], &T.K[id]};
+        MetPtF *dst[4] = {&T.Cf[id], &T.F1f[id], &T.F2f[id], &T.Kf[id]};
+        for (int q = 0; q < 4; ++q) {
+            const MetPt &m = *src[q];
+            *dst[q] = MetPtF{(float)m.al,  (float)m.b1,  (float)m.g11, (float)m.g13, (float)m.g22, (float)m.g33,
+                             (float)m.i11, (float)m.i13, (float)m.i22, (float)m.i33, (float)m.sg,  (float)m.isg};
+        }
+        MetDerF df;
+        for (int d = 0; d < 2; ++d) {
+            df.dal[d] = (float)dv.dal[d];
+            df.db1[d] = (float)dv.db1[d];
+            df.dg11[d] = (float)dv.dg11[d];
+            df.dg13[d] = (float)dv.dg13[d];
+            df.dg22[d] = (float)dv.dg22[d];
+            df.dg33[d] = (float)dv.dg33[d];
+        }
+        T.dCf[id] = df;
+    }
     if (j == 0) {
         T.floors[2 * i] = rho_floor * pow(exp(xc), rho_pow);
         T.floors[2 * i + 1] = p_floor * pow(exp(xc), p_pow);
