@@ -1288,11 +1288,11 @@ __device__ __forceinline__ void update_body(const Geom &g, const Phys &ph, const
 
 // Flat metric: 8 blocks of 256 per SM (32 registers, full occupancy; the
 // FP32 form streams and needs the warps in flight).  Kerr-Schild (sources):
-// FP32 6 blocks (40 registers, a 12-byte spill: the latency-bound kernel
+// FP32 8 blocks (32 registers, a 28-byte spill: the latency-bound kernel
 // gains more from the warps than it loses to the spill), FP64 3 blocks (the
 // occupancy its registers give anyway; that form is bound by the FP64 pipe).
 template <int MK, typename R>
-__global__ void __launch_bounds__(256, MK == 0 ? 8 : (sizeof(R) == 4 ? 6 : 3))
+__global__ void __launch_bounds__(256, MK == 0 ? 8 : (sizeof(R) == 4 ? 8 : 3))
     k_update(Geom g, Phys ph, Arrays<R> A, int stage, double *Lout)
 {
     update_body<MK, R>(g, ph, A, stage, Lout, (long long)blockIdx.x * blockDim.x + threadIdx.x);
