@@ -113,15 +113,16 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 def measure_fp64_peak(dev, repeats=3, iters=20000):
     """FP64 rate of the library's register-only FMA probe
-    (echo_selftest_dfma), best of `repeats` launches timed with CUDA events:
-    (TFLOP/s, source)."""
+    (echo_selftest_dfma, at the FP64 pipe's full issue rate), best of
+    `repeats` launches timed with CUDA events after one untimed launch of the
+    same length: (TFLOP/s, source)."""
     import torch
     from paper_1810_04597_gb300 import _lib
     try:
         blocks = _lib.echo_selftest_dfma_blocks()
         out = torch.empty(256 * blocks, dtype=torch.float64, device=dev)
         st = torch.cuda.current_stream(dev)
-        _lib.echo_selftest_dfma(1000, out, st.cuda_stream)
+        _lib.echo_selftest_dfma(iters, out, st.cuda_stream)   # warm-up as long as a timed launch
         best = 0.0
         for _ in range(repeats):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -143,9 +144,16 @@ FP64_PIPE_BUSY = {64: {"faces_x": 0.880, "faces_y": 0.880, "faces_z": 0.880, "em
                        "emf_z": 0.874, "c2p": 0.869, "update": 0.827},
                   32: {"c2p": 0.858}}
 # The FP64 pipe's nominal lane rate (thread instructions per second): 152 SMs
-# x 2 lanes per SM and clock x 2.07 GHz.  The FMA probe reaches ~84 % of it
-# (three 64-bit operands per FMA); DADD/DMUL-rich kernels can issue faster.
+# x 2 lanes per SM and clock x 2.07 GHz.  The FMA probe issues at 0.996 of
+# it; FMAs that read three distinct 64-bit registers issue at 0.80-0.97.
 FP64_PIPE_LANES_PER_S = 152 * 2 * 2.07e9
+
+
+def fp64_mix_cap(flops_per_unit, fp64_instr_per_unit, peak_tflops):
+    """Fraction of the FMA peak a kernel can reach with its own FP64
+    instruction mix when the pipe issues on every lane slot: DADD and DMUL
+    take a full slot for one flop, an FMA two."""
+    return flops_per_unit / fp64_instr_per_unit * FP64_PIPE_LANES_PER_S / 1e12 / peak_tflops
 
 
 def kernel_units(name, n):
@@ -513,6 +521,7 @@ def run_ours(args, world, rank, local, dist):
                 "fp64_pipe_busy_ncu": FP64_PIPE_BUSY[args.precision].get(dom),
                 "fp64_instr_frac": units * FP64_INSTR[args.precision][dom] / avg_s / FP64_PIPE_LANES_PER_S,
                 "fp64_instr_frac_of": "the FP64 pipe's nominal lane rate (152 SMs x 2 per clock x 2.07 GHz)",
+                "fp64_mix_cap_frac": fp64_mix_cap(fl[dom], FP64_INSTR[args.precision][dom], fp64_peak),
                 "traffic_note": "dram bytes per face of a 128^3 ncu capture x faces per launch"
                 if traffic is not None else "no ncu traffic figure for this kernel and precision",
                 "avg_launch_ms": avg_s * 1e3, "hbm_context": hbm_ctx, "time_share": share}
@@ -809,6 +818,7 @@ def fp32_c2p_roofline(prof, ms, zones, newton_iters, fp64_peak, fp64_src):
             "fp64_pipe_busy_ncu": FP64_PIPE_BUSY[32]["c2p"], "avg_launch_ms": avg_s * 1e3,
             "fp64_instr_frac": zones * FP64_INSTR[32]["c2p"] / avg_s / FP64_PIPE_LANES_PER_S,
             "fp64_instr_frac_of": "the FP64 pipe's nominal lane rate (152 SMs x 2 per clock x 2.07 GHz)",
+            "fp64_mix_cap_frac": fp64_mix_cap(FLOPS64[32]["c2p"], FP64_INSTR[32]["c2p"], fp64_peak),
             "time_share": {k: round(v[0] / ms, 4) for k, v in prof.items() if v[1] > 0}}
 
 

@@ -438,8 +438,9 @@ int echo_selftest_mp5_accept(long long n, unsigned long long seed, unsigned long
  * FP64 fused multiply-add throughput probe: echo_selftest_dfma_blocks()
  * blocks of 256 threads (4 per SM of the current device; -1 if the device
  * cannot be queried), each thread running 8 independent chains of `iters`
- * (1 .. 2^31-1, else ECHO_EINVAL) FMAs in registers, then writing one
- * double per thread to dev_out (device,
+ * (1 .. 2^31-1, else ECHO_EINVAL) FMAs c <- c * c - c in registers (one
+ * source register per FMA, the form that issues at the FP64 pipe's full
+ * rate), then writing one double per thread to dev_out (device,
  * at least 256 * blocks doubles, caller-owned).  *flops (host, may be NULL)
  * receives the launch's floating-point operations (2 per FMA), so that the
  * caller's event time around the launch gives the device's FP64 rate. */

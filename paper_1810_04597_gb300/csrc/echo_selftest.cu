@@ -138,24 +138,28 @@ __global__ void k_check_mp5_accept(long long n, unsigned long long seed, unsigne
 }
 
 // FP64 fused multiply-add throughput: every thread runs 8 independent
-// chains c <- c * b + a for `iters` rounds in registers (no memory traffic
+// chains c <- c * c - c for `iters` rounds in registers (no memory traffic
 // inside the loop) and writes one sum, so the compiler cannot drop the work.
-// a and b come from the arguments; with b slightly below 1 and a small the
-// chains stay finite.
+// All three operands of each FMA are one register: FMAs that read three
+// distinct 64-bit registers issue at 0.80-0.97 of the FP64 pipe's rate on
+// GB300, this form at its full rate, which is the FP64 peak.  The chains
+// start at (thread + chain + 1) * a with a small; two rounds map c to
+// c - 2c^3 + c^4, so they shrink slowly towards 0 and stay finite and normal.
 constexpr int kDfmaChains = 8;
 
 // The loop counter is 32-bit (64-bit integer adds and compares can take
 // FP64-pipe slots on GB300).
-__global__ void __launch_bounds__(256) k_dfma_throughput(int iters, double a, double b, double *out)
+__global__ void __launch_bounds__(256) k_dfma_throughput(int iters, double a, double *out)
 {
     double c[kDfmaChains];
 #pragma unroll
     for (int q = 0; q < kDfmaChains; ++q)
-        c[q] = (double)(threadIdx.x + q);
+        c[q] = (double)(threadIdx.x + q + 1) * a;
+#pragma unroll 2
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int q = 0; q < kDfmaChains; ++q)
-            c[q] = fma(c[q], b, a);
+            c[q] = fma(c[q], c[q], -c[q]);
     }
     double s = 0.0;
 #pragma unroll
@@ -183,7 +187,7 @@ extern "C" int echo_selftest_dfma(long long iters, double *dev_out, double *flop
     if (iters < 1 || iters > 0x7fffffffLL || !dev_out || blocks < 1)
         return ECHO_EINVAL;
     echo::k_dfma_throughput<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        (int)iters, 1e-3, 0.999999, dev_out);
+        (int)iters, 1e-6, dev_out);
     if (flops)
         *flops = 2.0 * echo::kDfmaChains * (double)iters * 256.0 * (double)blocks;
     return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;

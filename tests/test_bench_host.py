@@ -130,3 +130,16 @@ def test_torus_frame_l1_measure():
     assert abs(m["S_theta"] - want) <= 1e-12 * want
     s = bench.torus_frame_l1(prob, 3.0 * a, 3.0 * b)
     assert all(abs(s[k] - m[k]) <= 1e-14 + 1e-12 * m[k] for k in m)
+
+
+def test_fp64_mix_cap():
+    """At the nominal FP64 peak, an FMA-only kernel (2 flop per FP64
+    instruction) can reach the whole peak and a DADD-only kernel half of it;
+    the listed kernels' caps lie between."""
+    import bench
+    assert abs(bench.fp64_mix_cap(2.0, 1.0, bench.FP64_PEAK_TFLOPS) - 1.0) < 1e-12
+    assert abs(bench.fp64_mix_cap(1.0, 1.0, bench.FP64_PEAK_TFLOPS) - 0.5) < 1e-12
+    for prec, fl in bench.FLOPS64.items():
+        for k, f in fl.items():
+            cap = bench.fp64_mix_cap(f, bench.FP64_INSTR[prec][k], bench.FP64_PEAK_TFLOPS)
+            assert 0.5 <= cap <= 1.0, (prec, k, cap)

@@ -84,15 +84,16 @@ def test_fp32_refined_guess_converges_to_the_same_state(precision):
 
 def test_fp64_throughput_probe():
     """The FP64 FMA probe whose rate bench.py takes as the FP64 roofline
-    peak: the chains stay finite and the measured rate lies between a
-    quarter of and just above GB300's nominal FP64 peak (152 SMs x 2 FMA x 2
-    flop x 2.07 GHz = 1.26 TFLOP/s)."""
+    peak: the chains stay finite and nonzero, and the measured rate lies
+    between a quarter of and just above GB300's nominal FP64 peak (152 SMs x
+    2 FMA x 2 flop x 2.07 GHz = 1.259 TFLOP/s): above it the launch's flop
+    count would be wrong."""
     import torch
     from paper_1810_04597_gb300 import _lib
     blocks = _lib.echo_selftest_dfma_blocks()
     out = torch.empty(256 * blocks, dtype=torch.float64, device="cuda")
     s = torch.cuda.current_stream()
-    _lib.echo_selftest_dfma(1000, out, s.cuda_stream)          # warm-up
+    _lib.echo_selftest_dfma(20000, out, s.cuda_stream)         # warm-up
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(s)
     flops = _lib.echo_selftest_dfma(20000, out, s.cuda_stream)
@@ -100,5 +101,5 @@ def test_fp64_throughput_probe():
     torch.cuda.synchronize()
     rate = flops / (a.elapsed_time(b) * 1e-3)
     print(f"FP64 FMA probe: {rate / 1e12:.3f} TFLOP/s")
-    assert torch.isfinite(out).all()
-    assert 0.3e12 <= rate <= 1.4e12, rate
+    assert torch.isfinite(out).all() and (out != 0).all()
+    assert 0.3e12 <= rate <= 1.05 * 1.259e12, rate
