@@ -948,11 +948,16 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
         const double p = gm1g * (Z * om - Dc * sq);
         const double iZ2 = iZ * iZ;
         const double f = Z - p + (1.0 + v2) * hB2 - hSB2 * iZ2 - Uen;
+        const double iZ3 = iZ2 * iZ;
         const double iZB3 = iZB * iZB * iZB;
         // dv^2/dZ = -2 (S^2 Z^3 + (S.B)^2 (3 Z^2 + 3 Z B^2 + B^4)) / (Z^3 (Z + B^2)^3)
-        const double dv2 = -(scale2<1>(S2 * Z * Z * Z + SB2 * (3.0 * Z * Z + 3.0 * Z * B2 + B2 * B2)) * iZ2 * iZ * iZB3);
+        //         = -2 (S^2 + (S.B)^2 (Z (3 Z + 3 B^2) + B^4) / Z^3) / (Z + B^2)^3:
+        // Z^3 cancels against 1/Z^3, both terms stay positive (no
+        // cancellation), and 1/Z^3 serves f' below as well
+        const double P3 = fma(3.0 * Z, Z + B2, B2 * B2);
+        const double dv2 = -(scale2<1>(fma(SB2 * P3, iZ3, S2)) * iZB3);
         const double dp = gm1g * (om - Z * dv2 + hD * dv2 * isq);
-        const double fp = 1.0 - dp + hB2 * dv2 + SB2 * iZ2 * iZ;
+        const double fp = 1.0 - dp + hB2 * dv2 + SB2 * iZ3;
         double dZ = nr_div(f, fp);
         // A step within the tolerance ends the iteration: Z, 1/Z, 1/(Z + B^2),
         // v^2 and sqrt(1 - v^2) move along their first derivatives instead of
