@@ -416,6 +416,13 @@ int echo_selftest_conversions(long long n, unsigned long long seed, unsigned lon
  * hashed values (both signs, exponents -300..300): atomically maxes the
  * largest distance in ulp into *dev_max_ulp (device, caller-zeroed). */
 int echo_selftest_recip(long long n, unsigned long long seed, unsigned long long *dev_max_ulp, void *cuda_stream);
+/* Method: one Newton-Raphson step r <- r + r (1 - d r) of a reciprocal.
+ * The same check for the one-step reciprocal that forms the c2p Newton
+ * step's quotient dZ = f / f' (its error perturbs only the next iterate):
+ * the largest distance in ulp from the IEEE quotient into *dev_max_ulp
+ * (device, caller-zeroed) over the same hashed values. */
+int echo_selftest_recip1(long long n, unsigned long long seed, unsigned long long *dev_max_ulp,
+                         void *cuda_stream);
 /* Method: IEEE 754 binary64 exponent arithmetic (exact scaling by 2^k).
  * Self-check of the library's integer-pipe scaling by powers of two (the
  * exponent-field add the FP64 kernels use for alpha times a difference in

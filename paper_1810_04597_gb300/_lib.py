@@ -101,6 +101,7 @@ _SIGS = {
     "echo_counters": (ctypes.c_int, [_P, ctypes.POINTER(echo_totals)]),
     "echo_selftest_conversions": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_selftest_recip": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
+    "echo_selftest_recip1": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_selftest_scale2": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_selftest_mp5_accept": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_ulonglong, _P, _P]),
     "echo_selftest_dfma_blocks": (ctypes.c_int, []),
@@ -516,6 +517,11 @@ def echo_selftest_mp5_accept(n, seed, dev_mismatch, stream_handle: int = 0):
 def echo_selftest_recip(n, seed, dev_max, stream_handle: int = 0):
     _plain(load().echo_selftest_recip(int(n), ctypes.c_ulonglong(seed), _P(_dev_any(dev_max, "max")),
                                       _P(stream_handle)), "echo_selftest_recip")
+
+
+def echo_selftest_recip1(n, seed, dev_max, stream_handle: int = 0):
+    _plain(load().echo_selftest_recip1(int(n), ctypes.c_ulonglong(seed), _P(_dev_any(dev_max, "max")),
+                                       _P(stream_handle)), "echo_selftest_recip1")
 
 
 def echo_selftest_conversions(n, seed, dev_counter, stream_handle: int = 0):

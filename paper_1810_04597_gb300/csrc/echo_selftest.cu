@@ -63,8 +63,10 @@ __global__ void k_check_conversions(long long n, unsigned long long seed, unsign
         atomicAdd(mismatch, bad);
 }
 
-// Largest distance in ulp between nr_recip(d) and the IEEE quotient 1/d over
-// hashed d of both signs with exponents across [-300, 300].
+// Largest distance in ulp between nr_recip(d) (STEPS 2) or nr_recip1(d)
+// (STEPS 1) and the IEEE quotient 1/d over hashed d of both signs with
+// exponents across [-300, 300].
+template <int STEPS>
 __global__ void k_check_recip(long long n, unsigned long long seed, unsigned long long *max_ulp)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,7 +76,8 @@ __global__ void k_check_recip(long long n, unsigned long long seed, unsigned lon
     const unsigned long long e = 1023ULL - 300ULL + (h >> 52) % 601ULL;
     const unsigned long long m = mix64(h) & 0xfffffffffffffULL;
     const double d = __longlong_as_double((long long)(((h & 1ULL) << 63) | (e << 52) | m));
-    const long long a = __double_as_longlong(nr_recip(d)), b = __double_as_longlong(1.0 / d);
+    const double r = STEPS == 2 ? nr_recip(d) : nr_recip1(d);
+    const long long a = __double_as_longlong(r), b = __double_as_longlong(1.0 / d);
     const unsigned long long dist = (unsigned long long)(a > b ? a - b : b - a);
     atomicMax(max_ulp, dist);
 }
@@ -217,8 +220,18 @@ extern "C" int echo_selftest_recip(long long n, unsigned long long seed, unsigne
 {
     if (n < 1 || !dev_max_ulp)
         return ECHO_EINVAL;
-    echo::k_check_recip<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, seed,
-                                                                                                 dev_max_ulp);
+    echo::k_check_recip<2><<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, seed,
+                                                                                                    dev_max_ulp);
+    return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
+}
+
+extern "C" int echo_selftest_recip1(long long n, unsigned long long seed, unsigned long long *dev_max_ulp,
+                                    void *stream)
+{
+    if (n < 1 || !dev_max_ulp)
+        return ECHO_EINVAL;
+    echo::k_check_recip<1><<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, seed,
+                                                                                                    dev_max_ulp);
     return cudaGetLastError() == cudaSuccess ? ECHO_OK : ECHO_ECUDA;
 }
 

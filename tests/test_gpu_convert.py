@@ -34,6 +34,24 @@ def test_newton_raphson_reciprocal_within_two_ulp():
     assert int(mx.item()) <= 2
 
 
+def test_one_step_reciprocal_within_2_pow_minus_36():
+    """The c2p Newton step's quotient f / f' goes through one refinement
+    step of the hardware's approximate reciprocal.  A relative error e in
+    that quotient moves the converged Z by at most e tol Z (the last step
+    has |dZ| <= tol Z) and leaves Newton's convergence intact for e << 1;
+    with e below 2^-36 (at most 2^16 ulp of FP64) that shift is below
+    1.5e-11 tol Z, far inside the FP64 parity tolerance.  Measured on GB300:
+    8773 ulp (about 2^-39)."""
+    import torch
+    from paper_1810_04597_gb300 import _lib
+    mx = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for seed in (4, 5):
+        _lib.echo_selftest_recip1(1 << 22, seed, mx)
+    torch.cuda.synchronize()
+    print("max ulp distance of the one-step reciprocal:", int(mx.item()))
+    assert int(mx.item()) <= 1 << 16
+
+
 def test_integer_pipe_scaling_matches_fp64_products():
     """scale2 / alpha_times (exponent-field adds on the integer pipe) give
     the bit patterns of the FP64 products x*4, x*2, x*0.5 on 8 M values."""
