@@ -890,12 +890,17 @@ __device__ __forceinline__ void c2p_recip(double Z, double B2, double &iZ, doubl
 // Optional FP32 pre-refinement of the guess: up to 4 Newton steps of the same
 // residual in FP32 (stopping at |dZ| <= 4e-7 Z or at a step that leaves the
 // admissible set).  It only moves the starting point; the FP64 iterations
-// that follow decide convergence.
+// that follow decide convergence.  When it stops on the tolerance it also
+// hands back f' and dv^2/dZ of its last step (fp_out, dv2_out), provided the
+// terms of f' sum in absolute value to at most 1e3 |f'| (so that f' carries
+// a relative error below about 1e-4); otherwise fp_out = 0.
 __device__ __forceinline__ double c2p_refine_f32(double Zg, double S2d, double SB2d, double B2d, double Dd,
-                                                 double Ud, double gm1gd)
+                                                 double Ud, double gm1gd, float &fp_out, float &dv2_out)
 {
     const float S2 = d2f(S2d), SB2 = d2f(SB2d), B2 = d2f(B2d), D = d2f(Dd), U = d2f(Ud), gm1g = d2f(gm1gd);
     float Z = d2f(Zg);
+    fp_out = 0.0f;
+    dv2_out = 0.0f;
     for (int k = 0; k < 4; ++k) {
         const float iZ = 1.0f / Z, ZB = Z + B2, iZB = 1.0f / ZB;
         const float v2 = (S2 + SB2 * (2.0f * Z + B2) * iZ * iZ) * iZB * iZB;
@@ -913,14 +918,28 @@ __device__ __forceinline__ double c2p_refine_f32(double Zg, double S2d, double S
         const float Zn = Z - dZ;
         if (!(Zn > 0.0f))
             break;
-        Z = Zn;
-        if (fabsf(dZ) <= 4e-7f * Z)
+        if (fabsf(dZ) <= 4e-7f * Zn) {
+            const float mag = 1.0f + gm1g * (om + fabsf(Z * dv2) + fabsf(0.5f * D * dv2 * isq))
+                              + fabsf(0.5f * B2 * dv2) + SB2 * iZ * iZ * iZ;
+            if (fabsf(fp) <= 1e35f && mag <= 1e3f * fabsf(fp)) {
+                fp_out = fp;
+                dv2_out = dv2;
+            }
+            Z = Zn;
             break;
+        }
+        Z = Zn;
     }
     return f2d(Z);
 }
 
-template <typename M>
+// F32D: the first FP64 step after an FP32 refinement that stopped on its
+// tolerance takes f' and dv^2/dZ from that refinement (the FP32 storage
+// path, tol 1e-6): an inexact Newton step on the FP64 residual, whose
+// relative error e in f' (below about 1e-4) moves the result by at most
+// e |dZ| <= e tol Z.  Later steps, and every step without it, evaluate
+// both in FP64.
+template <bool F32D = false, typename M>
 __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], double tau, const double B[3],
                                                 double Zguess, double gm1g, const M &m, int maxit = NEWTON_MAXIT,
                                                 bool refine = false, double tol = NEWTON_TOL)
@@ -937,8 +956,9 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
     const double hB2 = scale2<-1>(B2), hSB2 = scale2<-1>(SB2), hD = scale2<-1>(Dc);
     C2PResult r;
     double Z = Zguess, iZ = 0.0, iZB = 0.0, v2 = 0.0;
+    float fp32 = 0.0f, dv2_32 = 0.0f;
     if (refine && is_pos(Z))
-        Z = c2p_refine_f32(Z, S2, SB2, B2, Dc, Uen, gm1g);
+        Z = c2p_refine_f32(Z, S2, SB2, B2, Dc, Uen, gm1g, fp32, dv2_32);
     int tries = 0;
     bool ok = true;
     for (;;) {
@@ -966,20 +986,27 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
         const double p = gm1g * (Z * om - Dc * sq);
         const double iZ2 = iZ * iZ;
         const double f = Z - p + (1.0 + v2) * hB2 - hSB2 * iZ2 - Uen;
-        const double iZ3 = iZ2 * iZ;
-        const double iZB3 = iZB * iZB * iZB;
-        // dv^2/dZ = -2 (S^2 Z^3 + (S.B)^2 (3 Z^2 + 3 Z B^2 + B^4)) / (Z^3 (Z + B^2)^3)
-        //         = -2 (S^2 + (S.B)^2 (Z (3 Z + 3 B^2) + B^4) / Z^3) / (Z + B^2)^3:
-        // Z^3 cancels against 1/Z^3, both terms stay positive (no
-        // cancellation), and 1/Z^3 serves f' below as well
-        const double P3 = fma(3.0 * Z, Z + B2, B2 * B2);
-        const double dv2 = -(scale2<1>(fma(SB2 * P3, iZ3, S2)) * iZB3);
-        const double dp = gm1g * (om - Z * dv2 + hD * dv2 * isq);
-        const double fp = 1.0 - dp + hB2 * dv2 + SB2 * iZ3;
-        // the step's quotient to about 2^-39: its error only perturbs the next
-        // iterate, which the iteration corrects, and at the final step (|dZ|
-        // <= tol Z) it moves Z by about 2^-39 tol Z
-        double dZ = nr_step_div(f, fp);
+        double dv2, dZ;
+        if (F32D && fp32 != 0.0f) {
+            dv2 = f2d(dv2_32);
+            dZ = f * f2d(__fdividef(1.0f, fp32));
+            fp32 = 0.0f;
+        } else {
+            const double iZ3 = iZ2 * iZ;
+            const double iZB3 = iZB * iZB * iZB;
+            // dv^2/dZ = -2 (S^2 Z^3 + (S.B)^2 (3 Z^2 + 3 Z B^2 + B^4)) / (Z^3 (Z + B^2)^3)
+            //         = -2 (S^2 + (S.B)^2 (Z (3 Z + 3 B^2) + B^4) / Z^3) / (Z + B^2)^3:
+            // Z^3 cancels against 1/Z^3, both terms stay positive (no
+            // cancellation), and 1/Z^3 serves f' below as well
+            const double P3 = fma(3.0 * Z, Z + B2, B2 * B2);
+            dv2 = -(scale2<1>(fma(SB2 * P3, iZ3, S2)) * iZB3);
+            const double dp = gm1g * (om - Z * dv2 + hD * dv2 * isq);
+            const double fp = 1.0 - dp + hB2 * dv2 + SB2 * iZ3;
+            // the step's quotient to about 2^-39: its error only perturbs the
+            // next iterate, which the iteration corrects, and at the final
+            // step (|dZ| <= tol Z) it moves Z by about 2^-39 tol Z
+            dZ = nr_step_div(f, fp);
+        }
         // A step within the tolerance ends the iteration: Z, 1/Z, 1/(Z + B^2),
         // v^2 and sqrt(1 - v^2) move along their first derivatives instead of
         // being evaluated again at Z - dZ (one division, the v^2 formula and a

@@ -287,9 +287,9 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
                 mfb = 1;
             }
             if constexpr (MK == 1)
-                r = c2p_newton(Dc, S, tc, B, start, ph.gm1g, MKS<double>(*mp), maxit, ref, tol);
+                r = c2p_newton<sizeof(R) == 4>(Dc, S, tc, B, start, ph.gm1g, MKS<double>(*mp), maxit, ref, tol);
             else
-                r = c2p_newton(Dc, S, tc, B, start, ph.gm1g, MFlat<double>(), maxit, ref, tol);
+                r = c2p_newton<sizeof(R) == 4>(Dc, S, tc, B, start, ph.gm1g, MFlat<double>(), maxit, ref, tol);
             if (!r.ok && pick == 1) {
                 mfb = 1;
                 const int first = r.iters;
@@ -302,9 +302,9 @@ __device__ __forceinline__ void c2p_body(const Geom &g, const Phys &ph, const Ar
             }
         } else {
             if constexpr (MK == 1)
-                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp), NEWTON_MAXIT, refine, tol);
+                r = c2p_newton<sizeof(R) == 4>(Dc, S, tc, B, zg, ph.gm1g, MKS<double>(*mp), NEWTON_MAXIT, refine, tol);
             else
-                r = c2p_newton(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>(), NEWTON_MAXIT, refine, tol);
+                r = c2p_newton<sizeof(R) == 4>(Dc, S, tc, B, zg, ph.gm1g, MFlat<double>(), NEWTON_MAXIT, refine, tol);
         }
         its = r.iters;
         calls = 1;
