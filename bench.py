@@ -90,8 +90,9 @@ FLOPS64 = {
          "emf_x": 236.4, "emf_y": 236.4, "emf_z": 236.4,
          "c2p": 359.5, "update": 79.0},
     # FP32-bulk path: only c2p computes in FP64 (previous-stage Z refined in
-    # FP32, then 1.01 FP64 Newton iterations per call)
-    32: {"c2p": 122.0},
+    # FP32, then 1.01 FP64 Newton iterations per call, the first with f'
+    # from the FP32 refinement)
+    32: {"c2p": 95.0},
 }
 # FP64-pipe thread instructions (DFMA + DADD + DMUL; ncu counts 64-bit
 # integer adds, compares and masks with the DADDs, and the kernels keep
@@ -102,7 +103,7 @@ FLOPS64 = {
 FP64_INSTR = {
     64: {"faces_x": 331.7, "faces_y": 331.7, "faces_z": 331.7, "emf_x": 167.8, "emf_y": 167.8, "emf_z": 167.8,
          "c2p": 251.3, "update": 53.0},
-    32: {"c2p": 87.0},
+    32: {"c2p": 69.0},
 }
 # Nominal FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2
 # DFMA lanes per SM and clock x 2 flop x 2.07 GHz (the 1.25 TFLOP/s figure);
@@ -142,7 +143,7 @@ TRAFFIC_PER_FACE64 = 337239040 / 2316324
 # (sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active).
 FP64_PIPE_BUSY = {64: {"faces_x": 0.880, "faces_y": 0.880, "faces_z": 0.880, "emf_x": 0.874, "emf_y": 0.874,
                        "emf_z": 0.874, "c2p": 0.869, "update": 0.827},
-                  32: {"c2p": 0.856}}
+                  32: {"c2p": 0.839}}
 # The FP64 pipe's nominal lane rate (thread instructions per second): 152 SMs
 # x 2 lanes per SM and clock x 2.07 GHz.  The FMA probe issues at 0.996 of
 # it; FMAs that read three distinct 64-bit registers issue at 0.80-0.97.
