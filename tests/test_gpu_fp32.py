@@ -87,3 +87,33 @@ def test_fp32_bulk_c2p_matches_fp64_solve():
         assert np.max(np.abs(P32[q] - P64[q]) / np.abs(P64[q])) <= 2e-7, q
     its = (c1["c2p_iters"] - c0["c2p_iters"]) / (c1["c2p_calls"] - c0["c2p_calls"])
     assert its <= 1.5, its
+
+
+def test_fp32_judging_step_both_derivative_branches():
+    """FP32 storage: a cell whose FP32 refinement meets its tolerance takes
+    f' for the FP64 judging step from that refinement; a cell without a
+    refinement (a cold start, Z = 0) evaluates f' in FP64.  With every other
+    cell cold the two branches mix within each warp, and both land on the
+    strict FP64 solution to 1e-10."""
+    from paper_1810_04597_gb300.echo import Solver
+    prob = inputs.sweep_box(48, seed=22)
+    s32 = Solver(prob, precision=32)
+    s32.set_prims()
+    s32.step()
+    st = s32.get_state()
+    z = s32.get_z()
+    rng = np.random.default_rng(6)
+    cold = (np.arange(z.size) % 2 == 0).reshape(z.shape)
+    zg = np.where(cold, 0.0, z * (1.0 + 1e-4 * rng.uniform(-1.0, 1.0, z.shape)))
+    s64 = Solver(prob, precision=64)
+    s64.set_state(st, z)
+    s32.set_state(st, zg)
+    t64 = s64.c2p(0)
+    t32 = s32.c2p(4)
+    assert t64["c2p_fail"] == 0 and t32["c2p_fail"] == 0
+    z64, z32 = s64.get_z(), s32.get_z()
+    rel = np.abs(z32 - z64) / z64
+    assert np.max(rel[cold]) <= 1e-10 and np.max(rel[~cold]) <= 1e-10, (np.max(rel[cold]), np.max(rel[~cold]))
+    P64, P32 = s64.get_prims(), s32.get_prims()
+    for q in (0, 4):
+        assert np.max(np.abs(P32[q] - P64[q]) / np.abs(P64[q])) <= 2e-7, q
