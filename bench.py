@@ -812,7 +812,8 @@ def fp32_c2p_roofline(prof, ms, zones, newton_iters, fp64_peak, fp64_src):
     return {"kernel": "c2p", "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
             "frac": achieved / fp64_peak, "peak_source": fp64_src, "flops_per_unit": alg,
             "flops_source": "the method's FP64 operations per cell at %.2f FP64 Newton iterations, oracle counting "
-                            "build (oracle/op_counts.json)" % newton_iters,
+                            "build (oracle/op_counts.json); the judging step's f' among them comes from the FP32 "
+                            "refinement" % newton_iters,
             "units_per_launch": zones,
             "kernel_flops_per_unit_ncu": FLOPS64[32]["c2p"],
             "kernel_flops_frac": zones * FLOPS64[32]["c2p"] / avg_s / 1e12 / fp64_peak,
