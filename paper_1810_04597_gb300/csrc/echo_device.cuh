@@ -974,6 +974,8 @@ __device__ __forceinline__ C2PResult c2p_newton(double Dc, const double S[3], do
             break;
         }
     }
+    if (tries != 0)
+        fp32 = 0.0f;        // the refinement's f' belongs to a Z since replaced
     int it = 0;
     bool conv = false;
     bool lin = false;       // the last step was taken to first order
